@@ -1,0 +1,360 @@
+"""FP64 oracle of the nonlocal + neural denoiser -- TEST INFRASTRUCTURE ONLY.
+
+Only tests/, __graft_entry__.smoke() and bench.py's cpu_baseline leg (and its
+reference arm) may import this package.  The product path (the CUDA library
+and its binding) never imports it, and it imports nothing from the product.
+
+Layout: the slow C restatement in oracle.c (built into _oracle.so by
+build()), wrapped here with numpy; the colour transform, the network
+composition of Eq. 2-3, the L1 loss, Adam and PSNR are plain numpy.
+
+Pins: every function here is checked by tests/test_oracle_*.py against
+library routines (scipy DCT, scipy Hadamard, numpy Kaiser, torch conv2d in
+FP64), closed forms (lambda3D = 0 identity, constant-image fixed point,
+NLM with h -> inf equals the window mean, repeated-tile matches), brute force
+on tiny images and finite differences.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "_oracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c with gcc (OpenMP, no FP contraction)."""
+    src = os.path.join(_HERE, "oracle.c")
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(src):
+        cmd = ["gcc", "-O2", "-std=gnu99", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+               "-o", _SO + ".tmp", src, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(_SO + ".tmp", _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_SO)
+        dp = ctypes.POINTER(ctypes.c_double)
+        ip = ctypes.POINTER(ctypes.c_int)
+        up = ctypes.POINTER(ctypes.c_ubyte)
+        i, d = ctypes.c_int, ctypes.c_double
+        L.or_dct8.argtypes = [dp]
+        L.or_dct2d_matrix.argtypes = [dp]
+        L.or_hadamard.argtypes = [i, dp]
+        L.or_kaiser.argtypes = [i, d, dp]
+        L.or_t3d.argtypes = [dp, i, i, dp]
+        L.or_grid.argtypes = [i, i, i, ip]
+        L.or_match.argtypes = [dp, i, i, i, i, i, i, d, ip, dp, ip, ip, up]
+        L.or_bm3d_pass1.argtypes = [dp, i, i, i, dp, i, i, i, i, d, d, d, d, dp, up, up]
+        L.or_bm3d_pass2.argtypes = [dp, dp, i, i, i, dp, i, i, i, i, d, d, dp, up, up]
+        L.or_nlm.argtypes = [dp, i, i, d, i, i, d, dp]
+        L.or_conv3x3.argtypes = [dp, i, i, i, i, dp, dp, i, dp]
+        L.or_conv3x3_bwd.argtypes = [dp, dp, i, i, i, i, dp, i, dp, dp, dp]
+        L.or_num_threads.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _dp(a):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _ip(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+def _up(a):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte))
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def num_threads() -> int:
+    return lib().or_num_threads()
+
+
+# --------------------------------------------------------------------------
+# Transforms and windows (exported for the pins)
+# --------------------------------------------------------------------------
+
+def dct8() -> np.ndarray:
+    C = np.empty((8, 8))
+    lib().or_dct8(_dp(C))
+    return C
+
+
+def dct2d_matrix() -> np.ndarray:
+    T = np.empty((64, 64))
+    lib().or_dct2d_matrix(_dp(T))
+    return T
+
+
+def hadamard(n: int) -> np.ndarray:
+    Hm = np.empty((n, n))
+    if lib().or_hadamard(n, _dp(Hm)):
+        raise ValueError("n must be a power of two <= 64")
+    return Hm
+
+
+def kaiser(M: int, beta: float) -> np.ndarray:
+    w = np.empty(M)
+    lib().or_kaiser(M, beta, _dp(w))
+    return w
+
+
+def t3d(G: np.ndarray, inverse: bool = False) -> np.ndarray:
+    """3D transform of a group G [n, 64] (2D DCT per patch, Hadamard along n)."""
+    G = _f64(G)
+    Z = np.empty_like(G)
+    if lib().or_t3d(_dp(G), G.shape[0], int(inverse), _dp(Z)):
+        raise ValueError("bad group size")
+    return Z
+
+
+def grid(L: int, k: int = 8, step: int = 3) -> np.ndarray:
+    n = lib().or_grid(L, k, step, None)
+    pos = np.zeros(max(n, 1), np.int32)
+    lib().or_grid(L, k, step, _ip(pos))
+    return pos[:n]
+
+
+# --------------------------------------------------------------------------
+# BM3D
+# --------------------------------------------------------------------------
+
+FLAG_TAU, FLAG_TIE, FLAG_THR = 1, 2, 4
+
+
+@dataclass
+class Pass:
+    """Parameters of one BM3D pass (standard BM3D notation)."""
+    patch: int = 8
+    step: int = 3
+    search: int = 39
+    n2: int = 16
+    tau: float = 2500.0
+    lambda3d: float = 2.7
+    beta: float = 2.0
+
+
+def default_passes(sigma: float, regime: int = 0):
+    """(hard, wiener) parameters.  regime 0: tau1 = 2500, tau2 = 400 for
+    sigma <= 40 and tau1 = 5000, tau2 = 3500 above; regime 1: 2500 / 400 always."""
+    hi = regime == 0 and sigma > 40.0
+    return (Pass(n2=16, tau=5000.0 if hi else 2500.0),
+            Pass(n2=32, tau=3500.0 if hi else 400.0))
+
+
+def match(guide: np.ndarray, p: Pass):
+    """Exhaustive block matching on one [H, W] guide.
+
+    Returns dict(idx [Ry, Rx, n2] int32, dist [Ry, Rx, n2+1], nkept, n, flag)."""
+    g = _f64(guide)
+    H, W = g.shape
+    Ry, Rx = len(grid(H, p.patch, p.step)), len(grid(W, p.patch, p.step))
+    R = Ry * Rx
+    idx = np.empty((R, p.n2), np.int32)
+    dist = np.empty((R, p.n2 + 1))
+    nk = np.empty(R, np.int32)
+    ng = np.empty(R, np.int32)
+    fl = np.empty(R, np.uint8)
+    rc = lib().or_match(_dp(g), H, W, p.patch, p.step, p.search, p.n2, p.tau,
+                        _ip(idx), _dp(dist), _ip(nk), _ip(ng), _up(fl))
+    if rc:
+        raise ValueError("or_match: bad arguments")
+    return dict(idx=idx.reshape(Ry, Rx, p.n2), dist=dist.reshape(Ry, Rx, p.n2 + 1),
+                nkept=nk.reshape(Ry, Rx), n=ng.reshape(Ry, Rx), flag=fl.reshape(Ry, Rx))
+
+
+def bm3d_pass1(img: np.ndarray, sig, p: Pass, band: float = 0.0):
+    """First pass on [C, H, W] (channel 0 guides matching).  Returns
+    (basic [C, H, W], pixel flags [H, W], group flags [Ry, Rx])."""
+    x = _f64(img)
+    C, H, W = x.shape
+    s = _f64(np.broadcast_to(np.asarray(sig, np.float64), (C,)))
+    out = np.empty_like(x)
+    pf = np.empty((H, W), np.uint8)
+    Ry, Rx = len(grid(H, p.patch, p.step)), len(grid(W, p.patch, p.step))
+    gf = np.empty((Ry, Rx), np.uint8)
+    rc = lib().or_bm3d_pass1(_dp(x), C, H, W, _dp(s), p.patch, p.step, p.search, p.n2, p.tau,
+                             p.lambda3d, p.beta, band, _dp(out), _up(pf), _up(gf))
+    if rc:
+        raise ValueError("or_bm3d_pass1 failed (%d)" % rc)
+    return out, pf, gf
+
+
+def bm3d_pass2(noisy: np.ndarray, basic: np.ndarray, sig, p: Pass):
+    """Second pass on [C, H, W] given the basic estimate.  Returns
+    (final [C, H, W], pixel flags [H, W], group flags [Ry, Rx])."""
+    y = _f64(noisy)
+    b = _f64(basic)
+    C, H, W = y.shape
+    s = _f64(np.broadcast_to(np.asarray(sig, np.float64), (C,)))
+    out = np.empty_like(y)
+    pf = np.empty((H, W), np.uint8)
+    Ry, Rx = len(grid(H, p.patch, p.step)), len(grid(W, p.patch, p.step))
+    gf = np.empty((Ry, Rx), np.uint8)
+    rc = lib().or_bm3d_pass2(_dp(y), _dp(b), C, H, W, _dp(s), p.patch, p.step, p.search, p.n2,
+                             p.tau, p.beta, _dp(out), _up(pf), _up(gf))
+    if rc:
+        raise ValueError("or_bm3d_pass2 failed (%d)" % rc)
+    return out, pf, gf
+
+
+# Full-range BT.601 RGB -> YCbCr rows (offsets drop out of the filter).
+YCC = np.array([[0.299, 0.587, 0.114],
+                [-0.168736, -0.331264, 0.5],
+                [0.5, -0.418688, -0.081312]])
+
+
+def rgb_to_ycc(x: np.ndarray) -> np.ndarray:
+    return np.einsum("ij,jhw->ihw", YCC, _f64(x))
+
+
+def ycc_to_rgb(x: np.ndarray) -> np.ndarray:
+    return np.einsum("ij,jhw->ihw", np.linalg.inv(YCC), _f64(x))
+
+
+def channel_sigmas(sigma: float, C: int) -> np.ndarray:
+    """Per-channel noise std after the colour transform: sigma * ||row||_2."""
+    if C == 1:
+        return np.array([float(sigma)])
+    return float(sigma) * np.sqrt((YCC ** 2).sum(axis=1))
+
+
+def bm3d(noisy: np.ndarray, sigma: float, regime: int = 0, hard: Pass = None, wiener: Pass = None):
+    """Both BM3D passes on one [C, H, W] image (C in {1, 3}); colour images are
+    matched on Y and filtered per YCbCr channel.  Returns (basic, final) in
+    the input colour space."""
+    C = noisy.shape[0]
+    dh, dw = default_passes(sigma, regime)
+    hard = hard or dh
+    wiener = wiener or dw
+    x = rgb_to_ycc(noisy) if C == 3 else _f64(noisy)
+    s = channel_sigmas(sigma, C)
+    basic, _, _ = bm3d_pass1(x, s, hard)
+    final, _, _ = bm3d_pass2(x, basic, s, wiener)
+    if C == 3:
+        return ycc_to_rgb(basic), ycc_to_rgb(final)
+    return basic, final
+
+
+# --------------------------------------------------------------------------
+# NL-means
+# --------------------------------------------------------------------------
+
+def nlm(noisy: np.ndarray, sigma: float, patch: int = 7, search: int = 21, h_over_sigma: float = 0.4,
+        h: float = None) -> np.ndarray:
+    """Pixel-wise NL-means of one [H, W] image; h defaults to h_over_sigma * sigma."""
+    y = _f64(noisy)
+    H, W = y.shape
+    out = np.empty_like(y)
+    hh = float(h_over_sigma * sigma) if h is None else float(h)
+    if lib().or_nlm(_dp(y), H, W, float(sigma), patch, search, hh, _dp(out)):
+        raise ValueError("or_nlm: bad arguments")
+    return out
+
+
+# --------------------------------------------------------------------------
+# Residual CNN (Eq. 2-3)
+# --------------------------------------------------------------------------
+
+def conv3x3(x: np.ndarray, w: np.ndarray, b: np.ndarray = None) -> np.ndarray:
+    """x [N, Cin, H, W], w [Cout, 3, 3, Cin], b [Cout] -> [N, Cout, H, W]."""
+    x = _f64(x)
+    w = _f64(w)
+    N, Cin, H, W = x.shape
+    Cout = w.shape[0]
+    y = np.empty((N, Cout, H, W))
+    lib().or_conv3x3(_dp(x), N, Cin, H, W, _dp(w), _dp(None if b is None else _f64(b)), Cout, _dp(y))
+    return y
+
+
+def conv3x3_bwd(x: np.ndarray, dy: np.ndarray, w: np.ndarray):
+    """(dx, dw, db) of conv3x3 given dy."""
+    x = _f64(x)
+    dy = _f64(dy)
+    w = _f64(w)
+    N, Cin, H, W = x.shape
+    Cout = w.shape[0]
+    dx = np.empty_like(x)
+    dw = np.empty_like(w)
+    db = np.empty(Cout)
+    lib().or_conv3x3_bwd(_dp(x), _dp(dy), N, Cin, H, W, _dp(w), Cout, _dp(dx), _dp(dw), _dp(db))
+    return dx, dw, db
+
+
+def cnn_forward(noisy: np.ndarray, pre: np.ndarray, params, keep: bool = False):
+    """Residual CNN on single-channel planes (Eq. 2-3).
+
+    noisy, pre: [N, H, W] (pre = BM3D or NLM output), 0..255 scale.
+    z = [pre / 255, noisy / 255]; K-1 conv+bias+ReLU layers and a final
+    conv+bias; output = pre + 255 * r.  params: list of (W [Cout,3,3,Cin], b).
+    With keep=True also returns the layer inputs and pre-activations."""
+    z = np.stack([_f64(pre) / 255.0, _f64(noisy) / 255.0], axis=1)
+    acts, pres = [z], []
+    h = z
+    for l, (w, b) in enumerate(params):
+        a = conv3x3(h, w, b)
+        pres.append(a)
+        h = np.maximum(a, 0.0) if l < len(params) - 1 else a
+        acts.append(h)
+    out = _f64(pre) + 255.0 * h[:, 0]
+    if keep:
+        return out, acts, pres
+    return out
+
+
+def l1_loss(out: np.ndarray, clean: np.ndarray) -> float:
+    """L = 1/N sum |x - (F(z) + BM3D(y))| (Eq. 2), N = number of pixels."""
+    return float(np.mean(np.abs(_f64(clean) - _f64(out))))
+
+
+def cnn_backward(noisy, pre, clean, params):
+    """Gradients of l1_loss(cnn_forward(...)) w.r.t. every (W, b).
+
+    dL/dout = sign(out - x) / N (0 where equal); dL/dr = 255 dL/dout."""
+    out, acts, pres = cnn_forward(noisy, pre, params, keep=True)
+    N = out.size
+    g_out = np.sign(out - _f64(clean)) / N
+    g = (255.0 * g_out)[:, None]
+    grads = [None] * len(params)
+    for l in range(len(params) - 1, -1, -1):
+        if l < len(params) - 1:
+            g = g * (pres[l] > 0)
+        dx, dw, db = conv3x3_bwd(acts[l], g, params[l][0])
+        grads[l] = (dw, db)
+        g = dx
+    return l1_loss(out, clean), grads
+
+
+def adam_step(param, grad, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam update (Kingma & Ba), bias-corrected; returns (param, m, v)."""
+    m = b1 * m + (1 - b1) * grad
+    v = b2 * v + (1 - b2) * grad * grad
+    mh = m / (1 - b1 ** t)
+    vh = v / (1 - b2 ** t)
+    return param - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+# --------------------------------------------------------------------------
+# Error metrics
+# --------------------------------------------------------------------------
+
+def psnr(out: np.ndarray, clean: np.ndarray, peak: float = 255.0) -> float:
+    """(C)PSNR of the output clipped to [0, peak]: MSE over every pixel and channel."""
+    e = np.clip(_f64(out), 0.0, peak) - _f64(clean)
+    mse = float(np.mean(e * e))
+    return float("inf") if mse == 0 else 10.0 * np.log10(peak * peak / mse)

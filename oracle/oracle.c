@@ -1,0 +1,622 @@
+/*
+ * FP64 oracle of the nonlocal + neural denoiser (TEST INFRASTRUCTURE ONLY).
+ *
+ * Only tests/, __graft_entry__.smoke() and bench.py's cpu_baseline / reference
+ * leg may load this library.  It shares no code, header, table or constant
+ * generator with the CUDA path: every matrix and window below is built here
+ * from its definition.
+ *
+ * The paper (Sec. II, Eq. 2-3) feeds a GPU BM3D (or NL-means) result and the
+ * noisy image to a residual CNN; it treats BM3D / NLM as black boxes.  The
+ * steps below restate the standard published definitions of those filters
+ * (BM3D: Dabov et al. 2007; NL-means: Buades et al. 2005) with the
+ * parameters of the workloads this library is checked on.  Every step is
+ * plain and slow on purpose: exhaustive matching with a full sort, the 2D
+ * transform as an explicit 64x64 Kronecker matrix, the group transform as an
+ * explicit Hadamard matrix, aggregation by direct accumulation, convolution
+ * by a 7-deep loop.
+ *
+ * Parallelism: OpenMP over reference patches / pixels.  Aggregation sums go
+ * to one private num/den buffer per thread, summed in thread order at the
+ * end (a summation-order detail only).
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_K 8          /* BM3D patch side; the 2D transform is 8x8 */
+#define OR_K2 64
+#define OR_NMAX 64      /* largest group size accepted */
+
+/* ------------------------------------------------------------------ */
+/* Transforms and windows                                              */
+/* ------------------------------------------------------------------ */
+
+/* Orthonormal DCT-II matrix: C[u][m] = a_u cos(pi (2m+1) u / 16),
+ * a_0 = sqrt(1/8), a_u = sqrt(2/8) = 1/2. */
+void or_dct8(double *C)
+{
+    for (int u = 0; u < OR_K; ++u)
+        for (int m = 0; m < OR_K; ++m) {
+            double a = (u == 0) ? sqrt(1.0 / OR_K) : sqrt(2.0 / OR_K);
+            C[u * OR_K + m] = a * cos(M_PI * (2.0 * m + 1.0) * u / (2.0 * OR_K));
+        }
+}
+
+/* 2D DCT as one 64x64 matrix acting on vec(P) (row-major, index i*8+j):
+ * T[u*8+v][i*8+j] = C[u][i] C[v][j], i.e. vec(C P C^T) = T vec(P). */
+void or_dct2d_matrix(double *T)
+{
+    double C[OR_K2];
+    or_dct8(C);
+    for (int u = 0; u < OR_K; ++u)
+        for (int v = 0; v < OR_K; ++v)
+            for (int i = 0; i < OR_K; ++i)
+                for (int j = 0; j < OR_K; ++j)
+                    T[(u * OR_K + v) * OR_K2 + i * OR_K + j] = C[u * OR_K + i] * C[v * OR_K + j];
+}
+
+/* Sylvester Hadamard matrix in natural order, scaled by 1/sqrt(n)
+ * (orthonormal and symmetric).  n must be a power of two. */
+int or_hadamard(int n, double *Hm)
+{
+    if (n < 1 || (n & (n - 1)) != 0 || n > OR_NMAX) return -1;
+    double s = 1.0 / sqrt((double)n);
+    for (int r = 0; r < n; ++r)
+        for (int c = 0; c < n; ++c) {
+            /* H[r][c] = (-1)^{popcount(r & c)} */
+            int bits = r & c, par = 0;
+            while (bits) { par ^= (bits & 1); bits >>= 1; }
+            Hm[r * n + c] = par ? -s : s;
+        }
+    return 0;
+}
+
+/* Modified Bessel function of the first kind, order 0, by its power series
+ * I0(x) = sum_k ((x/2)^k / k!)^2, summed until the term is negligible. */
+static double bessel_i0(double x)
+{
+    double sum = 1.0, term = 1.0, q = 0.25 * x * x;
+    for (int k = 1; k < 200; ++k) {
+        term *= q / ((double)k * (double)k);
+        sum += term;
+        if (term < 1e-17 * sum) break;
+    }
+    return sum;
+}
+
+/* Kaiser window of length M: w[m] = I0(beta sqrt(1 - (2m/(M-1) - 1)^2)) / I0(beta). */
+void or_kaiser(int M, double beta, double *w)
+{
+    for (int m = 0; m < M; ++m) {
+        double r = (M > 1) ? (2.0 * m / (M - 1) - 1.0) : 0.0;
+        double a = 1.0 - r * r;
+        if (a < 0) a = 0;
+        w[m] = bessel_i0(beta * sqrt(a)) / bessel_i0(beta);
+    }
+}
+
+/* 3D transform of a group G[n][64]: Z = H_n (G T^T), i.e. the 2D DCT of
+ * every patch followed by the normalised Hadamard transform along the group. */
+static void t3d_forward(const double *T, const double *Hn, int n, const double *G, double *Z)
+{
+    double T2[OR_NMAX * OR_K2];
+    for (int k = 0; k < n; ++k)
+        for (int a = 0; a < OR_K2; ++a) {
+            double s = 0.0;
+            for (int b = 0; b < OR_K2; ++b) s += T[a * OR_K2 + b] * G[k * OR_K2 + b];
+            T2[k * OR_K2 + a] = s;
+        }
+    for (int m = 0; m < n; ++m)
+        for (int a = 0; a < OR_K2; ++a) {
+            double s = 0.0;
+            for (int k = 0; k < n; ++k) s += Hn[m * n + k] * T2[k * OR_K2 + a];
+            Z[m * OR_K2 + a] = s;
+        }
+}
+
+/* Inverse of t3d_forward (both factors are orthonormal): G = T^T (H_n^T Z). */
+static void t3d_inverse(const double *T, const double *Hn, int n, const double *Z, double *G)
+{
+    double T2[OR_NMAX * OR_K2];
+    for (int k = 0; k < n; ++k)
+        for (int a = 0; a < OR_K2; ++a) {
+            double s = 0.0;
+            for (int m = 0; m < n; ++m) s += Hn[m * n + k] * Z[m * OR_K2 + a];
+            T2[k * OR_K2 + a] = s;
+        }
+    for (int k = 0; k < n; ++k)
+        for (int b = 0; b < OR_K2; ++b) {
+            double s = 0.0;
+            for (int a = 0; a < OR_K2; ++a) s += T[a * OR_K2 + b] * T2[k * OR_K2 + a];
+            G[k * OR_K2 + b] = s;
+        }
+}
+
+/* Exported for the transform pins. */
+int or_t3d(const double *G, int n, int inverse, double *Z)
+{
+    double T[OR_K2 * OR_K2], Hn[OR_NMAX * OR_NMAX];
+    if (or_hadamard(n, Hn)) return -1;
+    or_dct2d_matrix(T);
+    if (inverse) t3d_inverse(T, Hn, n, G, Z);
+    else t3d_forward(T, Hn, n, G, Z);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Block matching                                                      */
+/* ------------------------------------------------------------------ */
+
+/* Reference grid along one axis of length L: 0, step, 2 step, ... <= L-k,
+ * plus L-k itself when it is not on that lattice, so that every pixel is
+ * covered by at least one reference patch. */
+int or_grid(int L, int k, int step, int *pos)
+{
+    int last = L - k, n = 0;
+    if (last < 0 || step < 1) return 0;
+    for (int p = 0; p <= last; p += step) { if (pos) pos[n] = p; ++n; }
+    if (last % step != 0) { if (pos) pos[n] = last; ++n; }
+    return n;
+}
+
+typedef struct { double d; int idx; } cand_t;
+
+static int cand_cmp(const void *a, const void *b)
+{
+    const cand_t *x = (const cand_t *)a, *y = (const cand_t *)b;
+    if (x->d < y->d) return -1;
+    if (x->d > y->d) return 1;
+    return (x->idx > y->idx) - (x->idx < y->idx);
+}
+
+/* Largest power of two <= v (v >= 1). */
+static int pow2_floor(int v)
+{
+    int p = 1;
+    while (p * 2 <= v) p *= 2;
+    return p;
+}
+
+/* Flag bits (per reference / group). */
+#define OR_FLAG_TAU 1    /* a candidate's distance lies within 1e-5 tau of tau */
+#define OR_FLAG_TIE 2    /* two ranked neighbours within 1e-5 relative       */
+#define OR_FLAG_THR 4    /* a 3D coefficient lies within the band of lambda sigma */
+
+/* Exhaustive block matching for every reference patch of one guide image.
+ *
+ * d(P,Q) = ||P - Q||^2 / k^2 over every candidate whose top-left corner lies
+ * in the (search x search) window centred on the reference's top-left corner,
+ * clipped to the image.  The reference patch is always kept and always first;
+ * the other candidates with d <= tau follow in ascending (d, y*W + x) order.
+ * n = min(n2, largest power of two <= #kept).
+ *
+ * Outputs, R = Ry*Rx references in row-major grid order:
+ *   idx[R][n2]    row-major pixel index of each group member (-1 past #kept)
+ *   dist[R][n2+1] distances of ranks 0..n2 (-1 past #kept)
+ *   nkept[R], ngroup[R] (= n), flag[R] (OR_FLAG_TAU | OR_FLAG_TIE). */
+int or_match(const double *g, int H, int W, int k, int step, int search, int n2, double tau,
+             int *idx, double *dist, int *nkept, int *ngroup, unsigned char *flag)
+{
+    if (k != OR_K || H < k || W < k || search < 1 || (search & 1) == 0 || n2 < 1 || n2 > OR_NMAX)
+        return -1;
+    int gy[4096], gx[4096];
+    int Ry = or_grid(H, k, step, gy), Rx = or_grid(W, k, step, gx);
+    if (Ry > 4096 || Rx > 4096) return -1;
+    int hs = search / 2;
+    int ncand_max = search * search;
+#pragma omp parallel
+    {
+        cand_t *cl = (cand_t *)malloc(sizeof(cand_t) * (size_t)ncand_max);
+#pragma omp for schedule(static)
+        for (int r = 0; r < Ry * Rx; ++r) {
+            int y0 = gy[r / Rx], x0 = gx[r % Rx];
+            int nc = 0;
+            unsigned char fl = 0;
+            int ylo = y0 - hs < 0 ? 0 : y0 - hs, yhi = y0 + hs > H - k ? H - k : y0 + hs;
+            int xlo = x0 - hs < 0 ? 0 : x0 - hs, xhi = x0 + hs > W - k ? W - k : x0 + hs;
+            for (int y = ylo; y <= yhi; ++y)
+                for (int x = xlo; x <= xhi; ++x) {
+                    if (y == y0 && x == x0) continue;
+                    double s = 0.0;
+                    for (int i = 0; i < k; ++i)
+                        for (int j = 0; j < k; ++j) {
+                            double e = g[(size_t)(y0 + i) * W + x0 + j] - g[(size_t)(y + i) * W + x + j];
+                            s += e * e;
+                        }
+                    double d = s / (double)(k * k);
+                    if (fabs(d - tau) <= 1e-5 * tau) fl |= OR_FLAG_TAU;
+                    if (d <= tau) { cl[nc].d = d; cl[nc].idx = y * W + x; ++nc; }
+                }
+            qsort(cl, (size_t)nc, sizeof(cand_t), cand_cmp);
+            int kept = nc + 1;
+            int n = pow2_floor(kept < n2 ? kept : n2);
+            int *I = idx + (size_t)r * n2;
+            double *D = dist + (size_t)r * (n2 + 1);
+            I[0] = y0 * W + x0;
+            D[0] = 0.0;
+            for (int t = 1; t < n2; ++t) I[t] = (t < kept) ? cl[t - 1].idx : -1;
+            for (int t = 1; t <= n2; ++t) D[t] = (t < kept) ? cl[t - 1].d : -1.0;
+            /* near-ties among ranks 1..min(n, kept-1): order inside the group or the cut */
+            int last = n < kept - 1 ? n : kept - 1;
+            for (int t = 1; t < last; ++t) {
+                double a = cl[t - 1].d, b = cl[t].d;
+                if (!(a == 0.0 && b == 0.0) && fabs(b - a) <= 1e-5 * (a > b ? a : b)) fl |= OR_FLAG_TIE;
+            }
+            nkept[r] = kept;
+            ngroup[r] = n;
+            flag[r] = fl;
+        }
+        free(cl);
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Collaborative filtering and aggregation                            */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    int nthreads;
+    double *acc;   /* [nthreads][2*C*H*W]: num then den */
+} acc_t;
+
+static int acc_init(acc_t *a, size_t plane)
+{
+    int nt = 1;
+#ifdef _OPENMP
+    nt = omp_get_max_threads();
+#endif
+    a->nthreads = nt;
+    a->acc = (double *)calloc((size_t)nt * plane * 2, sizeof(double));
+    return a->acc ? 0 : -1;
+}
+
+/* out = num / den, summing the per-thread buffers in thread order. */
+static void acc_finish(acc_t *a, size_t plane, double *out)
+{
+    for (size_t p = 0; p < plane; ++p) {
+        double num = 0.0, den = 0.0;
+        for (int t = 0; t < a->nthreads; ++t) {
+            num += a->acc[(size_t)t * plane * 2 + p];
+            den += a->acc[(size_t)t * plane * 2 + plane + p];
+        }
+        out[p] = num / den;
+    }
+    free(a->acc);
+}
+
+/* Mark every pixel covered by the group's patches. */
+static void mark_group(unsigned char *pxflag, int W, const int *I, int n, unsigned char bits)
+{
+    if (!pxflag) return;
+    for (int t = 0; t < n; ++t) {
+        int y = I[t] / W, x = I[t] % W;
+        for (int i = 0; i < OR_K; ++i)
+            for (int j = 0; j < OR_K; ++j) {
+                unsigned char *p = &pxflag[(size_t)(y + i) * W + x + j];
+#pragma omp atomic
+                *p |= bits;
+            }
+    }
+}
+
+/* BM3D first pass (hard thresholding), on an image of C channels whose
+ * channel 0 is the matching guide (the Y channel for colour input).
+ *   img[C][H][W], sig[C] per-channel noise std, band: half-width of the
+ *   hard-threshold hazard band (absolute, added to 1e-5 lambda sigma).
+ * For each reference group: gather, 3D transform, zero |c| <= lambda sigma,
+ * N_har = #kept, inverse, weight 1/(sigma^2 N_har) (1 if N_har = 0), and
+ * Kaiser-windowed accumulation into num/den; basic = num / den.
+ * pxflag[H][W] (may be NULL) ORs the flags of every group covering a pixel;
+ * gflag[R] (may be NULL) receives each group's flags. */
+int or_bm3d_pass1(const double *img, int C, int H, int W, const double *sig,
+                  int k, int step, int search, int n2, double tau, double lambda3d, double beta,
+                  double band, double *basic, unsigned char *pxflag, unsigned char *gflag)
+{
+    if (C < 1 || k != OR_K) return -1;
+    int Ry = or_grid(H, k, step, NULL), Rx = or_grid(W, k, step, NULL);
+    int R = Ry * Rx;
+    if (R <= 0) return -1;
+    int *idx = (int *)malloc(sizeof(int) * (size_t)R * n2);
+    double *dist = (double *)malloc(sizeof(double) * (size_t)R * (n2 + 1));
+    int *nk = (int *)malloc(sizeof(int) * (size_t)R), *ng = (int *)malloc(sizeof(int) * (size_t)R);
+    unsigned char *fl = (unsigned char *)malloc((size_t)R);
+    if (!idx || !dist || !nk || !ng || !fl) return -2;
+    if (or_match(img, H, W, k, step, search, n2, tau, idx, dist, nk, ng, fl)) return -1;
+
+    double T[OR_K2 * OR_K2], kw[OR_K];
+    or_dct2d_matrix(T);
+    or_kaiser(OR_K, beta, kw);
+    size_t HW = (size_t)H * W, plane = (size_t)C * HW;
+    if (pxflag) memset(pxflag, 0, HW);
+    acc_t acc;
+    if (acc_init(&acc, plane)) return -2;
+
+#pragma omp parallel
+    {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        double *num = acc.acc + (size_t)tid * plane * 2, *den = num + plane;
+        double G[OR_NMAX * OR_K2], Z[OR_NMAX * OR_K2], E[OR_NMAX * OR_K2], Hn[OR_NMAX * OR_NMAX];
+#pragma omp for schedule(static)
+        for (int r = 0; r < R; ++r) {
+            int n = ng[r];
+            const int *I = idx + (size_t)r * n2;
+            unsigned char f = fl[r];
+            or_hadamard(n, Hn);
+            for (int c = 0; c < C; ++c) {
+                const double *ch = img + (size_t)c * HW;
+                double thr = lambda3d * sig[c];
+                for (int t = 0; t < n; ++t) {
+                    int y = I[t] / W, x = I[t] % W;
+                    for (int i = 0; i < OR_K; ++i)
+                        for (int j = 0; j < OR_K; ++j)
+                            G[t * OR_K2 + i * OR_K + j] = ch[(size_t)(y + i) * W + x + j];
+                }
+                t3d_forward(T, Hn, n, G, Z);
+                int nhar = 0;
+                for (int a = 0; a < n * OR_K2; ++a) {
+                    double m = fabs(Z[a]);
+                    if (fabs(m - thr) <= 1e-5 * thr + band) f |= OR_FLAG_THR;
+                    if (m > thr) ++nhar; else Z[a] = 0.0;
+                }
+                t3d_inverse(T, Hn, n, Z, E);
+                double w = nhar > 0 ? 1.0 / (sig[c] * sig[c] * nhar) : 1.0;
+                for (int t = 0; t < n; ++t) {
+                    int y = I[t] / W, x = I[t] % W;
+                    for (int i = 0; i < OR_K; ++i)
+                        for (int j = 0; j < OR_K; ++j) {
+                            size_t p = (size_t)c * HW + (size_t)(y + i) * W + x + j;
+                            double kk = w * kw[i] * kw[j];
+                            num[p] += kk * E[t * OR_K2 + i * OR_K + j];
+                            den[p] += kk;
+                        }
+                }
+            }
+            if (gflag) gflag[r] = f;
+            if (f) mark_group(pxflag, W, I, n, f);
+        }
+    }
+    acc_finish(&acc, plane, basic);
+    free(idx); free(dist); free(nk); free(ng); free(fl);
+    return 0;
+}
+
+/* BM3D second pass (empirical Wiener filtering).  Matching runs on channel 0
+ * of the basic estimate; for each group the basic-estimate group B and the
+ * noisy group Y (same positions) are 3D transformed, the Wiener gains
+ * w_a = B_a^2 / (B_a^2 + sigma^2) multiply Y, the product is inverted, and the
+ * group weight is 1/(sigma^2 sum_a w_a^2) (1 if that sum is 0). */
+int or_bm3d_pass2(const double *noisy, const double *basic, int C, int H, int W, const double *sig,
+                  int k, int step, int search, int n2, double tau, double beta,
+                  double *out, unsigned char *pxflag, unsigned char *gflag)
+{
+    if (C < 1 || k != OR_K) return -1;
+    int Ry = or_grid(H, k, step, NULL), Rx = or_grid(W, k, step, NULL);
+    int R = Ry * Rx;
+    if (R <= 0) return -1;
+    int *idx = (int *)malloc(sizeof(int) * (size_t)R * n2);
+    double *dist = (double *)malloc(sizeof(double) * (size_t)R * (n2 + 1));
+    int *nk = (int *)malloc(sizeof(int) * (size_t)R), *ng = (int *)malloc(sizeof(int) * (size_t)R);
+    unsigned char *fl = (unsigned char *)malloc((size_t)R);
+    if (!idx || !dist || !nk || !ng || !fl) return -2;
+    if (or_match(basic, H, W, k, step, search, n2, tau, idx, dist, nk, ng, fl)) return -1;
+
+    double T[OR_K2 * OR_K2], kw[OR_K];
+    or_dct2d_matrix(T);
+    or_kaiser(OR_K, beta, kw);
+    size_t HW = (size_t)H * W, plane = (size_t)C * HW;
+    if (pxflag) memset(pxflag, 0, HW);
+    acc_t acc;
+    if (acc_init(&acc, plane)) return -2;
+
+#pragma omp parallel
+    {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        double *num = acc.acc + (size_t)tid * plane * 2, *den = num + plane;
+        double Gb[OR_NMAX * OR_K2], Gy[OR_NMAX * OR_K2], Zb[OR_NMAX * OR_K2], Zy[OR_NMAX * OR_K2];
+        double E[OR_NMAX * OR_K2], Hn[OR_NMAX * OR_NMAX];
+#pragma omp for schedule(static)
+        for (int r = 0; r < R; ++r) {
+            int n = ng[r];
+            const int *I = idx + (size_t)r * n2;
+            or_hadamard(n, Hn);
+            for (int c = 0; c < C; ++c) {
+                const double *cb = basic + (size_t)c * HW, *cy = noisy + (size_t)c * HW;
+                double s2 = sig[c] * sig[c];
+                for (int t = 0; t < n; ++t) {
+                    int y = I[t] / W, x = I[t] % W;
+                    for (int i = 0; i < OR_K; ++i)
+                        for (int j = 0; j < OR_K; ++j) {
+                            size_t p = (size_t)(y + i) * W + x + j;
+                            Gb[t * OR_K2 + i * OR_K + j] = cb[p];
+                            Gy[t * OR_K2 + i * OR_K + j] = cy[p];
+                        }
+                }
+                t3d_forward(T, Hn, n, Gb, Zb);
+                t3d_forward(T, Hn, n, Gy, Zy);
+                double wsq = 0.0;
+                for (int a = 0; a < n * OR_K2; ++a) {
+                    double b2 = Zb[a] * Zb[a];
+                    double om = b2 / (b2 + s2);
+                    Zy[a] *= om;
+                    wsq += om * om;
+                }
+                t3d_inverse(T, Hn, n, Zy, E);
+                double w = wsq > 0.0 ? 1.0 / (s2 * wsq) : 1.0;
+                for (int t = 0; t < n; ++t) {
+                    int y = I[t] / W, x = I[t] % W;
+                    for (int i = 0; i < OR_K; ++i)
+                        for (int j = 0; j < OR_K; ++j) {
+                            size_t p = (size_t)c * HW + (size_t)(y + i) * W + x + j;
+                            double kk = w * kw[i] * kw[j];
+                            num[p] += kk * E[t * OR_K2 + i * OR_K + j];
+                            den[p] += kk;
+                        }
+                }
+            }
+            if (gflag) gflag[r] = fl[r];
+            if (fl[r]) mark_group(pxflag, W, I, n, fl[r]);
+        }
+    }
+    acc_finish(&acc, plane, out);
+    free(idx); free(dist); free(nk); free(ng); free(fl);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* NL-means                                                            */
+/* ------------------------------------------------------------------ */
+
+/* Half-sample symmetric reflection of index i into [0, L). */
+static int reflect(int i, int L)
+{
+    while (i < 0 || i >= L) {
+        if (i < 0) i = -i - 1;
+        if (i >= L) i = 2 * L - i - 1;
+    }
+    return i;
+}
+
+/* Pixel-wise NL-means.  For each pixel p and every q of the (search x search)
+ * window centred on p (clipped to the image, p itself included):
+ *   d2 = mean over the (patch x patch) neighbourhood of (y(p+t) - y(q+t))^2,
+ *        neighbourhoods read through half-sample symmetric reflection;
+ *   w  = exp(-max(d2 - 2 sigma^2, 0) / h^2);
+ * out(p) = sum_q w y(q) / sum_q w.  h = INFINITY gives w = 1. */
+int or_nlm(const double *y, int H, int W, double sigma, int patch, int search, double h, double *out)
+{
+    if (H < 1 || W < 1 || (patch & 1) == 0 || (search & 1) == 0) return -1;
+    int r = patch / 2, hs = search / 2;
+    double s2 = 2.0 * sigma * sigma, inv_np = 1.0 / (double)(patch * patch);
+#pragma omp parallel for schedule(static)
+    for (int py = 0; py < H; ++py)
+        for (int px = 0; px < W; ++px) {
+            double acc = 0.0, wsum = 0.0;
+            for (int qy = py - hs; qy <= py + hs; ++qy) {
+                if (qy < 0 || qy >= H) continue;
+                for (int qx = px - hs; qx <= px + hs; ++qx) {
+                    if (qx < 0 || qx >= W) continue;
+                    double d2 = 0.0;
+                    for (int ty = -r; ty <= r; ++ty)
+                        for (int tx = -r; tx <= r; ++tx) {
+                            double a = y[(size_t)reflect(py + ty, H) * W + reflect(px + tx, W)];
+                            double b = y[(size_t)reflect(qy + ty, H) * W + reflect(qx + tx, W)];
+                            d2 += (a - b) * (a - b);
+                        }
+                    d2 *= inv_np;
+                    double e = d2 - s2;
+                    if (e < 0) e = 0;
+                    double w = isinf(h) ? 1.0 : exp(-e / (h * h));
+                    acc += w * y[(size_t)qy * W + qx];
+                    wsum += w;
+                }
+            }
+            out[(size_t)py * W + px] = acc / wsum;
+        }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* 3x3 convolution (the residual CNN's only layer type)                */
+/* ------------------------------------------------------------------ */
+
+/* y[n][co][i][j] = b[co] + sum_{ci,ky,kx} w[co][ky][kx][ci] x[n][ci][i+ky-1][j+kx-1]
+ * (cross-correlation, zero padding of 1, NCHW activations, OHWI weights). */
+int or_conv3x3(const double *x, int N, int Cin, int H, int W, const double *w, const double *b,
+               int Cout, double *y)
+{
+    size_t HW = (size_t)H * W;
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int n = 0; n < N; ++n)
+        for (int co = 0; co < Cout; ++co)
+            for (int i = 0; i < H; ++i)
+                for (int j = 0; j < W; ++j) {
+                    double s = b ? b[co] : 0.0;
+                    for (int ky = 0; ky < 3; ++ky)
+                        for (int kx = 0; kx < 3; ++kx) {
+                            int yy = i + ky - 1, xx = j + kx - 1;
+                            if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+                            for (int ci = 0; ci < Cin; ++ci)
+                                s += w[((co * 3 + ky) * 3 + kx) * Cin + ci] *
+                                     x[((size_t)n * Cin + ci) * HW + (size_t)yy * W + xx];
+                        }
+                    y[((size_t)n * Cout + co) * HW + (size_t)i * W + j] = s;
+                }
+    return 0;
+}
+
+/* Gradients of or_conv3x3 given dy = dL/dy:
+ *   dx[n][ci][i][j]     = sum_{co,ky,kx} w[co][ky][kx][ci] dy[n][co][i-ky+1][j-kx+1]
+ *   dw[co][ky][kx][ci]  = sum_{n,i,j} dy[n][co][i][j] x[n][ci][i+ky-1][j+kx-1]
+ *   db[co]              = sum_{n,i,j} dy[n][co][i][j]
+ * Any of dx, dw, db may be NULL. */
+int or_conv3x3_bwd(const double *x, const double *dy, int N, int Cin, int H, int W,
+                   const double *w, int Cout, double *dx, double *dw, double *db)
+{
+    size_t HW = (size_t)H * W;
+    if (dx) {
+#pragma omp parallel for collapse(2) schedule(static)
+        for (int n = 0; n < N; ++n)
+            for (int ci = 0; ci < Cin; ++ci)
+                for (int i = 0; i < H; ++i)
+                    for (int j = 0; j < W; ++j) {
+                        double s = 0.0;
+                        for (int co = 0; co < Cout; ++co)
+                            for (int ky = 0; ky < 3; ++ky)
+                                for (int kx = 0; kx < 3; ++kx) {
+                                    int yy = i - ky + 1, xx = j - kx + 1;
+                                    if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+                                    s += w[((co * 3 + ky) * 3 + kx) * Cin + ci] *
+                                         dy[((size_t)n * Cout + co) * HW + (size_t)yy * W + xx];
+                                }
+                        dx[((size_t)n * Cin + ci) * HW + (size_t)i * W + j] = s;
+                    }
+    }
+    if (dw) {
+#pragma omp parallel for collapse(2) schedule(static)
+        for (int co = 0; co < Cout; ++co)
+            for (int t = 0; t < 9; ++t) {
+                int ky = t / 3, kx = t % 3;
+                for (int ci = 0; ci < Cin; ++ci) {
+                    double s = 0.0;
+                    for (int n = 0; n < N; ++n)
+                        for (int i = 0; i < H; ++i)
+                            for (int j = 0; j < W; ++j) {
+                                int yy = i + ky - 1, xx = j + kx - 1;
+                                if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+                                s += dy[((size_t)n * Cout + co) * HW + (size_t)i * W + j] *
+                                     x[((size_t)n * Cin + ci) * HW + (size_t)yy * W + xx];
+                            }
+                    dw[((co * 3 + ky) * 3 + kx) * Cin + ci] = s;
+                }
+            }
+    }
+    if (db) {
+        for (int co = 0; co < Cout; ++co) {
+            double s = 0.0;
+            for (int n = 0; n < N; ++n)
+                for (size_t p = 0; p < HW; ++p) s += dy[((size_t)n * Cout + co) * HW + p];
+            db[co] = s;
+        }
+    }
+    return 0;
+}
+
+int or_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
