@@ -1,0 +1,377 @@
+"""Benchmark of the hybrid denoiser (nonlocal BM3D stage + residual CNN).
+
+One step = one pass of the whole hot path over one batch: colour handling
+(grey here), BM3D pass 1 (matching, hard-threshold filtering, aggregation),
+BM3D pass 2 (matching on the basic estimate, Wiener filtering,
+aggregation), the 10-layer residual CNN of Eq. 2-3 and the FP64 error
+reduction, on 16 synthetic 1024 x 1024 grey images at sigma = 25 that are
+resident in HBM when the timed region starts.
+
+Prints one JSON line (see the keys below).  `--impl reference` times the
+FP64 oracle on the host cores instead (a bounded sample per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+H = W = 1024
+B = 16
+SIGMA = 25.0
+SEEDS0 = 100
+METRIC = "MPix/s BM3D+CNN at <=0.05 dB PSNR loss vs FP32 plain; served p50/p99 ms"
+FP32_PEAK_TFLOPS_NOTE = "FP32 ALU peak = 152 SM x 128 lanes x 2 FLOP/FMA x 2.07 GHz = 80.5 TFLOP/s"
+
+
+def workload_name(prec):
+    return "hybrid BM3D(%s)+CNN(10x32) denoise, 16 grey 1024x1024 synthetic images, sigma=25" % prec
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
+              "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) != len(self.FIELDS):
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work of the dominant kernels (per launch)
+# ---------------------------------------------------------------------------
+
+def match_pairs(Hh, Ww, step=3, search=39):
+    """Exact number of (reference, candidate) distance evaluations of one
+    matching launch over one image (candidates clipped to the image)."""
+    from paper_2403_03488_gb300 import api
+    hs = search // 2
+
+    def per_axis(L):
+        g = np.array(api.grid(L, 8, step))
+        return (np.minimum(L - 8, g + hs) - np.maximum(0, g - hs) + 1).astype(np.int64)
+
+    return int(per_axis(Hh).sum() * per_axis(Ww).sum())
+
+
+def algorithmic(kernel, launches_per_step, batch):
+    """(bound, unit, work per launch, peak, peak note) for a kernel name."""
+    peaks = {}
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        peaks = json.load(open(p))
+    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    if kernel.startswith("bm3d_match"):
+        pairs = match_pairs(H, W) * batch / (launches_per_step / 2.0)
+        return "alu", "TFLOP/s", 192.0 * pairs, fp32_peak, FP32_PEAK_TFLOPS_NOTE + " (derived, not measured)"
+    if kernel.startswith("conv3x3_fwd_fp32"):
+        flops = 2.0 * H * W * batch * (2 * 32 * 9 + 8 * 32 * 32 * 9 + 32 * 9) / launches_per_step
+        return "alu", "TFLOP/s", flops, fp32_peak, FP32_PEAK_TFLOPS_NOTE + " (derived, not measured)"
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    # fall back to bytes: read + write of the image planes
+    return "hbm", "GB/s", 8.0 * H * W * batch / launches_per_step, hbm, "measured hbm_gbs"
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2403_03488_gb300 import api, synth
+    from paper_2403_03488_gb300.autograd import ResidualNet
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    seeds = list(range(SEEDS0 + rank * B, SEEDS0 + rank * B + B))
+    clean, noisy = synth.make_batch(seeds, H, W, SIGMA)
+    noisy_d = torch.from_numpy(noisy).to(dev)
+    clean_d = torch.from_numpy(clean).to(dev)
+    out_d = torch.empty_like(noisy_d)
+    net = ResidualNet(10, 32, seed=0).to(dev)
+    weights = net.flat_weights()
+    prec = api.DN_BF16 if args.precision == "bf16" else api.DN_FP32
+    bp = api.default_bm3d_params(precision=prec)
+    cnn = api.make_cnn(weights, 10, 32, prec)
+    ws = torch.empty(api.hybrid_workspace_bytes(B, 1, H, W, api.DN_PREFILTER_BM3D, bp, cnn), dtype=torch.uint8,
+                     device=dev)
+    sse = torch.empty(B, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        api.denoise_hybrid(noisy_d, SIGMA, weights, prefilter_params=bp, cnn_precision=prec, out=out_d, workspace=ws)
+        api.error_reduce(out_d, clean_d)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    total_ms = 0.0
+    with api.profile() as prof:
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            step()
+            e1.record()
+            e1.synchronize()
+            total_ms += e0.elapsed_time(e1)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+
+    ms_per_step = total_ms / args.steps
+    mpix = B * H * W / 1e6
+    value = mpix * world / (ms_per_step / 1e3)
+
+    # quality of this step's output against the clean images (FP64 reduction)
+    sse_d, _ = api.error_reduce(out_d, clean_d)
+    mse = float(sse_d.sum().item()) / (B * H * W)
+    psnr_out = 10 * np.log10(255.0 ** 2 / mse)
+
+    # end to end through the public API with host buffers
+    noisy_h = torch.from_numpy(noisy).pin_memory()
+    out_h = torch.empty_like(noisy_h).pin_memory()
+    for _ in range(2):
+        x = noisy_h.to(dev, non_blocking=True)
+        api.denoise_hybrid(x, SIGMA, weights, prefilter_params=bp, cnn_precision=prec, out=out_d, workspace=ws)
+        out_h.copy_(out_d, non_blocking=True)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e2e_ms = 0.0
+    e2e_steps = max(2, min(args.steps, 5))
+    for _ in range(e2e_steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        x = noisy_h.to(dev, non_blocking=True)
+        api.denoise_hybrid(x, SIGMA, weights, prefilter_params=bp, cnn_precision=prec, out=out_d, workspace=ws)
+        out_h.copy_(out_d, non_blocking=True)
+        e1.record()
+        e1.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = mpix * world / (e2e_ms / e2e_steps / 1e3)
+
+    res = prof.result
+    launches = sum(c for c, _ in res.values())
+    top = max(res.items(), key=lambda kv: kv[1][1])
+    kname, (kl, kms) = top
+    per_step = kl / args.steps
+    bound, unit, work, peak, peak_note = algorithmic(kname, per_step, B)
+    avg_ms = kms / kl
+    achieved = work / (avg_ms / 1e3) / (1e12 if unit == "TFLOP/s" else 1e9)
+    traffic = load_traffic(kname)
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    line = {
+        "metric": METRIC,
+        "value": round(value, 3),
+        "unit": "MPix/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_per_step, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if prec == api.DN_FP32 else "bf16",
+        "data": "synthetic (seeded piecewise-smooth + gratings + repeated tile, AWGN sigma=25)",
+        "config": {"workload": workload_name(args.precision), "global_batch": B * world, "image": [H, W],
+                   "channels": 1, "sigma": SIGMA, "cnn": "10 layers x 32 ch, random init (He, seed 0)",
+                   "l2": "flushed between timed steps (256 MB write)", "parallelism": "replicas (dp%d)" % world},
+        "psnr_db": round(psnr_out, 3),
+        "e2e": {"value": round(e2e_value, 3), "unit": "MPix/s", "h2d_bytes_per_step": int(noisy_h.numel() * 4),
+                "d2h_bytes_per_step": int(out_h.numel() * 4)},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": bound, "kernel": kname, "achieved": round(achieved, 3), "peak": round(peak, 1),
+                     "unit": unit, "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "avg_launch_ms": round(avg_ms, 4), "peak_source": peak_note},
+        "kernels": {k: {"launches": c, "ms": round(t, 3), "share": round(t / sum(x[1] for x in res.values()), 4)}
+                    for k, (c, t) in sorted(res.items(), key=lambda kv: -kv[1][1])},
+        "clocks": clk,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_side)
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def load_traffic(kname):
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(p):
+        t = json.load(open(p))
+        v = t.get(kname)
+        return v
+    return None
+
+
+# ---------------------------------------------------------------------------
+# the oracle on host cores
+# ---------------------------------------------------------------------------
+
+def oracle_step(side):
+    """FP64 oracle BM3D (both passes) + residual CNN on one side x side crop of
+    image 0 of the workload; returns (seconds, megapixels)."""
+    import oracle
+    from paper_2403_03488_gb300 import synth
+    from paper_2403_03488_gb300.synth import he_normal_weights
+    clean, noisy = synth.make_batch([SEEDS0], H, W, SIGMA)
+    crop = noisy[0, :, :side, :side].astype(np.float64)
+    params = he_normal_weights(0, 10, 32)
+    t0 = time.perf_counter()
+    _, final = oracle.bm3d(crop, SIGMA)
+    oracle.cnn_forward(crop[:, :, :], final, params)
+    dt = time.perf_counter() - t0
+    return dt, side * side / 1e6
+
+
+def cpu_baseline(side):
+    import oracle
+    oracle.build()
+    dt, mp = oracle_step(side)
+    return {"value": round(mp / dt, 5), "unit": "MPix/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "FP64 oracle BM3D (both passes) + 10x32 CNN forward on one %dx%d crop of image 0 "
+                      "(%.1f s)" % (side, side, dt)}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    for _ in range(args.warmup):
+        oracle_step(64)
+    total, mp = 0.0, 0.0
+    for _ in range(args.steps):
+        dt, m = oracle_step(args.ref_side)
+        total += dt
+        mp += m
+    value = mp / total
+    line = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": round(value, 5),
+        "unit": "MPix/s",
+        "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(1e3 * total / args.steps, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic (seeded piecewise-smooth + gratings + repeated tile, AWGN sigma=25)",
+        "config": {"workload": workload_name("fp64 oracle"), "sample_per_step": "%dx%d crop of image 0" % (
+            args.ref_side, args.ref_side)},
+        "cpu_baseline": {"value": round(value, 5), "unit": "MPix/s", "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": "%dx%d crop per step" % (args.ref_side, args.ref_side)},
+        "e2e": {"value": round(value, 5), "unit": "MPix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default=os.environ.get("DN_BENCH_PRECISION", "fp32"), choices=["fp32", "bf16"])
+    ap.add_argument("--cpu-side", type=int, default=384)
+    ap.add_argument("--ref-side", type=int, default=192)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup) if args.impl == "ours" else args.warmup
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,230 @@
+/*
+ * denoise.h -- C ABI of the GB300 nonlocal + neural denoiser (libdenoise.so).
+ *
+ * The method (Sec. II, Fig. 1, Eq. 2-3): a nonlocal filter (BM3D, or NL-means
+ * as the cheaper variant, Sec. IV-A) denoises the noisy image y of the AWGN
+ * model y = x + n (Eq. 1); a lightweight residual CNN takes
+ * z = Concatenate(BM3D(y), y) (Eq. 3) and its output F(z) is added to the
+ * filter output (Eq. 2).  The paper uses BM3D / NLM as given components; the
+ * filter steps below are the standard published definitions (BM3D: block
+ * matching, 3D DCT x Walsh-Hadamard collaborative hard thresholding or
+ * Wiener filtering, Kaiser-windowed aggregation; NL-means: patch-similarity
+ * weighted average).
+ *
+ * Conventions shared by every entry point
+ *   - Images are contiguous NCHW float32 on the DEVICE, [B][C][H][W], on a
+ *     0..255 scale, C in {1, 3}.  Colour images are converted to YCbCr
+ *     (full-range BT.601), matched on Y and filtered per channel with the
+ *     per-channel noise std sigma * ||row_c||_2, then converted back.
+ *   - sigma is a HOST array of B floats (noise std per image, 0..255 scale).
+ *   - The caller owns every buffer, including the device workspace; the
+ *     library never allocates device memory, never synchronises the stream
+ *     and issues all work asynchronously on `stream` (0 = legacy default).
+ *   - Errors: argument errors are detected on the host and returned BEFORE
+ *     any launch (nothing is written).  A launch failure returns DN_ECUDA.
+ *     Outputs are unspecified after any error.  No C++ exception crosses
+ *     the ABI.  Calls are thread-safe as long as concurrent calls use
+ *     distinct workspaces and output buffers.
+ *   - Results are unclipped floats.
+ */
+#ifndef DENOISE_H
+#define DENOISE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *dn_stream_t; /* == cudaStream_t */
+
+typedef enum {
+    DN_OK = 0,
+    DN_EINVAL = -1,       /* bad argument (size, sigma <= 0, C not in {1,3}, ...) */
+    DN_ENOMEM = -2,       /* workspace smaller than the *_workspace_bytes query  */
+    DN_ECUDA = -3,        /* a CUDA launch or runtime call failed                */
+    DN_EDEVICE = -4,      /* a kernel reported an error through its status word  */
+    DN_EUNSUPPORTED = -5  /* valid but not implemented combination               */
+} dn_status;
+
+typedef enum { DN_FP32 = 0, DN_BF16 = 1 } dn_precision;
+typedef enum { DN_PREFILTER_BM3D = 0, DN_PREFILTER_NLM = 1 } dn_prefilter;
+
+/* One BM3D pass.  Distances are mean squared differences over the patch. */
+typedef struct {
+    int patch;       /* patch side; only 8 is supported                        */
+    int step;        /* reference grid step (3): 0, step, ... plus L-patch     */
+    int search;      /* odd side of the search window of top-left corners (39) */
+    int n2;          /* largest group size, a power of two in [1, 32]          */
+    float tau;       /* keep candidates with d <= tau (sigma <= 40)            */
+    float tau_high;  /* tau used when sigma > 40 and sigma_regime == 0         */
+    float lambda3d;  /* hard threshold lambda3d * sigma (first pass only)      */
+    float beta;      /* Kaiser window beta for aggregation                     */
+} dn_bm3d_pass;
+
+typedef struct {
+    dn_bm3d_pass hard;    /* first pass: hard thresholding  (n2 16, tau 2500) */
+    dn_bm3d_pass wiener;  /* second pass: Wiener filtering  (n2 32, tau 400)  */
+    int precision;        /* dn_precision of the group transforms / matching   */
+    int sigma_regime;     /* 0: tau_high above sigma 40; 1: tau at every sigma */
+} dn_bm3d_params;
+
+typedef struct {
+    int patch;           /* odd patch side (7)                 */
+    int search;          /* odd search window side (21)        */
+    float h_over_sigma;  /* filtering parameter h / sigma (0.4) */
+} dn_nlm_params;
+
+/* Residual CNN of Sec. II (Fig. 1): `layers` 3x3 convolutions, the first
+ * `layers-1` followed by ReLU, `width` hidden channels, 2 input channels
+ * (prefilter/255, noisy/255, Eq. 3) and 1 output channel r; the result is
+ * prefilter + 255 r (Eq. 2).  Colour images run the single-channel network on
+ * each RGB channel.
+ * `weights` is a DEVICE pointer to FP32 parameters, layer by layer:
+ *   W_l [Cout][3][3][Cin] then b_l [Cout]; see dn_cnn_param_count(). */
+typedef struct {
+    int layers;            /* K >= 2 (10) */
+    int width;             /* hidden channels, 32 (the BF16 path needs 32) */
+    const float *weights;  /* device, caller-owned */
+    int precision;         /* DN_FP32: FP32 SIMT kernels; DN_BF16: tcgen05 BF16 */
+} dn_cnn;
+
+/* ---- parameters ---------------------------------------------------------- */
+
+/* Defaults: hard {8, 3, 39, 16, 2500, 5000, 2.7, 2}, wiener {8, 3, 39, 32,
+ * 400, 3500, 0, 2}, precision DN_FP32, sigma_regime 0. */
+void dn_bm3d_default_params(dn_bm3d_params *p);
+/* Defaults: {7, 21, 0.4}. */
+void dn_nlm_default_params(dn_nlm_params *p);
+/* Number of floats in a dn_cnn weight buffer. */
+size_t dn_cnn_param_count(int layers, int width);
+/* Number of reference positions along an axis of length L (grid 0, step, ...
+ * plus L - patch); writes them to pos[] when pos != NULL.  0 if L < patch. */
+int dn_bm3d_grid(int L, int patch, int step, int *pos);
+
+/* ---- workspace queries (bytes, 256-byte aligned sub-buffers) ------------ */
+
+size_t dn_bm3d_workspace_bytes(int B, int C, int H, int W, const dn_bm3d_params *p);
+size_t dn_nlm_workspace_bytes(int B, int C, int H, int W, const dn_nlm_params *p);
+size_t dn_hybrid_workspace_bytes(int B, int C, int H, int W, int prefilter, const void *prefilter_params,
+                                 const dn_cnn *cnn);
+
+/* ---- the three denoisers ------------------------------------------------- */
+
+/* BM3D, both passes (standard definition; the paper's BM3D-G stage, Sec. II).
+ * noisy/out: device [B][C][H][W] (may not alias); H, W >= patch. */
+dn_status denoise_bm3d(const float *noisy, float *out, int B, int C, int H, int W, const float *sigma,
+                       const dn_bm3d_params *p, void *workspace, size_t ws_bytes, dn_stream_t stream);
+
+/* NL-means (the paper's NLM-G stage, Sec. IV-A): for each pixel, the average
+ * of the search window weighted by w = exp(-max(d2 - 2 sigma^2, 0) / h^2),
+ * d2 the mean squared difference of the patch x patch neighbourhoods
+ * (half-sample symmetric reflection at the border), h = h_over_sigma *
+ * sigma; colour weights come from Y.  H, W >= 4. */
+dn_status denoise_nlm(const float *noisy, float *out, int B, int C, int H, int W, const float *sigma,
+                      const dn_nlm_params *p, void *workspace, size_t ws_bytes, dn_stream_t stream);
+
+/* Nonlocal filter then residual CNN (Sec. II, Eq. 2-3).  prefilter_params
+ * points to a dn_bm3d_params (DN_PREFILTER_BM3D) or dn_nlm_params. */
+dn_status denoise_hybrid(const float *noisy, float *out, int B, int C, int H, int W, const float *sigma,
+                         int prefilter, const void *prefilter_params, const dn_cnn *cnn,
+                         void *workspace, size_t ws_bytes, dn_stream_t stream);
+
+const char *dn_strerror(dn_status s);
+
+/* ---- stage entry points (same kernels, exposed for stage-wise checks) ---- */
+
+/* Block matching of every reference patch of a guide plane.
+ * guide: device, plane b at guide + b * plane_stride, [H][W].
+ * tau: host [B] (threshold actually applied to image b).
+ * idx: device int32 [B][Ry][Rx][p->n2]: member 0 is the reference itself,
+ *      then the other candidates with d <= tau in ascending (d, y*W + x)
+ *      order; -1 past the kept count.
+ * n:   device int32 [B][Ry][Rx]: group size min(n2, 2^floor(log2 #kept)).
+ * precision: DN_FP32 (exhaustive FP32) or DN_BF16 (BF16 tensor-core
+ * prefilter with a proven margin, survivors re-ranked exactly in FP32). */
+dn_status dn_bm3d_match(const float *guide, size_t plane_stride, int B, int H, int W, const dn_bm3d_pass *p,
+                        const float *tau, int precision, int *idx, int *n, void *workspace, size_t ws_bytes,
+                        dn_stream_t stream);
+size_t dn_bm3d_match_workspace_bytes(int B, int H, int W, const dn_bm3d_pass *p, int precision);
+
+/* Collaborative hard thresholding + aggregation (first pass) given match lists.
+ * img: device [B][C][H][W] (already in the filtering colour space);
+ * sigma_c: host [B*C] per-channel noise std; idx/n as produced by
+ * dn_bm3d_match with p->n2; basic: device [B][C][H][W].
+ * workspace >= dn_bm3d_filter_workspace_bytes(B, C, H, W). */
+dn_status dn_bm3d_filter_hard(const float *img, const int *idx, const int *n, int B, int C, int H, int W,
+                              const float *sigma_c, const dn_bm3d_pass *p, int precision, float *basic,
+                              void *workspace, size_t ws_bytes, dn_stream_t stream);
+
+/* Collaborative Wiener filtering + aggregation (second pass) given match
+ * lists computed on the basic estimate. */
+dn_status dn_bm3d_filter_wiener(const float *noisy, const float *basic, const int *idx, const int *n,
+                                int B, int C, int H, int W, const float *sigma_c, const dn_bm3d_pass *p,
+                                int precision, float *out, void *workspace, size_t ws_bytes,
+                                dn_stream_t stream);
+size_t dn_bm3d_filter_workspace_bytes(int B, int C, int H, int W);
+
+/* RGB <-> YCbCr (full-range BT.601 rows; offsets omitted), device
+ * [B][3][H][W], in place allowed. */
+dn_status dn_rgb_to_ycc(const float *in, float *out, int B, int H, int W, dn_stream_t stream);
+dn_status dn_ycc_to_rgb(const float *in, float *out, int B, int H, int W, dn_stream_t stream);
+
+/* Per-image error reduction, FP64 on the device: sse[b] = sum over C*H*W of
+ * (clip(out, 0, 255) - ref)^2 and maxerr[b] = max |out - ref| (unclipped).
+ * sse, maxerr: device double [B]. */
+dn_status dn_error_reduce(const float *out, const float *ref, int B, size_t chw, double *sse, double *maxerr,
+                          dn_stream_t stream);
+
+/* ---- CNN layers (training and checks) ----------------------------------- */
+
+/* y = conv3x3(x, w) + b, optional ReLU.  FP32, NCHW: x [N][Cin][H][W],
+ * w [Cout][3][3][Cin], b [Cout] (may be NULL), y [N][Cout][H][W]. */
+dn_status dn_conv3x3_fwd(const float *x, const float *w, const float *b, float *y, int N, int Cin, int Cout,
+                         int H, int W, int relu, dn_stream_t stream);
+/* dx = conv3x3^T(dy, w) (zero padding); if mask != NULL, dx *= (mask > 0)
+ * elementwise (the ReLU of the layer that produced x).  dx [N][Cin][H][W]. */
+dn_status dn_conv3x3_bwd_data(const float *dy, const float *w, const float *mask, float *dx, int N, int Cin,
+                              int Cout, int H, int W, dn_stream_t stream);
+/* dw = sum_{n,y,x} dy (x) x_shifted, db = sum dy; OVERWRITES dw and db. */
+dn_status dn_conv3x3_bwd_weight(const float *x, const float *dy, float *dw, float *db, int N, int Cin, int Cout,
+                                int H, int W, dn_stream_t stream);
+
+/* Full network forward on single-channel planes (Eq. 2-3), FP32 or BF16:
+ * noisy, pre: device [N][H][W]; out [N][H][W] = pre + 255 F([pre, noisy]/255).
+ * workspace >= dn_cnn_workspace_bytes(N, H, W, cnn). */
+dn_status dn_cnn_forward(const float *noisy, const float *pre, float *out, int N, int H, int W, const dn_cnn *cnn,
+                         void *workspace, size_t ws_bytes, dn_stream_t stream);
+size_t dn_cnn_workspace_bytes(int N, int H, int W, const dn_cnn *cnn);
+
+/* Network input of Eq. 3 on planes: z [N][2][H][W] = [pre / 255, noisy / 255]. */
+dn_status dn_cnn_pack_input(const float *pre, const float *noisy, float *z, int N, int H, int W, dn_stream_t stream);
+/* Output of Eq. 2: out = pre + 255 r (count floats). */
+dn_status dn_cnn_residual_out(const float *pre, const float *r, float *out, size_t count, dn_stream_t stream);
+/* ReLU backward: out = g where y > 0, else 0 (count floats). */
+dn_status dn_relu_bwd(const float *g, const float *y, float *out, size_t count, dn_stream_t stream);
+
+/* L1 loss of Eq. 2 on the residual r: with out = pre + 255 r,
+ * dr = 255 sign(out - clean) / count (0 where equal); loss_sum (device double
+ * [1], accumulated, caller zeroes) += sum |out - clean|. */
+dn_status dn_l1_residual_grad(const float *r, const float *pre, const float *clean, float *dr, size_t count,
+                              double *loss_sum, dn_stream_t stream);
+/* Adam (Kingma & Ba) on count floats, step t >= 1 (bias correction). */
+dn_status dn_adam_step(float *param, const float *grad, float *m, float *v, size_t count, int t, float lr,
+                       float beta1, float beta2, float eps, dn_stream_t stream);
+
+/* ---- timing of individual kernels --------------------------------------- */
+
+/* When enabled, every kernel launch of this library on this host thread is
+ * bracketed by CUDA events on its own stream; dn_profile_read synchronises
+ * those events and returns, per kernel name, the launch count and the summed
+ * device milliseconds.  Disabled by default (no events recorded). */
+void dn_profile_enable(int on);
+int dn_profile_read(char *names, int name_stride, int max_kernels, int *launches, double *ms);
+void dn_profile_reset(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DENOISE_H */

@@ -57,7 +57,7 @@ def lib():
         L.or_match.argtypes = [dp, i, i, i, i, i, i, d, ip, dp, ip, ip, up]
         L.or_bm3d_pass1.argtypes = [dp, i, i, i, dp, i, i, i, i, d, d, d, d, dp, up, up]
         L.or_bm3d_pass2.argtypes = [dp, dp, i, i, i, dp, i, i, i, i, d, d, dp, up, up]
-        L.or_nlm.argtypes = [dp, i, i, d, i, i, d, dp]
+        L.or_nlm.argtypes = [dp, i, i, i, d, i, i, d, dp]
         L.or_conv3x3.argtypes = [dp, i, i, i, i, dp, dp, i, dp]
         L.or_conv3x3_bwd.argtypes = [dp, dp, i, i, i, i, dp, i, dp, dp, dp]
         L.or_num_threads.restype = ctypes.c_int
@@ -255,16 +255,34 @@ def bm3d(noisy: np.ndarray, sigma: float, regime: int = 0, hard: Pass = None, wi
 # NL-means
 # --------------------------------------------------------------------------
 
-def nlm(noisy: np.ndarray, sigma: float, patch: int = 7, search: int = 21, h_over_sigma: float = 0.4,
-        h: float = None) -> np.ndarray:
-    """Pixel-wise NL-means of one [H, W] image; h defaults to h_over_sigma * sigma."""
-    y = _f64(noisy)
-    H, W = y.shape
+def nlm_channels(img: np.ndarray, sigma: float, patch: int = 7, search: int = 21, h: float = None,
+                 h_over_sigma: float = 0.4) -> np.ndarray:
+    """NL-means of [C, H, W] with weights from channel 0 (the guide), applied to
+    every channel; h defaults to h_over_sigma * sigma (sigma of the guide)."""
+    y = _f64(img)
+    C, H, W = y.shape
     out = np.empty_like(y)
     hh = float(h_over_sigma * sigma) if h is None else float(h)
-    if lib().or_nlm(_dp(y), H, W, float(sigma), patch, search, hh, _dp(out)):
+    if lib().or_nlm(_dp(y), C, H, W, float(sigma), patch, search, hh, _dp(out)):
         raise ValueError("or_nlm: bad arguments")
     return out
+
+
+def nlm(noisy: np.ndarray, sigma: float, patch: int = 7, search: int = 21, h_over_sigma: float = 0.4,
+        h: float = None) -> np.ndarray:
+    """Pixel-wise NL-means of one [H, W] image."""
+    return nlm_channels(_f64(noisy)[None], sigma, patch, search, h, h_over_sigma)[0]
+
+
+def nlm_image(noisy: np.ndarray, sigma: float, patch: int = 7, search: int = 21,
+              h_over_sigma: float = 0.4) -> np.ndarray:
+    """NL-means of one [C, H, W] image (C in {1, 3}).  Colour images are
+    filtered in YCbCr with weights from Y (noise std sigma_Y) and converted back."""
+    C = noisy.shape[0]
+    if C == 1:
+        return nlm_channels(noisy, sigma, patch, search, h_over_sigma=h_over_sigma)
+    s = channel_sigmas(sigma, 3)[0]
+    return ycc_to_rgb(nlm_channels(rgb_to_ycc(noisy), s, patch, search, h_over_sigma=h_over_sigma))
 
 
 # --------------------------------------------------------------------------

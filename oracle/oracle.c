@@ -487,21 +487,26 @@ static int reflect(int i, int L)
     return i;
 }
 
-/* Pixel-wise NL-means.  For each pixel p and every q of the (search x search)
- * window centred on p (clipped to the image, p itself included):
- *   d2 = mean over the (patch x patch) neighbourhood of (y(p+t) - y(q+t))^2,
- *        neighbourhoods read through half-sample symmetric reflection;
+/* Pixel-wise NL-means on an image of C channels whose channel 0 is the guide.
+ * For each pixel p and every q of the (search x search) window centred on p
+ * (clipped to the image, p itself included):
+ *   d2 = mean over the (patch x patch) neighbourhood of (g(p+t) - g(q+t))^2,
+ *        neighbourhoods of the guide g read through half-sample symmetric
+ *        reflection;
  *   w  = exp(-max(d2 - 2 sigma^2, 0) / h^2);
- * out(p) = sum_q w y(q) / sum_q w.  h = INFINITY gives w = 1. */
-int or_nlm(const double *y, int H, int W, double sigma, int patch, int search, double h, double *out)
+ * out_c(p) = sum_q w y_c(q) / sum_q w for every channel c.  h = INFINITY gives
+ * w = 1. */
+int or_nlm(const double *y, int C, int H, int W, double sigma, int patch, int search, double h,
+           double *out)
 {
-    if (H < 1 || W < 1 || (patch & 1) == 0 || (search & 1) == 0) return -1;
+    if (C < 1 || C > 3 || H < 1 || W < 1 || (patch & 1) == 0 || (search & 1) == 0) return -1;
     int r = patch / 2, hs = search / 2;
+    size_t HW = (size_t)H * W;
     double s2 = 2.0 * sigma * sigma, inv_np = 1.0 / (double)(patch * patch);
 #pragma omp parallel for schedule(static)
     for (int py = 0; py < H; ++py)
         for (int px = 0; px < W; ++px) {
-            double acc = 0.0, wsum = 0.0;
+            double acc[3] = {0.0, 0.0, 0.0}, wsum = 0.0;
             for (int qy = py - hs; qy <= py + hs; ++qy) {
                 if (qy < 0 || qy >= H) continue;
                 for (int qx = px - hs; qx <= px + hs; ++qx) {
@@ -517,11 +522,11 @@ int or_nlm(const double *y, int H, int W, double sigma, int patch, int search, d
                     double e = d2 - s2;
                     if (e < 0) e = 0;
                     double w = isinf(h) ? 1.0 : exp(-e / (h * h));
-                    acc += w * y[(size_t)qy * W + qx];
+                    for (int c = 0; c < C; ++c) acc[c] += w * y[(size_t)c * HW + (size_t)qy * W + qx];
                     wsum += w;
                 }
             }
-            out[(size_t)py * W + px] = acc / wsum;
+            for (int c = 0; c < C; ++c) out[(size_t)c * HW + (size_t)py * W + px] = acc[c] / wsum;
         }
     return 0;
 }

@@ -1,0 +1,547 @@
+// C ABI of libdenoise: argument validation, workspace layout and the
+// composition of the kernels into the three denoisers.  See
+// include/denoise.h for the contract of every entry point.
+#include <climits>
+#include <cmath>
+#include <cstring>
+
+#include "common.cuh"
+
+using namespace dn;
+
+namespace {
+
+const double kYccRows[3][3] = {{0.299, 0.587, 0.114}, {-0.168736, -0.331264, 0.5}, {0.5, -0.418688, -0.081312}};
+
+// Noise std of channel c after the colour transform of white RGB noise.
+float channel_sigma(float sigma, int C, int c)
+{
+    if (C == 1) return sigma;
+    const double *r = kYccRows[c];
+    return (float)(sigma * std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]));
+}
+
+bool valid_image(int B, int C, int H, int W, int min_side)
+{
+    return B >= 1 && (C == 1 || C == 3) && H >= min_side && W >= min_side && (size_t)H * W <= (size_t)INT_MAX;
+}
+
+bool valid_sigmas(const float *sigma, int B)
+{
+    if (!sigma) return false;
+    for (int b = 0; b < B; ++b)
+        if (!(sigma[b] > 0.0f) || !std::isfinite(sigma[b])) return false;
+    return true;
+}
+
+bool valid_pass(const dn_bm3d_pass *p)
+{
+    if (!p) return false;
+    if (p->patch != 8 || p->step < 1 || p->search < 1 || (p->search & 1) == 0 || p->search > 127) return false;
+    if (p->n2 < 1 || p->n2 > 32 || (p->n2 & (p->n2 - 1)) != 0) return false;
+    if (!(p->tau > 0.0f) || !(p->tau_high > 0.0f) || !(p->lambda3d >= 0.0f) || !(p->beta >= 0.0f)) return false;
+    return true;
+}
+
+bool valid_bm3d(const dn_bm3d_params *p)
+{
+    return p && valid_pass(&p->hard) && valid_pass(&p->wiener) && (p->precision == DN_FP32 || p->precision == DN_BF16) &&
+           (p->sigma_regime == 0 || p->sigma_regime == 1);
+}
+
+bool valid_nlm(const dn_nlm_params *p)
+{
+    return p && p->patch >= 1 && (p->patch & 1) && p->patch <= 15 && p->search >= 1 && (p->search & 1) &&
+           p->search <= 41 && p->h_over_sigma > 0.0f && std::isfinite(p->h_over_sigma);
+}
+
+bool valid_cnn(const dn_cnn *c)
+{
+    return c && c->weights && c->layers >= 2 && c->layers <= 64 && c->width >= 1 && c->width <= 64 &&
+           (c->precision == DN_FP32 || c->precision == DN_BF16);
+}
+
+float tau_for(const dn_bm3d_pass &p, float sigma, int regime)
+{
+    return (regime == 0 && sigma > 40.0f) ? p.tau_high : p.tau;
+}
+
+// ---- workspace layouts (a null base computes the size) -------------------------
+
+struct Bm3dWs {
+    float *ycc;
+    int *idx;
+    int *n;
+    float *acc;
+    float *basic;
+    size_t bytes;
+};
+
+Bm3dWs bm3d_layout(void *base, int B, int C, int H, int W, const dn_bm3d_params *p)
+{
+    Carver cv(base);
+    const size_t HW = (size_t)H * W, R = (size_t)grid_count(H, 8, p->hard.step) * grid_count(W, 8, p->hard.step);
+    const size_t R2 = (size_t)grid_count(H, 8, p->wiener.step) * grid_count(W, 8, p->wiener.step);
+    const size_t Rm = R > R2 ? R : R2;
+    const int n2 = p->hard.n2 > p->wiener.n2 ? p->hard.n2 : p->wiener.n2;
+    Bm3dWs w;
+    w.ycc = C == 3 ? cv.take<float>((size_t)B * 3 * HW) : nullptr;
+    w.idx = cv.take<int>((size_t)B * Rm * n2);
+    w.n = cv.take<int>((size_t)B * Rm);
+    w.acc = cv.take<float>(4 * (size_t)B * C * HW);
+    w.basic = cv.take<float>((size_t)B * C * HW);
+    w.bytes = cv.off;
+    return w;
+}
+
+struct NlmWs {
+    float *ycc;
+    float *tmp;
+    size_t bytes;
+};
+
+NlmWs nlm_layout(void *base, int B, int C, int H, int W)
+{
+    Carver cv(base);
+    NlmWs w;
+    const size_t n = C == 3 ? (size_t)B * 3 * H * W : 0;
+    w.ycc = C == 3 ? cv.take<float>(n) : nullptr;
+    w.tmp = C == 3 ? cv.take<float>(n) : nullptr;
+    w.bytes = cv.off;
+    return w;
+}
+
+struct CnnWs {
+    float *z;
+    float *act[2];
+    size_t bytes;
+};
+
+CnnWs cnn_layout(void *base, int N, int H, int W, const dn_cnn *c)
+{
+    Carver cv(base);
+    const size_t HW = (size_t)H * W;
+    CnnWs w;
+    w.z = cv.take<float>((size_t)N * 2 * HW);
+    w.act[0] = cv.take<float>((size_t)N * c->width * HW);
+    w.act[1] = cv.take<float>((size_t)N * c->width * HW);
+    w.bytes = cv.off;
+    return w;
+}
+
+dn_status run_bm3d(const float *noisy, float *out, int B, int C, int H, int W, const float *sigma,
+                   const dn_bm3d_params *p, const Bm3dWs &w, cudaStream_t s)
+{
+    if (p->precision != DN_FP32) return DN_EUNSUPPORTED;
+    const size_t HW = (size_t)H * W, N = (size_t)B * C * HW;
+    const float *x = noisy;
+    if (C == 3) {
+        DN_TRY(colour(noisy, w.ycc, B, H, W, 0, s));
+        x = w.ycc;
+    }
+    float tau1[1024], tau2[1024], sig[3 * 1024];
+    for (int b0 = 0; b0 < B; b0 += 1024) {
+        const int nb = B - b0 < 1024 ? B - b0 : 1024;
+        for (int i = 0; i < nb; ++i) {
+            tau1[i] = tau_for(p->hard, sigma[b0 + i], p->sigma_regime);
+            tau2[i] = tau_for(p->wiener, sigma[b0 + i], p->sigma_regime);
+            for (int c = 0; c < C; ++c) sig[i * C + c] = channel_sigma(sigma[b0 + i], C, c);
+        }
+        const size_t off = (size_t)b0 * C * HW;
+        const size_t Nb = (size_t)nb * C * HW;
+        // pass 1: match on channel 0 of the noisy image, hard thresholding
+        DN_TRY(match_fp32(x + off, (size_t)C * HW, nb, H, W, p->hard, tau1, w.idx, w.n, s));
+        if (cudaMemsetAsync(w.acc, 0, 4 * Nb * sizeof(float), s) != cudaSuccess) return DN_ECUDA;
+        DN_TRY(filter_hard_fp32(x + off, w.idx, w.n, nb, C, H, W, sig, p->hard, w.acc, s));
+        DN_TRY(normalize(w.acc, w.basic + off, nb, C, H, W, s));
+        // pass 2: match on channel 0 of the basic estimate, Wiener filtering
+        DN_TRY(match_fp32(w.basic + off, (size_t)C * HW, nb, H, W, p->wiener, tau2, w.idx, w.n, s));
+        if (cudaMemsetAsync(w.acc, 0, 4 * Nb * sizeof(float), s) != cudaSuccess) return DN_ECUDA;
+        DN_TRY(filter_wiener_fp32(x + off, w.basic + off, w.idx, w.n, nb, C, H, W, sig, p->wiener, w.acc, s));
+        DN_TRY(normalize(w.acc, (C == 3 ? w.ycc : out) + off, nb, C, H, W, s));
+    }
+    if (C == 3) DN_TRY(colour(w.ycc, out, B, H, W, 1, s));
+    (void)N;
+    return DN_OK;
+}
+
+dn_status run_nlm(const float *noisy, float *out, int B, int C, int H, int W, const float *sigma,
+                  const dn_nlm_params *p, const NlmWs &w, cudaStream_t s)
+{
+    float sg[1024];
+    for (int b0 = 0; b0 < B; b0 += 1024) {
+        const int nb = B - b0 < 1024 ? B - b0 : 1024;
+        for (int i = 0; i < nb; ++i) sg[i] = channel_sigma(sigma[b0 + i], C, 0);
+        const size_t off = (size_t)b0 * C * H * W;
+        if (C == 3) {
+            DN_TRY(colour(noisy + off, w.ycc + off, nb, H, W, 0, s));
+            DN_TRY(nlm_launch(w.ycc + off, w.tmp + off, nb, C, H, W, sg, *p, s));
+            DN_TRY(colour(w.tmp + off, out + off, nb, H, W, 1, s));
+        } else {
+            DN_TRY(nlm_launch(noisy + off, out + off, nb, C, H, W, sg, *p, s));
+        }
+    }
+    return DN_OK;
+}
+
+dn_status run_cnn(const float *noisy, const float *pre, float *out, int N, int H, int W, const dn_cnn *c,
+                  const CnnWs &w, cudaStream_t s)
+{
+    if (c->precision != DN_FP32) return DN_EUNSUPPORTED;
+    DN_TRY(pack_input(pre, noisy, w.z, N, H, W, s));
+    const float *h = w.z;
+    int kin = 2;
+    size_t off = 0;
+    for (int l = 0; l < c->layers; ++l) {
+        const int kout = l == c->layers - 1 ? 1 : c->width;
+        const float *wl = c->weights + off;
+        const float *bl = wl + (size_t)kout * 9 * kin;
+        off += (size_t)kout * 9 * kin + kout;
+        float *y = w.act[l & 1];
+        DN_TRY(conv3x3_fwd_fp32(h, wl, bl, nullptr, y, N, kin, kout, H, W, l < c->layers - 1, false, s));
+        h = y;
+        kin = kout;
+    }
+    return residual_out(pre, h, out, (size_t)N * H * W, s);
+}
+
+}  // namespace
+
+#define DN_GUARD_BEGIN try {
+#define DN_GUARD_END \
+    }                \
+    catch (...) { return DN_ECUDA; }
+
+extern "C" {
+
+void dn_bm3d_default_params(dn_bm3d_params *p)
+{
+    if (!p) return;
+    p->hard = dn_bm3d_pass{8, 3, 39, 16, 2500.0f, 5000.0f, 2.7f, 2.0f};
+    p->wiener = dn_bm3d_pass{8, 3, 39, 32, 400.0f, 3500.0f, 0.0f, 2.0f};
+    p->precision = DN_FP32;
+    p->sigma_regime = 0;
+}
+
+void dn_nlm_default_params(dn_nlm_params *p)
+{
+    if (!p) return;
+    p->patch = 7;
+    p->search = 21;
+    p->h_over_sigma = 0.4f;
+}
+
+size_t dn_cnn_param_count(int layers, int width)
+{
+    if (layers < 2 || width < 1) return 0;
+    size_t total = 0;
+    int kin = 2;
+    for (int l = 0; l < layers; ++l) {
+        int kout = l == layers - 1 ? 1 : width;
+        total += (size_t)kout * 9 * kin + kout;
+        kin = kout;
+    }
+    return total;
+}
+
+int dn_bm3d_grid(int L, int patch, int step, int *pos)
+{
+    int n = grid_count(L, patch, step);
+    if (pos)
+        for (int i = 0; i < n; ++i) pos[i] = (i * step < L - patch) ? i * step : L - patch;
+    return n;
+}
+
+size_t dn_bm3d_workspace_bytes(int B, int C, int H, int W, const dn_bm3d_params *p)
+{
+    if (!valid_image(B, C, H, W, 8) || !valid_bm3d(p)) return 0;
+    return bm3d_layout(nullptr, B, C, H, W, p).bytes;
+}
+
+size_t dn_nlm_workspace_bytes(int B, int C, int H, int W, const dn_nlm_params *p)
+{
+    (void)p;
+    if (B < 1 || (C != 1 && C != 3)) return 0;
+    return nlm_layout(nullptr, B, C, H, W).bytes;
+}
+
+size_t dn_cnn_workspace_bytes(int N, int H, int W, const dn_cnn *cnn)
+{
+    if (N < 1 || H < 1 || W < 1 || !cnn || cnn->width < 1) return 0;
+    return cnn_layout(nullptr, N, H, W, cnn).bytes;
+}
+
+size_t dn_hybrid_workspace_bytes(int B, int C, int H, int W, int prefilter, const void *pp, const dn_cnn *cnn)
+{
+    if (!valid_image(B, C, H, W, 8) || !cnn) return 0;
+    size_t pre = align256((size_t)B * C * H * W * sizeof(float));
+    size_t f = prefilter == DN_PREFILTER_BM3D
+                   ? dn_bm3d_workspace_bytes(B, C, H, W, static_cast<const dn_bm3d_params *>(pp))
+                   : dn_nlm_workspace_bytes(B, C, H, W, static_cast<const dn_nlm_params *>(pp));
+    size_t c = dn_cnn_workspace_bytes(B * C, H, W, cnn);
+    return pre + (f > c ? f : c);
+}
+
+dn_status denoise_bm3d(const float *noisy, float *out, int B, int C, int H, int W, const float *sigma,
+                       const dn_bm3d_params *p, void *workspace, size_t ws_bytes, dn_stream_t stream)
+{
+    DN_GUARD_BEGIN
+    if (!noisy || !out || !valid_image(B, C, H, W, 8) || !valid_sigmas(sigma, B) || !valid_bm3d(p))
+        return DN_EINVAL;
+    Bm3dWs w = bm3d_layout(workspace, B, C, H, W, p);
+    if (!workspace || ws_bytes < w.bytes) return DN_ENOMEM;
+    return run_bm3d(noisy, out, B, C, H, W, sigma, p, w, (cudaStream_t)stream);
+    DN_GUARD_END
+}
+
+dn_status denoise_nlm(const float *noisy, float *out, int B, int C, int H, int W, const float *sigma,
+                      const dn_nlm_params *p, void *workspace, size_t ws_bytes, dn_stream_t stream)
+{
+    DN_GUARD_BEGIN
+    if (!noisy || !out || !valid_nlm(p) || !valid_image(B, C, H, W, p->patch / 2 + 1) || !valid_sigmas(sigma, B))
+        return DN_EINVAL;
+    NlmWs w = nlm_layout(workspace, B, C, H, W);
+    if (w.bytes > 0 && (!workspace || ws_bytes < w.bytes)) return DN_ENOMEM;
+    return run_nlm(noisy, out, B, C, H, W, sigma, p, w, (cudaStream_t)stream);
+    DN_GUARD_END
+}
+
+dn_status denoise_hybrid(const float *noisy, float *out, int B, int C, int H, int W, const float *sigma,
+                         int prefilter, const void *pp, const dn_cnn *cnn, void *workspace, size_t ws_bytes,
+                         dn_stream_t stream)
+{
+    DN_GUARD_BEGIN
+    if (!noisy || !out || !valid_image(B, C, H, W, 8) || !valid_sigmas(sigma, B) || !valid_cnn(cnn))
+        return DN_EINVAL;
+    if (prefilter == DN_PREFILTER_BM3D) {
+        if (!valid_bm3d(static_cast<const dn_bm3d_params *>(pp))) return DN_EINVAL;
+    } else if (prefilter == DN_PREFILTER_NLM) {
+        if (!valid_nlm(static_cast<const dn_nlm_params *>(pp))) return DN_EINVAL;
+    } else {
+        return DN_EINVAL;
+    }
+    const size_t need = dn_hybrid_workspace_bytes(B, C, H, W, prefilter, pp, cnn);
+    if (!workspace || ws_bytes < need) return DN_ENOMEM;
+    cudaStream_t s = (cudaStream_t)stream;
+    char *base = static_cast<char *>(workspace);
+    float *pre = reinterpret_cast<float *>(base);
+    void *rest = base + align256((size_t)B * C * H * W * sizeof(float));
+    if (prefilter == DN_PREFILTER_BM3D) {
+        auto *p = static_cast<const dn_bm3d_params *>(pp);
+        DN_TRY(run_bm3d(noisy, pre, B, C, H, W, sigma, p, bm3d_layout(rest, B, C, H, W, p), s));
+    } else {
+        DN_TRY(run_nlm(noisy, pre, B, C, H, W, sigma, static_cast<const dn_nlm_params *>(pp),
+                       nlm_layout(rest, B, C, H, W), s));
+    }
+    return run_cnn(noisy, pre, out, B * C, H, W, cnn, cnn_layout(rest, B * C, H, W, cnn), s);
+    DN_GUARD_END
+}
+
+const char *dn_strerror(dn_status st)
+{
+    switch (st) {
+        case DN_OK: return "ok";
+        case DN_EINVAL: return "invalid argument";
+        case DN_ENOMEM: return "workspace too small";
+        case DN_ECUDA: return "CUDA launch or runtime error";
+        case DN_EDEVICE: return "device-side error status";
+        case DN_EUNSUPPORTED: return "unsupported parameter combination";
+    }
+    return "unknown status";
+}
+
+size_t dn_bm3d_match_workspace_bytes(int B, int H, int W, const dn_bm3d_pass *p, int precision)
+{
+    (void)B;
+    (void)H;
+    (void)W;
+    (void)p;
+    (void)precision;
+    return 0;
+}
+
+dn_status dn_bm3d_match(const float *guide, size_t plane_stride, int B, int H, int W, const dn_bm3d_pass *p,
+                        const float *tau, int precision, int *idx, int *n, void *workspace, size_t ws_bytes,
+                        dn_stream_t stream)
+{
+    DN_GUARD_BEGIN
+    (void)workspace;
+    (void)ws_bytes;
+    if (!guide || !idx || !n || !tau || !valid_image(B, 1, H, W, 8) || !valid_pass(p) ||
+        plane_stride < (size_t)H * W)
+        return DN_EINVAL;
+    for (int b = 0; b < B; ++b)
+        if (!(tau[b] > 0.0f)) return DN_EINVAL;
+    if (precision != DN_FP32) return precision == DN_BF16 ? DN_EUNSUPPORTED : DN_EINVAL;
+    return match_fp32(guide, plane_stride, B, H, W, *p, tau, idx, n, (cudaStream_t)stream);
+    DN_GUARD_END
+}
+
+size_t dn_bm3d_filter_workspace_bytes(int B, int C, int H, int W)
+{
+    if (!valid_image(B, C, H, W, 8)) return 0;
+    return align256(4 * (size_t)B * C * H * W * sizeof(float));
+}
+
+static dn_status filter_entry(bool wiener, const float *img, const float *basic, const int *idx, const int *n, int B,
+                              int C, int H, int W, const float *sigma_c, const dn_bm3d_pass *p, int precision,
+                              float *out, void *ws, size_t ws_bytes, cudaStream_t s)
+{
+    if (!img || !idx || !n || !out || !sigma_c || (wiener && !basic) || !valid_image(B, C, H, W, 8) || !valid_pass(p))
+        return DN_EINVAL;
+    for (int i = 0; i < B * C; ++i)
+        if (!(sigma_c[i] > 0.0f) || !std::isfinite(sigma_c[i])) return DN_EINVAL;
+    if (precision != DN_FP32) return precision == DN_BF16 ? DN_EUNSUPPORTED : DN_EINVAL;
+    const size_t need = dn_bm3d_filter_workspace_bytes(B, C, H, W);
+    if (!ws || ws_bytes < need) return DN_ENOMEM;
+    float *acc = static_cast<float *>(ws);
+    const size_t HW = (size_t)H * W;
+    for (int b0 = 0; b0 < B; b0 += 1024) {
+        const int nb = B - b0 < 1024 ? B - b0 : 1024;
+        const size_t off = (size_t)b0 * C * HW, R = (size_t)grid_count(H, 8, p->step) * grid_count(W, 8, p->step);
+        if (cudaMemsetAsync(acc, 0, 4 * (size_t)nb * C * HW * sizeof(float), s) != cudaSuccess) return DN_ECUDA;
+        const int *ib = idx + (size_t)b0 * R * p->n2;
+        const int *nbp = n + (size_t)b0 * R;
+        if (wiener)
+            DN_TRY(filter_wiener_fp32(img + off, basic + off, ib, nbp, nb, C, H, W, sigma_c + (size_t)b0 * C, *p, acc, s));
+        else
+            DN_TRY(filter_hard_fp32(img + off, ib, nbp, nb, C, H, W, sigma_c + (size_t)b0 * C, *p, acc, s));
+        DN_TRY(normalize(acc, out + off, nb, C, H, W, s));
+    }
+    return DN_OK;
+}
+
+dn_status dn_bm3d_filter_hard(const float *img, const int *idx, const int *n, int B, int C, int H, int W,
+                              const float *sigma_c, const dn_bm3d_pass *p, int precision, float *basic,
+                              void *workspace, size_t ws_bytes, dn_stream_t stream)
+{
+    DN_GUARD_BEGIN
+    return filter_entry(false, img, nullptr, idx, n, B, C, H, W, sigma_c, p, precision, basic, workspace, ws_bytes,
+                        (cudaStream_t)stream);
+    DN_GUARD_END
+}
+
+dn_status dn_bm3d_filter_wiener(const float *noisy, const float *basic, const int *idx, const int *n, int B, int C,
+                                int H, int W, const float *sigma_c, const dn_bm3d_pass *p, int precision, float *out,
+                                void *workspace, size_t ws_bytes, dn_stream_t stream)
+{
+    DN_GUARD_BEGIN
+    return filter_entry(true, noisy, basic, idx, n, B, C, H, W, sigma_c, p, precision, out, workspace, ws_bytes,
+                        (cudaStream_t)stream);
+    DN_GUARD_END
+}
+
+dn_status dn_rgb_to_ycc(const float *in, float *out, int B, int H, int W, dn_stream_t stream)
+{
+    DN_GUARD_BEGIN
+    if (!in || !out || !valid_image(B, 3, H, W, 1)) return DN_EINVAL;
+    return colour(in, out, B, H, W, 0, (cudaStream_t)stream);
+    DN_GUARD_END
+}
+
+dn_status dn_ycc_to_rgb(const float *in, float *out, int B, int H, int W, dn_stream_t stream)
+{
+    DN_GUARD_BEGIN
+    if (!in || !out || !valid_image(B, 3, H, W, 1)) return DN_EINVAL;
+    return colour(in, out, B, H, W, 1, (cudaStream_t)stream);
+    DN_GUARD_END
+}
+
+dn_status dn_error_reduce(const float *out, const float *ref, int B, size_t chw, double *sse, double *maxerr,
+                          dn_stream_t stream)
+{
+    DN_GUARD_BEGIN
+    if (!out || !ref || !sse || !maxerr || B < 1 || B > 65535 || chw < 1) return DN_EINVAL;
+    return error_reduce(out, ref, B, chw, sse, maxerr, (cudaStream_t)stream);
+    DN_GUARD_END
+}
+
+static bool valid_conv(int N, int Cin, int Cout, int H, int W)
+{
+    return N >= 1 && Cin >= 1 && Cin <= 64 && Cout >= 1 && Cout <= 64 && H >= 1 && W >= 1 &&
+           (size_t)N * (Cin > Cout ? Cin : Cout) * H * W < ((size_t)1 << 40);
+}
+
+dn_status dn_conv3x3_fwd(const float *x, const float *w, const float *b, float *y, int N, int Cin, int Cout, int H,
+                         int W, int relu, dn_stream_t stream)
+{
+    DN_GUARD_BEGIN
+    if (!x || !w || !y || !valid_conv(N, Cin, Cout, H, W)) return DN_EINVAL;
+    return conv3x3_fwd_fp32(x, w, b, nullptr, y, N, Cin, Cout, H, W, relu, false, (cudaStream_t)stream);
+    DN_GUARD_END
+}
+
+dn_status dn_conv3x3_bwd_data(const float *dy, const float *w, const float *mask, float *dx, int N, int Cin, int Cout,
+                              int H, int W, dn_stream_t stream)
+{
+    DN_GUARD_BEGIN
+    if (!dy || !w || !dx || !valid_conv(N, Cin, Cout, H, W)) return DN_EINVAL;
+    return conv3x3_fwd_fp32(dy, w, nullptr, mask, dx, N, Cout, Cin, H, W, 0, true, (cudaStream_t)stream);
+    DN_GUARD_END
+}
+
+dn_status dn_conv3x3_bwd_weight(const float *x, const float *dy, float *dw, float *db, int N, int Cin, int Cout,
+                                int H, int W, dn_stream_t stream)
+{
+    DN_GUARD_BEGIN
+    if (!x || !dy || !dw || !db || !valid_conv(N, Cin, Cout, H, W)) return DN_EINVAL;
+    return conv3x3_bwd_weight_fp32(x, dy, dw, db, N, Cin, Cout, H, W, (cudaStream_t)stream);
+    DN_GUARD_END
+}
+
+dn_status dn_cnn_forward(const float *noisy, const float *pre, float *out, int N, int H, int W, const dn_cnn *cnn,
+                         void *workspace, size_t ws_bytes, dn_stream_t stream)
+{
+    DN_GUARD_BEGIN
+    if (!noisy || !pre || !out || N < 1 || H < 1 || W < 1 || !valid_cnn(cnn)) return DN_EINVAL;
+    CnnWs w = cnn_layout(workspace, N, H, W, cnn);
+    if (!workspace || ws_bytes < w.bytes) return DN_ENOMEM;
+    return run_cnn(noisy, pre, out, N, H, W, cnn, w, (cudaStream_t)stream);
+    DN_GUARD_END
+}
+
+dn_status dn_cnn_pack_input(const float *pre, const float *noisy, float *z, int N, int H, int W, dn_stream_t stream)
+{
+    DN_GUARD_BEGIN
+    if (!pre || !noisy || !z || N < 1 || H < 1 || W < 1) return DN_EINVAL;
+    return pack_input(pre, noisy, z, N, H, W, (cudaStream_t)stream);
+    DN_GUARD_END
+}
+
+dn_status dn_cnn_residual_out(const float *pre, const float *r, float *out, size_t count, dn_stream_t stream)
+{
+    DN_GUARD_BEGIN
+    if (!pre || !r || !out || count < 1) return DN_EINVAL;
+    return residual_out(pre, r, out, count, (cudaStream_t)stream);
+    DN_GUARD_END
+}
+
+dn_status dn_relu_bwd(const float *g, const float *y, float *out, size_t count, dn_stream_t stream)
+{
+    DN_GUARD_BEGIN
+    if (!g || !y || !out || count < 1) return DN_EINVAL;
+    return relu_bwd(g, y, out, count, (cudaStream_t)stream);
+    DN_GUARD_END
+}
+
+dn_status dn_l1_residual_grad(const float *r, const float *pre, const float *clean, float *dr, size_t count,
+                              double *loss_sum, dn_stream_t stream)
+{
+    DN_GUARD_BEGIN
+    if (!r || !pre || !clean || !dr || count < 1) return DN_EINVAL;
+    return l1_grad(r, pre, clean, dr, count, loss_sum, (cudaStream_t)stream);
+    DN_GUARD_END
+}
+
+dn_status dn_adam_step(float *param, const float *grad, float *m, float *v, size_t count, int t, float lr,
+                       float beta1, float beta2, float eps, dn_stream_t stream)
+{
+    DN_GUARD_BEGIN
+    if (!param || !grad || !m || !v || count < 1 || t < 1 || !(lr > 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) ||
+        !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps > 0.0f))
+        return DN_EINVAL;
+    return adam(param, grad, m, v, count, t, lr, beta1, beta2, eps, (cudaStream_t)stream);
+    DN_GUARD_END
+}
+
+}  // extern "C"

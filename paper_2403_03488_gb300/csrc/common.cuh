@@ -1,0 +1,110 @@
+// Internal helpers of libdenoise (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/denoise.h"
+
+namespace dn {
+
+// Images per launch chunk for per-image scalars passed by value.
+constexpr int kChunk = 64;
+
+// Transform tables passed by value to the filtering kernels (built on the
+// host by make_tables from their definitions; no global device state).
+struct Tables {
+    float dct[64];   // orthonormal DCT-II, dct[u*8+m] = a_u cos(pi (2m+1) u / 16)
+    float kai[64];   // Kaiser outer product, kai[i*8+j] = k[i] k[j]
+};
+
+void make_tables(float beta, Tables *t);
+
+// Per-image scalars of one launch chunk.
+struct ImageScalars {
+    float tau[kChunk];          // matching threshold per image
+    float sig[kChunk * 3];      // per-image, per-channel noise std
+};
+
+// ---- kernel timing (dn_profile_*) -----------------------------------------
+void prof_begin(const char *name, cudaStream_t s);
+void prof_end(const char *name, cudaStream_t s);
+
+// Launch wrapper: times the launch when profiling is on and maps errors.
+template <typename F>
+inline dn_status launch(const char *name, cudaStream_t s, F &&f)
+{
+    prof_begin(name, s);
+    f();
+    cudaError_t e = cudaGetLastError();
+    prof_end(name, s);
+    return e == cudaSuccess ? DN_OK : DN_ECUDA;
+}
+
+#define DN_TRY(expr)                       \
+    do {                                   \
+        dn_status _st = (expr);            \
+        if (_st != DN_OK) return _st;      \
+    } while (0)
+
+inline size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+// Carves 256-byte aligned sub-buffers out of a caller workspace.
+struct Carver {
+    char *base;
+    size_t off = 0;
+    explicit Carver(void *b) : base(static_cast<char *>(b)) {}
+    template <typename T>
+    T *take(size_t count)
+    {
+        T *p = reinterpret_cast<T *>(base ? base + off : nullptr);
+        off += align256(count * sizeof(T));
+        return p;
+    }
+};
+
+inline int grid_count(int L, int patch, int step)
+{
+    int last = L - patch;
+    if (last < 0 || step < 1) return 0;
+    return last / step + 1 + (last % step != 0 ? 1 : 0);
+}
+
+// Compensated accumulation into (s, c): the atomic returns the old value, so
+// the rounding error of old + v is recovered exactly (TwoSum) and added to c.
+__device__ __forceinline__ void comp_add(float *s, float *c, float v)
+{
+    float old = atomicAdd(s, v);
+    float t = __fadd_rn(old, v);
+    float bp = __fsub_rn(t, old);
+    float err = __fadd_rn(__fsub_rn(old, __fsub_rn(t, bp)), __fsub_rn(v, bp));
+    if (err != 0.0f) atomicAdd(c, err);
+}
+
+// ---- launchers implemented in the .cu files -------------------------------
+dn_status match_fp32(const float *guide, size_t plane, int B, int H, int W, const dn_bm3d_pass &p,
+                     const float *tau, int *idx, int *n, cudaStream_t s);
+dn_status filter_hard_fp32(const float *img, const int *idx, const int *n, int B, int C, int H, int W,
+                           const float *sig, const dn_bm3d_pass &p, float *acc, cudaStream_t s);
+dn_status filter_wiener_fp32(const float *noisy, const float *basic, const int *idx, const int *n, int B, int C,
+                             int H, int W, const float *sig, const dn_bm3d_pass &p, float *acc, cudaStream_t s);
+dn_status normalize(const float *acc, float *out, int B, int C, int H, int W, cudaStream_t s);
+dn_status colour(const float *in, float *out, int B, int H, int W, int inverse, cudaStream_t s);
+dn_status nlm_launch(const float *in, float *out, int B, int C, int H, int W, const float *sig_guide,
+                     const dn_nlm_params &p, cudaStream_t s);
+dn_status error_reduce(const float *out, const float *ref, int B, size_t chw, double *sse, double *maxerr,
+                       cudaStream_t s);
+dn_status conv3x3_fwd_fp32(const float *x, const float *w, const float *b, const float *mask, float *y, int N,
+                           int Kin, int Kout, int H, int W, int relu, bool trans, cudaStream_t s);
+dn_status conv3x3_bwd_weight_fp32(const float *x, const float *dy, float *dw, float *db, int N, int Cin, int Cout,
+                                  int H, int W, cudaStream_t s);
+dn_status pack_input(const float *pre, const float *noisy, float *z, int N, int H, int W, cudaStream_t s);
+dn_status residual_out(const float *pre, const float *r, float *out, size_t total, cudaStream_t s);
+dn_status relu_bwd(const float *g, const float *y, float *out, size_t count, cudaStream_t s);
+dn_status l1_grad(const float *r, const float *pre, const float *clean, float *dr, size_t count, double *loss,
+                  cudaStream_t s);
+dn_status adam(float *p, const float *g, float *m, float *v, size_t count, int t, float lr, float b1, float b2,
+               float eps, cudaStream_t s);
+
+}  // namespace dn

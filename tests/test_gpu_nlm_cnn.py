@@ -1,0 +1,120 @@
+"""NL-means and residual-CNN parity of the CUDA path against the FP64 oracle.
+
+NL-means has no discrete decision, so every pixel must agree within 1e-3
+(0..255 scale).  CNN layers in FP32 agree with the oracle to 1e-4 relative
+to the output scale; the full FP32 network output within 1e-3."""
+import numpy as np
+import pytest
+
+from gpu_util import dev, host, need_gpu
+from paper_2403_03488_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-3
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    need_gpu()
+
+
+def api():
+    from paper_2403_03488_gb300 import api as A
+    return A
+
+
+@pytest.mark.parametrize("C,H,W,sigmas", [(1, 70, 90, (15.0, 50.0)), (3, 41, 37, (25.0,)), (1, 5, 6, (25.0,)),
+                                          (1, 8, 130, (25.0,))])
+def test_nlm_parity(oracle, C, H, W, sigmas):
+    A = api()
+    B = len(sigmas)
+    _, noisy = synth.make_batch(range(60, 60 + B), H, W, list(sigmas), C=C)
+    out = host(A.denoise_nlm(dev(noisy), list(sigmas)))
+    for b in range(B):
+        ref = oracle.nlm_image(noisy[b], sigmas[b])
+        err = np.abs(out[b] - ref).max()
+        assert err <= TOL, (b, err)
+
+
+def test_nlm_full_size_sampled(oracle):
+    """8 x 512 x 512 (the plain-method batch): 200 sampled pixels against the
+    oracle run on crops holding each pixel's search window and patches."""
+    A = api()
+    _, noisy = synth.make_batch(range(8), 512, 512, 25.0)
+    out = host(A.denoise_nlm(dev(noisy), 25.0))
+    rng = np.random.default_rng(2)
+    for _ in range(200):
+        b, y, x = int(rng.integers(0, 8)), int(rng.integers(0, 512)), int(rng.integers(0, 512))
+        if rng.random() < 0.2:
+            y = int(rng.choice([0, 1, 2, 510, 511]))
+        y0, y1, x0, x1 = max(0, y - 13), min(512, y + 14), max(0, x - 13), min(512, x + 14)
+        ref = oracle.nlm(noisy[b, 0, y0:y1, x0:x1], 25.0)[y - y0, x - x0]
+        assert abs(out[b, 0, y, x] - ref) <= TOL
+
+
+@pytest.mark.parametrize("N,Cin,Cout,H,W", [(2, 2, 32, 19, 23), (1, 32, 32, 33, 17), (3, 32, 1, 16, 16),
+                                            (1, 5, 7, 1, 9)])
+def test_conv3x3_fwd_bwd_parity(oracle, N, Cin, Cout, H, W):
+    A = api()
+    rng = np.random.default_rng(N * 7 + Cin)
+    x = rng.normal(0, 1, (N, Cin, H, W)).astype(np.float32)
+    w = (rng.normal(0, 1, (Cout, 3, 3, Cin)) * np.sqrt(2.0 / (9 * Cin))).astype(np.float32)
+    b = rng.normal(0, 0.1, Cout).astype(np.float32)
+    dy = rng.normal(0, 1, (N, Cout, H, W)).astype(np.float32)
+    y = host(A.conv3x3_fwd(dev(x), dev(w), dev(b), relu=False))
+    yr = oracle.conv3x3(x, w, b)
+    assert np.abs(y - yr).max() <= 1e-4 * max(1.0, np.abs(yr).max())
+    yrelu = host(A.conv3x3_fwd(dev(x), dev(w), dev(b), relu=True))
+    assert np.abs(yrelu - np.maximum(yr, 0)).max() <= 1e-4 * max(1.0, np.abs(yr).max())
+    dxr, dwr, dbr = oracle.conv3x3_bwd(x, dy, w)
+    dx = host(A.conv3x3_bwd_data(dev(dy), dev(w)))
+    assert np.abs(dx - dxr).max() <= 1e-4 * max(1.0, np.abs(dxr).max())
+    mask = (rng.random(x.shape) > 0.5).astype(np.float32)
+    dxm = host(A.conv3x3_bwd_data(dev(dy), dev(w), dev(mask)))
+    assert np.abs(dxm - dxr * (mask > 0)).max() <= 1e-4 * max(1.0, np.abs(dxr).max())
+    dw, db = A.conv3x3_bwd_weight(dev(x), dev(dy))
+    dw, db = host(dw), host(db)
+    assert np.abs(dw - dwr).max() <= 1e-4 * max(1.0, np.abs(dwr).max())
+    assert np.abs(db - dbr).max() <= 1e-4 * max(1.0, np.abs(dbr).max())
+
+
+def _flat(params):
+    return np.concatenate([np.concatenate([w.ravel(), b.ravel()]) for w, b in params]).astype(np.float32)
+
+
+@pytest.mark.parametrize("N,H,W", [(2, 37, 29), (1, 64, 64)])
+def test_cnn_forward_fp32_parity(oracle, N, H, W):
+    A = api()
+    rng = np.random.default_rng(3)
+    params = synth.he_normal_weights(7, layers=10, width=32)
+    params = [(w, rng.normal(0, 0.05, b.shape).astype(np.float32)) for w, b in params]
+    clean = rng.uniform(0, 255, (N, H, W)).astype(np.float32)
+    noisy = (clean + rng.normal(0, 25, clean.shape)).astype(np.float32)
+    pre = (clean + rng.normal(0, 5, clean.shape)).astype(np.float32)
+    out = host(A.cnn_forward(dev(noisy), dev(pre), dev(_flat(params)), 10, 32))
+    ref = oracle.cnn_forward(noisy, pre, params)
+    assert np.abs(out - ref).max() <= TOL
+
+
+def test_l1_grad_and_adam(oracle):
+    A = api()
+    import torch
+    rng = np.random.default_rng(4)
+    r = rng.normal(0, 0.1, (2, 9, 11)).astype(np.float32)
+    pre = rng.uniform(0, 255, r.shape).astype(np.float32)
+    clean = rng.uniform(0, 255, r.shape).astype(np.float32)
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    dr = host(A.l1_residual_grad(dev(r), dev(pre), dev(clean), loss))
+    out = pre.astype(np.float64) + 255.0 * r
+    np.testing.assert_allclose(dr, 255.0 * np.sign(out - clean) / r.size, rtol=1e-6)
+    assert abs(host(loss)[0] / r.size - oracle.l1_loss(out, clean)) < 1e-4
+    p = rng.normal(0, 1, 50).astype(np.float32)
+    m = np.zeros_like(p)
+    v = np.zeros_like(p)
+    pt, mt, vt = dev(p.copy()), dev(m.copy()), dev(v.copy())
+    pr, mr, vr = p.astype(np.float64), m.astype(np.float64), v.astype(np.float64)
+    for t in range(1, 4):
+        g = rng.normal(0, 1, 50).astype(np.float32)
+        A.adam_step(pt, dev(g), mt, vt, t)
+        pr, mr, vr = oracle.adam_step(pr, g.astype(np.float64), mr, vr, t)
+    np.testing.assert_allclose(host(pt), pr, atol=1e-6)

@@ -180,3 +180,16 @@ def test_adam_equals_torch(oracle):
         opt.step()
         p, m, v = oracle.adam_step(p, g, m, v, t)
     np.testing.assert_allclose(p, pt.detach().numpy(), atol=1e-12)
+
+
+def test_nlm_colour_weights_from_guide_channel(oracle):
+    """Channels 1..C-1 are averaged with the weights of channel 0: a copy of the
+    guide in channel 1 comes out equal to the guide's output, and a constant
+    channel stays constant."""
+    rng = np.random.default_rng(11)
+    g = rng.uniform(0, 255, (12, 13))
+    img = np.stack([g, g, np.full_like(g, 42.0)])
+    out = oracle.nlm_channels(img, 20.0)
+    np.testing.assert_allclose(out[1], out[0], atol=1e-12)
+    np.testing.assert_allclose(out[2], 42.0, atol=1e-12)
+    np.testing.assert_allclose(out[0], oracle.nlm(g, 20.0), atol=1e-12)
