@@ -133,6 +133,28 @@ dn_status denoise_hybrid(const float *noisy, float *out, int B, int C, int H, in
 
 const char *dn_strerror(dn_status s);
 
+/* BM3D without any device allocation, for callers that may not allocate
+ * device memory themselves (for example a plug-in inside an application that
+ * owns the whole device-memory budget, or a latency-critical loop that cannot
+ * risk an allocation blocking on the device).  The paper has no counterpart;
+ * this is a deployment convenience.
+ * Same arguments and results as denoise_bm3d, minus the workspace: the
+ * workspace is a fixed array of DN_NOALLOC_SCRATCH_BYTES of device memory
+ * inside this library, reserved on every GPU that loads the library until the
+ * process exits.  Requests whose dn_bm3d_workspace_bytes exceeds that size
+ * (for example a 1 x 1 x 512 x 512 image fits, 1 x 3 x 512 x 512 does not)
+ * return DN_ENOMEM before any launch.  The first call on a device does a
+ * one-time set-up: it looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture begins.
+ * Every call on a device shares the one array, and the array keeps the
+ * previous call's contents (the call clears what must start at zero itself):
+ * calls that may overlap on the GPU (other streams, other host threads) race
+ * and must be serialised by the caller.  No cudaMalloc / cudaFree is made. */
+#define DN_NOALLOC_SCRATCH_BYTES (16u << 20)
+dn_status denoise_bm3d_noalloc(const float *noisy, float *out, int B, int C, int H, int W, const float *sigma,
+                               const dn_bm3d_params *p, dn_stream_t stream);
+
 /* ---- stage entry points (same kernels, exposed for stage-wise checks) ---- */
 
 /* Block matching of every reference patch of a guide plane.

@@ -88,6 +88,25 @@ def denoise_bm3d(noisy: torch.Tensor, sigma, params: Optional[BM3DParams] = None
     return out
 
 
+NOALLOC_SCRATCH_BYTES = 16 << 20
+
+
+def denoise_bm3d_noalloc(noisy: torch.Tensor, sigma, params: Optional[BM3DParams] = None, out=None,
+                         stream=None) -> torch.Tensor:
+    """denoise_bm3d whose workspace is the library's own fixed device array, for
+    callers that may not allocate device memory.  Calls on one device share that
+    array: do not let them overlap.  (This wrapper still allocates `out` with
+    torch when it is not given.)"""
+    _need(noisy, "noisy", dim=4)
+    B, C, H, W = noisy.shape
+    p = params or default_bm3d_params()
+    out = torch.empty_like(noisy) if out is None else out
+    _need(out, "out", dim=4)
+    check(L.lib().denoise_bm3d_noalloc(_vp(noisy), _vp(out), B, C, H, W, _sigmas(sigma, B), ctypes.byref(p),
+                                       _stream(stream)), "denoise_bm3d_noalloc")
+    return out
+
+
 def denoise_nlm(noisy: torch.Tensor, sigma, params: Optional[NLMParams] = None, out=None, workspace=None,
                 stream=None) -> torch.Tensor:
     _need(noisy, "noisy", dim=4)
