@@ -33,8 +33,8 @@ METRIC = "MPix/s BM3D+CNN at <=0.05 dB PSNR loss vs FP32 plain; served p50/p99 m
 FP32_PEAK_TFLOPS_NOTE = "FP32 ALU peak = 152 SM x 128 lanes x 2 FLOP/FMA x 2.07 GHz = 80.5 TFLOP/s"
 
 
-def workload_name(prec):
-    return "hybrid BM3D(%s)+CNN(10x32) denoise, 16 grey 1024x1024 synthetic images, sigma=25" % prec
+def workload_name(bm3d, cnn):
+    return "hybrid BM3D(%s)+CNN(10x32, %s) denoise, 16 grey 1024x1024 synthetic images, sigma=25" % (bm3d, cnn)
 
 
 # ---------------------------------------------------------------------------
@@ -151,10 +151,10 @@ def run_ours(args):
     noisy_d = torch.from_numpy(noisy).to(dev)
     clean_d = torch.from_numpy(clean).to(dev)
     out_d = torch.empty_like(noisy_d)
-    net = ResidualNet(10, 32, seed=0).to(dev)
-    weights = net.flat_weights()
-    prec = api.DN_BF16 if args.precision == "bf16" else api.DN_FP32
-    bp = api.default_bm3d_params(precision=prec)
+    weights, wsrc = load_weights(dev)
+    bprec = api.DN_BF16 if args.bm3d == "bf16" else api.DN_FP32
+    prec = api.DN_BF16 if args.cnn == "bf16" else api.DN_FP32
+    bp = api.default_bm3d_params(precision=bprec)
     cnn = api.make_cnn(weights, 10, 32, prec)
     ws = torch.empty(api.hybrid_workspace_bytes(B, 1, H, W, api.DN_PREFILTER_BM3D, bp, cnn), dtype=torch.uint8,
                      device=dev)
@@ -202,6 +202,15 @@ def run_ours(args):
     sse_d, _ = api.error_reduce(out_d, clean_d)
     mse = float(sse_d.sum().item()) / (B * H * W)
     psnr_out = 10 * np.log10(255.0 ** 2 / mse)
+    # the FP32 plain path on the same batch (untimed), for the PSNR-loss criterion
+    plain = api.denoise_hybrid(noisy_d, SIGMA, weights, prefilter_params=api.default_bm3d_params(),
+                               cnn_precision=api.DN_FP32)
+    sse_p, _ = api.error_reduce(plain, clean_d)
+    psnr_plain = 10 * np.log10(255.0 ** 2 / (float(sse_p.sum().item()) / (B * H * W)))
+    bm3d_only = api.denoise_bm3d(noisy_d, SIGMA, bp)
+    sse_b, _ = api.error_reduce(bm3d_only, clean_d)
+    psnr_bm3d = 10 * np.log10(255.0 ** 2 / (float(sse_b.sum().item()) / (B * H * W)))
+    del plain, bm3d_only
 
     # end to end through the public API with host buffers
     noisy_h = torch.from_numpy(noisy).pin_memory()
@@ -257,12 +266,15 @@ def run_ours(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32" if prec == api.DN_FP32 else "bf16",
+        "dtype": "+".join(sorted({"f32" if bprec == api.DN_FP32 else "bf16", "f32" if prec == api.DN_FP32 else "bf16"})),
         "data": "synthetic (seeded piecewise-smooth + gratings + repeated tile, AWGN sigma=25)",
-        "config": {"workload": workload_name(args.precision), "global_batch": B * world, "image": [H, W],
-                   "channels": 1, "sigma": SIGMA, "cnn": "10 layers x 32 ch, random init (He, seed 0)",
+        "config": {"workload": workload_name(args.bm3d, args.cnn), "global_batch": B * world, "image": [H, W],
+                   "channels": 1, "sigma": SIGMA, "cnn": "10 layers x 32 ch, " + wsrc,
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": "replicas (dp%d)" % world},
         "psnr_db": round(psnr_out, 3),
+        "psnr_fp32_plain_db": round(psnr_plain, 3),
+        "psnr_loss_vs_fp32_plain_db": round(psnr_plain - psnr_out, 4),
+        "psnr_bm3d_only_db": round(psnr_bm3d, 3),
         "e2e": {"value": round(e2e_value, 3), "unit": "MPix/s", "h2d_bytes_per_step": int(noisy_h.numel() * 4),
                 "d2h_bytes_per_step": int(out_h.numel() * 4)},
         "gpu_launches": int(launches),
@@ -278,6 +290,17 @@ def run_ours(args):
     print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+def load_weights(dev):
+    """Trained 10x32 weights when the repository ships them, else He init (seed 0)."""
+    import torch
+    from paper_2403_03488_gb300.autograd import ResidualNet
+    p = os.path.join(ROOT, "paper_2403_03488_gb300", "weights", "resnet10x32_bm3d.npy")
+    if os.path.exists(p):
+        w = torch.from_numpy(np.load(p).astype(np.float32)).to(dev)
+        return w.contiguous(), "trained weights (" + os.path.basename(p) + ")"
+    return ResidualNet(10, 32, seed=0).to(dev).flat_weights(), "random init (He, seed 0)"
 
 
 def load_traffic(kname):
@@ -346,7 +369,7 @@ def run_reference(args):
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic (seeded piecewise-smooth + gratings + repeated tile, AWGN sigma=25)",
-        "config": {"workload": workload_name("fp64 oracle"), "sample_per_step": "%dx%d crop of image 0" % (
+        "config": {"workload": workload_name("fp64 oracle", "fp64 oracle"), "sample_per_step": "%dx%d crop of image 0" % (
             args.ref_side, args.ref_side)},
         "cpu_baseline": {"value": round(value, 5), "unit": "MPix/s", "cores": oracle.num_threads(), "kind": "oracle",
                          "sample": "%dx%d crop per step" % (args.ref_side, args.ref_side)},
@@ -361,8 +384,9 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default=os.environ.get("DN_BENCH_PRECISION", "fp32"), choices=["fp32", "bf16"])
-    ap.add_argument("--cpu-side", type=int, default=384)
+    ap.add_argument("--bm3d", default="fp32", choices=["fp32", "bf16"], help="BM3D matching/transform precision")
+    ap.add_argument("--cnn", default="bf16", choices=["fp32", "bf16"], help="CNN precision")
+    ap.add_argument("--cpu-side", type=int, default=1024)
     ap.add_argument("--ref-side", type=int, default=192)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

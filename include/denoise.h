@@ -220,6 +220,19 @@ dn_status dn_cnn_forward(const float *noisy, const float *pre, float *out, int N
                          void *workspace, size_t ws_bytes, dn_stream_t stream);
 size_t dn_cnn_workspace_bytes(int N, int H, int W, const dn_cnn *cnn);
 
+/* One hidden 32 -> 32 layer on the tensor cores (tcgen05, BF16 x BF16 -> FP32):
+ * x, y: device NHWC bf16 [N][H][W][32] (64 bytes per pixel, 16-byte aligned);
+ * w: device FP32 [32][3][3][32] (rounded to BF16 inside), b: device FP32 [32];
+ * y = conv3x3(x, w) + b, ReLU when relu != 0, rounded to BF16.
+ * workspace: device, >= 18432 bytes (packed weights). */
+dn_status dn_conv3x3_tc_fwd(const void *x, const float *w, const float *b, void *y, int N, int H, int W, int relu,
+                            void *workspace, size_t ws_bytes, dn_stream_t stream);
+
+/* Reads (and with reset != 0 clears) the library's device error word on the
+ * current device: nonzero when a kernel's bounded wait on the tensor-core
+ * pipeline ran out.  Synchronous (waits for the device). */
+dn_status dn_device_error(int *code, int reset);
+
 /* Network input of Eq. 3 on planes: z [N][2][H][W] = [pre / 255, noisy / 255]. */
 dn_status dn_cnn_pack_input(const float *pre, const float *noisy, float *z, int N, int H, int W, dn_stream_t stream);
 /* Output of Eq. 2: out = pre + 255 r (count floats). */

@@ -88,6 +88,8 @@ def lib():
         "dn_conv3x3_bwd_weight": (i, [vp, vp, vp, vp, i, i, i, i, i, vp]),
         "dn_cnn_forward": (i, [vp, vp, vp, i, i, i, P(CNN), vp, sz, vp]),
         "dn_cnn_workspace_bytes": (sz, [i, i, i, P(CNN)]),
+        "dn_conv3x3_tc_fwd": (i, [vp, vp, vp, vp, i, i, i, i, vp, sz, vp]),
+        "dn_device_error": (i, [ip, i]),
         "dn_cnn_pack_input": (i, [vp, vp, vp, i, i, i, vp]),
         "dn_cnn_residual_out": (i, [vp, vp, vp, sz, vp]),
         "dn_relu_bwd": (i, [vp, vp, vp, sz, vp]),

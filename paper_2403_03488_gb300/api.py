@@ -277,6 +277,28 @@ def cnn_forward(noisy, pre, weights, layers=10, width=32, precision=DN_FP32, str
     return out
 
 
+def conv3x3_tc_fwd(x_nhwc, w, b, relu=True, stream=None):
+    """One 32 -> 32 layer on the tensor cores: x_nhwc bf16 [N, H, W, 32] -> same."""
+    _need(x_nhwc, "x_nhwc", torch.bfloat16, dim=4)
+    _need(w, "w", dim=4)
+    _need(b, "b", dim=1)
+    N, H, W, C = x_nhwc.shape
+    if C != 32 or tuple(w.shape) != (32, 3, 3, 32) or b.numel() != 32:
+        raise ValueError("conv3x3_tc_fwd handles 32 -> 32 channels")
+    y = torch.empty_like(x_nhwc)
+    ws = torch.empty(18432, dtype=torch.uint8, device=x_nhwc.device)
+    check(L.lib().dn_conv3x3_tc_fwd(_vp(x_nhwc), _vp(w), _vp(b), _vp(y), N, H, W, int(bool(relu)), _vp(ws),
+                                    ws.numel(), _stream(stream)), "dn_conv3x3_tc_fwd")
+    return y
+
+
+def device_error(reset: bool = True) -> int:
+    """The library's device error word (nonzero: a bounded wait ran out)."""
+    code = ctypes.c_int(0)
+    check(L.lib().dn_device_error(ctypes.byref(code), int(reset)), "dn_device_error")
+    return code.value
+
+
 def cnn_pack_input(pre, noisy, stream=None):
     """z [N, 2, H, W] = [pre / 255, noisy / 255] (Eq. 3) from planes [N, H, W]."""
     _need(pre, "pre", dim=3)

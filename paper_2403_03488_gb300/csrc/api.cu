@@ -112,19 +112,30 @@ NlmWs nlm_layout(void *base, int B, int C, int H, int W)
 }
 
 struct CnnWs {
-    float *z;
-    float *act[2];
+    float *z;        // FP32 path: packed input [N][2][H][W]
+    float *act[2];   // FP32: [N][width][H][W]; BF16: NHWC [N][H][W][32] bf16
+    char *wpack;     // BF16: packed B operands of the hidden layers
     size_t bytes;
 };
+
+constexpr size_t kWPackBytes = 9 * 4 * 32 * 16;
 
 CnnWs cnn_layout(void *base, int N, int H, int W, const dn_cnn *c)
 {
     Carver cv(base);
     const size_t HW = (size_t)H * W;
     CnnWs w;
-    w.z = cv.take<float>((size_t)N * 2 * HW);
-    w.act[0] = cv.take<float>((size_t)N * c->width * HW);
-    w.act[1] = cv.take<float>((size_t)N * c->width * HW);
+    if (c->precision == DN_BF16) {
+        w.z = nullptr;
+        w.act[0] = reinterpret_cast<float *>(cv.take<char>((size_t)N * HW * 64));
+        w.act[1] = reinterpret_cast<float *>(cv.take<char>((size_t)N * HW * 64));
+        w.wpack = cv.take<char>(kWPackBytes * (size_t)(c->layers > 2 ? c->layers - 2 : 1));
+    } else {
+        w.z = cv.take<float>((size_t)N * 2 * HW);
+        w.act[0] = cv.take<float>((size_t)N * c->width * HW);
+        w.act[1] = cv.take<float>((size_t)N * c->width * HW);
+        w.wpack = nullptr;
+    }
     w.bytes = cv.off;
     return w;
 }
@@ -187,7 +198,25 @@ dn_status run_nlm(const float *noisy, float *out, int B, int C, int H, int W, co
 dn_status run_cnn(const float *noisy, const float *pre, float *out, int N, int H, int W, const dn_cnn *c,
                   const CnnWs &w, cudaStream_t s)
 {
-    if (c->precision != DN_FP32) return DN_EUNSUPPORTED;
+    if (c->precision == DN_BF16) {
+        if (c->width != 32) return DN_EUNSUPPORTED;
+        int *err = device_error_ptr();
+        if (!err) return DN_ECUDA;
+        size_t off = (size_t)32 * 9 * 2 + 32;  // layer 1 (2 -> 32)
+        DN_TRY(conv_first_bf16(pre, noisy, c->weights, c->weights + 32 * 9 * 2, w.act[0], N, H, W, s));
+        int cur = 0;
+        for (int l = 1; l < c->layers - 1; ++l) {
+            const float *wl = c->weights + off;
+            const float *bl = wl + 32 * 9 * 32;
+            off += 32 * 9 * 32 + 32;
+            char *wp = w.wpack + kWPackBytes * (size_t)(l - 1);
+            DN_TRY(pack_w_tc(wl, wp, s));
+            DN_TRY(conv3x3_tc(w.act[cur], w.act[cur ^ 1], wp, bl, N, H, W, 1, err, s));
+            cur ^= 1;
+        }
+        const float *wl = c->weights + off;
+        return conv_last_bf16(w.act[cur], wl, wl + 9 * 32, pre, out, N, H, W, s);
+    }
     DN_TRY(pack_input(pre, noisy, w.z, N, H, W, s));
     const float *h = w.z;
     int kin = 2;
@@ -497,6 +526,20 @@ dn_status dn_cnn_forward(const float *noisy, const float *pre, float *out, int N
     CnnWs w = cnn_layout(workspace, N, H, W, cnn);
     if (!workspace || ws_bytes < w.bytes) return DN_ENOMEM;
     return run_cnn(noisy, pre, out, N, H, W, cnn, w, (cudaStream_t)stream);
+    DN_GUARD_END
+}
+
+dn_status dn_conv3x3_tc_fwd(const void *x, const float *w, const float *b, void *y, int N, int H, int W, int relu,
+                            void *workspace, size_t ws_bytes, dn_stream_t stream)
+{
+    DN_GUARD_BEGIN
+    if (!x || !w || !b || !y || N < 1 || H < 1 || W < 1 || (size_t)N * H * W > ((size_t)1 << 34)) return DN_EINVAL;
+    if (!workspace || ws_bytes < kWPackBytes) return DN_ENOMEM;
+    int *err = device_error_ptr();
+    if (!err) return DN_ECUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    DN_TRY(pack_w_tc(w, workspace, s));
+    return conv3x3_tc(x, y, workspace, b, N, H, W, relu, err, s);
     DN_GUARD_END
 }
 

@@ -104,6 +104,15 @@ dn_status residual_out(const float *pre, const float *r, float *out, size_t tota
 dn_status relu_bwd(const float *g, const float *y, float *out, size_t count, cudaStream_t s);
 dn_status l1_grad(const float *r, const float *pre, const float *clean, float *dr, size_t count, double *loss,
                   cudaStream_t s);
+int *device_error_ptr();
+size_t conv_tc_smem_bytes();
+dn_status pack_w_tc(const float *w, void *out, cudaStream_t s);
+dn_status conv3x3_tc(const void *x, void *y, const void *wpack, const float *bias, int N, int H, int W, int relu,
+                     int *err, cudaStream_t s);
+dn_status conv_first_bf16(const float *pre, const float *noisy, const float *w, const float *b, void *y, int N,
+                          int H, int W, cudaStream_t s);
+dn_status conv_last_bf16(const void *x, const float *w, const float *b, const float *pre, float *out, int N, int H,
+                         int W, cudaStream_t s);
 dn_status adam(float *p, const float *g, float *m, float *v, size_t count, int t, float lr, float b1, float b2,
                float eps, cudaStream_t s);
 

@@ -145,6 +145,26 @@ dn_status error_reduce(const float *out, const float *ref, int B, size_t chw, do
     });
 }
 
+// ---- device error word ---------------------------------------------------------
+
+// Kernels whose bounded waits run out record a nonzero code here.
+static __device__ int g_dn_error;
+
+int *device_error_ptr()
+{
+    static thread_local int cached_dev = -1;
+    static thread_local int *cached_ptr = nullptr;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    if (dev != cached_dev) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_dn_error) != cudaSuccess) return nullptr;
+        cached_dev = dev;
+        cached_ptr = static_cast<int *>(p);
+    }
+    return cached_ptr;
+}
+
 // ---- kernel timing ---------------------------------------------------------------
 
 namespace {
@@ -193,6 +213,20 @@ void prof_end(const char *name, cudaStream_t s)
 }  // namespace dn
 
 extern "C" {
+
+dn_status dn_device_error(int *code, int reset)
+{
+    try {
+        if (!code) return DN_EINVAL;
+        int *p = dn::device_error_ptr();
+        if (!p) return DN_ECUDA;
+        if (cudaMemcpy(code, p, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return DN_ECUDA;
+        if (reset && cudaMemset(p, 0, sizeof(int)) != cudaSuccess) return DN_ECUDA;
+        return DN_OK;
+    } catch (...) {
+        return DN_ECUDA;
+    }
+}
 
 void dn_profile_enable(int on) { dn::g_prof_on = on != 0; }
 

@@ -118,3 +118,45 @@ def test_l1_grad_and_adam(oracle):
         A.adam_step(pt, dev(g), mt, vt, t)
         pr, mr, vr = oracle.adam_step(pr, g.astype(np.float64), mr, vr, t)
     np.testing.assert_allclose(host(pt), pr, atol=1e-6)
+
+
+def _bf16(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(torch.bfloat16).float().numpy()
+
+
+@pytest.mark.parametrize("N,H,W,relu", [(2, 5, 200, True), (1, 37, 128, False), (1, 3, 1, True), (3, 17, 131, True)])
+def test_conv3x3_tc_bf16_parity(oracle, N, H, W, relu):
+    """tcgen05 hidden layer vs the FP64 oracle on the same BF16-rounded inputs and
+    weights: only FP32 accumulation and the final BF16 rounding differ
+    (<= 2 BF16 ulps of the output plus 1e-3 of its scale)."""
+    import torch
+    A = api()
+    rng = np.random.default_rng(N * 100 + W)
+    x = _bf16(np.maximum(rng.normal(0, 1, (N, 32, H, W)), 0))
+    w = _bf16(rng.normal(0, 1, (32, 3, 3, 32)) * np.sqrt(2.0 / 288))
+    b = rng.normal(0, 0.1, 32).astype(np.float32)
+    ref = oracle.conv3x3(x, w, b)
+    if relu:
+        ref = np.maximum(ref, 0)
+    xt = torch.from_numpy(x).permute(0, 2, 3, 1).contiguous().to(torch.bfloat16).cuda()
+    y = A.conv3x3_tc_fwd(xt, dev(w), dev(b), relu=relu)
+    got = host(y.float().permute(0, 3, 1, 2))
+    scale = np.abs(ref).max()
+    assert np.all(np.abs(got - ref) <= 2 ** -7 * np.abs(ref) + 1e-3 * scale)
+    assert A.device_error() == 0
+
+
+def test_cnn_forward_bf16_close_to_oracle(oracle):
+    A = api()
+    rng = np.random.default_rng(8)
+    params = synth.he_normal_weights(3, layers=10, width=32)
+    params = [(w * 0.5, rng.normal(0, 0.02, b.shape).astype(np.float32)) for w, b in params]
+    clean = rng.uniform(0, 255, (2, 45, 140)).astype(np.float32)
+    noisy = (clean + rng.normal(0, 25, clean.shape)).astype(np.float32)
+    pre = (clean + rng.normal(0, 5, clean.shape)).astype(np.float32)
+    out = host(A.cnn_forward(dev(noisy), dev(pre), dev(_flat(params)), 10, 32, precision=A.DN_BF16))
+    ref = oracle.cnn_forward(noisy, pre, params)
+    r = np.abs(ref - pre).max()
+    assert np.abs(out - ref).max() <= 0.03 * r + 1e-2
+    assert A.device_error() == 0
