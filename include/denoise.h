@@ -16,7 +16,8 @@
  *     0..255 scale, C in {1, 3}.  Colour images are converted to YCbCr
  *     (full-range BT.601), matched on Y and filtered per channel with the
  *     per-channel noise std sigma * ||row_c||_2, then converted back.
- *   - sigma is a HOST array of B floats (noise std per image, 0..255 scale).
+ *   - sigma is a HOST array of B floats (noise std per image, 0..255 scale,
+ *     0 < sigma <= 255).
  *   - The caller owns every buffer, including the device workspace; the
  *     library never allocates device memory, never synchronises the stream
  *     and issues all work asynchronously on `stream` (0 = legacy default).

@@ -30,7 +30,7 @@ bool valid_sigmas(const float *sigma, int B)
 {
     if (!sigma) return false;
     for (int b = 0; b < B; ++b)
-        if (!(sigma[b] > 0.0f) || !std::isfinite(sigma[b])) return false;
+        if (!(sigma[b] > 0.0f) || !(sigma[b] <= 255.0f)) return false;
     return true;
 }
 
@@ -419,7 +419,7 @@ static dn_status filter_entry(bool wiener, const float *img, const float *basic,
     if (!img || !idx || !n || !out || !sigma_c || (wiener && !basic) || !valid_image(B, C, H, W, 8) || !valid_pass(p))
         return DN_EINVAL;
     for (int i = 0; i < B * C; ++i)
-        if (!(sigma_c[i] > 0.0f) || !std::isfinite(sigma_c[i])) return DN_EINVAL;
+        if (!(sigma_c[i] > 0.0f) || !(sigma_c[i] <= 255.0f)) return DN_EINVAL;
     if (precision != DN_FP32) return precision == DN_BF16 ? DN_EUNSUPPORTED : DN_EINVAL;
     const size_t need = dn_bm3d_filter_workspace_bytes(B, C, H, W);
     if (!ws || ws_bytes < need) return DN_ENOMEM;

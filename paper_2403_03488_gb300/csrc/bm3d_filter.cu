@@ -10,36 +10,118 @@
 //   w = B^2 / (B^2 + sigma^2); estimate T3D^-1(w Y); weight 1/(sigma^2 sum w^2)
 //   (1 when the sum is 0).
 // Aggregation: every estimate pixel adds weight * kaiser(i) kaiser(j) * value to
-// num and weight * kaiser(i) kaiser(j) to den (compensated FP32 atomics);
-// the output is num / den.
+// num and weight * kaiser(i) kaiser(j) to den; the output is num / den.  The
+// sums are exact (64-bit fixed point, see to_fixed), so the result does not
+// depend on the order in which groups are aggregated.
 //
-// One warp owns one group; its patches live in shared memory as 8 rows of 9
-// floats (72 per patch), which makes both the row and the column passes of
-// the separable DCT hit 32 distinct banks.  The group transform runs in
-// registers: each lane owns 2 of the 64 coefficient positions and applies an
-// in-register fast Walsh-Hadamard butterfly along the group.
+// Layout: a CTA owns a tile of reference positions and aggregates its groups
+// into a shared-memory window first (one global add per window pixel instead
+// of one per contribution).  A warp filters one group at a time: lane k owns
+// patch k and computes its 8x8 DCT in registers with an even/odd fast DCT;
+// the group passes through a per-warp transpose buffer (rows of 65 floats,
+// conflict-free both ways) so that, for the group transform, each lane owns
+// two coefficient positions across all patches and runs the Walsh-Hadamard
+// butterflies in registers; the inverse goes back the same way and each lane
+// aggregates its own patch.
+#include <cmath>
+
 #include "common.cuh"
 
 namespace dn {
 
 namespace {
 
-constexpr int kWarps = 4;
-constexpr int kPS = 72;    // floats per staged patch (8 rows x 9)
-constexpr int kRS = 9;     // row stride inside a staged patch
+constexpr int kTS = 65;    // transpose buffer row stride (floats)
 constexpr int kNMax = 32;
+
+// cos(k pi / 16) for k = 1..7 and 1/sqrt(8): the constants of the 8-point DCT.
+struct DctK {
+    float c1, c2, c3, c4, c5, c6, c7, r8;
+};
 
 struct FilterArgs {
     const float *img;    // [b][C][H][W]: noisy (pass 2) or the image to filter (pass 1)
     const float *basic;  // pass 2 only
     const int *idx;
     const int *n;
-    float *num, *den, *numc, *denc;  // accumulation planes, same layout as img
-    int C, H, W, R, n2;
+    unsigned long long *num, *den;  // exact fixed-point accumulation planes, same layout as img
+    int C, H, W, R, Rx, Ry, n2, step, hs;
     float lambda;
     float sig[kChunk * 3];
-    Tables t;
+    float kai[64];  // Kaiser outer product
+    DctK k;
 };
+
+// ---- 8-point orthonormal DCT-II and its inverse (even/odd decomposition) ----
+
+// x[o], x[o+s], ..., x[o+7s] -> X[u] = a_u sum_m x[m] cos(pi (2m+1) u / 16)
+template <int O, int S>
+__device__ __forceinline__ void dct8(float (&v)[64], const DctK &K)
+{
+    const float s0 = v[O] + v[O + 7 * S], d0 = v[O] - v[O + 7 * S];
+    const float s1 = v[O + S] + v[O + 6 * S], d1 = v[O + S] - v[O + 6 * S];
+    const float s2 = v[O + 2 * S] + v[O + 5 * S], d2 = v[O + 2 * S] - v[O + 5 * S];
+    const float s3 = v[O + 3 * S] + v[O + 4 * S], d3 = v[O + 3 * S] - v[O + 4 * S];
+    const float e0 = s0 + s3, e1 = s1 + s2, f0 = s0 - s3, f1 = s1 - s2;
+    v[O] = K.r8 * (e0 + e1);
+    v[O + 4 * S] = 0.5f * K.c4 * (e0 - e1);
+    v[O + 2 * S] = 0.5f * (K.c2 * f0 + K.c6 * f1);
+    v[O + 6 * S] = 0.5f * (K.c6 * f0 - K.c2 * f1);
+    v[O + 1 * S] = 0.5f * (K.c1 * d0 + K.c3 * d1 + K.c5 * d2 + K.c7 * d3);
+    v[O + 3 * S] = 0.5f * (K.c3 * d0 - K.c7 * d1 - K.c1 * d2 - K.c5 * d3);
+    v[O + 5 * S] = 0.5f * (K.c5 * d0 - K.c1 * d1 + K.c7 * d2 + K.c3 * d3);
+    v[O + 7 * S] = 0.5f * (K.c7 * d0 - K.c5 * d1 + K.c3 * d2 - K.c1 * d3);
+}
+
+// inverse: x[m] = sum_u a_u X[u] cos(pi (2m+1) u / 16)
+template <int O, int S>
+__device__ __forceinline__ void idct8(float (&v)[64], const DctK &K)
+{
+    const float X0 = v[O] * K.r8, X4 = 0.5f * K.c4 * v[O + 4 * S];
+    const float X2 = 0.5f * v[O + 2 * S], X6 = 0.5f * v[O + 6 * S];
+    const float X1 = 0.5f * v[O + S], X3 = 0.5f * v[O + 3 * S], X5 = 0.5f * v[O + 5 * S], X7 = 0.5f * v[O + 7 * S];
+    const float a = X0 + X4, b = X0 - X4;
+    const float p = K.c2 * X2 + K.c6 * X6, q = K.c6 * X2 - K.c2 * X6;
+    const float e0 = a + p, e3 = a - p, e1 = b + q, e2 = b - q;
+    const float o0 = K.c1 * X1 + K.c3 * X3 + K.c5 * X5 + K.c7 * X7;
+    const float o1 = K.c3 * X1 - K.c7 * X3 - K.c1 * X5 - K.c5 * X7;
+    const float o2 = K.c5 * X1 - K.c1 * X3 + K.c7 * X5 + K.c3 * X7;
+    const float o3 = K.c7 * X1 - K.c5 * X3 + K.c3 * X5 - K.c1 * X7;
+    v[O] = e0 + o0;
+    v[O + 7 * S] = e0 - o0;
+    v[O + S] = e1 + o1;
+    v[O + 6 * S] = e1 - o1;
+    v[O + 2 * S] = e2 + o2;
+    v[O + 5 * S] = e2 - o2;
+    v[O + 3 * S] = e3 + o3;
+    v[O + 4 * S] = e3 - o3;
+}
+
+template <int I>
+__device__ __forceinline__ void dct2d_rows_cols(float (&v)[64], const DctK &K)
+{
+    if constexpr (I < 8) {
+        dct8<I * 8, 1>(v, K);
+        dct2d_rows_cols<I + 1>(v, K);
+    } else if constexpr (I < 16) {
+        dct8<I - 8, 8>(v, K);
+        dct2d_rows_cols<I + 1>(v, K);
+    }
+}
+
+template <int I>
+__device__ __forceinline__ void idct2d_cols_rows(float (&v)[64], const DctK &K)
+{
+    if constexpr (I < 8) {
+        idct8<I, 8>(v, K);
+        idct2d_cols_rows<I + 1>(v, K);
+    } else if constexpr (I < 16) {
+        idct8<(I - 8) * 8, 1>(v, K);
+        idct2d_cols_rows<I + 1>(v, K);
+    }
+}
+
+// ---- group transform along the patches (one coefficient column) -------------
 
 template <int N>
 __device__ __forceinline__ void fwht(float (&v)[N])
@@ -63,246 +145,302 @@ __device__ __forceinline__ float inv_sqrt_n()
          : N == 16 ? 0.25f : 0.17677669529663688f;
 }
 
-// Hard-threshold one coefficient column (position off) of an n-patch group.
+// Hard threshold of coefficient column `col` of an n-patch group in T.
 template <int N>
-__device__ __forceinline__ int hard_col(float *g, int off, float thr)
+__device__ __forceinline__ int hard_col(float *T, int col, float thr)
 {
     float v[N];
 #pragma unroll
-    for (int k = 0; k < N; ++k) v[k] = g[k * kPS + off];
+    for (int k = 0; k < N; ++k) v[k] = T[k * kTS + col];
     fwht<N>(v);
     const float sc = inv_sqrt_n<N>();
     int cnt = 0;
 #pragma unroll
     for (int k = 0; k < N; ++k) {
-        float z = v[k] * sc;
-        bool keep = fabsf(z) > thr;
+        const float z = v[k] * sc;
+        const bool keep = fabsf(z) > thr;
         cnt += keep ? 1 : 0;
         v[k] = keep ? z : 0.0f;
     }
     fwht<N>(v);
 #pragma unroll
-    for (int k = 0; k < N; ++k) g[k * kPS + off] = v[k] * sc;
+    for (int k = 0; k < N; ++k) T[k * kTS + col] = v[k] * sc;
     return cnt;
 }
 
-// Wiener-filter one coefficient column; returns sum of squared gains.
+// Wiener gains of column `col` of the basic-estimate group in T, kept in
+// registers (om); returns their sum of squares.
 template <int N>
-__device__ __forceinline__ float wiener_col(const float *gb, float *gy, int off, float s2)
+__device__ __forceinline__ float wiener_gains(const float *T, int col, float s2, float (&om)[N])
 {
-    float vb[N], vy[N];
+    float v[N];
 #pragma unroll
-    for (int k = 0; k < N; ++k) {
-        vb[k] = gb[k * kPS + off];
-        vy[k] = gy[k * kPS + off];
-    }
-    fwht<N>(vb);
-    fwht<N>(vy);
+    for (int k = 0; k < N; ++k) v[k] = T[k * kTS + col];
+    fwht<N>(v);
     const float sc = inv_sqrt_n<N>();
     float wsq = 0.0f;
 #pragma unroll
     for (int k = 0; k < N; ++k) {
-        float zb = vb[k] * sc;
-        float b2 = zb * zb;
-        float om = b2 / (b2 + s2);
-        vy[k] = vy[k] * sc * om;
-        wsq = fmaf(om, om, wsq);
+        const float zb = v[k] * sc;
+        const float b2 = zb * zb;
+        om[k] = b2 / (b2 + s2);
+        wsq = fmaf(om[k], om[k], wsq);
     }
-    fwht<N>(vy);
-#pragma unroll
-    for (int k = 0; k < N; ++k) gy[k * kPS + off] = vy[k] * sc;
     return wsq;
 }
 
-__device__ __forceinline__ void dct_rows(float *g, int n, int lane, const float *C, bool inverse)
+// Applies the gains to column `col` of the noisy group in T (in place).
+template <int N>
+__device__ __forceinline__ void wiener_apply(float *T, int col, const float (&om)[N])
 {
-    for (int t = lane; t < n * 8; t += 32) {
-        float *row = g + (t >> 3) * kPS + (t & 7) * kRS;
-        float v[8];
+    float v[N];
 #pragma unroll
-        for (int m = 0; m < 8; ++m) v[m] = row[m];
+    for (int k = 0; k < N; ++k) v[k] = T[k * kTS + col];
+    fwht<N>(v);
+    const float sc2 = inv_sqrt_n<N>() * inv_sqrt_n<N>();
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            float s = 0.0f;
+    for (int k = 0; k < N; ++k) v[k] *= om[k];
+    fwht<N>(v);
 #pragma unroll
-            for (int m = 0; m < 8; ++m) s = fmaf(inverse ? C[m * 8 + u] : C[u * 8 + m], v[m], s);
-            row[u] = s;
+    for (int k = 0; k < N; ++k) T[k * kTS + col] = v[k] * sc2;
+}
+
+__device__ __forceinline__ int hard_columns(float *T, int n, int lane, float thr)
+{
+    int cnt = 0;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int col = lane + 32 * h;
+        switch (n) {
+            case 1: cnt += hard_col<1>(T, col, thr); break;
+            case 2: cnt += hard_col<2>(T, col, thr); break;
+            case 4: cnt += hard_col<4>(T, col, thr); break;
+            case 8: cnt += hard_col<8>(T, col, thr); break;
+            case 16: cnt += hard_col<16>(T, col, thr); break;
+            default: cnt += hard_col<32>(T, col, thr); break;
         }
     }
+    return cnt;
 }
 
-__device__ __forceinline__ void dct_cols(float *g, int n, int lane, const float *C, bool inverse)
+// ---- exact aggregation ---------------------------------------------------------
+
+// Every contribution becomes a signed 64-bit fixed-point number with 36
+// fraction bits (its FP32 value is exact whenever |v| >= 2^-13) and is summed
+// with integer atomics, so num and den are bitwise reproducible whatever the
+// order of the groups.  Weights are used scaled by sigma^2 (1/N_har,
+// 1/sum w^2, or sigma^2 for an all-zero group), which leaves num/den unchanged
+// and keeps den below 2^23 for sigma <= 255 (no overflow: 2^59 < 2^63).
+__device__ __forceinline__ unsigned long long to_fixed(float v)
 {
-    for (int t = lane; t < n * 8; t += 32) {
-        float *col = g + (t >> 3) * kPS + (t & 7);
-        float v[8];
-#pragma unroll
-        for (int m = 0; m < 8; ++m) v[m] = col[m * kRS];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            float s = 0.0f;
-#pragma unroll
-            for (int m = 0; m < 8; ++m) s = fmaf(inverse ? C[m * 8 + u] : C[u * 8 + m], v[m], s);
-            col[u * kRS] = s;
-        }
-    }
+    return (unsigned long long)__float2ll_rn(v * 68719476736.0f);  // 2^36
 }
 
-__device__ __forceinline__ void dct2d(float *g, int n, int lane, const float *C)
-{
-    dct_rows(g, n, lane, C, false);
-    __syncwarp();
-    dct_cols(g, n, lane, C, false);
-    __syncwarp();
-}
+// Shared-memory aggregation window of one CTA: pixels [Y0, Y0+RH) x [X0, X0+RW)
+// of the current channel, num then den planes.
+struct Window {
+    unsigned long long *acc;  // [2][RH][RW] fixed point
+    int X0, Y0, RH, RW;
+};
 
-__device__ __forceinline__ void idct2d(float *g, int n, int lane, const float *C)
-{
-    dct_cols(g, n, lane, C, true);
-    __syncwarp();
-    dct_rows(g, n, lane, C, true);
-    __syncwarp();
-}
-
-__device__ __forceinline__ void gather(float *g, const float *ch, int W, int n, int lane, int py, int px)
-{
-    for (int e = lane; e < n * 64; e += 32) {
-        int k = e >> 6, p = e & 63;
-        int yk = __shfl_sync(0xffffffffu, py, k), xk = __shfl_sync(0xffffffffu, px, k);
-        g[k * kPS + (p >> 3) * kRS + (p & 7)] = ch[(size_t)(yk + (p >> 3)) * W + xk + (p & 7)];
-    }
-}
-
-__device__ __forceinline__ void aggregate(const FilterArgs &a, const float *g, size_t cbase, int n, int lane,
-                                          int py, int px, float w, const float *kai)
-{
-    for (int e = lane; e < n * 64; e += 32) {
-        int k = e >> 6, p = e & 63;
-        int yk = __shfl_sync(0xffffffffu, py, k), xk = __shfl_sync(0xffffffffu, px, k);
-        size_t pix = cbase + (size_t)(yk + (p >> 3)) * a.W + xk + (p & 7);
-        float kw = w * kai[p];
-        comp_add(a.num + pix, a.numc + pix, kw * g[k * kPS + (p >> 3) * kRS + (p & 7)]);
-        comp_add(a.den + pix, a.denc + pix, kw);
-    }
-}
-
-// Loads the group's positions; returns n (0 if the list is invalid).
+// Loads the group's positions (lane k < n gets patch k); returns n (0 if the list is invalid).
 __device__ __forceinline__ int load_group(const FilterArgs &a, int b, int r, int lane, int &py, int &px)
 {
     const size_t gr = (size_t)b * a.R + r;
-    int n = a.n[gr];
+    const int n = a.n[gr];
     if (n < 1 || n > a.n2 || n > kNMax || (n & (n - 1)) != 0) return 0;
-    int id = lane < n ? a.idx[gr * a.n2 + lane] : 0;
+    const int id = lane < n ? a.idx[gr * a.n2 + lane] : 0;
     py = id / a.W;
     px = id - py * a.W;
-    bool bad = lane < n && (id < 0 || py > a.H - 8 || px > a.W - 8);
+    const bool bad = lane < n && (id < 0 || py > a.H - 8 || px > a.W - 8);
     if (__any_sync(0xffffffffu, bad)) return 0;  // invalid list: the group is skipped
     return n;
 }
 
-__global__ void __launch_bounds__(kWarps * 32) k_filter_hard(FilterArgs a)
+// Coalesced gather of the group's patches into T (row k = patch k, 64 floats).
+__device__ __forceinline__ void gather_rows(float *T, const float *ch, int W, int n, int lane, int py, int px)
 {
-    extern __shared__ float dsm[];  // [64 dct][64 kaiser][kWarps][n2 * kPS]
-    float *sC = dsm, *sK = dsm + 64;
-    if (threadIdx.x < 64) {
-        sC[threadIdx.x] = a.t.dct[threadIdx.x];
-        sK[threadIdx.x] = a.t.kai[threadIdx.x];
-    }
-    __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int r = blockIdx.x * kWarps + warp, b = blockIdx.y;
-    if (r >= a.R) return;
-    int py = 0, px = 0;
-    const int n = load_group(a, b, r, lane, py, px);
-    if (n == 0) return;
-    float *g = dsm + 128 + (size_t)warp * a.n2 * kPS;
-    const size_t HW = (size_t)a.H * a.W;
-    for (int c = 0; c < a.C; ++c) {
-        const size_t cbase = ((size_t)b * a.C + c) * HW;
-        const float sig = a.sig[b * 3 + c];
-        const float thr = a.lambda * sig;
-        gather(g, a.img + cbase, a.W, n, lane, py, px);
-        __syncwarp();
-        dct2d(g, n, lane, sC);
-        int cnt = 0;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            int pos = lane + 32 * h;
-            int off = (pos >> 3) * kRS + (pos & 7);
-            switch (n) {
-                case 1: cnt += hard_col<1>(g, off, thr); break;
-                case 2: cnt += hard_col<2>(g, off, thr); break;
-                case 4: cnt += hard_col<4>(g, off, thr); break;
-                case 8: cnt += hard_col<8>(g, off, thr); break;
-                case 16: cnt += hard_col<16>(g, off, thr); break;
-                default: cnt += hard_col<32>(g, off, thr); break;
-            }
-        }
-        const int nhar = __reduce_add_sync(0xffffffffu, cnt);
-        __syncwarp();
-        idct2d(g, n, lane, sC);
-        const float w = nhar > 0 ? 1.0f / (sig * sig * (float)nhar) : 1.0f;
-        aggregate(a, g, cbase, n, lane, py, px, w, sK);
-        __syncwarp();
+    for (int e = lane; e < n * 64; e += 32) {
+        const int k = e >> 6, p = e & 63;
+        const int yk = __shfl_sync(0xffffffffu, py, k), xk = __shfl_sync(0xffffffffu, px, k);
+        T[k * kTS + p] = ch[(size_t)(yk + (p >> 3)) * W + xk + (p & 7)];
     }
 }
 
-__global__ void __launch_bounds__(kWarps * 32) k_filter_wiener(FilterArgs a)
+// Lane k < n: 2D DCT of its patch (row k of T), written back as coefficients.
+__device__ __forceinline__ void dct_own_row(float *T, int n, int lane, const DctK &K)
 {
-    extern __shared__ float dsm[];  // [64 dct][64 kaiser][kWarps][2][n2 * kPS]
-    float *sC = dsm, *sK = dsm + 64;
-    if (threadIdx.x < 64) {
-        sC[threadIdx.x] = a.t.dct[threadIdx.x];
-        sK[threadIdx.x] = a.t.kai[threadIdx.x];
-    }
-    __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int r = blockIdx.x * kWarps + warp, b = blockIdx.y;
-    if (r >= a.R) return;
-    int py = 0, px = 0;
-    const int n = load_group(a, b, r, lane, py, px);
-    if (n == 0) return;
-    float *gb = dsm + 128 + (size_t)warp * 2 * a.n2 * kPS;
-    float *gy = gb + (size_t)a.n2 * kPS;
-    const size_t HW = (size_t)a.H * a.W;
-    for (int c = 0; c < a.C; ++c) {
-        const size_t cbase = ((size_t)b * a.C + c) * HW;
-        const float sig = a.sig[b * 3 + c];
-        const float s2 = sig * sig;
-        gather(gb, a.basic + cbase, a.W, n, lane, py, px);
-        gather(gy, a.img + cbase, a.W, n, lane, py, px);
-        __syncwarp();
-        dct2d(gb, n, lane, sC);
-        dct2d(gy, n, lane, sC);
-        float wsq = 0.0f;
+    if (lane < n) {
+        float v[64];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            int pos = lane + 32 * h;
-            int off = (pos >> 3) * kRS + (pos & 7);
-            switch (n) {
-                case 1: wsq += wiener_col<1>(gb, gy, off, s2); break;
-                case 2: wsq += wiener_col<2>(gb, gy, off, s2); break;
-                case 4: wsq += wiener_col<4>(gb, gy, off, s2); break;
-                case 8: wsq += wiener_col<8>(gb, gy, off, s2); break;
-                case 16: wsq += wiener_col<16>(gb, gy, off, s2); break;
-                default: wsq += wiener_col<32>(gb, gy, off, s2); break;
-            }
+        for (int p = 0; p < 64; ++p) v[p] = T[lane * kTS + p];
+        dct2d_rows_cols<0>(v, K);
+#pragma unroll
+        for (int p = 0; p < 64; ++p) T[lane * kTS + p] = v[p];
+    }
+}
+
+// Wiener transform of one group of N patches: gains from the basic-estimate
+// group (kept in registers), applied to the noisy group, both through T.
+template <int N>
+__device__ __forceinline__ float wiener_group(const FilterArgs &a, float *T, size_t cbase, int lane, int py, int px,
+                                              float s2)
+{
+    gather_rows(T, a.basic + cbase, a.W, N, lane, py, px);
+    __syncwarp();
+    dct_own_row(T, N, lane, a.k);
+    __syncwarp();
+    float om0[N], om1[N];
+    const float wsq = wiener_gains<N>(T, lane, s2, om0) + wiener_gains<N>(T, lane + 32, s2, om1);
+    __syncwarp();
+    gather_rows(T, a.img + cbase, a.W, N, lane, py, px);
+    __syncwarp();
+    dct_own_row(T, N, lane, a.k);
+    __syncwarp();
+    wiener_apply<N>(T, lane, om0);
+    wiener_apply<N>(T, lane + 32, om1);
+    return wsq;
+}
+
+// One group on channel c: transforms, shrinkage, inverse, aggregation.
+template <bool WIENER>
+__device__ __forceinline__ void filter_group(const FilterArgs &a, const Window &win, float *T, int b, int c, int n,
+                                             int lane, int py, int px, unsigned long long *sden)
+{
+    const size_t HW = (size_t)a.H * a.W;
+    const size_t cbase = ((size_t)b * a.C + c) * HW;
+    const float sig = a.sig[b * 3 + c];
+    float w;
+    if (!WIENER) {
+        gather_rows(T, a.img + cbase, a.W, n, lane, py, px);
+        __syncwarp();
+        dct_own_row(T, n, lane, a.k);
+        __syncwarp();
+        const int cnt = hard_columns(T, n, lane, a.lambda * sig);
+        const int nhar = __reduce_add_sync(0xffffffffu, cnt);
+        w = nhar > 0 ? 1.0f / (float)nhar : sig * sig;  // 1/(sigma^2 N_har) or 1, times sigma^2
+    } else {
+        const float s2 = sig * sig;
+        float wsq;
+        switch (n) {
+            case 1: wsq = wiener_group<1>(a, T, cbase, lane, py, px, s2); break;
+            case 2: wsq = wiener_group<2>(a, T, cbase, lane, py, px, s2); break;
+            case 4: wsq = wiener_group<4>(a, T, cbase, lane, py, px, s2); break;
+            case 8: wsq = wiener_group<8>(a, T, cbase, lane, py, px, s2); break;
+            case 16: wsq = wiener_group<16>(a, T, cbase, lane, py, px, s2); break;
+            default: wsq = wiener_group<32>(a, T, cbase, lane, py, px, s2); break;
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) wsq += __shfl_xor_sync(0xffffffffu, wsq, o);
-        __syncwarp();
-        idct2d(gy, n, lane, sC);
-        const float w = wsq > 0.0f ? 1.0f / (s2 * wsq) : 1.0f;
-        aggregate(a, gy, cbase, n, lane, py, px, w, sK);
-        __syncwarp();
+        w = wsq > 0.0f ? 1.0f / wsq : s2;               // 1/(sigma^2 sum w^2) or 1, times sigma^2
+    }
+    const float *TY = T;
+    // den contributions w * kaiser(i) kaiser(j) are the same for every patch
+    sden[lane] = to_fixed(w * a.kai[lane]);
+    sden[lane + 32] = to_fixed(w * a.kai[lane + 32]);
+    __syncwarp();
+    if (lane < n) {
+        float v[64];
+#pragma unroll
+        for (int p = 0; p < 64; ++p) v[p] = TY[lane * kTS + p];
+        idct2d_cols_rows<0>(v, a.k);
+        const int ly0 = py - win.Y0, lx0 = px - win.X0;
+        const bool inside = ly0 >= 0 && ly0 + 8 <= win.RH && lx0 >= 0 && lx0 + 8 <= win.RW;
+        unsigned long long *wn = win.acc, *wd = win.acc + win.RH * win.RW;
+#pragma unroll
+        for (int p = 0; p < 64; ++p) {
+            const int i = p >> 3, j = p & 7;
+            const unsigned long long fn = to_fixed(w * a.kai[p] * v[p]);
+            if (inside) {
+                const int at = (ly0 + i) * win.RW + lx0 + j;
+                atomicAdd(wn + at, fn);
+                atomicAdd(wd + at, sden[p]);
+            } else {
+                const size_t pix = cbase + (size_t)(py + i) * a.W + px + j;
+                atomicAdd(a.num + pix, fn);
+                atomicAdd(a.den + pix, sden[p]);
+            }
+        }
+    }
+    __syncwarp();
+}
+
+// A CTA owns a TR x TR tile of reference positions; its warps filter the
+// tile's groups channel by channel and accumulate into the shared window
+// covering every patch those groups can hold (tile + search radius + patch),
+// then add the window once to the global fixed-point planes.
+template <bool WIENER>
+__global__ void __launch_bounds__(WIENER ? 384 : 512) k_filter(FilterArgs a, int TR, int RH, int RW)
+{
+    extern __shared__ __align__(16) unsigned char dsm_raw[];
+    const int nw = blockDim.x >> 5;
+    Window win;
+    win.acc = reinterpret_cast<unsigned long long *>(dsm_raw);
+    win.RH = RH;
+    win.RW = RW;
+    unsigned long long *sdens = win.acc + (size_t)2 * RH * RW;                   // [nw][64]
+    float *tbufs = reinterpret_cast<float *>(sdens + (size_t)nw * 64);           // [nw][32][65]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int b = blockIdx.z;
+    const int rx0 = blockIdx.x * TR, ry0 = blockIdx.y * TR;
+    const int Rx = a.Rx, Ry = a.Ry;
+    const int gx0 = min(rx0 * a.step, a.W - 8), gy0 = min(ry0 * a.step, a.H - 8);
+    win.X0 = max(0, gx0 - a.hs);
+    win.Y0 = max(0, gy0 - a.hs);
+
+    float *T = tbufs + (size_t)warp * 32 * kTS;
+    unsigned long long *sden = sdens + warp * 64;
+    const int tw = min(TR, Rx - rx0), th = min(TR, Ry - ry0);
+    const size_t HW = (size_t)a.H * a.W;
+    const int rh = min(RH, a.H - win.Y0), rw = min(RW, a.W - win.X0);
+    const int wtot = 2 * RH * RW;
+
+    for (int c = 0; c < a.C; ++c) {
+        for (int i = threadIdx.x; i < wtot; i += blockDim.x) win.acc[i] = 0ull;
+        __syncthreads();
+        for (int q = warp; q < tw * th; q += nw) {
+            const int ry = ry0 + q / tw, rx = rx0 + q % tw;
+            int py = 0, px = 0;
+            const int n = load_group(a, b, ry * Rx + rx, lane, py, px);
+            if (n == 0) continue;
+            filter_group<WIENER>(a, win, T, b, c, n, lane, py, px, sden);
+        }
+        __syncthreads();
+        const unsigned long long *wn = win.acc, *wd = win.acc + RH * RW;
+        const size_t cbase = ((size_t)b * a.C + c) * HW;
+        for (int i = threadIdx.x; i < rh * rw; i += blockDim.x) {
+            const int ly = i / rw, lx = i - ly * rw;
+            const unsigned long long d = wd[ly * RW + lx];
+            if (d != 0ull) {
+                const size_t pix = cbase + (size_t)(win.Y0 + ly) * a.W + win.X0 + lx;
+                atomicAdd(a.num + pix, wn[ly * RW + lx]);
+                atomicAdd(a.den + pix, d);
+            }
+        }
+        __syncthreads();  // the window is zeroed again for the next channel
     }
 }
 
-__global__ void k_normalize(const float *num, const float *den, const float *numc, const float *denc, float *out,
-                            size_t count)
+__global__ void k_normalize(const long long *num, const long long *den, float *out, size_t count)
 {
+    // the 2^36 scale cancels in the ratio
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
-        out[i] = (num[i] + numc[i]) / (den[i] + denc[i]);
+        out[i] = (float)((double)num[i] / (double)den[i]);
+}
+
+DctK make_dct_constants()
+{
+    const double pi = 3.14159265358979323846;
+    DctK k;
+    k.c1 = (float)std::cos(1 * pi / 16);
+    k.c2 = (float)std::cos(2 * pi / 16);
+    k.c3 = (float)std::cos(3 * pi / 16);
+    k.c4 = (float)std::cos(4 * pi / 16);
+    k.c5 = (float)std::cos(5 * pi / 16);
+    k.c6 = (float)std::cos(6 * pi / 16);
+    k.c7 = (float)std::cos(7 * pi / 16);
+    k.r8 = (float)(1.0 / std::sqrt(8.0));
+    return k;
 }
 
 dn_status filter_common(bool wiener, const float *img, const float *basic, const int *idx, const int *n, int B,
@@ -312,11 +450,34 @@ dn_status filter_common(bool wiener, const float *img, const float *basic, const
     a.C = C;
     a.H = H;
     a.W = W;
-    a.R = grid_count(H, 8, p.step) * grid_count(W, 8, p.step);
+    a.Ry = grid_count(H, 8, p.step);
+    a.Rx = grid_count(W, 8, p.step);
+    a.R = a.Ry * a.Rx;
     a.n2 = p.n2;
+    a.step = p.step;
+    a.hs = p.search / 2;
     a.lambda = p.lambda3d;
-    make_tables(p.beta, &a.t);
+    Tables t;
+    make_tables(p.beta, &t);
+    for (int i = 0; i < 64; ++i) a.kai[i] = t.kai[i];
+    a.k = make_dct_constants();
     const size_t HW = (size_t)H * W, N = (size_t)B * C * HW;
+    // tile of references per CTA and its aggregation window
+    const int nwarps = wiener ? 12 : 16;
+    const size_t per_warp = (size_t)32 * kTS * sizeof(float) + 64 * sizeof(unsigned long long);
+    int TR = 16;
+    int RH = 0, RW = 0;
+    size_t smem = 0;
+    for (; TR >= 1; TR /= 2) {
+        RH = (TR - 1) * p.step + 2 * a.hs + 8;
+        RW = RH;
+        smem = (size_t)nwarps * per_warp + (size_t)2 * RH * RW * sizeof(unsigned long long);
+        if (smem <= 225 * 1024) break;
+    }
+    if (TR < 1) return DN_EUNSUPPORTED;
+    const void *fn = wiener ? (const void *)k_filter<true> : (const void *)k_filter<false>;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return DN_ECUDA;
     for (int b0 = 0; b0 < B; b0 += kChunk) {
         int nb = B - b0 < kChunk ? B - b0 : kChunk;
         const size_t off = (size_t)b0 * C * HW;
@@ -324,19 +485,16 @@ dn_status filter_common(bool wiener, const float *img, const float *basic, const
         a.basic = basic ? basic + off : nullptr;
         a.idx = idx + (size_t)b0 * a.R * p.n2;
         a.n = n + (size_t)b0 * a.R;
-        a.num = acc + off;
-        a.den = acc + N + off;
-        a.numc = acc + 2 * N + off;
-        a.denc = acc + 3 * N + off;
+        unsigned long long *fx = reinterpret_cast<unsigned long long *>(acc);
+        a.num = fx + off;
+        a.den = fx + N + off;
         for (int i = 0; i < nb; ++i)
             for (int c = 0; c < 3; ++c) a.sig[i * 3 + c] = c < C ? sig[(size_t)(b0 + i) * C + c] : 0.0f;
-        dim3 grid((a.R + kWarps - 1) / kWarps, nb);
-        const size_t smem = (128 + (size_t)kWarps * (wiener ? 2 : 1) * p.n2 * kPS) * sizeof(float);
-        if (cudaFuncSetAttribute(wiener ? (const void *)k_filter_wiener : (const void *)k_filter_hard,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-            return DN_ECUDA;
-        dn_status st = wiener ? launch("bm3d_filter_wiener_fp32", s, [&] { k_filter_wiener<<<grid, kWarps * 32, smem, s>>>(a); })
-                              : launch("bm3d_filter_hard_fp32", s, [&] { k_filter_hard<<<grid, kWarps * 32, smem, s>>>(a); });
+        dim3 grid((a.Rx + TR - 1) / TR, (a.Ry + TR - 1) / TR, nb);
+        dn_status st = wiener ? launch("bm3d_filter_wiener_fp32", s,
+                                       [&] { k_filter<true><<<grid, nwarps * 32, smem, s>>>(a, TR, RH, RW); })
+                              : launch("bm3d_filter_hard_fp32", s,
+                                       [&] { k_filter<false><<<grid, nwarps * 32, smem, s>>>(a, TR, RH, RW); });
         if (st != DN_OK) return st;
     }
     return DN_OK;
@@ -361,8 +519,10 @@ dn_status normalize(const float *acc, float *out, int B, int C, int H, int W, cu
     const size_t N = (size_t)B * C * H * W;
     int blocks = (int)((N + 255) / 256);
     if (blocks > 152 * 16) blocks = 152 * 16;
-    return launch("bm3d_normalize", s,
-                  [&] { k_normalize<<<blocks, 256, 0, s>>>(acc, acc + N, acc + 2 * N, acc + 3 * N, out, N); });
+    return launch("bm3d_normalize", s, [&] {
+        const long long *fx = reinterpret_cast<const long long *>(acc);
+        k_normalize<<<blocks, 256, 0, s>>>(fx, fx + N, out, N);
+    });
 }
 
 }  // namespace dn

@@ -71,17 +71,6 @@ inline int grid_count(int L, int patch, int step)
     return last / step + 1 + (last % step != 0 ? 1 : 0);
 }
 
-// Compensated accumulation into (s, c): the atomic returns the old value, so
-// the rounding error of old + v is recovered exactly (TwoSum) and added to c.
-__device__ __forceinline__ void comp_add(float *s, float *c, float v)
-{
-    float old = atomicAdd(s, v);
-    float t = __fadd_rn(old, v);
-    float bp = __fsub_rn(t, old);
-    float err = __fadd_rn(__fsub_rn(old, __fsub_rn(t, bp)), __fsub_rn(v, bp));
-    if (err != 0.0f) atomicAdd(c, err);
-}
-
 // ---- launchers implemented in the .cu files -------------------------------
 dn_status match_fp32(const float *guide, size_t plane, int B, int H, int W, const dn_bm3d_pass &p,
                      const float *tau, int *idx, int *n, cudaStream_t s);

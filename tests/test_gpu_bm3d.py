@@ -236,6 +236,18 @@ def test_match_full_size_sampled(oracle):
     assert bad == 0
 
 
+def test_denoise_bm3d_is_bitwise_reproducible():
+    """Aggregation sums are exact (fixed point), so repeated runs, with other
+    work in between, give bit-identical outputs."""
+    A = api()
+    _, noisy = synth.make_batch([70, 71, 72], 200, 168, [25.0, 15.0, 50.0])
+    x = dev(noisy)
+    a = host(A.denoise_bm3d(x, [25.0, 15.0, 50.0]))
+    A.denoise_nlm(x, 25.0)
+    b = host(A.denoise_bm3d(x, [25.0, 15.0, 50.0]))
+    assert np.array_equal(a, b)
+
+
 def test_denoise_bm3d_full_size_properties(oracle):
     A = api()
     clean, noisy = synth.make_batch([100, 101], 1024, 1024, 25.0)
