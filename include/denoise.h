@@ -172,6 +172,20 @@ dn_status dn_bm3d_match(const float *guide, size_t plane_stride, int B, int H, i
                         dn_stream_t stream);
 size_t dn_bm3d_match_workspace_bytes(int B, int H, int W, const dn_bm3d_pass *p, int precision);
 
+/* Test surface of the BF16 tensor-core matching prefilter: runs dn_bm3d_match
+ * (DN_BF16) on one image and additionally writes the raw FP32 cross terms
+ * sum_k bf16(P_c)[k] bf16(Q_c)[k] (centred patches) of reference tile
+ * (tile_x, tile_y) (8 x 16 grid positions) to cross, device float
+ * [128][nchunks][256]: reference t = (ty * 8 + tx) of the tile against the
+ * candidate slot (row, col) = (4 c + s / 64, s % 64) of the tile's candidate
+ * region, whose origin is (max(0, y_first - search/2), max(0, x_first -
+ * search/2)) with (y_first, x_first) the tile's first grid position;
+ * nchunks = ceil(region rows / 4).  idx/n as in dn_bm3d_match; workspace as
+ * dn_bm3d_match_workspace_bytes(1, H, W, p, DN_BF16). */
+dn_status dn_bm3d_match_cross_terms(const float *guide, int H, int W, const dn_bm3d_pass *p, float tau, int tile_x,
+                                    int tile_y, float *cross, int *idx, int *n, void *workspace, size_t ws_bytes,
+                                    dn_stream_t stream);
+
 /* Collaborative hard thresholding + aggregation (first pass) given match lists.
  * img: device [B][C][H][W] (already in the filtering colour space);
  * sigma_c: host [B*C] per-channel noise std; idx/n as produced by

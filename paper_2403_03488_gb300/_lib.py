@@ -77,6 +77,7 @@ def lib():
         "denoise_bm3d_noalloc": (i, [vp, vp, i, i, i, i, fp, P(BM3DParams), vp]),
         "dn_bm3d_match": (i, [vp, sz, i, i, i, P(BM3DPass), fp, i, vp, vp, vp, sz, vp]),
         "dn_bm3d_match_workspace_bytes": (sz, [i, i, i, P(BM3DPass), i]),
+        "dn_bm3d_match_cross_terms": (i, [vp, i, i, P(BM3DPass), f, i, i, vp, vp, vp, vp, sz, vp]),
         "dn_bm3d_filter_hard": (i, [vp, vp, vp, i, i, i, i, fp, P(BM3DPass), i, vp, vp, sz, vp]),
         "dn_bm3d_filter_wiener": (i, [vp, vp, vp, vp, i, i, i, i, fp, P(BM3DPass), i, vp, vp, sz, vp]),
         "dn_bm3d_filter_workspace_bytes": (sz, [i, i, i, i]),

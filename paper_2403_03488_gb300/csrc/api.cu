@@ -74,6 +74,7 @@ struct Bm3dWs {
     int *n;
     float *acc;
     float *basic;
+    int *mws;  // tensor-core matcher: deferred-reference list
     size_t bytes;
 };
 
@@ -90,6 +91,8 @@ Bm3dWs bm3d_layout(void *base, int B, int C, int H, int W, const dn_bm3d_params 
     w.n = cv.take<int>((size_t)B * Rm);
     w.acc = cv.take<float>(4 * (size_t)B * C * HW);
     w.basic = cv.take<float>((size_t)B * C * HW);
+    const size_t m1 = match_tc_workspace_bytes(B, H, W, p->hard), m2 = match_tc_workspace_bytes(B, H, W, p->wiener);
+    w.mws = p->precision == DN_BF16 ? cv.take<int>((m1 > m2 ? m1 : m2) / sizeof(int)) : nullptr;
     w.bytes = cv.off;
     return w;
 }
@@ -140,10 +143,28 @@ CnnWs cnn_layout(void *base, int N, int H, int W, const dn_cnn *c)
     return w;
 }
 
+// Block matching in the requested precision: the BF16 tensor-core prefilter
+// with exact FP32 re-rank (same result as FP32) when its tiling supports the
+// parameters, the exhaustive FP32 kernel otherwise.
+bool tc_match_supported(const dn_bm3d_pass &p)
+{
+    return p.n2 >= 2 && 7 * p.step + 2 * (p.search / 2) + 1 <= 64 && match_tc_smem_bytes(p.step, p.search) <= 200 * 1024;
+}
+
+dn_status match_any(const float *guide, size_t plane, int B, int H, int W, const dn_bm3d_pass &p, const float *tau,
+                    int precision, int *idx, int *n, int *mws, cudaStream_t s)
+{
+    if (precision == DN_BF16 && mws && tc_match_supported(p)) {
+        int *err = device_error_ptr();
+        if (!err) return DN_ECUDA;
+        return match_tc(guide, plane, B, H, W, p, tau, idx, n, err, mws, s);
+    }
+    return match_fp32(guide, plane, B, H, W, p, tau, idx, n, s);
+}
+
 dn_status run_bm3d(const float *noisy, float *out, int B, int C, int H, int W, const float *sigma,
                    const dn_bm3d_params *p, const Bm3dWs &w, cudaStream_t s)
 {
-    if (p->precision != DN_FP32) return DN_EUNSUPPORTED;
     const size_t HW = (size_t)H * W, N = (size_t)B * C * HW;
     const float *x = noisy;
     if (C == 3) {
@@ -161,12 +182,12 @@ dn_status run_bm3d(const float *noisy, float *out, int B, int C, int H, int W, c
         const size_t off = (size_t)b0 * C * HW;
         const size_t Nb = (size_t)nb * C * HW;
         // pass 1: match on channel 0 of the noisy image, hard thresholding
-        DN_TRY(match_fp32(x + off, (size_t)C * HW, nb, H, W, p->hard, tau1, w.idx, w.n, s));
+        DN_TRY(match_any(x + off, (size_t)C * HW, nb, H, W, p->hard, tau1, p->precision, w.idx, w.n, w.mws, s));
         if (cudaMemsetAsync(w.acc, 0, 4 * Nb * sizeof(float), s) != cudaSuccess) return DN_ECUDA;
         DN_TRY(filter_hard_fp32(x + off, w.idx, w.n, nb, C, H, W, sig, p->hard, w.acc, s));
         DN_TRY(normalize(w.acc, w.basic + off, nb, C, H, W, s));
         // pass 2: match on channel 0 of the basic estimate, Wiener filtering
-        DN_TRY(match_fp32(w.basic + off, (size_t)C * HW, nb, H, W, p->wiener, tau2, w.idx, w.n, s));
+        DN_TRY(match_any(w.basic + off, (size_t)C * HW, nb, H, W, p->wiener, tau2, p->precision, w.idx, w.n, w.mws, s));
         if (cudaMemsetAsync(w.acc, 0, 4 * Nb * sizeof(float), s) != cudaSuccess) return DN_ECUDA;
         DN_TRY(filter_wiener_fp32(x + off, w.basic + off, w.idx, w.n, nb, C, H, W, sig, p->wiener, w.acc, s));
         DN_TRY(normalize(w.acc, (C == 3 ? w.ycc : out) + off, nb, C, H, W, s));
@@ -381,12 +402,8 @@ const char *dn_strerror(dn_status st)
 
 size_t dn_bm3d_match_workspace_bytes(int B, int H, int W, const dn_bm3d_pass *p, int precision)
 {
-    (void)B;
-    (void)H;
-    (void)W;
-    (void)p;
-    (void)precision;
-    return 0;
+    if (precision != DN_BF16 || !valid_image(B, 1, H, W, 8) || !valid_pass(p)) return 0;
+    return match_tc_workspace_bytes(B, H, W, *p);
 }
 
 dn_status dn_bm3d_match(const float *guide, size_t plane_stride, int B, int H, int W, const dn_bm3d_pass *p,
@@ -394,15 +411,34 @@ dn_status dn_bm3d_match(const float *guide, size_t plane_stride, int B, int H, i
                         dn_stream_t stream)
 {
     DN_GUARD_BEGIN
-    (void)workspace;
-    (void)ws_bytes;
     if (!guide || !idx || !n || !tau || !valid_image(B, 1, H, W, 8) || !valid_pass(p) ||
         plane_stride < (size_t)H * W)
         return DN_EINVAL;
     for (int b = 0; b < B; ++b)
         if (!(tau[b] > 0.0f)) return DN_EINVAL;
-    if (precision != DN_FP32) return precision == DN_BF16 ? DN_EUNSUPPORTED : DN_EINVAL;
-    return match_fp32(guide, plane_stride, B, H, W, *p, tau, idx, n, (cudaStream_t)stream);
+    if (precision != DN_FP32 && precision != DN_BF16) return DN_EINVAL;
+    const size_t need = dn_bm3d_match_workspace_bytes(B, H, W, p, precision);
+    if (need > 0 && (!workspace || ws_bytes < need)) return DN_ENOMEM;
+    return match_any(guide, plane_stride, B, H, W, *p, tau, precision, idx, n, static_cast<int *>(workspace),
+                     (cudaStream_t)stream);
+    DN_GUARD_END
+}
+
+dn_status dn_bm3d_match_cross_terms(const float *guide, int H, int W, const dn_bm3d_pass *p, float tau, int tile_x,
+                                    int tile_y, float *cross, int *idx, int *n, void *workspace, size_t ws_bytes,
+                                    dn_stream_t stream)
+{
+    DN_GUARD_BEGIN
+    if (!guide || !cross || !idx || !n || !valid_image(1, 1, H, W, 8) || !valid_pass(p) || !tc_match_supported(*p) ||
+        !(tau > 0.0f))
+        return DN_EINVAL;
+    if (tile_x < 0 || tile_y < 0 || tile_x * 8 >= grid_count(W, 8, p->step) || tile_y * 16 >= grid_count(H, 8, p->step))
+        return DN_EINVAL;
+    if (!workspace || ws_bytes < match_tc_workspace_bytes(1, H, W, *p)) return DN_ENOMEM;
+    int *err = device_error_ptr();
+    if (!err) return DN_ECUDA;
+    return match_tc(guide, (size_t)H * W, 1, H, W, *p, &tau, idx, n, err, static_cast<int *>(workspace),
+                    (cudaStream_t)stream, cross, tile_x, tile_y);
     DN_GUARD_END
 }
 

@@ -94,6 +94,12 @@ dn_status relu_bwd(const float *g, const float *y, float *out, size_t count, cud
 dn_status l1_grad(const float *r, const float *pre, const float *clean, float *dr, size_t count, double *loss,
                   cudaStream_t s);
 int *device_error_ptr();
+size_t match_tc_smem_bytes(int step, int search);
+// fb_ws: device workspace of match_tc_workspace_bytes (deferred references)
+size_t match_tc_workspace_bytes(int B, int H, int W, const dn_bm3d_pass &p);
+dn_status match_tc(const float *guide, size_t plane, int B, int H, int W, const dn_bm3d_pass &p, const float *tau,
+                   int *idx, int *n, int *err, int *fb_ws, cudaStream_t s, float *cross = nullptr, int cross_tx = 0,
+                   int cross_ty = 0);
 size_t conv_tc_smem_bytes();
 dn_status pack_w_tc(const float *w, void *out, cudaStream_t s);
 dn_status conv3x3_tc(const void *x, void *y, const void *wpack, const float *bias, int N, int H, int W, int relu,

@@ -236,6 +236,82 @@ def test_match_full_size_sampled(oracle):
     assert bad == 0
 
 
+@pytest.mark.parametrize("H,W,sigma,n2,tau,basic", [(64, 72, 25.0, 16, 2500.0, False), (101, 67, 50.0, 16, 5000.0, False),
+                                                  (9, 13, 25.0, 16, 2500.0, False), (130, 97, 25.0, 32, 400.0, True),
+                                                  (70, 61, 15.0, 8, 400.0, True), (40, 300, 25.0, 2, 2500.0, False)])
+def test_match_tc_prefilter_equals_fp32_and_oracle(oracle, H, W, sigma, n2, tau, basic):
+    """BF16 tensor-core prefilter + exact FP32 re-rank: bit-identical match
+    lists to the exhaustive FP32 kernel, and oracle parity."""
+    A = api()
+    _, noisy = synth.make_batch([80, 81], H, W, sigma)
+    g = noisy[:, 0]
+    if basic:
+        g = np.stack([oracle.bm3d_pass1(noisy[b], [sigma], oracle.Pass())[0][0] for b in range(2)]).astype(np.float32)
+    p = A.default_bm3d_params().hard
+    p.n2 = n2
+    i32, n32 = A.bm3d_match(dev(g), [tau, tau], p, precision=A.DN_FP32)
+    itc, ntc = A.bm3d_match(dev(g), [tau, tau], p, precision=A.DN_BF16)
+    i32, n32, itc, ntc = host(i32), host(n32), host(itc), host(ntc)
+    np.testing.assert_array_equal(ntc, n32)
+    for b in range(2):
+        for ry in range(n32.shape[1]):
+            for rx in range(n32.shape[2]):
+                k = n32[b, ry, rx]
+                np.testing.assert_array_equal(itc[b, ry, rx, :k], i32[b, ry, rx, :k])
+        om = oracle.match(g[b], oracle.Pass(n2=n2, tau=tau))
+        check_match(oracle, itc[b], ntc[b], om, g[b], tau)
+    assert A.device_error() == 0
+
+
+@pytest.mark.parametrize("H,W,tx,ty", [(200, 180, 1, 1), (64, 72, 0, 0)])
+def test_tc_cross_terms_within_proven_bound(H, W, tx, ty):
+    """The BF16 tensor-core cross terms of a reference tile agree with the exact
+    dot products of the centred patches within the bound the prefilter relies
+    on: |x_hat - x| <= 0.00397 ||P_c|| ||Q_c|| (+1e-3)."""
+    A = api()
+    _, noisy = synth.make_batch([85], H, W, 25.0)
+    g = noisy[0, 0]
+    p = A.default_bm3d_params().hard
+    cross, (cy0, cx0) = A.bm3d_match_cross_terms(dev(g), p, 2500.0, tx, ty)
+    cross = host(cross)
+    gy, gx = A.grid(H), A.grid(W)
+    hs = 19
+    y_last = gy[min(ty * 16 + 15, len(gy) - 1)]
+    x_last = gx[min(tx * 8 + 7, len(gx) - 1)]
+    CH, CW = min(H - 8, y_last + hs) - cy0 + 1, min(W - 8, x_last + hs) - cx0 + 1
+    g64 = g.astype(np.float64)
+    checked = 0
+    for t in range(0, 128, 7):
+        ry, rx = ty * 16 + t // 8, tx * 8 + t % 8
+        if ry >= len(gy) or rx >= len(gx):
+            continue
+        P = g64[gy[ry]:gy[ry] + 8, gx[rx]:gx[rx] + 8]
+        Pc = P - P.mean()
+        for s in range(0, cross.shape[1] * 256, 5):
+            row, col = s // 64, s % 64
+            if row >= CH or col >= CW:
+                continue
+            Q = g64[cy0 + row:cy0 + row + 8, cx0 + col:cx0 + col + 8]
+            Qc = Q - Q.mean()
+            x = (Pc * Qc).sum()
+            bound = 0.00397 * np.sqrt((Pc ** 2).sum() * (Qc ** 2).sum()) + 1e-3
+            assert abs(cross[t, row // 4, s % 256] - x) <= bound, (t, row, col, cross[t, row // 4, s % 256], x)
+            checked += 1
+    assert checked > 500
+
+
+def test_bm3d_with_tc_matching_equals_fp32():
+    """With the BF16-prefiltered matcher the match lists are the FP32 ones, so
+    the BM3D output is bit-identical (the filtering stays FP32)."""
+    A = api()
+    _, noisy = synth.make_batch([90, 91], 150, 170, [25.0, 50.0])
+    x = dev(noisy)
+    a = host(A.denoise_bm3d(x, [25.0, 50.0], A.default_bm3d_params(precision=A.DN_FP32)))
+    b = host(A.denoise_bm3d(x, [25.0, 50.0], A.default_bm3d_params(precision=A.DN_BF16)))
+    assert np.array_equal(a, b)
+    assert A.device_error() == 0
+
+
 def test_denoise_bm3d_is_bitwise_reproducible():
     """Aggregation sums are exact (fixed point), so repeated runs, with other
     work in between, give bit-identical outputs."""
