@@ -89,7 +89,7 @@ Bm3dWs bm3d_layout(void *base, int B, int C, int H, int W, const dn_bm3d_params 
     w.ycc = C == 3 ? cv.take<float>((size_t)B * 3 * HW) : nullptr;
     w.idx = cv.take<int>((size_t)B * Rm * n2);
     w.n = cv.take<int>((size_t)B * Rm);
-    w.acc = cv.take<float>(4 * (size_t)B * C * HW);
+    w.acc = cv.take<float>(kAccBytesPerPixel / sizeof(float) * (size_t)B * C * HW);
     w.basic = cv.take<float>((size_t)B * C * HW);
     const size_t m1 = match_tc_workspace_bytes(B, H, W, p->hard), m2 = match_tc_workspace_bytes(B, H, W, p->wiener);
     w.mws = p->precision == DN_BF16 ? cv.take<int>((m1 > m2 ? m1 : m2) / sizeof(int)) : nullptr;
@@ -183,12 +183,12 @@ dn_status run_bm3d(const float *noisy, float *out, int B, int C, int H, int W, c
         const size_t Nb = (size_t)nb * C * HW;
         // pass 1: match on channel 0 of the noisy image, hard thresholding
         DN_TRY(match_any(x + off, (size_t)C * HW, nb, H, W, p->hard, tau1, p->precision, w.idx, w.n, w.mws, s));
-        if (cudaMemsetAsync(w.acc, 0, 4 * Nb * sizeof(float), s) != cudaSuccess) return DN_ECUDA;
+        if (cudaMemsetAsync(w.acc, 0, kAccBytesPerPixel * Nb, s) != cudaSuccess) return DN_ECUDA;
         DN_TRY(filter_hard_fp32(x + off, w.idx, w.n, nb, C, H, W, sig, p->hard, w.acc, s));
         DN_TRY(normalize(w.acc, w.basic + off, nb, C, H, W, s));
         // pass 2: match on channel 0 of the basic estimate, Wiener filtering
         DN_TRY(match_any(w.basic + off, (size_t)C * HW, nb, H, W, p->wiener, tau2, p->precision, w.idx, w.n, w.mws, s));
-        if (cudaMemsetAsync(w.acc, 0, 4 * Nb * sizeof(float), s) != cudaSuccess) return DN_ECUDA;
+        if (cudaMemsetAsync(w.acc, 0, kAccBytesPerPixel * Nb, s) != cudaSuccess) return DN_ECUDA;
         DN_TRY(filter_wiener_fp32(x + off, w.basic + off, w.idx, w.n, nb, C, H, W, sig, p->wiener, w.acc, s));
         DN_TRY(normalize(w.acc, (C == 3 ? w.ycc : out) + off, nb, C, H, W, s));
     }
@@ -445,7 +445,7 @@ dn_status dn_bm3d_match_cross_terms(const float *guide, int H, int W, const dn_b
 size_t dn_bm3d_filter_workspace_bytes(int B, int C, int H, int W)
 {
     if (!valid_image(B, C, H, W, 8)) return 0;
-    return align256(4 * (size_t)B * C * H * W * sizeof(float));
+    return align256(kAccBytesPerPixel * (size_t)B * C * H * W);
 }
 
 static dn_status filter_entry(bool wiener, const float *img, const float *basic, const int *idx, const int *n, int B,
@@ -464,7 +464,7 @@ static dn_status filter_entry(bool wiener, const float *img, const float *basic,
     for (int b0 = 0; b0 < B; b0 += 1024) {
         const int nb = B - b0 < 1024 ? B - b0 : 1024;
         const size_t off = (size_t)b0 * C * HW, R = (size_t)grid_count(H, 8, p->step) * grid_count(W, 8, p->step);
-        if (cudaMemsetAsync(acc, 0, 4 * (size_t)nb * C * HW * sizeof(float), s) != cudaSuccess) return DN_ECUDA;
+        if (cudaMemsetAsync(acc, 0, kAccBytesPerPixel * (size_t)nb * C * HW, s) != cudaSuccess) return DN_ECUDA;
         const int *ib = idx + (size_t)b0 * R * p->n2;
         const int *nbp = n + (size_t)b0 * R;
         if (wiener)

@@ -16,13 +16,14 @@
 //
 // Layout: a CTA owns a tile of reference positions and aggregates its groups
 // into a shared-memory window first (one global add per window pixel instead
-// of one per contribution).  A warp filters one group at a time: lane k owns
-// patch k and computes its 8x8 DCT in registers with an even/odd fast DCT;
-// the group passes through a per-warp transpose buffer (rows of 65 floats,
-// conflict-free both ways) so that, for the group transform, each lane owns
-// two coefficient positions across all patches and runs the Walsh-Hadamard
-// butterflies in registers; the inverse goes back the same way and each lane
-// aggregates its own patch.
+// of one per contribution).  A warp filters one group at a time (in the first
+// pass, two groups of at most 16 patches at once): lane k owns patch k and
+// computes its 8x8 DCT in registers with an even/odd fast DCT; the group
+// passes through a per-warp transpose buffer (rows of 65 floats, conflict-free
+// both ways) so that, for the group transform, each lane owns two coefficient
+// positions across all patches and runs the Walsh-Hadamard butterflies in
+// registers; the inverse goes back the same way, and the warp then aggregates
+// patch by patch with its lanes spread over the 64 pixels.
 #include <cmath>
 
 #include "common.cuh"
@@ -44,7 +45,8 @@ struct FilterArgs {
     const float *basic;  // pass 2 only
     const int *idx;
     const int *n;
-    unsigned long long *num, *den;  // exact fixed-point accumulation planes, same layout as img
+    unsigned long long *num, *den;        // exact fixed-point accumulation planes, same layout as img
+    unsigned long long *num_hi, *den_hi;  // their high words (signed, units of 2^32)
     int C, H, W, R, Rx, Ry, n2, step, hs;
     float lambda;
     float sig[kChunk * 3];
@@ -225,152 +227,224 @@ __device__ __forceinline__ int hard_columns(float *T, int n, int lane, float thr
 
 // ---- exact aggregation ---------------------------------------------------------
 
-// Every contribution becomes a signed 64-bit fixed-point number with 36
-// fraction bits (its FP32 value is exact whenever |v| >= 2^-13) and is summed
-// with integer atomics, so num and den are bitwise reproducible whatever the
-// order of the groups.  Weights are used scaled by sigma^2 (1/N_har,
-// 1/sum w^2, or sigma^2 for an all-zero group), which leaves num/den unchanged
-// and keeps den below 2^23 for sigma <= 255 (no overflow: 2^59 < 2^63).
-__device__ __forceinline__ unsigned long long to_fixed(float v)
+// Every contribution becomes a signed fixed-point number with 36 fraction bits
+// (exact whenever the FP32 value is >= 2^-13 in magnitude) and is summed with
+// integer atomics, so num and den are bitwise reproducible whatever the order
+// of the groups.  Weights are used scaled by sigma^2 (1/N_har, 1/sum w^2, or
+// sigma^2 for an all-zero group), which leaves num/den unchanged.
+//
+// A contribution c with |c| < 512 (all of them, in practice) is added to the
+// 64-bit main plane as round(c 2^36) < 2^45; any other c (a heavy weight or a
+// large value) is clamped to |c| <= 2^40 and split as c 2^36 = hi 2^32 + lo,
+// 0 <= lo <= 2^32: lo goes to the main plane, hi to a high-word plane.  With at
+// most 2^14 contributions per pixel neither plane can overflow, and the value
+// is main + hi 2^32.
+
+// round(c 2^36) (ties to even) for |c| < 512, on the FP32 and integer pipes:
+// t = c 2^13 is split into its nearest integer A (magic-number rounding, valid
+// for |t| < 2^22) and the exact remainder r, |r| <= 1/2; then
+// round(c 2^36) = A 2^23 + round(r 2^23).
+__device__ __forceinline__ long long fix_fast(float c)
 {
-    return (unsigned long long)__float2ll_rn(v * 68719476736.0f);  // 2^36
+    const float M = 12582912.0f;  // 1.5 * 2^23
+    const float t = c * 8192.0f;
+    const float ta = t + M;
+    const int A = __float_as_int(ta) - 0x4B400000;
+    const float r = t - (ta - M);
+    const int Bq = __float_as_int(fmaf(r, 8388608.0f, M)) - 0x4B400000;
+    return (long long)A * 8388608ll + Bq;
+}
+
+struct Fix {
+    unsigned long long lo;  // main-plane part
+    long long hi;           // high-word part (0 on the fast path)
+};
+
+__device__ __forceinline__ Fix to_fixed(float c)
+{
+    Fix f;
+    if (fabsf(c) < 512.0f) {
+        f.lo = (unsigned long long)fix_fast(c);
+        f.hi = 0;
+    } else {
+        const float s = fminf(fmaxf(c, -1099511627776.0f), 1099511627776.0f) * 16.0f;  // |c| <= 2^40, times 2^4
+        const float fl = floorf(s);
+        f.hi = (long long)fl;
+        f.lo = (unsigned long long)__float2ll_rn((s - fl) * 4294967296.0f);
+    }
+    return f;
 }
 
 // Shared-memory aggregation window of one CTA: pixels [Y0, Y0+RH) x [X0, X0+RW)
-// of the current channel, num then den planes.
+// of the current channel, num then den planes, row stride RS (RS = 8 mod 16
+// words, so that two rows of 8 consecutive 64-bit words fill all 32 banks).
 struct Window {
-    unsigned long long *acc;  // [2][RH][RW] fixed point
-    int X0, Y0, RH, RW;
+    unsigned long long *acc;  // [2][RH][RS] fixed point
+    int X0, Y0, RH, RW, RS;
 };
 
-// Loads the group's positions (lane k < n gets patch k); returns n (0 if the list is invalid).
-__device__ __forceinline__ int load_group(const FilterArgs &a, int b, int r, int lane, int &py, int &px)
+// Loads a group's positions into lanes [base, base+n) (lane base+k gets patch
+// k; other lanes keep theirs).  Returns n, 0 if the list is invalid (the group
+// is skipped), or -n if it does not fit below row 32 (nothing loaded).
+__device__ __forceinline__ int load_group(const FilterArgs &a, int b, int r, int lane, int base, int &py, int &px)
 {
     const size_t gr = (size_t)b * a.R + r;
     const int n = a.n[gr];
     if (n < 1 || n > a.n2 || n > kNMax || (n & (n - 1)) != 0) return 0;
-    const int id = lane < n ? a.idx[gr * a.n2 + lane] : 0;
-    py = id / a.W;
-    px = id - py * a.W;
-    const bool bad = lane < n && (id < 0 || py > a.H - 8 || px > a.W - 8);
-    if (__any_sync(0xffffffffu, bad)) return 0;  // invalid list: the group is skipped
+    if (base + n > 32) return -n;
+    const bool mine = lane >= base && lane < base + n;
+    const int id = mine ? a.idx[gr * a.n2 + lane - base] : 0;
+    const int y = id / a.W, x = id - (id / a.W) * a.W;
+    const bool bad = mine && (id < 0 || y > a.H - 8 || x > a.W - 8);
+    if (__any_sync(0xffffffffu, bad)) return 0;
+    if (mine) {
+        py = y;
+        px = x;
+    }
     return n;
 }
 
-// Coalesced gather of the group's patches into T (row k = patch k, 64 floats).
-__device__ __forceinline__ void gather_rows(float *T, const float *ch, int W, int n, int lane, int py, int px)
+// Coalesced gather of n patches into rows [s, s+n) of T (row s+k = patch k).
+__device__ __forceinline__ void gather_rows(float *T, const float *ch, int W, int s, int n, int lane, int py, int px)
 {
     for (int e = lane; e < n * 64; e += 32) {
-        const int k = e >> 6, p = e & 63;
+        const int k = s + (e >> 6), p = e & 63;
         const int yk = __shfl_sync(0xffffffffu, py, k), xk = __shfl_sync(0xffffffffu, px, k);
         T[k * kTS + p] = ch[(size_t)(yk + (p >> 3)) * W + xk + (p & 7)];
     }
 }
 
-// Lane k < n: 2D DCT of its patch (row k of T), written back as coefficients.
-__device__ __forceinline__ void dct_own_row(float *T, int n, int lane, const DctK &K)
+// Lane-per-row 2D DCT (or its inverse) of row `lane` of T, in place.
+template <bool INVERSE>
+__device__ __forceinline__ void dct_own_row(float *T, bool valid, int lane, const DctK &K)
 {
-    if (lane < n) {
+    if (valid) {
         float v[64];
 #pragma unroll
         for (int p = 0; p < 64; ++p) v[p] = T[lane * kTS + p];
-        dct2d_rows_cols<0>(v, K);
+        if (INVERSE)
+            idct2d_cols_rows<0>(v, K);
+        else
+            dct2d_rows_cols<0>(v, K);
 #pragma unroll
         for (int p = 0; p < 64; ++p) T[lane * kTS + p] = v[p];
     }
 }
 
-// Wiener transform of one group of N patches: gains from the basic-estimate
-// group (kept in registers), applied to the noisy group, both through T.
+// Wiener transform of one group of N patches (rows [0, N) of T): gains from
+// the basic-estimate group (kept in registers), applied to the noisy group;
+// T is left holding the filtered spectra of the noisy patches.
 template <int N>
 __device__ __forceinline__ float wiener_group(const FilterArgs &a, float *T, size_t cbase, int lane, int py, int px,
                                               float s2)
 {
-    gather_rows(T, a.basic + cbase, a.W, N, lane, py, px);
+    gather_rows(T, a.basic + cbase, a.W, 0, N, lane, py, px);
     __syncwarp();
-    dct_own_row(T, N, lane, a.k);
+    dct_own_row<false>(T, lane < N, lane, a.k);
     __syncwarp();
     float om0[N], om1[N];
     const float wsq = wiener_gains<N>(T, lane, s2, om0) + wiener_gains<N>(T, lane + 32, s2, om1);
     __syncwarp();
-    gather_rows(T, a.img + cbase, a.W, N, lane, py, px);
+    gather_rows(T, a.img + cbase, a.W, 0, N, lane, py, px);
     __syncwarp();
-    dct_own_row(T, N, lane, a.k);
+    dct_own_row<false>(T, lane < N, lane, a.k);
     __syncwarp();
     wiener_apply<N>(T, lane, om0);
     wiener_apply<N>(T, lane + 32, om1);
     return wsq;
 }
 
-// One group on channel c: transforms, shrinkage, inverse, aggregation.
-template <bool WIENER>
-__device__ __forceinline__ void filter_group(const FilterArgs &a, const Window &win, float *T, int b, int c, int n,
-                                             int lane, int py, int px, unsigned long long *sden)
+// Aggregation of the estimates in rows [s, s+n) of T (one group, weight w):
+// the warp walks the patches and its lanes cover the 64 pixels of each (lane
+// l: pixels l and l+32), so the window atomics of one instruction hit 4 rows
+// of 8 consecutive words (no bank conflict).
+__device__ __forceinline__ void aggregate(const FilterArgs &a, const Window &win, const float *T, size_t cbase, int s,
+                                          int n, int lane, int py, int px, float w, const float (&ka)[2])
 {
-    const size_t HW = (size_t)a.H * a.W;
-    const size_t cbase = ((size_t)b * a.C + c) * HW;
-    const float sig = a.sig[b * 3 + c];
-    float w;
-    if (!WIENER) {
-        gather_rows(T, a.img + cbase, a.W, n, lane, py, px);
-        __syncwarp();
-        dct_own_row(T, n, lane, a.k);
-        __syncwarp();
-        const int cnt = hard_columns(T, n, lane, a.lambda * sig);
-        const int nhar = __reduce_add_sync(0xffffffffu, cnt);
-        w = nhar > 0 ? 1.0f / (float)nhar : sig * sig;  // 1/(sigma^2 N_har) or 1, times sigma^2
-    } else {
-        const float s2 = sig * sig;
-        float wsq;
-        switch (n) {
-            case 1: wsq = wiener_group<1>(a, T, cbase, lane, py, px, s2); break;
-            case 2: wsq = wiener_group<2>(a, T, cbase, lane, py, px, s2); break;
-            case 4: wsq = wiener_group<4>(a, T, cbase, lane, py, px, s2); break;
-            case 8: wsq = wiener_group<8>(a, T, cbase, lane, py, px, s2); break;
-            case 16: wsq = wiener_group<16>(a, T, cbase, lane, py, px, s2); break;
-            default: wsq = wiener_group<32>(a, T, cbase, lane, py, px, s2); break;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) wsq += __shfl_xor_sync(0xffffffffu, wsq, o);
-        w = wsq > 0.0f ? 1.0f / wsq : s2;               // 1/(sigma^2 sum w^2) or 1, times sigma^2
-    }
-    const float *TY = T;
-    // den contributions w * kaiser(i) kaiser(j) are the same for every patch
-    sden[lane] = to_fixed(w * a.kai[lane]);
-    sden[lane + 32] = to_fixed(w * a.kai[lane + 32]);
-    __syncwarp();
-    if (lane < n) {
-        float v[64];
-#pragma unroll
-        for (int p = 0; p < 64; ++p) v[p] = TY[lane * kTS + p];
-        idct2d_cols_rows<0>(v, a.k);
-        const int ly0 = py - win.Y0, lx0 = px - win.X0;
+    const Fix d0 = to_fixed(w * ka[0]), d1 = to_fixed(w * ka[1]);
+    unsigned long long *wn = win.acc, *wd = win.acc + (size_t)win.RH * win.RS;
+    const int i0 = lane >> 3, j = lane & 7;
+    for (int k = s; k < s + n; ++k) {
+        const int yk = __shfl_sync(0xffffffffu, py, k), xk = __shfl_sync(0xffffffffu, px, k);
+        const int ly0 = yk - win.Y0, lx0 = xk - win.X0;
         const bool inside = ly0 >= 0 && ly0 + 8 <= win.RH && lx0 >= 0 && lx0 + 8 <= win.RW;
-        unsigned long long *wn = win.acc, *wd = win.acc + win.RH * win.RW;
 #pragma unroll
-        for (int p = 0; p < 64; ++p) {
-            const int i = p >> 3, j = p & 7;
-            const unsigned long long fn = to_fixed(w * a.kai[p] * v[p]);
+        for (int h = 0; h < 2; ++h) {
+            const int i = i0 + 4 * h;
+            const Fix fn = to_fixed(w * ka[h] * T[k * kTS + lane + 32 * h]);
+            const Fix &fd = h ? d1 : d0;
+            const size_t pix = cbase + (size_t)(yk + i) * a.W + xk + j;
+            if (fn.hi != 0) atomicAdd(a.num_hi + pix, (unsigned long long)fn.hi);
+            if (fd.hi != 0) atomicAdd(a.den_hi + pix, (unsigned long long)fd.hi);
             if (inside) {
-                const int at = (ly0 + i) * win.RW + lx0 + j;
-                atomicAdd(wn + at, fn);
-                atomicAdd(wd + at, sden[p]);
+                const int at = (ly0 + i) * win.RS + lx0 + j;
+                atomicAdd(wn + at, fn.lo);
+                atomicAdd(wd + at, fd.lo);
             } else {
-                const size_t pix = cbase + (size_t)(py + i) * a.W + px + j;
-                atomicAdd(a.num + pix, fn);
-                atomicAdd(a.den + pix, sden[p]);
+                atomicAdd(a.num + pix, fn.lo);
+                atomicAdd(a.den + pix, fd.lo);
             }
         }
     }
+}
+
+// First pass on one batch of at most two groups: group A in rows [0, nA),
+// group B (nB may be 0) in rows [16, 16+nB).  Positions are already loaded.
+__device__ __forceinline__ void hard_batch(const FilterArgs &a, const Window &win, float *T, size_t cbase, float sig,
+                                           int nA, int nB, int lane, int py, int px, const float (&ka)[2])
+{
+    gather_rows(T, a.img + cbase, a.W, 0, nA, lane, py, px);
+    if (nB) gather_rows(T, a.img + cbase, a.W, 16, nB, lane, py, px);
+    const bool valid = lane < nA || (lane >= 16 && lane < 16 + nB);
+    __syncwarp();
+    dct_own_row<false>(T, valid, lane, a.k);
+    __syncwarp();
+    const float thr = a.lambda * sig;
+    const int nharA = __reduce_add_sync(0xffffffffu, hard_columns(T, nA, lane, thr));
+    const int nharB = nB ? __reduce_add_sync(0xffffffffu, hard_columns(T + 16 * kTS, nB, lane, thr)) : 0;
+    // 1/(sigma^2 N_har), or 1 when nothing survives, both times sigma^2
+    const float wA = nharA > 0 ? 1.0f / (float)nharA : sig * sig;
+    const float wB = nharB > 0 ? 1.0f / (float)nharB : sig * sig;
+    __syncwarp();
+    dct_own_row<true>(T, valid, lane, a.k);
+    __syncwarp();
+    aggregate(a, win, T, cbase, 0, nA, lane, py, px, wA, ka);
+    if (nB) aggregate(a, win, T, cbase, 16, nB, lane, py, px, wB, ka);
+    __syncwarp();
+}
+
+// Second pass on one group of n patches (rows [0, n)).
+__device__ __forceinline__ void wiener_one(const FilterArgs &a, const Window &win, float *T, size_t cbase, float sig,
+                                           int n, int lane, int py, int px, const float (&ka)[2])
+{
+    const float s2 = sig * sig;
+    float wsq;
+    switch (n) {
+        case 1: wsq = wiener_group<1>(a, T, cbase, lane, py, px, s2); break;
+        case 2: wsq = wiener_group<2>(a, T, cbase, lane, py, px, s2); break;
+        case 4: wsq = wiener_group<4>(a, T, cbase, lane, py, px, s2); break;
+        case 8: wsq = wiener_group<8>(a, T, cbase, lane, py, px, s2); break;
+        case 16: wsq = wiener_group<16>(a, T, cbase, lane, py, px, s2); break;
+        default: wsq = wiener_group<32>(a, T, cbase, lane, py, px, s2); break;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) wsq += __shfl_xor_sync(0xffffffffu, wsq, o);
+    const float w = wsq > 0.0f ? 1.0f / wsq : s2;  // 1/(sigma^2 sum w^2) or 1, times sigma^2
+    __syncwarp();
+    dct_own_row<true>(T, lane < n, lane, a.k);
+    __syncwarp();
+    aggregate(a, win, T, cbase, 0, n, lane, py, px, w, ka);
     __syncwarp();
 }
 
 // A CTA owns a TR x TR tile of reference positions; its warps filter the
 // tile's groups channel by channel and accumulate into the shared window
 // covering every patch those groups can hold (tile + search radius + patch),
-// then add the window once to the global fixed-point planes.
+// then add the window once to the global fixed-point planes.  In the first
+// pass a warp takes the tile's references two at a time and filters both
+// groups together when each has at most 16 patches.
 template <bool WIENER>
-__global__ void __launch_bounds__(WIENER ? 384 : 512) k_filter(FilterArgs a, int TR, int RH, int RW)
+__global__ void __launch_bounds__(WIENER ? 384 : 512) k_filter(FilterArgs a, int TR, int RH, int RW, int RS)
 {
     extern __shared__ __align__(16) unsigned char dsm_raw[];
     const int nw = blockDim.x >> 5;
@@ -378,8 +452,8 @@ __global__ void __launch_bounds__(WIENER ? 384 : 512) k_filter(FilterArgs a, int
     win.acc = reinterpret_cast<unsigned long long *>(dsm_raw);
     win.RH = RH;
     win.RW = RW;
-    unsigned long long *sdens = win.acc + (size_t)2 * RH * RW;                   // [nw][64]
-    float *tbufs = reinterpret_cast<float *>(sdens + (size_t)nw * 64);           // [nw][32][65]
+    win.RS = RS;
+    float *tbufs = reinterpret_cast<float *>(win.acc + (size_t)2 * RH * RS);  // [nw][32][65]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int b = blockIdx.z;
     const int rx0 = blockIdx.x * TR, ry0 = blockIdx.y * TR;
@@ -387,33 +461,50 @@ __global__ void __launch_bounds__(WIENER ? 384 : 512) k_filter(FilterArgs a, int
     const int gx0 = min(rx0 * a.step, a.W - 8), gy0 = min(ry0 * a.step, a.H - 8);
     win.X0 = max(0, gx0 - a.hs);
     win.Y0 = max(0, gy0 - a.hs);
+    const float ka[2] = {a.kai[lane], a.kai[lane + 32]};
 
     float *T = tbufs + (size_t)warp * 32 * kTS;
-    unsigned long long *sden = sdens + warp * 64;
-    const int tw = min(TR, Rx - rx0), th = min(TR, Ry - ry0);
+    const int tw = min(TR, Rx - rx0), th = min(TR, Ry - ry0), cnt = tw * th;
     const size_t HW = (size_t)a.H * a.W;
     const int rh = min(RH, a.H - win.Y0), rw = min(RW, a.W - win.X0);
-    const int wtot = 2 * RH * RW;
+    const int wtot = 2 * RH * RS;
+    auto ref_of = [&](int q) { return (ry0 + q / tw) * Rx + rx0 + q % tw; };
 
     for (int c = 0; c < a.C; ++c) {
+        const size_t cbase = ((size_t)b * a.C + c) * HW;
+        const float sig = a.sig[b * 3 + c];
         for (int i = threadIdx.x; i < wtot; i += blockDim.x) win.acc[i] = 0ull;
         __syncthreads();
-        for (int q = warp; q < tw * th; q += nw) {
-            const int ry = ry0 + q / tw, rx = rx0 + q % tw;
-            int py = 0, px = 0;
-            const int n = load_group(a, b, ry * Rx + rx, lane, py, px);
-            if (n == 0) continue;
-            filter_group<WIENER>(a, win, T, b, c, n, lane, py, px, sden);
+        if (WIENER) {
+            for (int q = warp; q < cnt; q += nw) {
+                int py = 0, px = 0;
+                const int n = load_group(a, b, ref_of(q), lane, 0, py, px);
+                if (n > 0) wiener_one(a, win, T, cbase, sig, n, lane, py, px, ka);
+            }
+        } else {
+            for (int q = 2 * warp; q < cnt; q += 2 * nw) {
+                int py = 0, px = 0;
+                const int nA = load_group(a, b, ref_of(q), lane, 0, py, px);
+                int nB = 0;
+                if (q + 1 < cnt) {
+                    nB = nA > 0 && nA <= 16 ? load_group(a, b, ref_of(q + 1), lane, 16, py, px) : -1;
+                    if (nB < 0 || nB > 16) nB = -1;  // filtered on its own below
+                }
+                if (nA > 0) hard_batch(a, win, T, cbase, sig, nA, nB > 0 ? nB : 0, lane, py, px, ka);
+                if (nB < 0) {
+                    const int n = load_group(a, b, ref_of(q + 1), lane, 0, py, px);
+                    if (n > 0) hard_batch(a, win, T, cbase, sig, n, 0, lane, py, px, ka);
+                }
+            }
         }
         __syncthreads();
-        const unsigned long long *wn = win.acc, *wd = win.acc + RH * RW;
-        const size_t cbase = ((size_t)b * a.C + c) * HW;
+        const unsigned long long *wn = win.acc, *wd = win.acc + (size_t)RH * RS;
         for (int i = threadIdx.x; i < rh * rw; i += blockDim.x) {
             const int ly = i / rw, lx = i - ly * rw;
-            const unsigned long long d = wd[ly * RW + lx];
+            const unsigned long long d = wd[ly * RS + lx];
             if (d != 0ull) {
                 const size_t pix = cbase + (size_t)(win.Y0 + ly) * a.W + win.X0 + lx;
-                atomicAdd(a.num + pix, wn[ly * RW + lx]);
+                atomicAdd(a.num + pix, wn[ly * RS + lx]);
                 atomicAdd(a.den + pix, d);
             }
         }
@@ -421,11 +512,17 @@ __global__ void __launch_bounds__(WIENER ? 384 : 512) k_filter(FilterArgs a, int
     }
 }
 
-__global__ void k_normalize(const long long *num, const long long *den, float *out, size_t count)
+__global__ void k_normalize(const long long *num, const long long *den, const long long *num_hi,
+                            const long long *den_hi, float *out, size_t count)
 {
-    // the 2^36 scale cancels in the ratio
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
-        out[i] = (float)((double)num[i] / (double)den[i]);
+    // the 2^36 scale cancels in the ratio; the high words are almost always 0
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+        double nu = (double)num[i], de = (double)den[i];
+        const long long nh = num_hi[i], dh = den_hi[i];
+        if (nh != 0) nu += (double)nh * 4294967296.0;
+        if (dh != 0) de += (double)dh * 4294967296.0;
+        out[i] = (float)(nu / de);
+    }
 }
 
 DctK make_dct_constants()
@@ -464,14 +561,15 @@ dn_status filter_common(bool wiener, const float *img, const float *basic, const
     const size_t HW = (size_t)H * W, N = (size_t)B * C * HW;
     // tile of references per CTA and its aggregation window
     const int nwarps = wiener ? 12 : 16;
-    const size_t per_warp = (size_t)32 * kTS * sizeof(float) + 64 * sizeof(unsigned long long);
+    const size_t per_warp = (size_t)32 * kTS * sizeof(float);
     int TR = 16;
-    int RH = 0, RW = 0;
+    int RH = 0, RW = 0, RS = 0;
     size_t smem = 0;
     for (; TR >= 1; TR /= 2) {
         RH = (TR - 1) * p.step + 2 * a.hs + 8;
         RW = RH;
-        smem = (size_t)nwarps * per_warp + (size_t)2 * RH * RW * sizeof(unsigned long long);
+        RS = RW + ((8 - RW % 16) + 16) % 16;  // row stride = 8 (mod 16) words
+        smem = (size_t)nwarps * per_warp + (size_t)2 * RH * RS * sizeof(unsigned long long);
         if (smem <= 225 * 1024) break;
     }
     if (TR < 1) return DN_EUNSUPPORTED;
@@ -488,13 +586,15 @@ dn_status filter_common(bool wiener, const float *img, const float *basic, const
         unsigned long long *fx = reinterpret_cast<unsigned long long *>(acc);
         a.num = fx + off;
         a.den = fx + N + off;
+        a.num_hi = fx + 2 * N + off;
+        a.den_hi = fx + 3 * N + off;
         for (int i = 0; i < nb; ++i)
             for (int c = 0; c < 3; ++c) a.sig[i * 3 + c] = c < C ? sig[(size_t)(b0 + i) * C + c] : 0.0f;
         dim3 grid((a.Rx + TR - 1) / TR, (a.Ry + TR - 1) / TR, nb);
         dn_status st = wiener ? launch("bm3d_filter_wiener_fp32", s,
-                                       [&] { k_filter<true><<<grid, nwarps * 32, smem, s>>>(a, TR, RH, RW); })
+                                       [&] { k_filter<true><<<grid, nwarps * 32, smem, s>>>(a, TR, RH, RW, RS); })
                               : launch("bm3d_filter_hard_fp32", s,
-                                       [&] { k_filter<false><<<grid, nwarps * 32, smem, s>>>(a, TR, RH, RW); });
+                                       [&] { k_filter<false><<<grid, nwarps * 32, smem, s>>>(a, TR, RH, RW, RS); });
         if (st != DN_OK) return st;
     }
     return DN_OK;
@@ -521,7 +621,7 @@ dn_status normalize(const float *acc, float *out, int B, int C, int H, int W, cu
     if (blocks > 152 * 16) blocks = 152 * 16;
     return launch("bm3d_normalize", s, [&] {
         const long long *fx = reinterpret_cast<const long long *>(acc);
-        k_normalize<<<blocks, 256, 0, s>>>(fx, fx + N, out, N);
+        k_normalize<<<blocks, 256, 0, s>>>(fx, fx + N, fx + 2 * N, fx + 3 * N, out, N);
     });
 }
 

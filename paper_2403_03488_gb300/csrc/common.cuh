@@ -71,6 +71,10 @@ inline int grid_count(int L, int patch, int step)
     return last / step + 1 + (last % step != 0 ? 1 : 0);
 }
 
+// Aggregation accumulators of the filtering passes: four 64-bit planes (num,
+// den, and their high words num_hi, den_hi) per image pixel.
+constexpr size_t kAccBytesPerPixel = 4 * sizeof(long long);
+
 // ---- launchers implemented in the .cu files -------------------------------
 dn_status match_fp32(const float *guide, size_t plane, int B, int H, int W, const dn_bm3d_pass &p,
                      const float *tau, int *idx, int *n, cudaStream_t s);

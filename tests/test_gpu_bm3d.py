@@ -159,6 +159,39 @@ def test_filter_wiener_parity_given_oracle_basic(oracle, C, H, W, sigma):
     assert err.max() <= TOL, err.max()
 
 
+def test_filter_parity_with_heavy_weights_and_large_values(oracle):
+    """Contributions beyond the fast fixed-point range: values up to ~1000
+    (the image scaled by 4, so w kai v >= 512 in the bright parts), an exact
+    zero block where every 3D coefficient is thresholded (N_har = 0, weight
+    sigma^2 = 10^4 after scaling), and for the Wiener pass a basic estimate
+    that is 0.2 on a block (sum of squared gains ~1e-4, weight ~1e4)."""
+    A = api()
+    H, W, sigma = 56, 64, 100.0
+    _, noisy = synth.make_batch([77], H, W, 25.0)
+    img = (noisy[0] * 4.0).astype(np.float32)
+    img[:, 8:32, 30:54] = 0.0
+    sc = [sigma]
+    P1, P2 = oracle.default_passes(sigma)
+    om = oracle.match(img[0].astype(np.float64), P1)
+    basic, pf, _ = oracle.bm3d_pass1(img.astype(np.float64), sc, P1, band=4 * BAND)
+    hard = A.default_bm3d_params().hard
+    hard.tau = P1.tau
+    out = host(A.bm3d_filter_hard(dev(img[None]), dev(om["idx"][None].astype(np.int32)),
+                                  dev(om["n"][None].astype(np.int32)), sc, hard))
+    ok = (pf & oracle.FLAG_THR) == 0
+    assert ok.mean() > 0.5
+    assert np.abs(out[0] - basic)[:, ok].max() <= 4 * TOL
+    basic32 = basic.astype(np.float32)
+    basic32[:, 30:50, 4:28] = 0.2
+    om2 = oracle.match(basic32[0].astype(np.float64), P2)
+    final, _, _ = oracle.bm3d_pass2(img.astype(np.float64), basic32.astype(np.float64), sc, P2)
+    p = A.default_bm3d_params().wiener
+    p.tau = P2.tau
+    out2 = host(A.bm3d_filter_wiener(dev(img[None]), dev(basic32[None]), dev(om2["idx"][None].astype(np.int32)),
+                                     dev(om2["n"][None].astype(np.int32)), sc, p))
+    assert np.abs(out2[0] - final).max() <= 4 * TOL
+
+
 @pytest.mark.parametrize("C,H,W,sigmas", [(1, 96, 96, (25.0, 25.0)), (3, 64, 72, (25.0,)), (1, 80, 88, (50.0,))])
 def test_denoise_bm3d_psnr_matches_oracle(oracle, C, H, W, sigmas):
     A = api()
