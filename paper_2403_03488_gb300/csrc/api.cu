@@ -185,12 +185,12 @@ dn_status run_bm3d(const float *noisy, float *out, int B, int C, int H, int W, c
         DN_TRY(match_any(x + off, (size_t)C * HW, nb, H, W, p->hard, tau1, p->precision, w.idx, w.n, w.mws, s));
         if (cudaMemsetAsync(w.acc, 0, kAccBytesPerPixel * Nb, s) != cudaSuccess) return DN_ECUDA;
         DN_TRY(filter_hard_fp32(x + off, w.idx, w.n, nb, C, H, W, sig, p->hard, w.acc, s));
-        DN_TRY(normalize(w.acc, w.basic + off, nb, C, H, W, s));
+        DN_TRY(normalize(w.acc, w.basic + off, nb, C, H, W, p->hard.beta, s));
         // pass 2: match on channel 0 of the basic estimate, Wiener filtering
         DN_TRY(match_any(w.basic + off, (size_t)C * HW, nb, H, W, p->wiener, tau2, p->precision, w.idx, w.n, w.mws, s));
         if (cudaMemsetAsync(w.acc, 0, kAccBytesPerPixel * Nb, s) != cudaSuccess) return DN_ECUDA;
         DN_TRY(filter_wiener_fp32(x + off, w.basic + off, w.idx, w.n, nb, C, H, W, sig, p->wiener, w.acc, s));
-        DN_TRY(normalize(w.acc, (C == 3 ? w.ycc : out) + off, nb, C, H, W, s));
+        DN_TRY(normalize(w.acc, (C == 3 ? w.ycc : out) + off, nb, C, H, W, p->wiener.beta, s));
     }
     if (C == 3) DN_TRY(colour(w.ycc, out, B, H, W, 1, s));
     (void)N;
@@ -471,7 +471,7 @@ static dn_status filter_entry(bool wiener, const float *img, const float *basic,
             DN_TRY(filter_wiener_fp32(img + off, basic + off, ib, nbp, nb, C, H, W, sigma_c + (size_t)b0 * C, *p, acc, s));
         else
             DN_TRY(filter_hard_fp32(img + off, ib, nbp, nb, C, H, W, sigma_c + (size_t)b0 * C, *p, acc, s));
-        DN_TRY(normalize(acc, out + off, nb, C, H, W, s));
+        DN_TRY(normalize(acc, out + off, nb, C, H, W, p->beta, s));
     }
     return DN_OK;
 }

@@ -12,11 +12,13 @@
 // Aggregation: every estimate pixel adds weight * kaiser(i) kaiser(j) * value to
 // num and weight * kaiser(i) kaiser(j) to den; the output is num / den.  The
 // sums are exact (64-bit fixed point, see to_fixed), so the result does not
-// depend on the order in which groups are aggregated.
+// depend on the order in which groups are aggregated; den is formed from the
+// per-position weight sums (see the aggregation section).
 //
-// Layout: a CTA owns a tile of reference positions and aggregates its groups
-// into a shared-memory window first (one global add per window pixel instead
-// of one per contribution).  A warp filters one group at a time (in the first
+// Layout: a CTA owns a tile of reference positions, reads its patches from an
+// image window staged in shared memory, and aggregates its groups into a
+// shared-memory num window first (one global add per window pixel instead of
+// one per contribution).  A warp filters one group at a time (in the first
 // pass, two groups of at most 16 patches at once): lane k owns patch k and
 // computes its 8x8 DCT in registers with an even/odd fast DCT; the group
 // passes through a per-warp transpose buffer (rows of 65 floats, conflict-free
@@ -45,8 +47,8 @@ struct FilterArgs {
     const float *basic;  // pass 2 only
     const int *idx;
     const int *n;
-    unsigned long long *num, *den;        // exact fixed-point accumulation planes, same layout as img
-    unsigned long long *num_hi, *den_hi;  // their high words (signed, units of 2^32)
+    unsigned long long *num, *wsum;        // fixed-point sums per pixel / per patch position, layout of img
+    unsigned long long *num_hi, *wsum_hi;  // their high words (signed, units of 2^32)
     int C, H, W, R, Rx, Ry, n2, step, hs;
     float lambda;
     float sig[kChunk * 3];
@@ -227,18 +229,22 @@ __device__ __forceinline__ int hard_columns(float *T, int n, int lane, float thr
 
 // ---- exact aggregation ---------------------------------------------------------
 
-// Every contribution becomes a signed fixed-point number with 36 fraction bits
-// (exact whenever the FP32 value is >= 2^-13 in magnitude) and is summed with
-// integer atomics, so num and den are bitwise reproducible whatever the order
-// of the groups.  Weights are used scaled by sigma^2 (1/N_har, 1/sum w^2, or
-// sigma^2 for an all-zero group), which leaves num/den unchanged.
+// num(x) = sum over (group g, patch q of g) of w_g kai(x - q) v_{g,q}(x - q) is
+// accumulated per pixel; den(x) = sum_q kai(x - q) W(q), W(q) = the sum of the
+// weights of the groups that hold patch q, is accumulated per patch position
+// (one addition per patch) and correlated with the Kaiser window when
+// normalising.  Both sums are fixed point with 36 fraction bits (exact whenever
+// the FP32 term is >= 2^-13 in magnitude) added with integer atomics, so they
+// are bitwise reproducible whatever the order of the groups.  Weights are used
+// scaled by sigma^2 (1/N_har, 1/sum w^2, or sigma^2 for an all-zero group),
+// which leaves num/den unchanged.
 //
-// A contribution c with |c| < 512 (all of them, in practice) is added to the
-// 64-bit main plane as round(c 2^36) < 2^45; any other c (a heavy weight or a
-// large value) is clamped to |c| <= 2^40 and split as c 2^36 = hi 2^32 + lo,
+// A term c with |c| < 512 (all of them, in practice) is added to the 64-bit
+// main plane as round(c 2^36) < 2^45; any other c (a heavy weight or a large
+// value) is clamped to |c| <= 2^40 and split as c 2^36 = hi 2^32 + lo,
 // 0 <= lo <= 2^32: lo goes to the main plane, hi to a high-word plane.  With at
-// most 2^14 contributions per pixel neither plane can overflow, and the value
-// is main + hi 2^32.
+// most 2^14 terms per sum neither plane can overflow, and the value is
+// main + hi 2^32.
 
 // round(c 2^36) (ties to even) for |c| < 512, on the FP32 and integer pipes:
 // t = c 2^13 is split into its nearest integer A (magic-number rounding, valid
@@ -275,11 +281,14 @@ __device__ __forceinline__ Fix to_fixed(float c)
     return f;
 }
 
-// Shared-memory aggregation window of one CTA: pixels [Y0, Y0+RH) x [X0, X0+RW)
-// of the current channel, num then den planes, row stride RS (RS = 8 mod 16
-// words, so that two rows of 8 consecutive 64-bit words fill all 32 banks).
+// Shared-memory state of one CTA for the current channel: the num window over
+// pixels [Y0, Y0+RH) x [X0, X0+RW) (row stride RS = 8 mod 16 words, so that two
+// rows of 8 consecutive 64-bit words fill all 32 banks) and the image windows
+// the patches are read from (row stride RW).
 struct Window {
-    unsigned long long *acc;  // [2][RH][RS] fixed point
+    unsigned long long *num;  // [RH][RS] fixed point
+    const float *img;         // [RH][RW]: the image to filter (noisy in pass 2)
+    const float *basic;       // [RH][RW]: pass 2 only
     int X0, Y0, RH, RW, RS;
 };
 
@@ -304,28 +313,41 @@ __device__ __forceinline__ int load_group(const FilterArgs &a, int b, int r, int
     return n;
 }
 
-// Coalesced gather of n patches into rows [s, s+n) of T (row s+k = patch k).
-__device__ __forceinline__ void gather_rows(float *T, const float *ch, int W, int s, int n, int lane, int py, int px)
+__device__ __forceinline__ bool in_window(const Window &win, int py, int px)
 {
-    for (int e = lane; e < n * 64; e += 32) {
-        const int k = s + (e >> 6), p = e & 63;
-        const int yk = __shfl_sync(0xffffffffu, py, k), xk = __shfl_sync(0xffffffffu, px, k);
-        T[k * kTS + p] = ch[(size_t)(yk + (p >> 3)) * W + xk + (p & 7)];
+    return py >= win.Y0 && py + 8 <= win.Y0 + win.RH && px >= win.X0 && px + 8 <= win.X0 + win.RW;
+}
+
+// Lane-per-row forward 2D DCT of the valid lanes' patches (row `lane` of T),
+// read from the shared image window, or from global memory when some patch
+// of the batch lies outside it (only possible for match lists not produced by
+// the matcher of this library).
+__device__ __forceinline__ void dct_rows(float *T, const Window &win, const float *wimg, const float *gimg, int W,
+                                         bool valid, int lane, int py, int px, const DctK &K)
+{
+    const bool all_in = __all_sync(0xffffffffu, !valid || in_window(win, py, px));
+    if (valid) {
+        const float *src = all_in ? wimg + (py - win.Y0) * win.RW + (px - win.X0) : gimg + (size_t)py * W + px;
+        const int stride = all_in ? win.RW : W;
+        float v[64];
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[r * 8 + j] = src[r * stride + j];
+        dct2d_rows_cols<0>(v, K);
+#pragma unroll
+        for (int p = 0; p < 64; ++p) T[lane * kTS + p] = v[p];
     }
 }
 
-// Lane-per-row 2D DCT (or its inverse) of row `lane` of T, in place.
-template <bool INVERSE>
-__device__ __forceinline__ void dct_own_row(float *T, bool valid, int lane, const DctK &K)
+// Lane-per-row inverse 2D DCT of row `lane` of T, in place.
+__device__ __forceinline__ void idct_rows(float *T, bool valid, int lane, const DctK &K)
 {
     if (valid) {
         float v[64];
 #pragma unroll
         for (int p = 0; p < 64; ++p) v[p] = T[lane * kTS + p];
-        if (INVERSE)
-            idct2d_cols_rows<0>(v, K);
-        else
-            dct2d_rows_cols<0>(v, K);
+        idct2d_cols_rows<0>(v, K);
 #pragma unroll
         for (int p = 0; p < 64; ++p) T[lane * kTS + p] = v[p];
     }
@@ -335,35 +357,38 @@ __device__ __forceinline__ void dct_own_row(float *T, bool valid, int lane, cons
 // the basic-estimate group (kept in registers), applied to the noisy group;
 // T is left holding the filtered spectra of the noisy patches.
 template <int N>
-__device__ __forceinline__ float wiener_group(const FilterArgs &a, float *T, size_t cbase, int lane, int py, int px,
-                                              float s2)
+__device__ __forceinline__ float wiener_group(const FilterArgs &a, const Window &win, float *T, size_t cbase,
+                                              int lane, int py, int px, float s2)
 {
-    gather_rows(T, a.basic + cbase, a.W, 0, N, lane, py, px);
-    __syncwarp();
-    dct_own_row<false>(T, lane < N, lane, a.k);
+    dct_rows(T, win, win.basic, a.basic + cbase, a.W, lane < N, lane, py, px, a.k);
     __syncwarp();
     float om0[N], om1[N];
     const float wsq = wiener_gains<N>(T, lane, s2, om0) + wiener_gains<N>(T, lane + 32, s2, om1);
     __syncwarp();
-    gather_rows(T, a.img + cbase, a.W, 0, N, lane, py, px);
-    __syncwarp();
-    dct_own_row<false>(T, lane < N, lane, a.k);
+    dct_rows(T, win, win.img, a.img + cbase, a.W, lane < N, lane, py, px, a.k);
     __syncwarp();
     wiener_apply<N>(T, lane, om0);
     wiener_apply<N>(T, lane + 32, om1);
     return wsq;
 }
 
-// Aggregation of the estimates in rows [s, s+n) of T (one group, weight w):
+// Aggregation of the estimates in rows [s, s+n) of T (one group, weight w).
+// The weight goes to the patch positions (lane k adds it for row k); for num
 // the warp walks the patches and its lanes cover the 64 pixels of each (lane
 // l: pixels l and l+32), so the window atomics of one instruction hit 4 rows
 // of 8 consecutive words (no bank conflict).
 __device__ __forceinline__ void aggregate(const FilterArgs &a, const Window &win, const float *T, size_t cbase, int s,
                                           int n, int lane, int py, int px, float w, const float (&ka)[2])
 {
-    const Fix d0 = to_fixed(w * ka[0]), d1 = to_fixed(w * ka[1]);
-    unsigned long long *wn = win.acc, *wd = win.acc + (size_t)win.RH * win.RS;
+    if (lane >= s && lane < s + n) {
+        const Fix fw = to_fixed(w);
+        const size_t q = cbase + (size_t)py * a.W + px;
+        atomicAdd(a.wsum + q, fw.lo);
+        if (fw.hi != 0) atomicAdd(a.wsum_hi + q, (unsigned long long)fw.hi);
+    }
+    const float wk0 = w * ka[0], wk1 = w * ka[1];
     const int i0 = lane >> 3, j = lane & 7;
+#pragma unroll 2
     for (int k = s; k < s + n; ++k) {
         const int yk = __shfl_sync(0xffffffffu, py, k), xk = __shfl_sync(0xffffffffu, px, k);
         const int ly0 = yk - win.Y0, lx0 = xk - win.X0;
@@ -371,19 +396,13 @@ __device__ __forceinline__ void aggregate(const FilterArgs &a, const Window &win
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int i = i0 + 4 * h;
-            const Fix fn = to_fixed(w * ka[h] * T[k * kTS + lane + 32 * h]);
-            const Fix &fd = h ? d1 : d0;
-            const size_t pix = cbase + (size_t)(yk + i) * a.W + xk + j;
-            if (fn.hi != 0) atomicAdd(a.num_hi + pix, (unsigned long long)fn.hi);
-            if (fd.hi != 0) atomicAdd(a.den_hi + pix, (unsigned long long)fd.hi);
+            const Fix fn = to_fixed((h ? wk1 : wk0) * T[k * kTS + lane + 32 * h]);
             if (inside) {
-                const int at = (ly0 + i) * win.RS + lx0 + j;
-                atomicAdd(wn + at, fn.lo);
-                atomicAdd(wd + at, fd.lo);
+                atomicAdd(win.num + (ly0 + i) * win.RS + lx0 + j, fn.lo);
             } else {
-                atomicAdd(a.num + pix, fn.lo);
-                atomicAdd(a.den + pix, fd.lo);
+                atomicAdd(a.num + cbase + (size_t)(yk + i) * a.W + xk + j, fn.lo);
             }
+            if (fn.hi != 0) atomicAdd(a.num_hi + cbase + (size_t)(yk + i) * a.W + xk + j, (unsigned long long)fn.hi);
         }
     }
 }
@@ -393,11 +412,8 @@ __device__ __forceinline__ void aggregate(const FilterArgs &a, const Window &win
 __device__ __forceinline__ void hard_batch(const FilterArgs &a, const Window &win, float *T, size_t cbase, float sig,
                                            int nA, int nB, int lane, int py, int px, const float (&ka)[2])
 {
-    gather_rows(T, a.img + cbase, a.W, 0, nA, lane, py, px);
-    if (nB) gather_rows(T, a.img + cbase, a.W, 16, nB, lane, py, px);
     const bool valid = lane < nA || (lane >= 16 && lane < 16 + nB);
-    __syncwarp();
-    dct_own_row<false>(T, valid, lane, a.k);
+    dct_rows(T, win, win.img, a.img + cbase, a.W, valid, lane, py, px, a.k);
     __syncwarp();
     const float thr = a.lambda * sig;
     const int nharA = __reduce_add_sync(0xffffffffu, hard_columns(T, nA, lane, thr));
@@ -406,7 +422,7 @@ __device__ __forceinline__ void hard_batch(const FilterArgs &a, const Window &wi
     const float wA = nharA > 0 ? 1.0f / (float)nharA : sig * sig;
     const float wB = nharB > 0 ? 1.0f / (float)nharB : sig * sig;
     __syncwarp();
-    dct_own_row<true>(T, valid, lane, a.k);
+    idct_rows(T, valid, lane, a.k);
     __syncwarp();
     aggregate(a, win, T, cbase, 0, nA, lane, py, px, wA, ka);
     if (nB) aggregate(a, win, T, cbase, 16, nB, lane, py, px, wB, ka);
@@ -420,40 +436,43 @@ __device__ __forceinline__ void wiener_one(const FilterArgs &a, const Window &wi
     const float s2 = sig * sig;
     float wsq;
     switch (n) {
-        case 1: wsq = wiener_group<1>(a, T, cbase, lane, py, px, s2); break;
-        case 2: wsq = wiener_group<2>(a, T, cbase, lane, py, px, s2); break;
-        case 4: wsq = wiener_group<4>(a, T, cbase, lane, py, px, s2); break;
-        case 8: wsq = wiener_group<8>(a, T, cbase, lane, py, px, s2); break;
-        case 16: wsq = wiener_group<16>(a, T, cbase, lane, py, px, s2); break;
-        default: wsq = wiener_group<32>(a, T, cbase, lane, py, px, s2); break;
+        case 1: wsq = wiener_group<1>(a, win, T, cbase, lane, py, px, s2); break;
+        case 2: wsq = wiener_group<2>(a, win, T, cbase, lane, py, px, s2); break;
+        case 4: wsq = wiener_group<4>(a, win, T, cbase, lane, py, px, s2); break;
+        case 8: wsq = wiener_group<8>(a, win, T, cbase, lane, py, px, s2); break;
+        case 16: wsq = wiener_group<16>(a, win, T, cbase, lane, py, px, s2); break;
+        default: wsq = wiener_group<32>(a, win, T, cbase, lane, py, px, s2); break;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) wsq += __shfl_xor_sync(0xffffffffu, wsq, o);
     const float w = wsq > 0.0f ? 1.0f / wsq : s2;  // 1/(sigma^2 sum w^2) or 1, times sigma^2
     __syncwarp();
-    dct_own_row<true>(T, lane < n, lane, a.k);
+    idct_rows(T, lane < n, lane, a.k);
     __syncwarp();
     aggregate(a, win, T, cbase, 0, n, lane, py, px, w, ka);
     __syncwarp();
 }
 
-// A CTA owns a TR x TR tile of reference positions; its warps filter the
-// tile's groups channel by channel and accumulate into the shared window
-// covering every patch those groups can hold (tile + search radius + patch),
-// then add the window once to the global fixed-point planes.  In the first
-// pass a warp takes the tile's references two at a time and filters both
-// groups together when each has at most 16 patches.
+// A CTA owns a TR x TR tile of reference positions; per channel it stages the
+// image window covering every patch its groups can hold (tile + search radius
+// + patch) in shared memory, its warps filter the tile's groups and add num
+// into a shared window, and the window is then added once to the global plane.
+// In the first pass a warp takes the tile's references two at a time and
+// filters both groups together when each has at most 16 patches.
 template <bool WIENER>
 __global__ void __launch_bounds__(WIENER ? 384 : 512) k_filter(FilterArgs a, int TR, int RH, int RW, int RS)
 {
     extern __shared__ __align__(16) unsigned char dsm_raw[];
     const int nw = blockDim.x >> 5;
     Window win;
-    win.acc = reinterpret_cast<unsigned long long *>(dsm_raw);
+    win.num = reinterpret_cast<unsigned long long *>(dsm_raw);
     win.RH = RH;
     win.RW = RW;
     win.RS = RS;
-    float *tbufs = reinterpret_cast<float *>(win.acc + (size_t)2 * RH * RS);  // [nw][32][65]
+    float *simg = reinterpret_cast<float *>(win.num + (size_t)RH * RS);  // [1 or 2][RH][RW]
+    float *tbufs = simg + (size_t)(WIENER ? 2 : 1) * RH * RW;            // [nw][32][65]
+    win.img = simg;
+    win.basic = WIENER ? simg + (size_t)RH * RW : nullptr;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int b = blockIdx.z;
     const int rx0 = blockIdx.x * TR, ry0 = blockIdx.y * TR;
@@ -467,13 +486,18 @@ __global__ void __launch_bounds__(WIENER ? 384 : 512) k_filter(FilterArgs a, int
     const int tw = min(TR, Rx - rx0), th = min(TR, Ry - ry0), cnt = tw * th;
     const size_t HW = (size_t)a.H * a.W;
     const int rh = min(RH, a.H - win.Y0), rw = min(RW, a.W - win.X0);
-    const int wtot = 2 * RH * RS;
     auto ref_of = [&](int q) { return (ry0 + q / tw) * Rx + rx0 + q % tw; };
 
     for (int c = 0; c < a.C; ++c) {
         const size_t cbase = ((size_t)b * a.C + c) * HW;
         const float sig = a.sig[b * 3 + c];
-        for (int i = threadIdx.x; i < wtot; i += blockDim.x) win.acc[i] = 0ull;
+        for (int i = threadIdx.x; i < RH * RS; i += blockDim.x) win.num[i] = 0ull;
+        for (int i = threadIdx.x; i < rh * rw; i += blockDim.x) {
+            const int ly = i / rw, lx = i - ly * rw;
+            const size_t g = cbase + (size_t)(win.Y0 + ly) * a.W + win.X0 + lx;
+            simg[ly * RW + lx] = a.img[g];
+            if (WIENER) simg[(size_t)RH * RW + ly * RW + lx] = a.basic[g];
+        }
         __syncthreads();
         if (WIENER) {
             for (int q = warp; q < cnt; q += nw) {
@@ -498,30 +522,66 @@ __global__ void __launch_bounds__(WIENER ? 384 : 512) k_filter(FilterArgs a, int
             }
         }
         __syncthreads();
-        const unsigned long long *wn = win.acc, *wd = win.acc + (size_t)RH * RS;
         for (int i = threadIdx.x; i < rh * rw; i += blockDim.x) {
             const int ly = i / rw, lx = i - ly * rw;
-            const unsigned long long d = wd[ly * RS + lx];
-            if (d != 0ull) {
-                const size_t pix = cbase + (size_t)(win.Y0 + ly) * a.W + win.X0 + lx;
-                atomicAdd(a.num + pix, wn[ly * RS + lx]);
-                atomicAdd(a.den + pix, d);
-            }
+            const unsigned long long v = win.num[ly * RS + lx];
+            if (v != 0ull) atomicAdd(a.num + cbase + (size_t)(win.Y0 + ly) * a.W + win.X0 + lx, v);
         }
-        __syncthreads();  // the window is zeroed again for the next channel
+        __syncthreads();  // the windows are refilled for the next channel
     }
 }
 
-__global__ void k_normalize(const long long *num, const long long *den, const long long *num_hi,
-                            const long long *den_hi, float *out, size_t count)
+// out = num / den, den(y, x) = sum_{i,j} k_i k_j W(y - i, x - j) over patch
+// positions, evaluated separably in FP32 (fixed order, so reproducible) from
+// the exact weight sums.  One CTA per 32 x 32 output tile of one plane.
+constexpr int kNT = 32;
+
+struct Kaiser1 {
+    float k[8];
+};
+
+__global__ void __launch_bounds__(256) k_normalize(const long long *num, const long long *wsum,
+                                                   const long long *num_hi, const long long *wsum_hi, float *out,
+                                                   int H, int W, Kaiser1 kw)
 {
-    // the 2^36 scale cancels in the ratio; the high words are almost always 0
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
-        double nu = (double)num[i], de = (double)den[i];
-        const long long nh = num_hi[i], dh = den_hi[i];
-        if (nh != 0) nu += (double)nh * 4294967296.0;
-        if (dh != 0) de += (double)dh * 4294967296.0;
-        out[i] = (float)(nu / de);
+    __shared__ float sw[kNT + 7][kNT + 8];  // W at positions (y0-7.., x0-7..)
+    __shared__ float sr[kNT + 7][kNT + 1];  // row pass
+    const size_t base = (size_t)blockIdx.z * H * W;
+    const int y0 = blockIdx.y * kNT, x0 = blockIdx.x * kNT;
+    for (int e = threadIdx.x; e < (kNT + 7) * (kNT + 7); e += blockDim.x) {
+        const int r = e / (kNT + 7), cc = e - r * (kNT + 7);
+        const int y = y0 - 7 + r, x = x0 - 7 + cc;
+        float v = 0.0f;
+        if (y >= 0 && y < H && x >= 0 && x < W) {
+            const size_t i = base + (size_t)y * W + x;
+            double d = (double)wsum[i];
+            const long long h = wsum_hi[i];
+            if (h != 0) d += (double)h * 4294967296.0;
+            v = (float)d;
+        }
+        sw[r][cc] = v;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < (kNT + 7) * kNT; e += blockDim.x) {
+        const int r = e / kNT, cc = e - r * kNT;
+        float acc = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc = fmaf(kw.k[j], sw[r][cc + 7 - j], acc);
+        sr[r][cc] = acc;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < kNT * kNT; e += blockDim.x) {
+        const int r = e / kNT, cc = e - r * kNT;
+        const int y = y0 + r, x = x0 + cc;
+        if (y >= H || x >= W) continue;
+        float den = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) den = fmaf(kw.k[i], sr[r + 7 - i][cc], den);
+        const size_t o = base + (size_t)y * W + x;
+        double nu = (double)num[o];
+        const long long h = num_hi[o];
+        if (h != 0) nu += (double)h * 4294967296.0;
+        out[o] = (float)(nu / (double)den);  // the 2^36 scale cancels
     }
 }
 
@@ -561,6 +621,7 @@ dn_status filter_common(bool wiener, const float *img, const float *basic, const
     const size_t HW = (size_t)H * W, N = (size_t)B * C * HW;
     // tile of references per CTA and its aggregation window
     const int nwarps = wiener ? 12 : 16;
+    const int nimg = wiener ? 2 : 1;
     const size_t per_warp = (size_t)32 * kTS * sizeof(float);
     int TR = 16;
     int RH = 0, RW = 0, RS = 0;
@@ -569,7 +630,8 @@ dn_status filter_common(bool wiener, const float *img, const float *basic, const
         RH = (TR - 1) * p.step + 2 * a.hs + 8;
         RW = RH;
         RS = RW + ((8 - RW % 16) + 16) % 16;  // row stride = 8 (mod 16) words
-        smem = (size_t)nwarps * per_warp + (size_t)2 * RH * RS * sizeof(unsigned long long);
+        smem = (size_t)nwarps * per_warp + (size_t)RH * RS * sizeof(unsigned long long) +
+               (size_t)nimg * RH * RW * sizeof(float);
         if (smem <= 225 * 1024) break;
     }
     if (TR < 1) return DN_EUNSUPPORTED;
@@ -585,9 +647,9 @@ dn_status filter_common(bool wiener, const float *img, const float *basic, const
         a.n = n + (size_t)b0 * a.R;
         unsigned long long *fx = reinterpret_cast<unsigned long long *>(acc);
         a.num = fx + off;
-        a.den = fx + N + off;
+        a.wsum = fx + N + off;
         a.num_hi = fx + 2 * N + off;
-        a.den_hi = fx + 3 * N + off;
+        a.wsum_hi = fx + 3 * N + off;
         for (int i = 0; i < nb; ++i)
             for (int c = 0; c < 3; ++c) a.sig[i * 3 + c] = c < C ? sig[(size_t)(b0 + i) * C + c] : 0.0f;
         dim3 grid((a.Rx + TR - 1) / TR, (a.Ry + TR - 1) / TR, nb);
@@ -614,14 +676,17 @@ dn_status filter_wiener_fp32(const float *noisy, const float *basic, const int *
     return filter_common(true, noisy, basic, idx, n, B, C, H, W, sig, p, acc, s);
 }
 
-dn_status normalize(const float *acc, float *out, int B, int C, int H, int W, cudaStream_t s)
+dn_status normalize(const float *acc, float *out, int B, int C, int H, int W, float beta, cudaStream_t s)
 {
     const size_t N = (size_t)B * C * H * W;
-    int blocks = (int)((N + 255) / 256);
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    Tables t;
+    make_tables(beta, &t);
+    Kaiser1 kw;
+    for (int i = 0; i < 8; ++i) kw.k[i] = t.kai1[i];
+    const dim3 grid((W + kNT - 1) / kNT, (H + kNT - 1) / kNT, B * C);
     return launch("bm3d_normalize", s, [&] {
         const long long *fx = reinterpret_cast<const long long *>(acc);
-        k_normalize<<<blocks, 256, 0, s>>>(fx, fx + N, fx + 2 * N, fx + 3 * N, out, N);
+        k_normalize<<<grid, 256, 0, s>>>(fx, fx + N, fx + 2 * N, fx + 3 * N, out, H, W, kw);
     });
 }
 

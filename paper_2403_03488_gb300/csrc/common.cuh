@@ -17,6 +17,7 @@ constexpr int kChunk = 64;
 struct Tables {
     float dct[64];   // orthonormal DCT-II, dct[u*8+m] = a_u cos(pi (2m+1) u / 16)
     float kai[64];   // Kaiser outer product, kai[i*8+j] = k[i] k[j]
+    float kai1[8];   // the 1D Kaiser window k
 };
 
 void make_tables(float beta, Tables *t);
@@ -71,8 +72,9 @@ inline int grid_count(int L, int patch, int step)
     return last / step + 1 + (last % step != 0 ? 1 : 0);
 }
 
-// Aggregation accumulators of the filtering passes: four 64-bit planes (num,
-// den, and their high words num_hi, den_hi) per image pixel.
+// Aggregation accumulators of the filtering passes: four 64-bit fixed-point
+// planes per image pixel: num (per pixel), wsum (group weights summed per patch
+// position), and their high words num_hi, wsum_hi.
 constexpr size_t kAccBytesPerPixel = 4 * sizeof(long long);
 
 // ---- launchers implemented in the .cu files -------------------------------
@@ -82,7 +84,8 @@ dn_status filter_hard_fp32(const float *img, const int *idx, const int *n, int B
                            const float *sig, const dn_bm3d_pass &p, float *acc, cudaStream_t s);
 dn_status filter_wiener_fp32(const float *noisy, const float *basic, const int *idx, const int *n, int B, int C,
                              int H, int W, const float *sig, const dn_bm3d_pass &p, float *acc, cudaStream_t s);
-dn_status normalize(const float *acc, float *out, int B, int C, int H, int W, cudaStream_t s);
+// out = num / den with den = the Kaiser window (parameter beta) correlated with wsum
+dn_status normalize(const float *acc, float *out, int B, int C, int H, int W, float beta, cudaStream_t s);
 dn_status colour(const float *in, float *out, int B, int H, int W, int inverse, cudaStream_t s);
 dn_status nlm_launch(const float *in, float *out, int B, int C, int H, int W, const float *sig_guide,
                      const dn_nlm_params &p, cudaStream_t s);

@@ -35,8 +35,10 @@ void make_tables(float beta, Tables *t)
         double r = 2.0 * m / 7.0 - 1.0;
         k[m] = bessel_i0_series(beta * std::sqrt(std::fmax(0.0, 1.0 - r * r))) / bessel_i0_series(beta);
     }
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < 8; ++i) {
+        t->kai1[i] = (float)k[i];
         for (int j = 0; j < 8; ++j) t->kai[i * 8 + j] = (float)(k[i] * k[j]);
+    }
 }
 
 // ---- colour ------------------------------------------------------------------
