@@ -3,28 +3,175 @@
 // For every reference patch P on the grid (0, step, ... plus L-8 on each axis)
 // and every candidate Q whose top-left corner lies in the search window
 // centred on P's corner (clipped to the image):
-//     d(P, Q) = ||P - Q||^2 / 64.
-// The reference is group member 0; the other candidates with d <= tau follow
-// in ascending (d, y*W + x) order; the group size is
-// n = min(n2, largest power of two <= #kept).
+//     d(P, Q) = ||P - Q||^2 / 64,
+// evaluated with the fixed association of match_exact.cuh.  The reference is
+// group member 0; the other candidates with d <= tau follow in ascending
+// (d, y*W + x) order; the group size is n = min(n2, largest power of two <=
+// #kept).
 //
-// Design: one CTA owns a 16 x 8 tile of reference positions and stages the
-// union of their search windows in shared memory (one coalesced load).  One
-// thread per reference keeps its patch in 64 registers and scans candidate
-// rows in chunks of 8 horizontally adjacent candidates: each of the 8 patch
-// rows loads 15 consecutive pixels once and feeds 8 accumulators, so shared
-// loads are 15 per 64 subtract-FMA pairs.  The per-candidate sum runs in the
-// same (row, column) order for every candidate, so equal pixel sets give
-// bit-equal distances and ties resolve by index exactly as in the definition.
-// The sorted top list lives in registers and is updated by a branch-free
-// insertion network (static register indices).  The smem row pitch is
-// 16 mod 32 floats: lanes hold references 3 pixels apart in two rows, which
-// then hit 32 distinct banks.
+// Step 3 (the default of both passes): k_match3.  A CTA owns 16 x 8 grid
+// references (those on the 3-aligned grid; the extra L-8 column and row go to
+// a warp-per-reference kernel) and stages the union of their windows in
+// shared memory.  For each candidate offset (oy, ox) the squared differences
+// D(y, x) = (I(y, x) - I(y + oy, x + ox))^2 are the same for every reference
+// whose patch covers (y, x), so the CTA forms the patch-row sums once:
+// threads own a 17-pixel segment of one tile row (4 reference columns 3
+// apart), split it into sums of 3 and 2 differences and combine them into the
+// 4 row sums (3 + 3 + 2 pixels), for 8 horizontally adjacent offsets at a time
+// (24 candidate pixels loaded per 8 offsets).  The row sums go through a
+// double-buffered shared array; then each thread, owning one reference,
+// combines its 8 row sums (3 + 3 + 2 rows) and updates its sorted list in
+// registers.  About 60 % fewer operations than one subtract and one FMA per
+// pixel and candidate.
+//
+// Other steps: k_match_fp32, one thread per reference over a 16 x 8 tile,
+// register-blocked over 8 horizontally adjacent candidates (15 shared loads
+// per patch row feed 8 candidates), same association.
 #include "common.cuh"
+#include "match_exact.cuh"
 
 namespace dn {
 
 namespace {
+
+// ---- step-3 tiled kernel --------------------------------------------------------
+
+constexpr int kSX = 16;                      // references per CTA along x
+constexpr int kSY = 8;                       // references per CTA along y
+constexpr int kS3T = kSX * kSY;              // threads (one reference each)
+constexpr int kSRows = 3 * (kSY - 1) + 8;    // pixel rows of the tile
+constexpr int kSG = kSX / 4;                 // column groups of 4 references
+constexpr int kSTasks = kSG * kSRows;        // row-sum tasks (row, group)
+constexpr int kSGS = 136;                    // floats per (offset, group) slab: 29 rows x 4, = 8 (mod 32)
+constexpr int kSK = 8;                       // offsets per chunk
+constexpr int kSBuf = kSK * kSG * kSGS;      // floats per row-sum buffer
+
+struct Match3Args {
+    const float *g;
+    size_t plane;
+    int H, W, Rxa, Rya, hs, pitch, rows, img_floats;
+    float tau[kChunk];
+    int *idx;
+    int *n;
+    int n2, Rx, Ry;
+};
+
+template <int L>
+__global__ void __launch_bounds__(kS3T, 3) k_match3(Match3Args a)
+{
+    extern __shared__ float4 sm_raw[];
+    float *img = reinterpret_cast<float *>(sm_raw);  // [rows][pitch], origin (3 r0 - hs, 3 c0 - hs)
+    float *hb = img + a.img_floats;                  // [2][kSK][kSG][kSGS]
+    const int b = blockIdx.z;
+    const float *g = a.g + (size_t)b * a.plane;
+    const int H = a.H, W = a.W, hs = a.hs, P = a.pitch;
+    const int c0 = blockIdx.x * kSX, r0 = blockIdx.y * kSY;
+    const int RX0 = 3 * c0 - hs, RY0 = 3 * r0 - hs;
+    for (int i = threadIdx.x; i < a.rows * P; i += kS3T) {
+        const int yy = i / P, xx = i - yy * P;
+        const int gy = RY0 + yy, gx = RX0 + xx;
+        img[i] = (gy >= 0 && gy < H && gx >= 0 && gx < W) ? g[(size_t)gy * W + gx] : 0.0f;
+    }
+    __syncthreads();
+
+    const int t = threadIdx.x;
+    // row-sum role: tile row ay, reference columns 4 ag .. 4 ag + 3 (pixels 12 ag .. 12 ag + 16)
+    const bool task = t < kSTasks;
+    const int ag = t / kSRows, ay = t - (t / kSRows) * kSRows;
+    float R[17];
+#pragma unroll
+    for (int x = 0; x < 17; ++x) R[x] = task ? img[(ay + hs) * P + 12 * ag + hs + x] : 0.0f;
+    // reference role
+    const int bc = t % kSX, br = t / kSX;
+    const int rx = c0 + bc, ry = r0 + br;
+    const bool own = rx < a.Rxa && ry < a.Rya;
+    const int xr = 3 * rx, yr = 3 * ry;
+    float bd[L];
+    int bi[L];
+#pragma unroll
+    for (int j = 0; j < L; ++j) {
+        bd[j] = __int_as_float(0x7f800000);  // +inf
+        bi[j] = -1;
+    }
+    const float tau = a.tau[b];
+    int kept = 0;
+    int it = 0;
+    for (int oy = -hs; oy <= hs; ++oy) {
+        const bool yok = own && (unsigned)(yr + oy) <= (unsigned)(H - 8);
+        for (int ox0 = -hs; ox0 <= hs; ox0 += kSK, ++it) {
+            float *hbuf = hb + (it & 1) * kSBuf;
+            if (task) {
+                const float *crow = img + (ay + hs + oy) * P + 12 * ag + hs + ox0;
+                float C[24];
+#pragma unroll
+                for (int q = 0; q < 24; ++q) C[q] = crow[q];
+#pragma unroll
+                for (int k = 0; k < kSK; ++k) {
+                    float pr[6], tr[5];
+#pragma unroll
+                    for (int u = 0; u < 5; ++u) {
+                        pr[u] = __fadd_rn(sqd(R[3 * u], C[3 * u + k]), sqd(R[3 * u + 1], C[3 * u + 1 + k]));
+                        tr[u] = __fadd_rn(pr[u], sqd(R[3 * u + 2], C[3 * u + 2 + k]));
+                    }
+                    pr[5] = __fadd_rn(sqd(R[15], C[15 + k]), sqd(R[16], C[16 + k]));
+                    float4 h;
+                    h.x = __fadd_rn(__fadd_rn(tr[0], tr[1]), pr[2]);
+                    h.y = __fadd_rn(__fadd_rn(tr[1], tr[2]), pr[3]);
+                    h.z = __fadd_rn(__fadd_rn(tr[2], tr[3]), pr[4]);
+                    h.w = __fadd_rn(__fadd_rn(tr[3], tr[4]), pr[5]);
+                    *reinterpret_cast<float4 *>(hbuf + (k * kSG + ag) * kSGS + 4 * ay) = h;
+                }
+            }
+            __syncthreads();  // one barrier per chunk: the buffers alternate
+            if (yok) {
+                const float *hc = hbuf + (bc >> 2) * kSGS + 12 * br + (bc & 3);
+#pragma unroll
+                for (int k = 0; k < kSK; ++k) {
+                    const float *hk = hc + k * kSG * kSGS;
+                    const float d = tree8(hk[0], hk[4], hk[8], hk[12], hk[16], hk[20], hk[24], hk[28]) * 0.015625f;
+                    const int ox = ox0 + k, cx = xr + ox;
+                    const bool ok = ox <= hs && (unsigned)cx <= (unsigned)(W - 8) && (ox | oy) != 0 && d <= tau;
+                    if (ok) {
+                        ++kept;
+                        if (d < bd[L - 1]) insert_sorted<L>(bd, bi, d, (yr + oy) * W + cx);
+                    }
+                }
+            }
+        }
+    }
+    if (!own) return;
+    const size_t r = ((size_t)b * a.Ry + ry) * a.Rx + rx;
+    int *out = a.idx + r * a.n2;
+    out[0] = yr * W + xr;
+#pragma unroll
+    for (int j = 0; j < L; ++j)
+        if (1 + j < a.n2) out[1 + j] = bi[j];
+    a.n[r] = group_size(kept, a.n2);
+}
+
+// The references off the 3-aligned grid (column Rx - 1 when Rxa < Rx, row
+// Ry - 1 when Rya < Ry): one warp each.
+template <int L>
+__global__ void __launch_bounds__(256) k_match_edges(Match3Args a, int count)
+{
+    const int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int b = blockIdx.y;
+    if (wg >= count) return;
+    const int ncol = a.Rx > a.Rxa ? a.Ry : 0;
+    int rx, ry;
+    if (wg < ncol) {
+        rx = a.Rx - 1;
+        ry = wg;
+    } else {
+        rx = wg - ncol;
+        ry = a.Ry - 1;
+    }
+    const size_t r = ((size_t)b * a.Ry + ry) * a.Rx + rx;
+    match_ref_warp<L>(a.g + (size_t)b * a.plane, a.H, a.W, 3, a.hs, a.tau[b], a.n2, rx, ry, a.idx + r * a.n2,
+                      a.n + r);
+}
+
+// ---- any step ------------------------------------------------------------------
 
 constexpr int kTX = 16;     // references per CTA along x
 constexpr int kTY = 8;      // references per CTA along y
@@ -39,25 +186,6 @@ struct MatchArgs {
     int *n;
     int n2;
 };
-
-template <int L>
-__device__ __forceinline__ void insert_sorted(float (&bd)[L], int (&bi)[L], float d, int id)
-{
-    // Keep bd ascending; equal distances keep scan (= index) order.
-#pragma unroll
-    for (int j = L - 1; j > 0; --j) {
-        bool before_prev = d < bd[j - 1];
-        bool before_this = d < bd[j];
-        float nd = before_prev ? bd[j - 1] : (before_this ? d : bd[j]);
-        int ni = before_prev ? bi[j - 1] : (before_this ? id : bi[j]);
-        bd[j] = nd;
-        bi[j] = ni;
-    }
-    if (d < bd[0]) {
-        bd[0] = d;
-        bi[0] = id;
-    }
-}
 
 // L = n2 - 1 list slots after the reference.
 template <int L>
@@ -109,9 +237,8 @@ __global__ void __launch_bounds__(kThreads) k_match_fp32(MatchArgs a)
     for (int y = ys; y <= ye; ++y) {
         const float *rowbase = sm + (y - Y0) * a.pitch - X0;
         for (int xc = xs; xc <= xe; xc += 8) {
-            float acc[8];
-#pragma unroll
-            for (int c = 0; c < 8; ++c) acc[c] = 0.0f;
+            // row sums h_i of the 8 candidates, combined as ((h0+h1)+h2) + ((h3+h4)+h5) + (h6+h7)
+            float part[8], t0[8], t1[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
                 const float *row = rowbase + i * a.pitch + xc;
@@ -119,17 +246,22 @@ __global__ void __launch_bounds__(kThreads) k_match_fp32(MatchArgs a)
 #pragma unroll
                 for (int k = 0; k < 15; ++k) s[k] = row[k];
 #pragma unroll
-                for (int c = 0; c < 8; ++c)
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        float e = ref[i * 8 + j] - s[c + j];
-                        acc[c] = fmaf(e, e, acc[c]);
-                    }
+                for (int c = 0; c < 8; ++c) {
+                    const float h = tree8(sqd(ref[i * 8], s[c]), sqd(ref[i * 8 + 1], s[c + 1]),
+                                          sqd(ref[i * 8 + 2], s[c + 2]), sqd(ref[i * 8 + 3], s[c + 3]),
+                                          sqd(ref[i * 8 + 4], s[c + 4]), sqd(ref[i * 8 + 5], s[c + 5]),
+                                          sqd(ref[i * 8 + 6], s[c + 6]), sqd(ref[i * 8 + 7], s[c + 7]));
+                    if (i == 0 || i == 3 || i == 6) part[c] = h;
+                    else if (i == 1 || i == 4) part[c] = __fadd_rn(part[c], h);
+                    else if (i == 2) t0[c] = __fadd_rn(part[c], h);
+                    else if (i == 5) t1[c] = __fadd_rn(part[c], h);
+                    else part[c] = __fadd_rn(part[c], h);
+                }
             }
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
                 const int x = xc + c;
-                const float d = acc[c] * 0.015625f;  // / 64, exact
+                const float d = __fadd_rn(__fadd_rn(t0[c], t1[c]), part[c]) * 0.015625f;  // / 64, exact
                 const bool valid = (x <= xe) && !(x == x0 && y == y0) && (d <= tau);
                 if (valid) {
                     ++kept;
@@ -145,10 +277,7 @@ __global__ void __launch_bounds__(kThreads) k_match_fp32(MatchArgs a)
 #pragma unroll
     for (int j = 0; j < L; ++j)
         if (1 + j < a.n2) out[1 + j] = bi[j];
-    int total = min(kept + 1, a.n2);
-    int n = 1;
-    while (n * 2 <= total) n *= 2;
-    a.n[r] = n;
+    a.n[r] = group_size(kept, a.n2);
 }
 
 template <int L>
@@ -161,11 +290,69 @@ dn_status launch_match(MatchArgs &a, int B, cudaStream_t s, size_t smem)
     return launch("bm3d_match_fp32", s, [&] { k_match_fp32<L><<<grid, kThreads, smem, s>>>(a); });
 }
 
+template <int L>
+dn_status launch_match3(Match3Args &a, int B, cudaStream_t s, size_t smem)
+{
+    if (cudaFuncSetAttribute(k_match3<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return DN_ECUDA;
+    if (a.Rxa > 0 && a.Rya > 0) {
+        dim3 grid((a.Rxa + kSX - 1) / kSX, (a.Rya + kSY - 1) / kSY, B);
+        DN_TRY(launch("bm3d_match_fp32", s, [&] { k_match3<L><<<grid, kS3T, smem, s>>>(a); }));
+    }
+    const int count = (a.Rx > a.Rxa ? a.Ry : 0) + (a.Ry > a.Rya ? a.Rxa : 0);
+    if (count > 0) {
+        dim3 grid((count + 7) / 8, B);
+        DN_TRY(launch("bm3d_match_edges", s, [&] { k_match_edges<L><<<grid, 256, 0, s>>>(a, count); }));
+    }
+    return DN_OK;
+}
+
+dn_status match_step3(const float *guide, size_t plane, int B, int H, int W, const dn_bm3d_pass &p,
+                      const float *tau, int *idx, int *n, cudaStream_t s)
+{
+    Match3Args a;
+    a.H = H;
+    a.W = W;
+    a.hs = p.search / 2;
+    a.Rx = grid_count(W, 8, 3);
+    a.Ry = grid_count(H, 8, 3);
+    a.Rxa = (W - 8) / 3 + 1;
+    a.Rya = (H - 8) / 3 + 1;
+    a.n2 = p.n2;
+    a.plane = plane;
+    a.rows = kSRows + 2 * a.hs;
+    a.pitch = (2 * a.hs + 60) | 1;  // odd: the row-sum tasks' loads hit at most 2 lanes per bank
+    a.img_floats = (a.rows * a.pitch + 3) & ~3;
+    const size_t smem = (size_t)(a.img_floats + 2 * kSBuf) * sizeof(float);
+    if (smem > 200 * 1024) return DN_EUNSUPPORTED;
+    for (int b0 = 0; b0 < B; b0 += kChunk) {
+        const int nb = B - b0 < kChunk ? B - b0 : kChunk;
+        a.g = guide + (size_t)b0 * plane;
+        for (int i = 0; i < nb; ++i) a.tau[i] = tau[b0 + i];
+        const size_t R = (size_t)a.Ry * a.Rx;
+        a.idx = idx + (size_t)b0 * R * p.n2;
+        a.n = n + (size_t)b0 * R;
+        dn_status st;
+        switch (p.n2) {
+            case 1: st = launch_match3<1>(a, nb, s, smem); break;  // slot unused (n2 = 1)
+            case 2: st = launch_match3<1>(a, nb, s, smem); break;
+            case 4: st = launch_match3<3>(a, nb, s, smem); break;
+            case 8: st = launch_match3<7>(a, nb, s, smem); break;
+            case 16: st = launch_match3<15>(a, nb, s, smem); break;
+            case 32: st = launch_match3<31>(a, nb, s, smem); break;
+            default: return DN_EINVAL;
+        }
+        if (st != DN_OK) return st;
+    }
+    return DN_OK;
+}
+
 }  // namespace
 
 dn_status match_fp32(const float *guide, size_t plane, int B, int H, int W, const dn_bm3d_pass &p,
                      const float *tau, int *idx, int *n, cudaStream_t s)
 {
+    if (p.step == 3) return match_step3(guide, plane, B, H, W, p, tau, idx, n, s);
     MatchArgs a;
     a.H = H;
     a.W = W;

@@ -2,7 +2,7 @@
 //
 // Result: the same match lists as the exhaustive FP32 kernel (bm3d_match.cu):
 // reference first, then the candidates with d <= tau in ascending (d, index)
-// order, d = ||P - Q||^2 / 64 evaluated in FP32 in the same operation order.
+// order, d = ||P - Q||^2 / 64 evaluated in FP32 with the same association.
 //
 // Prefilter.  With patch means mu and centred patches P_c = P - mu_P,
 //   d = (||P_c||^2 + ||Q_c||^2 - 2 P_c . Q_c) / 64 + (mu_P - mu_Q)^2
@@ -35,6 +35,7 @@
 #include <cmath>
 
 #include "common.cuh"
+#include "match_exact.cuh"
 #include "tc.cuh"
 
 namespace dn {
@@ -78,93 +79,21 @@ struct FallbackArgs {
 };
 
 // Exhaustive exact matching of the deferred references, one warp per
-// reference: lanes take every 32nd candidate of the window in row-major
-// order, keep their own sorted top list, and the warp merges the 32 lists by
-// repeated (d, index) minimum.  Same distance arithmetic as the FP32 kernel.
+// reference (match_ref_warp: same distance arithmetic as the FP32 kernels).
 template <int L>
 __global__ void __launch_bounds__(256) k_match_fallback(FallbackArgs a)
 {
-    const int lane = threadIdx.x & 31;
     const int wglobal = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     const int total = *a.fb_count;
-    const int W = a.W, H = a.H, hs = a.hs;
     const size_t R = (size_t)a.Ry * a.Rx;
     for (int f = wglobal; f < total; f += nwarps) {
         const int r = a.fb_list[f];
         const int b = (int)(r / R);
         const int rr = (int)(r - (size_t)b * R);
         const int ry = rr / a.Rx, rx = rr - ry * a.Rx;
-        const float *g = a.g + (size_t)b * a.plane;
-        const int x0 = min(rx * a.step, W - 8), y0 = min(ry * a.step, H - 8);
-        float ref[64];
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-#pragma unroll
-            for (int j = 0; j < 8; ++j) ref[i * 8 + j] = g[(size_t)(y0 + i) * W + x0 + j];
-        const float tau = a.tau[b];
-        const int xs = max(0, x0 - hs), xe = min(W - 8, x0 + hs);
-        const int ys = max(0, y0 - hs), ye = min(H - 8, y0 + hs);
-        const int ww = xe - xs + 1, cnt = (ye - ys + 1) * ww;
-        float bd[L];
-        int bi[L];
-#pragma unroll
-        for (int j = 0; j < L; ++j) {
-            bd[j] = __int_as_float(0x7f800000);
-            bi[j] = 0x7fffffff;
-        }
-        int kept = 0;
-        for (int e = lane; e < cnt; e += 32) {
-            const int y = ys + e / ww, x = xs + e % ww;
-            if (y == y0 && x == x0) continue;
-            float acc = 0.0f;
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const float d = ref[i * 8 + j] - g[(size_t)(y + i) * W + x + j];
-                    acc = fmaf(d, d, acc);
-                }
-            const float d = acc * 0.015625f;
-            if (d <= tau) {
-                ++kept;
-                if (d < bd[L - 1]) insert_lex<L>(bd, bi, d, y * W + x);
-            }
-        }
-        kept = __reduce_add_sync(0xffffffffu, kept);
-        int *out = a.idx + (size_t)r * a.n2;
-        if (lane == 0) out[0] = y0 * W + x0;
-        int head = 0;
-        for (int k = 0; k < L; ++k) {
-            // lane's current head (lists are sorted; exhausted lists give +inf)
-            float hd = __int_as_float(0x7f800000);
-            int hi = 0x7fffffff;
-#pragma unroll
-            for (int j = 0; j < L; ++j)
-                if (j == head) {
-                    hd = bd[j];
-                    hi = bi[j];
-                }
-            float md = hd;
-            int mi = hi;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const float od = __shfl_xor_sync(0xffffffffu, md, o);
-                const int oi = __shfl_xor_sync(0xffffffffu, mi, o);
-                if (od < md || (od == md && oi < mi)) {
-                    md = od;
-                    mi = oi;
-                }
-            }
-            if (hd == md && hi == mi && head < L) ++head;  // the winning lane pops its head
-            if (lane == 0 && 1 + k < a.n2) out[1 + k] = (mi == 0x7fffffff) ? -1 : mi;
-        }
-        if (lane == 0) {
-            const int tot = min(kept + 1, a.n2);
-            int n = 1;
-            while (n * 2 <= tot) n *= 2;
-            a.n[r] = n;
-        }
+        match_ref_warp<L>(a.g + (size_t)b * a.plane, a.H, a.W, a.step, a.hs, a.tau[b], a.n2, rx, ry,
+                          a.idx + (size_t)r * a.n2, a.n + r);
     }
 }
 
@@ -220,20 +149,11 @@ __device__ __forceinline__ void insert_lex(float (&bd)[L], int (&bi)[L], float d
     }
 }
 
-// Exact FP32 distance, same operation order as the exhaustive kernel.
+// Exact FP32 distance, same association as the exhaustive kernels.
 __device__ __forceinline__ float exact_d(const float (&ref)[64], const float *img, int RP, int ly, int lx)
 {
-    float acc = 0.0f;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const float *row = img + (ly + i) * RP + lx;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const float e = ref[i * 8 + j] - row[j];
-            acc = fmaf(e, e, acc);
-        }
-    }
-    return acc * 0.015625f;
+    const float *q = img + ly * RP + lx;
+    return canon_d64(ref, [&](int i, int j) { return q[i * RP + j]; }) * 0.015625f;
 }
 
 template <int L>

@@ -1,0 +1,144 @@
+// Exact FP32 block-matching distance and the warp-per-reference exhaustive
+// matcher shared by the matching kernels (internal header).
+//
+// Every path that ranks candidates with an FP32 distance evaluates
+// d = ||P - Q||^2 / 64 with one fixed association, so equal pixel sets give
+// bit-equal distances and the paths agree bit for bit: squared differences
+// are rounded individually, each patch row is summed as
+//     (((s0 + s1) + s2) + ((s3 + s4) + s5)) + (s6 + s7)
+// and the 8 row sums are combined in the same pattern.  The 3 + 3 + 2 split
+// matches the reference grid step of 3, which lets the tiled kernel share
+// partial sums between neighbouring references.  All products and sums use
+// the _rn intrinsics, so no compiler contraction changes the rounding.
+#pragma once
+
+#include "common.cuh"
+
+namespace dn {
+namespace {
+
+__device__ __forceinline__ float tree8(float a0, float a1, float a2, float a3, float a4, float a5, float a6, float a7)
+{
+    const float t0 = __fadd_rn(__fadd_rn(a0, a1), a2);
+    const float t1 = __fadd_rn(__fadd_rn(a3, a4), a5);
+    return __fadd_rn(__fadd_rn(t0, t1), __fadd_rn(a6, a7));
+}
+
+__device__ __forceinline__ float sqd(float a, float b)
+{
+    const float e = __fsub_rn(a, b);
+    return __fmul_rn(e, e);
+}
+
+// ||P - Q||^2 for P = ref (row-major registers), Q read through q(i, j).
+template <typename Q>
+__device__ __forceinline__ float canon_d64(const float (&ref)[64], Q q)
+{
+    float h[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        float s[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) s[j] = sqd(ref[i * 8 + j], q(i, j));
+        h[i] = tree8(s[0], s[1], s[2], s[3], s[4], s[5], s[6], s[7]);
+    }
+    return tree8(h[0], h[1], h[2], h[3], h[4], h[5], h[6], h[7]);
+}
+
+// Sorted insertion; candidates arrive in increasing index order, so a strict
+// comparison keeps equal distances in index order.
+template <int L>
+__device__ __forceinline__ void insert_sorted(float (&bd)[L], int (&bi)[L], float d, int id)
+{
+#pragma unroll
+    for (int j = L - 1; j > 0; --j) {
+        const bool before_prev = d < bd[j - 1];
+        const bool before_this = d < bd[j];
+        const float nd = before_prev ? bd[j - 1] : (before_this ? d : bd[j]);
+        const int ni = before_prev ? bi[j - 1] : (before_this ? id : bi[j]);
+        bd[j] = nd;
+        bi[j] = ni;
+    }
+    if (d < bd[0]) {
+        bd[0] = d;
+        bi[0] = id;
+    }
+}
+
+// Group size from the number of kept candidates (reference excluded).
+__device__ __forceinline__ int group_size(int kept, int n2)
+{
+    const int tot = min(kept + 1, n2);
+    int n = 1;
+    while (n * 2 <= tot) n *= 2;
+    return n;
+}
+
+// Exhaustive exact matching of reference (rx, ry) of image g by one warp:
+// lanes take every 32nd candidate of the window in row-major order, keep
+// their own sorted top list, and the warp merges the 32 lists by repeated
+// (d, index) minimum.  Writes out[0..n2) and *nout.  L = n2 - 1 (>= 1).
+template <int L>
+__device__ void match_ref_warp(const float *g, int H, int W, int step, int hs, float tau, int n2, int rx, int ry,
+                               int *out, int *nout)
+{
+    const int lane = threadIdx.x & 31;
+    const int x0 = min(rx * step, W - 8), y0 = min(ry * step, H - 8);
+    float ref[64];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) ref[i * 8 + j] = g[(size_t)(y0 + i) * W + x0 + j];
+    const int xs = max(0, x0 - hs), xe = min(W - 8, x0 + hs);
+    const int ys = max(0, y0 - hs), ye = min(H - 8, y0 + hs);
+    const int ww = xe - xs + 1, cnt = (ye - ys + 1) * ww;
+    float bd[L];
+    int bi[L];
+#pragma unroll
+    for (int j = 0; j < L; ++j) {
+        bd[j] = __int_as_float(0x7f800000);
+        bi[j] = 0x7fffffff;
+    }
+    int kept = 0;
+    for (int e = lane; e < cnt; e += 32) {
+        const int y = ys + e / ww, x = xs + e % ww;
+        if (y == y0 && x == x0) continue;
+        const float *q = g + (size_t)y * W + x;
+        const float d = canon_d64(ref, [&](int i, int j) { return q[(size_t)i * W + j]; }) * 0.015625f;
+        if (d <= tau) {
+            ++kept;
+            if (d < bd[L - 1]) insert_sorted<L>(bd, bi, d, y * W + x);
+        }
+    }
+    kept = __reduce_add_sync(0xffffffffu, kept);
+    if (lane == 0) out[0] = y0 * W + x0;
+    int head = 0;
+    for (int k = 0; k < L; ++k) {
+        // lane's current head (lists are sorted; exhausted lists give +inf)
+        float hd = __int_as_float(0x7f800000);
+        int hi = 0x7fffffff;
+#pragma unroll
+        for (int j = 0; j < L; ++j)
+            if (j == head) {
+                hd = bd[j];
+                hi = bi[j];
+            }
+        float md = hd;
+        int mi = hi;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float od = __shfl_xor_sync(0xffffffffu, md, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, mi, o);
+            if (od < md || (od == md && oi < mi)) {
+                md = od;
+                mi = oi;
+            }
+        }
+        if (hd == md && hi == mi && head < L) ++head;  // the winning lane pops its head
+        if (lane == 0 && 1 + k < n2) out[1 + k] = (mi == 0x7fffffff) ? -1 : mi;
+    }
+    if (lane == 0) *nout = group_size(kept, n2);
+}
+
+}  // namespace
+}  // namespace dn
