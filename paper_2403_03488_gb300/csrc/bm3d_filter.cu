@@ -37,9 +37,10 @@ namespace {
 constexpr int kTS = 65;    // transpose buffer row stride (floats)
 constexpr int kNMax = 32;
 
-// cos(k pi / 16) for k = 1..7 and 1/sqrt(8): the constants of the 8-point DCT.
+// h_k = cos(k pi / 16) / 2 for k = 1..7 (h_4 = 1/sqrt(8)) and r8 = 1/sqrt(8):
+// the constants of the orthonormal 8-point DCT with the 1/2 scale folded in.
 struct DctK {
-    float c1, c2, c3, c4, c5, c6, c7, r8;
+    float h1, h2, h3, h5, h6, h7, r8;
 };
 
 struct FilterArgs {
@@ -68,29 +69,28 @@ __device__ __forceinline__ void dct8(float (&v)[64], const DctK &K)
     const float s3 = v[O + 3 * S] + v[O + 4 * S], d3 = v[O + 3 * S] - v[O + 4 * S];
     const float e0 = s0 + s3, e1 = s1 + s2, f0 = s0 - s3, f1 = s1 - s2;
     v[O] = K.r8 * (e0 + e1);
-    v[O + 4 * S] = 0.5f * K.c4 * (e0 - e1);
-    v[O + 2 * S] = 0.5f * (K.c2 * f0 + K.c6 * f1);
-    v[O + 6 * S] = 0.5f * (K.c6 * f0 - K.c2 * f1);
-    v[O + 1 * S] = 0.5f * (K.c1 * d0 + K.c3 * d1 + K.c5 * d2 + K.c7 * d3);
-    v[O + 3 * S] = 0.5f * (K.c3 * d0 - K.c7 * d1 - K.c1 * d2 - K.c5 * d3);
-    v[O + 5 * S] = 0.5f * (K.c5 * d0 - K.c1 * d1 + K.c7 * d2 + K.c3 * d3);
-    v[O + 7 * S] = 0.5f * (K.c7 * d0 - K.c5 * d1 + K.c3 * d2 - K.c1 * d3);
+    v[O + 4 * S] = K.r8 * (e0 - e1);
+    v[O + 2 * S] = fmaf(K.h2, f0, K.h6 * f1);
+    v[O + 6 * S] = fmaf(K.h6, f0, -(K.h2 * f1));
+    v[O + 1 * S] = fmaf(K.h1, d0, fmaf(K.h3, d1, fmaf(K.h5, d2, K.h7 * d3)));
+    v[O + 3 * S] = fmaf(K.h3, d0, fmaf(-K.h7, d1, fmaf(-K.h1, d2, -(K.h5 * d3))));
+    v[O + 5 * S] = fmaf(K.h5, d0, fmaf(-K.h1, d1, fmaf(K.h7, d2, K.h3 * d3)));
+    v[O + 7 * S] = fmaf(K.h7, d0, fmaf(-K.h5, d1, fmaf(K.h3, d2, -(K.h1 * d3))));
 }
 
 // inverse: x[m] = sum_u a_u X[u] cos(pi (2m+1) u / 16)
 template <int O, int S>
 __device__ __forceinline__ void idct8(float (&v)[64], const DctK &K)
 {
-    const float X0 = v[O] * K.r8, X4 = 0.5f * K.c4 * v[O + 4 * S];
-    const float X2 = 0.5f * v[O + 2 * S], X6 = 0.5f * v[O + 6 * S];
-    const float X1 = 0.5f * v[O + S], X3 = 0.5f * v[O + 3 * S], X5 = 0.5f * v[O + 5 * S], X7 = 0.5f * v[O + 7 * S];
-    const float a = X0 + X4, b = X0 - X4;
-    const float p = K.c2 * X2 + K.c6 * X6, q = K.c6 * X2 - K.c2 * X6;
+    const float X0 = v[O], X1 = v[O + S], X2 = v[O + 2 * S], X3 = v[O + 3 * S];
+    const float X4 = v[O + 4 * S], X5 = v[O + 5 * S], X6 = v[O + 6 * S], X7 = v[O + 7 * S];
+    const float a = K.r8 * (X0 + X4), b = K.r8 * (X0 - X4);
+    const float p = fmaf(K.h2, X2, K.h6 * X6), q = fmaf(K.h6, X2, -(K.h2 * X6));
     const float e0 = a + p, e3 = a - p, e1 = b + q, e2 = b - q;
-    const float o0 = K.c1 * X1 + K.c3 * X3 + K.c5 * X5 + K.c7 * X7;
-    const float o1 = K.c3 * X1 - K.c7 * X3 - K.c1 * X5 - K.c5 * X7;
-    const float o2 = K.c5 * X1 - K.c1 * X3 + K.c7 * X5 + K.c3 * X7;
-    const float o3 = K.c7 * X1 - K.c5 * X3 + K.c3 * X5 - K.c1 * X7;
+    const float o0 = fmaf(K.h1, X1, fmaf(K.h3, X3, fmaf(K.h5, X5, K.h7 * X7)));
+    const float o1 = fmaf(K.h3, X1, fmaf(-K.h7, X3, fmaf(-K.h1, X5, -(K.h5 * X7))));
+    const float o2 = fmaf(K.h5, X1, fmaf(-K.h1, X3, fmaf(K.h7, X5, K.h3 * X7)));
+    const float o3 = fmaf(K.h7, X1, fmaf(-K.h5, X3, fmaf(K.h3, X5, -(K.h1 * X7))));
     v[O] = e0 + o0;
     v[O + 7 * S] = e0 - o0;
     v[O + S] = e1 + o1;
@@ -187,7 +187,7 @@ __device__ __forceinline__ float wiener_gains(const float *T, int col, float s2,
     for (int k = 0; k < N; ++k) {
         const float zb = v[k] * sc;
         const float b2 = zb * zb;
-        om[k] = b2 / (b2 + s2);
+        om[k] = __fdividef(b2, b2 + s2);  // b2 + s2 >= sigma^2 > 0
         wsq = fmaf(om[k], om[k], wsq);
     }
     return wsq;
@@ -589,13 +589,12 @@ DctK make_dct_constants()
 {
     const double pi = 3.14159265358979323846;
     DctK k;
-    k.c1 = (float)std::cos(1 * pi / 16);
-    k.c2 = (float)std::cos(2 * pi / 16);
-    k.c3 = (float)std::cos(3 * pi / 16);
-    k.c4 = (float)std::cos(4 * pi / 16);
-    k.c5 = (float)std::cos(5 * pi / 16);
-    k.c6 = (float)std::cos(6 * pi / 16);
-    k.c7 = (float)std::cos(7 * pi / 16);
+    k.h1 = (float)(0.5 * std::cos(1 * pi / 16));
+    k.h2 = (float)(0.5 * std::cos(2 * pi / 16));
+    k.h3 = (float)(0.5 * std::cos(3 * pi / 16));
+    k.h5 = (float)(0.5 * std::cos(5 * pi / 16));
+    k.h6 = (float)(0.5 * std::cos(6 * pi / 16));
+    k.h7 = (float)(0.5 * std::cos(7 * pi / 16));
     k.r8 = (float)(1.0 / std::sqrt(8.0));
     return k;
 }

@@ -50,16 +50,16 @@ __device__ __forceinline__ float canon_d64(const float (&ref)[64], Q q)
 template <int L>
 __device__ __forceinline__ void insert_sorted(float (&bd)[L], int (&bi)[L], float d, int id)
 {
+    // slot j takes slot j-1 if d precedes it, else d if d precedes the old slot j
+    bool after = d < bd[L - 1];
 #pragma unroll
     for (int j = L - 1; j > 0; --j) {
         const bool before_prev = d < bd[j - 1];
-        const bool before_this = d < bd[j];
-        const float nd = before_prev ? bd[j - 1] : (before_this ? d : bd[j]);
-        const int ni = before_prev ? bi[j - 1] : (before_this ? id : bi[j]);
-        bd[j] = nd;
-        bi[j] = ni;
+        bd[j] = before_prev ? bd[j - 1] : (after ? d : bd[j]);
+        bi[j] = before_prev ? bi[j - 1] : (after ? id : bi[j]);
+        after = before_prev;
     }
-    if (d < bd[0]) {
+    if (after) {
         bd[0] = d;
         bi[0] = id;
     }
