@@ -60,8 +60,8 @@ struct FilterArgs {
 // ---- 8-point orthonormal DCT-II and its inverse (even/odd decomposition) ----
 
 // x[o], x[o+s], ..., x[o+7s] -> X[u] = a_u sum_m x[m] cos(pi (2m+1) u / 16)
-template <int O, int S>
-__device__ __forceinline__ void dct8(float (&v)[64], const DctK &K)
+template <int O, int S, int NV>
+__device__ __forceinline__ void dct8(float (&v)[NV], const DctK &K)
 {
     const float s0 = v[O] + v[O + 7 * S], d0 = v[O] - v[O + 7 * S];
     const float s1 = v[O + S] + v[O + 6 * S], d1 = v[O + S] - v[O + 6 * S];
@@ -79,8 +79,8 @@ __device__ __forceinline__ void dct8(float (&v)[64], const DctK &K)
 }
 
 // inverse: x[m] = sum_u a_u X[u] cos(pi (2m+1) u / 16)
-template <int O, int S>
-__device__ __forceinline__ void idct8(float (&v)[64], const DctK &K)
+template <int O, int S, int NV>
+__device__ __forceinline__ void idct8(float (&v)[NV], const DctK &K)
 {
     const float X0 = v[O], X1 = v[O + S], X2 = v[O + 2 * S], X3 = v[O + 3 * S];
     const float X4 = v[O + 4 * S], X5 = v[O + 5 * S], X6 = v[O + 6 * S], X7 = v[O + 7 * S];
@@ -353,6 +353,38 @@ __device__ __forceinline__ void idct_rows(float *T, bool valid, int lane, const 
     }
 }
 
+// Two-pass variant of dct_rows with a small register footprint (used while
+// the Wiener gains occupy registers): 1D DCTs of the patch rows from the
+// window into row `lane` of T, then 1D DCTs of its columns in place.
+__device__ __forceinline__ void dct_rows_2pass(float *T, const Window &win, const float *wimg, const float *gimg,
+                                               int W, bool valid, int lane, int py, int px, const DctK &K)
+{
+    const bool all_in = __all_sync(0xffffffffu, !valid || in_window(win, py, px));
+    if (valid) {
+        const float *src = all_in ? wimg + (py - win.Y0) * win.RW + (px - win.X0) : gimg + (size_t)py * W + px;
+        const int stride = all_in ? win.RW : W;
+        float *row = T + lane * kTS;
+#pragma unroll 2
+        for (int r = 0; r < 8; ++r) {
+            float x[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) x[j] = src[r * stride + j];
+            dct8<0, 1>(x, K);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) row[r * 8 + j] = x[j];
+        }
+#pragma unroll 2
+        for (int j = 0; j < 8; ++j) {
+            float x[8];
+#pragma unroll
+            for (int r = 0; r < 8; ++r) x[r] = row[r * 8 + j];
+            dct8<0, 1>(x, K);
+#pragma unroll
+            for (int r = 0; r < 8; ++r) row[r * 8 + j] = x[r];
+        }
+    }
+}
+
 // Wiener transform of one group of N patches (rows [0, N) of T): gains from
 // the basic-estimate group (kept in registers), applied to the noisy group;
 // T is left holding the filtered spectra of the noisy patches.
@@ -365,7 +397,7 @@ __device__ __forceinline__ float wiener_group(const FilterArgs &a, const Window 
     float om0[N], om1[N];
     const float wsq = wiener_gains<N>(T, lane, s2, om0) + wiener_gains<N>(T, lane + 32, s2, om1);
     __syncwarp();
-    dct_rows(T, win, win.img, a.img + cbase, a.W, lane < N, lane, py, px, a.k);
+    dct_rows_2pass(T, win, win.img, a.img + cbase, a.W, lane < N, lane, py, px, a.k);
     __syncwarp();
     wiener_apply<N>(T, lane, om0);
     wiener_apply<N>(T, lane + 32, om1);
@@ -460,7 +492,7 @@ __device__ __forceinline__ void wiener_one(const FilterArgs &a, const Window &wi
 // In the first pass a warp takes the tile's references two at a time and
 // filters both groups together when each has at most 16 patches.
 template <bool WIENER>
-__global__ void __launch_bounds__(WIENER ? 384 : 512) k_filter(FilterArgs a, int TR, int RH, int RW, int RS)
+__global__ void __launch_bounds__(512) k_filter(FilterArgs a, int TR, int RH, int RW, int RS)
 {
     extern __shared__ __align__(16) unsigned char dsm_raw[];
     const int nw = blockDim.x >> 5;
@@ -619,7 +651,7 @@ dn_status filter_common(bool wiener, const float *img, const float *basic, const
     a.k = make_dct_constants();
     const size_t HW = (size_t)H * W, N = (size_t)B * C * HW;
     // tile of references per CTA and its aggregation window
-    const int nwarps = wiener ? 12 : 16;
+    const int nwarps = 16;
     const int nimg = wiener ? 2 : 1;
     const size_t per_warp = (size_t)32 * kTS * sizeof(float);
     int TR = 16;
