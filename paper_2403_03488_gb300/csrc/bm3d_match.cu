@@ -42,7 +42,7 @@ constexpr int kS3T = kSX * kSY;              // threads (one reference each)
 constexpr int kSRows = 3 * (kSY - 1) + 8;    // pixel rows of the tile
 constexpr int kSG = kSX / 4;                 // column groups of 4 references
 constexpr int kSTasks = kSG * kSRows;        // row-sum tasks (row, group)
-constexpr int kSGS = 136;                    // floats per (offset, group) slab: 29 rows x 4, = 8 (mod 32)
+constexpr int kSGS = 120;                    // floats per (offset, group) slab: 29 rows x 4, = 24 (mod 32)
 constexpr int kSK = 8;                       // offsets per chunk
 constexpr int kSBuf = kSK * kSG * kSGS;      // floats per row-sum buffer
 
@@ -57,7 +57,7 @@ struct Match3Args {
 };
 
 template <int L>
-__global__ void __launch_bounds__(kS3T, 3) k_match3(Match3Args a)
+__global__ void __launch_bounds__(kS3T, L <= 15 ? 4 : 3) k_match3(Match3Args a)
 {
     extern __shared__ float4 sm_raw[];
     float *img = reinterpret_cast<float *>(sm_raw);  // [rows][pitch], origin (3 r0 - hs, 3 c0 - hs)
@@ -78,9 +78,7 @@ __global__ void __launch_bounds__(kS3T, 3) k_match3(Match3Args a)
     // row-sum role: tile row ay, reference columns 4 ag .. 4 ag + 3 (pixels 12 ag .. 12 ag + 16)
     const bool task = t < kSTasks;
     const int ag = t / kSRows, ay = t - (t / kSRows) * kSRows;
-    float R[17];
-#pragma unroll
-    for (int x = 0; x < 17; ++x) R[x] = task ? img[(ay + hs) * P + 12 * ag + hs + x] : 0.0f;
+    const float *rrow = img + (ay + hs) * P + 12 * ag + hs;  // reference pixels of the segment
     // reference role
     const int bc = t % kSX, br = t / kSX;
     const int rx = c0 + bc, ry = r0 + br;
@@ -102,9 +100,11 @@ __global__ void __launch_bounds__(kS3T, 3) k_match3(Match3Args a)
             float *hbuf = hb + (it & 1) * kSBuf;
             if (task) {
                 const float *crow = img + (ay + hs + oy) * P + 12 * ag + hs + ox0;
-                float C[24];
+                float C[24], R[17];
 #pragma unroll
                 for (int q = 0; q < 24; ++q) C[q] = crow[q];
+#pragma unroll
+                for (int x = 0; x < 17; ++x) R[x] = rrow[x];
 #pragma unroll
                 for (int k = 0; k < kSK; ++k) {
                     float pr[6], tr[5];
@@ -321,7 +321,9 @@ dn_status match_step3(const float *guide, size_t plane, int B, int H, int W, con
     a.n2 = p.n2;
     a.plane = plane;
     a.rows = kSRows + 2 * a.hs;
-    a.pitch = (2 * a.hs + 60) | 1;  // odd: the row-sum tasks' loads hit at most 2 lanes per bank
+    // row-sum tasks read columns up to 12 * 3 + hs + (last chunk start) + 23; odd pitch: their loads
+    // hit at most 2 lanes per bank
+    a.pitch = (36 + a.hs + (-a.hs + kSK * ((2 * a.hs) / kSK)) + 24) | 1;
     a.img_floats = (a.rows * a.pitch + 3) & ~3;
     const size_t smem = (size_t)(a.img_floats + 2 * kSBuf) * sizeof(float);
     if (smem > 200 * 1024) return DN_EUNSUPPORTED;
