@@ -7,15 +7,18 @@
 // K = 9 taps x 32 input channels, FP32 accumulation in TMEM, BF16 activations
 // in HBM (NHWC, 64 bytes per pixel).
 //
-// Hidden-layer kernel: a CTA owns a 128-pixel column strip and a run of rows.
-// It keeps the packed weights (18 KB) and a ring of three staged input rows
-// (130 pixels incl. halo) in shared memory in the K-major core-matrix layout
-// [channel chunk of 8][pixel][8 channels], so the A operand of tap (dy, dx) is
-// the staged row y+dy-1 shifted by dx pixels: a descriptor offset, no im2col.
-// Per output row one thread issues 18 MMAs (9 taps x 2 K-steps of 16), commits
-// them to an mbarrier, and all 128 threads (thread = pixel = TMEM lane) read
-// the 32 accumulators back, add the bias, apply ReLU and store 64 B of BF16.
-// Each input row is read from HBM once per strip.
+// Hidden-layer kernel: persistent CTAs take work items of 32 output rows of
+// a 128-pixel column strip.  Packed weights (18 KB) stay in shared memory;
+// input rows (130 pixels incl. halo) are staged in a ring of 6 slots in the
+// K-major core-matrix layout [channel chunk of 8][pixel][8 channels], so the A
+// operand of tap (dy, dx) is the staged row y+dy-1 shifted by dx pixels: a
+// descriptor offset, no im2col.  Rows are fetched with cp.async three rows
+// ahead of use; per output row one thread issues 18 MMAs (9 taps x 2 K-steps
+// of 16) into one of two TMEM accumulator buffers and commits them to that
+// buffer's mbarrier, and while the tensor cores work on row y all 128 threads
+// (thread = pixel = TMEM lane) drain row y-1: read 32 accumulators, add the
+// bias, apply ReLU and store 64 B of BF16.  Each input row is read from HBM
+// once per strip and item (plus 2 halo rows per 32).
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -30,6 +33,10 @@ constexpr int kP = 130;                   // staged pixels per input row (P = 2 
 constexpr int kCh = 32;                   // hidden channels
 constexpr int kRowBytes = kP * kCh * 2;   // 8320
 constexpr int kWBytes = 9 * 4 * kCh * 16; // 18432: [tap][chunk][cout][8 ch] bf16
+constexpr int kPF = 1;                    // rows in flight beyond the next one
+constexpr int kSlots = kPF + 5;           // rows y-2 (last MMA) .. y+2+kPF
+constexpr int kItemRows = 32;             // output rows per work item
+constexpr int kCtasPerSm = 3;
 constexpr uint32_t kIdesc = tc::idesc_bf16(128, 32);
 
 struct ConvTcArgs {
@@ -37,18 +44,24 @@ struct ConvTcArgs {
     uint4 *y;             // same layout
     const uint4 *wpack;   // kWBytes
     const float *bias;    // [32]
-    int H, W, rows_per_cta, relu;
+    int N, H, W, strips, chunks, relu;
     int *err;
 };
 
-__device__ __forceinline__ void stage_row(const ConvTcArgs &a, uint8_t *slot, int n, int r, int x0, int tid)
+// Row r of image n, pixels x0-1 .. x0+128, into the chunk planes of a ring
+// slot: cp.async for pixels inside the image, zeros elsewhere.
+__device__ __forceinline__ void issue_row(const ConvTcArgs &a, uint8_t *slot, int n, int r, int x0, int tid)
 {
+    const bool rin = r >= 0 && r < a.H;
+    const uint4 *src = a.x + ((size_t)n * a.H + (rin ? r : 0)) * a.W * 4;
     for (int i = tid; i < kP * 4; i += 128) {
         const int px = i >> 2, ck = i & 3;
         const int gx = x0 - 1 + px;
-        uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (r >= 0 && r < a.H && gx >= 0 && gx < a.W) v = a.x[(((size_t)n * a.H + r) * a.W + gx) * 4 + ck];
-        *reinterpret_cast<uint4 *>(slot + ck * kP * 16 + px * 16) = v;
+        uint8_t *dst = slot + ck * kP * 16 + px * 16;
+        if (rin && gx >= 0 && gx < a.W)
+            tc::cp_async16(tc::smem_u32(dst), src + (size_t)gx * 4 + ck);
+        else
+            *reinterpret_cast<uint4 *>(dst) = make_uint4(0u, 0u, 0u, 0u);
     }
 }
 
@@ -56,61 +69,40 @@ __global__ void __launch_bounds__(128) k_conv3x3_tc(ConvTcArgs a)
 {
     extern __shared__ __align__(128) uint8_t sm[];
     uint8_t *wsm = sm;
-    uint8_t *rows = sm + kWBytes;
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(rows + 3 * kRowBytes);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
+    uint8_t *ring = sm + kWBytes;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(ring + kSlots * kRowBytes);  // [2]
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 2);
     float *sbias = reinterpret_cast<float *>(tslot + 4);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int x0 = blockIdx.x * kPX, n = blockIdx.z;
-    const int y_begin = blockIdx.y * a.rows_per_cta;
-    const int y_end = min(a.H, y_begin + a.rows_per_cta);
-    if (y_begin >= a.H) return;
-
     for (int i = tid; i < kWBytes / 16; i += 128) reinterpret_cast<uint4 *>(wsm)[i] = a.wpack[i];
     if (tid < kCh) sbias[tid] = a.bias[tid];
-    if (warp == 0) tc::tmem_alloc(tslot, 32);
-    if (tid == 0) tc::mbar_init(mbar, 1);
-    stage_row(a, rows + ((y_begin + 2) % 3) * kRowBytes, n, y_begin - 1, x0, tid);
-    stage_row(a, rows + (y_begin % 3) * kRowBytes, n, y_begin, x0, tid);
+    if (warp == 0) tc::tmem_alloc(tslot, 64);
+    if (tid == 0) {
+        tc::mbar_init(&mbar[0], 1);
+        tc::mbar_init(&mbar[1], 1);
+    }
+    tc::fence_proxy_async();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tslot;
     const uint32_t wbase = tc::smem_u32(wsm);
-    uint32_t phase = 0;
+    uint32_t phases = 0u;  // bit b: parity of the next completion of mbar[b]
     bool failed = false;
+    bool fail = false;  // this warp saw a wait time out
 
-    for (int y = y_begin; y < y_end; ++y) {
-        stage_row(a, rows + ((y + 1) % 3) * kRowBytes, n, y + 1, x0, tid);
-        tc::fence_proxy_async();
-        tc::fence_before_sync();
-        __syncthreads();
-        if (tid == 0) {
-            tc::fence_after_sync();
-#pragma unroll
-            for (int t = 0; t < 9; ++t) {
-                const int dy = t / 3, dx = t % 3;
-                const uint32_t rb = tc::smem_u32(rows + ((y + 2 + dy) % 3) * kRowBytes);
-#pragma unroll
-                for (int k = 0; k < 2; ++k) {
-                    const uint64_t ad = tc::sdesc(rb + (2 * k) * kP * 16 + dx * 16, kP * 16, 128);
-                    const uint64_t bd = tc::sdesc(wbase + ((t * 4 + 2 * k) * kCh) * 16, kCh * 16, 128);
-                    tc::mma_bf16(tmem, ad, bd, kIdesc, (t | k) != 0);
-                }
-            }
-            tc::mma_commit(mbar);
+    // drains output row yy from TMEM buffer `buf`
+    auto epilogue = [&](int n, int x0, int yy, int buf) {
+        const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(&mbar[buf], (phases >> buf) & 1u));
+        phases ^= 1u << buf;
+        if (!ok) {  // warp-uniform: the TMEM load below is a warp-collective
+            fail = true;
+            return;
         }
-        const bool ok = tc::mbar_wait(mbar, phase);
-        if (__syncthreads_or(!ok)) {  // block-uniform decision
-            failed = true;
-            if (tid == 0) atomicExch(a.err, 1);
-            break;
-        }
-        phase ^= 1;
         tc::fence_after_sync();
         uint32_t r[32];
-        tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), r);
+        tc::tmem_ld32(tmem + (uint32_t)(32 * buf) + ((uint32_t)(warp * 32) << 16), r);
         tc::tmem_wait_ld();
         const int x = x0 + warp * 32 + lane;
         if (x < a.W) {
@@ -125,20 +117,67 @@ __global__ void __launch_bounds__(128) k_conv3x3_tc(ConvTcArgs a)
                 }
                 pk[c] = tc::pack_bf16x2(v0, v1);
             }
-            uint4 *dst = a.y + (((size_t)n * a.H + y) * a.W + x) * 4;
+            uint4 *dst = a.y + (((size_t)n * a.H + yy) * a.W + x) * 4;
 #pragma unroll
             for (int q = 0; q < 4; ++q) dst[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
         }
         tc::fence_before_sync();
+    };
+
+    const int items = a.N * a.strips * a.chunks;
+    for (int it = blockIdx.x; it < items && !failed; it += gridDim.x) {
+        const int chunk = it % a.chunks, rest = it / a.chunks;
+        const int strip = rest % a.strips, n = rest / a.strips;
+        const int x0 = strip * kPX, y0 = chunk * kItemRows, y1 = min(a.H, y0 + kItemRows);
+        auto slot = [&](int r) { return ring + ((r - y0 + 1) % kSlots) * kRowBytes; };
+        for (int r = y0 - 1; r <= y0 + 1 + kPF; ++r) {
+            if (r <= y1) issue_row(a, slot(r), n, r, x0, tid);
+            tc::cp_async_commit();
+        }
+        for (int y = y0; y < y1; ++y) {
+            const int rn = y + 2 + kPF;
+            if (rn <= y1) issue_row(a, slot(rn), n, rn, x0, tid);
+            tc::cp_async_commit();
+            tc::cp_async_wait<kPF + 1>();  // rows up to y + 1 have landed (this thread's copies)
+            tc::fence_proxy_async();
+            tc::fence_before_sync();
+            if (__syncthreads_or(fail)) {  // block-uniform
+                failed = true;
+                break;
+            }
+            tc::fence_after_sync();
+            const int buf = (y - y0) & 1;
+            if (tid == 0) {
+#pragma unroll
+                for (int t = 0; t < 9; ++t) {
+                    const int dy = t / 3, dx = t % 3;
+                    const uint32_t rb = tc::smem_u32(slot(y - 1 + dy));
+#pragma unroll
+                    for (int k = 0; k < 2; ++k) {
+                        const uint64_t ad = tc::sdesc(rb + (2 * k) * kP * 16 + dx * 16, kP * 16, 128);
+                        const uint64_t bd = tc::sdesc(wbase + ((t * 4 + 2 * k) * kCh) * 16, kCh * 16, 128);
+                        tc::mma_bf16(tmem + (uint32_t)(32 * buf), ad, bd, kIdesc, (t | k) != 0);
+                    }
+                }
+                tc::mma_commit(&mbar[buf]);
+            }
+            if (y > y0) epilogue(n, x0, y - 1, buf ^ 1);
+        }
+        if (!failed) epilogue(n, x0, y1 - 1, (y1 - 1 - y0) & 1);
+        tc::cp_async_wait<0>();
+        if (__syncthreads_or(fail)) failed = true;
     }
     if (failed) {
-        // bounded second wait for MMAs still in flight before the TMEM is freed
-        tc::mbar_wait(mbar, phase);
+        if (tid == 0) atomicExch(a.err, 1);
+        // bounded waits for MMAs still in flight before the TMEM is freed
+        tc::mbar_wait(&mbar[0], phases & 1u);
+        tc::mbar_wait(&mbar[1], (phases >> 1) & 1u);
     }
+    tc::cp_async_wait<0>();
     __syncthreads();
     if (warp == 0) {
         tc::fence_after_sync();
-        tc::tmem_dealloc(tmem, 32);
+        tc::tmem_dealloc(tmem, 64);
     }
 }
 
@@ -154,90 +193,138 @@ __global__ void k_pack_w_tc(const float *w, uint16_t *out)
 }
 
 // Layer 1 (2 -> 32) + bias + ReLU: pre/noisy planes (0..255) -> NHWC bf16.
+// CTA: 32 x 16 output pixels; thread (tx, ty) computes pixels tx and tx + 16
+// of row ty (lanes on consecutive pixels), reading each output channel's 18
+// weights as float4 (padded rows).
 __global__ void __launch_bounds__(256) k_conv_first_bf16(const float *pre, const float *noisy, const float *w,
                                                         const float *b, uint4 *y, int H, int W)
 {
-    __shared__ float zs[2][18][18];
-    __shared__ float ws[kCh * 18];
+    __shared__ float zs[2][18][48];  // row stride 16 (mod 32): the two half-warps use disjoint banks
+    __shared__ __align__(16) float ws[kCh][20];
     __shared__ float bs[kCh];
-    const int n = blockIdx.z, X0 = blockIdx.x * 16, Y0 = blockIdx.y * 16;
+    const int n = blockIdx.z, X0 = blockIdx.x * 32, Y0 = blockIdx.y * 16;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const size_t HW = (size_t)H * W;
-    for (int i = threadIdx.x; i < kCh * 18; i += 256) ws[i] = w[i];
+    for (int i = threadIdx.x; i < kCh * 20; i += 256) {
+        const int c = i / 20, k = i - c * 20;
+        ws[c][k] = k < 18 ? w[c * 18 + k] : 0.0f;
+    }
     if (threadIdx.x < kCh) bs[threadIdx.x] = b[threadIdx.x];
-    for (int i = threadIdx.x; i < 2 * 324; i += 256) {
-        const int c = i / 324, p = i % 324, yy = p / 18, xx = p % 18;
+    // raw planes (scaled by 1/255 at use), all loads in flight at once
+    for (int i = threadIdx.x; i < 2 * 18 * 34; i += 256) {
+        const int c = i / (18 * 34), p = i - c * (18 * 34), yy = p / 34, xx = p - (p / 34) * 34;
         const int gy = Y0 - 1 + yy, gx = X0 - 1 + xx;
         const float *src = c == 0 ? pre : noisy;
-        zs[c][yy][xx] = (gy >= 0 && gy < H && gx >= 0 && gx < W) ? src[n * HW + (size_t)gy * W + gx] * (1.0f / 255.0f)
-                                                                  : 0.0f;
+        if (gy >= 0 && gy < H && gx >= 0 && gx < W)
+            tc::cp_async4(tc::smem_u32(&zs[c][yy][xx]), src + n * HW + (size_t)gy * W + gx);
+        else
+            zs[c][yy][xx] = 0.0f;
     }
+    tc::cp_async_commit();
+    tc::cp_async_wait<0>();
     __syncthreads();
-    const int px = X0 + tx, py = Y0 + ty;
-    if (px >= W || py >= H) return;
-    float v[18];
+    const int py = Y0 + ty;
+    if (py >= H || X0 + tx >= W) return;
+    float v0[18], v1[18];
 #pragma unroll
     for (int t = 0; t < 9; ++t) {
-        v[2 * t] = zs[0][ty + t / 3][tx + t % 3];
-        v[2 * t + 1] = zs[1][ty + t / 3][tx + t % 3];
+        v0[2 * t] = zs[0][ty + t / 3][tx + t % 3] * (1.0f / 255.0f);
+        v0[2 * t + 1] = zs[1][ty + t / 3][tx + t % 3] * (1.0f / 255.0f);
+        v1[2 * t] = zs[0][ty + t / 3][tx + 16 + t % 3] * (1.0f / 255.0f);
+        v1[2 * t + 1] = zs[1][ty + t / 3][tx + 16 + t % 3] * (1.0f / 255.0f);
     }
-    uint32_t pk[16];
+    uint32_t p0[16], p1[16];
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
-        float a0 = bs[2 * c], a1 = bs[2 * c + 1];
+        float a0 = bs[2 * c], a1 = bs[2 * c + 1], b0 = a0, b1 = a1;
+        const float4 *w0 = reinterpret_cast<const float4 *>(ws[2 * c]);
+        const float4 *w1 = reinterpret_cast<const float4 *>(ws[2 * c + 1]);
 #pragma unroll
-        for (int k = 0; k < 18; ++k) {
-            a0 = fmaf(ws[(2 * c) * 18 + k], v[k], a0);
-            a1 = fmaf(ws[(2 * c + 1) * 18 + k], v[k], a1);
+        for (int q = 0; q < 5; ++q) {
+            const float4 u0 = w0[q], u1 = w1[q];
+            const float e0[4] = {u0.x, u0.y, u0.z, u0.w}, e1[4] = {u1.x, u1.y, u1.z, u1.w};
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int k = 4 * q + r;
+                if (k < 18) {
+                    a0 = fmaf(e0[r], v0[k], a0);
+                    a1 = fmaf(e1[r], v0[k], a1);
+                    b0 = fmaf(e0[r], v1[k], b0);
+                    b1 = fmaf(e1[r], v1[k], b1);
+                }
+            }
         }
-        pk[c] = tc::pack_bf16x2(fmaxf(a0, 0.0f), fmaxf(a1, 0.0f));
+        p0[c] = tc::pack_bf16x2(fmaxf(a0, 0.0f), fmaxf(a1, 0.0f));
+        p1[c] = tc::pack_bf16x2(fmaxf(b0, 0.0f), fmaxf(b1, 0.0f));
     }
-    uint4 *dst = y + ((size_t)n * HW + (size_t)py * W + px) * 4;
+    uint4 *dst = y + ((size_t)n * HW + (size_t)py * W + X0 + tx) * 4;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) dst[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+    for (int q = 0; q < 4; ++q) dst[q] = make_uint4(p0[4 * q], p0[4 * q + 1], p0[4 * q + 2], p0[4 * q + 3]);
+    if (X0 + tx + 16 < W) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            dst[64 + q] = make_uint4(p1[4 * q], p1[4 * q + 1], p1[4 * q + 2], p1[4 * q + 3]);
+    }
 }
 
-// Last layer (32 -> 1) + bias, then out = pre + 255 r (Eq. 2).
+// Last layer (32 -> 1) + bias, then out = pre + 255 r (Eq. 2).  CTA: 32 x 16
+// output pixels; thread (tx, ty) computes pixels tx and tx + 16 of row ty.
+// Staged pixels are 80 bytes apart (64 B + 16 B pad), so the 8 lanes of each
+// 128-bit load phase hit disjoint banks.
+constexpr int kLastPS = 5;  // uint4 per staged pixel
+
 __global__ void __launch_bounds__(256) k_conv_last_bf16(const uint4 *x, const float *w, const float *b,
                                                        const float *pre, float *out, int H, int W)
 {
-    __shared__ uint4 xs[324 * 4];
-    __shared__ float ws[9 * kCh];
-    const int n = blockIdx.z, X0 = blockIdx.x * 16, Y0 = blockIdx.y * 16;
+    extern __shared__ uint4 xs_dyn[];  // [18 * 34 * kLastPS] pixels, then 9 x 32 weights
+    uint4 *xs = xs_dyn;
+    float *ws = reinterpret_cast<float *>(xs_dyn + 18 * 34 * kLastPS);
+    const int n = blockIdx.z, X0 = blockIdx.x * 32, Y0 = blockIdx.y * 16;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const size_t HW = (size_t)H * W;
     for (int i = threadIdx.x; i < 9 * kCh; i += 256) ws[i] = w[i];
-    for (int i = threadIdx.x; i < 324 * 4; i += 256) {
-        const int p = i >> 2, ck = i & 3, yy = p / 18, xx = p % 18;
+    for (int i = threadIdx.x; i < 18 * 34 * 4; i += 256) {
+        const int p = i >> 2, ck = i & 3, yy = p / 34, xx = p - (p / 34) * 34;
         const int gy = Y0 - 1 + yy, gx = X0 - 1 + xx;
-        xs[i] = (gy >= 0 && gy < H && gx >= 0 && gx < W) ? x[((size_t)n * HW + (size_t)gy * W + gx) * 4 + ck]
-                                                         : make_uint4(0u, 0u, 0u, 0u);
+        uint4 *dst = &xs[p * kLastPS + ck];
+        if (gy >= 0 && gy < H && gx >= 0 && gx < W)
+            tc::cp_async16(tc::smem_u32(dst), x + ((size_t)n * HW + (size_t)gy * W + gx) * 4 + ck);
+        else
+            *dst = make_uint4(0u, 0u, 0u, 0u);
     }
+    tc::cp_async_commit();
+    tc::cp_async_wait<0>();
     __syncthreads();
-    const int px = X0 + tx, py = Y0 + ty;
-    if (px >= W || py >= H) return;
-    float acc = b[0];
+    const int py = Y0 + ty;
+    if (py >= H || X0 + tx >= W) return;
+    float acc0 = b[0], acc1 = acc0;
+    const float4 *w4 = reinterpret_cast<const float4 *>(ws);
 #pragma unroll
     for (int t = 0; t < 9; ++t) {
-        const int p = (ty + t / 3) * 18 + tx + t % 3;
+        const int p = (ty + t / 3) * 34 + tx + t % 3;
 #pragma unroll
         for (int ck = 0; ck < 4; ++ck) {
-            const uint4 q = xs[p * 4 + ck];
-            const uint32_t u[4] = {q.x, q.y, q.z, q.w};
+            const uint4 q0 = xs[p * kLastPS + ck], q1 = xs[(p + 16) * kLastPS + ck];
+            const float4 wa = w4[(t * kCh + ck * 8) / 4], wb = w4[(t * kCh + ck * 8) / 4 + 1];
+            const float wv[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+            const uint32_t u0[4] = {q0.x, q0.y, q0.z, q0.w}, u1[4] = {q1.x, q1.y, q1.z, q1.w};
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                acc = fmaf(ws[t * kCh + ck * 8 + 2 * e], tc::bf16_lo(u[e]), acc);
-                acc = fmaf(ws[t * kCh + ck * 8 + 2 * e + 1], tc::bf16_hi(u[e]), acc);
+                acc0 = fmaf(wv[2 * e], tc::bf16_lo(u0[e]), acc0);
+                acc0 = fmaf(wv[2 * e + 1], tc::bf16_hi(u0[e]), acc0);
+                acc1 = fmaf(wv[2 * e], tc::bf16_lo(u1[e]), acc1);
+                acc1 = fmaf(wv[2 * e + 1], tc::bf16_hi(u1[e]), acc1);
             }
         }
     }
-    const size_t at = n * HW + (size_t)py * W + px;
-    out[at] = fmaf(255.0f, acc, pre[at]);
+    const size_t at = n * HW + (size_t)py * W + X0 + tx;
+    out[at] = fmaf(255.0f, acc0, pre[at]);
+    if (X0 + tx + 16 < W) out[at + 16] = fmaf(255.0f, acc1, pre[at + 16]);
 }
 
 }  // namespace
 
-size_t conv_tc_smem_bytes() { return kWBytes + 3 * kRowBytes + 64 + kCh * 4; }
+size_t conv_tc_smem_bytes() { return kWBytes + kSlots * kRowBytes + 32 + kCh * 4; }
 
 dn_status pack_w_tc(const float *w, void *out, cudaStream_t s)
 {
@@ -252,18 +339,15 @@ dn_status conv3x3_tc(const void *x, void *y, const void *wpack, const float *bia
     a.y = static_cast<uint4 *>(y);
     a.wpack = static_cast<const uint4 *>(wpack);
     a.bias = bias;
+    a.N = N;
     a.H = H;
     a.W = W;
     a.relu = relu;
     a.err = err;
-    const int strips = (W + kPX - 1) / kPX;
-    const long target = 152L * 10;
-    long chunks = (target + (long)strips * N - 1) / ((long)strips * N);
-    if (chunks < 1) chunks = 1;
-    int rows = (int)((H + chunks - 1) / chunks);
-    if (rows < 4) rows = 4;
-    a.rows_per_cta = rows;
-    dim3 grid(strips, (H + rows - 1) / rows, N);
+    a.strips = (W + kPX - 1) / kPX;
+    a.chunks = (H + kItemRows - 1) / kItemRows;
+    const long items = (long)N * a.strips * a.chunks;
+    const int grid = (int)(items < 152L * kCtasPerSm ? items : 152L * kCtasPerSm);
     const size_t smem = conv_tc_smem_bytes();
     if (cudaFuncSetAttribute(k_conv3x3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return DN_ECUDA;
@@ -273,7 +357,7 @@ dn_status conv3x3_tc(const void *x, void *y, const void *wpack, const float *bia
 dn_status conv_first_bf16(const float *pre, const float *noisy, const float *w, const float *b, void *y, int N,
                           int H, int W, cudaStream_t s)
 {
-    dim3 grid((W + 15) / 16, (H + 15) / 16, N);
+    dim3 grid((W + 31) / 32, (H + 15) / 16, N);
     return launch("conv_first_bf16", s,
                   [&] { k_conv_first_bf16<<<grid, 256, 0, s>>>(pre, noisy, w, b, static_cast<uint4 *>(y), H, W); });
 }
@@ -281,9 +365,12 @@ dn_status conv_first_bf16(const float *pre, const float *noisy, const float *w, 
 dn_status conv_last_bf16(const void *x, const float *w, const float *b, const float *pre, float *out, int N, int H,
                          int W, cudaStream_t s)
 {
-    dim3 grid((W + 15) / 16, (H + 15) / 16, N);
+    dim3 grid((W + 31) / 32, (H + 15) / 16, N);
+    const int smem = 18 * 34 * kLastPS * 16 + 9 * kCh * 4;
+    if (cudaFuncSetAttribute(k_conv_last_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+        return DN_ECUDA;
     return launch("conv_last_bf16", s, [&] {
-        k_conv_last_bf16<<<grid, 256, 0, s>>>(static_cast<const uint4 *>(x), w, b, pre, out, H, W);
+        k_conv_last_bf16<<<grid, 256, smem, s>>>(static_cast<const uint4 *>(x), w, b, pre, out, H, W);
     });
 }
 

@@ -147,6 +147,25 @@ def test_conv3x3_tc_bf16_parity(oracle, N, H, W, relu):
     assert A.device_error() == 0
 
 
+def test_conv3x3_tc_bf16_more_work_items_than_ctas():
+    """Persistent tcgen05 conv with more (image, strip, 32-row chunk) items than
+    resident CTAs (500 items: ragged last strip and chunk), against a plain
+    PyTorch FP32 conv of the same BF16-rounded operands."""
+    import torch
+    A = api()
+    N, H, W = 10, 300, 520
+    g = torch.Generator(device="cuda").manual_seed(5)
+    x = torch.relu(torch.randn(N, H, W, 32, device="cuda", generator=g)).to(torch.bfloat16)
+    w = (torch.randn(32, 3, 3, 32, device="cuda", generator=g) * (2.0 / 288) ** 0.5).to(torch.bfloat16).float()
+    b = torch.randn(32, device="cuda", generator=g) * 0.1
+    y = A.conv3x3_tc_fwd(x, w.contiguous(), b, relu=True)
+    ref = torch.relu(torch.nn.functional.conv2d(x.float().permute(0, 3, 1, 2), w.permute(0, 3, 1, 2), b, padding=1))
+    got = y.float().permute(0, 3, 1, 2)
+    scale = ref.abs().max()
+    assert bool(((got - ref).abs() <= 2 ** -7 * ref.abs() + 1e-3 * scale).all())
+    assert A.device_error() == 0
+
+
 def test_cnn_forward_bf16_close_to_oracle(oracle):
     A = api()
     rng = np.random.default_rng(8)
