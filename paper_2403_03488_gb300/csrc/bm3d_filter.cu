@@ -143,11 +143,17 @@ __device__ __forceinline__ void fwht(float (&v)[N])
 }
 
 template <int N>
-__device__ __forceinline__ float inv_sqrt_n()
+__device__ __forceinline__ float sqrt_n()
 {
-    return N == 1 ? 1.0f : N == 2 ? 0.70710678118654752f : N == 4 ? 0.5f : N == 8 ? 0.35355339059327376f
-         : N == 16 ? 0.25f : 0.17677669529663688f;
+    return N == 1 ? 1.0f : N == 2 ? 1.41421356237309505f : N == 4 ? 2.0f : N == 8 ? 2.82842712474619010f
+         : N == 16 ? 4.0f : 5.65685424949238019f;
 }
+
+// The group transform runs unnormalised: fwht twice multiplies by N, so the
+// thresholds and gains below are expressed on the unscaled coefficients
+// (|c| / sqrt(N) > thr  <=>  |c| > thr sqrt(N);  B^2 / N / (B^2 / N + s2) =
+// B^2 / (B^2 + N s2)) and the exact power-of-two factor 1/N is applied to the
+// aggregation weight of the estimate instead.
 
 // Hard threshold of coefficient column `col` of an n-patch group in T.
 template <int N>
@@ -157,18 +163,17 @@ __device__ __forceinline__ int hard_col(float *T, int col, float thr)
 #pragma unroll
     for (int k = 0; k < N; ++k) v[k] = T[k * kTS + col];
     fwht<N>(v);
-    const float sc = inv_sqrt_n<N>();
+    const float thr_n = thr * sqrt_n<N>();
     int cnt = 0;
 #pragma unroll
     for (int k = 0; k < N; ++k) {
-        const float z = v[k] * sc;
-        const bool keep = fabsf(z) > thr;
+        const bool keep = fabsf(v[k]) > thr_n;
         cnt += keep ? 1 : 0;
-        v[k] = keep ? z : 0.0f;
+        v[k] = keep ? v[k] : 0.0f;
     }
     fwht<N>(v);
 #pragma unroll
-    for (int k = 0; k < N; ++k) T[k * kTS + col] = v[k] * sc;
+    for (int k = 0; k < N; ++k) T[k * kTS + col] = v[k];
     return cnt;
 }
 
@@ -181,13 +186,12 @@ __device__ __forceinline__ float wiener_gains(const float *T, int col, float s2,
 #pragma unroll
     for (int k = 0; k < N; ++k) v[k] = T[k * kTS + col];
     fwht<N>(v);
-    const float sc = inv_sqrt_n<N>();
+    const float s2n = s2 * (float)N;
     float wsq = 0.0f;
 #pragma unroll
     for (int k = 0; k < N; ++k) {
-        const float zb = v[k] * sc;
-        const float b2 = zb * zb;
-        om[k] = __fdividef(b2, b2 + s2);  // b2 + s2 >= sigma^2 > 0
+        const float b2 = v[k] * v[k];
+        om[k] = __fdividef(b2, b2 + s2n);  // b2 + s2n >= sigma^2 > 0
         wsq = fmaf(om[k], om[k], wsq);
     }
     return wsq;
@@ -201,12 +205,11 @@ __device__ __forceinline__ void wiener_apply(float *T, int col, const float (&om
 #pragma unroll
     for (int k = 0; k < N; ++k) v[k] = T[k * kTS + col];
     fwht<N>(v);
-    const float sc2 = inv_sqrt_n<N>() * inv_sqrt_n<N>();
 #pragma unroll
     for (int k = 0; k < N; ++k) v[k] *= om[k];
     fwht<N>(v);
 #pragma unroll
-    for (int k = 0; k < N; ++k) T[k * kTS + col] = v[k] * sc2;
+    for (int k = 0; k < N; ++k) T[k * kTS + col] = v[k];
 }
 
 __device__ __forceinline__ int hard_columns(float *T, int n, int lane, float thr)
@@ -412,13 +415,14 @@ __device__ __forceinline__ float wiener_group(const FilterArgs &a, const Window 
 __device__ __forceinline__ void aggregate(const FilterArgs &a, const Window &win, const float *T, size_t cbase, int s,
                                           int n, int lane, int py, int px, float w, const float (&ka)[2])
 {
+    const float vs = 1.0f / (float)n;  // the unnormalised group transform's factor n (exact power of two)
     if (lane >= s && lane < s + n) {
         const Fix fw = to_fixed(w);
         const size_t q = cbase + (size_t)py * a.W + px;
         atomicAdd(a.wsum + q, fw.lo);
         if (fw.hi != 0) atomicAdd(a.wsum_hi + q, (unsigned long long)fw.hi);
     }
-    const float wk0 = w * ka[0], wk1 = w * ka[1];
+    const float wk0 = w * ka[0] * vs, wk1 = w * ka[1] * vs;
     const int i0 = lane >> 3, j = lane & 7;
 #pragma unroll 2
     for (int k = s; k < s + n; ++k) {

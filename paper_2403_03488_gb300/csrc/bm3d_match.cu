@@ -18,11 +18,13 @@
 // threads own a 17-pixel segment of one tile row (4 reference columns 3
 // apart), split it into sums of 3 and 2 differences and combine them into the
 // 4 row sums (3 + 3 + 2 pixels), for 8 horizontally adjacent offsets at a time
-// (24 candidate pixels loaded per 8 offsets).  The row sums go through a
-// double-buffered shared array; then each thread, owning one reference,
-// combines its 8 row sums (3 + 3 + 2 rows) and updates its sorted list in
-// registers.  About 60 % fewer operations than one subtract and one FMA per
-// pixel and candidate.
+// (24 candidate pixels loaded per 8 offsets), two offsets per packed FP32x2
+// instruction.  The row sums go through a double-buffered shared array (the
+// two offsets of a pair interleaved); then each thread, owning one reference,
+// combines its 8 row sums (3 + 3 + 2 rows), again two offsets per packed
+// instruction, and updates its sorted list in registers.  Packed lanes round
+// exactly like the scalar operations, so the distances are those of the
+// fixed association.
 //
 // Other steps: k_match_fp32, one thread per reference over a 16 x 8 tile,
 // register-blocked over 8 horizontally adjacent candidates (15 shared loads
@@ -42,9 +44,10 @@ constexpr int kS3T = kSX * kSY;              // threads (one reference each)
 constexpr int kSRows = 3 * (kSY - 1) + 8;    // pixel rows of the tile
 constexpr int kSG = kSX / 4;                 // column groups of 4 references
 constexpr int kSTasks = kSG * kSRows;        // row-sum tasks (row, group)
-constexpr int kSGS = 120;                    // floats per (offset, group) slab: 29 rows x 4, = 24 (mod 32)
-constexpr int kSK = 8;                       // offsets per chunk
-constexpr int kSBuf = kSK * kSG * kSGS;      // floats per row-sum buffer
+constexpr int kSK = 8;                       // offsets per chunk (4 packed pairs)
+constexpr int kSGS = kSRows * 8;             // floats per (offset pair, group) slab: rows x 4 columns x 2 offsets
+                                             // (232 = 8 mod 32: the per-reference 64-bit loads are conflict-free)
+constexpr int kSBuf = (kSK / 2) * kSG * kSGS;  // floats per row-sum buffer
 
 struct Match3Args {
     const float *g;
@@ -57,7 +60,7 @@ struct Match3Args {
 };
 
 template <int L>
-__global__ void __launch_bounds__(kS3T, L <= 15 ? 4 : 3) k_match3(Match3Args a)
+__global__ void __launch_bounds__(kS3T, 4) k_match3(Match3Args a)
 {
     extern __shared__ float4 sm_raw[];
     float *img = reinterpret_cast<float *>(sm_raw);  // [rows][pitch], origin (3 r0 - hs, 3 c0 - hs)
@@ -100,40 +103,54 @@ __global__ void __launch_bounds__(kS3T, L <= 15 ? 4 : 3) k_match3(Match3Args a)
             float *hbuf = hb + (it & 1) * kSBuf;
             if (task) {
                 const float *crow = img + (ay + hs + oy) * P + 12 * ag + hs + ox0;
-                float C[24], R[17];
+                float C[24];
 #pragma unroll
                 for (int q = 0; q < 24; ++q) C[q] = crow[q];
+                f2 RR[17];
 #pragma unroll
-                for (int x = 0; x < 17; ++x) R[x] = rrow[x];
+                for (int x = 0; x < 17; ++x) {
+                    const float r = rrow[x];
+                    RR[x] = f2_pack(r, r);
+                }
+                // offsets (2 kp, 2 kp + 1) in the two lanes of every packed value
 #pragma unroll
-                for (int k = 0; k < kSK; ++k) {
-                    float pr[6], tr[5];
+                for (int kp = 0; kp < kSK / 2; ++kp) {
+                    f2 pr[6], tr[5];
 #pragma unroll
                     for (int u = 0; u < 5; ++u) {
-                        pr[u] = __fadd_rn(sqd(R[3 * u], C[3 * u + k]), sqd(R[3 * u + 1], C[3 * u + 1 + k]));
-                        tr[u] = __fadd_rn(pr[u], sqd(R[3 * u + 2], C[3 * u + 2 + k]));
+                        const int j = 3 * u + 2 * kp;
+                        pr[u] = f2_add(f2_sqd(RR[3 * u], f2_pack(C[j], C[j + 1])),
+                                       f2_sqd(RR[3 * u + 1], f2_pack(C[j + 1], C[j + 2])));
+                        tr[u] = f2_add(pr[u], f2_sqd(RR[3 * u + 2], f2_pack(C[j + 2], C[j + 3])));
                     }
-                    pr[5] = __fadd_rn(sqd(R[15], C[15 + k]), sqd(R[16], C[16 + k]));
-                    float4 h;
-                    h.x = __fadd_rn(__fadd_rn(tr[0], tr[1]), pr[2]);
-                    h.y = __fadd_rn(__fadd_rn(tr[1], tr[2]), pr[3]);
-                    h.z = __fadd_rn(__fadd_rn(tr[2], tr[3]), pr[4]);
-                    h.w = __fadd_rn(__fadd_rn(tr[3], tr[4]), pr[5]);
-                    *reinterpret_cast<float4 *>(hbuf + (k * kSG + ag) * kSGS + 4 * ay) = h;
+                    pr[5] = f2_add(f2_sqd(RR[15], f2_pack(C[15 + 2 * kp], C[16 + 2 * kp])),
+                                   f2_sqd(RR[16], f2_pack(C[16 + 2 * kp], C[17 + 2 * kp])));
+                    const f2 h0 = f2_add(f2_add(tr[0], tr[1]), pr[2]);
+                    const f2 h1 = f2_add(f2_add(tr[1], tr[2]), pr[3]);
+                    const f2 h2 = f2_add(f2_add(tr[2], tr[3]), pr[4]);
+                    const f2 h3 = f2_add(f2_add(tr[3], tr[4]), pr[5]);
+                    ulonglong2 *dst = reinterpret_cast<ulonglong2 *>(hbuf + (kp * kSG + ag) * kSGS + 8 * ay);
+                    dst[0] = make_ulonglong2(h0.v, h1.v);
+                    dst[1] = make_ulonglong2(h2.v, h3.v);
                 }
             }
             __syncthreads();  // one barrier per chunk: the buffers alternate
             if (yok) {
-                const float *hc = hbuf + (bc >> 2) * kSGS + 12 * br + (bc & 3);
+                const f2 *hc = reinterpret_cast<const f2 *>(hbuf + (bc >> 2) * kSGS + 24 * br + 2 * (bc & 3));
+                const f2 s64 = f2_pack(0.015625f, 0.015625f);
 #pragma unroll
-                for (int k = 0; k < kSK; ++k) {
-                    const float *hk = hc + k * kSG * kSGS;
-                    const float d = tree8(hk[0], hk[4], hk[8], hk[12], hk[16], hk[20], hk[24], hk[28]) * 0.015625f;
-                    const int ox = ox0 + k, cx = xr + ox;
-                    const bool ok = ox <= hs && (unsigned)cx <= (unsigned)(W - 8) && (ox | oy) != 0 && d <= tau;
-                    if (ok) {
-                        ++kept;
-                        if (d < bd[L - 1]) insert_sorted<L>(bd, bi, d, (yr + oy) * W + cx);
+                for (int kp = 0; kp < kSK / 2; ++kp) {
+                    const f2 *hk = hc + kp * kSG * (kSGS / 2);
+                    const f2 dd = f2_mul(f2_tree8(hk[0], hk[4], hk[8], hk[12], hk[16], hk[20], hk[24], hk[28]), s64);
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        const float d = e ? f2_hi(dd) : f2_lo(dd);
+                        const int ox = ox0 + 2 * kp + e, cx = xr + ox;
+                        const bool ok = ox <= hs && (unsigned)cx <= (unsigned)(W - 8) && (ox | oy) != 0 && d <= tau;
+                        if (ok) {
+                            ++kept;
+                            if (d < bd[L - 1]) insert_sorted<L>(bd, bi, d, (yr + oy) * W + cx);
+                        }
                     }
                 }
             }

@@ -30,6 +30,59 @@ __device__ __forceinline__ float sqd(float a, float b)
     return __fmul_rn(e, e);
 }
 
+// ---- packed FP32x2 arithmetic (two IEEE FP32 operations per instruction,
+// each lane rounded exactly as the scalar _rn operation) ----------------------
+struct f2 {
+    unsigned long long v;
+};
+__device__ __forceinline__ f2 f2_pack(float lo, float hi)
+{
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ float f2_lo(f2 a)
+{
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a.v));
+    return lo;
+}
+__device__ __forceinline__ float f2_hi(f2 a)
+{
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a.v));
+    return hi;
+}
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b)
+{
+    f2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ f2 f2_sub(f2 a, f2 b)
+{
+    f2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b)
+{
+    f2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ f2 f2_sqd(f2 a, f2 b)
+{
+    const f2 e = f2_sub(a, b);
+    return f2_mul(e, e);
+}
+__device__ __forceinline__ f2 f2_tree8(f2 a0, f2 a1, f2 a2, f2 a3, f2 a4, f2 a5, f2 a6, f2 a7)
+{
+    const f2 t0 = f2_add(f2_add(a0, a1), a2);
+    const f2 t1 = f2_add(f2_add(a3, a4), a5);
+    return f2_add(f2_add(t0, t1), f2_add(a6, a7));
+}
+
 // ||P - Q||^2 for P = ref (row-major registers), Q read through q(i, j).
 template <typename Q>
 __device__ __forceinline__ float canon_d64(const float (&ref)[64], Q q)
