@@ -20,15 +20,17 @@
 // shared-memory num window first (one global add per window pixel instead of
 // one per contribution).  A warp filters one group at a time (in the first
 // pass, two groups of at most 16 patches at once): lane k owns patch k and
-// computes its 8x8 DCT in registers with an even/odd fast DCT; the group
-// passes through a per-warp transpose buffer (rows of 65 floats, conflict-free
-// both ways) so that, for the group transform, each lane owns two coefficient
-// positions across all patches and runs the Walsh-Hadamard butterflies in
-// registers; the inverse goes back the same way, and the warp then aggregates
-// patch by patch with its lanes spread over the 64 pixels.
+// computes its 8x8 DCT with an even/odd fast DCT in two passes through its
+// row of a per-warp transpose buffer (rows of 65 floats, conflict-free both
+// ways), two 1D transforms per packed FP32x2 instruction; for the group
+// transform each lane owns two coefficient positions across all patches and
+// runs the Walsh-Hadamard butterflies for both in packed registers; the
+// inverse goes back the same way, and the warp then aggregates patch by patch
+// with its lanes spread over the 64 pixels.
 #include <cmath>
 
 #include "common.cuh"
+#include "f32x2.cuh"
 
 namespace dn {
 
@@ -101,28 +103,65 @@ __device__ __forceinline__ void idct8(float (&v)[NV], const DctK &K)
     v[O + 4 * S] = e3 - o3;
 }
 
-template <int I>
-__device__ __forceinline__ void dct2d_rows_cols(float (&v)[64], const DctK &K)
+// ---- packed versions: two independent 8-point transforms per instruction ----
+
+// The DCT constants broadcast to both lanes (and negated where subtracted).
+struct DctK2 {
+    f2 h1, h2, h3, h5, h6, h7, r8, nh1, nh2, nh5, nh7;
+};
+
+__device__ __forceinline__ DctK2 pack_dct(const DctK &K)
 {
-    if constexpr (I < 8) {
-        dct8<I * 8, 1>(v, K);
-        dct2d_rows_cols<I + 1>(v, K);
-    } else if constexpr (I < 16) {
-        dct8<I - 8, 8>(v, K);
-        dct2d_rows_cols<I + 1>(v, K);
-    }
+    DctK2 P;
+    P.h1 = f2_pack(K.h1, K.h1);
+    P.h2 = f2_pack(K.h2, K.h2);
+    P.h3 = f2_pack(K.h3, K.h3);
+    P.h5 = f2_pack(K.h5, K.h5);
+    P.h6 = f2_pack(K.h6, K.h6);
+    P.h7 = f2_pack(K.h7, K.h7);
+    P.r8 = f2_pack(K.r8, K.r8);
+    P.nh1 = f2_pack(-K.h1, -K.h1);
+    P.nh2 = f2_pack(-K.h2, -K.h2);
+    P.nh5 = f2_pack(-K.h5, -K.h5);
+    P.nh7 = f2_pack(-K.h7, -K.h7);
+    return P;
 }
 
-template <int I>
-__device__ __forceinline__ void idct2d_cols_rows(float (&v)[64], const DctK &K)
+// dct8 / idct8 with the same operations, on two vectors at once.
+__device__ __forceinline__ void dct8_2(f2 (&v)[8], const DctK2 &K)
 {
-    if constexpr (I < 8) {
-        idct8<I, 8>(v, K);
-        idct2d_cols_rows<I + 1>(v, K);
-    } else if constexpr (I < 16) {
-        idct8<(I - 8) * 8, 1>(v, K);
-        idct2d_cols_rows<I + 1>(v, K);
-    }
+    const f2 s0 = f2_add(v[0], v[7]), d0 = f2_sub(v[0], v[7]);
+    const f2 s1 = f2_add(v[1], v[6]), d1 = f2_sub(v[1], v[6]);
+    const f2 s2 = f2_add(v[2], v[5]), d2 = f2_sub(v[2], v[5]);
+    const f2 s3 = f2_add(v[3], v[4]), d3 = f2_sub(v[3], v[4]);
+    const f2 e0 = f2_add(s0, s3), e1 = f2_add(s1, s2), f0 = f2_sub(s0, s3), f1 = f2_sub(s1, s2);
+    v[0] = f2_mul(K.r8, f2_add(e0, e1));
+    v[4] = f2_mul(K.r8, f2_sub(e0, e1));
+    v[2] = f2_fma(K.h2, f0, f2_mul(K.h6, f1));
+    v[6] = f2_fma(K.h6, f0, f2_mul(K.nh2, f1));
+    v[1] = f2_fma(K.h1, d0, f2_fma(K.h3, d1, f2_fma(K.h5, d2, f2_mul(K.h7, d3))));
+    v[3] = f2_fma(K.h3, d0, f2_fma(K.nh7, d1, f2_fma(K.nh1, d2, f2_mul(K.nh5, d3))));
+    v[5] = f2_fma(K.h5, d0, f2_fma(K.nh1, d1, f2_fma(K.h7, d2, f2_mul(K.h3, d3))));
+    v[7] = f2_fma(K.h7, d0, f2_fma(K.nh5, d1, f2_fma(K.h3, d2, f2_mul(K.nh1, d3))));
+}
+
+__device__ __forceinline__ void idct8_2(f2 (&v)[8], const DctK2 &K)
+{
+    const f2 a = f2_mul(K.r8, f2_add(v[0], v[4])), b = f2_mul(K.r8, f2_sub(v[0], v[4]));
+    const f2 p = f2_fma(K.h2, v[2], f2_mul(K.h6, v[6])), q = f2_fma(K.h6, v[2], f2_mul(K.nh2, v[6]));
+    const f2 e0 = f2_add(a, p), e3 = f2_sub(a, p), e1 = f2_add(b, q), e2 = f2_sub(b, q);
+    const f2 o0 = f2_fma(K.h1, v[1], f2_fma(K.h3, v[3], f2_fma(K.h5, v[5], f2_mul(K.h7, v[7]))));
+    const f2 o1 = f2_fma(K.h3, v[1], f2_fma(K.nh7, v[3], f2_fma(K.nh1, v[5], f2_mul(K.nh5, v[7]))));
+    const f2 o2 = f2_fma(K.h5, v[1], f2_fma(K.nh1, v[3], f2_fma(K.h7, v[5], f2_mul(K.h3, v[7]))));
+    const f2 o3 = f2_fma(K.h7, v[1], f2_fma(K.nh5, v[3], f2_fma(K.h3, v[5], f2_mul(K.nh1, v[7]))));
+    v[0] = f2_add(e0, o0);
+    v[7] = f2_sub(e0, o0);
+    v[1] = f2_add(e1, o1);
+    v[6] = f2_sub(e1, o1);
+    v[2] = f2_add(e2, o2);
+    v[5] = f2_sub(e2, o2);
+    v[3] = f2_add(e3, o3);
+    v[4] = f2_sub(e3, o3);
 }
 
 // ---- group transform along the patches (one coefficient column) -------------
@@ -155,79 +194,114 @@ __device__ __forceinline__ float sqrt_n()
 // B^2 / (B^2 + N s2)) and the exact power-of-two factor 1/N is applied to the
 // aggregation weight of the estimate instead.
 
-// Hard threshold of coefficient column `col` of an n-patch group in T.
 template <int N>
-__device__ __forceinline__ int hard_col(float *T, int col, float thr)
+__device__ __forceinline__ void fwht2(f2 (&v)[N])
 {
-    float v[N];
 #pragma unroll
-    for (int k = 0; k < N; ++k) v[k] = T[k * kTS + col];
-    fwht<N>(v);
+    for (int h = 1; h < N; h <<= 1)
+#pragma unroll
+        for (int i = 0; i < N; i += 2 * h)
+#pragma unroll
+            for (int j = i; j < i + h; ++j) {
+                const f2 x = v[j], y = v[j + h];
+                v[j] = f2_add(x, y);
+                v[j + h] = f2_sub(x, y);
+            }
+}
+
+// The lane's two coefficient columns (lane, lane + 32) of rows [0, N) of T,
+// packed: column lane in the low half, column lane + 32 in the high half.
+template <int N>
+__device__ __forceinline__ void load_cols(const float *T, int lane, f2 (&v)[N])
+{
+#pragma unroll
+    for (int k = 0; k < N; ++k) v[k] = f2_pack(T[k * kTS + lane], T[k * kTS + lane + 32]);
+}
+
+template <int N>
+__device__ __forceinline__ void store_cols(float *T, int lane, const f2 (&v)[N])
+{
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        T[k * kTS + lane] = f2_lo(v[k]);
+        T[k * kTS + lane + 32] = f2_hi(v[k]);
+    }
+}
+
+// Hard threshold of the lane's two coefficient columns of an N-patch group in
+// T; returns the number of kept coefficients.
+template <int N>
+__device__ __forceinline__ int hard_cols(float *T, int lane, float thr)
+{
+    f2 v[N];
+    load_cols<N>(T, lane, v);
+    fwht2<N>(v);
     const float thr_n = thr * sqrt_n<N>();
     int cnt = 0;
 #pragma unroll
     for (int k = 0; k < N; ++k) {
-        const bool keep = fabsf(v[k]) > thr_n;
-        cnt += keep ? 1 : 0;
-        v[k] = keep ? v[k] : 0.0f;
+        const float lo = f2_lo(v[k]), hi = f2_hi(v[k]);
+        const bool klo = fabsf(lo) > thr_n, khi = fabsf(hi) > thr_n;
+        cnt += (klo ? 1 : 0) + (khi ? 1 : 0);
+        v[k] = f2_pack(klo ? lo : 0.0f, khi ? hi : 0.0f);
     }
-    fwht<N>(v);
-#pragma unroll
-    for (int k = 0; k < N; ++k) T[k * kTS + col] = v[k];
+    fwht2<N>(v);
+    store_cols<N>(T, lane, v);
     return cnt;
 }
 
-// Wiener gains of column `col` of the basic-estimate group in T, kept in
-// registers (om); returns their sum of squares.
+// Wiener gains of the lane's two coefficient columns of the basic-estimate
+// group in T, kept in registers (om); returns their sum of squares.
 template <int N>
-__device__ __forceinline__ float wiener_gains(const float *T, int col, float s2, float (&om)[N])
+__device__ __forceinline__ float wiener_gains(const float *T, int lane, float s2, f2 (&om)[N])
 {
-    float v[N];
-#pragma unroll
-    for (int k = 0; k < N; ++k) v[k] = T[k * kTS + col];
-    fwht<N>(v);
+    f2 v[N];
+    load_cols<N>(T, lane, v);
+    fwht2<N>(v);
     const float s2n = s2 * (float)N;
-    float wsq = 0.0f;
+    const f2 s2n2 = f2_pack(s2n, s2n);
+    f2 wsq = f2_pack(0.0f, 0.0f);
 #pragma unroll
     for (int k = 0; k < N; ++k) {
-        const float b2 = v[k] * v[k];
-        om[k] = __fdividef(b2, b2 + s2n);  // b2 + s2n >= sigma^2 > 0
-        wsq = fmaf(om[k], om[k], wsq);
+        const f2 b2 = f2_mul(v[k], v[k]);
+        const f2 den = f2_add(b2, s2n2);  // >= sigma^2 > 0
+        om[k] = f2_pack(__fdividef(f2_lo(b2), f2_lo(den)), __fdividef(f2_hi(b2), f2_hi(den)));
+        wsq = f2_fma(om[k], om[k], wsq);
     }
-    return wsq;
+    return f2_lo(wsq) + f2_hi(wsq);
 }
 
-// Applies the gains to column `col` of the noisy group in T (in place).
+// Applies the gains to the lane's two coefficient columns of the noisy group
+// in T (in place), one column at a time (a packed pair of columns would keep
+// 128 registers live next to the gains).
 template <int N>
-__device__ __forceinline__ void wiener_apply(float *T, int col, const float (&om)[N])
+__device__ __forceinline__ void wiener_apply(float *T, int lane, const f2 (&om)[N])
 {
-    float v[N];
 #pragma unroll
-    for (int k = 0; k < N; ++k) v[k] = T[k * kTS + col];
-    fwht<N>(v);
+    for (int h = 0; h < 2; ++h) {
+        const int col = lane + 32 * h;
+        float v[N];
 #pragma unroll
-    for (int k = 0; k < N; ++k) v[k] *= om[k];
-    fwht<N>(v);
+        for (int k = 0; k < N; ++k) v[k] = T[k * kTS + col];
+        fwht<N>(v);
 #pragma unroll
-    for (int k = 0; k < N; ++k) T[k * kTS + col] = v[k];
+        for (int k = 0; k < N; ++k) v[k] *= h ? f2_hi(om[k]) : f2_lo(om[k]);
+        fwht<N>(v);
+#pragma unroll
+        for (int k = 0; k < N; ++k) T[k * kTS + col] = v[k];
+    }
 }
 
 __device__ __forceinline__ int hard_columns(float *T, int n, int lane, float thr)
 {
-    int cnt = 0;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int col = lane + 32 * h;
-        switch (n) {
-            case 1: cnt += hard_col<1>(T, col, thr); break;
-            case 2: cnt += hard_col<2>(T, col, thr); break;
-            case 4: cnt += hard_col<4>(T, col, thr); break;
-            case 8: cnt += hard_col<8>(T, col, thr); break;
-            case 16: cnt += hard_col<16>(T, col, thr); break;
-            default: cnt += hard_col<32>(T, col, thr); break;
-        }
+    switch (n) {
+        case 1: return hard_cols<1>(T, lane, thr);
+        case 2: return hard_cols<2>(T, lane, thr);
+        case 4: return hard_cols<4>(T, lane, thr);
+        case 8: return hard_cols<8>(T, lane, thr);
+        case 16: return hard_cols<16>(T, lane, thr);
+        default: return hard_cols<32>(T, lane, thr);
     }
-    return cnt;
 }
 
 // ---- exact aggregation ---------------------------------------------------------
@@ -321,46 +395,50 @@ __device__ __forceinline__ bool in_window(const Window &win, int py, int px)
     return py >= win.Y0 && py + 8 <= win.Y0 + win.RH && px >= win.X0 && px + 8 <= win.X0 + win.RW;
 }
 
-// Lane-per-row forward 2D DCT of the valid lanes' patches (row `lane` of T),
-// read from the shared image window, or from global memory when some patch
-// of the batch lies outside it (only possible for match lists not produced by
-// the matcher of this library).
-__device__ __forceinline__ void dct_rows(float *T, const Window &win, const float *wimg, const float *gimg, int W,
-                                         bool valid, int lane, int py, int px, const DctK &K)
+// Forward 2D DCT of the valid lanes' patches into row `lane` of T, in two
+// passes with two 1D transforms per packed instruction: patch rows (r, r+1)
+// from the shared image window (or from global memory when some patch of the
+// batch lies outside it, only possible for match lists not produced by the
+// matcher of this library) into T, then column pairs (j, j+1) of T in place.
+__device__ __forceinline__ void dct_2pass(float *T, const Window &win, const float *wimg, const float *gimg, int W,
+                                          bool valid, int lane, int py, int px, const DctK2 &K)
 {
     const bool all_in = __all_sync(0xffffffffu, !valid || in_window(win, py, px));
     if (valid) {
         const float *src = all_in ? wimg + (py - win.Y0) * win.RW + (px - win.X0) : gimg + (size_t)py * W + px;
         const int stride = all_in ? win.RW : W;
-        float v[64];
+        float *row = T + lane * kTS;
 #pragma unroll
-        for (int r = 0; r < 8; ++r)
+        for (int r = 0; r < 8; r += 2) {
+            f2 x[8];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) v[r * 8 + j] = src[r * stride + j];
-        dct2d_rows_cols<0>(v, K);
+            for (int j = 0; j < 8; ++j) x[j] = f2_pack(src[r * stride + j], src[(r + 1) * stride + j]);
+            dct8_2(x, K);
 #pragma unroll
-        for (int p = 0; p < 64; ++p) T[lane * kTS + p] = v[p];
+            for (int j = 0; j < 8; ++j) {
+                row[r * 8 + j] = f2_lo(x[j]);
+                row[(r + 1) * 8 + j] = f2_hi(x[j]);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 8; j += 2) {
+            f2 x[8];
+#pragma unroll
+            for (int r = 0; r < 8; ++r) x[r] = f2_pack(row[r * 8 + j], row[r * 8 + j + 1]);
+            dct8_2(x, K);
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                row[r * 8 + j] = f2_lo(x[r]);
+                row[r * 8 + j + 1] = f2_hi(x[r]);
+            }
+        }
     }
 }
 
-// Lane-per-row inverse 2D DCT of row `lane` of T, in place.
-__device__ __forceinline__ void idct_rows(float *T, bool valid, int lane, const DctK &K)
-{
-    if (valid) {
-        float v[64];
-#pragma unroll
-        for (int p = 0; p < 64; ++p) v[p] = T[lane * kTS + p];
-        idct2d_cols_rows<0>(v, K);
-#pragma unroll
-        for (int p = 0; p < 64; ++p) T[lane * kTS + p] = v[p];
-    }
-}
-
-// Two-pass variant of dct_rows with a small register footprint (used while
-// the Wiener gains occupy registers): 1D DCTs of the patch rows from the
-// window into row `lane` of T, then 1D DCTs of its columns in place.
-__device__ __forceinline__ void dct_rows_2pass(float *T, const Window &win, const float *wimg, const float *gimg,
-                                               int W, bool valid, int lane, int py, int px, const DctK &K)
+// Scalar variant of dct_2pass with the smallest register footprint, for the
+// noisy patches of the Wiener pass (the gains occupy 64 registers then).
+__device__ __forceinline__ void dct_2pass_scalar(float *T, const Window &win, const float *wimg, const float *gimg,
+                                                 int W, bool valid, int lane, int py, int px, const DctK &K)
 {
     const bool all_in = __all_sync(0xffffffffu, !valid || in_window(win, py, px));
     if (valid) {
@@ -388,22 +466,53 @@ __device__ __forceinline__ void dct_rows_2pass(float *T, const Window &win, cons
     }
 }
 
+// Inverse 2D DCT of row `lane` of T in place: column pairs, then row pairs.
+__device__ __forceinline__ void idct_2pass(float *T, bool valid, int lane, const DctK2 &K)
+{
+    if (valid) {
+        float *row = T + lane * kTS;
+#pragma unroll
+        for (int j = 0; j < 8; j += 2) {
+            f2 x[8];
+#pragma unroll
+            for (int r = 0; r < 8; ++r) x[r] = f2_pack(row[r * 8 + j], row[r * 8 + j + 1]);
+            idct8_2(x, K);
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                row[r * 8 + j] = f2_lo(x[r]);
+                row[r * 8 + j + 1] = f2_hi(x[r]);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < 8; r += 2) {
+            f2 x[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) x[j] = f2_pack(row[r * 8 + j], row[(r + 1) * 8 + j]);
+            idct8_2(x, K);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                row[r * 8 + j] = f2_lo(x[j]);
+                row[(r + 1) * 8 + j] = f2_hi(x[j]);
+            }
+        }
+    }
+}
+
 // Wiener transform of one group of N patches (rows [0, N) of T): gains from
 // the basic-estimate group (kept in registers), applied to the noisy group;
 // T is left holding the filtered spectra of the noisy patches.
 template <int N>
 __device__ __forceinline__ float wiener_group(const FilterArgs &a, const Window &win, float *T, size_t cbase,
-                                              int lane, int py, int px, float s2)
+                                              int lane, int py, int px, float s2, const DctK2 &K)
 {
-    dct_rows(T, win, win.basic, a.basic + cbase, a.W, lane < N, lane, py, px, a.k);
+    dct_2pass(T, win, win.basic, a.basic + cbase, a.W, lane < N, lane, py, px, K);
     __syncwarp();
-    float om0[N], om1[N];
-    const float wsq = wiener_gains<N>(T, lane, s2, om0) + wiener_gains<N>(T, lane + 32, s2, om1);
+    f2 om[N];
+    const float wsq = wiener_gains<N>(T, lane, s2, om);
     __syncwarp();
-    dct_rows_2pass(T, win, win.img, a.img + cbase, a.W, lane < N, lane, py, px, a.k);
+    dct_2pass_scalar(T, win, win.img, a.img + cbase, a.W, lane < N, lane, py, px, a.k);
     __syncwarp();
-    wiener_apply<N>(T, lane, om0);
-    wiener_apply<N>(T, lane + 32, om1);
+    wiener_apply<N>(T, lane, om);
     return wsq;
 }
 
@@ -449,7 +558,7 @@ __device__ __forceinline__ void hard_batch(const FilterArgs &a, const Window &wi
                                            int nA, int nB, int lane, int py, int px, const float (&ka)[2])
 {
     const bool valid = lane < nA || (lane >= 16 && lane < 16 + nB);
-    dct_rows(T, win, win.img, a.img + cbase, a.W, valid, lane, py, px, a.k);
+    dct_2pass(T, win, win.img, a.img + cbase, a.W, valid, lane, py, px, pack_dct(a.k));
     __syncwarp();
     const float thr = a.lambda * sig;
     const int nharA = __reduce_add_sync(0xffffffffu, hard_columns(T, nA, lane, thr));
@@ -458,7 +567,7 @@ __device__ __forceinline__ void hard_batch(const FilterArgs &a, const Window &wi
     const float wA = nharA > 0 ? 1.0f / (float)nharA : sig * sig;
     const float wB = nharB > 0 ? 1.0f / (float)nharB : sig * sig;
     __syncwarp();
-    idct_rows(T, valid, lane, a.k);
+    idct_2pass(T, valid, lane, pack_dct(a.k));
     __syncwarp();
     aggregate(a, win, T, cbase, 0, nA, lane, py, px, wA, ka);
     if (nB) aggregate(a, win, T, cbase, 16, nB, lane, py, px, wB, ka);
@@ -472,18 +581,18 @@ __device__ __forceinline__ void wiener_one(const FilterArgs &a, const Window &wi
     const float s2 = sig * sig;
     float wsq;
     switch (n) {
-        case 1: wsq = wiener_group<1>(a, win, T, cbase, lane, py, px, s2); break;
-        case 2: wsq = wiener_group<2>(a, win, T, cbase, lane, py, px, s2); break;
-        case 4: wsq = wiener_group<4>(a, win, T, cbase, lane, py, px, s2); break;
-        case 8: wsq = wiener_group<8>(a, win, T, cbase, lane, py, px, s2); break;
-        case 16: wsq = wiener_group<16>(a, win, T, cbase, lane, py, px, s2); break;
-        default: wsq = wiener_group<32>(a, win, T, cbase, lane, py, px, s2); break;
+        case 1: wsq = wiener_group<1>(a, win, T, cbase, lane, py, px, s2, pack_dct(a.k)); break;
+        case 2: wsq = wiener_group<2>(a, win, T, cbase, lane, py, px, s2, pack_dct(a.k)); break;
+        case 4: wsq = wiener_group<4>(a, win, T, cbase, lane, py, px, s2, pack_dct(a.k)); break;
+        case 8: wsq = wiener_group<8>(a, win, T, cbase, lane, py, px, s2, pack_dct(a.k)); break;
+        case 16: wsq = wiener_group<16>(a, win, T, cbase, lane, py, px, s2, pack_dct(a.k)); break;
+        default: wsq = wiener_group<32>(a, win, T, cbase, lane, py, px, s2, pack_dct(a.k)); break;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) wsq += __shfl_xor_sync(0xffffffffu, wsq, o);
     const float w = wsq > 0.0f ? 1.0f / wsq : s2;  // 1/(sigma^2 sum w^2) or 1, times sigma^2
     __syncwarp();
-    idct_rows(T, lane < n, lane, a.k);
+    idct_2pass(T, lane < n, lane, pack_dct(a.k));
     __syncwarp();
     aggregate(a, win, T, cbase, 0, n, lane, py, px, w, ka);
     __syncwarp();

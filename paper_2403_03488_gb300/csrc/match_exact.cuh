@@ -13,6 +13,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "f32x2.cuh"
 
 namespace dn {
 namespace {
@@ -30,47 +31,6 @@ __device__ __forceinline__ float sqd(float a, float b)
     return __fmul_rn(e, e);
 }
 
-// ---- packed FP32x2 arithmetic (two IEEE FP32 operations per instruction,
-// each lane rounded exactly as the scalar _rn operation) ----------------------
-struct f2 {
-    unsigned long long v;
-};
-__device__ __forceinline__ f2 f2_pack(float lo, float hi)
-{
-    f2 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(lo), "f"(hi));
-    return r;
-}
-__device__ __forceinline__ float f2_lo(f2 a)
-{
-    float lo, hi;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a.v));
-    return lo;
-}
-__device__ __forceinline__ float f2_hi(f2 a)
-{
-    float lo, hi;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a.v));
-    return hi;
-}
-__device__ __forceinline__ f2 f2_add(f2 a, f2 b)
-{
-    f2 r;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
-    return r;
-}
-__device__ __forceinline__ f2 f2_sub(f2 a, f2 b)
-{
-    f2 r;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
-    return r;
-}
-__device__ __forceinline__ f2 f2_mul(f2 a, f2 b)
-{
-    f2 r;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
-    return r;
-}
 __device__ __forceinline__ f2 f2_sqd(f2 a, f2 b)
 {
     const f2 e = f2_sub(a, b);
