@@ -676,6 +676,17 @@ __global__ void __launch_bounds__(512) k_filter(FilterArgs a, int TR, int RH, in
     }
 }
 
+// A fixed-point sum (main + hi 2^32, in units of 2^-36) as an FP32 value in
+// the same units, from 32-bit halves (the int64 -> FP64 path would run on the
+// narrow FP64 unit): relative error <= 2^-23.
+__device__ __forceinline__ float fixed_to_float(long long main, long long hi)
+{
+    const float m = fmaf((float)(int)(main >> 32), 4294967296.0f, (float)(unsigned)(main & 0xFFFFFFFFll));
+    if (hi == 0) return m;
+    const float h = fmaf((float)(int)(hi >> 32), 4294967296.0f, (float)(unsigned)(hi & 0xFFFFFFFFll));
+    return fmaf(h, 4294967296.0f, m);
+}
+
 // out = num / den, den(y, x) = sum_{i,j} k_i k_j W(y - i, x - j) over patch
 // positions, evaluated separably in FP32 (fixed order, so reproducible) from
 // the exact weight sums.  One CTA per 32 x 32 output tile of one plane.
@@ -699,10 +710,7 @@ __global__ void __launch_bounds__(256) k_normalize(const long long *num, const l
         float v = 0.0f;
         if (y >= 0 && y < H && x >= 0 && x < W) {
             const size_t i = base + (size_t)y * W + x;
-            double d = (double)wsum[i];
-            const long long h = wsum_hi[i];
-            if (h != 0) d += (double)h * 4294967296.0;
-            v = (float)d;
+            v = fixed_to_float(wsum[i], wsum_hi[i]);
         }
         sw[r][cc] = v;
     }
@@ -723,10 +731,7 @@ __global__ void __launch_bounds__(256) k_normalize(const long long *num, const l
 #pragma unroll
         for (int i = 0; i < 8; ++i) den = fmaf(kw.k[i], sr[r + 7 - i][cc], den);
         const size_t o = base + (size_t)y * W + x;
-        double nu = (double)num[o];
-        const long long h = num_hi[o];
-        if (h != 0) nu += (double)h * 4294967296.0;
-        out[o] = (float)(nu / (double)den);  // the 2^36 scale cancels
+        out[o] = fixed_to_float(num[o], num_hi[o]) / den;  // the 2^36 scale cancels
     }
 }
 
