@@ -110,20 +110,26 @@ struct DctK2 {
     f2 h1, h2, h3, h5, h6, h7, r8, nh1, nh2, nh5, nh7;
 };
 
-__device__ __forceinline__ DctK2 pack_dct(const DctK &K)
+// cos(k pi / 16) / 2 and 1/sqrt(8) rounded to FP32 (the values make_dct_constants
+// derives on the host); as compile-time literals the packed pairs can be
+// rematerialised instead of occupying registers.
+constexpr float kH1 = 0.490392625f, kH2 = 0.461939752f, kH3 = 0.415734798f, kH5 = 0.277785122f,
+                kH6 = 0.191341713f, kH7 = 0.0975451618f, kR8 = 0.353553385f;
+
+__device__ __forceinline__ DctK2 pack_dct()
 {
     DctK2 P;
-    P.h1 = f2_pack(K.h1, K.h1);
-    P.h2 = f2_pack(K.h2, K.h2);
-    P.h3 = f2_pack(K.h3, K.h3);
-    P.h5 = f2_pack(K.h5, K.h5);
-    P.h6 = f2_pack(K.h6, K.h6);
-    P.h7 = f2_pack(K.h7, K.h7);
-    P.r8 = f2_pack(K.r8, K.r8);
-    P.nh1 = f2_pack(-K.h1, -K.h1);
-    P.nh2 = f2_pack(-K.h2, -K.h2);
-    P.nh5 = f2_pack(-K.h5, -K.h5);
-    P.nh7 = f2_pack(-K.h7, -K.h7);
+    P.h1 = f2_pack(kH1, kH1);
+    P.h2 = f2_pack(kH2, kH2);
+    P.h3 = f2_pack(kH3, kH3);
+    P.h5 = f2_pack(kH5, kH5);
+    P.h6 = f2_pack(kH6, kH6);
+    P.h7 = f2_pack(kH7, kH7);
+    P.r8 = f2_pack(kR8, kR8);
+    P.nh1 = f2_pack(-kH1, -kH1);
+    P.nh2 = f2_pack(-kH2, -kH2);
+    P.nh5 = f2_pack(-kH5, -kH5);
+    P.nh7 = f2_pack(-kH7, -kH7);
     return P;
 }
 
@@ -558,7 +564,7 @@ __device__ __forceinline__ void hard_batch(const FilterArgs &a, const Window &wi
                                            int nA, int nB, int lane, int py, int px, const float (&ka)[2])
 {
     const bool valid = lane < nA || (lane >= 16 && lane < 16 + nB);
-    dct_2pass(T, win, win.img, a.img + cbase, a.W, valid, lane, py, px, pack_dct(a.k));
+    dct_2pass(T, win, win.img, a.img + cbase, a.W, valid, lane, py, px, pack_dct());
     __syncwarp();
     const float thr = a.lambda * sig;
     const int nharA = __reduce_add_sync(0xffffffffu, hard_columns(T, nA, lane, thr));
@@ -567,7 +573,7 @@ __device__ __forceinline__ void hard_batch(const FilterArgs &a, const Window &wi
     const float wA = nharA > 0 ? 1.0f / (float)nharA : sig * sig;
     const float wB = nharB > 0 ? 1.0f / (float)nharB : sig * sig;
     __syncwarp();
-    idct_2pass(T, valid, lane, pack_dct(a.k));
+    idct_2pass(T, valid, lane, pack_dct());
     __syncwarp();
     aggregate(a, win, T, cbase, 0, nA, lane, py, px, wA, ka);
     if (nB) aggregate(a, win, T, cbase, 16, nB, lane, py, px, wB, ka);
@@ -581,18 +587,18 @@ __device__ __forceinline__ void wiener_one(const FilterArgs &a, const Window &wi
     const float s2 = sig * sig;
     float wsq;
     switch (n) {
-        case 1: wsq = wiener_group<1>(a, win, T, cbase, lane, py, px, s2, pack_dct(a.k)); break;
-        case 2: wsq = wiener_group<2>(a, win, T, cbase, lane, py, px, s2, pack_dct(a.k)); break;
-        case 4: wsq = wiener_group<4>(a, win, T, cbase, lane, py, px, s2, pack_dct(a.k)); break;
-        case 8: wsq = wiener_group<8>(a, win, T, cbase, lane, py, px, s2, pack_dct(a.k)); break;
-        case 16: wsq = wiener_group<16>(a, win, T, cbase, lane, py, px, s2, pack_dct(a.k)); break;
-        default: wsq = wiener_group<32>(a, win, T, cbase, lane, py, px, s2, pack_dct(a.k)); break;
+        case 1: wsq = wiener_group<1>(a, win, T, cbase, lane, py, px, s2, pack_dct()); break;
+        case 2: wsq = wiener_group<2>(a, win, T, cbase, lane, py, px, s2, pack_dct()); break;
+        case 4: wsq = wiener_group<4>(a, win, T, cbase, lane, py, px, s2, pack_dct()); break;
+        case 8: wsq = wiener_group<8>(a, win, T, cbase, lane, py, px, s2, pack_dct()); break;
+        case 16: wsq = wiener_group<16>(a, win, T, cbase, lane, py, px, s2, pack_dct()); break;
+        default: wsq = wiener_group<32>(a, win, T, cbase, lane, py, px, s2, pack_dct()); break;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) wsq += __shfl_xor_sync(0xffffffffu, wsq, o);
     const float w = wsq > 0.0f ? 1.0f / wsq : s2;  // 1/(sigma^2 sum w^2) or 1, times sigma^2
     __syncwarp();
-    idct_2pass(T, lane < n, lane, pack_dct(a.k));
+    idct_2pass(T, lane < n, lane, pack_dct());
     __syncwarp();
     aggregate(a, win, T, cbase, 0, n, lane, py, px, w, ka);
     __syncwarp();
@@ -737,15 +743,14 @@ __global__ void __launch_bounds__(256) k_normalize(const long long *num, const l
 
 DctK make_dct_constants()
 {
-    const double pi = 3.14159265358979323846;
     DctK k;
-    k.h1 = (float)(0.5 * std::cos(1 * pi / 16));
-    k.h2 = (float)(0.5 * std::cos(2 * pi / 16));
-    k.h3 = (float)(0.5 * std::cos(3 * pi / 16));
-    k.h5 = (float)(0.5 * std::cos(5 * pi / 16));
-    k.h6 = (float)(0.5 * std::cos(6 * pi / 16));
-    k.h7 = (float)(0.5 * std::cos(7 * pi / 16));
-    k.r8 = (float)(1.0 / std::sqrt(8.0));
+    k.h1 = kH1;
+    k.h2 = kH2;
+    k.h3 = kH3;
+    k.h5 = kH5;
+    k.h6 = kH6;
+    k.h7 = kH7;
+    k.r8 = kR8;
     return k;
 }
 
