@@ -135,7 +135,11 @@ __global__ void __launch_bounds__(kS3T, 4) k_match3(Match3Args a)
                 }
             }
             __syncthreads();  // one barrier per chunk: the buffers alternate
-            if (yok) {
+            // offsets ox0 + k inside the window (|ox| <= hs), the image and not the reference itself
+            const int klo = max(0, -xr - ox0), khi = min(kSK - 1, min(hs, W - 8 - xr) - ox0);
+            unsigned valid = (yok && khi >= klo) ? ((2u << (khi - klo)) - 1u) << klo : 0u;
+            if (oy == 0 && ox0 <= 0 && ox0 + kSK > 0) valid &= ~(1u << (-ox0));
+            if (valid) {
                 const f2 *hc = reinterpret_cast<const f2 *>(hbuf + (bc >> 2) * kSGS + 24 * br + 2 * (bc & 3));
                 const f2 s64 = f2_pack(0.015625f, 0.015625f);
 #pragma unroll
@@ -145,11 +149,9 @@ __global__ void __launch_bounds__(kS3T, 4) k_match3(Match3Args a)
 #pragma unroll
                     for (int e = 0; e < 2; ++e) {
                         const float d = e ? f2_hi(dd) : f2_lo(dd);
-                        const int ox = ox0 + 2 * kp + e, cx = xr + ox;
-                        const bool ok = ox <= hs && (unsigned)cx <= (unsigned)(W - 8) && (ox | oy) != 0 && d <= tau;
-                        if (ok) {
+                        if (((valid >> (2 * kp + e)) & 1u) && d <= tau) {
                             ++kept;
-                            if (d < bd[L - 1]) insert_sorted<L>(bd, bi, d, (yr + oy) * W + cx);
+                            if (d < bd[L - 1]) insert_sorted<L>(bd, bi, d, (yr + oy) * W + xr + ox0 + 2 * kp + e);
                         }
                     }
                 }
