@@ -310,6 +310,14 @@ def serving_replay(args):
                 "budget_gb": 60, "slots": 8,
                 "fp32_plain": {k: round(plain[k], 3) for k in keys}})
     out["saturated"] = bool(fast["served_mpix_s"] < 0.9 * fast["offered_mpix_s"])
+    if out["saturated"]:
+        # the same trace shape at 60 % of the served rate: latency without a growing queue
+        rate = args.serve_rate * 0.6 * fast["served_mpix_s"] / fast["offered_mpix_s"]
+        stable = serve.replay(rate=rate, n=args.serve_requests, side=(128, 2048),
+                              bm3d_precision=api.DN_BF16 if args.bm3d == "bf16" else api.DN_FP32,
+                              cnn_precision=api.DN_BF16 if args.cnn == "bf16" else api.DN_FP32, warm=False)
+        out["stable_load"] = {k: round(stable[k], 3) for k in keys}
+        out["stable_load"].update({"rate_per_s": round(rate, 1), "offered_mpix_s": round(stable["offered_mpix_s"], 1)})
     return out
 
 
