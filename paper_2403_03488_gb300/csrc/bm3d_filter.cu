@@ -344,6 +344,18 @@ __device__ __forceinline__ long long fix_fast(float c)
     return (long long)A * 8388608ll + Bq;
 }
 
+// fix_fast on the two lanes of a packed pair (same operations, so the same bits).
+__device__ __forceinline__ void fix_fast2(f2 c, long long &x0, long long &x1)
+{
+    const f2 M = f2_pack(12582912.0f, 12582912.0f);
+    const f2 t = f2_mul(c, f2_pack(8192.0f, 8192.0f));
+    const f2 ta = f2_add(t, M);
+    const f2 r = f2_sub(t, f2_sub(ta, M));
+    const f2 u = f2_fma(r, f2_pack(8388608.0f, 8388608.0f), M);
+    x0 = (long long)(__float_as_int(f2_lo(ta)) - 0x4B400000) * 8388608ll + (__float_as_int(f2_lo(u)) - 0x4B400000);
+    x1 = (long long)(__float_as_int(f2_hi(ta)) - 0x4B400000) * 8388608ll + (__float_as_int(f2_hi(u)) - 0x4B400000);
+}
+
 struct Fix {
     unsigned long long lo;  // main-plane part
     long long hi;           // high-word part (0 on the fast path)
@@ -537,23 +549,36 @@ __device__ __forceinline__ void aggregate(const FilterArgs &a, const Window &win
         atomicAdd(a.wsum + q, fw.lo);
         if (fw.hi != 0) atomicAdd(a.wsum_hi + q, (unsigned long long)fw.hi);
     }
-    const float wk0 = w * ka[0] * vs, wk1 = w * ka[1] * vs;
+    const f2 wk = f2_pack(w * ka[0] * vs, w * ka[1] * vs);
     const int i0 = lane >> 3, j = lane & 7;
 #pragma unroll 2
     for (int k = s; k < s + n; ++k) {
         const int yk = __shfl_sync(0xffffffffu, py, k), xk = __shfl_sync(0xffffffffu, px, k);
         const int ly0 = yk - win.Y0, lx0 = xk - win.X0;
         const bool inside = ly0 >= 0 && ly0 + 8 <= win.RH && lx0 >= 0 && lx0 + 8 <= win.RW;
+        // the lane's two pixels (rows i0 and i0 + 4 of the patch, column j)
+        const f2 c = f2_mul(wk, f2_pack(T[k * kTS + lane], T[k * kTS + lane + 32]));
+        Fix f[2];
+        if (fabsf(f2_lo(c)) < 512.0f && fabsf(f2_hi(c)) < 512.0f) {
+            long long x0, x1;
+            fix_fast2(c, x0, x1);
+            f[0].lo = (unsigned long long)x0;
+            f[1].lo = (unsigned long long)x1;
+            f[0].hi = f[1].hi = 0;
+        } else {
+            f[0] = to_fixed(f2_lo(c));
+            f[1] = to_fixed(f2_hi(c));
+        }
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int i = i0 + 4 * h;
-            const Fix fn = to_fixed((h ? wk1 : wk0) * T[k * kTS + lane + 32 * h]);
             if (inside) {
-                atomicAdd(win.num + (ly0 + i) * win.RS + lx0 + j, fn.lo);
+                atomicAdd(win.num + (ly0 + i) * win.RS + lx0 + j, f[h].lo);
             } else {
-                atomicAdd(a.num + cbase + (size_t)(yk + i) * a.W + xk + j, fn.lo);
+                atomicAdd(a.num + cbase + (size_t)(yk + i) * a.W + xk + j, f[h].lo);
             }
-            if (fn.hi != 0) atomicAdd(a.num_hi + cbase + (size_t)(yk + i) * a.W + xk + j, (unsigned long long)fn.hi);
+            if (f[h].hi != 0)
+                atomicAdd(a.num_hi + cbase + (size_t)(yk + i) * a.W + xk + j, (unsigned long long)f[h].hi);
         }
     }
 }
