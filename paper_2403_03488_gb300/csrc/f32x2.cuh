@@ -51,5 +51,12 @@ __device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c)
     return r;
 }
 
+// (a - b)^2 per lane, the product rounded separately (no contraction).
+__device__ __forceinline__ f2 f2_sqd(f2 a, f2 b)
+{
+    const f2 e = f2_sub(a, b);
+    return f2_mul(e, e);
+}
+
 }  // namespace
 }  // namespace dn

@@ -31,11 +31,6 @@ __device__ __forceinline__ float sqd(float a, float b)
     return __fmul_rn(e, e);
 }
 
-__device__ __forceinline__ f2 f2_sqd(f2 a, f2 b)
-{
-    const f2 e = f2_sub(a, b);
-    return f2_mul(e, e);
-}
 __device__ __forceinline__ f2 f2_tree8(f2 a0, f2 a1, f2 a2, f2 a3, f2 a4, f2 a5, f2 a6, f2 a7)
 {
     const f2 t0 = f2_add(f2_add(a0, a1), a2);

@@ -7,19 +7,23 @@
 //     w        = exp(-max(d2 - 2 sigma^2, 0) / h^2),
 // out_c(p) = sum_q w y_c(q) / sum_q w for every channel c.
 //
-// Design: offset-major box filtering.  A CTA owns a 32 x 8 output tile and
+// Design: offset-major box filtering.  A CTA owns a 32 x 16 output tile and
 // stages the reflected guide (tile + patch and search halos) and the other
-// channels in shared memory once.  For each offset it forms the squared
-// difference image over tile + patch halo, sums it vertically then
-// horizontally (2 * patch adds per pixel instead of patch^2), and each thread
-// folds its pixel's weight into register accumulators.
+// channels in shared memory once.  For each pair of horizontally adjacent
+// offsets (dx, dx + 1) it forms the two squared-difference images over tile +
+// patch halo in the two lanes of packed FP32x2 values, sums them vertically
+// then horizontally (2 * patch adds per pixel instead of patch^2; each sum in
+// the same sequential order as a scalar loop), and each thread folds its
+// pixel's two weights into register accumulators.  Threads map to rows and
+// columns of the difference image directly (no index division).
 #include "common.cuh"
+#include "f32x2.cuh"
 
 namespace dn {
 
 namespace {
 
-constexpr int kTX = 32, kTY = 8, kThreads = kTX * kTY;
+constexpr int kTX = 32, kTY = 16, kThreads = kTX * kTY;
 
 struct NlmArgs {
     const float *in;
@@ -46,10 +50,10 @@ __global__ void __launch_bounds__(kThreads) k_nlm(NlmArgs a)
     const int GW = kTX + 2 * r + 2 * hs, GH = kTY + 2 * r + 2 * hs;  // guide region
     const int DW = kTX + 2 * r, DH = kTY + 2 * r;                    // difference image
     const int VW = kTX + 2 * hs, VH = kTY + 2 * hs;                  // value regions (other channels)
-    float *S = sm;                    // [GH][GW]
-    float *D = S + GH * GW;           // [DH][DW]
-    float *V = D + DH * DW;           // [kTY][DW]
-    float *Y = V + kTY * DW;          // [C-1][VH][VW]
+    float *S = sm;                                                   // [GH][GW]
+    f2 *D = reinterpret_cast<f2 *>(S + ((GH * GW + 1) & ~1));        // [DH][DW] offset pairs
+    f2 *V = D + DH * DW;                                             // [kTY][DW]
+    float *Y = reinterpret_cast<float *>(V + kTY * DW);              // [C-1][VH][VW]
 
     const int b = blockIdx.z;
     const int X0 = blockIdx.x * kTX, Y0 = blockIdx.y * kTY;
@@ -73,36 +77,45 @@ __global__ void __launch_bounds__(kThreads) k_nlm(NlmArgs a)
     const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
     const int px = X0 + tx, py = Y0 + ty;
     const float two_s2 = a.two_s2[b], inv_h2 = a.inv_h2[b];
+    const f2 inv_np = f2_pack(a.inv_np, a.inv_np);
     float acc[3] = {0.0f, 0.0f, 0.0f};
     float wsum = 0.0f;
 
     for (int dy = -hs; dy <= hs; ++dy)
-        for (int dx = -hs; dx <= hs; ++dx) {
-            for (int i = threadIdx.x; i < DH * DW; i += kThreads) {
-                int yy = i / DW, xx = i - yy * DW;
-                float e = S[(yy + hs) * GW + xx + hs] - S[(yy + hs + dy) * GW + xx + hs + dx];
-                D[i] = e * e;
+        for (int dx = -hs; dx <= hs; dx += 2) {
+            // squared differences for offsets dx (low lane) and dx + 1 (high lane)
+            for (int yy = ty; yy < DH; yy += kTY)
+                for (int xx = tx; xx < DW; xx += kTX) {
+                    const float s0 = S[(yy + hs) * GW + xx + hs];
+                    const float *q = S + (yy + hs + dy) * GW + xx + hs + dx;
+                    D[yy * DW + xx] = f2_sqd(f2_pack(s0, s0), f2_pack(q[0], q[1]));
+                }
+            __syncthreads();
+            for (int xx = tx; xx < DW; xx += kTX) {
+                f2 v = D[ty * DW + xx];
+                for (int t = 1; t < P; ++t) v = f2_add(v, D[(ty + t) * DW + xx]);
+                V[ty * DW + xx] = v;
             }
             __syncthreads();
-            for (int i = threadIdx.x; i < kTY * DW; i += kThreads) {
-                int yy = i / DW, xx = i - yy * DW;
-                float s = 0.0f;
-                for (int t = 0; t < P; ++t) s += D[(yy + t) * DW + xx];
-                V[i] = s;
-            }
-            __syncthreads();
-            float d2 = 0.0f;
-            for (int t = 0; t < P; ++t) d2 += V[ty * DW + tx + t];
-            d2 *= a.inv_np;
-            const int qy = py + dy, qx = px + dx;
-            if (qy >= 0 && qy < H && qx >= 0 && qx < W) {
-                float e = fmaxf(d2 - two_s2, 0.0f);
-                float w = __expf(-e * inv_h2);
-                acc[0] = fmaf(w, S[(ty + r + hs + dy) * GW + tx + r + hs + dx], acc[0]);
+            f2 d2 = V[ty * DW + tx];
+            for (int t = 1; t < P; ++t) d2 = f2_add(d2, V[ty * DW + tx + t]);
+            d2 = f2_mul(d2, inv_np);
+            const int qy = py + dy;
+            if (qy >= 0 && qy < H) {
 #pragma unroll
-                for (int c = 1; c < 3; ++c)
-                    if (c < a.C) acc[c] = fmaf(w, Y[(c - 1) * VH * VW + (ty + hs + dy) * VW + tx + hs + dx], acc[c]);
-                wsum += w;
+                for (int e = 0; e < 2; ++e) {
+                    const int ox = dx + e, qx = px + ox;
+                    if (ox <= hs && qx >= 0 && qx < W) {
+                        const float ee = fmaxf((e ? f2_hi(d2) : f2_lo(d2)) - two_s2, 0.0f);
+                        const float w = __expf(-ee * inv_h2);
+                        acc[0] = fmaf(w, S[(ty + r + hs + dy) * GW + tx + r + hs + ox], acc[0]);
+#pragma unroll
+                        for (int c = 1; c < 3; ++c)
+                            if (c < a.C)
+                                acc[c] = fmaf(w, Y[(c - 1) * VH * VW + (ty + hs + dy) * VW + tx + hs + ox], acc[c]);
+                        wsum += w;
+                    }
+                }
             }
         }
     if (px < W && py < H) {
@@ -128,7 +141,8 @@ dn_status nlm_launch(const float *in, float *out, int B, int C, int H, int W, co
     const int GW = kTX + 2 * a.r + 2 * a.hs, GH = kTY + 2 * a.r + 2 * a.hs;
     const int DW = kTX + 2 * a.r, DH = kTY + 2 * a.r;
     const int VW = kTX + 2 * a.hs, VH = kTY + 2 * a.hs;
-    size_t smem = sizeof(float) * ((size_t)GH * GW + (size_t)DH * DW + (size_t)kTY * DW + (size_t)(C - 1) * VH * VW);
+    size_t smem = sizeof(float) * ((size_t)((GH * GW + 1) & ~1) + 2 * (size_t)DH * DW + 2 * (size_t)kTY * DW +
+                                   (size_t)(C - 1) * VH * VW);
     if (smem > 200 * 1024) return DN_EUNSUPPORTED;
     if (cudaFuncSetAttribute(k_nlm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return DN_ECUDA;
