@@ -78,17 +78,20 @@ typedef struct {
 } dn_nlm_params;
 
 /* Residual CNN of Sec. II (Fig. 1): `layers` 3x3 convolutions, the first
- * `layers-1` followed by ReLU, `width` hidden channels, 2 input channels
- * (prefilter/255, noisy/255, Eq. 3) and 1 output channel r; the result is
- * prefilter + 255 r (Eq. 2).  Colour images run the single-channel network on
- * each RGB channel.
+ * `layers-1` followed by ReLU, `width` hidden channels, 2 cc input channels
+ * (prefilter/255 and noisy/255 for each of cc colour planes, Eq. 3) and cc
+ * output channels r; the result is prefilter + 255 r (Eq. 2).
+ * channels = 1 (or 0): the grey network (cc = 1), run on each channel of a
+ * colour image; channels = 3: a colour-native network (cc = 3, 6 -> width ->
+ * ... -> 3) for RGB images.
  * `weights` is a DEVICE pointer to FP32 parameters, layer by layer:
- *   W_l [Cout][3][3][Cin] then b_l [Cout]; see dn_cnn_param_count(). */
+ *   W_l [Cout][3][3][Cin] then b_l [Cout]; see dn_cnn_param_count_c(). */
 typedef struct {
     int layers;            /* K >= 2 (10) */
-    int width;             /* hidden channels, 32 (the BF16 path needs 32) */
+    int width;             /* hidden channels, 32 (the BF16 path takes 32 or 64) */
     const float *weights;  /* device, caller-owned */
     int precision;         /* DN_FP32: FP32 SIMT kernels; DN_BF16: tcgen05 BF16 */
+    int channels;          /* 0 or 1: grey network per channel; 3: colour-native network */
 } dn_cnn;
 
 /* ---- parameters ---------------------------------------------------------- */
@@ -98,8 +101,10 @@ typedef struct {
 void dn_bm3d_default_params(dn_bm3d_params *p);
 /* Defaults: {7, 21, 0.4}. */
 void dn_nlm_default_params(dn_nlm_params *p);
-/* Number of floats in a dn_cnn weight buffer. */
+/* Number of floats in a dn_cnn weight buffer (grey network, channels = 1). */
 size_t dn_cnn_param_count(int layers, int width);
+/* The same for `channels` colour planes (1 or 3). */
+size_t dn_cnn_param_count_c(int layers, int width, int channels);
 /* Number of reference positions along an axis of length L (grid 0, step, ...
  * plus L - patch); writes them to pos[] when pos != NULL.  0 if L < patch. */
 int dn_bm3d_grid(int L, int patch, int step, int *pos);
@@ -228,20 +233,21 @@ dn_status dn_conv3x3_bwd_data(const float *dy, const float *w, const float *mask
 dn_status dn_conv3x3_bwd_weight(const float *x, const float *dy, float *dw, float *db, int N, int Cin, int Cout,
                                 int H, int W, dn_stream_t stream);
 
-/* Full network forward on single-channel planes (Eq. 2-3), FP32 or BF16:
- * noisy, pre: device [N][H][W]; out [N][H][W] = pre + 255 F([pre, noisy]/255).
+/* Full network forward (Eq. 2-3), FP32 or BF16: noisy, pre, out: device
+ * [N][cc][H][W] with cc = 3 for a colour-native network (channels = 3), else
+ * cc = 1; out = pre + 255 F([pre, noisy]/255).
  * workspace >= dn_cnn_workspace_bytes(N, H, W, cnn). */
 dn_status dn_cnn_forward(const float *noisy, const float *pre, float *out, int N, int H, int W, const dn_cnn *cnn,
                          void *workspace, size_t ws_bytes, dn_stream_t stream);
 size_t dn_cnn_workspace_bytes(int N, int H, int W, const dn_cnn *cnn);
 
-/* One hidden 32 -> 32 layer on the tensor cores (tcgen05, BF16 x BF16 -> FP32):
- * x, y: device NHWC bf16 [N][H][W][32] (64 bytes per pixel, 16-byte aligned);
- * w: device FP32 [32][3][3][32] (rounded to BF16 inside), b: device FP32 [32];
- * y = conv3x3(x, w) + b, ReLU when relu != 0, rounded to BF16.
- * workspace: device, >= 18432 bytes (packed weights). */
-dn_status dn_conv3x3_tc_fwd(const void *x, const float *w, const float *b, void *y, int N, int H, int W, int relu,
-                            void *workspace, size_t ws_bytes, dn_stream_t stream);
+/* One hidden C -> C layer on the tensor cores (tcgen05, BF16 x BF16 -> FP32),
+ * C = 32 or 64: x, y: device NHWC bf16 [N][H][W][C] (2 C bytes per pixel,
+ * 16-byte aligned); w: device FP32 [C][3][3][C] (rounded to BF16 inside),
+ * b: device FP32 [C]; y = conv3x3(x, w) + b, ReLU when relu != 0, rounded to
+ * BF16.  workspace: device, >= 9 * C * C * 2 bytes (packed weights). */
+dn_status dn_conv3x3_tc_fwd(const void *x, const float *w, const float *b, void *y, int N, int H, int W, int C,
+                            int relu, void *workspace, size_t ws_bytes, dn_stream_t stream);
 
 /* Reads (and with reset != 0 clears) the library's device error word on the
  * current device: nonzero when a kernel's bounded wait on the tensor-core

@@ -315,13 +315,18 @@ def conv3x3_bwd(x: np.ndarray, dy: np.ndarray, w: np.ndarray):
 
 
 def cnn_forward(noisy: np.ndarray, pre: np.ndarray, params, keep: bool = False):
-    """Residual CNN on single-channel planes (Eq. 2-3).
+    """Residual CNN (Eq. 2-3).
 
-    noisy, pre: [N, H, W] (pre = BM3D or NLM output), 0..255 scale.
-    z = [pre / 255, noisy / 255]; K-1 conv+bias+ReLU layers and a final
-    conv+bias; output = pre + 255 * r.  params: list of (W [Cout,3,3,Cin], b).
+    noisy, pre: [N, H, W] single-channel planes, or [N, cc, H, W] for a
+    colour-native network (pre = BM3D or NLM output), 0..255 scale.
+    z = [pre / 255, noisy / 255] (all pre planes, then all noisy planes);
+    K-1 conv+bias+ReLU layers and a final conv+bias with cc outputs;
+    output = pre + 255 * r.  params: list of (W [Cout,3,3,Cin], b).
     With keep=True also returns the layer inputs and pre-activations."""
-    z = np.stack([_f64(pre) / 255.0, _f64(noisy) / 255.0], axis=1)
+    colour = np.ndim(noisy) == 4
+    p4 = _f64(pre) if colour else _f64(pre)[:, None]
+    n4 = _f64(noisy) if colour else _f64(noisy)[:, None]
+    z = np.concatenate([p4 / 255.0, n4 / 255.0], axis=1)
     acts, pres = [z], []
     h = z
     for l, (w, b) in enumerate(params):
@@ -329,7 +334,8 @@ def cnn_forward(noisy: np.ndarray, pre: np.ndarray, params, keep: bool = False):
         pres.append(a)
         h = np.maximum(a, 0.0) if l < len(params) - 1 else a
         acts.append(h)
-    out = _f64(pre) + 255.0 * h[:, 0]
+    out = p4 + 255.0 * h
+    out = out if colour else out[:, 0]
     if keep:
         return out, acts, pres
     return out

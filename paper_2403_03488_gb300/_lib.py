@@ -43,7 +43,7 @@ class NLMParams(ctypes.Structure):
 
 class CNN(ctypes.Structure):
     _fields_ = [("layers", ctypes.c_int), ("width", ctypes.c_int), ("weights", ctypes.c_void_p),
-                ("precision", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("channels", ctypes.c_int)]
 
 
 _lib = None
@@ -66,6 +66,7 @@ def lib():
         "dn_bm3d_default_params": (None, [P(BM3DParams)]),
         "dn_nlm_default_params": (None, [P(NLMParams)]),
         "dn_cnn_param_count": (sz, [i, i]),
+        "dn_cnn_param_count_c": (sz, [i, i, i]),
         "dn_bm3d_grid": (i, [i, i, i, ip]),
         "dn_bm3d_workspace_bytes": (sz, [i, i, i, i, P(BM3DParams)]),
         "dn_nlm_workspace_bytes": (sz, [i, i, i, i, P(NLMParams)]),
@@ -89,7 +90,7 @@ def lib():
         "dn_conv3x3_bwd_weight": (i, [vp, vp, vp, vp, i, i, i, i, i, vp]),
         "dn_cnn_forward": (i, [vp, vp, vp, i, i, i, P(CNN), vp, sz, vp]),
         "dn_cnn_workspace_bytes": (sz, [i, i, i, P(CNN)]),
-        "dn_conv3x3_tc_fwd": (i, [vp, vp, vp, vp, i, i, i, i, vp, sz, vp]),
+        "dn_conv3x3_tc_fwd": (i, [vp, vp, vp, vp, i, i, i, i, i, vp, sz, vp]),
         "dn_device_error": (i, [ip, i]),
         "dn_cnn_pack_input": (i, [vp, vp, vp, i, i, i, vp]),
         "dn_cnn_residual_out": (i, [vp, vp, vp, sz, vp]),

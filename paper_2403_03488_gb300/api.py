@@ -66,8 +66,9 @@ def grid(L_: int, patch: int = 8, step: int = 3):
     return list(pos)[:n]
 
 
-def cnn_param_count(layers: int = 10, width: int = 32) -> int:
-    return int(L.lib().dn_cnn_param_count(layers, width))
+def cnn_param_count(layers: int = 10, width: int = 32, channels: int = 1) -> int:
+    """Floats in a weight buffer; channels = 3 for a colour-native network."""
+    return int(L.lib().dn_cnn_param_count_c(layers, width, channels))
 
 
 def bm3d_workspace_bytes(B, C, H, W, params: BM3DParams) -> int:
@@ -120,11 +121,12 @@ def denoise_nlm(noisy: torch.Tensor, sigma, params: Optional[NLMParams] = None, 
     return out
 
 
-def make_cnn(weights: torch.Tensor, layers: int = 10, width: int = 32, precision: int = DN_FP32) -> CNN:
+def make_cnn(weights: torch.Tensor, layers: int = 10, width: int = 32, precision: int = DN_FP32,
+             channels: int = 1) -> CNN:
     _need(weights, "weights", dim=1)
-    if weights.numel() != cnn_param_count(layers, width):
-        raise ValueError("weights must hold %d floats" % cnn_param_count(layers, width))
-    return CNN(layers, width, ctypes.c_void_p(weights.data_ptr()), precision)
+    if weights.numel() != cnn_param_count(layers, width, channels):
+        raise ValueError("weights must hold %d floats" % cnn_param_count(layers, width, channels))
+    return CNN(layers, width, ctypes.c_void_p(weights.data_ptr()), precision, channels)
 
 
 def hybrid_workspace_bytes(B, C, H, W, prefilter, pparams, cnn: CNN) -> int:
@@ -134,13 +136,14 @@ def hybrid_workspace_bytes(B, C, H, W, prefilter, pparams, cnn: CNN) -> int:
 
 def denoise_hybrid(noisy: torch.Tensor, sigma, weights: torch.Tensor, layers: int = 10, width: int = 32,
                    prefilter: int = DN_PREFILTER_BM3D, prefilter_params=None, cnn_precision: int = DN_FP32,
-                   out=None, workspace=None, stream=None) -> torch.Tensor:
-    """Nonlocal prefilter then the residual CNN (Eq. 2-3)."""
+                   out=None, workspace=None, stream=None, cnn_channels: int = 1) -> torch.Tensor:
+    """Nonlocal prefilter then the residual CNN (Eq. 2-3); cnn_channels = 3
+    selects a colour-native network for RGB input."""
     _need(noisy, "noisy", dim=4)
     B, C, H, W = noisy.shape
     if prefilter_params is None:
         prefilter_params = default_bm3d_params() if prefilter == DN_PREFILTER_BM3D else default_nlm_params()
-    cnn = make_cnn(weights, layers, width, cnn_precision)
+    cnn = make_cnn(weights, layers, width, cnn_precision, cnn_channels)
     out = torch.empty_like(noisy) if out is None else out
     _need(out, "out", dim=4)
     ws, nb = _ws(hybrid_workspace_bytes(B, C, H, W, prefilter, prefilter_params, cnn), noisy.device, workspace)
@@ -286,11 +289,15 @@ def conv3x3_bwd_weight(x, dy, dw=None, db=None, stream=None):
 
 
 def cnn_forward(noisy, pre, weights, layers=10, width=32, precision=DN_FP32, stream=None):
-    """Residual network on planes [N, H, W]: pre + 255 F([pre, noisy] / 255)."""
-    _need(noisy, "noisy", dim=3)
-    _need(pre, "pre", dim=3)
-    N, H, W = noisy.shape
-    cnn = make_cnn(weights, layers, width, precision)
+    """Residual network pre + 255 F([pre, noisy] / 255) on planes [N, H, W]
+    (grey network) or [N, 3, H, W] (colour-native network)."""
+    colour = noisy.dim() == 4
+    _need(noisy, "noisy", dim=4 if colour else 3)
+    _need(pre, "pre", dim=4 if colour else 3)
+    if colour and noisy.shape[1] != 3:
+        raise ValueError("a colour-native network takes 3 planes")
+    N, H, W = noisy.shape[0], noisy.shape[-2], noisy.shape[-1]
+    cnn = make_cnn(weights, layers, width, precision, 3 if colour else 1)
     out = torch.empty_like(noisy)
     ws, nb = _ws(int(L.lib().dn_cnn_workspace_bytes(N, H, W, ctypes.byref(cnn))), noisy.device, None)
     check(L.lib().dn_cnn_forward(_vp(noisy), _vp(pre), _vp(out), N, H, W, ctypes.byref(cnn), _vp(ws), nb,
@@ -299,16 +306,16 @@ def cnn_forward(noisy, pre, weights, layers=10, width=32, precision=DN_FP32, str
 
 
 def conv3x3_tc_fwd(x_nhwc, w, b, relu=True, stream=None):
-    """One 32 -> 32 layer on the tensor cores: x_nhwc bf16 [N, H, W, 32] -> same."""
+    """One C -> C layer on the tensor cores (C = 32 or 64): x_nhwc bf16 [N, H, W, C] -> same."""
     _need(x_nhwc, "x_nhwc", torch.bfloat16, dim=4)
     _need(w, "w", dim=4)
     _need(b, "b", dim=1)
     N, H, W, C = x_nhwc.shape
-    if C != 32 or tuple(w.shape) != (32, 3, 3, 32) or b.numel() != 32:
-        raise ValueError("conv3x3_tc_fwd handles 32 -> 32 channels")
+    if C not in (32, 64) or tuple(w.shape) != (C, 3, 3, C) or b.numel() != C:
+        raise ValueError("conv3x3_tc_fwd handles C -> C channels, C = 32 or 64")
     y = torch.empty_like(x_nhwc)
-    ws = torch.empty(18432, dtype=torch.uint8, device=x_nhwc.device)
-    check(L.lib().dn_conv3x3_tc_fwd(_vp(x_nhwc), _vp(w), _vp(b), _vp(y), N, H, W, int(bool(relu)), _vp(ws),
+    ws = torch.empty(9 * C * C * 2, dtype=torch.uint8, device=x_nhwc.device)
+    check(L.lib().dn_conv3x3_tc_fwd(_vp(x_nhwc), _vp(w), _vp(b), _vp(y), N, H, W, C, int(bool(relu)), _vp(ws),
                                     ws.numel(), _stream(stream)), "dn_conv3x3_tc_fwd")
     return y
 

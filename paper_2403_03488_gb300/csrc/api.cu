@@ -58,8 +58,12 @@ bool valid_nlm(const dn_nlm_params *p)
 bool valid_cnn(const dn_cnn *c)
 {
     return c && c->weights && c->layers >= 2 && c->layers <= 64 && c->width >= 1 && c->width <= 64 &&
-           (c->precision == DN_FP32 || c->precision == DN_BF16);
+           (c->precision == DN_FP32 || c->precision == DN_BF16) &&
+           (c->channels == 0 || c->channels == 1 || c->channels == 3);
 }
+
+// Colour planes the network takes and produces (1: grey network).
+int cnn_cc(const dn_cnn *c) { return c->channels == 3 ? 3 : 1; }
 
 float tau_for(const dn_bm3d_pass &p, float sigma, int regime)
 {
@@ -115,13 +119,14 @@ NlmWs nlm_layout(void *base, int B, int C, int H, int W)
 }
 
 struct CnnWs {
-    float *z;        // FP32 path: packed input [N][2][H][W]
-    float *act[2];   // FP32: [N][width][H][W]; BF16: NHWC [N][H][W][32] bf16
+    float *z;        // FP32 path: packed input [N][2 cc][H][W]
+    float *act[2];   // FP32: [N][width][H][W]; BF16: NHWC [N][H][W][width] bf16
     char *wpack;     // BF16: packed B operands of the hidden layers
     size_t bytes;
 };
 
-constexpr size_t kWPackBytes = 9 * 4 * 32 * 16;
+// Packed B operand of one width x width hidden layer ([tap][chunk][cout][8] bf16).
+size_t wpack_bytes(int width) { return (size_t)9 * width * width * 2; }
 
 CnnWs cnn_layout(void *base, int N, int H, int W, const dn_cnn *c)
 {
@@ -130,11 +135,11 @@ CnnWs cnn_layout(void *base, int N, int H, int W, const dn_cnn *c)
     CnnWs w;
     if (c->precision == DN_BF16) {
         w.z = nullptr;
-        w.act[0] = reinterpret_cast<float *>(cv.take<char>((size_t)N * HW * 64));
-        w.act[1] = reinterpret_cast<float *>(cv.take<char>((size_t)N * HW * 64));
-        w.wpack = cv.take<char>(kWPackBytes * (size_t)(c->layers > 2 ? c->layers - 2 : 1));
+        w.act[0] = reinterpret_cast<float *>(cv.take<char>((size_t)N * HW * c->width * 2));
+        w.act[1] = reinterpret_cast<float *>(cv.take<char>((size_t)N * HW * c->width * 2));
+        w.wpack = cv.take<char>(wpack_bytes(c->width) * (size_t)(c->layers > 2 ? c->layers - 2 : 1));
     } else {
-        w.z = cv.take<float>((size_t)N * 2 * HW);
+        w.z = cv.take<float>((size_t)N * 2 * cnn_cc(c) * HW);
         w.act[0] = cv.take<float>((size_t)N * c->width * HW);
         w.act[1] = cv.take<float>((size_t)N * c->width * HW);
         w.wpack = nullptr;
@@ -219,31 +224,33 @@ dn_status run_nlm(const float *noisy, float *out, int B, int C, int H, int W, co
 dn_status run_cnn(const float *noisy, const float *pre, float *out, int N, int H, int W, const dn_cnn *c,
                   const CnnWs &w, cudaStream_t s)
 {
+    const int cc = cnn_cc(c), C = c->width;
     if (c->precision == DN_BF16) {
-        if (c->width != 32) return DN_EUNSUPPORTED;
+        if (C != 32 && C != 64) return DN_EUNSUPPORTED;
         int *err = device_error_ptr();
         if (!err) return DN_ECUDA;
-        size_t off = (size_t)32 * 9 * 2 + 32;  // layer 1 (2 -> 32)
-        DN_TRY(conv_first_bf16(pre, noisy, c->weights, c->weights + 32 * 9 * 2, w.act[0], N, H, W, s));
+        size_t off = (size_t)C * 9 * 2 * cc + C;  // layer 1 (2 cc -> C)
+        DN_TRY(conv_first_bf16(pre, noisy, c->weights, c->weights + (size_t)C * 9 * 2 * cc, w.act[0], N, cc, H, W, C,
+                               s));
         int cur = 0;
         for (int l = 1; l < c->layers - 1; ++l) {
             const float *wl = c->weights + off;
-            const float *bl = wl + 32 * 9 * 32;
-            off += 32 * 9 * 32 + 32;
-            char *wp = w.wpack + kWPackBytes * (size_t)(l - 1);
-            DN_TRY(pack_w_tc(wl, wp, s));
-            DN_TRY(conv3x3_tc(w.act[cur], w.act[cur ^ 1], wp, bl, N, H, W, 1, err, s));
+            const float *bl = wl + (size_t)C * 9 * C;
+            off += (size_t)C * 9 * C + C;
+            char *wp = w.wpack + wpack_bytes(C) * (size_t)(l - 1);
+            DN_TRY(pack_w_tc(wl, wp, C, s));
+            DN_TRY(conv3x3_tc(w.act[cur], w.act[cur ^ 1], wp, bl, N, H, W, C, 1, err, s));
             cur ^= 1;
         }
         const float *wl = c->weights + off;
-        return conv_last_bf16(w.act[cur], wl, wl + 9 * 32, pre, out, N, H, W, s);
+        return conv_last_bf16(w.act[cur], wl, wl + (size_t)cc * 9 * C, pre, out, N, cc, H, W, C, s);
     }
-    DN_TRY(pack_input(pre, noisy, w.z, N, H, W, s));
+    DN_TRY(pack_input(pre, noisy, w.z, N, cc, H, W, s));
     const float *h = w.z;
-    int kin = 2;
+    int kin = 2 * cc;
     size_t off = 0;
     for (int l = 0; l < c->layers; ++l) {
-        const int kout = l == c->layers - 1 ? 1 : c->width;
+        const int kout = l == c->layers - 1 ? cc : C;
         const float *wl = c->weights + off;
         const float *bl = wl + (size_t)kout * 9 * kin;
         off += (size_t)kout * 9 * kin + kout;
@@ -252,7 +259,7 @@ dn_status run_cnn(const float *noisy, const float *pre, float *out, int N, int H
         h = y;
         kin = kout;
     }
-    return residual_out(pre, h, out, (size_t)N * H * W, s);
+    return residual_out(pre, h, out, (size_t)N * cc * H * W, s);
 }
 
 }  // namespace
@@ -281,18 +288,20 @@ void dn_nlm_default_params(dn_nlm_params *p)
     p->h_over_sigma = 0.4f;
 }
 
-size_t dn_cnn_param_count(int layers, int width)
+size_t dn_cnn_param_count_c(int layers, int width, int channels)
 {
-    if (layers < 2 || width < 1) return 0;
+    if (layers < 2 || width < 1 || (channels != 1 && channels != 3)) return 0;
     size_t total = 0;
-    int kin = 2;
+    int kin = 2 * channels;
     for (int l = 0; l < layers; ++l) {
-        int kout = l == layers - 1 ? 1 : width;
+        int kout = l == layers - 1 ? channels : width;
         total += (size_t)kout * 9 * kin + kout;
         kin = kout;
     }
     return total;
 }
+
+size_t dn_cnn_param_count(int layers, int width) { return dn_cnn_param_count_c(layers, width, 1); }
 
 int dn_bm3d_grid(int L, int patch, int step, int *pos)
 {
@@ -328,7 +337,8 @@ size_t dn_hybrid_workspace_bytes(int B, int C, int H, int W, int prefilter, cons
     size_t f = prefilter == DN_PREFILTER_BM3D
                    ? dn_bm3d_workspace_bytes(B, C, H, W, static_cast<const dn_bm3d_params *>(pp))
                    : dn_nlm_workspace_bytes(B, C, H, W, static_cast<const dn_nlm_params *>(pp));
-    size_t c = dn_cnn_workspace_bytes(B * C, H, W, cnn);
+    const int n = cnn->channels == 3 ? B : B * C;
+    size_t c = dn_cnn_workspace_bytes(n, H, W, cnn);
     return pre + (f > c ? f : c);
 }
 
@@ -383,7 +393,9 @@ dn_status denoise_hybrid(const float *noisy, float *out, int B, int C, int H, in
         DN_TRY(run_nlm(noisy, pre, B, C, H, W, sigma, static_cast<const dn_nlm_params *>(pp),
                        nlm_layout(rest, B, C, H, W), s));
     }
-    return run_cnn(noisy, pre, out, B * C, H, W, cnn, cnn_layout(rest, B * C, H, W, cnn), s);
+    if (cnn->channels == 3 && C != 3) return DN_EINVAL;  // a colour-native network needs RGB input
+    const int n = cnn->channels == 3 ? B : B * C;
+    return run_cnn(noisy, pre, out, n, H, W, cnn, cnn_layout(rest, n, H, W, cnn), s);
     DN_GUARD_END
 }
 
@@ -565,17 +577,19 @@ dn_status dn_cnn_forward(const float *noisy, const float *pre, float *out, int N
     DN_GUARD_END
 }
 
-dn_status dn_conv3x3_tc_fwd(const void *x, const float *w, const float *b, void *y, int N, int H, int W, int relu,
-                            void *workspace, size_t ws_bytes, dn_stream_t stream)
+dn_status dn_conv3x3_tc_fwd(const void *x, const float *w, const float *b, void *y, int N, int H, int W, int C,
+                            int relu, void *workspace, size_t ws_bytes, dn_stream_t stream)
 {
     DN_GUARD_BEGIN
-    if (!x || !w || !b || !y || N < 1 || H < 1 || W < 1 || (size_t)N * H * W > ((size_t)1 << 34)) return DN_EINVAL;
-    if (!workspace || ws_bytes < kWPackBytes) return DN_ENOMEM;
+    if (!x || !w || !b || !y || N < 1 || H < 1 || W < 1 || (size_t)N * H * W > ((size_t)1 << 34) ||
+        (C != 32 && C != 64))
+        return DN_EINVAL;
+    if (!workspace || ws_bytes < wpack_bytes(C)) return DN_ENOMEM;
     int *err = device_error_ptr();
     if (!err) return DN_ECUDA;
     cudaStream_t s = (cudaStream_t)stream;
-    DN_TRY(pack_w_tc(w, workspace, s));
-    return conv3x3_tc(x, y, workspace, b, N, H, W, relu, err, s);
+    DN_TRY(pack_w_tc(w, workspace, C, s));
+    return conv3x3_tc(x, y, workspace, b, N, H, W, C, relu, err, s);
     DN_GUARD_END
 }
 
@@ -583,7 +597,7 @@ dn_status dn_cnn_pack_input(const float *pre, const float *noisy, float *z, int 
 {
     DN_GUARD_BEGIN
     if (!pre || !noisy || !z || N < 1 || H < 1 || W < 1) return DN_EINVAL;
-    return pack_input(pre, noisy, z, N, H, W, (cudaStream_t)stream);
+    return pack_input(pre, noisy, z, N, 1, H, W, (cudaStream_t)stream);
     DN_GUARD_END
 }
 

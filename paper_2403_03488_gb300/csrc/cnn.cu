@@ -127,12 +127,14 @@ __global__ void __launch_bounds__(kT *kT) k_conv3x3_bwd_w(const float *x, const 
     }
 }
 
-__global__ void k_pack_input(const float *pre, const float *noisy, float *z, size_t HW, size_t total)
+// z[n] = [pre[n] / 255 (cc planes), noisy[n] / 255 (cc planes)]; i runs over
+// the N cc HW elements of pre / noisy.
+__global__ void k_pack_input(const float *pre, const float *noisy, float *z, size_t HW, int cc, size_t total)
 {
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        size_t n = i / HW, p = i - n * HW;
-        z[(2 * n) * HW + p] = pre[i] * (1.0f / 255.0f);
-        z[(2 * n + 1) * HW + p] = noisy[i] * (1.0f / 255.0f);
+        const size_t nc = i / HW, p = i - nc * HW, n = nc / cc, c = nc - n * cc;
+        z[(2 * cc * n + c) * HW + p] = pre[i] * (1.0f / 255.0f);
+        z[(2 * cc * n + cc + c) * HW + p] = noisy[i] * (1.0f / 255.0f);
     }
 }
 
@@ -222,10 +224,11 @@ dn_status conv3x3_bwd_weight_fp32(const float *x, const float *dy, float *dw, fl
                   [&] { k_conv3x3_bwd_w<<<grid, kT * kT, smem, s>>>(x, dy, dw, db, Cin, Cout, H, W); });
 }
 
-dn_status pack_input(const float *pre, const float *noisy, float *z, int N, int H, int W, cudaStream_t s)
+dn_status pack_input(const float *pre, const float *noisy, float *z, int N, int cc, int H, int W, cudaStream_t s)
 {
-    size_t HW = (size_t)H * W, total = (size_t)N * HW;
-    return launch("cnn_pack_input", s, [&] { k_pack_input<<<ew_blocks(total), 256, 0, s>>>(pre, noisy, z, HW, total); });
+    size_t HW = (size_t)H * W, total = (size_t)N * cc * HW;
+    return launch("cnn_pack_input", s,
+                  [&] { k_pack_input<<<ew_blocks(total), 256, 0, s>>>(pre, noisy, z, HW, cc, total); });
 }
 
 dn_status residual_out(const float *pre, const float *r, float *out, size_t total, cudaStream_t s)

@@ -95,7 +95,8 @@ dn_status conv3x3_fwd_fp32(const float *x, const float *w, const float *b, const
                            int Kin, int Kout, int H, int W, int relu, bool trans, cudaStream_t s);
 dn_status conv3x3_bwd_weight_fp32(const float *x, const float *dy, float *dw, float *db, int N, int Cin, int Cout,
                                   int H, int W, cudaStream_t s);
-dn_status pack_input(const float *pre, const float *noisy, float *z, int N, int H, int W, cudaStream_t s);
+// z [N][2 cc][H][W] = [pre / 255 (cc planes), noisy / 255 (cc planes)]
+dn_status pack_input(const float *pre, const float *noisy, float *z, int N, int cc, int H, int W, cudaStream_t s);
 dn_status residual_out(const float *pre, const float *r, float *out, size_t total, cudaStream_t s);
 dn_status relu_bwd(const float *g, const float *y, float *out, size_t count, cudaStream_t s);
 dn_status l1_grad(const float *r, const float *pre, const float *clean, float *dr, size_t count, double *loss,
@@ -108,13 +109,13 @@ dn_status match_tc(const float *guide, size_t plane, int B, int H, int W, const 
                    int *idx, int *n, int *err, int *fb_ws, cudaStream_t s, float *cross = nullptr, int cross_tx = 0,
                    int cross_ty = 0);
 size_t conv_tc_smem_bytes();
-dn_status pack_w_tc(const float *w, void *out, cudaStream_t s);
-dn_status conv3x3_tc(const void *x, void *y, const void *wpack, const float *bias, int N, int H, int W, int relu,
-                     int *err, cudaStream_t s);
+dn_status pack_w_tc(const float *w, void *out, int C, cudaStream_t s);
+dn_status conv3x3_tc(const void *x, void *y, const void *wpack, const float *bias, int N, int H, int W, int C,
+                     int relu, int *err, cudaStream_t s);
 dn_status conv_first_bf16(const float *pre, const float *noisy, const float *w, const float *b, void *y, int N,
-                          int H, int W, cudaStream_t s);
-dn_status conv_last_bf16(const void *x, const float *w, const float *b, const float *pre, float *out, int N, int H,
-                         int W, cudaStream_t s);
+                          int cc, int H, int W, int C, cudaStream_t s);
+dn_status conv_last_bf16(const void *x, const float *w, const float *b, const float *pre, float *out, int N, int cc,
+                         int H, int W, int C, cudaStream_t s);
 dn_status adam(float *p, const float *g, float *m, float *v, size_t count, int t, float lr, float b1, float b2,
                float eps, cudaStream_t s);
 

@@ -30,54 +30,66 @@ namespace {
 
 constexpr int kPX = 128;                  // output pixels per row tile (MMA M)
 constexpr int kP = 130;                   // staged pixels per input row (P = 2 mod 8: conflict-free chunk planes)
-constexpr int kCh = 32;                   // hidden channels
-constexpr int kRowBytes = kP * kCh * 2;   // 8320
-constexpr int kWBytes = 9 * 4 * kCh * 16; // 18432: [tap][chunk][cout][8 ch] bf16
+constexpr int kCh = 32;                   // channels of the default (10 x 32) network
 constexpr int kPF = 1;                    // rows in flight beyond the next one
 constexpr int kSlots = kPF + 5;           // rows y-2 (last MMA) .. y+2+kPF
 constexpr int kItemRows = 32;             // output rows per work item
-constexpr int kCtasPerSm = 3;
-constexpr uint32_t kIdesc = tc::idesc_bf16(128, 32);
+
+// Shapes of a C -> C hidden layer (C = 32 or 64 channels).
+template <int C>
+struct Shape {
+    static constexpr int kChunks = C / 8;                   // 16-byte channel chunks per pixel
+    static constexpr int kRowBytes = kP * C * 2;            // one staged row
+    static constexpr int kWBytes = 9 * kChunks * C * 16;    // [tap][chunk][cout][8 ch] bf16
+    static constexpr int kSmem = kWBytes + kSlots * kRowBytes + 32 + C * 4;
+    static constexpr int kCtasPerSm = (227 * 1024) / (kSmem + 1024);
+    static constexpr uint32_t kIdesc = tc::idesc_bf16(128, C);
+};
 
 struct ConvTcArgs {
-    const uint4 *x;       // [N][H][W][32] bf16, 4 x uint4 per pixel
+    const uint4 *x;       // [N][H][W][C] bf16, C / 8 x uint4 per pixel
     uint4 *y;             // same layout
-    const uint4 *wpack;   // kWBytes
-    const float *bias;    // [32]
+    const uint4 *wpack;   // Shape<C>::kWBytes
+    const float *bias;    // [C]
     int N, H, W, strips, chunks, relu;
     int *err;
 };
 
 // Row r of image n, pixels x0-1 .. x0+128, into the chunk planes of a ring
 // slot: cp.async for pixels inside the image, zeros elsewhere.
+template <int C>
 __device__ __forceinline__ void issue_row(const ConvTcArgs &a, uint8_t *slot, int n, int r, int x0, int tid)
 {
+    constexpr int K = Shape<C>::kChunks;
     const bool rin = r >= 0 && r < a.H;
-    const uint4 *src = a.x + ((size_t)n * a.H + (rin ? r : 0)) * a.W * 4;
-    for (int i = tid; i < kP * 4; i += 128) {
-        const int px = i >> 2, ck = i & 3;
+    const uint4 *src = a.x + ((size_t)n * a.H + (rin ? r : 0)) * a.W * K;
+    for (int i = tid; i < kP * K; i += 128) {
+        const int px = i / K, ck = i % K;
         const int gx = x0 - 1 + px;
         uint8_t *dst = slot + ck * kP * 16 + px * 16;
         if (rin && gx >= 0 && gx < a.W)
-            tc::cp_async16(tc::smem_u32(dst), src + (size_t)gx * 4 + ck);
+            tc::cp_async16(tc::smem_u32(dst), src + (size_t)gx * K + ck);
         else
             *reinterpret_cast<uint4 *>(dst) = make_uint4(0u, 0u, 0u, 0u);
     }
 }
 
+template <int C>
 __global__ void __launch_bounds__(128) k_conv3x3_tc(ConvTcArgs a)
 {
+    using S = Shape<C>;
+    constexpr int K = S::kChunks;
     extern __shared__ __align__(128) uint8_t sm[];
     uint8_t *wsm = sm;
-    uint8_t *ring = sm + kWBytes;
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(ring + kSlots * kRowBytes);  // [2]
+    uint8_t *ring = sm + S::kWBytes;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(ring + kSlots * S::kRowBytes);  // [2]
     uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 2);
     float *sbias = reinterpret_cast<float *>(tslot + 4);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    for (int i = tid; i < kWBytes / 16; i += 128) reinterpret_cast<uint4 *>(wsm)[i] = a.wpack[i];
-    if (tid < kCh) sbias[tid] = a.bias[tid];
-    if (warp == 0) tc::tmem_alloc(tslot, 64);
+    for (int i = tid; i < S::kWBytes / 16; i += 128) reinterpret_cast<uint4 *>(wsm)[i] = a.wpack[i];
+    for (int i = tid; i < C; i += 128) sbias[i] = a.bias[i];
+    if (warp == 0) tc::tmem_alloc(tslot, 2 * C);
     if (tid == 0) {
         tc::mbar_init(&mbar[0], 1);
         tc::mbar_init(&mbar[1], 1);
@@ -101,25 +113,29 @@ __global__ void __launch_bounds__(128) k_conv3x3_tc(ConvTcArgs a)
             return;
         }
         tc::fence_after_sync();
-        uint32_t r[32];
-        tc::tmem_ld32(tmem + (uint32_t)(32 * buf) + ((uint32_t)(warp * 32) << 16), r);
-        tc::tmem_wait_ld();
         const int x = x0 + warp * 32 + lane;
-        if (x < a.W) {
-            uint32_t pk[16];
+        uint4 *dst = a.y + (((size_t)n * a.H + yy) * a.W + x) * K;
 #pragma unroll
-            for (int c = 0; c < 16; ++c) {
-                float v0 = __uint_as_float(r[2 * c]) + sbias[2 * c];
-                float v1 = __uint_as_float(r[2 * c + 1]) + sbias[2 * c + 1];
-                if (a.relu) {
-                    v0 = fmaxf(v0, 0.0f);
-                    v1 = fmaxf(v1, 0.0f);
+        for (int h = 0; h < C / 32; ++h) {
+            uint32_t r[32];
+            tc::tmem_ld32(tmem + (uint32_t)(C * buf + 32 * h) + ((uint32_t)(warp * 32) << 16), r);
+            tc::tmem_wait_ld();
+            if (x < a.W) {
+                uint32_t pk[16];
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {
+                    float v0 = __uint_as_float(r[2 * c]) + sbias[32 * h + 2 * c];
+                    float v1 = __uint_as_float(r[2 * c + 1]) + sbias[32 * h + 2 * c + 1];
+                    if (a.relu) {
+                        v0 = fmaxf(v0, 0.0f);
+                        v1 = fmaxf(v1, 0.0f);
+                    }
+                    pk[c] = tc::pack_bf16x2(v0, v1);
                 }
-                pk[c] = tc::pack_bf16x2(v0, v1);
-            }
-            uint4 *dst = a.y + (((size_t)n * a.H + yy) * a.W + x) * 4;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) dst[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+                for (int q = 0; q < 4; ++q)
+                    dst[4 * h + q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+            }
         }
         tc::fence_before_sync();
     };
@@ -129,14 +145,14 @@ __global__ void __launch_bounds__(128) k_conv3x3_tc(ConvTcArgs a)
         const int chunk = it % a.chunks, rest = it / a.chunks;
         const int strip = rest % a.strips, n = rest / a.strips;
         const int x0 = strip * kPX, y0 = chunk * kItemRows, y1 = min(a.H, y0 + kItemRows);
-        auto slot = [&](int r) { return ring + ((r - y0 + 1) % kSlots) * kRowBytes; };
+        auto slot = [&](int r) { return ring + ((r - y0 + 1) % kSlots) * S::kRowBytes; };
         for (int r = y0 - 1; r <= y0 + 1 + kPF; ++r) {
-            if (r <= y1) issue_row(a, slot(r), n, r, x0, tid);
+            if (r <= y1) issue_row<C>(a, slot(r), n, r, x0, tid);
             tc::cp_async_commit();
         }
         for (int y = y0; y < y1; ++y) {
             const int rn = y + 2 + kPF;
-            if (rn <= y1) issue_row(a, slot(rn), n, rn, x0, tid);
+            if (rn <= y1) issue_row<C>(a, slot(rn), n, rn, x0, tid);
             tc::cp_async_commit();
             tc::cp_async_wait<kPF + 1>();  // rows up to y + 1 have landed (this thread's copies)
             tc::fence_proxy_async();
@@ -153,10 +169,10 @@ __global__ void __launch_bounds__(128) k_conv3x3_tc(ConvTcArgs a)
                     const int dy = t / 3, dx = t % 3;
                     const uint32_t rb = tc::smem_u32(slot(y - 1 + dy));
 #pragma unroll
-                    for (int k = 0; k < 2; ++k) {
+                    for (int k = 0; k < C / 16; ++k) {
                         const uint64_t ad = tc::sdesc(rb + (2 * k) * kP * 16 + dx * 16, kP * 16, 128);
-                        const uint64_t bd = tc::sdesc(wbase + ((t * 4 + 2 * k) * kCh) * 16, kCh * 16, 128);
-                        tc::mma_bf16(tmem + (uint32_t)(32 * buf), ad, bd, kIdesc, (t | k) != 0);
+                        const uint64_t bd = tc::sdesc(wbase + ((t * K + 2 * k) * C) * 16, C * 16, 128);
+                        tc::mma_bf16(tmem + (uint32_t)(C * buf), ad, bd, S::kIdesc, (t | k) != 0);
                     }
                 }
                 tc::mma_commit(&mbar[buf]);
@@ -177,19 +193,112 @@ __global__ void __launch_bounds__(128) k_conv3x3_tc(ConvTcArgs a)
     __syncthreads();
     if (warp == 0) {
         tc::fence_after_sync();
-        tc::tmem_dealloc(tmem, 64);
+        tc::tmem_dealloc(tmem, 2 * C);
     }
 }
 
-// W [32][3][3][32] fp32 -> [tap][chunk][cout][8 ch] bf16 (the B operand layout).
+// W [C][3][3][C] fp32 -> [tap][chunk][cout][8 ch] bf16 (the B operand layout).
+template <int C>
 __global__ void k_pack_w_tc(const float *w, uint16_t *out)
 {
+    constexpr int K = C / 8;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= 9 * 4 * kCh * 8) return;
-    const int j = i & 7, co = (i >> 3) & 31, ck = (i >> 8) & 3, t = i >> 10;
-    const float v = w[(co * 9 + t) * kCh + ck * 8 + j];
+    if (i >= 9 * K * C * 8) return;
+    const int j = i & 7, co = (i >> 3) % C, ck = (i / (8 * C)) % K, t = i / (8 * C * K);
+    const float v = w[(co * 9 + t) * C + ck * 8 + j];
     __nv_bfloat16 b = __float2bfloat16_rn(v);
     out[i] = *reinterpret_cast<uint16_t *>(&b);
+}
+
+// First layer of any other shape (2 cc -> C, cc = 1 or 3 colour planes):
+// z = [pre / 255 (cc planes), noisy / 255 (cc planes)], bias, ReLU, NHWC bf16
+// out.  One pixel per thread over a 16 x 16 tile, weights and the tile's
+// input planes in shared memory (plain loops; the 2 -> 32 case has its own
+// kernel below).
+template <int C>
+__global__ void __launch_bounds__(256) k_conv_first_any(const float *pre, const float *noisy, const float *w,
+                                                       const float *b, uint4 *y, int cc, int H, int W)
+{
+    extern __shared__ float fsm[];
+    const int cin = 2 * cc;
+    float *zs = fsm;                  // [cin][18][18]
+    float *ws = zs + cin * 324;       // [C][9][cin]
+    float *bs = ws + C * 9 * cin;     // [C]
+    const int n = blockIdx.z, X0 = blockIdx.x * 16, Y0 = blockIdx.y * 16;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const size_t HW = (size_t)H * W;
+    for (int i = threadIdx.x; i < C * 9 * cin; i += 256) ws[i] = w[i];
+    for (int i = threadIdx.x; i < C; i += 256) bs[i] = b[i];
+    for (int i = threadIdx.x; i < cin * 324; i += 256) {
+        const int c = i / 324, p = i - c * 324, yy = p / 18, xx = p - yy * 18;
+        const int gy = Y0 - 1 + yy, gx = X0 - 1 + xx;
+        const float *src = c < cc ? pre + ((size_t)n * cc + c) * HW : noisy + ((size_t)n * cc + c - cc) * HW;
+        zs[i] = (gy >= 0 && gy < H && gx >= 0 && gx < W) ? src[(size_t)gy * W + gx] * (1.0f / 255.0f) : 0.0f;
+    }
+    __syncthreads();
+    const int px = X0 + tx, py = Y0 + ty;
+    if (px >= W || py >= H) return;
+    uint4 *dst = y + ((size_t)n * HW + (size_t)py * W + px) * (C / 8);
+    for (int c0 = 0; c0 < C; c0 += 8) {
+        uint32_t pk[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            float acc[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int co = c0 + 2 * e + h;
+                float a = bs[co];
+                for (int t = 0; t < 9; ++t)
+                    for (int ci = 0; ci < cin; ++ci)
+                        a = fmaf(ws[(co * 9 + t) * cin + ci], zs[ci * 324 + (ty + t / 3) * 18 + tx + t % 3], a);
+                acc[h] = fmaxf(a, 0.0f);
+            }
+            pk[e] = tc::pack_bf16x2(acc[0], acc[1]);
+        }
+        dst[c0 / 8] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    }
+}
+
+// Last layer of any other shape (C -> cc) + bias, then out = pre + 255 r per
+// colour plane (Eq. 2).  One pixel per thread over a 16 x 16 tile.
+template <int C>
+__global__ void __launch_bounds__(256) k_conv_last_any(const uint4 *x, const float *w, const float *b,
+                                                      const float *pre, float *out, int cc, int H, int W)
+{
+    extern __shared__ uint4 lsm[];
+    constexpr int K = C / 8;
+    uint4 *xs = lsm;                                        // [324][K]
+    float *ws = reinterpret_cast<float *>(xs + 324 * K);    // [cc][9][C]
+    const int n = blockIdx.z, X0 = blockIdx.x * 16, Y0 = blockIdx.y * 16;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const size_t HW = (size_t)H * W;
+    for (int i = threadIdx.x; i < cc * 9 * C; i += 256) ws[i] = w[i];
+    for (int i = threadIdx.x; i < 324 * K; i += 256) {
+        const int p = i / K, ck = i % K, yy = p / 18, xx = p - yy * 18;
+        const int gy = Y0 - 1 + yy, gx = X0 - 1 + xx;
+        xs[i] = (gy >= 0 && gy < H && gx >= 0 && gx < W) ? x[((size_t)n * HW + (size_t)gy * W + gx) * K + ck]
+                                                         : make_uint4(0u, 0u, 0u, 0u);
+    }
+    __syncthreads();
+    const int px = X0 + tx, py = Y0 + ty;
+    if (px >= W || py >= H) return;
+    for (int co = 0; co < cc; ++co) {
+        float acc = b[co];
+        for (int t = 0; t < 9; ++t) {
+            const int p = (ty + t / 3) * 18 + tx + t % 3;
+            for (int ck = 0; ck < K; ++ck) {
+                const uint4 q = xs[p * K + ck];
+                const uint32_t u[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    acc = fmaf(ws[(co * 9 + t) * C + ck * 8 + 2 * e], tc::bf16_lo(u[e]), acc);
+                    acc = fmaf(ws[(co * 9 + t) * C + ck * 8 + 2 * e + 1], tc::bf16_hi(u[e]), acc);
+                }
+            }
+        }
+        const size_t at = ((size_t)n * cc + co) * HW + (size_t)py * W + px;
+        out[at] = fmaf(255.0f, acc, pre[at]);
+    }
 }
 
 // Layer 1 (2 -> 32) + bias + ReLU: pre/noisy planes (0..255) -> NHWC bf16.
@@ -324,15 +433,33 @@ __global__ void __launch_bounds__(256) k_conv_last_bf16(const uint4 *x, const fl
 
 }  // namespace
 
-size_t conv_tc_smem_bytes() { return kWBytes + kSlots * kRowBytes + 32 + kCh * 4; }
+size_t conv_tc_smem_bytes() { return Shape<kCh>::kSmem; }
 
-dn_status pack_w_tc(const float *w, void *out, cudaStream_t s)
+dn_status pack_w_tc(const float *w, void *out, int C, cudaStream_t s)
 {
-    return launch("pack_w_tc", s, [&] { k_pack_w_tc<<<(9 * 4 * kCh * 8 + 255) / 256, 256, 0, s>>>(w, (uint16_t *)out); });
+    if (C == 32)
+        return launch("pack_w_tc", s,
+                      [&] { k_pack_w_tc<32><<<(9 * 4 * 32 * 8 + 255) / 256, 256, 0, s>>>(w, (uint16_t *)out); });
+    if (C == 64)
+        return launch("pack_w_tc", s,
+                      [&] { k_pack_w_tc<64><<<(9 * 8 * 64 * 8 + 255) / 256, 256, 0, s>>>(w, (uint16_t *)out); });
+    return DN_EUNSUPPORTED;
 }
 
-dn_status conv3x3_tc(const void *x, void *y, const void *wpack, const float *bias, int N, int H, int W, int relu,
-                     int *err, cudaStream_t s)
+template <int C>
+dn_status conv3x3_tc_c(ConvTcArgs &a, cudaStream_t s)
+{
+    using S = Shape<C>;
+    const long items = (long)a.N * a.strips * a.chunks;
+    const int grid = (int)(items < 152L * S::kCtasPerSm ? items : 152L * S::kCtasPerSm);
+    if (cudaFuncSetAttribute(k_conv3x3_tc<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kSmem) != cudaSuccess)
+        return DN_ECUDA;
+    return launch(C == 32 ? "conv3x3_tc_bf16" : "conv3x3_tc64_bf16", s,
+                  [&] { k_conv3x3_tc<C><<<grid, 128, S::kSmem, s>>>(a); });
+}
+
+dn_status conv3x3_tc(const void *x, void *y, const void *wpack, const float *bias, int N, int H, int W, int C,
+                     int relu, int *err, cudaStream_t s)
 {
     ConvTcArgs a;
     a.x = static_cast<const uint4 *>(x);
@@ -346,32 +473,66 @@ dn_status conv3x3_tc(const void *x, void *y, const void *wpack, const float *bia
     a.err = err;
     a.strips = (W + kPX - 1) / kPX;
     a.chunks = (H + kItemRows - 1) / kItemRows;
-    const long items = (long)N * a.strips * a.chunks;
-    const int grid = (int)(items < 152L * kCtasPerSm ? items : 152L * kCtasPerSm);
-    const size_t smem = conv_tc_smem_bytes();
-    if (cudaFuncSetAttribute(k_conv3x3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    if (C == 32) return conv3x3_tc_c<32>(a, s);
+    if (C == 64) return conv3x3_tc_c<64>(a, s);
+    return DN_EUNSUPPORTED;
+}
+
+template <int C>
+dn_status conv_first_any(const float *pre, const float *noisy, const float *w, const float *b, void *y, int N, int cc,
+                         int H, int W, cudaStream_t s)
+{
+    const int smem = (int)sizeof(float) * (2 * cc * 324 + C * 9 * 2 * cc + C);
+    if (cudaFuncSetAttribute(k_conv_first_any<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
         return DN_ECUDA;
-    return launch("conv3x3_tc_bf16", s, [&] { k_conv3x3_tc<<<grid, 128, smem, s>>>(a); });
+    dim3 grid((W + 15) / 16, (H + 15) / 16, N);
+    return launch("conv_first_bf16", s, [&] {
+        k_conv_first_any<C><<<grid, 256, smem, s>>>(pre, noisy, w, b, static_cast<uint4 *>(y), cc, H, W);
+    });
+}
+
+template <int C>
+dn_status conv_last_any(const void *x, const float *w, const float *b, const float *pre, float *out, int N, int cc,
+                        int H, int W, cudaStream_t s)
+{
+    const int smem = 324 * (C / 8) * 16 + (int)sizeof(float) * cc * 9 * C;
+    if (cudaFuncSetAttribute(k_conv_last_any<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+        return DN_ECUDA;
+    dim3 grid((W + 15) / 16, (H + 15) / 16, N);
+    return launch("conv_last_bf16", s, [&] {
+        k_conv_last_any<C><<<grid, 256, smem, s>>>(static_cast<const uint4 *>(x), w, b, pre, out, cc, H, W);
+    });
 }
 
 dn_status conv_first_bf16(const float *pre, const float *noisy, const float *w, const float *b, void *y, int N,
-                          int H, int W, cudaStream_t s)
+                          int cc, int H, int W, int C, cudaStream_t s)
 {
-    dim3 grid((W + 31) / 32, (H + 15) / 16, N);
-    return launch("conv_first_bf16", s,
-                  [&] { k_conv_first_bf16<<<grid, 256, 0, s>>>(pre, noisy, w, b, static_cast<uint4 *>(y), H, W); });
+    if (cc == 1 && C == 32) {
+        dim3 grid((W + 31) / 32, (H + 15) / 16, N);
+        return launch("conv_first_bf16", s, [&] {
+            k_conv_first_bf16<<<grid, 256, 0, s>>>(pre, noisy, w, b, static_cast<uint4 *>(y), H, W);
+        });
+    }
+    if (C == 32) return conv_first_any<32>(pre, noisy, w, b, y, N, cc, H, W, s);
+    if (C == 64) return conv_first_any<64>(pre, noisy, w, b, y, N, cc, H, W, s);
+    return DN_EUNSUPPORTED;
 }
 
-dn_status conv_last_bf16(const void *x, const float *w, const float *b, const float *pre, float *out, int N, int H,
-                         int W, cudaStream_t s)
+dn_status conv_last_bf16(const void *x, const float *w, const float *b, const float *pre, float *out, int N, int cc,
+                         int H, int W, int C, cudaStream_t s)
 {
-    dim3 grid((W + 31) / 32, (H + 15) / 16, N);
-    const int smem = 18 * 34 * kLastPS * 16 + 9 * kCh * 4;
-    if (cudaFuncSetAttribute(k_conv_last_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
-        return DN_ECUDA;
-    return launch("conv_last_bf16", s, [&] {
-        k_conv_last_bf16<<<grid, 256, smem, s>>>(static_cast<const uint4 *>(x), w, b, pre, out, H, W);
-    });
+    if (cc == 1 && C == 32) {
+        dim3 grid((W + 31) / 32, (H + 15) / 16, N);
+        const int smem = 18 * 34 * kLastPS * 16 + 9 * kCh * 4;
+        if (cudaFuncSetAttribute(k_conv_last_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+            return DN_ECUDA;
+        return launch("conv_last_bf16", s, [&] {
+            k_conv_last_bf16<<<grid, 256, smem, s>>>(static_cast<const uint4 *>(x), w, b, pre, out, H, W);
+        });
+    }
+    if (C == 32) return conv_last_any<32>(x, w, b, pre, out, N, cc, H, W, s);
+    if (C == 64) return conv_last_any<64>(x, w, b, pre, out, N, cc, H, W, s);
+    return DN_EUNSUPPORTED;
 }
 
 }  // namespace dn

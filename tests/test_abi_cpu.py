@@ -26,6 +26,10 @@ def test_exports_every_declared_function(lib):
 
 def test_param_count_and_defaults(lib):
     assert lib.dn_cnn_param_count(10, 32) == 2 * 32 * 9 + 32 + 8 * (32 * 32 * 9 + 32) + 32 * 9 + 1
+    assert lib.dn_cnn_param_count_c(10, 32, 1) == lib.dn_cnn_param_count(10, 32)
+    # colour-native: 6 -> 64 -> ... -> 64 -> 3
+    assert lib.dn_cnn_param_count_c(16, 64, 3) == 6 * 64 * 9 + 64 + 14 * (64 * 64 * 9 + 64) + 3 * 64 * 9 + 3
+    assert lib.dn_cnn_param_count_c(10, 32, 2) == 0
     p = L.default_bm3d_params()
     assert (p.hard.patch, p.hard.step, p.hard.search, p.hard.n2) == (8, 3, 39, 16)
     assert (p.hard.tau, p.hard.tau_high, p.hard.lambda3d, p.hard.beta) == (2500.0, 5000.0, 2.700000047683716, 2.0)

@@ -125,17 +125,18 @@ def _bf16(a):
     return torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(torch.bfloat16).float().numpy()
 
 
-@pytest.mark.parametrize("N,H,W,relu", [(2, 5, 200, True), (1, 37, 128, False), (1, 3, 1, True), (3, 17, 131, True)])
-def test_conv3x3_tc_bf16_parity(oracle, N, H, W, relu):
+@pytest.mark.parametrize("N,H,W,relu,C", [(2, 5, 200, True, 32), (1, 37, 128, False, 32), (1, 3, 1, True, 32),
+                                          (3, 17, 131, True, 32), (1, 37, 131, True, 64), (2, 5, 9, False, 64)])
+def test_conv3x3_tc_bf16_parity(oracle, N, H, W, relu, C):
     """tcgen05 hidden layer vs the FP64 oracle on the same BF16-rounded inputs and
     weights: only FP32 accumulation and the final BF16 rounding differ
     (<= 2 BF16 ulps of the output plus 1e-3 of its scale)."""
     import torch
     A = api()
-    rng = np.random.default_rng(N * 100 + W)
-    x = _bf16(np.maximum(rng.normal(0, 1, (N, 32, H, W)), 0))
-    w = _bf16(rng.normal(0, 1, (32, 3, 3, 32)) * np.sqrt(2.0 / 288))
-    b = rng.normal(0, 0.1, 32).astype(np.float32)
+    rng = np.random.default_rng(N * 100 + W + C)
+    x = _bf16(np.maximum(rng.normal(0, 1, (N, C, H, W)), 0))
+    w = _bf16(rng.normal(0, 1, (C, 3, 3, C)) * np.sqrt(2.0 / (9 * C)))
+    b = rng.normal(0, 0.1, C).astype(np.float32)
     ref = oracle.conv3x3(x, w, b)
     if relu:
         ref = np.maximum(ref, 0)
@@ -164,6 +165,85 @@ def test_conv3x3_tc_bf16_more_work_items_than_ctas():
     scale = ref.abs().max()
     assert bool(((got - ref).abs() <= 2 ** -7 * ref.abs() + 1e-3 * scale).all())
     assert A.device_error() == 0
+
+
+def test_conv3x3_tc64_bf16_more_work_items_than_ctas():
+    """64-channel tcgen05 layer (one CTA per SM) with 5 x 3 x 10 = 150 work
+    items over 152 CTAs plus ragged strips/chunks, against PyTorch FP32."""
+    import torch
+    A = api()
+    N, H, W = 5, 300, 300
+    g = torch.Generator(device="cuda").manual_seed(6)
+    x = torch.relu(torch.randn(N, H, W, 64, device="cuda", generator=g)).to(torch.bfloat16)
+    w = (torch.randn(64, 3, 3, 64, device="cuda", generator=g) * (2.0 / 576) ** 0.5).to(torch.bfloat16).float()
+    b = torch.randn(64, device="cuda", generator=g) * 0.1
+    y = A.conv3x3_tc_fwd(x, w.contiguous(), b, relu=False)
+    ref = torch.nn.functional.conv2d(x.float().permute(0, 3, 1, 2), w.permute(0, 3, 1, 2), b, padding=1)
+    got = y.float().permute(0, 3, 1, 2)
+    scale = ref.abs().max()
+    assert bool(((got - ref).abs() <= 2 ** -7 * ref.abs() + 1e-3 * scale).all())
+    assert A.device_error() == 0
+
+
+def _colour_case(seed, H, W):
+    rng = np.random.default_rng(seed)
+    clean = rng.uniform(0, 255, (2, 3, H, W)).astype(np.float32)
+    noisy = (clean + rng.normal(0, 25, clean.shape)).astype(np.float32)
+    pre = (clean + rng.normal(0, 5, clean.shape)).astype(np.float32)
+    return noisy, pre
+
+
+def test_cnn_forward_fp32_colour_native_k16_matches_oracle(oracle):
+    """Colour-native network (6 -> 32 -> ... -> 3, K = 16) on the FP32 path."""
+    A = api()
+    rng = np.random.default_rng(11)
+    params = synth.he_normal_weights(12, layers=16, width=32, cin=6, cout=3)
+    params = [(w * 0.6, rng.normal(0, 0.02, b.shape).astype(np.float32)) for w, b in params]
+    noisy, pre = _colour_case(12, 23, 37)
+    out = host(A.cnn_forward(dev(noisy), dev(pre), dev(_flat(params)), 16, 32, precision=A.DN_FP32))
+    ref = oracle.cnn_forward(noisy, pre, params)
+    assert out.shape == ref.shape == (2, 3, 23, 37)
+    assert np.abs(out - ref).max() <= 1e-3 * max(1.0, np.abs(ref - pre).max())
+
+
+@pytest.mark.parametrize("layers,width,colour", [(10, 32, True), (10, 64, False), (16, 64, True)])
+def test_cnn_forward_bf16_wider_and_colour_close_to_oracle(oracle, layers, width, colour):
+    """tcgen05 path for the shapes beyond 10 x 32 grey: 64 channels (one CTA per
+    SM), colour-native input/output planes, K = 16."""
+    A = api()
+    rng = np.random.default_rng(layers * width)
+    cc = 3 if colour else 1
+    params = synth.he_normal_weights(5, layers=layers, width=width, cin=2 * cc, cout=cc)
+    params = [(w * 0.5, rng.normal(0, 0.02, b.shape).astype(np.float32)) for w, b in params]
+    noisy, pre = _colour_case(layers + width, 21, 140)
+    if not colour:
+        noisy, pre = noisy[:, 0], pre[:, 0]
+    out = host(A.cnn_forward(dev(noisy), dev(pre), dev(_flat(params)), layers, width, precision=A.DN_BF16))
+    ref = oracle.cnn_forward(noisy, pre, params)
+    r = np.abs(ref - pre).max()
+    assert np.abs(out - ref).max() <= 0.03 * r + 1e-2
+    assert A.device_error() == 0
+
+
+def test_hybrid_with_colour_native_network():
+    """denoise_hybrid with a colour-native network: RGB only (grey input is
+    refused), BF16 tcgen05 close to the FP32 path."""
+    import torch
+    from paper_2403_03488_gb300 import _lib as L
+    A = api()
+    rng = np.random.default_rng(21)
+    params = synth.he_normal_weights(21, layers=10, width=32, cin=6, cout=3)
+    params = [(w * 0.5, rng.normal(0, 0.02, b.shape).astype(np.float32)) for w, b in params]
+    wts = dev(_flat(params))
+    _, noisy = synth.make_batch([61, 62], 48, 56, [25.0, 15.0], C=3)
+    x = dev(noisy)
+    f32 = host(A.denoise_hybrid(x, [25.0, 15.0], wts, cnn_precision=A.DN_FP32, cnn_channels=3))
+    b16 = host(A.denoise_hybrid(x, [25.0, 15.0], wts, cnn_precision=A.DN_BF16, cnn_channels=3))
+    pre = host(A.denoise_bm3d(x, [25.0, 15.0]))
+    assert np.isfinite(b16).all()
+    assert np.abs(b16 - f32).max() <= 0.03 * np.abs(f32 - pre).max() + 1e-2
+    with pytest.raises(L.DenoiseError):
+        A.denoise_hybrid(x[:, :1].contiguous(), [25.0, 15.0], wts, cnn_channels=3)
 
 
 def test_cnn_forward_bf16_close_to_oracle(oracle):

@@ -193,3 +193,37 @@ def test_nlm_colour_weights_from_guide_channel(oracle):
     np.testing.assert_allclose(out[1], out[0], atol=1e-12)
     np.testing.assert_allclose(out[2], 42.0, atol=1e-12)
     np.testing.assert_allclose(out[0], oracle.nlm(g, 20.0), atol=1e-12)
+
+
+def test_cnn_forward_colour_native_block_diagonal_equals_grey_per_channel(oracle):
+    """Eq. 3 on RGB: z = [pre R, G, B, noisy R, G, B] / 255.  A colour-native
+    network whose weights never mix colour planes (layer 1 reads only planes
+    c and 3 + c into hidden block c, hidden layers are block diagonal, the
+    last layer writes block c to output c) must equal the grey network run on
+    each plane -- an independent check of the channel order and of the
+    per-plane residual."""
+    rng = np.random.default_rng(4)
+    grey = [(w * 0.7, rng.normal(0, 0.05, b.shape)) for w, b in synth.he_normal_weights(9, layers=4, width=4)]
+    wd = 4
+    colour = []
+    for l, (w, b) in enumerate(grey):
+        cout, _, _, cin = w.shape
+        big_out = 3 if l == len(grey) - 1 else 3 * wd
+        big_in = 6 if l == 0 else 3 * wd
+        W = np.zeros((big_out, 3, 3, big_in))
+        B = np.zeros(big_out)
+        for c in range(3):
+            oi = slice(c, c + 1) if l == len(grey) - 1 else slice(c * wd, (c + 1) * wd)
+            if l == 0:
+                W[oi, :, :, c] = w[:, :, :, 0]          # the pre plane of colour c
+                W[oi, :, :, 3 + c] = w[:, :, :, 1]      # the noisy plane of colour c
+            else:
+                W[oi, :, :, c * wd:(c + 1) * wd] = w
+            B[oi] = b
+        colour.append((W, B))
+    noisy = rng.uniform(0, 255, (2, 3, 11, 13))
+    pre = noisy + rng.normal(0, 5, noisy.shape)
+    out = oracle.cnn_forward(noisy, pre, colour)
+    for c in range(3):
+        ref = oracle.cnn_forward(noisy[:, c], pre[:, c], grey)
+        np.testing.assert_allclose(out[:, c], ref, rtol=0, atol=1e-10)
