@@ -212,23 +212,25 @@ __global__ void k_pack_w_tc(const float *w, uint16_t *out)
 
 // First layer of any other shape (2 cc -> C, cc = 1 or 3 colour planes):
 // z = [pre / 255 (cc planes), noisy / 255 (cc planes)], bias, ReLU, NHWC bf16
-// out.  One pixel per thread over a 16 x 16 tile, weights and the tile's
-// input planes in shared memory (plain loops; the 2 -> 32 case has its own
+// out.  One pixel per thread over a 16 x 16 tile; the C accumulators stay in
+// registers and the weights, transposed to [tap][cin][C] in shared memory, are
+// read as float4 along the output channel (the 2 -> 32 case has its own
 // kernel below).
 template <int C>
 __global__ void __launch_bounds__(256) k_conv_first_any(const float *pre, const float *noisy, const float *w,
                                                        const float *b, uint4 *y, int cc, int H, int W)
 {
-    extern __shared__ float fsm[];
+    extern __shared__ float4 fsm4[];
     const int cin = 2 * cc;
-    float *zs = fsm;                  // [cin][18][18]
-    float *ws = zs + cin * 324;       // [C][9][cin]
-    float *bs = ws + C * 9 * cin;     // [C]
+    float *ws = reinterpret_cast<float *>(fsm4);  // [9][cin][C]
+    float *zs = ws + 9 * cin * C;                 // [cin][18][18]
     const int n = blockIdx.z, X0 = blockIdx.x * 16, Y0 = blockIdx.y * 16;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const size_t HW = (size_t)H * W;
-    for (int i = threadIdx.x; i < C * 9 * cin; i += 256) ws[i] = w[i];
-    for (int i = threadIdx.x; i < C; i += 256) bs[i] = b[i];
+    for (int i = threadIdx.x; i < C * 9 * cin; i += 256) {
+        const int co = i / (9 * cin), rest = i - co * 9 * cin;  // w [co][t][ci], rest = t cin + ci
+        ws[rest * C + co] = w[i];
+    }
     for (int i = threadIdx.x; i < cin * 324; i += 256) {
         const int c = i / 324, p = i - c * 324, yy = p / 18, xx = p - yy * 18;
         const int gy = Y0 - 1 + yy, gx = X0 - 1 + xx;
@@ -238,29 +240,36 @@ __global__ void __launch_bounds__(256) k_conv_first_any(const float *pre, const 
     __syncthreads();
     const int px = X0 + tx, py = Y0 + ty;
     if (px >= W || py >= H) return;
+    float acc[C];
+#pragma unroll
+    for (int co = 0; co < C; ++co) acc[co] = b[co];
+    for (int t = 0; t < 9; ++t)
+        for (int ci = 0; ci < cin; ++ci) {
+            const float z = zs[ci * 324 + (ty + t / 3) * 18 + tx + t % 3];
+            const float4 *w4 = reinterpret_cast<const float4 *>(ws + (t * cin + ci) * C);
+#pragma unroll
+            for (int q = 0; q < C / 4; ++q) {
+                const float4 u = w4[q];
+                acc[4 * q] = fmaf(u.x, z, acc[4 * q]);
+                acc[4 * q + 1] = fmaf(u.y, z, acc[4 * q + 1]);
+                acc[4 * q + 2] = fmaf(u.z, z, acc[4 * q + 2]);
+                acc[4 * q + 3] = fmaf(u.w, z, acc[4 * q + 3]);
+            }
+        }
     uint4 *dst = y + ((size_t)n * HW + (size_t)py * W + px) * (C / 8);
-    for (int c0 = 0; c0 < C; c0 += 8) {
+#pragma unroll
+    for (int q = 0; q < C / 8; ++q) {
         uint32_t pk[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            float acc[2];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int co = c0 + 2 * e + h;
-                float a = bs[co];
-                for (int t = 0; t < 9; ++t)
-                    for (int ci = 0; ci < cin; ++ci)
-                        a = fmaf(ws[(co * 9 + t) * cin + ci], zs[ci * 324 + (ty + t / 3) * 18 + tx + t % 3], a);
-                acc[h] = fmaxf(a, 0.0f);
-            }
-            pk[e] = tc::pack_bf16x2(acc[0], acc[1]);
-        }
-        dst[c0 / 8] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        for (int e = 0; e < 4; ++e)
+            pk[e] = tc::pack_bf16x2(fmaxf(acc[8 * q + 2 * e], 0.0f), fmaxf(acc[8 * q + 2 * e + 1], 0.0f));
+        dst[q] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
     }
 }
 
 // Last layer of any other shape (C -> cc) + bias, then out = pre + 255 r per
-// colour plane (Eq. 2).  One pixel per thread over a 16 x 16 tile.
+// colour plane (Eq. 2).  One pixel per thread over a 16 x 16 tile; weights
+// transposed to [tap][channel][cc] so each input channel feeds all cc outputs.
 template <int C>
 __global__ void __launch_bounds__(256) k_conv_last_any(const uint4 *x, const float *w, const float *b,
                                                       const float *pre, float *out, int cc, int H, int W)
@@ -268,37 +277,53 @@ __global__ void __launch_bounds__(256) k_conv_last_any(const uint4 *x, const flo
     extern __shared__ uint4 lsm[];
     constexpr int K = C / 8;
     uint4 *xs = lsm;                                        // [324][K]
-    float *ws = reinterpret_cast<float *>(xs + 324 * K);    // [cc][9][C]
+    float *ws = reinterpret_cast<float *>(xs + 324 * K);    // [9][C][cc]
     const int n = blockIdx.z, X0 = blockIdx.x * 16, Y0 = blockIdx.y * 16;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const size_t HW = (size_t)H * W;
-    for (int i = threadIdx.x; i < cc * 9 * C; i += 256) ws[i] = w[i];
+    for (int i = threadIdx.x; i < cc * 9 * C; i += 256) {
+        const int co = i / (9 * C), rest = i - co * 9 * C;  // w [co][t][ci], rest = t C + ci
+        ws[rest * cc + co] = w[i];
+    }
     for (int i = threadIdx.x; i < 324 * K; i += 256) {
         const int p = i / K, ck = i % K, yy = p / 18, xx = p - yy * 18;
         const int gy = Y0 - 1 + yy, gx = X0 - 1 + xx;
-        xs[i] = (gy >= 0 && gy < H && gx >= 0 && gx < W) ? x[((size_t)n * HW + (size_t)gy * W + gx) * K + ck]
-                                                         : make_uint4(0u, 0u, 0u, 0u);
+        if (gy >= 0 && gy < H && gx >= 0 && gx < W)
+            tc::cp_async16(tc::smem_u32(&xs[i]), x + ((size_t)n * HW + (size_t)gy * W + gx) * K + ck);
+        else
+            xs[i] = make_uint4(0u, 0u, 0u, 0u);
     }
+    tc::cp_async_commit();
+    tc::cp_async_wait<0>();
     __syncthreads();
     const int px = X0 + tx, py = Y0 + ty;
     if (px >= W || py >= H) return;
-    for (int co = 0; co < cc; ++co) {
-        float acc = b[co];
-        for (int t = 0; t < 9; ++t) {
-            const int p = (ty + t / 3) * 18 + tx + t % 3;
-            for (int ck = 0; ck < K; ++ck) {
-                const uint4 q = xs[p * K + ck];
-                const uint32_t u[4] = {q.x, q.y, q.z, q.w};
+    float acc[3] = {b[0], cc > 1 ? b[1] : 0.0f, cc > 2 ? b[2] : 0.0f};
+    for (int t = 0; t < 9; ++t) {
+        const int p = (ty + t / 3) * 18 + tx + t % 3;
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    acc = fmaf(ws[(co * 9 + t) * C + ck * 8 + 2 * e], tc::bf16_lo(u[e]), acc);
-                    acc = fmaf(ws[(co * 9 + t) * C + ck * 8 + 2 * e + 1], tc::bf16_hi(u[e]), acc);
-                }
+        for (int ck = 0; ck < K; ++ck) {
+            const uint4 q = xs[p * K + ck];
+            const uint32_t u[4] = {q.x, q.y, q.z, q.w};
+            const float *wt = ws + (t * C + ck * 8) * cc;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float lo = tc::bf16_lo(u[e]), hi = tc::bf16_hi(u[e]);
+#pragma unroll
+                for (int co = 0; co < 3; ++co)
+                    if (co < cc) {
+                        acc[co] = fmaf(wt[(2 * e) * cc + co], lo, acc[co]);
+                        acc[co] = fmaf(wt[(2 * e + 1) * cc + co], hi, acc[co]);
+                    }
             }
         }
-        const size_t at = ((size_t)n * cc + co) * HW + (size_t)py * W + px;
-        out[at] = fmaf(255.0f, acc, pre[at]);
     }
+#pragma unroll
+    for (int co = 0; co < 3; ++co)
+        if (co < cc) {
+            const size_t at = ((size_t)n * cc + co) * HW + (size_t)py * W + px;
+            out[at] = fmaf(255.0f, acc[co], pre[at]);
+        }
 }
 
 // Layer 1 (2 -> 32) + bias + ReLU: pre/noisy planes (0..255) -> NHWC bf16.
@@ -482,7 +507,7 @@ template <int C>
 dn_status conv_first_any(const float *pre, const float *noisy, const float *w, const float *b, void *y, int N, int cc,
                          int H, int W, cudaStream_t s)
 {
-    const int smem = (int)sizeof(float) * (2 * cc * 324 + C * 9 * 2 * cc + C);
+    const int smem = (int)sizeof(float) * (C * 9 * 2 * cc + 2 * cc * 324);
     if (cudaFuncSetAttribute(k_conv_first_any<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
         return DN_ECUDA;
     dim3 grid((W + 15) / 16, (H + 15) / 16, N);
