@@ -80,6 +80,20 @@ def test_match_parity_hard(oracle, H, W, sigmas):
         check_match(oracle, idx[b], n[b], om, noisy[b, 0], taus[b])
 
 
+@pytest.mark.parametrize("step,search,n2,H,W", [(4, 39, 16, 61, 70), (2, 21, 8, 40, 37), (5, 15, 32, 33, 52),
+                                                (1, 9, 4, 20, 19)])
+def test_match_parity_other_steps(oracle, step, search, n2, H, W):
+    """Grid steps other than 3 take the any-step kernel (register-blocked over
+    8 candidates, same distance association); lists exact vs the oracle."""
+    A = api()
+    _, noisy = synth.make_batch([14], H, W, 25.0)
+    p = A.default_bm3d_params().hard
+    p.step, p.search, p.n2 = step, search, n2
+    idx, n = A.bm3d_match(dev(noisy[:, 0]), [2500.0], p)
+    om = oracle.match(noisy[0, 0], oracle.Pass(step=step, search=search, n2=n2, tau=2500.0))
+    check_match(oracle, host(idx)[0], host(n)[0], om, noisy[0, 0], 2500.0)
+
+
 @pytest.mark.parametrize("n2", [1, 2, 8, 32])
 def test_match_parity_group_sizes_on_basic(oracle, n2):
     A = api()

@@ -36,6 +36,19 @@ def test_nlm_parity(oracle, C, H, W, sigmas):
         assert err <= TOL, (b, err)
 
 
+@pytest.mark.parametrize("C,patch,search", [(1, 5, 11), (1, 9, 25), (3, 3, 15)])
+def test_nlm_parity_other_patch_and_search(oracle, C, patch, search):
+    """Non-default neighbourhood and window sizes (the kernel's halos and tile
+    loops follow the parameters)."""
+    A = api()
+    _, noisy = synth.make_batch([66], 45, 71, 25.0, C=C)
+    p = A.default_nlm_params()
+    p.patch, p.search = patch, search
+    out = host(A.denoise_nlm(dev(noisy), [25.0], p))
+    ref = oracle.nlm_image(noisy[0], 25.0, patch, search)
+    assert np.abs(out[0] - ref).max() <= TOL
+
+
 def test_nlm_full_size_sampled(oracle):
     """8 x 512 x 512 (the plain-method batch): 200 sampled pixels against the
     oracle run on crops holding each pixel's search window and patches."""
