@@ -22,9 +22,10 @@
 // pass, two groups of at most 16 patches at once): lane k owns patch k and
 // computes its 8x8 DCT with an even/odd fast DCT in two passes through its
 // row of a per-warp transpose buffer (rows of 65 floats, conflict-free both
-// ways), two 1D transforms per packed FP32x2 instruction; for the group
-// transform each lane owns two coefficient positions across all patches and
-// runs the Walsh-Hadamard butterflies for both in packed registers; the
+// ways), two 1D transforms per packed FP32x2 instruction (scalar for the noisy
+// patches of the second pass, whose gains then hold 64 registers); for the
+// group transform each lane owns two coefficient positions across all patches
+// and runs the Walsh-Hadamard butterflies for both in packed registers; the
 // inverse goes back the same way, and the warp then aggregates patch by patch
 // with its lanes spread over the 64 pixels.
 #include <cmath>
@@ -80,28 +81,6 @@ __device__ __forceinline__ void dct8(float (&v)[NV], const DctK &K)
     v[O + 7 * S] = fmaf(K.h7, d0, fmaf(-K.h5, d1, fmaf(K.h3, d2, -(K.h1 * d3))));
 }
 
-// inverse: x[m] = sum_u a_u X[u] cos(pi (2m+1) u / 16)
-template <int O, int S, int NV>
-__device__ __forceinline__ void idct8(float (&v)[NV], const DctK &K)
-{
-    const float X0 = v[O], X1 = v[O + S], X2 = v[O + 2 * S], X3 = v[O + 3 * S];
-    const float X4 = v[O + 4 * S], X5 = v[O + 5 * S], X6 = v[O + 6 * S], X7 = v[O + 7 * S];
-    const float a = K.r8 * (X0 + X4), b = K.r8 * (X0 - X4);
-    const float p = fmaf(K.h2, X2, K.h6 * X6), q = fmaf(K.h6, X2, -(K.h2 * X6));
-    const float e0 = a + p, e3 = a - p, e1 = b + q, e2 = b - q;
-    const float o0 = fmaf(K.h1, X1, fmaf(K.h3, X3, fmaf(K.h5, X5, K.h7 * X7)));
-    const float o1 = fmaf(K.h3, X1, fmaf(-K.h7, X3, fmaf(-K.h1, X5, -(K.h5 * X7))));
-    const float o2 = fmaf(K.h5, X1, fmaf(-K.h1, X3, fmaf(K.h7, X5, K.h3 * X7)));
-    const float o3 = fmaf(K.h7, X1, fmaf(-K.h5, X3, fmaf(K.h3, X5, -(K.h1 * X7))));
-    v[O] = e0 + o0;
-    v[O + 7 * S] = e0 - o0;
-    v[O + S] = e1 + o1;
-    v[O + 6 * S] = e1 - o1;
-    v[O + 2 * S] = e2 + o2;
-    v[O + 5 * S] = e2 - o2;
-    v[O + 3 * S] = e3 + o3;
-    v[O + 4 * S] = e3 - o3;
-}
 
 // ---- packed versions: two independent 8-point transforms per instruction ----
 
@@ -133,7 +112,9 @@ __device__ __forceinline__ DctK2 pack_dct()
     return P;
 }
 
-// dct8 / idct8 with the same operations, on two vectors at once.
+// The 8-point DCT (the same operations as dct8) and its inverse, on two vectors
+// at once:
+//   inverse x[m] = sum_u a_u X[u] cos(pi (2m+1) u / 16).
 __device__ __forceinline__ void dct8_2(f2 (&v)[8], const DctK2 &K)
 {
     const f2 s0 = f2_add(v[0], v[7]), d0 = f2_sub(v[0], v[7]);
