@@ -1,24 +1,26 @@
 // Residual CNN forward in BF16 on the 5th-generation tensor cores (sm_103a).
 //
-// Network of Sec. II (Fig. 1, Eq. 2-3): z = [pre/255, noisy/255];
-// layer 1 (2 -> 32) and the last layer (32 -> 1, plus out = pre + 255 r) are
-// thin and run on CUDA cores; every 32 -> 32 hidden layer is an implicit GEMM
-// on tcgen05: M = 128 output pixels (one row segment), N = 32 output channels,
-// K = 9 taps x 32 input channels, FP32 accumulation in TMEM, BF16 activations
-// in HBM (NHWC, 64 bytes per pixel).
+// Network of Sec. II (Fig. 1, Eq. 2-3): z = [pre/255, noisy/255] (cc planes
+// each: cc = 1 for the grey network, 3 for a colour-native one); layer 1
+// (2 cc -> C) and the last layer (C -> cc, plus out = pre + 255 r) are thin and
+// run on CUDA cores; every C -> C hidden layer (C = 32 or 64) is an implicit
+// GEMM on tcgen05: M = 128 output pixels (one row segment), N = C output
+// channels, K = 9 taps x C input channels, FP32 accumulation in TMEM, BF16
+// activations in HBM (NHWC, 2 C bytes per pixel).
 //
 // Hidden-layer kernel: persistent CTAs take work items of 32 output rows of
-// a 128-pixel column strip.  Packed weights (18 KB) stay in shared memory;
-// input rows (130 pixels incl. halo) are staged in a ring of 6 slots in the
-// K-major core-matrix layout [channel chunk of 8][pixel][8 channels], so the A
-// operand of tap (dy, dx) is the staged row y+dy-1 shifted by dx pixels: a
-// descriptor offset, no im2col.  Rows are fetched with cp.async three rows
-// ahead of use; per output row one thread issues 18 MMAs (9 taps x 2 K-steps
-// of 16) into one of two TMEM accumulator buffers and commits them to that
-// buffer's mbarrier, and while the tensor cores work on row y all 128 threads
-// (thread = pixel = TMEM lane) drain row y-1: read 32 accumulators, add the
-// bias, apply ReLU and store 64 B of BF16.  Each input row is read from HBM
-// once per strip and item (plus 2 halo rows per 32).
+// a 128-pixel column strip.  Packed weights (18 KB at C = 32, 72 KB at 64)
+// stay in shared memory; input rows (130 pixels incl. halo) are staged in a
+// ring of 6 slots in the K-major core-matrix layout [channel chunk of 8]
+// [pixel][8 channels], so the A operand of tap (dy, dx) is the staged row
+// y+dy-1 shifted by dx pixels: a descriptor offset, no im2col.  Rows are
+// fetched with cp.async three rows ahead of use; per output row one thread
+// issues 9 C / 16 MMAs (9 taps x C/16 K-steps of 16) into one of two TMEM
+// accumulator buffers and commits them to that buffer's mbarrier, and while
+// the tensor cores work on row y all 128 threads (thread = pixel = TMEM lane)
+// drain row y-1: read C accumulators, add the bias, apply ReLU and store 2 C
+// bytes of BF16.  Each input row is read from HBM once per strip and item
+// (plus 2 halo rows per 32).
 #include <cuda_bf16.h>
 
 #include "common.cuh"
