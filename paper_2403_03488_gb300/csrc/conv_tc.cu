@@ -24,6 +24,7 @@
 #include <cuda_bf16.h>
 
 #include "common.cuh"
+#include "f32x2.cuh"
 #include "tc.cuh"
 
 namespace dn {
@@ -330,20 +331,20 @@ __global__ void __launch_bounds__(256) k_conv_last_any(const uint4 *x, const flo
 
 // Layer 1 (2 -> 32) + bias + ReLU: pre/noisy planes (0..255) -> NHWC bf16.
 // CTA: 32 x 16 output pixels; thread (tx, ty) computes pixels tx and tx + 16
-// of row ty (lanes on consecutive pixels), reading each output channel's 18
-// weights as float4 (padded rows).
+// of row ty (lanes on consecutive pixels), two output channels per packed
+// FP32x2 FMA (weights transposed so a channel pair is one 64-bit load).
 __global__ void __launch_bounds__(256) k_conv_first_bf16(const float *pre, const float *noisy, const float *w,
                                                         const float *b, uint4 *y, int H, int W)
 {
     __shared__ float zs[2][18][48];  // row stride 16 (mod 32): the two half-warps use disjoint banks
-    __shared__ __align__(16) float ws[kCh][20];
-    __shared__ float bs[kCh];
+    __shared__ __align__(16) float ws[18][kCh];  // transposed: the weights of one input tap, channel-contiguous
+    __shared__ __align__(8) float bs[kCh];
     const int n = blockIdx.z, X0 = blockIdx.x * 32, Y0 = blockIdx.y * 16;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const size_t HW = (size_t)H * W;
-    for (int i = threadIdx.x; i < kCh * 20; i += 256) {
-        const int c = i / 20, k = i - c * 20;
-        ws[c][k] = k < 18 ? w[c * 18 + k] : 0.0f;
+    for (int i = threadIdx.x; i < kCh * 18; i += 256) {
+        const int c = i / 18, k = i - c * 18;
+        ws[k][c] = w[i];
     }
     if (threadIdx.x < kCh) bs[threadIdx.x] = b[threadIdx.x];
     // raw planes (scaled by 1/255 at use), all loads in flight at once
@@ -361,37 +362,32 @@ __global__ void __launch_bounds__(256) k_conv_first_bf16(const float *pre, const
     __syncthreads();
     const int py = Y0 + ty;
     if (py >= H || X0 + tx >= W) return;
-    float v0[18], v1[18];
+    // the inputs of the thread's two pixels, each broadcast to both lanes of a packed pair
+    f2 v0[18], v1[18];
 #pragma unroll
-    for (int t = 0; t < 9; ++t) {
-        v0[2 * t] = zs[0][ty + t / 3][tx + t % 3] * (1.0f / 255.0f);
-        v0[2 * t + 1] = zs[1][ty + t / 3][tx + t % 3] * (1.0f / 255.0f);
-        v1[2 * t] = zs[0][ty + t / 3][tx + 16 + t % 3] * (1.0f / 255.0f);
-        v1[2 * t + 1] = zs[1][ty + t / 3][tx + 16 + t % 3] * (1.0f / 255.0f);
-    }
+    for (int t = 0; t < 9; ++t)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const float a = zs[c][ty + t / 3][tx + t % 3] * (1.0f / 255.0f);
+            const float e = zs[c][ty + t / 3][tx + 16 + t % 3] * (1.0f / 255.0f);
+            v0[2 * t + c] = f2_pack(a, a);
+            v1[2 * t + c] = f2_pack(e, e);
+        }
     uint32_t p0[16], p1[16];
+    const f2 *w2 = reinterpret_cast<const f2 *>(&ws[0][0]);
+    const f2 *b2 = reinterpret_cast<const f2 *>(bs);
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
-        float a0 = bs[2 * c], a1 = bs[2 * c + 1], b0 = a0, b1 = a1;
-        const float4 *w0 = reinterpret_cast<const float4 *>(ws[2 * c]);
-        const float4 *w1 = reinterpret_cast<const float4 *>(ws[2 * c + 1]);
+        // channels (2c, 2c+1) in the two lanes, same accumulation order as one channel at a time
+        f2 a = b2[c], bb = b2[c];
 #pragma unroll
-        for (int q = 0; q < 5; ++q) {
-            const float4 u0 = w0[q], u1 = w1[q];
-            const float e0[4] = {u0.x, u0.y, u0.z, u0.w}, e1[4] = {u1.x, u1.y, u1.z, u1.w};
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const int k = 4 * q + r;
-                if (k < 18) {
-                    a0 = fmaf(e0[r], v0[k], a0);
-                    a1 = fmaf(e1[r], v0[k], a1);
-                    b0 = fmaf(e0[r], v1[k], b0);
-                    b1 = fmaf(e1[r], v1[k], b1);
-                }
-            }
+        for (int k = 0; k < 18; ++k) {
+            const f2 wk = w2[k * (kCh / 2) + c];
+            a = f2_fma(wk, v0[k], a);
+            bb = f2_fma(wk, v1[k], bb);
         }
-        p0[c] = tc::pack_bf16x2(fmaxf(a0, 0.0f), fmaxf(a1, 0.0f));
-        p1[c] = tc::pack_bf16x2(fmaxf(b0, 0.0f), fmaxf(b1, 0.0f));
+        p0[c] = tc::pack_bf16x2(fmaxf(f2_lo(a), 0.0f), fmaxf(f2_hi(a), 0.0f));
+        p1[c] = tc::pack_bf16x2(fmaxf(f2_lo(bb), 0.0f), fmaxf(f2_hi(bb), 0.0f));
     }
     uint4 *dst = y + ((size_t)n * HW + (size_t)py * W + X0 + tx) * 4;
 #pragma unroll
