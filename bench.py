@@ -33,8 +33,9 @@ METRIC = "MPix/s BM3D+CNN at <=0.05 dB PSNR loss vs FP32 plain; served p50/p99 m
 FP32_PEAK_TFLOPS_NOTE = "FP32 ALU peak = 152 SM x 128 lanes x 2 FLOP/FMA x 2.07 GHz = 80.5 TFLOP/s"
 
 
-def workload_name(bm3d, cnn):
-    return "hybrid BM3D(%s)+CNN(10x32, %s) denoise, %d grey %dx%d synthetic images, sigma=25" % (bm3d, cnn, B, H, W)
+def workload_name(bm3d, cnn, prefilter="bm3d"):
+    pre = "BM3D(%s)" % bm3d if prefilter == "bm3d" else "NLM(fp32)"
+    return "hybrid %s+CNN(10x32, %s) denoise, %d grey %dx%d synthetic images, sigma=25" % (pre, cnn, B, H, W)
 
 
 # ---------------------------------------------------------------------------
@@ -119,6 +120,11 @@ def algorithmic(kernel, launches_per_step, batch):
     if kernel.startswith("bm3d_match"):
         pairs = match_pairs(H, W) * batch / (launches_per_step / 2.0)
         return "alu", "TFLOP/s", 192.0 * pairs, fp32_peak, FP32_PEAK_TFLOPS_NOTE + " (derived, not measured)"
+    if kernel.startswith("nlm_fp32"):
+        # per pixel and search offset: difference + square (2), separable 7 + 7 box sums (12), weight (4:
+        # subtract, clamp, scale, exp) and the two weighted accumulations (4)
+        flops = 22.0 * 441 * H * W * batch / launches_per_step
+        return "alu", "TFLOP/s", flops, fp32_peak, FP32_PEAK_TFLOPS_NOTE + " (derived, not measured)"
     if kernel.startswith("conv3x3_fwd_fp32"):
         flops = 2.0 * H * W * batch * (2 * 32 * 9 + 8 * 32 * 32 * 9 + 32 * 9) / launches_per_step
         return "alu", "TFLOP/s", flops, fp32_peak, FP32_PEAK_TFLOPS_NOTE + " (derived, not measured)"
@@ -154,15 +160,17 @@ def run_ours(args):
     weights, wsrc = load_weights(dev)
     bprec = api.DN_BF16 if args.bm3d == "bf16" else api.DN_FP32
     prec = api.DN_BF16 if args.cnn == "bf16" else api.DN_FP32
-    bp = api.default_bm3d_params(precision=bprec)
+    nlm = args.prefilter == "nlm"
+    pf = api.DN_PREFILTER_NLM if nlm else api.DN_PREFILTER_BM3D
+    bp = api.default_nlm_params() if nlm else api.default_bm3d_params(precision=bprec)
     cnn = api.make_cnn(weights, 10, 32, prec)
-    ws = torch.empty(api.hybrid_workspace_bytes(B, 1, H, W, api.DN_PREFILTER_BM3D, bp, cnn), dtype=torch.uint8,
-                     device=dev)
+    ws = torch.empty(api.hybrid_workspace_bytes(B, 1, H, W, pf, bp, cnn), dtype=torch.uint8, device=dev)
     sse = torch.empty(B, dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def step():
-        api.denoise_hybrid(noisy_d, SIGMA, weights, prefilter_params=bp, cnn_precision=prec, out=out_d, workspace=ws)
+        api.denoise_hybrid(noisy_d, SIGMA, weights, prefilter=pf, prefilter_params=bp, cnn_precision=prec, out=out_d,
+                           workspace=ws)
         api.error_reduce(out_d, clean_d)
 
     for _ in range(args.warmup):
@@ -203,11 +211,11 @@ def run_ours(args):
     mse = float(sse_d.sum().item()) / (B * H * W)
     psnr_out = 10 * np.log10(255.0 ** 2 / mse)
     # the FP32 plain path on the same batch (untimed), for the PSNR-loss criterion
-    plain = api.denoise_hybrid(noisy_d, SIGMA, weights, prefilter_params=api.default_bm3d_params(),
-                               cnn_precision=api.DN_FP32)
+    plain = api.denoise_hybrid(noisy_d, SIGMA, weights, prefilter=pf,
+                               prefilter_params=bp if nlm else api.default_bm3d_params(), cnn_precision=api.DN_FP32)
     sse_p, _ = api.error_reduce(plain, clean_d)
     psnr_plain = 10 * np.log10(255.0 ** 2 / (float(sse_p.sum().item()) / (B * H * W)))
-    bm3d_only = api.denoise_bm3d(noisy_d, SIGMA, bp)
+    bm3d_only = api.denoise_nlm(noisy_d, SIGMA, bp) if nlm else api.denoise_bm3d(noisy_d, SIGMA, bp)
     sse_b, _ = api.error_reduce(bm3d_only, clean_d)
     psnr_bm3d = 10 * np.log10(255.0 ** 2 / (float(sse_b.sum().item()) / (B * H * W)))
     del plain, bm3d_only
@@ -217,7 +225,8 @@ def run_ours(args):
     out_h = torch.empty_like(noisy_h).pin_memory()
     for _ in range(2):
         x = noisy_h.to(dev, non_blocking=True)
-        api.denoise_hybrid(x, SIGMA, weights, prefilter_params=bp, cnn_precision=prec, out=out_d, workspace=ws)
+        api.denoise_hybrid(x, SIGMA, weights, prefilter=pf, prefilter_params=bp, cnn_precision=prec, out=out_d,
+                           workspace=ws)
         out_h.copy_(out_d, non_blocking=True)
     torch.cuda.synchronize()
     if world > 1:
@@ -230,7 +239,8 @@ def run_ours(args):
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
         x = noisy_h.to(dev, non_blocking=True)
-        api.denoise_hybrid(x, SIGMA, weights, prefilter_params=bp, cnn_precision=prec, out=out_d, workspace=ws)
+        api.denoise_hybrid(x, SIGMA, weights, prefilter=pf, prefilter_params=bp, cnn_precision=prec, out=out_d,
+                           workspace=ws)
         out_h.copy_(out_d, non_blocking=True)
         e1.record()
         e1.synchronize()
@@ -256,7 +266,7 @@ def run_ours(args):
             dist.destroy_process_group()
         return
     line = {
-        "metric": METRIC,
+        "metric": METRIC if args.prefilter == "bm3d" else METRIC.replace("BM3D+CNN", "NLM+CNN"),
         "value": round(value, 3),
         "unit": "MPix/s",
         "n_gpus": world,
@@ -268,13 +278,14 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "+".join(sorted({"f32" if bprec == api.DN_FP32 else "bf16", "f32" if prec == api.DN_FP32 else "bf16"})),
         "data": "synthetic (seeded piecewise-smooth + gratings + repeated tile, AWGN sigma=25)",
-        "config": {"workload": workload_name(args.bm3d, args.cnn), "global_batch": B * world, "image": [H, W],
+        "config": {"workload": workload_name(args.bm3d, args.cnn, args.prefilter), "global_batch": B * world,
+                   "image": [H, W],
                    "channels": 1, "sigma": SIGMA, "cnn": "10 layers x 32 ch, " + wsrc,
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": "replicas (dp%d)" % world},
         "psnr_db": round(psnr_out, 3),
         "psnr_fp32_plain_db": round(psnr_plain, 3),
         "psnr_loss_vs_fp32_plain_db": round(psnr_plain - psnr_out, 4),
-        "psnr_bm3d_only_db": round(psnr_bm3d, 3),
+        ("psnr_nlm_only_db" if args.prefilter == "nlm" else "psnr_bm3d_only_db"): round(psnr_bm3d, 3),
         "e2e": {"value": round(e2e_value, 3), "unit": "MPix/s", "h2d_bytes_per_step": int(noisy_h.numel() * 4),
                 "d2h_bytes_per_step": int(out_h.numel() * 4)},
         "gpu_launches": int(launches),
@@ -415,6 +426,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--bm3d", default="fp32", choices=["fp32", "bf16"], help="BM3D matching/transform precision")
     ap.add_argument("--cnn", default="bf16", choices=["fp32", "bf16"], help="CNN precision")
+    ap.add_argument("--prefilter", default="bm3d", choices=["bm3d", "nlm"],
+                    help="nonlocal prefilter of the hybrid (nlm: the lighter NL-means + CNN variant)")
     ap.add_argument("--cpu-side", type=int, default=1024)
     ap.add_argument("--ref-side", type=int, default=192)
     ap.add_argument("--no-cpu-baseline", action="store_true")
