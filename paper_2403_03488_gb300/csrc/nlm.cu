@@ -43,10 +43,13 @@ __device__ __forceinline__ int reflect_hs(int i, int L, int r)
     return max(0, min(L - 1, i));
 }
 
+// RT > 0: patch radius fixed at compile time (unrolled box sums, constant
+// strides); RT = 0: the radius from the arguments.
+template <int RT>
 __global__ void __launch_bounds__(kThreads) k_nlm(NlmArgs a)
 {
     extern __shared__ float sm[];
-    const int r = a.r, hs = a.hs, P = 2 * r + 1;
+    const int r = RT > 0 ? RT : a.r, hs = a.hs, P = 2 * r + 1;
     const int GW = kTX + 2 * r + 2 * hs, GH = kTY + 2 * r + 2 * hs;  // guide region
     const int DW = kTX + 2 * r, DH = kTY + 2 * r;                    // difference image
     const int VW = kTX + 2 * hs, VH = kTY + 2 * hs;                  // value regions (other channels)
@@ -81,24 +84,53 @@ __global__ void __launch_bounds__(kThreads) k_nlm(NlmArgs a)
     float acc[3] = {0.0f, 0.0f, 0.0f};
     float wsum = 0.0f;
 
+    // this thread's elements of the difference image (at most 2 x 2): the
+    // reference pixel does not depend on the offset
+    constexpr int kMaxR = RT > 0 ? RT : 7;
+    constexpr int kEY = (kTY + 2 * kMaxR + kTY - 1) / kTY, kEX = (kTX + 2 * kMaxR + kTX - 1) / kTX;
+    float s0[kEY][kEX];
+#pragma unroll
+    for (int ey = 0; ey < kEY; ++ey)
+#pragma unroll
+        for (int ex = 0; ex < kEX; ++ex) {
+            const int yy = ty + ey * kTY, xx = tx + ex * kTX;
+            s0[ey][ex] = (yy < DH && xx < DW) ? S[(yy + hs) * GW + xx + hs] : 0.0f;
+        }
+
     for (int dy = -hs; dy <= hs; ++dy)
         for (int dx = -hs; dx <= hs; dx += 2) {
             // squared differences for offsets dx (low lane) and dx + 1 (high lane)
-            for (int yy = ty; yy < DH; yy += kTY)
-                for (int xx = tx; xx < DW; xx += kTX) {
-                    const float s0 = S[(yy + hs) * GW + xx + hs];
-                    const float *q = S + (yy + hs + dy) * GW + xx + hs + dx;
-                    D[yy * DW + xx] = f2_sqd(f2_pack(s0, s0), f2_pack(q[0], q[1]));
+#pragma unroll
+            for (int ey = 0; ey < kEY; ++ey)
+#pragma unroll
+                for (int ex = 0; ex < kEX; ++ex) {
+                    const int yy = ty + ey * kTY, xx = tx + ex * kTX;
+                    if (yy < DH && xx < DW) {
+                        const float *q = S + (yy + hs + dy) * GW + xx + hs + dx;
+                        D[yy * DW + xx] = f2_sqd(f2_pack(s0[ey][ex], s0[ey][ex]), f2_pack(q[0], q[1]));
+                    }
                 }
             __syncthreads();
-            for (int xx = tx; xx < DW; xx += kTX) {
-                f2 v = D[ty * DW + xx];
-                for (int t = 1; t < P; ++t) v = f2_add(v, D[(ty + t) * DW + xx]);
-                V[ty * DW + xx] = v;
+#pragma unroll
+            for (int ex = 0; ex < kEX; ++ex) {
+                const int xx = tx + ex * kTX;
+                if (xx < DW) {
+                    const f2 *d = D + ty * DW + xx;
+                    f2 v = d[0];
+#pragma unroll
+                    for (int t = 1; t < (RT > 0 ? 2 * RT + 1 : 1); ++t) v = f2_add(v, d[t * DW]);
+                    if (RT == 0)
+                        for (int t = 1; t < P; ++t) v = f2_add(v, d[t * DW]);
+                    V[ty * DW + xx] = v;
+                }
             }
             __syncthreads();
-            f2 d2 = V[ty * DW + tx];
-            for (int t = 1; t < P; ++t) d2 = f2_add(d2, V[ty * DW + tx + t]);
+            const f2 *vr = V + ty * DW + tx;
+            f2 d2 = vr[0];
+#pragma unroll
+            for (int t = 1; t < (RT > 0 ? 2 * RT + 1 : 1); ++t) d2 = f2_add(d2, vr[t]);
+            if (RT == 0)
+                for (int t = 1; t < P; ++t) d2 = f2_add(d2, vr[t]);
             d2 = f2_mul(d2, inv_np);
             const int qy = py + dy;
             if (qy >= 0 && qy < H) {
@@ -144,7 +176,9 @@ dn_status nlm_launch(const float *in, float *out, int B, int C, int H, int W, co
     size_t smem = sizeof(float) * ((size_t)((GH * GW + 1) & ~1) + 2 * (size_t)DH * DW + 2 * (size_t)kTY * DW +
                                    (size_t)(C - 1) * VH * VW);
     if (smem > 200 * 1024) return DN_EUNSUPPORTED;
-    if (cudaFuncSetAttribute(k_nlm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    void (*kern)(NlmArgs) = a.r == 1 ? k_nlm<1> : a.r == 2 ? k_nlm<2> : a.r == 3 ? k_nlm<3> : a.r == 4 ? k_nlm<4>
+                          : a.r == 5 ? k_nlm<5> : k_nlm<0>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return DN_ECUDA;
     for (int b0 = 0; b0 < B; b0 += kChunk) {
         int nb = B - b0 < kChunk ? B - b0 : kChunk;
@@ -156,7 +190,7 @@ dn_status nlm_launch(const float *in, float *out, int B, int C, int H, int W, co
             a.inv_h2[i] = 1.0f / (h * h);
         }
         dim3 grid((W + kTX - 1) / kTX, (H + kTY - 1) / kTY, nb);
-        DN_TRY(launch("nlm_fp32", s, [&] { k_nlm<<<grid, kThreads, smem, s>>>(a); }));
+        DN_TRY(launch("nlm_fp32", s, [&] { kern<<<grid, kThreads, smem, s>>>(a); }));
     }
     return DN_OK;
 }
