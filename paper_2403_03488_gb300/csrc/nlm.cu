@@ -158,6 +158,195 @@ __global__ void __launch_bounds__(kThreads) k_nlm(NlmArgs a)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Register-resident variant (grey images, patch radius R = 2..4).
+//
+// A warp owns TY = 2R + 2 output rows and 128 difference-image columns, four
+// adjacent columns per lane; warps of a CTA are stacked vertically and share
+// one staged guide region (fixed row pitch, 16-byte aligned per lane).  For
+// each pair of offsets (dx, dx + 1), packed in the two FP32x2 lanes, a warp
+// sweeps the 2P = TY + 2R rows of squared differences it needs:
+//   * vertical P-row box sums of the TY output rows with one split at row P
+//     (suffix sums of rows 0..P-1, prefix sums of rows P..2P-1, one add per
+//     window: 3(P - 1) adds for P + 1 windows instead of (P + 1)(P - 1));
+//   * horizontal P-column sums of the lane's four columns from its own
+//     suffix sums and the prefix sums of the next two lanes (shuffles), so
+//     the last lanes of a warp are halo: a CTA writes OW < 128 columns;
+//   * weights w = 2^min(k (2 sigma^2 - d2), 0), k = log2(e) / h^2, folded
+//     into one packed FMA whose additive term is -inf for a candidate
+//     outside the search window or the image.
+// Accumulators stay in registers for the whole offset loop.
+constexpr int kRW = 4;         // warps per CTA
+constexpr int kPitch = 176;    // staged row pitch in floats: 130 + 2 * 20 + 3 rounded up to 16
+
+template <int R>
+struct RegGeo {
+    static constexpr int P = 2 * R + 1, TY = P + 1;
+    static constexpr int OW = R <= 2 ? 124 : 120;  // output columns per CTA
+    static constexpr int RowsPerCta = kRW * TY;
+};
+
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Columns 4..4+m-1 after a lane's own four columns are covered by the next
+// lane's prefix sums (m <= 4) or by the next lane's total plus the prefix of
+// the lane after it.  Which prefix sums a lane must fetch:
+template <int R>
+__host__ __device__ constexpr bool need_from1(int j)  // prefix j (1..4) of lane + 1
+{
+    bool n = false;
+    for (int k = 0; k < 4; ++k) {
+        const int m = k + 2 * R - 3;
+        n = n || (m <= 4 ? m == j : j == 4);
+    }
+    return n;
+}
+template <int R>
+__host__ __device__ constexpr bool need_from2(int j)  // prefix j (1..4) of lane + 2
+{
+    bool n = false;
+    for (int k = 0; k < 4; ++k) n = n || (k + 2 * R - 3 - 4 == j);
+    return n;
+}
+
+template <int R>
+__global__ void __launch_bounds__(kRW * 32, R <= 3 ? 3 : 2) k_nlm_reg(NlmArgs a)
+{
+    using G = RegGeo<R>;
+    constexpr int P = G::P, TY = G::TY;
+    extern __shared__ float4 sm4[];
+    float *S = reinterpret_cast<float *>(sm4);
+    const int hs = a.hs, H = a.H, W = a.W;
+    const int A = (4 - (hs & 3)) & 3;  // column pad: makes the lane's reference columns 16-byte aligned
+    const int SR = G::RowsPerCta + 2 * R + 2 * hs;
+    const int b = blockIdx.z, X0 = blockIdx.x * G::OW, Y0 = blockIdx.y * G::RowsPerCta;
+    const float *g = a.in + (size_t)b * H * W;
+    {
+        const int xs = X0 - R - hs - A, ys = Y0 - R - hs;
+        for (int i = threadIdx.x; i < SR * kPitch; i += kRW * 32) {
+            const int yy = i / kPitch, xx = i - yy * kPitch;
+            S[i] = g[(size_t)reflect_hs(ys + yy, H, R) * W + reflect_hs(xs + xx, W, R)];
+        }
+    }
+    __syncthreads();
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int Yw = Y0 + warp * TY;
+    // reference value of difference row i, column 4 lane + c: pb[i * kPitch + c]
+    const float *pb = S + (warp * TY + hs) * kPitch + 4 * lane + hs + A;
+    const float kk = a.inv_h2[b] * 1.44269504088896341f;
+    const float kc = kk * a.two_s2[b];
+    const f2 kn = f2_pack(-kk * a.inv_np, -kk * a.inv_np);
+    const float ninf = __int_as_float(0xff800000);
+
+    float acc[TY][4], ws[TY][4];
+#pragma unroll
+    for (int k = 0; k < TY; ++k)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[k][c] = ws[k][c] = 0.0f;
+
+    // offsets (dx, dx + 1) with dx + hs + A even, so candidate pairs load as
+    // aligned 8-byte words; the lane outside [-hs, hs] is masked
+    const int dx0 = -hs - (hs & 1);
+    for (int pr = 0; pr <= hs; ++pr) {
+        const int dx = dx0 + 2 * pr;
+        f2 cadd[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int qx = X0 + 4 * lane + c + dx;
+            const bool lo = dx >= -hs && (unsigned)qx < (unsigned)W;
+            const bool hi = dx + 1 <= hs && (unsigned)(qx + 1) < (unsigned)W;
+            cadd[c] = f2_pack(lo ? kc : ninf, hi ? kc : ninf);
+        }
+        for (int dy = -hs; dy <= hs; ++dy) {
+            const float *qb = pb + dy * kPitch + dx;
+            auto drow = [&](int i, f2 (&d)[4]) {
+                const float4 p = *reinterpret_cast<const float4 *>(pb + i * kPitch);
+                const float2 q0 = *reinterpret_cast<const float2 *>(qb + i * kPitch);
+                const float2 q1 = *reinterpret_cast<const float2 *>(qb + i * kPitch + 2);
+                const float q4 = qb[i * kPitch + 4];
+                d[0] = f2_sqd(f2_pack(p.x, p.x), f2_pack(q0.x, q0.y));
+                d[1] = f2_sqd(f2_pack(p.y, p.y), f2_pack(q0.y, q1.x));
+                d[2] = f2_sqd(f2_pack(p.z, p.z), f2_pack(q1.x, q1.y));
+                d[3] = f2_sqd(f2_pack(p.w, p.w), f2_pack(q1.y, q4));
+            };
+            // output row k from its vertical box sums v[4]
+            auto emit = [&](int k, const f2 (&v)[4]) {
+                if ((unsigned)(Yw + k + dy) >= (unsigned)H) return;  // warp-uniform
+                f2 pre[5], suf[4];
+                pre[1] = v[0];
+                pre[2] = f2_add(pre[1], v[1]);
+                pre[3] = f2_add(pre[2], v[2]);
+                pre[4] = f2_add(pre[3], v[3]);
+                suf[3] = v[3];
+                suf[2] = f2_add(v[2], suf[3]);
+                suf[1] = f2_add(v[1], suf[2]);
+                suf[0] = f2_add(v[0], suf[1]);
+                f2 n1[5], n2[5];
+#pragma unroll
+                for (int j = 1; j <= 4; ++j) {
+                    if (need_from1<R>(j)) n1[j].v = __shfl_down_sync(0xffffffffu, pre[j].v, 1);
+                    if (need_from2<R>(j)) n2[j].v = __shfl_down_sync(0xffffffffu, pre[j].v, 2);
+                }
+                // candidate values: row k + R of the sweep, columns c + R + (0, 1)
+                const float *vb = qb + (k + R) * kPitch + (R & ~1);
+                const float2 v0 = *reinterpret_cast<const float2 *>(vb);
+                const float2 v1 = *reinterpret_cast<const float2 *>(vb + 2);
+                const float2 v2 = *reinterpret_cast<const float2 *>(vb + 4);
+                const float vv[6] = {v0.x, v0.y, v1.x, v1.y, v2.x, v2.y};
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int m = c + 2 * R - 3;
+                    const f2 nb = m <= 4 ? n1[m] : f2_add(n1[4], n2[m - 4]);
+                    const f2 box = f2_add(suf[c], nb);
+                    const f2 t = f2_fma(box, kn, cadd[c]);
+                    const float wl = ex2_approx(fminf(f2_lo(t), 0.0f));
+                    const float wh = ex2_approx(fminf(f2_hi(t), 0.0f));
+                    const int o = c + (R & 1);
+                    acc[k][c] = fmaf(wh, vv[o + 1], fmaf(wl, vv[o], acc[k][c]));
+                    ws[k][c] += wl + wh;
+                }
+            };
+            f2 sf[P][4];
+#pragma unroll
+            for (int i = 0; i < P; ++i) drow(i, sf[i]);
+#pragma unroll
+            for (int i = P - 2; i >= 0; --i)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) sf[i][c] = f2_add(sf[i][c], sf[i + 1][c]);
+            emit(0, sf[0]);
+            f2 pre[4];
+#pragma unroll
+            for (int i = P; i < 2 * P; ++i) {
+                f2 d[4];
+                drow(i, d);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) pre[c] = i == P ? d[c] : f2_add(pre[c], d[c]);
+                const int k = i - P + 1;
+                f2 v[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) v[c] = k < P ? f2_add(sf[k][c], pre[c]) : pre[c];
+                emit(k, v);
+            }
+        }
+    }
+    float *o = a.out + (size_t)b * H * W;
+#pragma unroll
+    for (int k = 0; k < TY; ++k) {
+        const int py = Yw + k;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int j = 4 * lane + c, px = X0 + j;
+            if (j < G::OW && px < W && py < H) o[(size_t)py * W + px] = acc[k][c] / ws[k][c];
+        }
+    }
+}
+
 }  // namespace
 
 dn_status nlm_launch(const float *in, float *out, int B, int C, int H, int W, const float *sig_guide,
@@ -175,6 +364,26 @@ dn_status nlm_launch(const float *in, float *out, int B, int C, int H, int W, co
     const int VW = kTX + 2 * a.hs, VH = kTY + 2 * a.hs;
     size_t smem = sizeof(float) * ((size_t)((GH * GW + 1) & ~1) + 2 * (size_t)DH * DW + 2 * (size_t)kTY * DW +
                                    (size_t)(C - 1) * VH * VW);
+    if (C == 1 && a.r >= 2 && a.r <= 4 && a.hs <= 20) {
+        const int RT = a.r, TY = 2 * RT + 2, OW = RT <= 2 ? 124 : 120;
+        const size_t sm_reg = sizeof(float) * (size_t)(kRW * TY + 2 * RT + 2 * a.hs) * kPitch;
+        void (*kr)(NlmArgs) = RT == 2 ? k_nlm_reg<2> : RT == 3 ? k_nlm_reg<3> : k_nlm_reg<4>;
+        if (cudaFuncSetAttribute(kr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_reg) != cudaSuccess)
+            return DN_ECUDA;
+        for (int b0 = 0; b0 < B; b0 += kChunk) {
+            int nb = B - b0 < kChunk ? B - b0 : kChunk;
+            a.in = in + (size_t)b0 * H * W;
+            a.out = out + (size_t)b0 * H * W;
+            for (int i = 0; i < nb; ++i) {
+                float sg = sig_guide[b0 + i], h = p.h_over_sigma * sg;
+                a.two_s2[i] = 2.0f * sg * sg;
+                a.inv_h2[i] = 1.0f / (h * h);
+            }
+            dim3 grid((W + OW - 1) / OW, (H + kRW * TY - 1) / (kRW * TY), nb);
+            DN_TRY(launch("nlm_fp32", s, [&] { kr<<<grid, kRW * 32, sm_reg, s>>>(a); }));
+        }
+        return DN_OK;
+    }
     if (smem > 200 * 1024) return DN_EUNSUPPORTED;
     void (*kern)(NlmArgs) = a.r == 1 ? k_nlm<1> : a.r == 2 ? k_nlm<2> : a.r == 3 ? k_nlm<3> : a.r == 4 ? k_nlm<4>
                           : a.r == 5 ? k_nlm<5> : k_nlm<0>;

@@ -36,10 +36,12 @@ def test_nlm_parity(oracle, C, H, W, sigmas):
         assert err <= TOL, (b, err)
 
 
-@pytest.mark.parametrize("C,patch,search", [(1, 5, 11), (1, 9, 25), (3, 3, 15)])
+@pytest.mark.parametrize("C,patch,search", [(1, 5, 11), (1, 9, 25), (3, 3, 15), (1, 7, 19), (1, 7, 41), (1, 5, 1),
+                                             (1, 3, 21), (1, 11, 21)])
 def test_nlm_parity_other_patch_and_search(oracle, C, patch, search):
-    """Non-default neighbourhood and window sizes (the kernel's halos and tile
-    loops follow the parameters)."""
+    """Non-default neighbourhood and window sizes (the kernels' halos, tile
+    loops and masked offset lanes follow the parameters; odd and even search
+    radii, the largest window, a window of one offset)."""
     A = api()
     _, noisy = synth.make_batch([66], 45, 71, 25.0, C=C)
     p = A.default_nlm_params()
