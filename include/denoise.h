@@ -49,7 +49,17 @@ typedef enum {
     DN_EUNSUPPORTED = -5  /* valid but not implemented combination               */
 } dn_status;
 
-typedef enum { DN_FP32 = 0, DN_BF16 = 1 } dn_precision;
+/* Arithmetic of the BM3D stages (dn_bm3d_params.precision is a bit set):
+ *   DN_FP32        every stage in FP32 on the CUDA cores;
+ *   DN_BF16        the 2D patch transforms of both filtering passes as 64 x 64
+ *                  contractions on the tensor cores (BF16 operands, FP32
+ *                  accumulation; patches centred on their FP32 mean first,
+ *                  which stays in FP32); group transform, shrinkage and
+ *                  aggregation in FP32;
+ *   DN_BF16_MATCH  block matching with the BF16 tensor-core prefilter and an
+ *                  exact FP32 re-rank (match lists identical to FP32).
+ * For the CNN (dn_cnn.precision) DN_BF16 selects the tcgen05 BF16 layers. */
+typedef enum { DN_FP32 = 0, DN_BF16 = 1, DN_BF16_MATCH = 2 } dn_precision;
 typedef enum { DN_PREFILTER_BM3D = 0, DN_PREFILTER_NLM = 1 } dn_prefilter;
 
 /* One BM3D pass.  Distances are mean squared differences over the patch. */
@@ -67,7 +77,7 @@ typedef struct {
 typedef struct {
     dn_bm3d_pass hard;    /* first pass: hard thresholding  (n2 16, tau 2500) */
     dn_bm3d_pass wiener;  /* second pass: Wiener filtering  (n2 32, tau 400)  */
-    int precision;        /* dn_precision of the group transforms / matching   */
+    int precision;        /* dn_precision bits: DN_BF16, DN_BF16_MATCH          */
     int sigma_regime;     /* 0: tau_high above sigma 40; 1: tau at every sigma */
 } dn_bm3d_params;
 
@@ -170,8 +180,9 @@ dn_status denoise_bm3d_noalloc(const float *noisy, float *out, int B, int C, int
  *      then the other candidates with d <= tau in ascending (d, y*W + x)
  *      order; -1 past the kept count.
  * n:   device int32 [B][Ry][Rx]: group size min(n2, 2^floor(log2 #kept)).
- * precision: DN_FP32 (exhaustive FP32) or DN_BF16 (BF16 tensor-core
- * prefilter with a proven margin, survivors re-ranked exactly in FP32). */
+ * precision: DN_FP32 (exhaustive FP32), or DN_BF16_MATCH (DN_BF16 is taken
+ * as the same): BF16 tensor-core prefilter with a proven margin, survivors
+ * re-ranked exactly in FP32, so the lists equal the FP32 ones. */
 dn_status dn_bm3d_match(const float *guide, size_t plane_stride, int B, int H, int W, const dn_bm3d_pass *p,
                         const float *tau, int precision, int *idx, int *n, void *workspace, size_t ws_bytes,
                         dn_stream_t stream);
@@ -195,6 +206,9 @@ dn_status dn_bm3d_match_cross_terms(const float *guide, int H, int W, const dn_b
  * img: device [B][C][H][W] (already in the filtering colour space);
  * sigma_c: host [B*C] per-channel noise std; idx/n as produced by
  * dn_bm3d_match with p->n2; basic: device [B][C][H][W].
+ * precision: DN_FP32 (FP32 SIMT transforms) or DN_BF16 (2D transforms on the
+ * tensor cores, see dn_precision; DN_EDEVICE-class failures set the device
+ * status word, see dn_device_error).
  * workspace >= dn_bm3d_filter_workspace_bytes(B, C, H, W). */
 dn_status dn_bm3d_filter_hard(const float *img, const int *idx, const int *n, int B, int C, int H, int W,
                               const float *sigma_c, const dn_bm3d_pass *p, int precision, float *basic,

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "libdenoise.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "denoise.h")
 
 DN_OK, DN_EINVAL, DN_ENOMEM, DN_ECUDA, DN_EDEVICE, DN_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
-DN_FP32, DN_BF16 = 0, 1
+DN_FP32, DN_BF16, DN_BF16_MATCH = 0, 1, 2
 DN_PREFILTER_BM3D, DN_PREFILTER_NLM = 0, 1
 
 

@@ -12,13 +12,13 @@ from typing import Optional, Sequence
 import torch
 
 from . import _lib as L
-from ._lib import (BM3DParams, BM3DPass, CNN, DN_BF16, DN_FP32, DN_PREFILTER_BM3D, DN_PREFILTER_NLM, NLMParams,
-                   check, default_bm3d_params, default_nlm_params, farr)
+from ._lib import (BM3DParams, BM3DPass, CNN, DN_BF16, DN_BF16_MATCH, DN_FP32, DN_PREFILTER_BM3D,
+                   DN_PREFILTER_NLM, NLMParams, check, default_bm3d_params, default_nlm_params, farr)
 
 __all__ = ["denoise_bm3d", "denoise_nlm", "denoise_hybrid", "bm3d_match", "bm3d_filter_hard", "bm3d_filter_wiener",
            "rgb_to_ycc", "ycc_to_rgb", "error_reduce", "conv3x3_fwd", "conv3x3_bwd_data", "conv3x3_bwd_weight",
            "cnn_forward", "l1_residual_grad", "adam_step", "grid", "default_bm3d_params", "default_nlm_params",
-           "cnn_param_count", "profile", "DN_FP32", "DN_BF16", "DN_PREFILTER_BM3D", "DN_PREFILTER_NLM"]
+           "cnn_param_count", "profile", "DN_FP32", "DN_BF16", "DN_BF16_MATCH", "DN_PREFILTER_BM3D", "DN_PREFILTER_NLM"]
 
 
 def _vp(t: Optional[torch.Tensor]):

@@ -45,7 +45,8 @@ bool valid_pass(const dn_bm3d_pass *p)
 
 bool valid_bm3d(const dn_bm3d_params *p)
 {
-    return p && valid_pass(&p->hard) && valid_pass(&p->wiener) && (p->precision == DN_FP32 || p->precision == DN_BF16) &&
+    return p && valid_pass(&p->hard) && valid_pass(&p->wiener) && p->precision >= 0 &&
+           p->precision <= (DN_BF16 | DN_BF16_MATCH) &&
            (p->sigma_regime == 0 || p->sigma_regime == 1);
 }
 
@@ -96,7 +97,7 @@ Bm3dWs bm3d_layout(void *base, int B, int C, int H, int W, const dn_bm3d_params 
     w.acc = cv.take<float>(kAccBytesPerPixel / sizeof(float) * (size_t)B * C * HW);
     w.basic = cv.take<float>((size_t)B * C * HW);
     const size_t m1 = match_tc_workspace_bytes(B, H, W, p->hard), m2 = match_tc_workspace_bytes(B, H, W, p->wiener);
-    w.mws = p->precision == DN_BF16 ? cv.take<int>((m1 > m2 ? m1 : m2) / sizeof(int)) : nullptr;
+    w.mws = (p->precision & DN_BF16_MATCH) ? cv.take<int>((m1 > m2 ? m1 : m2) / sizeof(int)) : nullptr;
     w.bytes = cv.off;
     return w;
 }
@@ -148,9 +149,9 @@ CnnWs cnn_layout(void *base, int N, int H, int W, const dn_cnn *c)
     return w;
 }
 
-// Block matching in the requested precision: the BF16 tensor-core prefilter
-// with exact FP32 re-rank (same result as FP32) when its tiling supports the
-// parameters, the exhaustive FP32 kernel otherwise.
+// Block matching in the requested precision: with DN_BF16_MATCH the BF16
+// tensor-core prefilter with exact FP32 re-rank (same result as FP32) when its
+// tiling supports the parameters, the exhaustive FP32 kernel otherwise.
 bool tc_match_supported(const dn_bm3d_pass &p)
 {
     return p.n2 >= 2 && 7 * p.step + 2 * (p.search / 2) + 1 <= 64 && match_tc_smem_bytes(p.step, p.search) <= 200 * 1024;
@@ -159,12 +160,26 @@ bool tc_match_supported(const dn_bm3d_pass &p)
 dn_status match_any(const float *guide, size_t plane, int B, int H, int W, const dn_bm3d_pass &p, const float *tau,
                     int precision, int *idx, int *n, int *mws, cudaStream_t s)
 {
-    if (precision == DN_BF16 && mws && tc_match_supported(p)) {
+    if ((precision & DN_BF16_MATCH) && mws && tc_match_supported(p)) {
         int *err = device_error_ptr();
         if (!err) return DN_ECUDA;
         return match_tc(guide, plane, B, H, W, p, tau, idx, n, err, mws, s);
     }
     return match_fp32(guide, plane, B, H, W, p, tau, idx, n, s);
+}
+
+// Collaborative filtering (pass 1, or pass 2 when `wiener`) with the 2D
+// transforms on the tensor cores when `tc`, FP32 SIMT otherwise.
+dn_status filter_any(bool wiener, bool tc, const float *img, const float *basic, const int *idx, const int *n, int B,
+                     int C, int H, int W, const float *sig, const dn_bm3d_pass &p, float *acc, cudaStream_t s)
+{
+    if (tc) {
+        int *err = device_error_ptr();
+        if (!err) return DN_ECUDA;
+        return filter_tc(wiener, img, basic, idx, n, B, C, H, W, sig, p, acc, err, s);
+    }
+    return wiener ? filter_wiener_fp32(img, basic, idx, n, B, C, H, W, sig, p, acc, s)
+                  : filter_hard_fp32(img, idx, n, B, C, H, W, sig, p, acc, s);
 }
 
 dn_status run_bm3d(const float *noisy, float *out, int B, int C, int H, int W, const float *sigma,
@@ -189,12 +204,13 @@ dn_status run_bm3d(const float *noisy, float *out, int B, int C, int H, int W, c
         // pass 1: match on channel 0 of the noisy image, hard thresholding
         DN_TRY(match_any(x + off, (size_t)C * HW, nb, H, W, p->hard, tau1, p->precision, w.idx, w.n, w.mws, s));
         if (cudaMemsetAsync(w.acc, 0, kAccBytesPerPixel * Nb, s) != cudaSuccess) return DN_ECUDA;
-        DN_TRY(filter_hard_fp32(x + off, w.idx, w.n, nb, C, H, W, sig, p->hard, w.acc, s));
+        const bool tc = (p->precision & DN_BF16) != 0;
+        DN_TRY(filter_any(false, tc, x + off, nullptr, w.idx, w.n, nb, C, H, W, sig, p->hard, w.acc, s));
         DN_TRY(normalize(w.acc, w.basic + off, nb, C, H, W, p->hard.beta, s));
         // pass 2: match on channel 0 of the basic estimate, Wiener filtering
         DN_TRY(match_any(w.basic + off, (size_t)C * HW, nb, H, W, p->wiener, tau2, p->precision, w.idx, w.n, w.mws, s));
         if (cudaMemsetAsync(w.acc, 0, kAccBytesPerPixel * Nb, s) != cudaSuccess) return DN_ECUDA;
-        DN_TRY(filter_wiener_fp32(x + off, w.basic + off, w.idx, w.n, nb, C, H, W, sig, p->wiener, w.acc, s));
+        DN_TRY(filter_any(true, tc, x + off, w.basic + off, w.idx, w.n, nb, C, H, W, sig, p->wiener, w.acc, s));
         DN_TRY(normalize(w.acc, (C == 3 ? w.ycc : out) + off, nb, C, H, W, p->wiener.beta, s));
     }
     if (C == 3) DN_TRY(colour(w.ycc, out, B, H, W, 1, s));
@@ -414,7 +430,8 @@ const char *dn_strerror(dn_status st)
 
 size_t dn_bm3d_match_workspace_bytes(int B, int H, int W, const dn_bm3d_pass *p, int precision)
 {
-    if (precision != DN_BF16 || !valid_image(B, 1, H, W, 8) || !valid_pass(p)) return 0;
+    if ((precision != DN_BF16 && precision != DN_BF16_MATCH) || !valid_image(B, 1, H, W, 8) || !valid_pass(p))
+        return 0;
     return match_tc_workspace_bytes(B, H, W, *p);
 }
 
@@ -428,11 +445,11 @@ dn_status dn_bm3d_match(const float *guide, size_t plane_stride, int B, int H, i
         return DN_EINVAL;
     for (int b = 0; b < B; ++b)
         if (!(tau[b] > 0.0f)) return DN_EINVAL;
-    if (precision != DN_FP32 && precision != DN_BF16) return DN_EINVAL;
+    if (precision != DN_FP32 && precision != DN_BF16 && precision != DN_BF16_MATCH) return DN_EINVAL;
     const size_t need = dn_bm3d_match_workspace_bytes(B, H, W, p, precision);
     if (need > 0 && (!workspace || ws_bytes < need)) return DN_ENOMEM;
-    return match_any(guide, plane_stride, B, H, W, *p, tau, precision, idx, n, static_cast<int *>(workspace),
-                     (cudaStream_t)stream);
+    return match_any(guide, plane_stride, B, H, W, *p, tau, precision == DN_FP32 ? DN_FP32 : DN_BF16_MATCH, idx, n,
+                     static_cast<int *>(workspace), (cudaStream_t)stream);
     DN_GUARD_END
 }
 
@@ -468,7 +485,7 @@ static dn_status filter_entry(bool wiener, const float *img, const float *basic,
         return DN_EINVAL;
     for (int i = 0; i < B * C; ++i)
         if (!(sigma_c[i] > 0.0f) || !(sigma_c[i] <= 255.0f)) return DN_EINVAL;
-    if (precision != DN_FP32) return precision == DN_BF16 ? DN_EUNSUPPORTED : DN_EINVAL;
+    if (precision != DN_FP32 && precision != DN_BF16) return DN_EINVAL;
     const size_t need = dn_bm3d_filter_workspace_bytes(B, C, H, W);
     if (!ws || ws_bytes < need) return DN_ENOMEM;
     float *acc = static_cast<float *>(ws);
@@ -479,10 +496,8 @@ static dn_status filter_entry(bool wiener, const float *img, const float *basic,
         if (cudaMemsetAsync(acc, 0, kAccBytesPerPixel * (size_t)nb * C * HW, s) != cudaSuccess) return DN_ECUDA;
         const int *ib = idx + (size_t)b0 * R * p->n2;
         const int *nbp = n + (size_t)b0 * R;
-        if (wiener)
-            DN_TRY(filter_wiener_fp32(img + off, basic + off, ib, nbp, nb, C, H, W, sigma_c + (size_t)b0 * C, *p, acc, s));
-        else
-            DN_TRY(filter_hard_fp32(img + off, ib, nbp, nb, C, H, W, sigma_c + (size_t)b0 * C, *p, acc, s));
+        DN_TRY(filter_any(wiener, precision == DN_BF16, img + off, wiener ? basic + off : nullptr, ib, nbp, nb, C, H, W,
+                          sigma_c + (size_t)b0 * C, *p, acc, s));
         DN_TRY(normalize(acc, out + off, nb, C, H, W, p->beta, s));
     }
     return DN_OK;

@@ -84,6 +84,13 @@ dn_status filter_hard_fp32(const float *img, const int *idx, const int *n, int B
                            const float *sig, const dn_bm3d_pass &p, float *acc, cudaStream_t s);
 dn_status filter_wiener_fp32(const float *noisy, const float *basic, const int *idx, const int *n, int B, int C,
                              int H, int W, const float *sig, const dn_bm3d_pass &p, float *acc, cudaStream_t s);
+// The same two passes with the 2D transforms on the tensor cores (BF16
+// operands, FP32 accumulation); err: device status word (3 = a wait timed out).
+dn_status filter_tc(bool wiener, const float *img, const float *basic, const int *idx, const int *n, int B, int C,
+                    int H, int W, const float *sig, const dn_bm3d_pass &p, float *acc, int *err, cudaStream_t s);
+// Shared memory of the tensor-core filter (0: the search window is too large);
+// *tr receives the side of its tile of reference positions.
+size_t filter_tc_smem_bytes(bool wiener, int step, int search, int *tr);
 // out = num / den with den = the Kaiser window (parameter beta) correlated with wsum
 dn_status normalize(const float *acc, float *out, int B, int C, int H, int W, float beta, cudaStream_t s);
 dn_status colour(const float *in, float *out, int B, int H, int W, int inverse, cudaStream_t s);

@@ -297,7 +297,7 @@ def test_match_tc_prefilter_equals_fp32_and_oracle(oracle, H, W, sigma, n2, tau,
     p = A.default_bm3d_params().hard
     p.n2 = n2
     i32, n32 = A.bm3d_match(dev(g), [tau, tau], p, precision=A.DN_FP32)
-    itc, ntc = A.bm3d_match(dev(g), [tau, tau], p, precision=A.DN_BF16)
+    itc, ntc = A.bm3d_match(dev(g), [tau, tau], p, precision=A.DN_BF16_MATCH)
     i32, n32, itc, ntc = host(i32), host(n32), host(itc), host(ntc)
     np.testing.assert_array_equal(ntc, n32)
     for b in range(2):
@@ -354,7 +354,7 @@ def test_bm3d_with_tc_matching_equals_fp32():
     _, noisy = synth.make_batch([90, 91], 150, 170, [25.0, 50.0])
     x = dev(noisy)
     a = host(A.denoise_bm3d(x, [25.0, 50.0], A.default_bm3d_params(precision=A.DN_FP32)))
-    b = host(A.denoise_bm3d(x, [25.0, 50.0], A.default_bm3d_params(precision=A.DN_BF16)))
+    b = host(A.denoise_bm3d(x, [25.0, 50.0], A.default_bm3d_params(precision=A.DN_BF16_MATCH)))
     assert np.array_equal(a, b)
     assert A.device_error() == 0
 
