@@ -454,19 +454,80 @@ __device__ __forceinline__ float wiener_group(const FilterArgs &a, const Window 
 // The weight goes to the patch positions (lane k adds it for row k); for num
 // the warp walks the patches and its lanes cover the 64 pixels of each (lane
 // l: pixels l and l+32), so the window atomics of one instruction hit 4 rows
-// of 8 consecutive words (no bank conflict).
+// of 8 consecutive words (no bank conflict).  When every patch of the group
+// lies inside the window (always, for lists from this library's matcher) the
+// patches go in chunks of up to 8: the chunk's terms are formed first and
+// one warp vote picks the branch-free fast path for the whole chunk, so the
+// chunk's conversions and atomics are independent and overlap.
+
+// Terms of patches [k0, k0+K) scaled by 2^13 (wk carries the exact factor),
+// then their exact fixed-point additions to the window; wo = the window
+// offset of the lane's own patch, poff = the lane's pixel offset.
+template <int K>
+__device__ __forceinline__ void agg_chunk(const FilterArgs &a, const Window &win, const float *T, size_t cbase, int k0,
+                                          int lane, f2 wk, int wo, int poff, int gpos, int pg)
+{
+    f2 t[K];
+    bool fast = true;
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+        const int k = k0 + q;
+        t[q] = f2_mul(wk, f2_pack(T[k * kTS + lane], T[k * kTS + lane + 32]));
+        fast = fast && fabsf(f2_lo(t[q])) < 4194304.0f && fabsf(f2_hi(t[q])) < 4194304.0f;  // |term| < 512
+    }
+    if (__all_sync(0xffffffffu, fast)) {
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+            const int o = __shfl_sync(0xffffffffu, wo, k0 + q) + poff;
+            long long x0, x1;
+            fix_t2(t[q], x0, x1);
+            atomicAdd(win.num + o, (unsigned long long)x0);
+            atomicAdd(win.num + o + 4 * win.RS, (unsigned long long)x1);
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+            const int o = __shfl_sync(0xffffffffu, wo, k0 + q) + poff;
+            const size_t g = cbase + (size_t)__shfl_sync(0xffffffffu, gpos, k0 + q) + pg;
+            const Fix f0 = to_fixed(f2_lo(t[q]) * (1.0f / 8192.0f)), f1 = to_fixed(f2_hi(t[q]) * (1.0f / 8192.0f));
+            atomicAdd(win.num + o, f0.lo);
+            atomicAdd(win.num + o + 4 * win.RS, f1.lo);
+            if (f0.hi != 0) atomicAdd(a.num_hi + g, (unsigned long long)f0.hi);
+            if (f1.hi != 0) atomicAdd(a.num_hi + g + 4 * (size_t)a.W, (unsigned long long)f1.hi);
+        }
+    }
+}
+
 __device__ __forceinline__ void aggregate(const FilterArgs &a, const Window &win, const float *T, size_t cbase, int s,
                                           int n, int lane, int py, int px, float w, const float (&ka)[2])
 {
     const float vs = 1.0f / (float)n;  // the unnormalised group transform's factor n (exact power of two)
-    if (lane >= s && lane < s + n) {
+    const bool mine = lane >= s && lane < s + n;
+    if (mine) {
         const Fix fw = to_fixed(w);
         const size_t q = cbase + (size_t)py * a.W + px;
         atomicAdd(a.wsum + q, fw.lo);
         if (fw.hi != 0) atomicAdd(a.wsum_hi + q, (unsigned long long)fw.hi);
     }
-    const f2 wk = f2_pack(w * ka[0] * vs, w * ka[1] * vs);
     const int i0 = lane >> 3, j = lane & 7;
+    const int ly = py - win.Y0, lx = px - win.X0;
+    const bool in = ly >= 0 && ly + 8 <= win.RH && lx >= 0 && lx + 8 <= win.RW;
+    const unsigned gm = n == 32 ? 0xffffffffu : ((1u << n) - 1u) << s;
+    if ((__ballot_sync(0xffffffffu, in && mine) & gm) == gm) {
+        // w kai / n times the fixed-point scale 2^13 (exact powers of two)
+        const f2 wk = f2_pack(w * ka[0] * vs * 8192.0f, w * ka[1] * vs * 8192.0f);
+        const int wo = ly * win.RS + lx, poff = i0 * win.RS + j, gpos = py * a.W + px, pg = i0 * a.W + j;
+        switch (n) {
+            case 1: agg_chunk<1>(a, win, T, cbase, s, lane, wk, wo, poff, gpos, pg); break;
+            case 2: agg_chunk<2>(a, win, T, cbase, s, lane, wk, wo, poff, gpos, pg); break;
+            case 4: agg_chunk<4>(a, win, T, cbase, s, lane, wk, wo, poff, gpos, pg); break;
+            default:
+                for (int k0 = s; k0 < s + n; k0 += 8) agg_chunk<8>(a, win, T, cbase, k0, lane, wk, wo, poff, gpos, pg);
+                break;
+        }
+        return;
+    }
+    const f2 wk = f2_pack(w * ka[0] * vs, w * ka[1] * vs);
 #pragma unroll 2
     for (int k = s; k < s + n; ++k) {
         const int yk = __shfl_sync(0xffffffffu, py, k), xk = __shfl_sync(0xffffffffu, px, k);
