@@ -158,7 +158,7 @@ def run_ours(args):
     clean_d = torch.from_numpy(clean).to(dev)
     out_d = torch.empty_like(noisy_d)
     weights, wsrc = load_weights(dev)
-    bprec = api.DN_BF16 if args.bm3d == "bf16" else api.DN_FP32
+    bprec = bm3d_precision(args)
     prec = api.DN_BF16 if args.cnn == "bf16" else api.DN_FP32
     nlm = args.prefilter == "nlm"
     pf = api.DN_PREFILTER_NLM if nlm else api.DN_PREFILTER_BM3D
@@ -305,13 +305,18 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def bm3d_precision(args):
+    from paper_2403_03488_gb300 import api
+    return {"fp32": api.DN_FP32, "bf16": api.DN_BF16, "bf16+match": api.DN_BF16 | api.DN_BF16_MATCH}[args.bm3d]
+
+
 def serving_replay(args):
     """Open-loop Poisson replay through the continuous-batching server (the
     served p50/p99 part of the metric), for the fast path and, on the same
     trace, the FP32 plain path."""
     from paper_2403_03488_gb300 import api, serve
     fast = serve.replay(rate=args.serve_rate, n=args.serve_requests, side=(128, 2048),
-                        bm3d_precision=api.DN_BF16 if args.bm3d == "bf16" else api.DN_FP32,
+                        bm3d_precision=bm3d_precision(args),
                         cnn_precision=api.DN_BF16 if args.cnn == "bf16" else api.DN_FP32)
     plain = serve.replay(rate=args.serve_rate, n=args.serve_requests, side=(128, 2048),
                          bm3d_precision=api.DN_FP32, cnn_precision=api.DN_FP32, warm=False)
@@ -325,7 +330,7 @@ def serving_replay(args):
         # the same trace shape at 60 % of the served rate: latency without a growing queue
         rate = args.serve_rate * 0.6 * fast["served_mpix_s"] / fast["offered_mpix_s"]
         stable = serve.replay(rate=rate, n=args.serve_requests, side=(128, 2048),
-                              bm3d_precision=api.DN_BF16 if args.bm3d == "bf16" else api.DN_FP32,
+                              bm3d_precision=bm3d_precision(args),
                               cnn_precision=api.DN_BF16 if args.cnn == "bf16" else api.DN_FP32, warm=False)
         out["stable_load"] = {k: round(stable[k], 3) for k in keys}
         out["stable_load"].update({"rate_per_s": round(rate, 1), "offered_mpix_s": round(stable["offered_mpix_s"], 1)})
@@ -424,7 +429,9 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--bm3d", default="fp32", choices=["fp32", "bf16"], help="BM3D matching/transform precision")
+    ap.add_argument("--bm3d", default="fp32", choices=["fp32", "bf16", "bf16+match"],
+                    help="BM3D precision: fp32 SIMT; bf16 = 2D transforms on the tensor cores; bf16+match = also "
+                         "the BF16 tensor-core matching prefilter (exact FP32 re-rank)")
     ap.add_argument("--cnn", default="bf16", choices=["fp32", "bf16"], help="CNN precision")
     ap.add_argument("--prefilter", default="bm3d", choices=["bm3d", "nlm"],
                     help="nonlocal prefilter of the hybrid (nlm: the lighter NL-means + CNN variant)")

@@ -76,7 +76,7 @@ struct WgMeta {
 };
 
 constexpr int kMetaBytes = (sizeof(WgMeta) + 127) / 128 * 128;
-constexpr int kFixedBytes = 2 * kOpBytes + kWgs * kOpBytes + kWgs * kMetaBytes + 128;
+constexpr int kFixedBytes = 2 * kOpBytes + kWgs * kOpBytes + kWgs * 2 * kMetaBytes + 128;
 
 struct TcArgs {
     const float *img;    // [b][C][H][W]: image to filter (pass 1) or noisy (pass 2)
@@ -324,8 +324,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_filter_tc(TcArgs a)
     uint8_t *afwd = sm, *ainv = sm + kOpBytes;
     const int tid = threadIdx.x, wg = tid >> 7, t = tid & 127, wq = t >> 5, lane = tid & 31;
     uint8_t *op = sm + 2 * kOpBytes + wg * kOpBytes;
-    WgMeta &mt = *reinterpret_cast<WgMeta *>(sm + (2 + kWgs) * kOpBytes + wg * kMetaBytes);
-    uint8_t *ctl = sm + (2 + kWgs) * kOpBytes + kWgs * kMetaBytes;
+    // two metadata buffers per warpgroup, alternating between its tiles, so that
+    // a tile's gather may start while slower warps still aggregate the last one
+    uint8_t *meta = sm + (2 + kWgs) * kOpBytes + wg * 2 * kMetaBytes;
+    uint8_t *ctl = sm + (2 + kWgs) * kOpBytes + kWgs * 2 * kMetaBytes;
     uint64_t *mbar = reinterpret_cast<uint64_t *>(ctl) + 2 * wg;  // [forward, inverse]
     uint32_t *tslot = reinterpret_cast<uint32_t *>(ctl + 64);
     int *sfail = reinterpret_cast<int *>(ctl + 72);
@@ -364,9 +366,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_filter_tc(TcArgs a)
     const int half = wq >> 1;            // which groups of the tile this thread's warp works on
     const float kp = a.kai[u];
     const int pi = u >> 3, pj = u & 7;
-    uint32_t phase = 0;                     // parity of the next completion of both mbarriers
-    bool pend_f = false, pend_i = false;    // committed MMAs not yet waited for
-    bool failed = false;
+    uint32_t phase = 0;  // parity of the next completion of both mbarriers
+    uint32_t it = 0;     // tiles of this warpgroup so far (selects the metadata buffer)
+    bool failed = false, wait_failed = false;
+    // this thread's gather column: forward column t, inverse column jc, group g, member k
+    const bool second = WIENER && t >= 64;  // noisy half of the Wiener columns
+    const int jc = WIENER ? (t & 63) : t;
+    const int gcol = jc / S, kcol = jc % S;
 
     const int tiles = a.nb * a.tiles_y * a.tiles_x;
     const size_t HW = (size_t)a.H * a.W;
@@ -389,22 +395,31 @@ __global__ void __launch_bounds__(kThreads, 1) k_filter_tc(TcArgs a)
             }
             __syncthreads();
             failed = failed || *sfail != 0;
-            for (int gt = wg; !failed && gt * G < cnt; gt += kWgs) {
+            // group size and match index of this thread's column in tile gtt (both
+            // loads independent, issued one tile ahead of their use)
+            auto fetch = [&](int gtt, int &nn, int &id) {
+                const int q = gtt * G + gcol;
+                nn = 0;
+                id = -1;
+                if (q < cnt) {
+                    const size_t gr = (size_t)b * a.R + (size_t)(ry0 + q / tw) * a.Rx + rx0 + q % tw;
+                    nn = a.n[gr];
+                    id = a.idx[gr * a.n2 + min(kcol, a.n2 - 1)];
+                }
+            };
+            int n_next, id_next;
+            fetch(wg, n_next, id_next);
+            for (int gt = wg; !failed && gt * G < cnt; gt += kWgs, ++it) {
+                WgMeta &mt = *reinterpret_cast<WgMeta *>(meta + (it & 1) * kMetaBytes);
                 // ---- 1. gather: thread t owns forward column t ----------------------
                 {
-                    const bool second = WIENER && t >= 64;        // noisy half of the Wiener columns
-                    const int jc = WIENER ? (t & 63) : t;         // inverse column of this patch
-                    const int g = jc / S, k = jc % S, q = gt * G + g;
-                    int n = 0, py = 0, px = 0;
-                    size_t gr = 0;
-                    if (q < cnt) {
-                        gr = (size_t)b * a.R + (size_t)(ry0 + q / tw) * a.Rx + rx0 + q % tw;
-                        n = a.n[gr];
-                        if (n < 1 || n > a.n2 || n > S || (n & (n - 1)) != 0) n = 0;
-                    }
+                    const int g = gcol, k = kcol;
+                    int n = n_next, py = 0, px = 0;
+                    const int id = id_next;
+                    fetch(gt + kWgs, n_next, id_next);
+                    if (n < 1 || n > a.n2 || n > S || (n & (n - 1)) != 0) n = 0;
                     bool bad = false;
                     if (k < n) {
-                        const int id = a.idx[gr * a.n2 + k];
                         py = id / a.W;
                         px = id - py * a.W;
                         bad = id < 0 || py > a.H - 8 || px > a.W - 8;
@@ -470,12 +485,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_filter_tc(TcArgs a)
                                      tc::sdesc(op_s + s * 2 * kLbo, kLbo, 128), kIdF, s);
                     tc::mma_commit(&mbar[0]);
                 }
-                pend_f = true;
-                if (!tc::bar_and(bar_id, 128, tc::mbar_wait(&mbar[0], phase))) {
-                    failed = true;
-                    break;
-                }
-                pend_f = false;
+                // bounded wait; on a timeout the tile goes on with whatever TMEM holds (the
+                // status word reports it and the CTA stops at its next block-wide sync)
+                if (!tc::mbar_wait(&mbar[0], phase)) wait_failed = true;
                 tc::fence_after_sync();
                 // ---- 3. group transform, shrinkage, spectra back to shared memory ----
                 {
@@ -531,7 +543,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_filter_tc(TcArgs a)
                                      tc::sdesc(op_s + s * 2 * kLboI, kLboI, 128), kIdI, s);
                     tc::mma_commit(&mbar[1]);
                 }
-                pend_i = true;
+
                 // group weights, scaled by sigma^2: 1/N_har or 1/sum w^2, sigma^2 when 0
                 auto weight = [&](int g) {
                     if (WIENER) {
@@ -550,11 +562,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_filter_tc(TcArgs a)
                         if (fw.hi != 0) atomicAdd(a.wsum_hi + q, (unsigned long long)fw.hi);
                     }
                 }
-                if (!tc::bar_and(bar_id, 128, tc::mbar_wait(&mbar[1], phase))) {
-                    failed = true;
-                    break;
-                }
-                pend_i = false;
+                if (!tc::mbar_wait(&mbar[1], phase)) wait_failed = true;
                 phase ^= 1u;
                 tc::fence_after_sync();
                 {
@@ -583,9 +591,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_filter_tc(TcArgs a)
                     }
                 }
                 tc::fence_before_sync();
-                tc::bar_sync(bar_id, 128);  // metadata, operand buffer and TMEM free for the next tile
             }
-            if (failed && t == 0) {
+            if (wait_failed) {
                 *sfail = 1;
                 atomicExch(a.err, 3);
             }
@@ -600,9 +607,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_filter_tc(TcArgs a)
         }
         if (failed) break;
     }
-    // bounded waits for MMAs still in flight before the TMEM is freed
-    if (pend_f) tc::mbar_wait(&mbar[0], phase);
-    if (pend_i) tc::mbar_wait(&mbar[1], phase);
+    // after a timeout: bounded waits for MMAs that may still be in flight before
+    // the TMEM is freed
+    if (failed) {
+        tc::mbar_wait(&mbar[0], phase ^ 1u);
+        tc::mbar_wait(&mbar[1], phase ^ 1u);
+    }
     tc::fence_before_sync();
     __syncthreads();
     if (tid < 32) {
