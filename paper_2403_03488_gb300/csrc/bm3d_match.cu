@@ -119,12 +119,17 @@ __global__ void __launch_bounds__(kS3T, 4) k_match3(Match3Args a)
 #pragma unroll
                     for (int u = 0; u < 5; ++u) {
                         const int j = 3 * u + 2 * kp;
-                        pr[u] = f2_add(f2_sqd(RR[3 * u], f2_pack(C[j], C[j + 1])),
-                                       f2_sqd(RR[3 * u + 1], f2_pack(C[j + 1], C[j + 2])));
-                        tr[u] = f2_add(pr[u], f2_sqd(RR[3 * u + 2], f2_pack(C[j + 2], C[j + 3])));
+                        const f2 e0 = f2_sub(RR[3 * u], f2_pack(C[j], C[j + 1]));
+                        const f2 e1 = f2_sub(RR[3 * u + 1], f2_pack(C[j + 1], C[j + 2]));
+                        const f2 e2 = f2_sub(RR[3 * u + 2], f2_pack(C[j + 2], C[j + 3]));
+                        pr[u] = f2_fma(e1, e1, f2_mul(e0, e0));
+                        tr[u] = f2_fma(e2, e2, pr[u]);
                     }
-                    pr[5] = f2_add(f2_sqd(RR[15], f2_pack(C[15 + 2 * kp], C[16 + 2 * kp])),
-                                   f2_sqd(RR[16], f2_pack(C[16 + 2 * kp], C[17 + 2 * kp])));
+                    {
+                        const f2 e0 = f2_sub(RR[15], f2_pack(C[15 + 2 * kp], C[16 + 2 * kp]));
+                        const f2 e1 = f2_sub(RR[16], f2_pack(C[16 + 2 * kp], C[17 + 2 * kp]));
+                        pr[5] = f2_fma(e1, e1, f2_mul(e0, e0));
+                    }
                     const f2 h0 = f2_add(f2_add(tr[0], tr[1]), pr[2]);
                     const f2 h1 = f2_add(f2_add(tr[1], tr[2]), pr[3]);
                     const f2 h2 = f2_add(f2_add(tr[2], tr[3]), pr[4]);
@@ -266,10 +271,10 @@ __global__ void __launch_bounds__(kThreads) k_match_fp32(MatchArgs a)
                 for (int k = 0; k < 15; ++k) s[k] = row[k];
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
-                    const float h = tree8(sqd(ref[i * 8], s[c]), sqd(ref[i * 8 + 1], s[c + 1]),
-                                          sqd(ref[i * 8 + 2], s[c + 2]), sqd(ref[i * 8 + 3], s[c + 3]),
-                                          sqd(ref[i * 8 + 4], s[c + 4]), sqd(ref[i * 8 + 5], s[c + 5]),
-                                          sqd(ref[i * 8 + 6], s[c + 6]), sqd(ref[i * 8 + 7], s[c + 7]));
+                    const float h = row_sumsq(__fsub_rn(ref[i * 8], s[c]), __fsub_rn(ref[i * 8 + 1], s[c + 1]),
+                                              __fsub_rn(ref[i * 8 + 2], s[c + 2]), __fsub_rn(ref[i * 8 + 3], s[c + 3]),
+                                              __fsub_rn(ref[i * 8 + 4], s[c + 4]), __fsub_rn(ref[i * 8 + 5], s[c + 5]),
+                                              __fsub_rn(ref[i * 8 + 6], s[c + 6]), __fsub_rn(ref[i * 8 + 7], s[c + 7]));
                     if (i == 0 || i == 3 || i == 6) part[c] = h;
                     else if (i == 1 || i == 4) part[c] = __fadd_rn(part[c], h);
                     else if (i == 2) t0[c] = __fadd_rn(part[c], h);
@@ -280,7 +285,7 @@ __global__ void __launch_bounds__(kThreads) k_match_fp32(MatchArgs a)
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
                 const int x = xc + c;
-                const float d = __fadd_rn(__fadd_rn(t0[c], t1[c]), part[c]) * 0.015625f;  // / 64, exact
+                const float d = __fmul_rn(__fadd_rn(__fadd_rn(t0[c], t1[c]), part[c]), 0.015625f);  // / 64, exact
                 const bool valid = (x <= xe) && !(x == x0 && y == y0) && (d <= tau);
                 if (valid) {
                     ++kept;

@@ -153,7 +153,7 @@ __device__ __forceinline__ void insert_lex(float (&bd)[L], int (&bi)[L], float d
 __device__ __forceinline__ float exact_d(const float (&ref)[64], const float *img, int RP, int ly, int lx)
 {
     const float *q = img + ly * RP + lx;
-    return canon_d64(ref, [&](int i, int j) { return q[i * RP + j]; }) * 0.015625f;
+    return __fmul_rn(canon_d64(ref, [&](int i, int j) { return q[i * RP + j]; }), 0.015625f);
 }
 
 template <int L>

@@ -1,5 +1,8 @@
 // Packed FP32x2 arithmetic (sm_100 and later): two IEEE FP32 operations per
-// instruction, each lane rounded exactly as the scalar _rn operation.
+// instruction, each lane rounded exactly as the scalar _rn operation.  Unlike
+// the scalar _rn intrinsics, a packed multiply feeding a packed add may be
+// fused into one packed fma by the compiler (measured on sm_103a), so code
+// that must reproduce a fixed rounding sequence writes its fmas explicitly.
 #pragma once
 
 namespace dn {
@@ -51,7 +54,8 @@ __device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c)
     return r;
 }
 
-// (a - b)^2 per lane, the product rounded separately (no contraction).
+// (a - b)^2 per lane (the compiler may fuse the product into a following
+// packed add).
 __device__ __forceinline__ f2 f2_sqd(f2 a, f2 b)
 {
     const f2 e = f2_sub(a, b);

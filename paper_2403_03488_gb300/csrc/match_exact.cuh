@@ -3,13 +3,18 @@
 //
 // Every path that ranks candidates with an FP32 distance evaluates
 // d = ||P - Q||^2 / 64 with one fixed association, so equal pixel sets give
-// bit-equal distances and the paths agree bit for bit: squared differences
-// are rounded individually, each patch row is summed as
-//     (((s0 + s1) + s2) + ((s3 + s4) + s5)) + (s6 + s7)
-// and the 8 row sums are combined in the same pattern.  The 3 + 3 + 2 split
-// matches the reference grid step of 3, which lets the tiled kernel share
-// partial sums between neighbouring references.  All products and sums use
-// the _rn intrinsics, so no compiler contraction changes the rounding.
+// bit-equal distances and the paths agree bit for bit.  With e_j the rounded
+// differences of a patch row, the row sum is
+//     (fma(e2, e2, fma(e1, e1, e0 e0)) + fma(e5, e5, fma(e4, e4, e3 e3)))
+//         + fma(e7, e7, e6 e6)
+// (the 3 + 3 + 2 split of ((e0^2 + e1^2) + e2^2) + ((e3^2 + e4^2) + e5^2) +
+// (e6^2 + e7^2) with every "sum + e^2" a single fused multiply-add), and the
+// 8 row sums are added as (((h0 + h1) + h2) + ((h3 + h4) + h5)) + (h6 + h7).
+// The 3 + 3 + 2 split matches the reference grid step of 3, which lets the
+// tiled kernel share partial sums between neighbouring references.  The
+// fused multiply-adds are written out: left to itself the compiler fuses a
+// product into a following sum in some kernels and not in others (measured
+// for the packed FP32x2 instructions), which would break the bit equality.
 #pragma once
 
 #include "common.cuh"
@@ -25,10 +30,13 @@ __device__ __forceinline__ float tree8(float a0, float a1, float a2, float a3, f
     return __fadd_rn(__fadd_rn(t0, t1), __fadd_rn(a6, a7));
 }
 
-__device__ __forceinline__ float sqd(float a, float b)
+// Row sum of squares of 8 rounded differences in the fixed association.
+__device__ __forceinline__ float row_sumsq(float e0, float e1, float e2, float e3, float e4, float e5, float e6,
+                                           float e7)
 {
-    const float e = __fsub_rn(a, b);
-    return __fmul_rn(e, e);
+    const float t0 = __fmaf_rn(e2, e2, __fmaf_rn(e1, e1, __fmul_rn(e0, e0)));
+    const float t1 = __fmaf_rn(e5, e5, __fmaf_rn(e4, e4, __fmul_rn(e3, e3)));
+    return __fadd_rn(__fadd_rn(t0, t1), __fmaf_rn(e7, e7, __fmul_rn(e6, e6)));
 }
 
 __device__ __forceinline__ f2 f2_tree8(f2 a0, f2 a1, f2 a2, f2 a3, f2 a4, f2 a5, f2 a6, f2 a7)
@@ -45,10 +53,10 @@ __device__ __forceinline__ float canon_d64(const float (&ref)[64], Q q)
     float h[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-        float s[8];
+        float e[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) s[j] = sqd(ref[i * 8 + j], q(i, j));
-        h[i] = tree8(s[0], s[1], s[2], s[3], s[4], s[5], s[6], s[7]);
+        for (int j = 0; j < 8; ++j) e[j] = __fsub_rn(ref[i * 8 + j], q(i, j));
+        h[i] = row_sumsq(e[0], e[1], e[2], e[3], e[4], e[5], e[6], e[7]);
     }
     return tree8(h[0], h[1], h[2], h[3], h[4], h[5], h[6], h[7]);
 }
@@ -112,7 +120,7 @@ __device__ void match_ref_warp(const float *g, int H, int W, int step, int hs, f
         const int y = ys + e / ww, x = xs + e % ww;
         if (y == y0 && x == x0) continue;
         const float *q = g + (size_t)y * W + x;
-        const float d = canon_d64(ref, [&](int i, int j) { return q[(size_t)i * W + j]; }) * 0.015625f;
+        const float d = __fmul_rn(canon_d64(ref, [&](int i, int j) { return q[(size_t)i * W + j]; }), 0.015625f);
         if (d <= tau) {
             ++kept;
             if (d < bd[L - 1]) insert_sorted<L>(bd, bi, d, y * W + x);

@@ -347,6 +347,29 @@ def test_tc_cross_terms_within_proven_bound(H, W, tx, ty):
     assert checked > 500
 
 
+def test_match_tc_prefilter_equals_fp32_full_size():
+    """At the precision-path size (two 1024^2 images) the BF16 prefilter with
+    exact re-rank and the FP32 kernels (tiled step-3 kernel, warp kernel for
+    the off-lattice row and column) give identical lists and group sizes for
+    both passes: one distance association, exact ties broken by index."""
+    A = api()
+    _, noisy = synth.make_batch([100, 101], 1024, 1024, 25.0)
+    x = dev(noisy)
+    hard = A.default_bm3d_params().hard
+    i32, n32 = A.bm3d_match(x[:, 0].contiguous(), [2500.0, 2500.0], hard, precision=A.DN_FP32)
+    itc, ntc = A.bm3d_match(x[:, 0].contiguous(), [2500.0, 2500.0], hard, precision=A.DN_BF16_MATCH)
+    assert np.array_equal(host(n32), host(ntc))
+    assert np.array_equal(host(i32), host(itc))
+    basic = A.bm3d_filter_hard(x, i32, n32, [25.0, 25.0], hard)
+    wien = A.default_bm3d_params().wiener
+    g = basic[:, 0].contiguous()
+    i32, n32 = A.bm3d_match(g, [400.0, 400.0], wien, precision=A.DN_FP32)
+    itc, ntc = A.bm3d_match(g, [400.0, 400.0], wien, precision=A.DN_BF16_MATCH)
+    assert np.array_equal(host(n32), host(ntc))
+    assert np.array_equal(host(i32), host(itc))
+    assert A.device_error() == 0
+
+
 def test_bm3d_with_tc_matching_equals_fp32():
     """With the BF16-prefiltered matcher the match lists are the FP32 ones, so
     the BM3D output is bit-identical (the filtering stays FP32)."""
