@@ -134,6 +134,33 @@ def algorithmic(kernel, launches_per_step, batch):
 
 
 # ---------------------------------------------------------------------------
+# multi-rank host logic (weak scaling: each rank denoises its own images, no
+# data-path collective; only the timing is reduced across ranks)
+# ---------------------------------------------------------------------------
+
+def rank_seeds(rank, batch=B):
+    """Image seeds of one rank: a batch of its own, disjoint from every other rank's."""
+    return list(range(SEEDS0 + rank * batch, SEEDS0 + (rank + 1) * batch))
+
+
+def max_over_ranks(x):
+    """The largest value of x over all ranks (x itself without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(mpix_per_rank, world, ms_per_step):
+    """Megapixels all ranks processed per second, timed by the slowest rank."""
+    return mpix_per_rank * world / (ms_per_step / 1e3)
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 
@@ -152,7 +179,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    seeds = list(range(SEEDS0 + rank * B, SEEDS0 + rank * B + B))
+    seeds = rank_seeds(rank)
     clean, noisy = synth.make_batch(seeds, H, W, SIGMA)
     noisy_d = torch.from_numpy(noisy).to(dev)
     clean_d = torch.from_numpy(clean).to(dev)
@@ -196,15 +223,13 @@ def run_ours(args):
             total_ms += e0.elapsed_time(e1)
     torch.cuda.synchronize()
     clk = clocks.stop()
+    total_ms = max_over_ranks(total_ms)
     if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
         dist.barrier()
 
     ms_per_step = total_ms / args.steps
     mpix = B * H * W / 1e6
-    value = mpix * world / (ms_per_step / 1e3)
+    value = whole_job_value(mpix, world, ms_per_step)
 
     # quality of this step's output against the clean images (FP64 reduction)
     sse_d, _ = api.error_reduce(out_d, clean_d)
@@ -245,11 +270,8 @@ def run_ours(args):
         e1.record()
         e1.synchronize()
         e2e_ms += e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = mpix * world / (e2e_ms / e2e_steps / 1e3)
+    e2e_ms = max_over_ranks(e2e_ms)
+    e2e_value = whole_job_value(mpix, world, e2e_ms / e2e_steps)
 
     res = prof.result
     launches = sum(c for c, _ in res.values())
