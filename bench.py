@@ -133,6 +133,39 @@ def algorithmic(kernel, launches_per_step, batch):
     return "hbm", "GB/s", 8.0 * H * W * batch / launches_per_step, hbm, "measured hbm_gbs"
 
 
+def kernel_rooflines(res, steps, batch, launches_per_step=None):
+    """Roofline fraction of every library kernel whose algorithmic work has a
+    plain count: the matcher in FLOP (see `algorithmic`), the CNN layers, the
+    normalisation and the error reduction in bytes that must cross HBM per
+    launch (activations / planes read and written once, halos excluded)."""
+    peaks = {}
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        peaks = json.load(open(p))
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    px = batch * H * W
+    bytes_per_launch = {
+        "conv3x3_tc_bf16": 2 * px * 32 * 2,   # NHWC BF16 activations in and out
+        "conv_first_bf16": px * (8 + 64),     # prefilter + noisy FP32 in, 32 BF16 channels out
+        "conv_last_bf16": px * (64 + 4 + 4),  # 32 BF16 channels + prefilter in, FP32 out
+        "bm3d_normalize": px * (4 * 8 + 4),   # four 64-bit fixed-point planes in, FP32 out
+        "error_reduce_fp64": px * 8,          # output and clean image
+    }
+    out = {}
+    for k, (n, ms) in res.items():
+        avg = ms / n
+        if k in bytes_per_launch:
+            ach = bytes_per_launch[k] / (avg / 1e3) / 1e9
+            out[k] = {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
+                      "frac": round(ach / hbm, 4), "avg_launch_ms": round(avg, 4)}
+        elif k.startswith("bm3d_match_fp32"):
+            bound, unit, work, peak, _ = algorithmic(k, n / steps, batch)
+            ach = work / (avg / 1e3) / 1e12
+            out[k] = {"bound": bound, "achieved": round(ach, 3), "peak": round(peak, 1), "unit": unit,
+                      "frac": round(ach / peak, 4), "avg_launch_ms": round(avg, 4)}
+    return out
+
+
 # ---------------------------------------------------------------------------
 # multi-rank host logic (weak scaling: each rank denoises its own images, no
 # data-path collective; only the timing is reduced across ranks)
@@ -316,6 +349,7 @@ def run_ours(args):
                      "avg_launch_ms": round(avg_ms, 4), "peak_source": peak_note},
         "kernels": {k: {"launches": c, "ms": round(t, 3), "share": round(t / sum(x[1] for x in res.values()), 4)}
                     for k, (c, t) in sorted(res.items(), key=lambda kv: -kv[1][1])},
+        "kernel_rooflines": kernel_rooflines(res, args.steps, B),
         "clocks": clk,
     }
     if not args.no_serving:

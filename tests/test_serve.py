@@ -37,19 +37,24 @@ def _small_requests(n, seed=0):
 
 
 @pytest.mark.gpu
-def test_results_same_alone_and_in_the_mix():
+@pytest.mark.parametrize("bm3d_bf16", [False, True])
+def test_results_same_alone_and_in_the_mix(bm3d_bf16):
+    """Also with the tensor-core group transforms, whose persistent CTAs then
+    share the SMs with the other requests' kernels."""
     from gpu_util import need_gpu
     need_gpu()
+    from paper_2403_03488_gb300 import api
+    prec = api.DN_BF16 if bm3d_bf16 else api.DN_FP32
     w = serve.load_weights()
     reqs = _small_requests(10, seed=5)
     alone = []
     for r in reqs:
-        srv = serve.Server(w, slots=1)
+        srv = serve.Server(w, slots=1, bm3d_precision=prec)
         q = serve.Request(r.rid, r.image, r.sigma)
         srv.run([q], realtime=False, keep_results=True)
         alone.append(q.result)
     mix = [serve.Request(r.rid, r.image, r.sigma) for r in reqs]
-    srv = serve.Server(w, slots=8)
+    srv = serve.Server(w, slots=8, bm3d_precision=prec)
     st = srv.run(mix, realtime=False, keep_results=True)
     assert st.max_inflight > 1  # the requests really overlapped
     for q, ref in zip(mix, alone):
