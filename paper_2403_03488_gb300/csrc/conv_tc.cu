@@ -374,20 +374,26 @@ __global__ void __launch_bounds__(256) k_conv_first_bf16(const float *pre, const
             v1[2 * t + c] = f2_pack(e, e);
         }
     uint32_t p0[16], p1[16];
-    const f2 *w2 = reinterpret_cast<const f2 *>(&ws[0][0]);
+    const float4 *w4 = reinterpret_cast<const float4 *>(&ws[0][0]);
     const f2 *b2 = reinterpret_cast<const f2 *>(bs);
 #pragma unroll
-    for (int c = 0; c < 16; ++c) {
-        // channels (2c, 2c+1) in the two lanes, same accumulation order as one channel at a time
-        f2 a = b2[c], bb = b2[c];
+    for (int c = 0; c < 16; c += 2) {
+        // channels (2c, 2c+1) and (2c+2, 2c+3) in the lanes of two packed pairs, one
+        // 16-byte weight load per tap, same accumulation order as one channel at a time
+        f2 a = b2[c], a2 = b2[c + 1], bb = b2[c], bb2 = b2[c + 1];
 #pragma unroll
         for (int k = 0; k < 18; ++k) {
-            const f2 wk = w2[k * (kCh / 2) + c];
+            const float4 wq = w4[k * (kCh / 4) + c / 2];
+            const f2 wk = f2_pack(wq.x, wq.y), wk2 = f2_pack(wq.z, wq.w);
             a = f2_fma(wk, v0[k], a);
+            a2 = f2_fma(wk2, v0[k], a2);
             bb = f2_fma(wk, v1[k], bb);
+            bb2 = f2_fma(wk2, v1[k], bb2);
         }
         p0[c] = tc::pack_bf16x2(fmaxf(f2_lo(a), 0.0f), fmaxf(f2_hi(a), 0.0f));
+        p0[c + 1] = tc::pack_bf16x2(fmaxf(f2_lo(a2), 0.0f), fmaxf(f2_hi(a2), 0.0f));
         p1[c] = tc::pack_bf16x2(fmaxf(f2_lo(bb), 0.0f), fmaxf(f2_hi(bb), 0.0f));
+        p1[c + 1] = tc::pack_bf16x2(fmaxf(f2_lo(bb2), 0.0f), fmaxf(f2_hi(bb2), 0.0f));
     }
     uint4 *dst = y + ((size_t)n * HW + (size_t)py * W + X0 + tx) * 4;
 #pragma unroll

@@ -82,19 +82,41 @@ __global__ void k_colour(const float *in, float *out, size_t HW, size_t total, M
     }
 }
 
+// Exact sum and product of FP32 values as unevaluated pairs (Knuth's TwoSum,
+// and the fused multiply-add form of Dekker's TwoProduct).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Per-thread partial sums of the squared errors in double-FP32 (hi + lo,
+// about 44 significant bits): each pixel's error e = clip(v) - t is the exact
+// pair (d, de), e^2 = d^2 (exact pair from an fma) + 2 d de + de^2, and the
+// pair accumulator adds it with TwoSum.  The per-thread sums then go to FP64
+// for the block and image reductions, so no per-pixel work runs on the
+// narrow FP64 units.
 __global__ void k_error_reduce(const float *out, const float *ref, size_t chw, double *sse, unsigned long long *mx)
 {
     const int b = blockIdx.y;
     const float *o = out + (size_t)b * chw;
     const float *r = ref + (size_t)b * chw;
-    double s = 0.0;
+    float sh = 0.0f, sl = 0.0f;
     float m = 0.0f;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < chw; i += (size_t)gridDim.x * blockDim.x) {
-        float v = o[i], t = r[i];
-        double e = (double)fminf(fmaxf(v, 0.0f), 255.0f) - (double)t;
-        s += e * e;
+        const float v = o[i], t = r[i];
+        float d, de;
+        two_sum(fminf(fmaxf(v, 0.0f), 255.0f), -t, d, de);
+        const float p = __fmul_rn(d, d), pe = __fmaf_rn(d, d, -p);
+        const float small = __fmaf_rn(de, de, __fmaf_rn(2.0f * d, de, pe));
+        float h, he;
+        two_sum(sh, p, h, he);
+        sl = __fadd_rn(sl, __fadd_rn(he, small));
+        sh = h;
         m = fmaxf(m, fabsf(v - t));
     }
+    double s = (double)sh + (double)sl;
     __shared__ double ss[32];
     __shared__ float sm[32];
     for (int off = 16; off > 0; off >>= 1) {
