@@ -171,8 +171,10 @@ def kernel_rooflines(res, steps, batch, launches_per_step=None):
 # data-path collective; only the timing is reduced across ranks)
 # ---------------------------------------------------------------------------
 
-def rank_seeds(rank, batch=B):
-    """Image seeds of one rank: a batch of its own, disjoint from every other rank's."""
+def rank_seeds(rank, batch=None):
+    """Image seeds of one rank: a batch of its own (B images unless given),
+    disjoint from every other rank's."""
+    batch = B if batch is None else batch
     return list(range(SEEDS0 + rank * batch, SEEDS0 + (rank + 1) * batch))
 
 

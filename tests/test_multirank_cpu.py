@@ -64,3 +64,10 @@ def test_whole_job_value_and_single_process_reduction():
     # without a process group the reduction is the identity
     assert bench.max_over_ranks(3.5) == 3.5
     assert bench.rank_seeds(0, batch=2) == [100, 101] and bench.rank_seeds(1, batch=2) == [102, 103]
+    # the batch of a profiling run (--batch) is the one the seeds follow
+    old = bench.B
+    try:
+        bench.B = 3
+        assert bench.rank_seeds(1) == [103, 104, 105]
+    finally:
+        bench.B = old
