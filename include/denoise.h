@@ -263,6 +263,45 @@ size_t dn_cnn_workspace_bytes(int N, int H, int W, const dn_cnn *cnn);
 dn_status dn_conv3x3_tc_fwd(const void *x, const float *w, const float *b, void *y, int N, int H, int W, int C,
                             int relu, void *workspace, size_t ws_bytes, dn_stream_t stream);
 
+/* ---- layers of the flexible lightweight network (Sec. III, "Ours-FL") -----
+ * A U-Net of depthwise-separable 3x3 convolutions with stride-2 downsampling,
+ * 2x2 transposed-convolution upsampling and additive skips, whose input
+ * carries the noise level as a plane (the paper gives the structure, not the
+ * widths).  All tensors are DEVICE float32, NCHW, contiguous; FP32 CUDA-core
+ * kernels; results are deterministic (fixed reduction orders). */
+
+/* Depthwise 3x3, zero padding 1, stride 1 or 2: y [N][C][Ho][Wo], Ho = ceil(H / stride),
+ * y = b[c] + sum_{i,j} w[c][i][j] x[n][c][stride yo + i - 1][stride xo + j - 1],
+ * then ReLU when relu != 0.  w [C][3][3]; b [C] or NULL. */
+dn_status dn_dw3x3_fwd(const float *x, const float *w, const float *b, float *y, int N, int C, int H, int W,
+                       int stride, int relu, dn_stream_t stream);
+/* Gradients of the depthwise layer (before any ReLU) given g = dL/dy [N][C][Ho][Wo]:
+ * dx [N][C][H][W] (skipped when NULL), dw [C][3][3], db [C] (skipped when NULL);
+ * dw and db are overwritten. */
+dn_status dn_dw3x3_bwd(const float *x, const float *g, const float *w, float *dx, float *dw, float *db, int N, int C,
+                       int H, int W, int stride, dn_stream_t stream);
+/* Pointwise (1x1): y [N][Cout][HW] = b[co] + sum_ci w[co][ci] x[n][ci][p], ReLU when
+ * relu != 0; w [Cout][Cin], b [Cout] or NULL.  transposed != 0 multiplies by the
+ * transpose of a [Cin][Cout] weight instead (the data gradient of a Cout -> Cin layer). */
+dn_status dn_pw_fwd(const float *x, const float *w, const float *b, float *y, int N, int Cin, int Cout, int HW,
+                    int relu, int transposed, dn_stream_t stream);
+/* dw [Cout][Cin] = sum_{n,p} g[n][co][p] x[n][ci][p]; db [Cout] = sum g (NULL: skipped). */
+dn_status dn_pw_bwd_weight(const float *x, const float *g, float *dw, float *db, int N, int Cin, int Cout, int HW,
+                           dn_stream_t stream);
+/* Transposed 2x2 convolution, stride 2: y [N][Cout][2H][2W],
+ * y[n][co][2i+a][2j+c] = b[co] + skip[n][co][2i+a][2j+c] + sum_ci w[ci][co][a][c] x[n][ci][i][j];
+ * w [Cin][Cout][2][2] (16-byte aligned), b and skip may be NULL. */
+dn_status dn_deconv2x2_fwd(const float *x, const float *w, const float *b, const float *skip, float *y, int N, int Cin,
+                           int Cout, int H, int W, dn_stream_t stream);
+/* Gradients of the transposed convolution given g [N][Cout][2H][2W]: dx [N][Cin][H][W]
+ * (NULL: skipped), dw [Cin][Cout][2][2], db [Cout] (NULL: skipped). */
+dn_status dn_deconv2x2_bwd(const float *x, const float *g, const float *w, float *dx, float *dw, float *db, int N,
+                           int Cin, int Cout, int H, int W, dn_stream_t stream);
+/* Network input with the noise-level map: z [N][3][H][W] = [pre / 255, noisy / 255,
+ * sigma_n / 255]; sigma a HOST array of N floats in [0, 255]. */
+dn_status dn_fl_pack_input(const float *pre, const float *noisy, const float *sigma, float *z, int N, int H, int W,
+                           dn_stream_t stream);
+
 /* Reads (and with reset != 0 clears) the library's device error word on the
  * current device: nonzero when a kernel's bounded wait on the tensor-core
  * pipeline ran out.  Synchronous (waits for the device). */

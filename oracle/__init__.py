@@ -374,6 +374,79 @@ def adam_step(param, grad, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
 
 
 # --------------------------------------------------------------------------
+# Flexible lightweight network (Sec. III, "Ours-FL")
+# --------------------------------------------------------------------------
+#
+# Read from Sec. III: a U-Net of 4 encoder and 4 decoder levels built from 3x3
+# depthwise-separable convolutions (depthwise 3x3 with bias, pointwise with
+# bias, ReLU), a stride-2 block for every downsampling, a 2x2 stride-2
+# transposed convolution plus the encoder output of the same level for every
+# upsampling, a noise-level plane in the input (FFDNet style) and the
+# residual output of Eq. 2.  Parameter order (the interface shared with the
+# GPU network): per block dw_w [cin,3,3], dw_b, pw_w [cout,cin], pw_b; per
+# upsampling w [cin,cout,2,2], b; then the output pw w [1,c0], b [1].  Plain
+# PyTorch CPU ops in FP64 (grouped conv2d, conv_transpose2d, autograd), pinned
+# in tests/test_oracle_flnet.py by brute-force numpy definitions, the adjoint
+# identity of the transposed convolution and finite differences.
+
+def _fl_torch():
+    import torch
+    import torch.nn.functional as F
+    return torch, F
+
+
+def fl_residual_t(noisy, pre, sigma, params):
+    """The network's residual r [N, H, W] as a float64 torch tensor (params:
+    float64 torch tensors, may require grad)."""
+    torch, F = _fl_torch()
+    nz = torch.as_tensor(_f64(noisy))
+    pr = torch.as_tensor(_f64(pre))
+    N, H, W = nz.shape
+    sig = torch.as_tensor(np.asarray(sigma, np.float64).reshape(N, 1, 1) / 255.0).expand(N, H, W)
+    h = torch.stack([pr / 255.0, nz / 255.0, sig], dim=1)
+    it = iter(params)
+
+    def block(h, stride):
+        dw_w, dw_b, pw_w, pw_b = next(it), next(it), next(it), next(it)
+        C = h.shape[1]
+        h = F.conv2d(h, dw_w.reshape(C, 1, 3, 3), dw_b, stride=stride, padding=1, groups=C)
+        h = F.conv2d(h, pw_w.reshape(pw_w.shape[0], C, 1, 1), pw_b)
+        return torch.relu(h)
+
+    h = block(block(h, 1), 1)
+    enc = [h]
+    for _ in range(4):
+        h = block(block(h, 2), 1)
+        enc.append(h)
+    for k in range(4, 0, -1):
+        w, b = next(it), next(it)
+        h = F.conv_transpose2d(h, w, b, stride=2) + enc[k - 1]
+        h = block(h, 1)
+    w, b = next(it), next(it)
+    r = F.conv2d(h, w.reshape(1, -1, 1, 1), b)
+    return r[:, 0]
+
+
+def fl_forward(noisy, pre, sigma, params):
+    """out = pre + 255 r (numpy float64)."""
+    torch, _ = _fl_torch()
+    p = [torch.as_tensor(_f64(a)) for a in params]
+    r = fl_residual_t(noisy, pre, sigma, p)
+    return _f64(pre) + 255.0 * r.numpy()
+
+
+def fl_backward(noisy, pre, clean, sigma, params):
+    """(L1 loss of Eq. 2, gradients of every parameter) in float64."""
+    torch, _ = _fl_torch()
+    p = [torch.as_tensor(_f64(a)).requires_grad_(True) for a in params]
+    r = fl_residual_t(noisy, pre, sigma, p)
+    out = torch.as_tensor(_f64(pre)) + 255.0 * r
+    loss = (out - torch.as_tensor(_f64(clean))).abs().mean()
+    loss.backward()
+    return float(loss.detach()), [q.grad.numpy() for q in p]
+
+
+# --------------------------------------------------------------------------
 # Error metrics
 # --------------------------------------------------------------------------
 

@@ -369,6 +369,94 @@ def adam_step(param, grad, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, s
                                _stream(stream)), "dn_adam_step")
 
 
+# ---- layers of the flexible lightweight network (Sec. III) -------------------
+
+def dw3x3_fwd(x, w, b=None, stride=1, relu=False, stream=None):
+    """Depthwise 3x3 (zero padding 1, stride 1 or 2): x [N, C, H, W], w [C, 3, 3], b [C]."""
+    _need(x, "x", dim=4)
+    _need(w, "w")
+    N, C, H, W = x.shape
+    y = torch.empty(N, C, (H + stride - 1) // stride, (W + stride - 1) // stride, device=x.device)
+    check(L.lib().dn_dw3x3_fwd(_vp(x), _vp(w), _vp(b), _vp(y), N, C, H, W, stride, int(relu), _stream(stream)),
+          "dn_dw3x3_fwd")
+    return y
+
+
+def dw3x3_bwd(x, g, w, stride=1, need_dx=True, stream=None):
+    """(dx or None, dw [C, 3, 3], db [C]) of the depthwise layer for g = dL/dy."""
+    _need(x, "x", dim=4)
+    _need(g, "g", dim=4)
+    N, C, H, W = x.shape
+    dx = torch.empty_like(x) if need_dx else None
+    dw = torch.empty(C, 3, 3, device=x.device)
+    db = torch.empty(C, device=x.device)
+    check(L.lib().dn_dw3x3_bwd(_vp(x), _vp(g), _vp(w), _vp(dx), _vp(dw), _vp(db), N, C, H, W, stride,
+                               _stream(stream)), "dn_dw3x3_bwd")
+    return dx, dw, db
+
+
+def pw_fwd(x, w, b=None, relu=False, transposed=False, stream=None):
+    """Pointwise: x [N, Cin, H, W], w [Cout, Cin] -> [N, Cout, H, W]; transposed: w [Cin', Cout'] used as W^T."""
+    _need(x, "x", dim=4)
+    _need(w, "w")
+    N, Cin, H, W = x.shape
+    Cout = w.shape[1] if transposed else w.shape[0]
+    y = torch.empty(N, Cout, H, W, device=x.device)
+    check(L.lib().dn_pw_fwd(_vp(x), _vp(w), _vp(b), _vp(y), N, Cin, Cout, H * W, int(relu), int(transposed),
+                            _stream(stream)), "dn_pw_fwd")
+    return y
+
+
+def pw_bwd_weight(x, g, stream=None):
+    """(dw [Cout, Cin], db [Cout]) of a pointwise layer."""
+    _need(x, "x", dim=4)
+    _need(g, "g", dim=4)
+    N, Cin, H, W = x.shape
+    Cout = g.shape[1]
+    dw = torch.empty(Cout, Cin, device=x.device)
+    db = torch.empty(Cout, device=x.device)
+    check(L.lib().dn_pw_bwd_weight(_vp(x), _vp(g), _vp(dw), _vp(db), N, Cin, Cout, H * W, _stream(stream)),
+          "dn_pw_bwd_weight")
+    return dw, db
+
+
+def deconv2x2_fwd(x, w, b=None, skip=None, stream=None):
+    """Transposed 2x2 conv, stride 2: x [N, Cin, H, W], w [Cin, Cout, 2, 2] -> [N, Cout, 2H, 2W] (+ skip)."""
+    _need(x, "x", dim=4)
+    _need(w, "w")
+    N, Cin, H, W = x.shape
+    Cout = w.shape[1]
+    y = torch.empty(N, Cout, 2 * H, 2 * W, device=x.device)
+    check(L.lib().dn_deconv2x2_fwd(_vp(x), _vp(w), _vp(b), _vp(skip), _vp(y), N, Cin, Cout, H, W, _stream(stream)),
+          "dn_deconv2x2_fwd")
+    return y
+
+
+def deconv2x2_bwd(x, g, w, need_dx=True, stream=None):
+    """(dx or None, dw [Cin, Cout, 2, 2], db [Cout]) of the transposed convolution."""
+    _need(x, "x", dim=4)
+    _need(g, "g", dim=4)
+    N, Cin, H, W = x.shape
+    Cout = w.shape[1]
+    dx = torch.empty_like(x) if need_dx else None
+    dw = torch.empty(Cin, Cout, 2, 2, device=x.device)
+    db = torch.empty(Cout, device=x.device)
+    check(L.lib().dn_deconv2x2_bwd(_vp(x), _vp(g), _vp(w), _vp(dx), _vp(dw), _vp(db), N, Cin, Cout, H, W,
+                                   _stream(stream)), "dn_deconv2x2_bwd")
+    return dx, dw, db
+
+
+def fl_pack_input(pre, noisy, sigma, stream=None):
+    """z [N, 3, H, W] = [pre / 255, noisy / 255, sigma_n / 255] from planes [N, H, W]."""
+    _need(pre, "pre", dim=3)
+    _need(noisy, "noisy", dim=3)
+    N, H, W = pre.shape
+    z = torch.empty(N, 3, H, W, device=pre.device)
+    check(L.lib().dn_fl_pack_input(_vp(pre), _vp(noisy), _sigmas(sigma, N), _vp(z), N, H, W, _stream(stream)),
+          "dn_fl_pack_input")
+    return z
+
+
 class profile:
     """Context manager timing every library kernel with CUDA events on its stream.
 

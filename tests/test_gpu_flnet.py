@@ -1,0 +1,150 @@
+"""The flexible lightweight network (Sec. III) on the GPU against the FP64
+oracle: every layer kernel forward and backward (odd sizes, channel counts
+that are not multiples of the kernels' channel blocks, stride 2), the whole
+network's output and gradients, one L1 + Adam training step, and a short
+training run that lowers the loss."""
+import numpy as np
+import pytest
+
+from gpu_util import dev, host, need_gpu
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    need_gpu()
+
+
+def A():
+    from paper_2403_03488_gb300 import api
+    return api
+
+
+def ref_grads(fn, *arrays):
+    ts = [torch.as_tensor(np.asarray(a, np.float64)).requires_grad_(True) for a in arrays]
+    return fn(*ts), ts
+
+
+def close(a, b, rel=1e-5):
+    b = np.asarray(b, np.float64)
+    assert np.abs(np.asarray(a, np.float64) - b).max() <= rel * max(1.0, np.abs(b).max()), (
+        np.abs(np.asarray(a, np.float64) - b).max(), np.abs(b).max())
+
+
+@pytest.mark.parametrize("stride,relu", [(1, False), (2, False), (1, True), (2, True)])
+def test_depthwise_forward_and_backward(oracle, stride, relu):
+    _, F = oracle._fl_torch()
+    rng = np.random.default_rng(stride)
+    x = rng.standard_normal((2, 5, 13, 18)).astype(np.float32)
+    w = rng.standard_normal((5, 3, 3)).astype(np.float32)
+    b = rng.standard_normal(5).astype(np.float32)
+    y = host(A().dw3x3_fwd(dev(x), dev(w), dev(b), stride=stride, relu=relu))
+    yr, (tx, tw, tb) = ref_grads(lambda X, Wt, B: F.conv2d(X, Wt.reshape(5, 1, 3, 3), B, stride=stride, padding=1,
+                                                           groups=5), x, w, b)
+    close(y, (yr.clamp(min=0) if relu else yr).detach().numpy())
+    g = rng.standard_normal(yr.shape).astype(np.float32)
+    yr.backward(torch.as_tensor(g, dtype=torch.float64))
+    dx, dw, db = A().dw3x3_bwd(dev(x), dev(g), dev(w), stride=stride)
+    close(host(dx), tx.grad.numpy())
+    close(host(dw), tw.grad.numpy(), 1e-4)
+    close(host(db), tb.grad.numpy(), 1e-4)
+
+
+@pytest.mark.parametrize("relu", [False, True])
+def test_pointwise_forward_and_backward(oracle, relu):
+    _, F = oracle._fl_torch()
+    rng = np.random.default_rng(7)
+    x = rng.standard_normal((2, 20, 7, 9)).astype(np.float32)
+    w = rng.standard_normal((37, 20)).astype(np.float32)
+    b = rng.standard_normal(37).astype(np.float32)
+    y = host(A().pw_fwd(dev(x), dev(w), dev(b), relu=relu))
+    yr, (tx, tw, tb) = ref_grads(lambda X, Wt, B: F.conv2d(X, Wt.reshape(37, 20, 1, 1), B), x, w, b)
+    close(y, (yr.clamp(min=0) if relu else yr).detach().numpy())
+    g = rng.standard_normal(yr.shape).astype(np.float32)
+    yr.backward(torch.as_tensor(g, dtype=torch.float64))
+    close(host(A().pw_fwd(dev(g), dev(w), None, transposed=True)), tx.grad.numpy())
+    dw, db = A().pw_bwd_weight(dev(x), dev(g))
+    close(host(dw), tw.grad.numpy(), 1e-4)
+    close(host(db), tb.grad.numpy(), 1e-4)
+
+
+def test_transposed_convolution_forward_and_backward(oracle):
+    _, F = oracle._fl_torch()
+    rng = np.random.default_rng(9)
+    x = rng.standard_normal((2, 13, 5, 6)).astype(np.float32)
+    w = rng.standard_normal((13, 11, 2, 2)).astype(np.float32)
+    b = rng.standard_normal(11).astype(np.float32)
+    skip = rng.standard_normal((2, 11, 10, 12)).astype(np.float32)
+    y = host(A().deconv2x2_fwd(dev(x), dev(w), dev(b), dev(skip)))
+    yr, (tx, tw, tb) = ref_grads(lambda X, Wt, B: F.conv_transpose2d(X, Wt, B, stride=2), x, w, b)
+    close(y, yr.detach().numpy() + skip)
+    g = rng.standard_normal(yr.shape).astype(np.float32)
+    yr.backward(torch.as_tensor(g, dtype=torch.float64))
+    dx, dw, db = A().deconv2x2_bwd(dev(x), dev(g), dev(w))
+    close(host(dx), tx.grad.numpy())
+    close(host(dw), tw.grad.numpy(), 1e-4)
+    close(host(db), tb.grad.numpy(), 1e-4)
+
+
+def _batch(seed, n, h, w):
+    from paper_2403_03488_gb300 import synth
+    sig = [15.0, 50.0, 25.0, 35.0][:n]
+    clean, noisy = synth.make_batch(range(seed, seed + n), h, w, sig)
+    rng = np.random.default_rng(seed)
+    pre = (clean[:, 0] + rng.normal(0, 4, clean[:, 0].shape)).astype(np.float32)  # a prefilter-like input
+    return clean[:, 0], noisy[:, 0], pre, sig
+
+
+@pytest.mark.parametrize("widths,h,w", [((8, 12, 16, 20, 24), 32, 48), (None, 32, 32)])
+def test_network_forward_and_gradients_match_oracle(oracle, widths, h, w):
+    from paper_2403_03488_gb300.flnet import FLNet, WIDTHS
+    widths = widths or WIDTHS
+    clean, noisy, pre, sig = _batch(600, 2, h, w)
+    net = FLNet(widths, seed=3).cuda()
+    with torch.no_grad():  # nonzero biases so that every bias path is exercised
+        net.flat.add_(0.01 * torch.sin(torch.arange(net.flat.numel(), device="cuda", dtype=torch.float32)))
+    prm = net.numpy_params()
+    out = host(net(dev(noisy), dev(pre), sig))
+    ref = oracle.fl_forward(noisy, pre, sig, prm)
+    # an untrained network's outputs reach ~1e4 grey levels: FP32 relative error
+    assert np.abs(out - ref).max() <= 2e-5 * max(255.0, np.abs(ref).max()), (np.abs(out - ref).max(), np.abs(ref).max())
+    # gradients of the L1 loss through the library's backward kernels
+    r = net.residual(dev(noisy), dev(pre), sig).contiguous()
+    dr = A().l1_residual_grad(r, dev(pre), dev(clean))
+    r.backward(dr)
+    gflat = net.flat.grad.detach()
+    _, grads = oracle.fl_backward(noisy, pre, clean, sig, prm)
+    for o, s, gref in zip(net.offsets, net.shapes, grads):
+        g = host(gflat[o:o + int(np.prod(s))]).reshape(s)
+        assert np.abs(g - gref).max() <= 2e-4 * max(1e-3, np.abs(gref).max()), (s, np.abs(g - gref).max(),
+                                                                               np.abs(gref).max())
+
+
+def test_training_step_matches_oracle_adam(oracle):
+    from paper_2403_03488_gb300.flnet import FLNet
+    widths = (8, 12, 16, 20, 24)
+    clean, noisy, pre, sig = _batch(700, 2, 32, 32)
+    net = FLNet(widths, seed=5).cuda()
+    before = net.numpy_params()
+    loss = net.train_step(dev(noisy), dev(pre), dev(clean), sig, lr=1e-3)
+    lref, grads = oracle.fl_backward(noisy, pre, clean, sig, before)
+    assert abs(loss - lref) <= 1e-4 * lref
+    after = net.numpy_params()
+    for p0, p1, g in zip(before, after, grads):
+        exp, _, _ = oracle.adam_step(p0.astype(np.float64), g, np.zeros_like(g), np.zeros_like(g), 1)
+        # Adam's first step moves every coordinate by ~lr * sign(g): compare where |g| is not tiny
+        m = np.abs(g) > 1e-3 * max(1e-6, np.abs(g).max())
+        assert np.abs(p1 - exp)[m].max() <= 2e-6 if m.any() else True
+
+
+def test_short_training_lowers_the_loss():
+    from paper_2403_03488_gb300.flnet import FLNet
+    clean, noisy, pre, sig = _batch(800, 4, 64, 64)
+    net = FLNet((16, 24, 32, 48, 64), seed=1).cuda()
+    xs = [dev(a) for a in (noisy, pre, clean)]
+    losses = [net.train_step(*xs, sig, lr=2e-3) for _ in range(60)]
+    assert np.isfinite(losses).all()
+    assert np.mean(losses[-10:]) < 0.8 * np.mean(losses[:5]), (losses[:5], losses[-10:])
+    assert A().device_error() == 0
