@@ -33,9 +33,10 @@ METRIC = "MPix/s BM3D+CNN at <=0.05 dB PSNR loss vs FP32 plain; served p50/p99 m
 FP32_PEAK_TFLOPS_NOTE = "FP32 ALU peak = 152 SM x 128 lanes x 2 FLOP/FMA x 2.07 GHz = 80.5 TFLOP/s"
 
 
-def workload_name(bm3d, cnn, prefilter="bm3d"):
+def workload_name(bm3d, cnn, prefilter="bm3d", net="resnet"):
     pre = "BM3D(%s)" % bm3d if prefilter == "bm3d" else "NLM(fp32)"
-    return "hybrid %s+CNN(10x32, %s) denoise, %d grey %dx%d synthetic images, sigma=25" % (pre, cnn, B, H, W)
+    body = "CNN(10x32, %s)" % cnn if net == "resnet" else "FL-UNet(48-192, fp32)"
+    return "hybrid %s+%s denoise, %d grey %dx%d synthetic images, sigma=25" % (pre, body, B, H, W)
 
 
 # ---------------------------------------------------------------------------
@@ -230,9 +231,29 @@ def run_ours(args):
     sse = torch.empty(B, dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
+    fl = args.net == "fl"
+    if fl:
+        flnet, wsrc = load_fl(dev)
+        pre_d = torch.empty_like(noisy_d)
+        ws_pre = torch.empty(api.bm3d_workspace_bytes(B, 1, H, W, bp) if not nlm else 1, dtype=torch.uint8,
+                             device=dev)
+
+    def denoise(x, out):
+        """The hybrid on device tensors: the C-ABI hybrid, or prefilter + the flexible network."""
+        if not fl:
+            api.denoise_hybrid(x, SIGMA, weights, prefilter=pf, prefilter_params=bp, cnn_precision=prec, out=out,
+                               workspace=ws)
+            return
+        if nlm:
+            api.denoise_nlm(x, SIGMA, bp, out=pre_d)
+        else:
+            api.denoise_bm3d(x, SIGMA, bp, out=pre_d, workspace=ws_pre)
+        n = x.shape[0]
+        with torch.no_grad():
+            flnet(x.view(n, H, W), pre_d.view(n, H, W), [SIGMA] * n, out=out.view(n, H, W))
+
     def step():
-        api.denoise_hybrid(noisy_d, SIGMA, weights, prefilter=pf, prefilter_params=bp, cnn_precision=prec, out=out_d,
-                           workspace=ws)
+        denoise(noisy_d, out_d)
         api.error_reduce(out_d, clean_d)
 
     for _ in range(args.warmup):
@@ -271,8 +292,12 @@ def run_ours(args):
     mse = float(sse_d.sum().item()) / (B * H * W)
     psnr_out = 10 * np.log10(255.0 ** 2 / mse)
     # the FP32 plain path on the same batch (untimed), for the PSNR-loss criterion
-    plain = api.denoise_hybrid(noisy_d, SIGMA, weights, prefilter=pf,
-                               prefilter_params=bp if nlm else api.default_bm3d_params(), cnn_precision=api.DN_FP32)
+    if fl:
+        plain = out_d.clone()  # the flexible network runs in FP32 only: it is its own plain path
+    else:
+        plain = api.denoise_hybrid(noisy_d, SIGMA, weights, prefilter=pf,
+                                   prefilter_params=bp if nlm else api.default_bm3d_params(),
+                                   cnn_precision=api.DN_FP32)
     sse_p, _ = api.error_reduce(plain, clean_d)
     psnr_plain = 10 * np.log10(255.0 ** 2 / (float(sse_p.sum().item()) / (B * H * W)))
     bm3d_only = api.denoise_nlm(noisy_d, SIGMA, bp) if nlm else api.denoise_bm3d(noisy_d, SIGMA, bp)
@@ -285,8 +310,7 @@ def run_ours(args):
     out_h = torch.empty_like(noisy_h).pin_memory()
     for _ in range(2):
         x = noisy_h.to(dev, non_blocking=True)
-        api.denoise_hybrid(x, SIGMA, weights, prefilter=pf, prefilter_params=bp, cnn_precision=prec, out=out_d,
-                           workspace=ws)
+        denoise(x, out_d)
         out_h.copy_(out_d, non_blocking=True)
     torch.cuda.synchronize()
     if world > 1:
@@ -299,8 +323,7 @@ def run_ours(args):
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
         x = noisy_h.to(dev, non_blocking=True)
-        api.denoise_hybrid(x, SIGMA, weights, prefilter=pf, prefilter_params=bp, cnn_precision=prec, out=out_d,
-                           workspace=ws)
+        denoise(x, out_d)
         out_h.copy_(out_d, non_blocking=True)
         e1.record()
         e1.synchronize()
@@ -323,7 +346,8 @@ def run_ours(args):
             dist.destroy_process_group()
         return
     line = {
-        "metric": METRIC if args.prefilter == "bm3d" else METRIC.replace("BM3D+CNN", "NLM+CNN"),
+        "metric": (METRIC if args.prefilter == "bm3d" else METRIC.replace("BM3D+CNN", "NLM+CNN")).replace(
+            "+CNN", "+CNN" if args.net == "resnet" else "+FL-CNN"),
         "value": round(value, 3),
         "unit": "MPix/s",
         "n_gpus": world,
@@ -333,11 +357,13 @@ def run_ours(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "+".join(sorted({"f32" if bprec == api.DN_FP32 else "bf16", "f32" if prec == api.DN_FP32 else "bf16"})),
+        "dtype": "+".join(sorted({"f32" if bprec == api.DN_FP32 else "bf16",
+                                  "f32" if prec == api.DN_FP32 or args.net == "fl" else "bf16"})),
         "data": "synthetic (seeded piecewise-smooth + gratings + repeated tile, AWGN sigma=25)",
-        "config": {"workload": workload_name(args.bm3d, args.cnn, args.prefilter), "global_batch": B * world,
+        "config": {"workload": workload_name(args.bm3d, args.cnn, args.prefilter, args.net), "global_batch": B * world,
                    "image": [H, W],
-                   "channels": 1, "sigma": SIGMA, "cnn": "10 layers x 32 ch, " + wsrc,
+                   "channels": 1, "sigma": SIGMA,
+                   "cnn": ("10 layers x 32 ch, " if args.net == "resnet" else "flexible U-Net (Sec. III), ") + wsrc,
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": "replicas (dp%d)" % world},
         "psnr_db": round(psnr_out, 3),
         "psnr_fp32_plain_db": round(psnr_plain, 3),
@@ -404,6 +430,17 @@ def load_weights(dev):
         w = torch.from_numpy(np.load(p).astype(np.float32)).to(dev)
         return w.contiguous(), "trained weights (" + os.path.basename(p) + ")"
     return ResidualNet(10, 32, seed=0).to(dev).flat_weights(), "random init (He, seed 0)"
+
+
+def load_fl(dev):
+    """The flexible network with the shipped trained weights when present, else He init (seed 0)."""
+    from paper_2403_03488_gb300.flnet import FLNet
+    import torch
+    p = os.path.join(ROOT, "paper_2403_03488_gb300", "weights", "flnet_bm3d.npy")
+    if os.path.exists(p):
+        return FLNet(flat=torch.from_numpy(np.load(p).astype(np.float32))).to(dev), \
+            "trained weights (" + os.path.basename(p) + ")"
+    return FLNet(seed=0).to(dev), "random init (He, seed 0)"
 
 
 def load_traffic(kname):
@@ -491,6 +528,8 @@ def main():
                     help="BM3D precision: fp32 SIMT; bf16 = 2D transforms on the tensor cores; bf16+match = also "
                          "the BF16 tensor-core matching prefilter (exact FP32 re-rank)")
     ap.add_argument("--cnn", default="bf16", choices=["fp32", "bf16"], help="CNN precision")
+    ap.add_argument("--net", default="resnet", choices=["resnet", "fl"],
+                    help="network after the prefilter: the 10x32 residual CNN, or the flexible U-Net of Sec. III")
     ap.add_argument("--prefilter", default="bm3d", choices=["bm3d", "nlm"],
                     help="nonlocal prefilter of the hybrid (nlm: the lighter NL-means + CNN variant)")
     ap.add_argument("--cpu-side", type=int, default=1024)

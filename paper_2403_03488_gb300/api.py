@@ -337,11 +337,14 @@ def cnn_pack_input(pre, noisy, stream=None):
     return z
 
 
-def cnn_residual_out(pre, r, stream=None):
-    """out = pre + 255 r (Eq. 2)."""
+def cnn_residual_out(pre, r, out=None, stream=None):
+    """out = pre + 255 r (Eq. 2); out may be given (same shape as pre)."""
     _need(pre, "pre")
     _need(r, "r")
-    out = torch.empty_like(pre)
+    out = torch.empty_like(pre) if out is None else out
+    _need(out, "out")
+    if out.numel() != pre.numel() or r.numel() != pre.numel():
+        raise ValueError("pre, r and out must have the same number of elements")
     check(L.lib().dn_cnn_residual_out(_vp(pre), _vp(r), _vp(out), pre.numel(), _stream(stream)), "dn_cnn_residual_out")
     return out
 

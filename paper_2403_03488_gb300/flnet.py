@@ -191,9 +191,10 @@ class FLNet(torch.nn.Module):
         r = PwFn.apply(h, P[i], P[i + 1], False)
         return r[:, 0]
 
-    def forward(self, noisy, pre, sigma):
+    def forward(self, noisy, pre, sigma, out=None):
+        """out = pre + 255 r for planes [N, H, W] (written into `out` when given)."""
         r = self.residual(noisy, pre, sigma)
-        return api.cnn_residual_out(pre.contiguous(), r.contiguous())
+        return api.cnn_residual_out(pre.contiguous(), r.contiguous(), out=out)
 
     def train_step(self, noisy, pre, clean, sigma, lr=1e-3, sync=True):
         """One L1 (Eq. 2) + Adam step; every kernel is the library's."""

@@ -1,4 +1,5 @@
-"""Training of the residual CNN (Sec. II, Eq. 2-3) on the library's kernels.
+"""Training of the residual CNN (Sec. II, Eq. 2-3), or of the flexible
+lightweight network of Sec. III (--net fl), on the library's kernels.
 
 Pairs: seeded synthetic 512 x 512 scenes, sigma ~ U[5, 50] per image (one
 blind model), noisy = clean + AWGN, pre = the GPU BM3D of the noisy image
@@ -8,6 +9,9 @@ Adam lr 1e-3, every forward / backward / update in the library's kernels
 step and crop-sampler state, so a resumed run is bit-identical.
 
     python -m paper_2403_03488_gb300.train --steps 20000 --out weights/resnet10x32_bm3d.npy
+    python -m paper_2403_03488_gb300.train --net fl --steps 20000 --out weights/flnet_bm3d.npy
+
+The flexible network also receives each crop's noise level (its input plane).
 """
 from __future__ import annotations
 
@@ -21,6 +25,7 @@ import torch
 
 from . import api, synth
 from .autograd import ResidualNet
+from .flnet import FLNet
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_OUT = os.path.join(HERE, "weights", "resnet10x32_bm3d.npy")
@@ -63,18 +68,20 @@ class CropSampler:
         i = self.rng.integers(0, self.n, self.batch)
         y = self.rng.integers(0, self.H - self.crop + 1, self.batch)
         x = self.rng.integers(0, self.W - self.crop + 1, self.batch)
+        self.last = i
         base = torch.from_numpy(i * self.H * self.W + y * self.W + x).to(self.device).view(-1, 1, 1)
         idx = base + self.offs
         return [p.view(-1)[idx] for p in pools]
 
 
 def train(steps=20000, batch=64, crop=64, lr=1e-3, seed=0, n_images=256, prefilter="bm3d", log_every=500,
-          checkpoint=None, resume=True, device="cuda", log=print):
+          checkpoint=None, resume=True, device="cuda", log=print, net_kind="resnet", max_minutes=None):
     t0 = time.time()
-    clean, noisy, pre, _ = make_pool(n_images=n_images, prefilter=prefilter, device=device)
+    clean, noisy, pre, sig = make_pool(n_images=n_images, prefilter=prefilter, device=device)
     torch.cuda.synchronize()
     log("pool of %d images ready in %.1f s" % (n_images, time.time() - t0))
-    net = ResidualNet(10, 32, seed=seed).to(device)
+    fl = net_kind == "fl"
+    net = (FLNet(seed=seed) if fl else ResidualNet(10, 32, seed=seed)).to(device)
     sampler = CropSampler(n_images, clean.shape[1], clean.shape[2], crop, batch, seed + 1, device)
     start = 0
     if checkpoint and resume and os.path.exists(checkpoint):
@@ -91,8 +98,13 @@ def train(steps=20000, batch=64, crop=64, lr=1e-3, seed=0, n_images=256, prefilt
     t1 = time.time()
     for s in range(start, steps):
         nc, pc, cc = sampler.next(noisy, pre, clean)
-        acc += net.train_step(nc, pc, cc, lr=lr, sync=False)
-        if (s + 1) % log_every == 0 or s + 1 == steps:
+        if fl:
+            acc += net.train_step(nc, pc, cc, list(sig[sampler.last]), lr=lr, sync=False)
+        else:
+            acc += net.train_step(nc, pc, cc, lr=lr, sync=False)
+        # wall-clock cap: stop at a multiple of 50 steps once the budget is spent
+        stop = max_minutes is not None and (s + 1) % 50 == 0 and time.time() - t1 > 60.0 * max_minutes
+        if (s + 1) % log_every == 0 or s + 1 == steps or stop:
             k = log_every if (s + 1) % log_every == 0 else (s + 1) % log_every
             loss = float(acc.item()) / k
             acc.zero_()
@@ -101,6 +113,9 @@ def train(steps=20000, batch=64, crop=64, lr=1e-3, seed=0, n_images=256, prefilt
             if checkpoint:
                 torch.save({"flat": net.flat.data, "m": net.m, "v": net.v, "t": net.t, "step": s + 1,
                             "rng": sampler.rng.bit_generator.state}, checkpoint)
+        if stop:
+            log("stopped at step %d (wall-clock cap of %.1f min)" % (s + 1, max_minutes))
+            break
     return net, history
 
 
@@ -127,6 +142,28 @@ def evaluate(weights, sigmas=(15.0, 25.0, 50.0), n_images=32, H=512, W=512, seed
     return res
 
 
+@torch.no_grad()
+def evaluate_fl(net, sigmas=(15.0, 25.0, 50.0), n_images=32, H=512, W=512, seed0=5000, prefilter="bm3d",
+                device="cuda"):
+    """PSNR of the nonlocal filter alone and of prefilter + flexible network on held-out scenes."""
+    res = {}
+    seeds = list(range(seed0, seed0 + n_images))
+    for s in sigmas:
+        pf, ph, pn = [], [], []
+        for c0 in range(0, n_images, 16):
+            cl, ny = synth.make_batch(seeds[c0:c0 + 16], H, W, s)
+            x = torch.from_numpy(ny).to(device)
+            c = torch.from_numpy(cl).to(device)
+            pre = api.denoise_bm3d(x, s) if prefilter == "bm3d" else api.denoise_nlm(x, s)
+            hyb = net(x[:, 0].contiguous(), pre[:, 0].contiguous(), [s] * x.shape[0]).unsqueeze(1).contiguous()
+            for t, lst in ((pre, pf), (hyb, ph), (x, pn)):
+                sse, _ = api.error_reduce(t, c)
+                lst += list((10 * torch.log10(255.0 ** 2 / (sse / (H * W)))).cpu().numpy())
+        res[s] = {"noisy": float(np.mean(pn)), prefilter: float(np.mean(pf)), "hybrid": float(np.mean(ph)),
+                  "gain_db": float(np.mean(ph) - np.mean(pf))}
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--steps", type=int, default=20000)
@@ -136,19 +173,25 @@ def main():
     ap.add_argument("--images", type=int, default=256)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--prefilter", default="bm3d", choices=["bm3d", "nlm"])
+    ap.add_argument("--net", default="resnet", choices=["resnet", "fl"],
+                    help="resnet: the 10x32 residual CNN of Sec. II; fl: the flexible network of Sec. III")
+    ap.add_argument("--max-minutes", type=float, default=None, help="stop training after this wall-clock time")
     ap.add_argument("--out", default=DEFAULT_OUT)
     ap.add_argument("--checkpoint", default=None)
     ap.add_argument("--eval-images", type=int, default=32)
     ap.add_argument("--report", default=None)
     args = ap.parse_args()
     net, hist = train(args.steps, args.batch, args.crop, args.lr, args.seed, args.images, args.prefilter,
-                      checkpoint=args.checkpoint)
+                      checkpoint=args.checkpoint, net_kind=args.net, max_minutes=args.max_minutes)
     os.makedirs(os.path.dirname(os.path.abspath(args.out)), exist_ok=True)
-    w = net.flat_weights().cpu().numpy().astype(np.float32)
+    w = net.flat.detach().cpu().numpy().astype(np.float32)
     np.save(args.out, w)
-    ev = evaluate(net.flat_weights(), n_images=args.eval_images, prefilter=args.prefilter)
-    rep = {"steps": args.steps, "batch": args.batch, "crop": args.crop, "lr": args.lr, "images": args.images,
-           "prefilter": args.prefilter, "loss_history": hist, "eval": ev}
+    if args.net == "fl":
+        ev = evaluate_fl(net, n_images=args.eval_images, prefilter=args.prefilter)
+    else:
+        ev = evaluate(net.flat_weights(), n_images=args.eval_images, prefilter=args.prefilter)
+    rep = {"net": args.net, "steps": hist[-1][0] if hist else 0, "batch": args.batch, "crop": args.crop,
+           "lr": args.lr, "images": args.images, "prefilter": args.prefilter, "loss_history": hist, "eval": ev}
     print(json.dumps(rep["eval"]))
     if args.report:
         json.dump(rep, open(args.report, "w"), indent=1)
