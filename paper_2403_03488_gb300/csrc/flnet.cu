@@ -25,29 +25,68 @@ __device__ __forceinline__ float relu_if(float v, int relu) { return relu ? fmax
 
 // ---- depthwise 3x3 ----------------------------------------------------------------
 
-__global__ void k_dw_fwd(const float *x, const float *w, const float *b, float *y, int N, int C, int H, int W,
-                         int s, int Ho, int Wo, int relu)
+constexpr int kDwRows = 16;  // output rows per thread in the depthwise forward
+
+// One block per (plane n*C + c, column chunk, band of rows); each thread owns one
+// output column and walks down kDwRows output rows keeping the three input rows
+// of its 3-tap window in registers, so each output row costs 3 (stride 1) or 6
+// (stride 2) new loads instead of 9.  Threads of a warp hold consecutive
+// columns, so every row load is coalesced.  Block shape: cw columns x (kT / cw)
+// row bands, cw = min(kT, Wo rounded up to 32).
+__global__ void __launch_bounds__(kT) k_dw_fwd(const float *__restrict__ x, const float *__restrict__ w,
+                                               const float *__restrict__ b, float *__restrict__ y, int C, int H, int W,
+                                               int s, int Ho, int Wo, int cw, int bands_per_block, int col_chunks,
+                                               int c0, int relu)
 {
-    const size_t total = (size_t)N * C * Ho * Wo;
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-        const int xo = (int)(e % Wo);
-        const int yo = (int)((e / Wo) % Ho);
-        const size_t nc = e / ((size_t)Wo * Ho);
-        const int c = (int)(nc % C);
-        const float *xp = x + nc * H * W;
-        const float *wc = w + c * 9;
-        float acc = b ? b[c] : 0.0f;
+    const size_t nc = blockIdx.y;
+    const int c = (int)((c0 + nc) % C);
+    const int chunk = blockIdx.x % col_chunks, band0 = (blockIdx.x / col_chunks) * bands_per_block;
+    const int xo = chunk * cw + (int)threadIdx.x % cw;
+    const int yo0 = (band0 + (int)threadIdx.x / cw) * kDwRows;
+    if (xo >= Wo || yo0 >= Ho) return;
+    float k[9];
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            const int yy = s * yo + i - 1;
-            if (yy < 0 || yy >= H) continue;
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                const int xx = s * xo + j - 1;
-                if (xx >= 0 && xx < W) acc = fmaf(wc[i * 3 + j], xp[(size_t)yy * W + xx], acc);
-            }
+    for (int t = 0; t < 9; ++t) k[t] = w[c * 9 + t];
+    const float bias = b ? b[c] : 0.0f;
+    const float *xp = x + nc * H * W;
+    float *yp = y + nc * Ho * Wo;
+    const int xc = s * xo;
+    const bool hl = xc - 1 >= 0, hr = xc + 1 < W;
+    auto row = [&](int yy, float &l, float &m, float &r) {
+        if (yy < 0 || yy >= H) {
+            l = m = r = 0.0f;
+            return;
         }
-        y[e] = relu_if(acc, relu);
+        const float *rp = xp + (size_t)yy * W + xc;
+        l = hl ? rp[-1] : 0.0f;
+        m = rp[0];
+        r = hr ? rp[1] : 0.0f;
+    };
+    // window rows a (top), m (middle), d (bottom) for output row yo: input rows s*yo - 1 .. s*yo + 1
+    float a0, a1, a2, m0, m1, m2, d0, d1, d2;
+    row(s * yo0 - 1, a0, a1, a2);
+    row(s * yo0, m0, m1, m2);
+    const int yend = yo0 + kDwRows < Ho ? yo0 + kDwRows : Ho;
+    for (int yo = yo0; yo < yend; ++yo) {
+        row(s * yo + 1, d0, d1, d2);
+        float acc = bias;
+        acc = fmaf(k[0], a0, acc);
+        acc = fmaf(k[1], a1, acc);
+        acc = fmaf(k[2], a2, acc);
+        acc = fmaf(k[3], m0, acc);
+        acc = fmaf(k[4], m1, acc);
+        acc = fmaf(k[5], m2, acc);
+        acc = fmaf(k[6], d0, acc);
+        acc = fmaf(k[7], d1, acc);
+        acc = fmaf(k[8], d2, acc);
+        yp[(size_t)yo * Wo + xo] = relu_if(acc, relu);
+        if (s == 1) {
+            a0 = m0, a1 = m1, a2 = m2;
+            m0 = d0, m1 = d1, m2 = d2;
+        } else {  // next window starts at the bottom row of this one
+            a0 = d0, a1 = d1, a2 = d2;
+            row(s * (yo + 1), m0, m1, m2);
+        }
     }
 }
 
@@ -139,39 +178,130 @@ __global__ void __launch_bounds__(kT) k_dw_bwd_weight(const float *x, const floa
 
 // ---- pointwise ----------------------------------------------------------------------
 
-constexpr int kPC = 16;  // output channels per thread
+constexpr int kPC = 16;   // output channels per block row (grid.y)
+constexpr int kPMax = 256; // largest Cin of the shared-memory weight block
 
 // y[n][co][p] = b[co] + sum_ci W(co, ci) x[n][ci][p], W(co, ci) = w[co * wso + ci * wsi]
 // (wso = Cin, wsi = 1 for the forward pass; wso = 1, wsi = Cout for the data
-// gradient, which multiplies by the transposed weights).
-__global__ void k_pw(const float *x, const float *w, const float *b, float *y, int N, int Cin, int Cout, int HW,
-                     int wso, int wsi, int relu)
+// gradient, which multiplies by the transposed weights).  The block's kPC x Cin
+// weights are staged once in shared memory as [ci][kPC] and read with 16-byte
+// broadcast loads; each thread owns two pixels (blockDim apart, so loads and
+// stores stay coalesced) and kPC accumulators for each.
+__global__ void __launch_bounds__(kT) k_pw(const float *__restrict__ x, const float *__restrict__ w,
+                                           const float *__restrict__ b, float *__restrict__ y, int N, int Cin,
+                                           int Cout, int HW, int wso, int wsi, int relu)
 {
-    const int cg = blockIdx.y;  // block of kPC output channels
+    __shared__ __align__(16) float ws[kPMax * kPC];
+    __shared__ float bias[kPC];
+    // blockIdx.x = output-channel chunk (fastest, so the chunks reading one pixel
+    // tile run together and the tile comes from DRAM once), blockIdx.y = pixel tile
+    const int co0 = blockIdx.x * kPC;
+    for (int i = threadIdx.x; i < Cin * kPC; i += kT) {
+        const int ci = i / kPC, k = i % kPC;
+        ws[i] = co0 + k < Cout ? w[(size_t)(co0 + k) * wso + (size_t)ci * wsi] : 0.0f;
+    }
+    if (threadIdx.x < kPC) bias[threadIdx.x] = (b && co0 + threadIdx.x < Cout) ? b[co0 + threadIdx.x] : 0.0f;
+    __syncthreads();
+    const float4 *w4 = reinterpret_cast<const float4 *>(ws);
     const size_t total = (size_t)N * HW;
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-        const size_t n = e / HW, p = e % HW;
-        const float *xp = x + n * Cin * HW + p;
-        float acc[kPC];
+    for (size_t e0 = (size_t)blockIdx.y * 2 * kT + threadIdx.x; e0 < total; e0 += (size_t)gridDim.y * 2 * kT) {
+        const size_t e1 = e0 + kT;
+        const bool has1 = e1 < total;
+        const size_t n0 = e0 / HW, p0 = e0 % HW, n1 = has1 ? e1 / HW : n0, p1 = has1 ? e1 % HW : p0;
+        const float *xp0 = x + n0 * Cin * HW + p0, *xp1 = x + n1 * Cin * HW + p1;
+        float a0[kPC], a1[kPC];
 #pragma unroll
-        for (int k = 0; k < kPC; ++k) {
-            const int co = cg * kPC + k;
-            acc[k] = (b && co < Cout) ? b[co] : 0.0f;
-        }
-        for (int ci = 0; ci < Cin; ++ci) {
-            const float xv = xp[(size_t)ci * HW];
+        for (int k = 0; k < kPC; ++k) a0[k] = a1[k] = bias[k];
+        auto step = [&](int ci, float x0, float x1) {
 #pragma unroll
-            for (int k = 0; k < kPC; ++k) {
-                const int co = cg * kPC + k;
-                if (co < Cout) acc[k] = fmaf(__ldg(w + (size_t)co * wso + (size_t)ci * wsi), xv, acc[k]);
+            for (int q = 0; q < kPC / 4; ++q) {
+                const float4 wq = w4[ci * (kPC / 4) + q];
+                a0[4 * q] = fmaf(wq.x, x0, a0[4 * q]);
+                a0[4 * q + 1] = fmaf(wq.y, x0, a0[4 * q + 1]);
+                a0[4 * q + 2] = fmaf(wq.z, x0, a0[4 * q + 2]);
+                a0[4 * q + 3] = fmaf(wq.w, x0, a0[4 * q + 3]);
+                a1[4 * q] = fmaf(wq.x, x1, a1[4 * q]);
+                a1[4 * q + 1] = fmaf(wq.y, x1, a1[4 * q + 1]);
+                a1[4 * q + 2] = fmaf(wq.z, x1, a1[4 * q + 2]);
+                a1[4 * q + 3] = fmaf(wq.w, x1, a1[4 * q + 3]);
             }
-        }
-        float *yp = y + n * Cout * HW + p;
+        };
+        int ci = 0;
+        for (; ci + 4 <= Cin; ci += 4) {  // four input channels' loads in flight at once
+            float u0[4], u1[4];
 #pragma unroll
-        for (int k = 0; k < kPC; ++k) {
-            const int co = cg * kPC + k;
-            if (co < Cout) yp[(size_t)co * HW] = relu_if(acc[k], relu);
+            for (int q = 0; q < 4; ++q) {
+                u0[q] = xp0[(size_t)(ci + q) * HW];
+                u1[q] = xp1[(size_t)(ci + q) * HW];
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) step(ci + q, u0[q], u1[q]);
         }
+        for (; ci < Cin; ++ci) step(ci, xp0[(size_t)ci * HW], xp1[(size_t)ci * HW]);
+        float *yp0 = y + n0 * Cout * HW + p0, *yp1 = y + n1 * Cout * HW + p1;
+#pragma unroll
+        for (int k = 0; k < kPC; ++k)
+            if (co0 + k < Cout) {
+                yp0[(size_t)k * HW + (size_t)co0 * HW] = relu_if(a0[k], relu);
+                if (has1) yp1[(size_t)k * HW + (size_t)co0 * HW] = relu_if(a1[k], relu);
+            }
+    }
+}
+
+// Vector form of k_pw for HW % 4 == 0 with 16-byte aligned x and y: each thread
+// owns four consecutive pixels of one image (one float4 per channel row), so a
+// warp's load moves 512 bytes and four channels' loads are in flight together.
+__global__ void __launch_bounds__(kT) k_pw4(const float *__restrict__ x, const float *__restrict__ w,
+                                            const float *__restrict__ b, float *__restrict__ y, int N, int Cin,
+                                            int Cout, int HW, int wso, int wsi, int relu)
+{
+    __shared__ __align__(16) float ws[kPMax * kPC];
+    __shared__ float bias[kPC];
+    const int co0 = blockIdx.x * kPC;
+    for (int i = threadIdx.x; i < Cin * kPC; i += kT) {
+        const int ci = i / kPC, k = i % kPC;
+        ws[i] = co0 + k < Cout ? w[(size_t)(co0 + k) * wso + (size_t)ci * wsi] : 0.0f;
+    }
+    if (threadIdx.x < kPC) bias[threadIdx.x] = (b && co0 + threadIdx.x < Cout) ? b[co0 + threadIdx.x] : 0.0f;
+    __syncthreads();
+    const float4 *w4 = reinterpret_cast<const float4 *>(ws);
+    const size_t HW4 = (size_t)HW / 4, total = (size_t)N * HW4;
+    for (size_t e = (size_t)blockIdx.y * kT + threadIdx.x; e < total; e += (size_t)gridDim.y * kT) {
+        const size_t n = e / HW4, q = e % HW4;
+        const float4 *xp = reinterpret_cast<const float4 *>(x) + n * Cin * HW4 + q;
+        float a[kPC][4];
+#pragma unroll
+        for (int k = 0; k < kPC; ++k) a[k][0] = a[k][1] = a[k][2] = a[k][3] = bias[k];
+        auto step = [&](int ci, float4 v) {
+#pragma unroll
+            for (int g = 0; g < kPC / 4; ++g) {
+                const float4 wq = w4[ci * (kPC / 4) + g];
+                const float wk[4] = {wq.x, wq.y, wq.z, wq.w};
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    float *ak = a[4 * g + t];
+                    ak[0] = fmaf(wk[t], v.x, ak[0]);
+                    ak[1] = fmaf(wk[t], v.y, ak[1]);
+                    ak[2] = fmaf(wk[t], v.z, ak[2]);
+                    ak[3] = fmaf(wk[t], v.w, ak[3]);
+                }
+            }
+        };
+        int ci = 0;
+        for (; ci + 4 <= Cin; ci += 4) {
+            float4 u[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) u[t] = xp[(size_t)(ci + t) * HW4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) step(ci + t, u[t]);
+        }
+        for (; ci < Cin; ++ci) step(ci, xp[(size_t)ci * HW4]);
+        float4 *yp = reinterpret_cast<float4 *>(y) + (n * Cout + co0) * HW4 + q;
+#pragma unroll
+        for (int k = 0; k < kPC; ++k)
+            if (co0 + k < Cout)
+                yp[(size_t)k * HW4] = make_float4(relu_if(a[k][0], relu), relu_if(a[k][1], relu),
+                                                  relu_if(a[k][2], relu), relu_if(a[k][3], relu));
     }
 }
 
@@ -209,20 +339,28 @@ __global__ void __launch_bounds__(kT) k_pw_bwd_weight(const float *x, const floa
 constexpr int kDC = 8;  // output channels per thread
 
 // One thread per input pixel (n, i, j) and block of kDC output channels: the
-// 2 x 2 output pixels it feeds.
-__global__ void k_deconv_fwd(const float *x, const float *w, const float *b, const float *skip, float *y, int N,
-                             int Cin, int Cout, int H, int W)
+// 2 x 2 output pixels it feeds.  The block's Cin x kDC x 4 weights are staged
+// in shared memory ([ci][k][a][c], 16-byte broadcast loads).
+__global__ void __launch_bounds__(kT) k_deconv_fwd(const float *x, const float *w, const float *b, const float *skip,
+                                                   float *y, int N, int Cin, int Cout, int H, int W)
 {
-    const int cg = blockIdx.y;
+    __shared__ __align__(16) float ws[kPMax * kDC * 4];
+    const int co0 = blockIdx.x * kDC;  // output-channel chunk fastest (pixel tile read once from DRAM)
+    for (int i = threadIdx.x; i < Cin * kDC * 4; i += kT) {
+        const int ci = i / (kDC * 4), k = (i / 4) % kDC, t = i % 4;
+        ws[i] = co0 + k < Cout ? w[((size_t)ci * Cout + co0 + k) * 4 + t] : 0.0f;
+    }
+    __syncthreads();
+    const float4 *w4 = reinterpret_cast<const float4 *>(ws);
     const size_t HW = (size_t)H * W, total = (size_t)N * HW;
     const int W2 = 2 * W;
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    for (size_t e = (size_t)blockIdx.y * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.y * blockDim.x) {
         const size_t n = e / HW, q = e % HW;
         const int i = (int)(q / W), j = (int)(q % W);
         float acc[kDC][4];
 #pragma unroll
         for (int k = 0; k < kDC; ++k) {
-            const int co = cg * kDC + k;
+            const int co = co0 + k;
             const float bb = (b && co < Cout) ? b[co] : 0.0f;
 #pragma unroll
             for (int t = 0; t < 4; ++t) acc[k][t] = bb;
@@ -232,25 +370,98 @@ __global__ void k_deconv_fwd(const float *x, const float *w, const float *b, con
             const float xv = xp[(size_t)ci * HW];
 #pragma unroll
             for (int k = 0; k < kDC; ++k) {
-                const int co = cg * kDC + k;
-                if (co < Cout) {
-                    const float4 w4 = __ldg(reinterpret_cast<const float4 *>(w + ((size_t)ci * Cout + co) * 4));
-                    acc[k][0] = fmaf(w4.x, xv, acc[k][0]);
-                    acc[k][1] = fmaf(w4.y, xv, acc[k][1]);
-                    acc[k][2] = fmaf(w4.z, xv, acc[k][2]);
-                    acc[k][3] = fmaf(w4.w, xv, acc[k][3]);
-                }
+                const float4 w4v = w4[ci * kDC + k];
+                acc[k][0] = fmaf(w4v.x, xv, acc[k][0]);
+                acc[k][1] = fmaf(w4v.y, xv, acc[k][1]);
+                acc[k][2] = fmaf(w4v.z, xv, acc[k][2]);
+                acc[k][3] = fmaf(w4v.w, xv, acc[k][3]);
             }
         }
 #pragma unroll
         for (int k = 0; k < kDC; ++k) {
-            const int co = cg * kDC + k;
+            const int co = co0 + k;
             if (co >= Cout) continue;
             const size_t base = ((n * Cout + co) * (2 * H) + 2 * i) * (size_t)W2 + 2 * j;
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
                 const size_t o = base + (size_t)(t >> 1) * W2 + (t & 1);
                 y[o] = acc[k][t] + (skip ? skip[o] : 0.0f);
+            }
+        }
+    }
+}
+
+constexpr int kDC4 = 4;  // output channels per block in the vector transposed conv
+
+// Vector form of k_deconv_fwd for W % 4 == 0 with 16-byte aligned x, y and skip:
+// each thread owns four consecutive input pixels of a row (one float4 per
+// channel) and kDC4 output channels, i.e. two 8-wide output row segments per
+// channel, stored as float4 pairs.
+__global__ void __launch_bounds__(kT) k_deconv_fwd4(const float *__restrict__ x, const float *__restrict__ w,
+                                                    const float *__restrict__ b, const float *__restrict__ skip,
+                                                    float *__restrict__ y, int N, int Cin, int Cout, int H, int W)
+{
+    __shared__ __align__(16) float ws[kPMax * kDC4 * 4];
+    const int co0 = blockIdx.x * kDC4;
+    for (int i = threadIdx.x; i < Cin * kDC4 * 4; i += kT) {
+        const int ci = i / (kDC4 * 4), k = (i / 4) % kDC4, t = i % 4;
+        ws[i] = co0 + k < Cout ? w[((size_t)ci * Cout + co0 + k) * 4 + t] : 0.0f;
+    }
+    __syncthreads();
+    const float4 *w4 = reinterpret_cast<const float4 *>(ws);
+    const int W4 = W / 4, W2 = 2 * W;
+    const size_t HW4 = (size_t)H * W4, total = (size_t)N * HW4;
+    for (size_t e = (size_t)blockIdx.y * kT + threadIdx.x; e < total; e += (size_t)gridDim.y * kT) {
+        const size_t n = e / HW4, q = e % HW4;
+        const int i = (int)(q / W4), j = 4 * (int)(q % W4);
+        float acc[kDC4][4][4];  // [co][tap a*2+c][pixel]
+#pragma unroll
+        for (int k = 0; k < kDC4; ++k) {
+            const float bb = (b && co0 + k < Cout) ? b[co0 + k] : 0.0f;
+#pragma unroll
+            for (int t = 0; t < 4; ++t) acc[k][t][0] = acc[k][t][1] = acc[k][t][2] = acc[k][t][3] = bb;
+        }
+        const float4 *xp = reinterpret_cast<const float4 *>(x) + n * Cin * HW4 + q;
+        auto step = [&](int ci, float4 v) {
+#pragma unroll
+            for (int k = 0; k < kDC4; ++k) {
+                const float4 wq = w4[ci * kDC4 + k];
+                const float wt[4] = {wq.x, wq.y, wq.z, wq.w};
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    acc[k][t][0] = fmaf(wt[t], v.x, acc[k][t][0]);
+                    acc[k][t][1] = fmaf(wt[t], v.y, acc[k][t][1]);
+                    acc[k][t][2] = fmaf(wt[t], v.z, acc[k][t][2]);
+                    acc[k][t][3] = fmaf(wt[t], v.w, acc[k][t][3]);
+                }
+            }
+        };
+        int ci = 0;
+        for (; ci + 4 <= Cin; ci += 4) {
+            float4 u[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) u[t] = xp[(size_t)(ci + t) * HW4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) step(ci + t, u[t]);
+        }
+        for (; ci < Cin; ++ci) step(ci, xp[(size_t)ci * HW4]);
+#pragma unroll
+        for (int k = 0; k < kDC4; ++k) {
+            if (co0 + k >= Cout) continue;
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                // output row 2i + a, columns 2j .. 2j + 7: taps (a, 0), (a, 1) of pixels j .. j + 3
+                const size_t o = ((n * Cout + co0 + k) * (2 * (size_t)H) + 2 * i + a) * (size_t)W2 + 2 * j;
+                const float *c0 = acc[k][2 * a], *c1 = acc[k][2 * a + 1];
+                float4 lo = make_float4(c0[0], c1[0], c0[1], c1[1]), hi = make_float4(c0[2], c1[2], c0[3], c1[3]);
+                if (skip) {
+                    const float4 s0 = *reinterpret_cast<const float4 *>(skip + o);
+                    const float4 s1 = *reinterpret_cast<const float4 *>(skip + o + 4);
+                    lo.x += s0.x, lo.y += s0.y, lo.z += s0.z, lo.w += s0.w;
+                    hi.x += s1.x, hi.y += s1.y, hi.z += s1.z, hi.w += s1.w;
+                }
+                *reinterpret_cast<float4 *>(y + o) = lo;
+                *reinterpret_cast<float4 *>(y + o + 4) = hi;
             }
         }
     }
@@ -343,6 +554,8 @@ int blocks_for(size_t total)
     return (int)(b < 152 * 32 ? (b > 0 ? b : 1) : 152 * 32);
 }
 
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
 bool dims_ok(long a, long b, long c, long d) { return a >= 1 && b >= 1 && c >= 1 && d >= 1; }
 
 }  // namespace
@@ -358,10 +571,20 @@ dn_status dn_dw3x3_fwd(const float *x, const float *w, const float *b, float *y,
 {
     if (!x || !w || !y || !dims_ok(N, C, H, W) || (stride != 1 && stride != 2)) return DN_EINVAL;
     const int Ho = (H + stride - 1) / stride, Wo = (W + stride - 1) / stride;
-    const size_t total = (size_t)N * C * Ho * Wo;
-    return launch("fl_dw3x3_fwd", (cudaStream_t)stream, [&] {
-        k_dw_fwd<<<blocks_for(total), kT, 0, (cudaStream_t)stream>>>(x, w, b, y, N, C, H, W, stride, Ho, Wo, relu);
-    });
+    const int cw = Wo >= kT ? kT : (Wo + 31) / 32 * 32, bpb = kT / cw;
+    const int col_chunks = (Wo + cw - 1) / cw, bands = (Ho + kDwRows - 1) / kDwRows;
+    const int gx = col_chunks * ((bands + bpb - 1) / bpb);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t planes = (size_t)N * C, in_plane = (size_t)H * W, out_plane = (size_t)Ho * Wo;
+    for (size_t p0 = 0; p0 < planes; p0 += 65535) {  // grid.y = planes of this launch
+        const unsigned np = (unsigned)(planes - p0 < 65535 ? planes - p0 : 65535);
+        // this launch's first plane has channel p0 % C
+        DN_TRY(launch("fl_dw3x3_fwd", s, [&] {
+            k_dw_fwd<<<dim3(gx, np), kT, 0, s>>>(x + p0 * in_plane, w, b, y + p0 * out_plane, C, H, W, stride, Ho, Wo,
+                                                 cw, bpb, col_chunks, (int)(p0 % C), relu);
+        }));
+    }
+    return DN_OK;
 }
 
 dn_status dn_dw3x3_bwd(const float *x, const float *g, const float *w, float *dx, float *dw, float *db, int N, int C,
@@ -382,10 +605,14 @@ dn_status dn_dw3x3_bwd(const float *x, const float *g, const float *w, float *dx
 dn_status dn_pw_fwd(const float *x, const float *w, const float *b, float *y, int N, int Cin, int Cout, int HW,
                     int relu, int transposed, dn_stream_t stream)
 {
-    if (!x || !w || !y || !dims_ok(N, Cin, Cout, HW)) return DN_EINVAL;
+    if (!x || !w || !y || !dims_ok(N, Cin, Cout, HW) || Cin > kPMax) return DN_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
-    dim3 grid(blocks_for((size_t)N * HW), (Cout + kPC - 1) / kPC);
+    dim3 grid((Cout + kPC - 1) / kPC, blocks_for(((size_t)N * HW + 1) / 2));
     const int wso = transposed ? 1 : Cin, wsi = transposed ? Cout : 1;
+    if (HW % 4 == 0 && aligned16(x) && aligned16(y)) {
+        dim3 g4((Cout + kPC - 1) / kPC, blocks_for((size_t)N * HW / 4));
+        return launch("fl_pw_fwd", s, [&] { k_pw4<<<g4, kT, 0, s>>>(x, w, b, y, N, Cin, Cout, HW, wso, wsi, relu); });
+    }
     return launch("fl_pw_fwd", s, [&] { k_pw<<<grid, kT, 0, s>>>(x, w, b, y, N, Cin, Cout, HW, wso, wsi, relu); });
 }
 
@@ -401,10 +628,15 @@ dn_status dn_pw_bwd_weight(const float *x, const float *g, float *dw, float *db,
 dn_status dn_deconv2x2_fwd(const float *x, const float *w, const float *b, const float *skip, float *y, int N, int Cin,
                            int Cout, int H, int W, dn_stream_t stream)
 {
-    if (!x || !w || !y || !dims_ok(N, Cin, Cout, (long)H * W)) return DN_EINVAL;
+    if (!x || !w || !y || !dims_ok(N, Cin, Cout, (long)H * W) || Cin > kPMax) return DN_EINVAL;
     if ((reinterpret_cast<uintptr_t>(w) & 15) != 0) return DN_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
-    dim3 grid(blocks_for((size_t)N * H * W), (Cout + kDC - 1) / kDC);
+    if (W % 4 == 0 && aligned16(x) && aligned16(y) && (!skip || aligned16(skip))) {
+        dim3 g4((Cout + kDC4 - 1) / kDC4, blocks_for((size_t)N * H * W / 4));
+        return launch("fl_deconv2x2_fwd", s,
+                      [&] { k_deconv_fwd4<<<g4, kT, 0, s>>>(x, w, b, skip, y, N, Cin, Cout, H, W); });
+    }
+    dim3 grid((Cout + kDC - 1) / kDC, blocks_for((size_t)N * H * W));
     return launch("fl_deconv2x2_fwd", s, [&] { k_deconv_fwd<<<grid, kT, 0, s>>>(x, w, b, skip, y, N, Cin, Cout, H, W); });
 }
 

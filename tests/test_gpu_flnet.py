@@ -33,16 +33,21 @@ def close(a, b, rel=1e-5):
         np.abs(np.asarray(a, np.float64) - b).max(), np.abs(b).max())
 
 
-@pytest.mark.parametrize("stride,relu", [(1, False), (2, False), (1, True), (2, True)])
-def test_depthwise_forward_and_backward(oracle, stride, relu):
+@pytest.mark.parametrize("stride,relu,shape", [(1, False, (2, 5, 13, 18)), (2, False, (2, 5, 13, 18)),
+                                               (1, True, (2, 5, 13, 18)), (2, True, (2, 5, 13, 18)),
+                                               (1, True, (2, 3, 70, 301)), (2, False, (3, 3, 71, 600))])
+def test_depthwise_forward_and_backward(oracle, stride, relu, shape):
+    """Small planes, and planes with several 16-row bands and 256-column chunks
+    (ragged in both) for the banded forward kernel."""
     _, F = oracle._fl_torch()
     rng = np.random.default_rng(stride)
-    x = rng.standard_normal((2, 5, 13, 18)).astype(np.float32)
-    w = rng.standard_normal((5, 3, 3)).astype(np.float32)
-    b = rng.standard_normal(5).astype(np.float32)
+    C = shape[1]
+    x = rng.standard_normal(shape).astype(np.float32)
+    w = rng.standard_normal((C, 3, 3)).astype(np.float32)
+    b = rng.standard_normal(C).astype(np.float32)
     y = host(A().dw3x3_fwd(dev(x), dev(w), dev(b), stride=stride, relu=relu))
-    yr, (tx, tw, tb) = ref_grads(lambda X, Wt, B: F.conv2d(X, Wt.reshape(5, 1, 3, 3), B, stride=stride, padding=1,
-                                                           groups=5), x, w, b)
+    yr, (tx, tw, tb) = ref_grads(lambda X, Wt, B: F.conv2d(X, Wt.reshape(C, 1, 3, 3), B, stride=stride, padding=1,
+                                                           groups=C), x, w, b)
     close(y, (yr.clamp(min=0) if relu else yr).detach().numpy())
     g = rng.standard_normal(yr.shape).astype(np.float32)
     yr.backward(torch.as_tensor(g, dtype=torch.float64))
@@ -52,15 +57,21 @@ def test_depthwise_forward_and_backward(oracle, stride, relu):
     close(host(db), tb.grad.numpy(), 1e-4)
 
 
-@pytest.mark.parametrize("relu", [False, True])
-def test_pointwise_forward_and_backward(oracle, relu):
+@pytest.mark.parametrize("relu,shape,cout", [(False, (2, 20, 7, 9), 37), (True, (2, 20, 7, 9), 37),
+                                             (True, (3, 21, 37, 41), 18), (False, (1, 3, 64, 33), 48),
+                                             (True, (2, 21, 16, 20), 18)])
+def test_pointwise_forward_and_backward(oracle, relu, shape, cout):
+    """Channel counts off the 4-channel load groups and the 16-channel blocks,
+    pixel counts over several 512-pixel tiles with a ragged tail; the last two
+    shapes (pixels per image a multiple of 4) take the float4 kernel."""
     _, F = oracle._fl_torch()
     rng = np.random.default_rng(7)
-    x = rng.standard_normal((2, 20, 7, 9)).astype(np.float32)
-    w = rng.standard_normal((37, 20)).astype(np.float32)
-    b = rng.standard_normal(37).astype(np.float32)
+    cin = shape[1]
+    x = rng.standard_normal(shape).astype(np.float32)
+    w = rng.standard_normal((cout, cin)).astype(np.float32)
+    b = rng.standard_normal(cout).astype(np.float32)
     y = host(A().pw_fwd(dev(x), dev(w), dev(b), relu=relu))
-    yr, (tx, tw, tb) = ref_grads(lambda X, Wt, B: F.conv2d(X, Wt.reshape(37, 20, 1, 1), B), x, w, b)
+    yr, (tx, tw, tb) = ref_grads(lambda X, Wt, B: F.conv2d(X, Wt.reshape(cout, cin, 1, 1), B), x, w, b)
     close(y, (yr.clamp(min=0) if relu else yr).detach().numpy())
     g = rng.standard_normal(yr.shape).astype(np.float32)
     yr.backward(torch.as_tensor(g, dtype=torch.float64))
@@ -70,13 +81,16 @@ def test_pointwise_forward_and_backward(oracle, relu):
     close(host(db), tb.grad.numpy(), 1e-4)
 
 
-def test_transposed_convolution_forward_and_backward(oracle):
+@pytest.mark.parametrize("shape", [(2, 13, 5, 6), (2, 13, 5, 8), (1, 7, 9, 36)])
+def test_transposed_convolution_forward_and_backward(oracle, shape):
+    """Odd channel counts; widths that are multiples of 4 take the float4 kernel."""
     _, F = oracle._fl_torch()
     rng = np.random.default_rng(9)
-    x = rng.standard_normal((2, 13, 5, 6)).astype(np.float32)
-    w = rng.standard_normal((13, 11, 2, 2)).astype(np.float32)
+    n, cin, h, wd = shape
+    x = rng.standard_normal(shape).astype(np.float32)
+    w = rng.standard_normal((cin, 11, 2, 2)).astype(np.float32)
     b = rng.standard_normal(11).astype(np.float32)
-    skip = rng.standard_normal((2, 11, 10, 12)).astype(np.float32)
+    skip = rng.standard_normal((n, 11, 2 * h, 2 * wd)).astype(np.float32)
     y = host(A().deconv2x2_fwd(dev(x), dev(w), dev(b), dev(skip)))
     yr, (tx, tw, tb) = ref_grads(lambda X, Wt, B: F.conv_transpose2d(X, Wt, B, stride=2), x, w, b)
     close(y, yr.detach().numpy() + skip)
