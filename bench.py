@@ -130,6 +130,13 @@ def algorithmic(kernel, launches_per_step, batch):
         flops = 2.0 * H * W * batch * (2 * 32 * 9 + 8 * 32 * 32 * 9 + 32 * 9) / launches_per_step
         return "alu", "TFLOP/s", flops, fp32_peak, FP32_PEAK_TFLOPS_NOTE + " (derived, not measured)"
     hbm = peaks.get("hbm_gbs", 6800.0)
+    if kernel.startswith(("fl_pw_fwd", "fl_deconv2x2_fwd", "fl_dw3x3_fwd")):
+        from paper_2403_03488_gb300.flnet import work_per_pixel
+        wpp, px = work_per_pixel(), H * W * batch / launches_per_step
+        if kernel.startswith("fl_dw3x3_fwd"):  # 9 MAC per output: moves bytes, not FLOPs
+            return "hbm", "GB/s", wpp["dw_bytes"] * px, hbm, "measured hbm_gbs"
+        macs = wpp["pw_macs"] if kernel.startswith("fl_pw_fwd") else wpp["up_macs"]
+        return "alu", "TFLOP/s", 2.0 * macs * px, fp32_peak, FP32_PEAK_TFLOPS_NOTE + " (derived, not measured)"
     # fall back to bytes: read + write of the image planes
     return "hbm", "GB/s", 8.0 * H * W * batch / launches_per_step, hbm, "measured hbm_gbs"
 
@@ -159,9 +166,9 @@ def kernel_rooflines(res, steps, batch, launches_per_step=None):
             ach = bytes_per_launch[k] / (avg / 1e3) / 1e9
             out[k] = {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
                       "frac": round(ach / hbm, 4), "avg_launch_ms": round(avg, 4)}
-        elif k.startswith("bm3d_match_fp32"):
+        elif k.startswith(("bm3d_match_fp32", "nlm_fp32", "fl_")) and not k.startswith("fl_pack"):
             bound, unit, work, peak, _ = algorithmic(k, n / steps, batch)
-            ach = work / (avg / 1e3) / 1e12
+            ach = work / (avg / 1e3) / (1e12 if unit == "TFLOP/s" else 1e9)
             out[k] = {"bound": bound, "achieved": round(ach, 3), "peak": round(peak, 1), "unit": unit,
                       "frac": round(ach / peak, 4), "avg_launch_ms": round(avg, 4)}
     return out
@@ -233,7 +240,7 @@ def run_ours(args):
 
     fl = args.net == "fl"
     if fl:
-        flnet, wsrc = load_fl(dev)
+        flnet, wsrc = load_fl(dev, args.prefilter)
         pre_d = torch.empty_like(noisy_d)
         ws_pre = torch.empty(api.bm3d_workspace_bytes(B, 1, H, W, bp) if not nlm else 1, dtype=torch.uint8,
                              device=dev)
@@ -432,11 +439,12 @@ def load_weights(dev):
     return ResidualNet(10, 32, seed=0).to(dev).flat_weights(), "random init (He, seed 0)"
 
 
-def load_fl(dev):
-    """The flexible network with the shipped trained weights when present, else He init (seed 0)."""
+def load_fl(dev, prefilter="bm3d"):
+    """The flexible network with the shipped weights trained on this prefilter's
+    output when present, else He init (seed 0)."""
     from paper_2403_03488_gb300.flnet import FLNet
     import torch
-    p = os.path.join(ROOT, "paper_2403_03488_gb300", "weights", "flnet_bm3d.npy")
+    p = os.path.join(ROOT, "paper_2403_03488_gb300", "weights", "flnet_%s.npy" % prefilter)
     if os.path.exists(p):
         return FLNet(flat=torch.from_numpy(np.load(p).astype(np.float32))).to(dev), \
             "trained weights (" + os.path.basename(p) + ")"

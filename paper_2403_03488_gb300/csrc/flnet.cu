@@ -25,68 +25,60 @@ __device__ __forceinline__ float relu_if(float v, int relu) { return relu ? fmax
 
 // ---- depthwise 3x3 ----------------------------------------------------------------
 
-constexpr int kDwRows = 16;  // output rows per thread in the depthwise forward
+// Output rows per thread in the depthwise forward: the thread loads the
+// S * (rows - 1) + 3 input rows of its 3-column window at once (all loads in
+// flight together), then forms the outputs from registers.
+template <int S> struct DwRows {
+    static constexpr int value = S == 1 ? 16 : 8;
+};
 
 // One block per (plane n*C + c, column chunk, band of rows); each thread owns one
-// output column and walks down kDwRows output rows keeping the three input rows
-// of its 3-tap window in registers, so each output row costs 3 (stride 1) or 6
-// (stride 2) new loads instead of 9.  Threads of a warp hold consecutive
-// columns, so every row load is coalesced.  Block shape: cw columns x (kT / cw)
-// row bands, cw = min(kT, Wo rounded up to 32).
+// output column of a band.  Threads of a warp hold consecutive columns, so every
+// row load is coalesced.  Block shape: cw columns x (kT / cw) bands, cw =
+// min(kT, Wo rounded up to 32).  Zero padding outside the image.
+template <int S>
 __global__ void __launch_bounds__(kT) k_dw_fwd(const float *__restrict__ x, const float *__restrict__ w,
                                                const float *__restrict__ b, float *__restrict__ y, int C, int H, int W,
-                                               int s, int Ho, int Wo, int cw, int bands_per_block, int col_chunks,
-                                               int c0, int relu)
+                                               int Ho, int Wo, int cw, int bands_per_block, int col_chunks, int c0,
+                                               int relu)
 {
+    constexpr int R = DwRows<S>::value, IN = S * (R - 1) + 3;
     const size_t nc = blockIdx.y;
     const int c = (int)((c0 + nc) % C);
     const int chunk = blockIdx.x % col_chunks, band0 = (blockIdx.x / col_chunks) * bands_per_block;
     const int xo = chunk * cw + (int)threadIdx.x % cw;
-    const int yo0 = (band0 + (int)threadIdx.x / cw) * kDwRows;
+    const int yo0 = (band0 + (int)threadIdx.x / cw) * R;
     if (xo >= Wo || yo0 >= Ho) return;
+    const float *xp = x + nc * H * W;
+    const int xc = S * xo, y0 = S * yo0 - 1;
+    const bool hl = xc - 1 >= 0, hr = xc + 1 < W;
+    float v[IN][3];
+#pragma unroll
+    for (int r = 0; r < IN; ++r) {
+        const int yy = y0 + r;
+        if (yy >= 0 && yy < H) {
+            const float *rp = xp + (size_t)yy * W + xc;
+            v[r][0] = hl ? rp[-1] : 0.0f;
+            v[r][1] = rp[0];
+            v[r][2] = hr ? rp[1] : 0.0f;
+        } else {
+            v[r][0] = v[r][1] = v[r][2] = 0.0f;
+        }
+    }
     float k[9];
 #pragma unroll
     for (int t = 0; t < 9; ++t) k[t] = w[c * 9 + t];
     const float bias = b ? b[c] : 0.0f;
-    const float *xp = x + nc * H * W;
-    float *yp = y + nc * Ho * Wo;
-    const int xc = s * xo;
-    const bool hl = xc - 1 >= 0, hr = xc + 1 < W;
-    auto row = [&](int yy, float &l, float &m, float &r) {
-        if (yy < 0 || yy >= H) {
-            l = m = r = 0.0f;
-            return;
-        }
-        const float *rp = xp + (size_t)yy * W + xc;
-        l = hl ? rp[-1] : 0.0f;
-        m = rp[0];
-        r = hr ? rp[1] : 0.0f;
-    };
-    // window rows a (top), m (middle), d (bottom) for output row yo: input rows s*yo - 1 .. s*yo + 1
-    float a0, a1, a2, m0, m1, m2, d0, d1, d2;
-    row(s * yo0 - 1, a0, a1, a2);
-    row(s * yo0, m0, m1, m2);
-    const int yend = yo0 + kDwRows < Ho ? yo0 + kDwRows : Ho;
-    for (int yo = yo0; yo < yend; ++yo) {
-        row(s * yo + 1, d0, d1, d2);
+    float *yp = y + nc * Ho * Wo + xo;
+#pragma unroll
+    for (int o = 0; o < R; ++o) {
+        if (yo0 + o >= Ho) break;
         float acc = bias;
-        acc = fmaf(k[0], a0, acc);
-        acc = fmaf(k[1], a1, acc);
-        acc = fmaf(k[2], a2, acc);
-        acc = fmaf(k[3], m0, acc);
-        acc = fmaf(k[4], m1, acc);
-        acc = fmaf(k[5], m2, acc);
-        acc = fmaf(k[6], d0, acc);
-        acc = fmaf(k[7], d1, acc);
-        acc = fmaf(k[8], d2, acc);
-        yp[(size_t)yo * Wo + xo] = relu_if(acc, relu);
-        if (s == 1) {
-            a0 = m0, a1 = m1, a2 = m2;
-            m0 = d0, m1 = d1, m2 = d2;
-        } else {  // next window starts at the bottom row of this one
-            a0 = d0, a1 = d1, a2 = d2;
-            row(s * (yo + 1), m0, m1, m2);
-        }
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) acc = fmaf(k[i * 3 + j], v[S * o + i][j], acc);
+        yp[(size_t)(yo0 + o) * Wo] = relu_if(acc, relu);
     }
 }
 
@@ -248,6 +240,47 @@ __global__ void __launch_bounds__(kT) k_pw(const float *__restrict__ x, const fl
     }
 }
 
+// Feeds step(ci, v) the float4 xp[ci * stride] of every channel ci < Cin in
+// order, loading four channels at a time; with Prefetch the next four are
+// loaded while the current ones are consumed (eight 16-byte loads in flight
+// per thread, at the cost of 16 registers).
+template <bool Prefetch, class Step>
+__device__ __forceinline__ void quad_channels(const float4 *__restrict__ xp, size_t stride, int Cin, Step &step)
+{
+    int ci = 0;
+    if (!Prefetch) {
+        for (; ci + 4 <= Cin; ci += 4) {
+            float4 u[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) u[t] = xp[(size_t)(ci + t) * stride];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) step(ci + t, u[t]);
+        }
+        for (; ci < Cin; ++ci) step(ci, xp[(size_t)ci * stride]);
+        return;
+    }
+    float4 u[4];
+    if (Cin >= 4) {
+#pragma unroll
+        for (int t = 0; t < 4; ++t) u[t] = xp[(size_t)t * stride];
+    }
+    for (; ci + 4 <= Cin; ci += 4) {
+        float4 nx[4];
+        const bool more = ci + 8 <= Cin;
+        if (more) {
+#pragma unroll
+            for (int t = 0; t < 4; ++t) nx[t] = xp[(size_t)(ci + 4 + t) * stride];
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) step(ci + t, u[t]);
+        if (more) {
+#pragma unroll
+            for (int t = 0; t < 4; ++t) u[t] = nx[t];
+        }
+    }
+    for (; ci < Cin; ++ci) step(ci, xp[(size_t)ci * stride]);
+}
+
 // Vector form of k_pw for HW % 4 == 0 with 16-byte aligned x and y: each thread
 // owns four consecutive pixels of one image (one float4 per channel row), so a
 // warp's load moves 512 bytes and four channels' loads are in flight together.
@@ -287,15 +320,7 @@ __global__ void __launch_bounds__(kT) k_pw4(const float *__restrict__ x, const f
                 }
             }
         };
-        int ci = 0;
-        for (; ci + 4 <= Cin; ci += 4) {
-            float4 u[4];
-#pragma unroll
-            for (int t = 0; t < 4; ++t) u[t] = xp[(size_t)(ci + t) * HW4];
-#pragma unroll
-            for (int t = 0; t < 4; ++t) step(ci + t, u[t]);
-        }
-        for (; ci < Cin; ++ci) step(ci, xp[(size_t)ci * HW4]);
+        quad_channels<false>(xp, HW4, Cin, step);  // measured: prefetching is slower here
         float4 *yp = reinterpret_cast<float4 *>(y) + (n * Cout + co0) * HW4 + q;
 #pragma unroll
         for (int k = 0; k < kPC; ++k)
@@ -397,7 +422,7 @@ constexpr int kDC4 = 4;  // output channels per block in the vector transposed c
 // each thread owns four consecutive input pixels of a row (one float4 per
 // channel) and kDC4 output channels, i.e. two 8-wide output row segments per
 // channel, stored as float4 pairs.
-__global__ void __launch_bounds__(kT) k_deconv_fwd4(const float *__restrict__ x, const float *__restrict__ w,
+__global__ void __launch_bounds__(kT, 2) k_deconv_fwd4(const float *__restrict__ x, const float *__restrict__ w,
                                                     const float *__restrict__ b, const float *__restrict__ skip,
                                                     float *__restrict__ y, int N, int Cin, int Cout, int H, int W)
 {
@@ -436,15 +461,7 @@ __global__ void __launch_bounds__(kT) k_deconv_fwd4(const float *__restrict__ x,
                 }
             }
         };
-        int ci = 0;
-        for (; ci + 4 <= Cin; ci += 4) {
-            float4 u[4];
-#pragma unroll
-            for (int t = 0; t < 4; ++t) u[t] = xp[(size_t)(ci + t) * HW4];
-#pragma unroll
-            for (int t = 0; t < 4; ++t) step(ci + t, u[t]);
-        }
-        for (; ci < Cin; ++ci) step(ci, xp[(size_t)ci * HW4]);
+        quad_channels<true>(xp, HW4, Cin, step);
 #pragma unroll
         for (int k = 0; k < kDC4; ++k) {
             if (co0 + k >= Cout) continue;
@@ -572,16 +589,21 @@ dn_status dn_dw3x3_fwd(const float *x, const float *w, const float *b, float *y,
     if (!x || !w || !y || !dims_ok(N, C, H, W) || (stride != 1 && stride != 2)) return DN_EINVAL;
     const int Ho = (H + stride - 1) / stride, Wo = (W + stride - 1) / stride;
     const int cw = Wo >= kT ? kT : (Wo + 31) / 32 * 32, bpb = kT / cw;
-    const int col_chunks = (Wo + cw - 1) / cw, bands = (Ho + kDwRows - 1) / kDwRows;
+    const int R = stride == 1 ? DwRows<1>::value : DwRows<2>::value;
+    const int col_chunks = (Wo + cw - 1) / cw, bands = (Ho + R - 1) / R;
     const int gx = col_chunks * ((bands + bpb - 1) / bpb);
     cudaStream_t s = (cudaStream_t)stream;
     const size_t planes = (size_t)N * C, in_plane = (size_t)H * W, out_plane = (size_t)Ho * Wo;
     for (size_t p0 = 0; p0 < planes; p0 += 65535) {  // grid.y = planes of this launch
         const unsigned np = (unsigned)(planes - p0 < 65535 ? planes - p0 : 65535);
-        // this launch's first plane has channel p0 % C
+        const float *xs = x + p0 * in_plane;
+        float *ys = y + p0 * out_plane;
+        const int c0 = (int)(p0 % C);  // channel of this launch's first plane
         DN_TRY(launch("fl_dw3x3_fwd", s, [&] {
-            k_dw_fwd<<<dim3(gx, np), kT, 0, s>>>(x + p0 * in_plane, w, b, y + p0 * out_plane, C, H, W, stride, Ho, Wo,
-                                                 cw, bpb, col_chunks, (int)(p0 % C), relu);
+            if (stride == 1)
+                k_dw_fwd<1><<<dim3(gx, np), kT, 0, s>>>(xs, w, b, ys, C, H, W, Ho, Wo, cw, bpb, col_chunks, c0, relu);
+            else
+                k_dw_fwd<2><<<dim3(gx, np), kT, 0, s>>>(xs, w, b, ys, C, H, W, Ho, Wo, cw, bpb, col_chunks, c0, relu);
         }));
     }
     return DN_OK;

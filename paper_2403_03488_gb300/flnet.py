@@ -75,6 +75,28 @@ def macs_per_pixel(widths=WIDTHS):
     return t + c[0]
 
 
+def work_per_pixel(widths=WIDTHS):
+    """Algorithmic work of one forward pass per full-resolution pixel, by layer
+    kind: multiply-adds of the depthwise, pointwise (output layer included) and
+    transposed layers, and the FP32 bytes the depthwise layers must move (input
+    plane read once, output plane written once)."""
+    w = {"dw_macs": 0.0, "pw_macs": 0.0, "up_macs": 0.0, "dw_bytes": 0.0}
+    level = 0
+    for kind, cin, cout, s in layer_specs(widths):
+        if kind == "ds":
+            lo = level + (1 if s == 2 else 0)
+            w["dw_macs"] += 9 * cin / 4 ** lo
+            w["pw_macs"] += cin * cout / 4 ** lo
+            w["dw_bytes"] += 4 * cin / 4 ** level + 4 * cin / 4 ** lo
+            level = lo
+        elif kind == "up":
+            level -= 1
+            w["up_macs"] += cin * cout / 4 ** level
+        else:
+            w["pw_macs"] += cin * cout / 4 ** level
+    return w
+
+
 def init_params(widths=WIDTHS, seed=0):
     """He-normal weights (fan-in 9 for depthwise, cin for pointwise, cin for the
     transposed 2x2, whose outputs each see one tap), zero biases."""

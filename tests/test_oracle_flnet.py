@@ -160,3 +160,21 @@ def test_network_size_matches_table_III():
     assert abs(n - flnet.macs_per_pixel()) < 1e-6
     assert len(flnet.param_shapes()) == len(shapes(c))
     assert all(tuple(a) == tuple(b) for a, b in zip(flnet.param_shapes(), shapes(c)))
+
+
+def test_work_per_pixel_splits_the_network_count():
+    """The per-kind counts the roofline uses add up to the whole network's
+    multiply-adds, and the depthwise bytes match a count on explicit plane sizes
+    (a 1024 x 1024 image, planes read once and written once)."""
+    from paper_2403_03488_gb300 import flnet
+    w = flnet.work_per_pixel()
+    assert abs(w["dw_macs"] + w["pw_macs"] + w["up_macs"] - flnet.macs_per_pixel()) < 1e-9
+    side, b = 1024, 0
+    for kind, cin, cout, s in flnet.layer_specs():
+        if kind == "ds":
+            out = side // s
+            b += 4 * cin * (side * side + out * out)
+            side = out
+        elif kind == "up":
+            side *= 2
+    assert abs(b / 1024 ** 2 - w["dw_bytes"]) < 1e-9
