@@ -130,6 +130,16 @@ def algorithmic(kernel, launches_per_step, batch):
         flops = 2.0 * H * W * batch * (2 * 32 * 9 + 8 * 32 * 32 * 9 + 32 * 9) / launches_per_step
         return "alu", "TFLOP/s", flops, fp32_peak, FP32_PEAK_TFLOPS_NOTE + " (derived, not measured)"
     hbm = peaks.get("hbm_gbs", 6800.0)
+    px = H * W * batch  # every launch of these kernels covers the whole batch
+    hbm_bytes = {
+        "conv3x3_tc_bf16": 2 * px * 32 * 2,   # NHWC BF16 activations in and out
+        "conv_first_bf16": px * (8 + 64),     # prefilter + noisy FP32 in, 32 BF16 channels out
+        "conv_last_bf16": px * (64 + 4 + 4),  # 32 BF16 channels + prefilter in, FP32 out
+        "bm3d_normalize": px * (4 * 8 + 4),   # four 64-bit fixed-point planes in, FP32 out
+        "error_reduce_fp64": px * 8,          # output and clean image
+    }
+    if kernel in hbm_bytes:
+        return "hbm", "GB/s", float(hbm_bytes[kernel]), hbm, "measured hbm_gbs"
     if kernel.startswith(("fl_pw_fwd", "fl_deconv2x2_fwd", "fl_dw3x3_fwd")):
         from paper_2403_03488_gb300.flnet import work_per_pixel
         wpp, px = work_per_pixel(), H * W * batch / launches_per_step
@@ -141,36 +151,23 @@ def algorithmic(kernel, launches_per_step, batch):
     return "hbm", "GB/s", 8.0 * H * W * batch / launches_per_step, hbm, "measured hbm_gbs"
 
 
-def kernel_rooflines(res, steps, batch, launches_per_step=None):
+def kernel_rooflines(res, steps, batch):
     """Roofline fraction of every library kernel whose algorithmic work has a
-    plain count: the matcher in FLOP (see `algorithmic`), the CNN layers, the
-    normalisation and the error reduction in bytes that must cross HBM per
-    launch (activations / planes read and written once, halos excluded)."""
-    peaks = {}
-    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(p):
-        peaks = json.load(open(p))
-    hbm = peaks.get("hbm_gbs", 6800.0)
-    px = batch * H * W
-    bytes_per_launch = {
-        "conv3x3_tc_bf16": 2 * px * 32 * 2,   # NHWC BF16 activations in and out
-        "conv_first_bf16": px * (8 + 64),     # prefilter + noisy FP32 in, 32 BF16 channels out
-        "conv_last_bf16": px * (64 + 4 + 4),  # 32 BF16 channels + prefilter in, FP32 out
-        "bm3d_normalize": px * (4 * 8 + 4),   # four 64-bit fixed-point planes in, FP32 out
-        "error_reduce_fp64": px * 8,          # output and clean image
-    }
+    plain count (see `algorithmic`): the matcher, NLM and the flexible network's
+    layers in FLOP, the CNN layers, the normalisation, the depthwise layers and
+    the error reduction in bytes that must cross HBM per launch (activations /
+    planes read and written once, halos excluded)."""
     out = {}
     for k, (n, ms) in res.items():
+        if not (k.startswith(("bm3d_match_fp32", "nlm_fp32", "fl_pw_fwd", "fl_deconv2x2_fwd", "fl_dw3x3_fwd",
+                              "conv3x3_tc_bf16", "conv_first_bf16", "conv_last_bf16", "bm3d_normalize",
+                              "error_reduce_fp64"))):
+            continue
         avg = ms / n
-        if k in bytes_per_launch:
-            ach = bytes_per_launch[k] / (avg / 1e3) / 1e9
-            out[k] = {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
-                      "frac": round(ach / hbm, 4), "avg_launch_ms": round(avg, 4)}
-        elif k.startswith(("bm3d_match_fp32", "nlm_fp32", "fl_")) and not k.startswith("fl_pack"):
-            bound, unit, work, peak, _ = algorithmic(k, n / steps, batch)
-            ach = work / (avg / 1e3) / (1e12 if unit == "TFLOP/s" else 1e9)
-            out[k] = {"bound": bound, "achieved": round(ach, 3), "peak": round(peak, 1), "unit": unit,
-                      "frac": round(ach / peak, 4), "avg_launch_ms": round(avg, 4)}
+        bound, unit, work, peak, _ = algorithmic(k, n / steps, batch)
+        ach = work / (avg / 1e3) / (1e12 if unit == "TFLOP/s" else 1e9)
+        out[k] = {"bound": bound, "achieved": round(ach, 3 if unit == "TFLOP/s" else 1), "peak": round(peak, 1),
+                  "unit": unit, "frac": round(ach / peak, 4), "avg_launch_ms": round(avg, 4)}
     return out
 
 
