@@ -55,7 +55,8 @@ def lib():
         L.or_t3d.argtypes = [dp, i, i, dp]
         L.or_grid.argtypes = [i, i, i, ip]
         L.or_match.argtypes = [dp, i, i, i, i, i, i, d, ip, dp, ip, ip, up]
-        L.or_bm3d_pass1.argtypes = [dp, i, i, i, dp, i, i, i, i, d, d, d, d, dp, up, up]
+        L.or_match_pre.argtypes = [dp, i, i, i, i, i, i, d, d, d, d, d, ip, dp, ip, ip, up]
+        L.or_bm3d_pass1.argtypes = [dp, i, i, i, dp, i, i, i, i, d, d, d, d, d, d, dp, up, up]
         L.or_bm3d_pass2.argtypes = [dp, dp, i, i, i, dp, i, i, i, i, d, d, dp, up, up]
         L.or_nlm.argtypes = [dp, i, i, i, d, i, i, d, dp]
         L.or_conv3x3.argtypes = [dp, i, i, i, i, dp, dp, i, dp]
@@ -134,7 +135,9 @@ def grid(L: int, k: int = 8, step: int = 3) -> np.ndarray:
 # BM3D
 # --------------------------------------------------------------------------
 
-FLAG_TAU, FLAG_TIE, FLAG_THR = 1, 2, 4
+FLAG_TAU, FLAG_TIE, FLAG_THR, FLAG_PRE = 1, 2, 4, 8
+LAMBDA2D_HIGH = 2.0  # 2D prethreshold of the first-pass distance above sigma 40 (regime 0)
+PRE_BAND = 0.005     # hazard band of the prethreshold decision (absolute, 0..255 scale)
 
 
 @dataclass
@@ -147,13 +150,16 @@ class Pass:
     tau: float = 2500.0
     lambda3d: float = 2.7
     beta: float = 2.0
+    lambda2d: float = 0.0  # > 0: first-pass distances on 2D-prethresholded patches (threshold lambda2d * sigma)
 
 
 def default_passes(sigma: float, regime: int = 0):
     """(hard, wiener) parameters.  regime 0: tau1 = 2500, tau2 = 400 for
-    sigma <= 40 and tau1 = 5000, tau2 = 3500 above; regime 1: 2500 / 400 always."""
+    sigma <= 40; above, tau1 = 5000, tau2 = 3500 and the first pass matches on
+    2D-prethresholded patches (lambda2d = 2); regime 1: 2500 / 400 and raw
+    patches always."""
     hi = regime == 0 and sigma > 40.0
-    return (Pass(n2=16, tau=5000.0 if hi else 2500.0),
+    return (Pass(n2=16, tau=5000.0 if hi else 2500.0, lambda2d=LAMBDA2D_HIGH if hi else 0.0),
             Pass(n2=32, tau=3500.0 if hi else 400.0))
 
 
@@ -178,6 +184,29 @@ def match(guide: np.ndarray, p: Pass):
                 nkept=nk.reshape(Ry, Rx), n=ng.reshape(Ry, Rx), flag=fl.reshape(Ry, Rx))
 
 
+def match_pre(guide: np.ndarray, p: Pass, thr: float, band: float = PRE_BAND, rtie: float = 1e-5,
+              atie: float = 1e-3):
+    """Block matching on 2D-prethresholded patches (threshold thr) of one
+    [H, W] guide; same outputs as `match`, flags including FLAG_PRE.  Ties:
+    |a - b| <= rtie max(a, b) + atie (sqrt(a) + sqrt(b)) (atie = 1e-3 covers
+    coefficient differences off by up to 5e-4, the FP32 transforms' error)."""
+    g = _f64(guide)
+    H, W = g.shape
+    Ry, Rx = len(grid(H, p.patch, p.step)), len(grid(W, p.patch, p.step))
+    R = Ry * Rx
+    idx = np.empty((R, p.n2), np.int32)
+    dist = np.empty((R, p.n2 + 1))
+    nk = np.empty(R, np.int32)
+    ng = np.empty(R, np.int32)
+    fl = np.empty(R, np.uint8)
+    rc = lib().or_match_pre(_dp(g), H, W, p.patch, p.step, p.search, p.n2, p.tau, float(thr), float(band),
+                            float(rtie), float(atie), _ip(idx), _dp(dist), _ip(nk), _ip(ng), _up(fl))
+    if rc:
+        raise ValueError("or_match_pre: bad arguments (%d)" % rc)
+    return dict(idx=idx.reshape(Ry, Rx, p.n2), dist=dist.reshape(Ry, Rx, p.n2 + 1),
+                nkept=nk.reshape(Ry, Rx), n=ng.reshape(Ry, Rx), flag=fl.reshape(Ry, Rx))
+
+
 def bm3d_pass1(img: np.ndarray, sig, p: Pass, band: float = 0.0):
     """First pass on [C, H, W] (channel 0 guides matching).  Returns
     (basic [C, H, W], pixel flags [H, W], group flags [Ry, Rx])."""
@@ -189,7 +218,8 @@ def bm3d_pass1(img: np.ndarray, sig, p: Pass, band: float = 0.0):
     Ry, Rx = len(grid(H, p.patch, p.step)), len(grid(W, p.patch, p.step))
     gf = np.empty((Ry, Rx), np.uint8)
     rc = lib().or_bm3d_pass1(_dp(x), C, H, W, _dp(s), p.patch, p.step, p.search, p.n2, p.tau,
-                             p.lambda3d, p.beta, band, _dp(out), _up(pf), _up(gf))
+                             p.lambda3d, p.beta, band, p.lambda2d * float(s[0]), PRE_BAND, _dp(out), _up(pf),
+                             _up(gf))
     if rc:
         raise ValueError("or_bm3d_pass1 failed (%d)" % rc)
     return out, pf, gf

@@ -185,6 +185,7 @@ static int pow2_floor(int v)
 #define OR_FLAG_TAU 1    /* a candidate's distance lies within 1e-5 tau of tau */
 #define OR_FLAG_TIE 2    /* two ranked neighbours within 1e-5 relative       */
 #define OR_FLAG_THR 4    /* a 3D coefficient lies within the band of lambda sigma */
+#define OR_FLAG_PRE 8    /* a prethresholded 2D coefficient near lambda2d sigma could change the list */
 
 /* Exhaustive block matching for every reference patch of one guide image.
  *
@@ -255,6 +256,123 @@ int or_match(const double *g, int H, int W, int k, int step, int search, int n2,
     return 0;
 }
 
+/* Block matching on 2D-prethresholded patches: the first-pass distance BM3D
+ * uses at high noise.  Every patch P is replaced by Y(P), its 2D transform
+ * T2D(P) (orthonormal DCT-II, or_dct2d_matrix) with every coefficient of
+ * magnitude <= thr set to zero, and
+ *     d(P, Q) = ||Y(P) - Y(Q)||^2 / k^2.
+ * With thr = 0 this is or_match's distance (T2D is orthonormal).  Window,
+ * ordering, group size and outputs as or_match.  Two distances a, b count as
+ * tied when |a - b| <= rtie max(a, b) + atie (sqrt(a) + sqrt(b)): an error
+ * of at most delta on each coefficient difference moves a distance d by at
+ * most 2 delta sqrt(d) (Cauchy-Schwarz over the 64 terms), so atie = 2 delta
+ * covers coefficients computed in lower precision.  Flags:
+ *   OR_FLAG_TAU  a candidate tied with tau;
+ *   OR_FLAG_TIE  two ranked neighbours (up to the group cut) tied;
+ *   OR_FLAG_PRE  the reference patch has a coefficient whose magnitude lies
+ *                within `band` of thr, or a candidate with such a coefficient
+ *                could, with that coefficient's keep/zero decision reversed,
+ *                reach the group: its smallest possible distance is <= the
+ *                distance of the last listed candidate (of tau while at most
+ *                n2 candidates are kept, when one more or one fewer changes
+ *                the group size). */
+int or_match_pre(const double *g, int H, int W, int k, int step, int search, int n2, double tau, double thr,
+                 double band, double rtie, double atie, int *idx, double *dist, int *nkept, int *ngroup,
+                 unsigned char *flag)
+{
+    if (k != OR_K || H < k || W < k || search < 1 || (search & 1) == 0 || n2 < 1 || n2 > OR_NMAX || thr < 0.0)
+        return -1;
+    int gy[4096], gx[4096];
+    int Ry = or_grid(H, k, step, gy), Rx = or_grid(W, k, step, gx);
+    if (Ry > 4096 || Rx > 4096) return -1;
+    const int Hp = H - k + 1, Wp = W - k + 1;
+    const size_t np = (size_t)Hp * Wp;
+    double *Y = (double *)malloc(sizeof(double) * np * OR_K2);     /* prethresholded coefficients */
+    double *A = (double *)malloc(sizeof(double) * np * OR_K2);     /* value under the other decision */
+    unsigned char *hz = (unsigned char *)malloc(np);               /* patch has a coefficient in the band */
+    if (!Y || !A || !hz) return -2;
+    double T[OR_K2 * OR_K2];
+    or_dct2d_matrix(T);
+#pragma omp parallel for schedule(static)
+    for (long q = 0; q < (long)np; ++q) {
+        int y = (int)(q / Wp), x = (int)(q % Wp);
+        double P[OR_K2];
+        for (int i = 0; i < OR_K; ++i)
+            for (int j = 0; j < OR_K; ++j) P[i * OR_K + j] = g[(size_t)(y + i) * W + x + j];
+        unsigned char h = 0;
+        for (int a = 0; a < OR_K2; ++a) {
+            double c = 0.0;
+            for (int m = 0; m < OR_K2; ++m) c += T[a * OR_K2 + m] * P[m];
+            int keep = fabs(c) > thr;
+            int near = fabs(fabs(c) - thr) <= band;
+            Y[(size_t)q * OR_K2 + a] = keep ? c : 0.0;
+            A[(size_t)q * OR_K2 + a] = near ? (keep ? 0.0 : c) : (keep ? c : 0.0);
+            h |= (unsigned char)near;
+        }
+        hz[q] = h;
+    }
+    int hs = search / 2;
+    int ncand_max = search * search;
+    int fail = 0;
+#pragma omp parallel
+    {
+        cand_t *cl = (cand_t *)malloc(sizeof(cand_t) * (size_t)ncand_max);
+        double *hlo = (double *)malloc(sizeof(double) * (size_t)ncand_max);  /* smallest d of hazardous candidates */
+        if (!cl || !hlo) fail = 1;
+#pragma omp for schedule(static)
+        for (int r = 0; r < Ry * Rx; ++r) {
+            if (fail) continue;
+            int y0 = gy[r / Rx], x0 = gx[r % Rx];
+            const double *yr = Y + ((size_t)y0 * Wp + x0) * OR_K2;
+            int nc = 0, nh = 0;
+            unsigned char fl = hz[(size_t)y0 * Wp + x0] ? OR_FLAG_PRE : 0;
+            int ylo = y0 - hs < 0 ? 0 : y0 - hs, yhi = y0 + hs > H - k ? H - k : y0 + hs;
+            int xlo = x0 - hs < 0 ? 0 : x0 - hs, xhi = x0 + hs > W - k ? W - k : x0 + hs;
+            for (int y = ylo; y <= yhi; ++y)
+                for (int x = xlo; x <= xhi; ++x) {
+                    if (y == y0 && x == x0) continue;
+                    size_t q = (size_t)y * Wp + x;
+                    const double *yq = Y + q * OR_K2, *aq = A + q * OR_K2;
+                    double s = 0.0, slo = 0.0;
+                    for (int a = 0; a < OR_K2; ++a) {
+                        double e = yr[a] - yq[a], f = yr[a] - aq[a];
+                        s += e * e;
+                        slo += (e * e < f * f) ? e * e : f * f;
+                    }
+                    double d = s / (double)(k * k);
+                    if (fabs(d - tau) <= rtie * tau + 2.0 * atie * sqrt(tau)) fl |= OR_FLAG_TAU;
+                    if (d <= tau) { cl[nc].d = d; cl[nc].idx = y * W + x; ++nc; }
+                    if (hz[q]) hlo[nh++] = slo / (double)(k * k);
+                }
+            qsort(cl, (size_t)nc, sizeof(cand_t), cand_cmp);
+            int kept = nc + 1;
+            int n = pow2_floor(kept < n2 ? kept : n2);
+            int *I = idx + (size_t)r * n2;
+            double *D = dist + (size_t)r * (n2 + 1);
+            I[0] = y0 * W + x0;
+            D[0] = 0.0;
+            for (int t = 1; t < n2; ++t) I[t] = (t < kept) ? cl[t - 1].idx : -1;
+            for (int t = 1; t <= n2; ++t) D[t] = (t < kept) ? cl[t - 1].d : -1.0;
+            int last = n < kept - 1 ? n : kept - 1;
+            for (int t = 1; t < last; ++t) {
+                double a = cl[t - 1].d, b = cl[t].d;
+                if (!(a == 0.0 && b == 0.0) && fabs(b - a) <= rtie * (a > b ? a : b) + atie * (sqrt(a) + sqrt(b)))
+                    fl |= OR_FLAG_TIE;
+            }
+            double edge = kept > n2 ? cl[n2 - 2].d : tau;
+            for (int t = 0; t < nh; ++t)
+                if (hlo[t] <= edge * (1.0 + rtie) + 2.0 * atie * sqrt(edge)) fl |= OR_FLAG_PRE;
+            nkept[r] = kept;
+            ngroup[r] = n;
+            flag[r] = fl;
+        }
+        free(cl);
+        free(hlo);
+    }
+    free(Y); free(A); free(hz);
+    return fail ? -2 : 0;
+}
+
 /* ------------------------------------------------------------------ */
 /* Collaborative filtering and aggregation                            */
 /* ------------------------------------------------------------------ */
@@ -315,7 +433,8 @@ static void mark_group(unsigned char *pxflag, int W, const int *I, int n, unsign
  * gflag[R] (may be NULL) receives each group's flags. */
 int or_bm3d_pass1(const double *img, int C, int H, int W, const double *sig,
                   int k, int step, int search, int n2, double tau, double lambda3d, double beta,
-                  double band, double *basic, unsigned char *pxflag, unsigned char *gflag)
+                  double band, double thr2d, double band2d, double *basic, unsigned char *pxflag,
+                  unsigned char *gflag)
 {
     if (C < 1 || k != OR_K) return -1;
     int Ry = or_grid(H, k, step, NULL), Rx = or_grid(W, k, step, NULL);
@@ -326,7 +445,12 @@ int or_bm3d_pass1(const double *img, int C, int H, int W, const double *sig,
     int *nk = (int *)malloc(sizeof(int) * (size_t)R), *ng = (int *)malloc(sizeof(int) * (size_t)R);
     unsigned char *fl = (unsigned char *)malloc((size_t)R);
     if (!idx || !dist || !nk || !ng || !fl) return -2;
-    if (or_match(img, H, W, k, step, search, n2, tau, idx, dist, nk, ng, fl)) return -1;
+    /* thr2d > 0: distances on 2D-prethresholded patches (tie tolerances of
+     * the FP32 transforms, see or_match_pre) */
+    if (thr2d > 0.0 ? or_match_pre(img, H, W, k, step, search, n2, tau, thr2d, band2d, 1e-5, 1e-3, idx, dist, nk,
+                                   ng, fl)
+                    : or_match(img, H, W, k, step, search, n2, tau, idx, dist, nk, ng, fl))
+        return -1;
 
     double T[OR_K2 * OR_K2], kw[OR_K];
     or_dct2d_matrix(T);
