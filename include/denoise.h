@@ -72,6 +72,10 @@ typedef struct {
     float tau_high;  /* tau used when sigma > 40 and sigma_regime == 0         */
     float lambda3d;  /* hard threshold lambda3d * sigma (first pass only)      */
     float beta;      /* Kaiser window beta for aggregation                     */
+    float lambda2d;  /* first pass, sigma > 40 and sigma_regime == 0: match on
+                        2D-prethresholded patches, coefficients of magnitude
+                        <= lambda2d * sigma zeroed (BM3D's high-noise distance;
+                        0 disables; ignored by the second pass)              */
 } dn_bm3d_pass;
 
 typedef struct {
@@ -106,8 +110,8 @@ typedef struct {
 
 /* ---- parameters ---------------------------------------------------------- */
 
-/* Defaults: hard {8, 3, 39, 16, 2500, 5000, 2.7, 2}, wiener {8, 3, 39, 32,
- * 400, 3500, 0, 2}, precision DN_FP32, sigma_regime 0. */
+/* Defaults: hard {8, 3, 39, 16, 2500, 5000, 2.7, 2, 2}, wiener {8, 3, 39, 32,
+ * 400, 3500, 0, 2, 0}, precision DN_FP32, sigma_regime 0. */
 void dn_bm3d_default_params(dn_bm3d_params *p);
 /* Defaults: {7, 21, 0.4}. */
 void dn_nlm_default_params(dn_nlm_params *p);
@@ -187,6 +191,19 @@ dn_status dn_bm3d_match(const float *guide, size_t plane_stride, int B, int H, i
                         const float *tau, int precision, int *idx, int *n, void *workspace, size_t ws_bytes,
                         dn_stream_t stream);
 size_t dn_bm3d_match_workspace_bytes(int B, int H, int W, const dn_bm3d_pass *p, int precision);
+
+/* Block matching on 2D-prethresholded patches (the first-pass distance BM3D
+ * uses at high noise; the denoisers select it per image, see
+ * dn_bm3d_pass.lambda2d): every patch P becomes Y(P), its orthonormal 8 x 8
+ * DCT-II with the coefficients of magnitude <= thr[b] set to zero, and
+ * d(P, Q) = ||Y(P) - Y(Q)||^2 / 64; window, tau test, ordering and group size
+ * as dn_bm3d_match.  guide as dn_bm3d_match; tau, thr: host [B] (tau > 0,
+ * thr >= 0); idx/n as dn_bm3d_match with p->n2.  FP32 transforms and
+ * distances; no workspace.  DN_EUNSUPPORTED when the staged window exceeds
+ * shared memory (search > 127 is already DN_EINVAL). */
+dn_status dn_bm3d_match_prethresh(const float *guide, size_t plane_stride, int B, int H, int W,
+                                  const dn_bm3d_pass *p, const float *tau, const float *thr, int *idx, int *n,
+                                  dn_stream_t stream);
 
 /* Test surface of the BF16 tensor-core matching prefilter: runs dn_bm3d_match
  * (DN_BF16) on one image and additionally writes the raw FP32 cross terms

@@ -29,7 +29,7 @@ class DenoiseError(RuntimeError):
 class BM3DPass(ctypes.Structure):
     _fields_ = [("patch", ctypes.c_int), ("step", ctypes.c_int), ("search", ctypes.c_int), ("n2", ctypes.c_int),
                 ("tau", ctypes.c_float), ("tau_high", ctypes.c_float), ("lambda3d", ctypes.c_float),
-                ("beta", ctypes.c_float)]
+                ("beta", ctypes.c_float), ("lambda2d", ctypes.c_float)]
 
 
 class BM3DParams(ctypes.Structure):
@@ -78,6 +78,7 @@ def lib():
         "denoise_bm3d_noalloc": (i, [vp, vp, i, i, i, i, fp, P(BM3DParams), vp]),
         "dn_bm3d_match": (i, [vp, sz, i, i, i, P(BM3DPass), fp, i, vp, vp, vp, sz, vp]),
         "dn_bm3d_match_workspace_bytes": (sz, [i, i, i, P(BM3DPass), i]),
+        "dn_bm3d_match_prethresh": (i, [vp, sz, i, i, i, P(BM3DPass), fp, fp, vp, vp, vp]),
         "dn_bm3d_match_cross_terms": (i, [vp, i, i, P(BM3DPass), f, i, i, vp, vp, vp, vp, sz, vp]),
         "dn_bm3d_filter_hard": (i, [vp, vp, vp, i, i, i, i, fp, P(BM3DPass), i, vp, vp, sz, vp]),
         "dn_bm3d_filter_wiener": (i, [vp, vp, vp, vp, i, i, i, i, fp, P(BM3DPass), i, vp, vp, sz, vp]),

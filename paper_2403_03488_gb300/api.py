@@ -173,6 +173,26 @@ def bm3d_match(guide: torch.Tensor, tau, p: BM3DPass, precision: int = DN_FP32, 
     return idx, n
 
 
+def bm3d_match_prethresh(guide: torch.Tensor, tau, thr, p: BM3DPass, stream=None):
+    """Block matching on 2D-prethresholded patches (coefficients of magnitude
+    <= thr[b] zeroed): guide [B, H, W] (or [B, C, H, W], channel 0).
+    Returns (idx int32 [B, Ry, Rx, n2], n int32 [B, Ry, Rx])."""
+    if guide.dim() == 4:
+        B, C, H, W = guide.shape
+        plane = C * H * W
+    else:
+        B, H, W = guide.shape
+        plane = H * W
+    _need(guide, "guide")
+    Ry, Rx = len(grid(H, 8, p.step)), len(grid(W, 8, p.step))
+    idx = torch.empty((B, Ry, Rx, p.n2), dtype=torch.int32, device=guide.device)
+    n = torch.empty((B, Ry, Rx), dtype=torch.int32, device=guide.device)
+    check(L.lib().dn_bm3d_match_prethresh(_vp(guide), plane, B, H, W, ctypes.byref(p), _sigmas(tau, B),
+                                          _sigmas(thr, B), _vp(idx), _vp(n), _stream(stream)),
+          "dn_bm3d_match_prethresh")
+    return idx, n
+
+
 def bm3d_match_cross_terms(guide: torch.Tensor, p: BM3DPass, tau: float, tile_x: int, tile_y: int, stream=None):
     """Raw tensor-core cross terms of one 8 x 16 reference tile (test surface):
     returns (cross [128, nchunks, 256], (cy0, cx0) candidate-region origin)."""

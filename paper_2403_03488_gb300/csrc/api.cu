@@ -40,6 +40,7 @@ bool valid_pass(const dn_bm3d_pass *p)
     if (p->patch != 8 || p->step < 1 || p->search < 1 || (p->search & 1) == 0 || p->search > 127) return false;
     if (p->n2 < 1 || p->n2 > 32 || (p->n2 & (p->n2 - 1)) != 0) return false;
     if (!(p->tau > 0.0f) || !(p->tau_high > 0.0f) || !(p->lambda3d >= 0.0f) || !(p->beta >= 0.0f)) return false;
+    if (!(p->lambda2d >= 0.0f) || !std::isfinite(p->lambda2d)) return false;
     return true;
 }
 
@@ -168,6 +169,37 @@ dn_status match_any(const float *guide, size_t plane, int B, int H, int W, const
     return match_fp32(guide, plane, B, H, W, p, tau, idx, n, s);
 }
 
+// First-pass matching of nb images: those in the high-noise regime (sigma >
+// 40 with sigma_regime 0 and lambda2d > 0) on 2D-prethresholded patches with
+// threshold lambda2d * (guide-channel sigma), runs of the others through
+// match_any.  sig: per-image, per-channel noise std [nb][C].
+dn_status match_pass1(const float *x, size_t plane, int nb, int C, int H, int W, const dn_bm3d_params *p,
+                      const float *sigma, const float *sig, const float *tau, int *idx, int *n, int *mws,
+                      cudaStream_t s)
+{
+    const size_t R = (size_t)grid_count(H, 8, p->hard.step) * grid_count(W, 8, p->hard.step);
+    auto pre = [&](int i) { return p->sigma_regime == 0 && sigma[i] > 40.0f && p->hard.lambda2d > 0.0f; };
+    for (int i0 = 0; i0 < nb;) {
+        int i1 = i0 + 1;
+        while (i1 < nb && pre(i1) == pre(i0)) ++i1;
+        const float *g = x + (size_t)i0 * plane;
+        int *ix = idx + (size_t)i0 * R * p->hard.n2, *nn = n + (size_t)i0 * R;
+        if (pre(i0)) {
+            float thr[kChunk];
+            for (int i = i0; i < i1; i += kChunk) {
+                const int m = i1 - i < kChunk ? i1 - i : kChunk;
+                for (int j = 0; j < m; ++j) thr[j] = p->hard.lambda2d * sig[(size_t)(i + j) * C];
+                DN_TRY(match_prethresh(x + (size_t)i * plane, plane, m, H, W, p->hard, tau + i, thr,
+                                       idx + (size_t)i * R * p->hard.n2, n + (size_t)i * R, s));
+            }
+        } else {
+            DN_TRY(match_any(g, plane, i1 - i0, H, W, p->hard, tau + i0, p->precision, ix, nn, mws, s));
+        }
+        i0 = i1;
+    }
+    return DN_OK;
+}
+
 // Collaborative filtering (pass 1, or pass 2 when `wiener`) with the 2D
 // transforms on the tensor cores when `tc`, FP32 SIMT otherwise.
 dn_status filter_any(bool wiener, bool tc, const float *img, const float *basic, const int *idx, const int *n, int B,
@@ -202,7 +234,7 @@ dn_status run_bm3d(const float *noisy, float *out, int B, int C, int H, int W, c
         const size_t off = (size_t)b0 * C * HW;
         const size_t Nb = (size_t)nb * C * HW;
         // pass 1: match on channel 0 of the noisy image, hard thresholding
-        DN_TRY(match_any(x + off, (size_t)C * HW, nb, H, W, p->hard, tau1, p->precision, w.idx, w.n, w.mws, s));
+        DN_TRY(match_pass1(x + off, (size_t)C * HW, nb, C, H, W, p, sigma + b0, sig, tau1, w.idx, w.n, w.mws, s));
         if (cudaMemsetAsync(w.acc, 0, kAccBytesPerPixel * Nb, s) != cudaSuccess) return DN_ECUDA;
         const bool tc = (p->precision & DN_BF16) != 0;
         DN_TRY(filter_any(false, tc, x + off, nullptr, w.idx, w.n, nb, C, H, W, sig, p->hard, w.acc, s));
@@ -290,8 +322,8 @@ extern "C" {
 void dn_bm3d_default_params(dn_bm3d_params *p)
 {
     if (!p) return;
-    p->hard = dn_bm3d_pass{8, 3, 39, 16, 2500.0f, 5000.0f, 2.7f, 2.0f};
-    p->wiener = dn_bm3d_pass{8, 3, 39, 32, 400.0f, 3500.0f, 0.0f, 2.0f};
+    p->hard = dn_bm3d_pass{8, 3, 39, 16, 2500.0f, 5000.0f, 2.7f, 2.0f, 2.0f};
+    p->wiener = dn_bm3d_pass{8, 3, 39, 32, 400.0f, 3500.0f, 0.0f, 2.0f, 0.0f};
     p->precision = DN_FP32;
     p->sigma_regime = 0;
 }
@@ -450,6 +482,20 @@ dn_status dn_bm3d_match(const float *guide, size_t plane_stride, int B, int H, i
     if (need > 0 && (!workspace || ws_bytes < need)) return DN_ENOMEM;
     return match_any(guide, plane_stride, B, H, W, *p, tau, precision == DN_FP32 ? DN_FP32 : DN_BF16_MATCH, idx, n,
                      static_cast<int *>(workspace), (cudaStream_t)stream);
+    DN_GUARD_END
+}
+
+dn_status dn_bm3d_match_prethresh(const float *guide, size_t plane_stride, int B, int H, int W,
+                                  const dn_bm3d_pass *p, const float *tau, const float *thr, int *idx, int *n,
+                                  dn_stream_t stream)
+{
+    DN_GUARD_BEGIN
+    if (!guide || !idx || !n || !tau || !thr || !valid_image(B, 1, H, W, 8) || !valid_pass(p) ||
+        plane_stride < (size_t)H * W)
+        return DN_EINVAL;
+    for (int b = 0; b < B; ++b)
+        if (!(tau[b] > 0.0f) || !(thr[b] >= 0.0f) || !std::isfinite(thr[b])) return DN_EINVAL;
+    return match_prethresh(guide, plane_stride, B, H, W, *p, tau, thr, idx, n, (cudaStream_t)stream);
     DN_GUARD_END
 }
 

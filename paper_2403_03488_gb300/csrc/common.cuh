@@ -80,6 +80,11 @@ constexpr size_t kAccBytesPerPixel = 4 * sizeof(long long);
 // ---- launchers implemented in the .cu files -------------------------------
 dn_status match_fp32(const float *guide, size_t plane, int B, int H, int W, const dn_bm3d_pass &p,
                      const float *tau, int *idx, int *n, cudaStream_t s);
+// Block matching on 2D-prethresholded patches (first pass at high noise):
+// thr[b] = lambda2d * sigma of image b's guide channel (host arrays of B).
+dn_status match_prethresh(const float *guide, size_t plane, int B, int H, int W, const dn_bm3d_pass &p,
+                          const float *tau, const float *thr, int *idx, int *n, cudaStream_t s);
+size_t match_pre_smem_bytes(int W, const dn_bm3d_pass &p);
 dn_status filter_hard_fp32(const float *img, const int *idx, const int *n, int B, int C, int H, int W,
                            const float *sig, const dn_bm3d_pass &p, float *acc, cudaStream_t s);
 dn_status filter_wiener_fp32(const float *noisy, const float *basic, const int *idx, const int *n, int B, int C,

@@ -34,6 +34,7 @@ def test_param_count_and_defaults(lib):
     assert (p.hard.patch, p.hard.step, p.hard.search, p.hard.n2) == (8, 3, 39, 16)
     assert (p.hard.tau, p.hard.tau_high, p.hard.lambda3d, p.hard.beta) == (2500.0, 5000.0, 2.700000047683716, 2.0)
     assert (p.wiener.n2, p.wiener.tau, p.wiener.tau_high) == (32, 400.0, 3500.0)
+    assert (p.hard.lambda2d, p.wiener.lambda2d) == (2.0, 0.0)
     q = L.default_nlm_params()
     assert (q.patch, q.search) == (7, 21) and abs(q.h_over_sigma - 0.4) < 1e-7
 
@@ -67,6 +68,19 @@ def test_bm3d_rejects_bad_arguments_on_host(lib):
     p = L.default_bm3d_params()
     p.hard.patch = 7
     assert _call_bm3d(lib, p=p) == L.DN_EINVAL
+    p = L.default_bm3d_params()
+    p.hard.lambda2d = -1.0
+    assert _call_bm3d(lib, p=p) == L.DN_EINVAL
+    p.hard.lambda2d = float("inf")
+    assert _call_bm3d(lib, p=p) == L.DN_EINVAL
+    # the prethresholded matcher checks its host arrays before any launch
+    q = L.default_bm3d_params().hard
+    dummy = ctypes.c_void_p(16)
+    for tau, thr in (([5000.0], [-1.0]), ([5000.0], [float("nan")]), ([0.0], [100.0])):
+        assert lib.dn_bm3d_match_prethresh(dummy, 32 * 32, 1, 32, 32, ctypes.byref(q), L.farr(tau), L.farr(thr),
+                                           dummy, dummy, None) == L.DN_EINVAL
+    assert lib.dn_bm3d_match_prethresh(dummy, 32 * 32, 1, 32, 32, ctypes.byref(q), L.farr([5000.0]), None,
+                                       dummy, dummy, None) == L.DN_EINVAL
     assert _call_bm3d(lib, ws=0) == L.DN_ENOMEM
     assert _call_bm3d(lib, ws_bytes=100) == L.DN_ENOMEM
     assert lib.denoise_bm3d(None, None, 1, 1, 32, 32, L.farr([25.0]), ctypes.byref(L.default_bm3d_params()),
