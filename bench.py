@@ -36,7 +36,7 @@ FP32_PEAK_TFLOPS_NOTE = "FP32 ALU peak = 152 SM x 128 lanes x 2 FLOP/FMA x 2.07 
 def workload_name(bm3d, cnn, prefilter="bm3d", net="resnet"):
     pre = "BM3D(%s)" % bm3d if prefilter == "bm3d" else "NLM(fp32)"
     body = "CNN(10x32, %s)" % cnn if net == "resnet" else "FL-UNet(48-192, fp32)"
-    return "hybrid %s+%s denoise, %d grey %dx%d synthetic images, sigma=25" % (pre, body, B, H, W)
+    return "hybrid %s+%s denoise, %d grey %dx%d synthetic images, sigma=%g" % (pre, body, B, H, W, SIGMA)
 
 
 # ---------------------------------------------------------------------------
@@ -119,7 +119,9 @@ def algorithmic(kernel, launches_per_step, batch):
         peaks = json.load(open(p))
     fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
     if kernel.startswith("bm3d_match"):
-        pairs = match_pairs(H, W) * batch / (launches_per_step / 2.0)
+        # one launch covers up to 64 images of one pass; 192 FLOP (sub, mul, add over 64 pixels or
+        # prethresholded coefficients) per (reference, candidate) pair
+        pairs = match_pairs(H, W) * min(batch, 64)
         return "alu", "TFLOP/s", 192.0 * pairs, fp32_peak, FP32_PEAK_TFLOPS_NOTE + " (derived, not measured)"
     if kernel.startswith("nlm_fp32"):
         # per pixel and search offset: difference + square (2), separable 7 + 7 box sums (12), weight (4:
@@ -159,9 +161,9 @@ def kernel_rooflines(res, steps, batch):
     planes read and written once, halos excluded)."""
     out = {}
     for k, (n, ms) in res.items():
-        if not (k.startswith(("bm3d_match_fp32", "nlm_fp32", "fl_pw_fwd", "fl_deconv2x2_fwd", "fl_dw3x3_fwd",
-                              "conv3x3_tc_bf16", "conv_first_bf16", "conv_last_bf16", "bm3d_normalize",
-                              "error_reduce_fp64"))):
+        if not k.startswith(("bm3d_match_fp32", "bm3d_match_pre", "nlm_fp32", "fl_pw_fwd", "fl_deconv2x2_fwd",
+                             "fl_dw3x3_fwd", "conv3x3_tc_bf16", "conv_first_bf16", "conv_last_bf16",
+                             "bm3d_normalize", "error_reduce_fp64")):
             continue
         avg = ms / n
         bound, unit, work, peak, _ = algorithmic(k, n / steps, batch)
@@ -363,7 +365,7 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "+".join(sorted({"f32" if bprec == api.DN_FP32 else "bf16",
                                   "f32" if prec == api.DN_FP32 or args.net == "fl" else "bf16"})),
-        "data": "synthetic (seeded piecewise-smooth + gratings + repeated tile, AWGN sigma=25)",
+        "data": "synthetic (seeded piecewise-smooth + gratings + repeated tile, AWGN sigma=%g)" % SIGMA,
         "config": {"workload": workload_name(args.bm3d, args.cnn, args.prefilter, args.net), "global_batch": B * world,
                    "image": [H, W],
                    "channels": 1, "sigma": SIGMA,
@@ -513,7 +515,7 @@ def run_reference(args):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f64",
-        "data": "synthetic (seeded piecewise-smooth + gratings + repeated tile, AWGN sigma=25)",
+        "data": "synthetic (seeded piecewise-smooth + gratings + repeated tile, AWGN sigma=%g)" % SIGMA,
         "config": {"workload": workload_name("fp64 oracle", "fp64 oracle"), "sample_per_step": "%dx%d crop of image 0" % (
             args.ref_side, args.ref_side)},
         "cpu_baseline": {"value": round(value, 5), "unit": "MPix/s", "cores": oracle.num_threads(), "kind": "oracle",
@@ -545,8 +547,12 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=300)
     ap.add_argument("--batch", type=int, default=None, help="images per step (profiling runs; default 16)")
     ap.add_argument("--size", type=int, default=None, help="image side (profiling runs; default 1024)")
+    ap.add_argument("--sigma", type=float, default=None,
+                    help="noise level (default 25; above 40 the first pass matches on prethresholded patches)")
     args = ap.parse_args()
-    global H, W, B
+    global H, W, B, SIGMA
+    if args.sigma:
+        SIGMA = args.sigma
     if args.size:
         H = W = args.size
     if args.batch:

@@ -207,6 +207,14 @@ def match_pre(guide: np.ndarray, p: Pass, thr: float, band: float = PRE_BAND, rt
                 nkept=nk.reshape(Ry, Rx), n=ng.reshape(Ry, Rx), flag=fl.reshape(Ry, Rx))
 
 
+def pass1_matches(guide: np.ndarray, p: Pass, sig_guide: float):
+    """The match lists `bm3d_pass1` groups with: on 2D-prethresholded patches
+    (threshold p.lambda2d * sig_guide) when p.lambda2d > 0, on pixels otherwise."""
+    if p.lambda2d > 0.0:
+        return match_pre(guide, p, p.lambda2d * float(sig_guide))
+    return match(guide, p)
+
+
 def bm3d_pass1(img: np.ndarray, sig, p: Pass, band: float = 0.0):
     """First pass on [C, H, W] (channel 0 guides matching).  Returns
     (basic [C, H, W], pixel flags [H, W], group flags [Ry, Rx])."""

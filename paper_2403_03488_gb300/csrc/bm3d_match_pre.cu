@@ -15,8 +15,10 @@
 // down one candidate row transforms one new pixel row; the column transforms
 //     c[u][v] = sum_i C[u][i] t[y + i][x][v]
 // then give the thresholded coefficient vectors of the row's candidates,
-// staged with a 66-float stride (the 64-bit loads of a warp, whose lanes hold
-// references `step` apart, fall in distinct banks for step 3).  Each thread
+// staged with a 68-float stride (the 16-byte loads of a quarter warp, whose
+// lanes hold references `step` apart, fall in distinct banks for step 3);
+// the next pixel row is loaded into registers while the current row is
+// matched.  Each thread
 // forms its own reference's vector with the same operations in the same
 // order, so equal patches give equal vectors, and accumulates (r - q)^2 with
 // packed FP32x2 operations in four interleaved partial sums.  No coefficient
@@ -34,7 +36,8 @@ namespace {
 constexpr int kPX = 32;            // references per CTA along x
 constexpr int kPY = 4;             // references per CTA along y
 constexpr int kPT = kPX * kPY;
-constexpr int kCS = 66;            // staged floats per candidate vector (64 + 2 pad)
+constexpr int kCS = 68;            // staged floats per candidate vector (64 + 4 pad, 16-byte rows)
+constexpr int kPF = 2;             // pixels of the next row prefetched per thread (kPT * kPF >= nc + 7)
 
 struct PreArgs {
     const float *g;
@@ -110,6 +113,19 @@ __global__ void __launch_bounds__(kPT) k_match_pre(PreArgs a)
     auto load_row = [&](int y) {
         for (int i = tid; i < npx; i += kPT) prow[i] = g[(size_t)y * W + X0 + i];
     };
+    float nxt[kPF];  // the next pixel row, in flight while a row is matched
+    auto fetch_row = [&](int y) {
+#pragma unroll
+        for (int j = 0; j < kPF; ++j) {
+            const int i = tid + j * kPT;
+            nxt[j] = (y < H && i < npx) ? g[(size_t)y * W + X0 + i] : 0.0f;
+        }
+    };
+    auto store_row = [&]() {
+#pragma unroll
+        for (int j = 0; j < kPF; ++j)
+            if (tid + j * kPT < npx) prow[tid + j * kPT] = nxt[j];
+    };
     auto row_transform = [&](int y) {
         float *dst = ring + (y & 7) * nc * 8;
         for (int o = tid; o < ncol * 8; o += kPT) dst[o] = dct8_at(a.C, o & 7, prow + (o >> 3));
@@ -132,35 +148,51 @@ __global__ void __launch_bounds__(kPT) k_match_pre(PreArgs a)
     const int xs = max(0, x0 - a.hs), xe = min(W - 8, x0 + a.hs);
     const int ys = max(0, y0 - a.hs), ye = min(H - 8, y0 + a.hs);
 
+    const bool prefetch = npx <= kPT * kPF;  // else (wide windows) rows are loaded directly
+    if (prefetch) fetch_row(Y0 + 7);
     for (int yy = Y0; yy <= Y1; ++yy) {
         __syncthreads();  // the previous row's readers of prow and S are done
-        load_row(yy + 7);
+        if (prefetch) store_row();  // pixel row yy + 7
+        else load_row(yy + 7);
         __syncthreads();
         row_transform(yy + 7);
         __syncthreads();
-        for (int o = tid; o < ncol * 64; o += kPT) {
-            const int x = o >> 6, k = o & 63, u = k >> 3, v = k & 7;
-            const float *tc = ring + x * 8 + v;
-            float c = __fmul_rn(a.C[u * 8], tc[(yy & 7) * nc * 8]);
+        // column transforms: one (x, v) job gives the 8 coefficients (u, v) of candidate x
+        for (int o = tid; o < ncol * 8; o += kPT) {
+            const int x = o >> 3, v = o & 7;
+            float t[8];
 #pragma unroll
-            for (int i = 1; i < 8; ++i) c = __fmaf_rn(a.C[u * 8 + i], tc[((yy + i) & 7) * nc * 8], c);
-            S[x * kCS + k] = keep_above(c, thr);
+            for (int i = 0; i < 8; ++i) t[i] = ring[((yy + i) & 7) * nc * 8 + x * 8 + v];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                float c = __fmul_rn(a.C[u * 8], t[0]);
+#pragma unroll
+                for (int i = 1; i < 8; ++i) c = __fmaf_rn(a.C[u * 8 + i], t[i], c);
+                S[x * kCS + u * 8 + v] = keep_above(c, thr);
+            }
         }
         __syncthreads();
+        if (prefetch && yy < Y1) fetch_row(yy + 8);
         if (!active || yy < ys || yy > ye) continue;
         for (int x = xs; x <= xe; ++x) {
             if (x == x0 && yy == y0) continue;
-            const f2 *q = reinterpret_cast<const f2 *>(S + (x - X0) * kCS);
-            f2 s0 = f2_pack(0.0f, 0.0f), s1 = s0, s2 = s0, s3 = s0;
+            const float4 *q4 = reinterpret_cast<const float4 *>(S + (x - X0) * kCS);
+            f2 acc[4];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const f2 e0 = f2_sub(rr[k], q[k]), e1 = f2_sub(rr[8 + k], q[8 + k]);
-                const f2 e2 = f2_sub(rr[16 + k], q[16 + k]), e3 = f2_sub(rr[24 + k], q[24 + k]);
-                s0 = f2_fma(e0, e0, s0);
-                s1 = f2_fma(e1, e1, s1);
-                s2 = f2_fma(e2, e2, s2);
-                s3 = f2_fma(e3, e3, s3);
-            }
+            for (int j = 0; j < 4; ++j) acc[j] = f2_pack(0.0f, 0.0f);
+            // partial sum j takes coefficient pairs 8 j .. 8 j + 7 in order (float4 4 j + k holds pairs
+            // 8 j + 2 k and 8 j + 2 k + 1)
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float4 v = q4[4 * j + k];
+                    f2 e = f2_sub(rr[8 * j + 2 * k], f2_pack(v.x, v.y));
+                    acc[j] = f2_fma(e, e, acc[j]);
+                    e = f2_sub(rr[8 * j + 2 * k + 1], f2_pack(v.z, v.w));
+                    acc[j] = f2_fma(e, e, acc[j]);
+                }
+            const f2 s0 = acc[0], s1 = acc[1], s2 = acc[2], s3 = acc[3];
             const float h01 = __fadd_rn(__fadd_rn(f2_lo(s0), f2_hi(s0)), __fadd_rn(f2_lo(s1), f2_hi(s1)));
             const float h23 = __fadd_rn(__fadd_rn(f2_lo(s2), f2_hi(s2)), __fadd_rn(f2_lo(s3), f2_hi(s3)));
             const float d = __fmul_rn(__fadd_rn(h01, h23), 0.015625f);  // / 64, exact

@@ -138,7 +138,7 @@ def test_filter_hard_parity_given_oracle_matches(oracle, C, H, W, sigmas):
         sc = oracle.channel_sigmas(sigmas[b], C)
         sig_flat += list(sc)
         P = oracle.default_passes(sigmas[b])[0]
-        om = oracle.match(img[b, 0], P)
+        om = oracle.pass1_matches(img[b, 0], P, sc[0])
         basic, pf, _ = oracle.bm3d_pass1(img[b], sc, P, band=BAND)
         idx.append(om["idx"])
         ns.append(om["n"])
@@ -186,7 +186,7 @@ def test_filter_parity_with_heavy_weights_and_large_values(oracle):
     img[:, 8:32, 30:54] = 0.0
     sc = [sigma]
     P1, P2 = oracle.default_passes(sigma)
-    om = oracle.match(img[0].astype(np.float64), P1)
+    om = oracle.pass1_matches(img[0].astype(np.float64), P1, sc[0])
     basic, pf, _ = oracle.bm3d_pass1(img.astype(np.float64), sc, P1, band=4 * BAND)
     hard = A.default_bm3d_params().hard
     hard.tau = P1.tau

@@ -58,7 +58,7 @@ def test_filter_bf16_stagewise(oracle, C, H, W, sigma):
     cref = _img(oracle, clean)[0]
     sc = oracle.channel_sigmas(sigma, C)
     P1, P2 = oracle.default_passes(sigma)
-    om = oracle.match(img[0], P1)
+    om = oracle.pass1_matches(img[0], P1, sc[0])
     basic, _, _ = oracle.bm3d_pass1(img, sc, P1)
     hard = A.default_bm3d_params().hard
     hard.tau = P1.tau
