@@ -176,20 +176,24 @@ __global__ void __launch_bounds__(kPT) k_match_pre(PreArgs a)
         if (!active || yy < ys || yy > ye) continue;
         for (int x = xs; x <= xe; ++x) {
             if (x == x0 && yy == y0) continue;
-            const float4 *q4 = reinterpret_cast<const float4 *>(S + (x - X0) * kCS);
+            // 16-byte loads straight into two packed pairs (no repacking of float4 lanes)
+            const ulonglong2 *q4 = reinterpret_cast<const ulonglong2 *>(S + (x - X0) * kCS);
             f2 acc[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) acc[j] = f2_pack(0.0f, 0.0f);
-            // partial sum j takes coefficient pairs 8 j .. 8 j + 7 in order (float4 4 j + k holds pairs
+            // partial sum j takes coefficient pairs 8 j .. 8 j + 7 in order (load 4 j + k holds pairs
             // 8 j + 2 k and 8 j + 2 k + 1)
 #pragma unroll
             for (int k = 0; k < 4; ++k)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    const float4 v = q4[4 * j + k];
-                    f2 e = f2_sub(rr[8 * j + 2 * k], f2_pack(v.x, v.y));
+                    const ulonglong2 v = q4[4 * j + k];
+                    f2 qa, qb;
+                    qa.v = v.x;
+                    qb.v = v.y;
+                    f2 e = f2_sub(rr[8 * j + 2 * k], qa);
                     acc[j] = f2_fma(e, e, acc[j]);
-                    e = f2_sub(rr[8 * j + 2 * k + 1], f2_pack(v.z, v.w));
+                    e = f2_sub(rr[8 * j + 2 * k + 1], qb);
                     acc[j] = f2_fma(e, e, acc[j]);
                 }
             const f2 s0 = acc[0], s1 = acc[1], s2 = acc[2], s3 = acc[3];
