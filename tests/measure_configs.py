@@ -43,7 +43,9 @@ def gpu_ms(fn, reps=5):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--quick", action="store_true", help="oracle on one image per configuration only")
+    ap.add_argument("--only", default="cfg1,cfg2,cfg3,cfg4", help="comma-separated configurations to run")
     args = ap.parse_args()
+    want = set(args.only.split(","))
     import oracle
     from paper_2403_03488_gb300 import api as A, synth
     oracle.build()
@@ -53,7 +55,19 @@ def main():
     P16 = A.default_bm3d_params(precision=A.DN_BF16)
     P16M = A.default_bm3d_params(precision=A.DN_BF16 | A.DN_BF16_MATCH)
 
-    # cfg1
+    if "cfg1" in want:
+        cfg1(A, oracle, synth, P32, res)
+    if "cfg2" in want:
+        cfg2(A, oracle, synth, P32, P16, res, args.quick)
+    if "cfg3" in want:
+        cfg3(A, oracle, synth, P32, P16, P16M, res)
+    if "cfg4" in want:
+        cfg4(A, oracle, synth, P32, P16, res)
+    res["device_error"] = A.device_error()
+    print(json.dumps(res, indent=1, default=float))
+
+
+def cfg1(A, oracle, synth, P32, res):
     clean, noisy = synth.make_batch([0], 128, 128, 25.0)
     x = torch.from_numpy(noisy).cuda()
     ms = gpu_ms(lambda: A.denoise_bm3d(x, 25.0, P32), reps=20)
@@ -65,7 +79,9 @@ def main():
                    oracle.psnr(ref, clean[0]), "max_abs_err": float(np.abs(out - ref).max()),
                    "oracle_mpix_s": 128 * 128 / 1e6 / to}
 
-    # cfg2
+
+
+def cfg2(A, oracle, synth, P32, P16, res, quick):
     c2 = {}
     for s in (15.0, 25.0, 50.0):
         clean, noisy = synth.make_batch(range(8), 512, 512, s)
@@ -77,7 +93,7 @@ def main():
         on = A.denoise_nlm(x, s).cpu().numpy()
         o32 = A.denoise_bm3d(x, s, P32).cpu().numpy()
         o16 = A.denoise_bm3d(x, s, P16).cpu().numpy()
-        imgs = range(1) if args.quick else range(8)
+        imgs = range(1) if quick else range(8)
         dn, db, d16, en, eb, e16, tn, tb = [], [], [], [], [], [], 0.0, 0.0
         for i in imgs:
             t0 = time.perf_counter()
@@ -102,7 +118,8 @@ def main():
         c2["sigma%d" % int(s)] = row
     res["cfg2"] = c2
 
-    # cfg3
+
+def cfg3(A, oracle, synth, P32, P16, P16M, res):
     clean, noisy = synth.make_batch(range(100, 116), 1024, 1024, 25.0)
     x = torch.from_numpy(noisy).cuda()
     mp = 16 * 1024 * 1024 / 1e6
@@ -125,7 +142,8 @@ def main():
         c3[name + "_crop_max_abs_err"] = float(np.abs(oc - rc).max())
     res["cfg3"] = c3
 
-    # cfg4
+
+def cfg4(A, oracle, synth, P32, P16, res):
     from bench import load_weights
     w, wsrc = load_weights(torch.device("cuda", 0))
     clean, noisy = synth.make_batch(range(5000, 5032), 512, 512, 25.0)
@@ -140,8 +158,6 @@ def main():
     ob = A.denoise_bm3d(x, 25.0, P32).cpu().numpy()
     c4["bm3d_only_psnr_db"] = float(np.mean([oracle.psnr(ob[i], clean[i]) for i in range(32)]))
     res["cfg4"] = c4
-    res["device_error"] = A.device_error()
-    print(json.dumps(res, indent=1, default=float))
 
 
 if __name__ == "__main__":

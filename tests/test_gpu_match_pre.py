@@ -149,3 +149,34 @@ def test_denoise_high_sigma_psnr_matches_oracle(oracle, C, sigma):
     # the prethresholded first pass is what the oracle's regime-0 BM3D runs at this sigma
     _, o_raw = oracle.bm3d(noisy[0].astype(np.float64), sigma, regime=1)
     assert np.abs(o - o_raw).max() > 1e-3
+
+
+def test_match_pre_full_size_sampled(oracle):
+    """1024 x 1024 at sigma = 50 (the size the high-noise bench runs): the
+    lists of 200 sampled references against the oracle run on crops that
+    contain each reference's whole search window (unflagged references exact)."""
+    A = api()
+    _, noisy = synth.make_batch([110, 111], 1024, 1024, 50.0)
+    p = A.default_bm3d_params().hard
+    idx, n = A.bm3d_match_prethresh(dev(noisy[:, 0]), [5000.0, 5000.0], [100.0, 100.0], p)
+    idx, n = host(idx), host(n)
+    gy = np.array(A.grid(1024))
+    rng = np.random.default_rng(6)
+    checked = bad = 0
+    for _ in range(200):
+        b = int(rng.integers(0, 2))
+        ry, rx = int(rng.integers(0, len(gy))), int(rng.integers(0, len(gy)))
+        y0, x0 = int(gy[ry]), int(gy[rx])
+        cy, cx = (max(0, y0 - 19) // 3) * 3, (max(0, x0 - 19) // 3) * 3
+        ey, ex = min(1024, y0 + 27), min(1024, x0 + 27)
+        om = oracle.match_pre(noisy[b, 0, cy:ey, cx:ex], oracle.Pass(tau=5000.0), 100.0)
+        oy, ox = list(oracle.grid(ey - cy)).index(y0 - cy), list(oracle.grid(ex - cx)).index(x0 - cx)
+        if om["flag"][oy, ox]:
+            continue
+        checked += 1
+        k = int(om["n"][oy, ox])
+        assert n[b, ry, rx] == k
+        ol = om["idx"][oy, ox, :k]
+        full = (ol // (ex - cx) + cy) * 1024 + ol % (ex - cx) + cx
+        bad += int(not np.array_equal(idx[b, ry, rx, :k], full))
+    assert bad == 0 and checked >= 80, (bad, checked)
