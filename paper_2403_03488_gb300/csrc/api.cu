@@ -177,24 +177,20 @@ dn_status match_pass1(const float *x, size_t plane, int nb, int C, int H, int W,
                       const float *sigma, const float *sig, const float *tau, int *idx, int *n, int *mws,
                       cudaStream_t s)
 {
+    if (nb > 1024) return DN_EINVAL;  // callers pass chunks of at most 1024 images
     const size_t R = (size_t)grid_count(H, 8, p->hard.step) * grid_count(W, 8, p->hard.step);
     auto pre = [&](int i) { return p->sigma_regime == 0 && sigma[i] > 40.0f && p->hard.lambda2d > 0.0f; };
+    float thr[1024];
+    for (int i = 0; i < nb; ++i) thr[i] = p->hard.lambda2d * sig[(size_t)i * C];
     for (int i0 = 0; i0 < nb;) {
         int i1 = i0 + 1;
         while (i1 < nb && pre(i1) == pre(i0)) ++i1;
         const float *g = x + (size_t)i0 * plane;
         int *ix = idx + (size_t)i0 * R * p->hard.n2, *nn = n + (size_t)i0 * R;
-        if (pre(i0)) {
-            float thr[kChunk];
-            for (int i = i0; i < i1; i += kChunk) {
-                const int m = i1 - i < kChunk ? i1 - i : kChunk;
-                for (int j = 0; j < m; ++j) thr[j] = p->hard.lambda2d * sig[(size_t)(i + j) * C];
-                DN_TRY(match_prethresh(x + (size_t)i * plane, plane, m, H, W, p->hard, tau + i, thr,
-                                       idx + (size_t)i * R * p->hard.n2, n + (size_t)i * R, s));
-            }
-        } else {
+        if (pre(i0))
+            DN_TRY(match_prethresh(g, plane, i1 - i0, H, W, p->hard, tau + i0, thr + i0, ix, nn, s));
+        else
             DN_TRY(match_any(g, plane, i1 - i0, H, W, p->hard, tau + i0, p->precision, ix, nn, mws, s));
-        }
         i0 = i1;
     }
     return DN_OK;
