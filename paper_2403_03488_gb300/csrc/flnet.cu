@@ -82,6 +82,73 @@ __global__ void __launch_bounds__(kT) k_dw_fwd(const float *__restrict__ x, cons
     }
 }
 
+// Vector form for planes whose width is a multiple of 4 (stride 1) or 8
+// (stride 2), 16-byte aligned: each thread owns 4 adjacent output columns (one
+// float4 store per output row) and DwRows4<S> output rows.  Per input row it
+// loads the values under its outputs with 16-byte loads (4 at stride 1, 8 at
+// stride 2) plus the edge values beside them: input columns S xo - 1 ..
+// S xo + 4 S, where output j takes columns S j .. S j + 2 of that run.
+template <int S> struct DwRows4 {
+    static constexpr int value = S == 1 ? 8 : 4;
+};
+
+template <int S>
+__global__ void __launch_bounds__(kT) k_dw_fwd4(const float *__restrict__ x, const float *__restrict__ w,
+                                                const float *__restrict__ b, float *__restrict__ y, int C, int H,
+                                                int W, int Ho, int Wo, int cw, int bands_per_block, int col_chunks,
+                                                int c0, int relu)
+{
+    constexpr int R = DwRows4<S>::value, IN = S * (R - 1) + 3, NV = S == 1 ? 6 : 9;
+    const size_t nc = blockIdx.y;
+    const int c = (int)((c0 + nc) % C);
+    const int chunk = blockIdx.x % col_chunks, band0 = (blockIdx.x / col_chunks) * bands_per_block;
+    const int q = chunk * cw + (int)threadIdx.x % cw;  // output quad: columns 4 q .. 4 q + 3
+    const int yo0 = (band0 + (int)threadIdx.x / cw) * R;
+    if (4 * q >= Wo || yo0 >= Ho) return;
+    const float *xp = x + nc * H * W;
+    const int xl = S * 4 * q - 1, y0 = S * yo0 - 1;  // first input column and row of the thread's window
+    float v[IN][NV];
+#pragma unroll
+    for (int r = 0; r < IN; ++r) {
+        const int yy = y0 + r;
+        if (yy < 0 || yy >= H) {
+#pragma unroll
+            for (int k = 0; k < NV; ++k) v[r][k] = 0.0f;
+            continue;
+        }
+        const float *rp = xp + (size_t)yy * W;
+        v[r][0] = xl >= 0 ? rp[xl] : 0.0f;
+        const float4 a = *reinterpret_cast<const float4 *>(rp + xl + 1);
+        v[r][1] = a.x, v[r][2] = a.y, v[r][3] = a.z, v[r][4] = a.w;
+        if (S == 1) {
+            v[r][5] = xl + 5 < W ? rp[xl + 5] : 0.0f;
+        } else {  // W % 8 == 0: the second quad ends at column 8 q + 7 <= W - 1
+            const float4 e = *reinterpret_cast<const float4 *>(rp + xl + 5);
+            v[r][5] = e.x, v[r][6] = e.y, v[r][7] = e.z, v[r][8] = e.w;
+        }
+    }
+    float k[9];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) k[t] = w[c * 9 + t];
+    const float bias = b ? b[c] : 0.0f;
+    float *yp = y + nc * Ho * Wo + 4 * q;
+#pragma unroll
+    for (int o = 0; o < R; ++o) {
+        if (yo0 + o >= Ho) break;
+        float acc[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            float s = bias;
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int t = 0; t < 3; ++t) s = fmaf(k[i * 3 + t], v[S * o + i][S * j + t], s);
+            acc[j] = relu_if(s, relu);
+        }
+        *reinterpret_cast<float4 *>(yp + (size_t)(yo0 + o) * Wo) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+    }
+}
+
 // dx[n][c][yy][xx] = sum over the outputs that read (yy, xx) of g * w.
 __global__ void k_dw_bwd_data(const float *g, const float *w, float *dx, int N, int C, int H, int W, int s, int Ho,
                               int Wo)
@@ -588,9 +655,12 @@ dn_status dn_dw3x3_fwd(const float *x, const float *w, const float *b, float *y,
 {
     if (!x || !w || !y || !dims_ok(N, C, H, W) || (stride != 1 && stride != 2)) return DN_EINVAL;
     const int Ho = (H + stride - 1) / stride, Wo = (W + stride - 1) / stride;
-    const int cw = Wo >= kT ? kT : (Wo + 31) / 32 * 32, bpb = kT / cw;
-    const int R = stride == 1 ? DwRows<1>::value : DwRows<2>::value;
-    const int col_chunks = (Wo + cw - 1) / cw, bands = (Ho + R - 1) / R;
+    const bool vec = (stride == 1 ? W % 4 == 0 : W % 8 == 0) && aligned16(x) && aligned16(y);
+    const int cols = vec ? Wo / 4 : Wo;  // threads along a row: output quads or columns
+    const int cw = cols >= kT ? kT : (cols + 31) / 32 * 32, bpb = kT / cw;
+    const int R = vec ? (stride == 1 ? DwRows4<1>::value : DwRows4<2>::value)
+                      : (stride == 1 ? DwRows<1>::value : DwRows<2>::value);
+    const int col_chunks = (cols + cw - 1) / cw, bands = (Ho + R - 1) / R;
     const int gx = col_chunks * ((bands + bpb - 1) / bpb);
     cudaStream_t s = (cudaStream_t)stream;
     const size_t planes = (size_t)N * C, in_plane = (size_t)H * W, out_plane = (size_t)Ho * Wo;
@@ -600,10 +670,15 @@ dn_status dn_dw3x3_fwd(const float *x, const float *w, const float *b, float *y,
         float *ys = y + p0 * out_plane;
         const int c0 = (int)(p0 % C);  // channel of this launch's first plane
         DN_TRY(launch("fl_dw3x3_fwd", s, [&] {
-            if (stride == 1)
-                k_dw_fwd<1><<<dim3(gx, np), kT, 0, s>>>(xs, w, b, ys, C, H, W, Ho, Wo, cw, bpb, col_chunks, c0, relu);
+            const dim3 grid(gx, np);
+            if (vec && stride == 1)
+                k_dw_fwd4<1><<<grid, kT, 0, s>>>(xs, w, b, ys, C, H, W, Ho, Wo, cw, bpb, col_chunks, c0, relu);
+            else if (vec)
+                k_dw_fwd4<2><<<grid, kT, 0, s>>>(xs, w, b, ys, C, H, W, Ho, Wo, cw, bpb, col_chunks, c0, relu);
+            else if (stride == 1)
+                k_dw_fwd<1><<<grid, kT, 0, s>>>(xs, w, b, ys, C, H, W, Ho, Wo, cw, bpb, col_chunks, c0, relu);
             else
-                k_dw_fwd<2><<<dim3(gx, np), kT, 0, s>>>(xs, w, b, ys, C, H, W, Ho, Wo, cw, bpb, col_chunks, c0, relu);
+                k_dw_fwd<2><<<grid, kT, 0, s>>>(xs, w, b, ys, C, H, W, Ho, Wo, cw, bpb, col_chunks, c0, relu);
         }));
     }
     return DN_OK;

@@ -35,10 +35,13 @@ def close(a, b, rel=1e-5):
 
 @pytest.mark.parametrize("stride,relu,shape", [(1, False, (2, 5, 13, 18)), (2, False, (2, 5, 13, 18)),
                                                (1, True, (2, 5, 13, 18)), (2, True, (2, 5, 13, 18)),
-                                               (1, True, (2, 3, 70, 301)), (2, False, (3, 3, 71, 600))])
+                                               (1, True, (2, 3, 70, 301)), (2, False, (3, 3, 71, 600)),
+                                               (1, True, (2, 3, 37, 520)), (2, True, (2, 5, 13, 16)),
+                                               (1, False, (1, 4, 21, 1032))])
 def test_depthwise_forward_and_backward(oracle, stride, relu, shape):
-    """Small planes, and planes with several 16-row bands and 256-column chunks
-    (ragged in both) for the banded forward kernel."""
+    """Small planes, and planes with several row bands and column chunks
+    (ragged in both) for the banded forward kernels; widths that are multiples
+    of 4 (stride 1) or 8 (stride 2) take the float4 form."""
     _, F = oracle._fl_torch()
     rng = np.random.default_rng(stride)
     C = shape[1]
