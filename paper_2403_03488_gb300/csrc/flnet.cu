@@ -14,6 +14,7 @@
 // order (per-thread partial sums, then a block tree), so every result is
 // deterministic.
 #include "common.cuh"
+#include "tc.cuh"
 
 namespace dn {
 
@@ -307,66 +308,63 @@ __global__ void __launch_bounds__(kT) k_pw(const float *__restrict__ x, const fl
     }
 }
 
+constexpr int kKC = 8;  // input channels per cp.async stage
+constexpr size_t kStageBytes = 2 * kKC * kT * sizeof(float4);  // dynamic shared memory of the staged kernels
+
 // Feeds step(ci, v) the float4 xp[ci * stride] of every channel ci < Cin in
-// order, loading four channels at a time; with Prefetch the next four are
-// loaded while the current ones are consumed (eight 16-byte loads in flight
-// per thread, at the cost of 16 registers).
-template <bool Prefetch, class Step>
-__device__ __forceinline__ void quad_channels(const float4 *__restrict__ xp, size_t stride, int Cin, Step &step)
+// order, through the calling thread's slots of `stage` ([2][kKC][kT] float4):
+// the thread copies kKC channels per stage with cp.async, two stages deep (the
+// next kKC channels are in flight while the current ones are consumed), and
+// reads back only what it copied itself, so no barrier is needed and the loads
+// in flight hold no registers.
+template <class Step>
+__device__ __forceinline__ void staged_channels(const float4 *__restrict__ xp, size_t stride, int Cin, float4 *stage,
+                                                int tid, Step &step)
 {
-    int ci = 0;
-    if (!Prefetch) {
-        for (; ci + 4 <= Cin; ci += 4) {
-            float4 u[4];
+    const int nchunk = (Cin + kKC - 1) / kKC;
+    auto issue = [&](int c) {  // channels c kKC .. c kKC + kKC - 1 into stage c & 1
 #pragma unroll
-            for (int t = 0; t < 4; ++t) u[t] = xp[(size_t)(ci + t) * stride];
-#pragma unroll
-            for (int t = 0; t < 4; ++t) step(ci + t, u[t]);
+        for (int t = 0; t < kKC; ++t) {
+            const int ci = c * kKC + t;
+            if (ci < Cin)
+                tc::cp_async16(tc::smem_u32(&stage[((c & 1) * kKC + t) * kT + tid]), xp + (size_t)ci * stride);
         }
-        for (; ci < Cin; ++ci) step(ci, xp[(size_t)ci * stride]);
-        return;
-    }
-    float4 u[4];
-    if (Cin >= 4) {
+        tc::cp_async_commit();
+    };
+    issue(0);
+    for (int c = 0; c < nchunk; ++c) {
+        if (c + 1 < nchunk) issue(c + 1);
+        else tc::cp_async_commit();  // an empty group keeps "all but the newest group" meaning chunk c
+        tc::cp_async_wait<1>();
 #pragma unroll
-        for (int t = 0; t < 4; ++t) u[t] = xp[(size_t)t * stride];
-    }
-    for (; ci + 4 <= Cin; ci += 4) {
-        float4 nx[4];
-        const bool more = ci + 8 <= Cin;
-        if (more) {
-#pragma unroll
-            for (int t = 0; t < 4; ++t) nx[t] = xp[(size_t)(ci + 4 + t) * stride];
-        }
-#pragma unroll
-        for (int t = 0; t < 4; ++t) step(ci + t, u[t]);
-        if (more) {
-#pragma unroll
-            for (int t = 0; t < 4; ++t) u[t] = nx[t];
+        for (int t = 0; t < kKC; ++t) {
+            const int ci = c * kKC + t;
+            if (ci >= Cin) break;
+            step(ci, stage[((c & 1) * kKC + t) * kT + tid]);
         }
     }
-    for (; ci < Cin; ++ci) step(ci, xp[(size_t)ci * stride]);
 }
 
 // Vector form of k_pw for HW % 4 == 0 with 16-byte aligned x and y: each thread
-// owns four consecutive pixels of one image (one float4 per channel row), so a
-// warp's load moves 512 bytes and four channels' loads are in flight together.
+// owns four consecutive pixels of one image (one float4 per channel row) and
+// kPC output channels; its input float4s arrive through staged_channels.
 __global__ void __launch_bounds__(kT) k_pw4(const float *__restrict__ x, const float *__restrict__ w,
                                             const float *__restrict__ b, float *__restrict__ y, int N, int Cin,
                                             int Cout, int HW, int wso, int wsi, int relu)
 {
+    extern __shared__ __align__(16) float4 stage[];  // [2][kKC][kT]
     __shared__ __align__(16) float ws[kPMax * kPC];
     __shared__ float bias[kPC];
-    const int co0 = blockIdx.x * kPC;
-    for (int i = threadIdx.x; i < Cin * kPC; i += kT) {
+    const int co0 = blockIdx.x * kPC, tid = threadIdx.x;
+    for (int i = tid; i < Cin * kPC; i += kT) {
         const int ci = i / kPC, k = i % kPC;
         ws[i] = co0 + k < Cout ? w[(size_t)(co0 + k) * wso + (size_t)ci * wsi] : 0.0f;
     }
-    if (threadIdx.x < kPC) bias[threadIdx.x] = (b && co0 + threadIdx.x < Cout) ? b[co0 + threadIdx.x] : 0.0f;
+    if (tid < kPC) bias[tid] = (b && co0 + tid < Cout) ? b[co0 + tid] : 0.0f;
     __syncthreads();
     const float4 *w4 = reinterpret_cast<const float4 *>(ws);
     const size_t HW4 = (size_t)HW / 4, total = (size_t)N * HW4;
-    for (size_t e = (size_t)blockIdx.y * kT + threadIdx.x; e < total; e += (size_t)gridDim.y * kT) {
+    for (size_t e = (size_t)blockIdx.y * kT + tid; e < total; e += (size_t)gridDim.y * kT) {
         const size_t n = e / HW4, q = e % HW4;
         const float4 *xp = reinterpret_cast<const float4 *>(x) + n * Cin * HW4 + q;
         float a[kPC][4];
@@ -378,16 +376,16 @@ __global__ void __launch_bounds__(kT) k_pw4(const float *__restrict__ x, const f
                 const float4 wq = w4[ci * (kPC / 4) + g];
                 const float wk[4] = {wq.x, wq.y, wq.z, wq.w};
 #pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    float *ak = a[4 * g + t];
-                    ak[0] = fmaf(wk[t], v.x, ak[0]);
-                    ak[1] = fmaf(wk[t], v.y, ak[1]);
-                    ak[2] = fmaf(wk[t], v.z, ak[2]);
-                    ak[3] = fmaf(wk[t], v.w, ak[3]);
+                for (int u = 0; u < 4; ++u) {
+                    float *ak = a[4 * g + u];
+                    ak[0] = fmaf(wk[u], v.x, ak[0]);
+                    ak[1] = fmaf(wk[u], v.y, ak[1]);
+                    ak[2] = fmaf(wk[u], v.z, ak[2]);
+                    ak[3] = fmaf(wk[u], v.w, ak[3]);
                 }
             }
         };
-        quad_channels<false>(xp, HW4, Cin, step);  // measured: prefetching is slower here
+        staged_channels(xp, HW4, Cin, stage, tid, step);
         float4 *yp = reinterpret_cast<float4 *>(y) + (n * Cout + co0) * HW4 + q;
 #pragma unroll
         for (int k = 0; k < kPC; ++k)
@@ -487,12 +485,13 @@ constexpr int kDC4 = 4;  // output channels per block in the vector transposed c
 
 // Vector form of k_deconv_fwd for W % 4 == 0 with 16-byte aligned x, y and skip:
 // each thread owns four consecutive input pixels of a row (one float4 per
-// channel) and kDC4 output channels, i.e. two 8-wide output row segments per
-// channel, stored as float4 pairs.
+// channel, arriving through staged_channels) and kDC4 output channels, i.e.
+// two 8-wide output row segments per channel, stored as float4 pairs.
 __global__ void __launch_bounds__(kT, 2) k_deconv_fwd4(const float *__restrict__ x, const float *__restrict__ w,
                                                     const float *__restrict__ b, const float *__restrict__ skip,
                                                     float *__restrict__ y, int N, int Cin, int Cout, int H, int W)
 {
+    extern __shared__ __align__(16) float4 stage[];  // [2][kKC][kT]: staged_channels
     __shared__ __align__(16) float ws[kPMax * kDC4 * 4];
     const int co0 = blockIdx.x * kDC4;
     for (int i = threadIdx.x; i < Cin * kDC4 * 4; i += kT) {
@@ -528,7 +527,7 @@ __global__ void __launch_bounds__(kT, 2) k_deconv_fwd4(const float *__restrict__
                 }
             }
         };
-        quad_channels<true>(xp, HW4, Cin, step);
+        staged_channels(xp, HW4, Cin, stage, (int)threadIdx.x, step);
 #pragma unroll
         for (int k = 0; k < kDC4; ++k) {
             if (co0 + k >= Cout) continue;
@@ -707,8 +706,11 @@ dn_status dn_pw_fwd(const float *x, const float *w, const float *b, float *y, in
     dim3 grid((Cout + kPC - 1) / kPC, blocks_for(((size_t)N * HW + 1) / 2));
     const int wso = transposed ? 1 : Cin, wsi = transposed ? Cout : 1;
     if (HW % 4 == 0 && aligned16(x) && aligned16(y)) {
+        if (cudaFuncSetAttribute(k_pw4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStageBytes) != cudaSuccess)
+            return DN_ECUDA;
         dim3 g4((Cout + kPC - 1) / kPC, blocks_for((size_t)N * HW / 4));
-        return launch("fl_pw_fwd", s, [&] { k_pw4<<<g4, kT, 0, s>>>(x, w, b, y, N, Cin, Cout, HW, wso, wsi, relu); });
+        return launch("fl_pw_fwd", s,
+                      [&] { k_pw4<<<g4, kT, kStageBytes, s>>>(x, w, b, y, N, Cin, Cout, HW, wso, wsi, relu); });
     }
     return launch("fl_pw_fwd", s, [&] { k_pw<<<grid, kT, 0, s>>>(x, w, b, y, N, Cin, Cout, HW, wso, wsi, relu); });
 }
@@ -729,9 +731,12 @@ dn_status dn_deconv2x2_fwd(const float *x, const float *w, const float *b, const
     if ((reinterpret_cast<uintptr_t>(w) & 15) != 0) return DN_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     if (W % 4 == 0 && aligned16(x) && aligned16(y) && (!skip || aligned16(skip))) {
+        if (cudaFuncSetAttribute(k_deconv_fwd4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStageBytes) !=
+            cudaSuccess)
+            return DN_ECUDA;
         dim3 g4((Cout + kDC4 - 1) / kDC4, blocks_for((size_t)N * H * W / 4));
         return launch("fl_deconv2x2_fwd", s,
-                      [&] { k_deconv_fwd4<<<g4, kT, 0, s>>>(x, w, b, skip, y, N, Cin, Cout, H, W); });
+                      [&] { k_deconv_fwd4<<<g4, kT, kStageBytes, s>>>(x, w, b, skip, y, N, Cin, Cout, H, W); });
     }
     dim3 grid((Cout + kDC - 1) / kDC, blocks_for((size_t)N * H * W));
     return launch("fl_deconv2x2_fwd", s, [&] { k_deconv_fwd<<<grid, kT, 0, s>>>(x, w, b, skip, y, N, Cin, Cout, H, W); });
