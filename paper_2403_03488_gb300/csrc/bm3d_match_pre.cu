@@ -18,11 +18,13 @@
 // staged with a 68-float stride (the 16-byte loads of a quarter warp, whose
 // lanes hold references `step` apart, fall in distinct banks for step 3);
 // the next pixel row is loaded into registers while the current row is
-// matched.  Each thread
-// forms its own reference's vector with the same operations in the same
-// order, so equal patches give equal vectors, and accumulates (r - q)^2 with
-// packed FP32x2 operations in four interleaved partial sums.  No coefficient
-// buffer: the transforms cost about a tenth of the distance arithmetic.
+// matched.  Each thread forms its own reference's vector with the same
+// operations in the same order, so equal patches give equal vectors, and
+// accumulates (r - q)^2 with packed FP32x2 operations in four interleaved
+// partial sums.  No coefficient buffer: the transforms cost about an eighth of
+// the distance arithmetic.  The kernel is bound by shared-memory bandwidth
+// (each pair reads the candidate's 256-byte vector; lanes read different
+// candidates).
 #include <cmath>
 
 #include "common.cuh"

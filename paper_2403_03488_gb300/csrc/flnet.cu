@@ -8,11 +8,16 @@
 //   pointwise       y[n][co][p] = b[co] + sum_ci w[co][ci] x[n][ci][p]
 //   transposed 2x2  y[n][co][2i + a][2j + c] = b[co] + skip[...] + sum_ci w[ci][co][a][c] x[n][ci][i][j]
 //
-// Forward kernels map one thread to one output pixel (and a block of output
-// channels in registers); data gradients map one thread to one input pixel
-// (gathers, no atomics); weight gradients reduce over all pixels in a fixed
-// order (per-thread partial sums, then a block tree), so every result is
-// deterministic.
+// Forward kernels: the depthwise layer gives each thread 4 adjacent output
+// columns and a band of output rows (its whole input window loaded at once
+// with 16-byte loads); the pointwise and transposed layers keep a block of
+// output channels' weights in shared memory and give each thread 4 pixels x
+// a block of output channels in registers, its inputs staged through shared
+// memory with per-thread cp.async; scalar forms cover widths that are not
+// multiples of 4 (or 8 at stride 2).  Data gradients map one thread to one
+// input pixel (gathers, no atomics); weight gradients reduce over all pixels
+// in a fixed order (per-thread partial sums, then a block tree), so every
+// result is deterministic.
 #include "common.cuh"
 #include "tc.cuh"
 
