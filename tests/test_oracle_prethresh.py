@@ -119,3 +119,13 @@ def test_first_pass_with_zero_prethreshold_is_the_plain_first_pass(oracle):
     np.testing.assert_allclose(b, a, rtol=0, atol=1e-9)
     c, _, _ = oracle.bm3d_pass1(x, [50.0], oracle.Pass(n2=16, tau=5000.0, lambda2d=2.0))
     assert np.abs(c - a).max() > 1e-3  # the prethreshold changes the groups at sigma 50
+
+
+def test_regime_selects_the_prethreshold_above_sigma_40(oracle):
+    """Regime 0 switches to tau = 5000 / 3500 and the prethresholded first
+    pass strictly above sigma = 40; regime 1 never does; the second pass never
+    prethresholds."""
+    for sigma, regime, lam, t1, t2 in ((40.0, 0, 0.0, 2500.0, 400.0), (40.5, 0, 2.0, 5000.0, 3500.0),
+                                       (50.0, 1, 0.0, 2500.0, 400.0), (15.0, 0, 0.0, 2500.0, 400.0)):
+        h, w = oracle.default_passes(sigma, regime)
+        assert (h.lambda2d, h.tau, w.tau, w.lambda2d) == (lam, t1, t2, 0.0), (sigma, regime)
