@@ -30,7 +30,19 @@ B = 16
 SIGMA = 25.0
 SEEDS0 = 100
 METRIC = "MPix/s BM3D+CNN at <=0.05 dB PSNR loss vs FP32 plain; served p50/p99 ms"
-FP32_PEAK_TFLOPS_NOTE = "FP32 ALU peak = 152 SM x 128 lanes x 2 FLOP/FMA x 2.07 GHz = 80.5 TFLOP/s"
+# the machine the FP32 ALU peak is derived for when the device is not queried
+# (host-only use of the work counts): GB300's SM count and maximum SM clock
+DEFAULT_HW = {"sm_count": 152, "sm_mhz": 2070.0, "source": "assumed (GB300: 152 SMs, 2070 MHz)"}
+
+
+def fp32_peak(hw):
+    """FP32 ALU peak in TFLOP/s: SMs x 128 FP32 lanes x 2 FLOP per FMA x SM clock."""
+    return hw["sm_count"] * 128 * 2 * hw["sm_mhz"] * 1e6 / 1e12
+
+
+def fp32_note(hw):
+    return ("FP32 ALU peak = %d SM x 128 lanes x 2 FLOP/FMA x %.0f MHz = %.1f TFLOP/s (derived; SM count and clock %s)"
+            % (hw["sm_count"], hw["sm_mhz"], fp32_peak(hw), hw["source"]))
 
 
 def workload_name(bm3d, cnn, prefilter="bm3d", net="resnet"):
@@ -111,26 +123,65 @@ def match_pairs(Hh, Ww, step=3, search=39):
     return int(per_axis(Hh).sum() * per_axis(Ww).sum())
 
 
-def algorithmic(kernel, launches_per_step, batch):
+# Collaborative filtering work per patch of a full group (n = n2 patches), in
+# FLOP.  "tensor": the 3D transform written as dense contractions, as the
+# nominal per-pixel figures of the filtering rows count it: the 2D DCT of a
+# patch and its inverse as 64 x 64 matrix-vector products (2 x 8192 each) and
+# the group transform as an n x n product per coefficient (2 n per coefficient
+# and direction); pass 1 transforms the noisy group forward and back (2 + 2),
+# pass 2 the basic and noisy groups forward and the estimate back (3 + 3).
+# "alu": the separable form the CUDA-core kernels evaluate: each 2D DCT as 16
+# 8-point matrix-vector products (2 x 8 x 8 each = 2048 FLOP per patch), the
+# group transform as a fast Walsh-Hadamard transform (log2 n additions per
+# coefficient and direction), 2 FLOP per coefficient for shrinkage (pass 2:
+# 4, the Wiener gain) and 3 per pixel for the windowed aggregation.
+def filter_flops_per_patch(wiener, n):
+    lg = max(1, int(np.log2(n)))
+    nt = 3 if wiener else 2  # 2D transforms per patch
+    tensor = nt * 2 * 64 * 64 + nt * 2 * n * 64
+    alu = nt * 2048 + nt * 64 * lg + (4 if wiener else 2) * 64 + 3 * 64
+    return tensor, alu
+
+
+def filter_work(wiener, Hh, Ww, batch, step=3):
+    """(tensor FLOP, ALU FLOP) of one filtering launch over `batch` images,
+    every group full (n = 16 in pass 1, 32 in pass 2): an upper count, since
+    groups below the threshold hold fewer patches."""
+    from paper_2403_03488_gb300 import api
+    refs = len(api.grid(Hh, 8, step)) * len(api.grid(Ww, 8, step)) * batch
+    n = 32 if wiener else 16
+    t, a = filter_flops_per_patch(wiener, n)
+    return refs * n * t, refs * n * a
+
+
+def algorithmic(kernel, launches_per_step, batch, hw=None):
     """(bound, unit, work per launch, peak, peak note) for a kernel name."""
+    hw = hw or DEFAULT_HW
     peaks = {}
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         peaks = json.load(open(p))
-    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    fpk, fnote = fp32_peak(hw), fp32_note(hw)
     if kernel.startswith("bm3d_match"):
         # one launch covers up to 64 images of one pass; 192 FLOP (sub, mul, add over 64 pixels or
         # prethresholded coefficients) per (reference, candidate) pair
         pairs = match_pairs(H, W) * min(batch, 64)
-        return "alu", "TFLOP/s", 192.0 * pairs, fp32_peak, FP32_PEAK_TFLOPS_NOTE + " (derived, not measured)"
+        return "alu", "TFLOP/s", 192.0 * pairs, fpk, fnote
+    if kernel.startswith("bm3d_filter_"):
+        wiener = "wiener" in kernel
+        tensor, alu = filter_work(wiener, H, W, batch)
+        if kernel.endswith("bf16"):
+            bf = peaks.get("bf16_tflops_sustained", 1700.0)
+            return "tensor", "TFLOP/s", float(tensor), bf, "measured bf16_tflops_sustained (dense contractions count)"
+        return "alu", "TFLOP/s", float(alu), fpk, fnote + " (separable count)"
     if kernel.startswith("nlm_fp32"):
         # per pixel and search offset: difference + square (2), separable 7 + 7 box sums (12), weight (4:
         # subtract, clamp, scale, exp) and the two weighted accumulations (4)
         flops = 22.0 * 441 * H * W * batch / launches_per_step
-        return "alu", "TFLOP/s", flops, fp32_peak, FP32_PEAK_TFLOPS_NOTE + " (derived, not measured)"
+        return "alu", "TFLOP/s", flops, fpk, fnote
     if kernel.startswith("conv3x3_fwd_fp32"):
         flops = 2.0 * H * W * batch * (2 * 32 * 9 + 8 * 32 * 32 * 9 + 32 * 9) / launches_per_step
-        return "alu", "TFLOP/s", flops, fp32_peak, FP32_PEAK_TFLOPS_NOTE + " (derived, not measured)"
+        return "alu", "TFLOP/s", flops, fpk, fnote
     hbm = peaks.get("hbm_gbs", 6800.0)
     px = H * W * batch  # every launch of these kernels covers the whole batch
     hbm_bytes = {
@@ -148,28 +199,40 @@ def algorithmic(kernel, launches_per_step, batch):
         if kernel.startswith("fl_dw3x3_fwd"):  # 9 MAC per output: moves bytes, not FLOPs
             return "hbm", "GB/s", wpp["dw_bytes"] * px, hbm, "measured hbm_gbs"
         macs = wpp["pw_macs"] if kernel.startswith("fl_pw_fwd") else wpp["up_macs"]
-        return "alu", "TFLOP/s", 2.0 * macs * px, fp32_peak, FP32_PEAK_TFLOPS_NOTE + " (derived, not measured)"
+        return "alu", "TFLOP/s", 2.0 * macs * px, fpk, fnote
     # fall back to bytes: read + write of the image planes
     return "hbm", "GB/s", 8.0 * H * W * batch / launches_per_step, hbm, "measured hbm_gbs"
 
 
-def kernel_rooflines(res, steps, batch):
+def kernel_rooflines(res, steps, batch, hw=None):
     """Roofline fraction of every library kernel whose algorithmic work has a
-    plain count (see `algorithmic`): the matcher, NLM and the flexible network's
-    layers in FLOP, the CNN layers, the normalisation, the depthwise layers and
-    the error reduction in bytes that must cross HBM per launch (activations /
-    planes read and written once, halos excluded)."""
+    plain count (see `algorithmic`): the matcher, NLM, the collaborative
+    filters and the flexible network's layers in FLOP, the CNN layers, the
+    normalisation, the depthwise layers and the error reduction in bytes that
+    must cross HBM per launch (activations / planes read and written once,
+    halos excluded).  The FP32 filters also carry their dense-contraction
+    count against the BF16 tensor peak (`tensor_frac`)."""
     out = {}
+    peaks = {}
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        peaks = json.load(open(p))
     for k, (n, ms) in res.items():
-        if not k.startswith(("bm3d_match_fp32", "bm3d_match_pre", "nlm_fp32", "fl_pw_fwd", "fl_deconv2x2_fwd",
-                             "fl_dw3x3_fwd", "conv3x3_tc_bf16", "conv_first_bf16", "conv_last_bf16",
-                             "bm3d_normalize", "error_reduce_fp64")):
+        if not k.startswith(("bm3d_match_fp32", "bm3d_match_pre", "bm3d_match_tc", "bm3d_filter_", "nlm_fp32",
+                             "fl_pw_fwd", "fl_deconv2x2_fwd", "fl_dw3x3_fwd", "conv3x3_tc_bf16", "conv_first_bf16",
+                             "conv_last_bf16", "bm3d_normalize", "error_reduce_fp64")):
             continue
         avg = ms / n
-        bound, unit, work, peak, _ = algorithmic(k, n / steps, batch)
+        bound, unit, work, peak, _ = algorithmic(k, n / steps, batch, hw)
         ach = work / (avg / 1e3) / (1e12 if unit == "TFLOP/s" else 1e9)
         out[k] = {"bound": bound, "achieved": round(ach, 3 if unit == "TFLOP/s" else 1), "peak": round(peak, 1),
                   "unit": unit, "frac": round(ach / peak, 4), "avg_launch_ms": round(avg, 4)}
+        if k.startswith("bm3d_filter_") and k.endswith("fp32"):
+            tensor, _ = filter_work("wiener" in k, H, W, batch)
+            t_ach = tensor / (avg / 1e3) / 1e12
+            bf = peaks.get("bf16_tflops_sustained", 1700.0)
+            out[k].update({"tensor_achieved": round(t_ach, 3), "tensor_peak": round(bf, 1),
+                           "tensor_frac": round(t_ach / bf, 4)})
     return out
 
 
@@ -306,6 +369,28 @@ def run_ours(args):
                                    cnn_precision=api.DN_FP32)
     sse_p, _ = api.error_reduce(plain, clean_d)
     psnr_plain = 10 * np.log10(255.0 ** 2 / (float(sse_p.sum().item()) / (B * H * W)))
+    # throughput of the FP32 plain path on the same batch (FP32 BM3D, FP32 SIMT CNN; same L2 flush)
+    plain_ms = None
+    if not fl:
+        plain_out = torch.empty_like(noisy_d)
+        pparams = bp if nlm else api.default_bm3d_params()
+        plain_steps = 2
+        plain_ms = 0.0
+        for _ in range(plain_steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            api.denoise_hybrid(noisy_d, SIGMA, weights, prefilter=pf, prefilter_params=pparams,
+                               cnn_precision=api.DN_FP32, out=plain_out)
+            api.error_reduce(plain_out, clean_d)
+            e1.record()
+            e1.synchronize()
+            plain_ms += e0.elapsed_time(e1)
+        plain_ms = max_over_ranks(plain_ms) / plain_steps
+        del plain_out
+    out0 = out_d[0].clone()
+    plain0 = plain[0].clone()
     bm3d_only = api.denoise_nlm(noisy_d, SIGMA, bp) if nlm else api.denoise_bm3d(noisy_d, SIGMA, bp)
     sse_b, _ = api.error_reduce(bm3d_only, clean_d)
     psnr_bm3d = 10 * np.log10(255.0 ** 2 / (float(sse_b.sum().item()) / (B * H * W)))
@@ -342,7 +427,11 @@ def run_ours(args):
     top = max(res.items(), key=lambda kv: kv[1][1])
     kname, (kl, kms) = top
     per_step = kl / args.steps
-    bound, unit, work, peak, peak_note = algorithmic(kname, per_step, B)
+    props = torch.cuda.get_device_properties(local)
+    hw = {"sm_count": int(props.multi_processor_count),
+          "sm_mhz": float(clk.get("sm_mhz") or clk.get("sm_max_mhz") or DEFAULT_HW["sm_mhz"]),
+          "source": "read: multi_processor_count of the device, median SM clock sampled in the timed region"}
+    bound, unit, work, peak, peak_note = algorithmic(kname, per_step, B, hw)
     avg_ms = kms / kl
     achieved = work / (avg_ms / 1e3) / (1e12 if unit == "TFLOP/s" else 1e9)
     traffic = load_traffic(kname)
@@ -383,13 +472,22 @@ def run_ours(args):
                      "avg_launch_ms": round(avg_ms, 4), "peak_source": peak_note},
         "kernels": {k: {"launches": c, "ms": round(t, 3), "share": round(t / sum(x[1] for x in res.values()), 4)}
                     for k, (c, t) in sorted(res.items(), key=lambda kv: -kv[1][1])},
-        "kernel_rooflines": kernel_rooflines(res, args.steps, B),
+        "kernel_rooflines": kernel_rooflines(res, args.steps, B, hw),
+        "fp32_peak": {"tflops": round(fp32_peak(hw), 2), "sm_count": hw["sm_count"], "sm_mhz": hw["sm_mhz"],
+                      "source": hw["source"]},
         "clocks": clk,
     }
+    if plain_ms is not None:
+        line["fp32_plain"] = {"value": round(whole_job_value(mpix, world, plain_ms), 3), "unit": "MPix/s",
+                              "ms_per_step": round(plain_ms, 3),
+                              "what": "same workload, FP32 BM3D + FP32 CUDA-core CNN, same timing rules"}
     if not args.no_serving:
         line["serving"] = serving_replay(args)
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.cpu_side)
+        line["cpu_baseline"], oracle_out = cpu_baseline(args.cpu_side, None if fl else weights)
+        if not fl:
+            line["vs_fp64_oracle"] = vs_oracle(oracle_out, noisy_d, clean, args.cpu_side, out0, plain0, denoise,
+                                               weights, pf, bp, nlm)
     print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
@@ -463,29 +561,65 @@ def load_traffic(kname):
 # the oracle on host cores
 # ---------------------------------------------------------------------------
 
-def oracle_step(side):
+def oracle_step(side, weights=None):
     """FP64 oracle BM3D (both passes) + residual CNN on one side x side crop of
-    image 0 of the workload; returns (seconds, megapixels)."""
+    image 0 of the workload; returns (seconds, megapixels, output [side, side]).
+    weights: the flat FP32 parameters the GPU runs (host or device tensor), else
+    He init (seed 0)."""
     import oracle
     from paper_2403_03488_gb300 import synth
     from paper_2403_03488_gb300.synth import he_normal_weights
     clean, noisy = synth.make_batch([SEEDS0], H, W, SIGMA)
     crop = noisy[0, :, :side, :side].astype(np.float64)
-    params = he_normal_weights(0, 10, 32)
+    if weights is None:
+        params = he_normal_weights(0, 10, 32)
+    else:
+        from paper_2403_03488_gb300.autograd import ResidualNet
+        params = ResidualNet(10, 32, flat=weights.detach().cpu()).numpy_params()
     t0 = time.perf_counter()
     _, final = oracle.bm3d(crop, SIGMA)
-    oracle.cnn_forward(crop[:, :, :], final, params)
+    out = oracle.cnn_forward(crop[:, :, :], final, params)
     dt = time.perf_counter() - t0
-    return dt, side * side / 1e6
+    return dt, side * side / 1e6, np.asarray(out)[0]
 
 
-def cpu_baseline(side):
+def cpu_baseline(side, weights=None):
     import oracle
     oracle.build()
-    dt, mp = oracle_step(side)
+    dt, mp, out = oracle_step(side, weights)
     return {"value": round(mp / dt, 5), "unit": "MPix/s", "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": "FP64 oracle BM3D (both passes) + 10x32 CNN forward on one %dx%d crop of image 0 "
-                      "(%.1f s)" % (side, side, dt)}
+            "sample": "FP64 oracle BM3D (both passes) + 10x32 CNN forward (%s) on one %dx%d crop of image 0 "
+                      "(%.1f s)" % ("the bench's weights" if weights is not None else "He init", side, side, dt)}, out
+
+
+def vs_oracle(ref, noisy_d, clean, side, out0, plain0, denoise, weights, pf, bp, nlm):
+    """PSNR delta and max |error| of the GPU results against the FP64 oracle on
+    the cpu_baseline crop (image 0; when the crop is the whole image, the
+    outputs of the timed step are compared directly)."""
+    import torch
+    from paper_2403_03488_gb300 import api
+    c = clean[0, 0, :side, :side].astype(np.float64)
+    if side == H and side == W:
+        fast, plain = out0[0].cpu().numpy(), plain0[0].cpu().numpy()
+    else:
+        x = noisy_d[:1, :, :side, :side].contiguous()
+        o = torch.empty_like(x)
+        denoise(x, o)
+        fast = o[0, 0].cpu().numpy()
+        plain = api.denoise_hybrid(x, SIGMA, weights, prefilter=pf,
+                                   prefilter_params=bp if nlm else api.default_bm3d_params(),
+                                   cnn_precision=api.DN_FP32)[0, 0].cpu().numpy()
+
+    def psnr(a):
+        return 10 * np.log10(255.0 ** 2 / np.mean((np.clip(a, 0, 255) - c) ** 2))
+
+    out = {"crop": "%dx%d of image 0" % (side, side), "oracle_psnr_db": round(psnr(ref), 4)}
+    for name, a in (("fast", fast), ("fp32_plain", plain)):
+        e = np.abs(a.astype(np.float64) - ref)
+        out[name] = {"psnr_delta_db": round(psnr(a) - psnr(ref), 5), "max_abs_err": round(float(e.max()), 5),
+                     "p999_abs_err": round(float(np.quantile(e, 0.999)), 5),
+                     "mean_abs_err": round(float(e.mean()), 6)}
+    return out
 
 
 def run_reference(args):
@@ -498,7 +632,7 @@ def run_reference(args):
         oracle_step(64)
     total, mp = 0.0, 0.0
     for _ in range(args.steps):
-        dt, m = oracle_step(args.ref_side)
+        dt, m, _ = oracle_step(args.ref_side)
         total += dt
         mp += m
     value = mp / total

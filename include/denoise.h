@@ -133,7 +133,13 @@ size_t dn_hybrid_workspace_bytes(int B, int C, int H, int W, int prefilter, cons
 /* ---- the three denoisers ------------------------------------------------- */
 
 /* BM3D, both passes (standard definition; the paper's BM3D-G stage, Sec. II).
- * noisy/out: device [B][C][H][W] (may not alias); H, W >= patch. */
+ * noisy/out: device [B][C][H][W] (may not alias); H, W >= patch.
+ * DN_EUNSUPPORTED (before any launch) when an image takes the high-noise
+ * first pass (sigma > 40, sigma_regime 0, hard.lambda2d > 0) and the
+ * prethresholded matcher's staged window, (31 step + search) columns wide,
+ * does not fit in 200 KB of shared memory (for example step 12 with search
+ * 21 on an image wider than 400 pixels); the same
+ * holds for denoise_hybrid and denoise_bm3d_noalloc. */
 dn_status denoise_bm3d(const float *noisy, float *out, int B, int C, int H, int W, const float *sigma,
                        const dn_bm3d_params *p, void *workspace, size_t ws_bytes, dn_stream_t stream);
 
@@ -160,18 +166,24 @@ const char *dn_strerror(dn_status s);
  * this is a deployment convenience.
  * Same arguments and results as denoise_bm3d, minus the workspace: the
  * workspace is a fixed array of DN_NOALLOC_SCRATCH_BYTES of device memory
- * inside this library, reserved on every GPU that loads the library until the
- * process exits.  Requests whose dn_bm3d_workspace_bytes exceeds that size
- * (for example a 1 x 1 x 512 x 512 image fits, 1 x 3 x 512 x 512 does not)
- * return DN_ENOMEM before any launch.  The first call on a device does a
- * one-time set-up: it looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture begins.
+ * inside this library.  Requests whose dn_bm3d_workspace_bytes exceeds that
+ * size (for example a 1 x 1 x 512 x 512 image fits, 1 x 3 x 512 x 512 does
+ * not) return DN_ENOMEM before any launch.
+ * Reservation: under lazy module loading (CUDA's default) the array is
+ * reserved on a device when the library's device code is first loaded there,
+ * which can be this entry point's first call on that device; it then stays
+ * reserved until the process exits.  Make that first call a warm-up call
+ * before any stream capture and before the application takes the rest of the
+ * device memory: it returns DN_ECUDA when the device has no room left for the
+ * array.  Every call looks the array's device address up in the current
+ * context (cudaGetSymbolAddress), so a device reset between calls is safe.
  * Every call on a device shares the one array, and the array keeps the
  * previous call's contents (the call clears what must start at zero itself):
  * calls that may overlap on the GPU (other streams, other host threads) race
  * and must be serialised by the caller.  No cudaMalloc / cudaFree is made. */
 #define DN_NOALLOC_SCRATCH_BYTES (16u << 20)
+/* The size of that array in bytes (DN_NOALLOC_SCRATCH_BYTES of this build). */
+size_t dn_noalloc_scratch_bytes(void);
 dn_status denoise_bm3d_noalloc(const float *noisy, float *out, int B, int C, int H, int W, const float *sigma,
                                const dn_bm3d_params *p, dn_stream_t stream);
 

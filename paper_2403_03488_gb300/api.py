@@ -89,15 +89,19 @@ def denoise_bm3d(noisy: torch.Tensor, sigma, params: Optional[BM3DParams] = None
     return out
 
 
-NOALLOC_SCRATCH_BYTES = 16 << 20
+
+
+def noalloc_scratch_bytes() -> int:
+    """Size of the fixed device array behind denoise_bm3d_noalloc, as built."""
+    return int(L.lib().dn_noalloc_scratch_bytes())
 
 
 def denoise_bm3d_noalloc(noisy: torch.Tensor, sigma, params: Optional[BM3DParams] = None, out=None,
                          stream=None) -> torch.Tensor:
-    """denoise_bm3d whose workspace is the library's own fixed device array, for
-    callers that may not allocate device memory.  Calls on one device share that
-    array: do not let them overlap.  (This wrapper still allocates `out` with
-    torch when it is not given.)"""
+    """denoise_bm3d whose workspace is the library's own fixed device array
+    (noalloc_scratch_bytes() bytes), for callers that may not allocate device
+    memory.  Calls on one device share that array: do not let them overlap.
+    (This wrapper still allocates `out` with torch when it is not given.)"""
     _need(noisy, "noisy", dim=4)
     B, C, H, W = noisy.shape
     p = params or default_bm3d_params()

@@ -41,6 +41,21 @@ class Conv3x3Fn(torch.autograd.Function):
         return gx, gw, gb, None
 
 
+class ResidualOutFn(torch.autograd.Function):
+    """out = pre + 255 r (Eq. 2) by the library's dn_cnn_residual_out; the
+    gradient reaching r, 255 g, is the same kernel applied to (0, g)."""
+
+    @staticmethod
+    def forward(ctx, pre, r):
+        return api.cnn_residual_out(pre, r)
+
+    @staticmethod
+    def backward(ctx, g):
+        g = g.contiguous()
+        gr = api.cnn_residual_out(torch.zeros_like(g), g) if ctx.needs_input_grad[1] else None
+        return g, gr
+
+
 class ResidualNet(torch.nn.Module):
     """K 3x3 conv layers, `width` channels, 2 inputs (pre/255, noisy/255), 1 output."""
 
@@ -89,7 +104,7 @@ class ResidualNet(torch.nn.Module):
         h = z
         for l, (w, b) in enumerate(self.params()):
             h = Conv3x3Fn.apply(h, w, b, l < self.layers - 1)
-        return pre + 255.0 * h[:, 0]
+        return ResidualOutFn.apply(pre.contiguous(), h[:, 0].contiguous())
 
     @torch.no_grad()
     def train_step(self, noisy, pre, clean, lr=1e-3, sync=True):

@@ -67,6 +67,17 @@ bool valid_cnn(const dn_cnn *c)
 // Colour planes the network takes and produces (1: grey network).
 int cnn_cc(const dn_cnn *c) { return c->channels == 3 ? 3 : 1; }
 
+// The high-noise first pass (prethresholded patches) stages a window as wide
+// as the CTA's union of search windows in shared memory; wide windows with
+// large steps do not fit.  Checked on the host before any launch.
+bool prethresh_fits(int B, int W, const float *sigma, const dn_bm3d_params *p)
+{
+    if (p->sigma_regime != 0 || !(p->hard.lambda2d > 0.0f)) return true;
+    for (int b = 0; b < B; ++b)
+        if (sigma[b] > 40.0f) return match_pre_smem_bytes(W, p->hard) <= 200 * 1024;
+    return true;
+}
+
 float tau_for(const dn_bm3d_pass &p, float sigma, int regime)
 {
     return (regime == 0 && sigma > 40.0f) ? p.tau_high : p.tau;
@@ -392,6 +403,7 @@ dn_status denoise_bm3d(const float *noisy, float *out, int B, int C, int H, int 
     DN_GUARD_BEGIN
     if (!noisy || !out || !valid_image(B, C, H, W, 8) || !valid_sigmas(sigma, B) || !valid_bm3d(p))
         return DN_EINVAL;
+    if (!prethresh_fits(B, W, sigma, p)) return DN_EUNSUPPORTED;
     Bm3dWs w = bm3d_layout(workspace, B, C, H, W, p);
     if (!workspace || ws_bytes < w.bytes) return DN_ENOMEM;
     return run_bm3d(noisy, out, B, C, H, W, sigma, p, w, (cudaStream_t)stream);
@@ -419,6 +431,7 @@ dn_status denoise_hybrid(const float *noisy, float *out, int B, int C, int H, in
         return DN_EINVAL;
     if (prefilter == DN_PREFILTER_BM3D) {
         if (!valid_bm3d(static_cast<const dn_bm3d_params *>(pp))) return DN_EINVAL;
+        if (!prethresh_fits(B, W, sigma, static_cast<const dn_bm3d_params *>(pp))) return DN_EUNSUPPORTED;
     } else if (prefilter == DN_PREFILTER_NLM) {
         if (!valid_nlm(static_cast<const dn_nlm_params *>(pp))) return DN_EINVAL;
     } else {

@@ -176,17 +176,11 @@ static __device__ int g_dn_error;
 
 int *device_error_ptr()
 {
-    static thread_local int cached_dev = -1;
-    static thread_local int *cached_ptr = nullptr;
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
-    if (dev != cached_dev) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_dn_error) != cudaSuccess) return nullptr;
-        cached_dev = dev;
-        cached_ptr = static_cast<int *>(p);
-    }
-    return cached_ptr;
+    // looked up in the current context on every call: a cached address would go
+    // stale after a device reset
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_dn_error) != cudaSuccess) return nullptr;
+    return static_cast<int *>(p);
 }
 
 // ---- kernel timing ---------------------------------------------------------------

@@ -8,38 +8,30 @@
 // device memory that is part of the library itself: it is reserved when the
 // library's device code is loaded on a GPU and stays reserved until the
 // process exits.
-#include <mutex>
-
 #include "common.cuh"
 
 // The scratch array.  In host code its name is only a host-side stand-in; the
-// device address is looked up once per device with cudaGetSymbolAddress.
+// device address is looked up on every call with cudaGetSymbolAddress (a host
+// lookup in the current context, so a device reset or a new primary context
+// never leaves a stale address behind).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[DN_NOALLOC_SCRATCH_BYTES];
 
 namespace {
 
-constexpr int kMaxDevices = 128;
-std::mutex g_mutex;
-void *g_scratch_addr[kMaxDevices];
-
-// Device address of the scratch array on the current device (looked up on the
-// first call per device).
+// Device address of the scratch array in the current context.  Under lazy
+// module loading the first lookup on a device loads the library's device code
+// there, which is when the array is reserved.
 dn_status scratch_for_current_device(void **out)
 {
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess) return DN_ECUDA;
-    if (dev < 0 || dev >= kMaxDevices) return DN_EUNSUPPORTED;
-    std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_scratch_addr[dev]) {
-        void *ptr = nullptr;
-        if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || ptr == nullptr) return DN_ECUDA;
-        g_scratch_addr[dev] = ptr;
-    }
-    *out = g_scratch_addr[dev];
+    void *ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || ptr == nullptr) return DN_ECUDA;
+    *out = ptr;
     return DN_OK;
 }
 
 }  // namespace
+
+extern "C" size_t dn_noalloc_scratch_bytes(void) { return (size_t)DN_NOALLOC_SCRATCH_BYTES; }
 
 extern "C" dn_status denoise_bm3d_noalloc(const float *noisy, float *out, int B, int C, int H, int W,
                                           const float *sigma, const dn_bm3d_params *p, dn_stream_t stream)

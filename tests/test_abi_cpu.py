@@ -142,3 +142,32 @@ def test_strerror(lib):
     for s in (0, -1, -2, -3, -4, -5):
         assert lib.dn_strerror(s)
     assert b"workspace" in lib.dn_strerror(L.DN_ENOMEM)
+
+
+def test_noalloc_scratch_size_matches_header(lib):
+    """The size the library reports for its fixed no-allocation array is the
+    one include/denoise.h defines (read from the header text)."""
+    import os
+    import re
+    hdr = open(os.path.join(os.path.dirname(L.LIB_PATH), "..", "include", "denoise.h")).read()
+    m = re.search(r"#define\s+DN_NOALLOC_SCRATCH_BYTES\s+\((\d+)u\s*<<\s*(\d+)\)", hdr)
+    assert m, "DN_NOALLOC_SCRATCH_BYTES not found in the header"
+    assert lib.dn_noalloc_scratch_bytes() == int(m.group(1)) << int(m.group(2))
+
+
+def test_high_noise_first_pass_window_limit_is_checked_before_launch(lib):
+    """A sigma > 40 image whose prethresholded first pass would stage more than
+    200 KB of window (step 12, search 21, 512 wide) is refused with
+    DN_EUNSUPPORTED on the host.  With sigma_regime 1 or lambda2d = 0 the first
+    pass matches raw pixels, so only the workspace check remains (a 0-byte
+    workspace fails it)."""
+    p = L.default_bm3d_params()
+    p.hard.step = 12
+    p.hard.search = 21
+    assert _call_bm3d(lib, H=64, W=512, sigma=50.0, p=p) == L.DN_EUNSUPPORTED
+    p.sigma_regime = 1
+    p2 = L.default_bm3d_params()
+    p2.hard.step, p2.hard.search = 12, 21
+    p2.hard.lambda2d = 0.0
+    assert _call_bm3d(lib, H=64, W=512, sigma=50.0, p=p, ws_bytes=0) == L.DN_ENOMEM
+    assert _call_bm3d(lib, H=64, W=512, sigma=50.0, p=p2, ws_bytes=0) == L.DN_ENOMEM

@@ -44,3 +44,25 @@ def test_table_matches_top_level_object(bench):
         assert table[k]["bound"] == bound and table[k]["unit"] == unit
         assert table[k]["achieved"] == pytest.approx(ach, rel=1e-3)
         assert table[k]["frac"] == pytest.approx(ach / peak, abs=1e-4)
+
+
+def test_filter_counts_per_pixel(bench):
+    """The dense-contraction counts of the two filtering passes per pixel of a
+    1024 x 1024 image (full groups): 36 kFLOP (pass 1: 2D DCT forward and back
+    as 64 x 64 products, 16 x 16 Walsh-Hadamard both ways) and 130 kFLOP
+    (pass 2: three of each with 32-patch groups)."""
+    px = 1024 * 1024
+    t1, a1 = bench.filter_work(False, 1024, 1024, 1)
+    t2, a2 = bench.filter_work(True, 1024, 1024, 1)
+    assert t1 / px == pytest.approx(36.1e3, rel=0.01)
+    assert t2 / px == pytest.approx(130.0e3, rel=0.01)
+    # the separable form does about a quarter of the 2D-transform work
+    assert 0.15 < a1 / t1 < 0.4 and 0.15 < a2 / t2 < 0.4
+
+
+def test_fp32_peak_from_device_numbers(bench):
+    hw = {"sm_count": 152, "sm_mhz": 2070.0, "source": "test"}
+    assert bench.fp32_peak(hw) == pytest.approx(80.56, rel=1e-3)
+    hw2 = dict(hw, sm_count=144, sm_mhz=1900.0)
+    b, u, w, peak, note = bench.algorithmic("bm3d_match_fp32", 2, 2, hw2)
+    assert peak == pytest.approx(144 * 128 * 2 * 1.9e9 / 1e12) and "144 SM" in note

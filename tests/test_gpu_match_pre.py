@@ -97,6 +97,21 @@ def test_match_pre_other_steps_and_zero_threshold(oracle, step, search, thr):
     check_pre(oracle, host(idx)[0], host(n)[0], om, noisy[0, 0], 2500.0, thr)
 
 
+def test_match_pre_wide_window_direct_row_loads(oracle):
+    """A step and window wide enough (step 6, search 77: 270 staged pixels per
+    row, more than the 256 the CTA prefetches) that the kernel loads each new
+    pixel row directly; the image is 300 pixels wide so the staged row is not
+    clipped."""
+    A = api()
+    _, noisy = synth.make_batch([48], 40, 300, 50.0)
+    p = A.default_bm3d_params().hard
+    p.step, p.search = 6, 77
+    idx, n = A.bm3d_match_prethresh(dev(noisy[:, 0]), [5000.0], [100.0], p)
+    om = oracle.match_pre(noisy[0, 0], oracle.Pass(step=6, search=77, n2=16, tau=5000.0), 100.0)
+    t, f = check_pre(oracle, host(idx)[0], host(n)[0], om, noisy[0, 0], 5000.0, 100.0)
+    assert f <= 0.6 * t + 1, (f, t)
+
+
 def test_match_pre_repeated_tile_exact(oracle):
     """Exact duplicates of the reference get distance 0 (same transform
     arithmetic for reference and candidates), so lists on a periodic image

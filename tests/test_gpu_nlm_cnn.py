@@ -165,8 +165,10 @@ def test_conv3x3_tc_bf16_parity(oracle, N, H, W, relu, C):
 
 def test_conv3x3_tc_bf16_more_work_items_than_ctas():
     """Persistent tcgen05 conv with more (image, strip, 32-row chunk) items than
-    resident CTAs (500 items: ragged last strip and chunk), against a plain
-    PyTorch FP32 conv of the same BF16-rounded operands."""
+    resident CTAs (500 items: ragged last strip and chunk), against an FP64
+    convolution of the same BF16-rounded operands (FP64 on the GPU: cuDNN's
+    FP32 convolutions may run in TF32, narrower than the kernel's FP32
+    accumulation)."""
     import torch
     A = api()
     N, H, W = 10, 300, 520
@@ -175,8 +177,9 @@ def test_conv3x3_tc_bf16_more_work_items_than_ctas():
     w = (torch.randn(32, 3, 3, 32, device="cuda", generator=g) * (2.0 / 288) ** 0.5).to(torch.bfloat16).float()
     b = torch.randn(32, device="cuda", generator=g) * 0.1
     y = A.conv3x3_tc_fwd(x, w.contiguous(), b, relu=True)
-    ref = torch.relu(torch.nn.functional.conv2d(x.float().permute(0, 3, 1, 2), w.permute(0, 3, 1, 2), b, padding=1))
-    got = y.float().permute(0, 3, 1, 2)
+    ref = torch.relu(torch.nn.functional.conv2d(x.double().permute(0, 3, 1, 2), w.double().permute(0, 3, 1, 2),
+                                                b.double(), padding=1))
+    got = y.double().permute(0, 3, 1, 2)
     scale = ref.abs().max()
     assert bool(((got - ref).abs() <= 2 ** -7 * ref.abs() + 1e-3 * scale).all())
     assert A.device_error() == 0
@@ -184,7 +187,8 @@ def test_conv3x3_tc_bf16_more_work_items_than_ctas():
 
 def test_conv3x3_tc64_bf16_more_work_items_than_ctas():
     """64-channel tcgen05 layer (one CTA per SM) with 5 x 3 x 10 = 150 work
-    items over 152 CTAs plus ragged strips/chunks, against PyTorch FP32."""
+    items over 152 CTAs plus ragged strips/chunks, against an FP64 convolution
+    on the GPU."""
     import torch
     A = api()
     N, H, W = 5, 300, 300
@@ -193,8 +197,9 @@ def test_conv3x3_tc64_bf16_more_work_items_than_ctas():
     w = (torch.randn(64, 3, 3, 64, device="cuda", generator=g) * (2.0 / 576) ** 0.5).to(torch.bfloat16).float()
     b = torch.randn(64, device="cuda", generator=g) * 0.1
     y = A.conv3x3_tc_fwd(x, w.contiguous(), b, relu=False)
-    ref = torch.nn.functional.conv2d(x.float().permute(0, 3, 1, 2), w.permute(0, 3, 1, 2), b, padding=1)
-    got = y.float().permute(0, 3, 1, 2)
+    ref = torch.nn.functional.conv2d(x.double().permute(0, 3, 1, 2), w.double().permute(0, 3, 1, 2), b.double(),
+                                     padding=1)
+    got = y.double().permute(0, 3, 1, 2)
     scale = ref.abs().max()
     assert bool(((got - ref).abs() <= 2 ** -7 * ref.abs() + 1e-3 * scale).all())
     assert A.device_error() == 0
