@@ -56,8 +56,10 @@ typedef enum {
  *                  accumulation; patches centred on their FP32 mean first,
  *                  which stays in FP32); group transform, shrinkage and
  *                  aggregation in FP32;
- *   DN_BF16_MATCH  block matching with the BF16 tensor-core prefilter and an
- *                  exact FP32 re-rank (match lists identical to FP32).
+ *   DN_BF16_MATCH  block matching with the tensor-core prefilter (distance
+ *                  cross terms as FP16 GEMMs with FP32 accumulation, a proven
+ *                  error bound per pair) and an exact FP32 re-rank: match
+ *                  lists identical to FP32.
  * For the CNN (dn_cnn.precision) DN_BF16 selects the tcgen05 BF16 layers. */
 typedef enum { DN_FP32 = 0, DN_BF16 = 1, DN_BF16_MATCH = 2 } dn_precision;
 typedef enum { DN_PREFILTER_BM3D = 0, DN_PREFILTER_NLM = 1 } dn_prefilter;
@@ -197,7 +199,7 @@ dn_status denoise_bm3d_noalloc(const float *noisy, float *out, int B, int C, int
  *      order; -1 past the kept count.
  * n:   device int32 [B][Ry][Rx]: group size min(n2, 2^floor(log2 #kept)).
  * precision: DN_FP32 (exhaustive FP32), or DN_BF16_MATCH (DN_BF16 is taken
- * as the same): BF16 tensor-core prefilter with a proven margin, survivors
+ * as the same): tensor-core prefilter with a proven margin, survivors
  * re-ranked exactly in FP32, so the lists equal the FP32 ones. */
 dn_status dn_bm3d_match(const float *guide, size_t plane_stride, int B, int H, int W, const dn_bm3d_pass *p,
                         const float *tau, int precision, int *idx, int *n, void *workspace, size_t ws_bytes,
@@ -217,16 +219,17 @@ dn_status dn_bm3d_match_prethresh(const float *guide, size_t plane_stride, int B
                                   const dn_bm3d_pass *p, const float *tau, const float *thr, int *idx, int *n,
                                   dn_stream_t stream);
 
-/* Test surface of the BF16 tensor-core matching prefilter: runs dn_bm3d_match
- * (DN_BF16) on one image and additionally writes the raw FP32 cross terms
- * sum_k bf16(P_c)[k] bf16(Q_c)[k] (centred patches) of reference tile
- * (tile_x, tile_y) (8 x 16 grid positions) to cross, device float
- * [128][nchunks][256]: reference t = (ty * 8 + tx) of the tile against the
- * candidate slot (row, col) = (4 c + s / 64, s % 64) of the tile's candidate
- * region, whose origin is (max(0, y_first - search/2), max(0, x_first -
- * search/2)) with (y_first, x_first) the tile's first grid position;
- * nchunks = ceil(region rows / 4).  idx/n as in dn_bm3d_match; workspace as
- * dn_bm3d_match_workspace_bytes(1, H, W, p, DN_BF16). */
+/* Test surface of the tensor-core matching prefilter: runs dn_bm3d_match
+ * (DN_BF16_MATCH) on one image and additionally writes, for the reference tile
+ * (tile_x, tile_y) (8 x 16 grid positions), cross[0] = m, the constant the
+ * tile's pixels are centred on, then the raw FP32 tensor-core results
+ * sum_k f16(P - m)[k] f16(Q - m)[k] at cross[1 + (t * nchunks + c) * 128 + j]:
+ * reference t = (ty * 8 + tx) of the tile against the candidate at row
+ * 2 c + j / 64, column j % 64 of the tile's candidate region, whose origin is
+ * (max(0, y_first - search/2), max(0, x_first - search/2)) with
+ * (y_first, x_first) the tile's first grid position; nchunks = ceil(region
+ * rows / 2).  idx/n as in dn_bm3d_match; workspace as
+ * dn_bm3d_match_workspace_bytes(1, H, W, p, DN_BF16_MATCH). */
 dn_status dn_bm3d_match_cross_terms(const float *guide, int H, int W, const dn_bm3d_pass *p, float tau, int tile_x,
                                     int tile_y, float *cross, int *idx, int *n, void *workspace, size_t ws_bytes,
                                     dn_stream_t stream);

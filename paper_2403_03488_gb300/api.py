@@ -199,7 +199,9 @@ def bm3d_match_prethresh(guide: torch.Tensor, tau, thr, p: BM3DPass, stream=None
 
 def bm3d_match_cross_terms(guide: torch.Tensor, p: BM3DPass, tau: float, tile_x: int, tile_y: int, stream=None):
     """Raw tensor-core cross terms of one 8 x 16 reference tile (test surface):
-    returns (cross [128, nchunks, 256], (cy0, cx0) candidate-region origin)."""
+    returns (cross [128, nchunks, 128], m, (cy0, cx0)): reference t of the tile
+    against candidate (cy0 + 2 c + j // 64, cx0 + j % 64) at cross[t, c, j], the
+    dot product of the FP16-rounded patches centred on the tile's constant m."""
     _need(guide, "guide", dim=2)
     H, W = guide.shape
     hs = p.search // 2
@@ -207,15 +209,15 @@ def bm3d_match_cross_terms(guide: torch.Tensor, p: BM3DPass, tau: float, tile_x:
     y_first, x_first = gy[tile_y * 16], gx[tile_x * 8]
     y_last = gy[min(tile_y * 16 + 15, len(gy) - 1)]
     cy0, cy1 = max(0, y_first - hs), min(H - 8, y_last + hs)
-    nchunks = (cy1 - cy0 + 1 + 3) // 4
-    cross = torch.zeros((128, nchunks, 256), dtype=torch.float32, device=guide.device)
+    nchunks = (cy1 - cy0 + 1 + 1) // 2
+    buf = torch.zeros(1 + 128 * nchunks * 128, dtype=torch.float32, device=guide.device)
     idx = torch.empty((len(gy), len(gx), p.n2), dtype=torch.int32, device=guide.device)
     n = torch.empty((len(gy), len(gx)), dtype=torch.int32, device=guide.device)
     ws, nb = _ws(int(L.lib().dn_bm3d_match_workspace_bytes(1, H, W, ctypes.byref(p), DN_BF16)), guide.device, None)
     check(L.lib().dn_bm3d_match_cross_terms(_vp(guide), H, W, ctypes.byref(p), float(tau), tile_x, tile_y,
-                                            _vp(cross), _vp(idx), _vp(n), _vp(ws), nb, _stream(stream)),
+                                            _vp(buf), _vp(idx), _vp(n), _vp(ws), nb, _stream(stream)),
           "dn_bm3d_match_cross_terms")
-    return cross, (cy0, max(0, x_first - hs))
+    return buf[1:].view(128, nchunks, 128), buf[:1], (cy0, max(0, x_first - hs))
 
 
 def _filter(wiener, img, basic, idx, n, sigma_c, p, precision, stream):

@@ -164,10 +164,7 @@ CnnWs cnn_layout(void *base, int N, int H, int W, const dn_cnn *c)
 // Block matching in the requested precision: with DN_BF16_MATCH the BF16
 // tensor-core prefilter with exact FP32 re-rank (same result as FP32) when its
 // tiling supports the parameters, the exhaustive FP32 kernel otherwise.
-bool tc_match_supported(const dn_bm3d_pass &p)
-{
-    return p.n2 >= 2 && 7 * p.step + 2 * (p.search / 2) + 1 <= 64 && match_tc_smem_bytes(p.step, p.search) <= 200 * 1024;
-}
+bool tc_match_supported(const dn_bm3d_pass &p) { return match_tc_supported(p); }
 
 dn_status match_any(const float *guide, size_t plane, int B, int H, int W, const dn_bm3d_pass &p, const float *tau,
                     int precision, int *idx, int *n, int *mws, cudaStream_t s)

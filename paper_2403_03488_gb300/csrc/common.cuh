@@ -115,6 +115,9 @@ dn_status l1_grad(const float *r, const float *pre, const float *clean, float *d
                   cudaStream_t s);
 int *device_error_ptr();
 size_t match_tc_smem_bytes(int step, int search);
+// Whether the tensor-core matcher's tiling (64 candidate columns per CTA, its
+// shared memory) supports the pass parameters.
+bool match_tc_supported(const dn_bm3d_pass &p);
 // fb_ws: device workspace of match_tc_workspace_bytes (deferred references)
 size_t match_tc_workspace_bytes(int B, int H, int W, const dn_bm3d_pass &p);
 dn_status match_tc(const float *guide, size_t plane, int B, int H, int W, const dn_bm3d_pass &p, const float *tau,
