@@ -161,6 +161,34 @@ dn_status denoise_hybrid(const float *noisy, float *out, int B, int C, int H, in
 
 const char *dn_strerror(dn_status s);
 
+/* ---- one large image in tiles with a halo ---------------------------------
+ * A BM3D output pixel depends only on the noisy pixels within a fixed
+ * distance (per axis) of it: a pass-1 estimate at p comes from the groups
+ * whose reference lies within search/2 + 7 of p, and each group's matching
+ * and filtering read pixels within another search/2 + 7 of its reference;
+ * the second pass does the same on the basic estimate.  So a tile extended by
+ * that radius on every side (clipped at the image border), with its origin on
+ * both passes' reference grids, yields exactly the whole-image result inside
+ * its interior: every kernel here is deterministic and the aggregation sums
+ * are exact, so the tiled result equals denoise_bm3d bit for bit.  This bounds
+ * the workspace of very large images (and shards one image across devices,
+ * each processing its tiles). */
+
+/* The radius: (2 (hard.search / 2) + 7) + (2 (wiener.search / 2) + 7),
+ * 90 for the defaults; -1 for invalid parameters. */
+int dn_bm3d_halo(const dn_bm3d_params *p);
+
+/* Workspace of denoise_bm3d_tiled (0 for invalid arguments). */
+size_t dn_bm3d_tiled_workspace_bytes(int C, int H, int W, const dn_bm3d_params *p, int tile, int max_batch);
+
+/* BM3D of ONE image noisy/out: device [C][H][W], in tiles whose interiors
+ * are tile x tile pixels (rounded up to a multiple of both grid steps),
+ * each extended by the halo (rounded likewise); tiles of equal extent run
+ * together, up to max_batch per launch.  Same result as denoise_bm3d. */
+dn_status denoise_bm3d_tiled(const float *noisy, float *out, int C, int H, int W, float sigma,
+                             const dn_bm3d_params *p, int tile, int max_batch, void *workspace, size_t ws_bytes,
+                             dn_stream_t stream);
+
 /* BM3D without any device allocation, for callers that may not allocate
  * device memory themselves (for example a plug-in inside an application that
  * owns the whole device-memory budget, or a latency-critical loop that cannot

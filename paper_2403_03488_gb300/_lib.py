@@ -77,6 +77,9 @@ def lib():
         "dn_strerror": (ctypes.c_char_p, [i]),
         "denoise_bm3d_noalloc": (i, [vp, vp, i, i, i, i, fp, P(BM3DParams), vp]),
         "dn_noalloc_scratch_bytes": (sz, []),
+        "dn_bm3d_halo": (i, [P(BM3DParams)]),
+        "dn_bm3d_tiled_workspace_bytes": (sz, [i, i, i, P(BM3DParams), i, i]),
+        "denoise_bm3d_tiled": (i, [vp, vp, i, i, i, f, P(BM3DParams), i, i, vp, sz, vp]),
         "dn_bm3d_match": (i, [vp, sz, i, i, i, P(BM3DPass), fp, i, vp, vp, vp, sz, vp]),
         "dn_bm3d_match_workspace_bytes": (sz, [i, i, i, P(BM3DPass), i]),
         "dn_bm3d_match_prethresh": (i, [vp, sz, i, i, i, P(BM3DPass), fp, fp, vp, vp, vp]),

@@ -18,7 +18,8 @@ from ._lib import (BM3DParams, BM3DPass, CNN, DN_BF16, DN_BF16_MATCH, DN_FP32, D
 __all__ = ["denoise_bm3d", "denoise_nlm", "denoise_hybrid", "bm3d_match", "bm3d_filter_hard", "bm3d_filter_wiener",
            "rgb_to_ycc", "ycc_to_rgb", "error_reduce", "conv3x3_fwd", "conv3x3_bwd_data", "conv3x3_bwd_weight",
            "cnn_forward", "l1_residual_grad", "adam_step", "grid", "default_bm3d_params", "default_nlm_params",
-           "cnn_param_count", "profile", "DN_FP32", "DN_BF16", "DN_BF16_MATCH", "DN_PREFILTER_BM3D", "DN_PREFILTER_NLM"]
+           "cnn_param_count", "profile", "bm3d_halo", "denoise_bm3d_tiled", "DN_FP32", "DN_BF16", "DN_BF16_MATCH",
+           "DN_PREFILTER_BM3D", "DN_PREFILTER_NLM"]
 
 
 def _vp(t: Optional[torch.Tensor]):
@@ -109,6 +110,27 @@ def denoise_bm3d_noalloc(noisy: torch.Tensor, sigma, params: Optional[BM3DParams
     _need(out, "out", dim=4)
     check(L.lib().denoise_bm3d_noalloc(_vp(noisy), _vp(out), B, C, H, W, _sigmas(sigma, B), ctypes.byref(p),
                                        _stream(stream)), "denoise_bm3d_noalloc")
+    return out
+
+
+def bm3d_halo(params: Optional[BM3DParams] = None) -> int:
+    """Pixels (per axis) an output pixel of BM3D depends on: the halo of a tile."""
+    return int(L.lib().dn_bm3d_halo(ctypes.byref(params or default_bm3d_params())))
+
+
+def denoise_bm3d_tiled(noisy: torch.Tensor, sigma: float, params: Optional[BM3DParams] = None, tile: int = 512,
+                       max_batch: int = 4, out=None, workspace=None, stream=None) -> torch.Tensor:
+    """BM3D of one [C, H, W] image in tiles of tile x tile pixels plus the halo
+    (bit-identical to denoise_bm3d on the whole image)."""
+    _need(noisy, "noisy", dim=3)
+    C, H, W = noisy.shape
+    p = params or default_bm3d_params()
+    out = torch.empty_like(noisy) if out is None else out
+    _need(out, "out", dim=3)
+    nbytes = int(L.lib().dn_bm3d_tiled_workspace_bytes(C, H, W, ctypes.byref(p), tile, max_batch))
+    ws, nb = _ws(nbytes, noisy.device, workspace)
+    check(L.lib().denoise_bm3d_tiled(_vp(noisy), _vp(out), C, H, W, float(sigma), ctypes.byref(p), tile, max_batch,
+                                     _vp(ws), nb, _stream(stream)), "denoise_bm3d_tiled")
     return out
 
 

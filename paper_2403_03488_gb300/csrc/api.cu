@@ -453,6 +453,146 @@ dn_status denoise_hybrid(const float *noisy, float *out, int B, int C, int H, in
     DN_GUARD_END
 }
 
+// ---- one image in tiles with a halo -------------------------------------------------
+
+int dn_bm3d_halo(const dn_bm3d_params *p)
+{
+    if (!valid_bm3d(p)) return -1;
+    return (2 * (p->hard.search / 2) + 7) + (2 * (p->wiener.search / 2) + 7);
+}
+
+namespace {
+
+int gcd_int(int a, int b) { return b == 0 ? a : gcd_int(b, a % b); }
+
+struct TilePlan {
+    int T, hr, ny, nx;  // interior side, halo (both multiples of the grid steps' lcm), tile counts
+    int rh_max, rw_max;
+};
+
+bool tile_plan(int H, int W, const dn_bm3d_params *p, int tile, TilePlan *tp)
+{
+    const int s1 = p->hard.step, s2 = p->wiener.step;
+    const int g = s1 / gcd_int(s1, s2) * s2;  // tile origins on both reference grids
+    if (tile < 8 || g > 4096) return false;
+    const int R = dn_bm3d_halo(p);
+    tp->T = (tile + g - 1) / g * g;
+    tp->hr = (R + g - 1) / g * g;
+    tp->ny = (H + tp->T - 1) / tp->T;
+    tp->nx = (W + tp->T - 1) / tp->T;
+    tp->rh_max = H < tp->T + 2 * tp->hr ? H : tp->T + 2 * tp->hr;
+    tp->rw_max = W < tp->T + 2 * tp->hr ? W : tp->T + 2 * tp->hr;
+    return true;
+}
+
+// Region [y0, y1) x [x0, x1) of tile (i, j) and its interior offset.
+void tile_region(const TilePlan &tp, int H, int W, int i, int j, int *y0, int *y1, int *x0, int *x1)
+{
+    const int iy0 = i * tp.T, ix0 = j * tp.T;
+    const int iy1 = iy0 + tp.T < H ? iy0 + tp.T : H, ix1 = ix0 + tp.T < W ? ix0 + tp.T : W;
+    *y0 = iy0 - tp.hr > 0 ? iy0 - tp.hr : 0;
+    *x0 = ix0 - tp.hr > 0 ? ix0 - tp.hr : 0;
+    *y1 = iy1 + tp.hr < H ? iy1 + tp.hr : H;
+    *x1 = ix1 + tp.hr < W ? ix1 + tp.hr : W;
+}
+
+struct TiledWs {
+    float *in, *out;
+    void *rest;
+    size_t rest_bytes, bytes;
+};
+
+TiledWs tiled_layout(void *base, int C, const TilePlan &tp, const dn_bm3d_params *p, int max_batch)
+{
+    Carver cv(base);
+    TiledWs w;
+    const size_t n = (size_t)max_batch * C * tp.rh_max * tp.rw_max;
+    w.in = cv.take<float>(n);
+    w.out = cv.take<float>(n);
+    w.rest_bytes = bm3d_layout(nullptr, max_batch, C, tp.rh_max, tp.rw_max, p).bytes;
+    w.rest = cv.take<char>(w.rest_bytes);
+    w.bytes = cv.off;
+    return w;
+}
+
+}  // namespace
+
+size_t dn_bm3d_tiled_workspace_bytes(int C, int H, int W, const dn_bm3d_params *p, int tile, int max_batch)
+{
+    TilePlan tp;
+    if (!valid_image(1, C, H, W, 8) || !valid_bm3d(p) || max_batch < 1 || !tile_plan(H, W, p, tile, &tp)) return 0;
+    return tiled_layout(nullptr, C, tp, p, max_batch).bytes;
+}
+
+dn_status denoise_bm3d_tiled(const float *noisy, float *out, int C, int H, int W, float sigma, const dn_bm3d_params *p,
+                             int tile, int max_batch, void *workspace, size_t ws_bytes, dn_stream_t stream)
+{
+    DN_GUARD_BEGIN
+    TilePlan tp;
+    if (!noisy || !out || !valid_image(1, C, H, W, 8) || !valid_sigmas(&sigma, 1) || !valid_bm3d(p) ||
+        max_batch < 1 || max_batch > 1024 || !tile_plan(H, W, p, tile, &tp))
+        return DN_EINVAL;
+    if (!prethresh_fits(1, tp.rw_max, &sigma, p)) return DN_EUNSUPPORTED;
+    TiledWs w = tiled_layout(workspace, C, tp, p, max_batch);
+    if (!workspace || ws_bytes < w.bytes) return DN_ENOMEM;
+    cudaStream_t s = (cudaStream_t)stream;
+    // tiles grouped by region size (interior, edge and corner tiles differ), up to max_batch per launch
+    struct T { int y0, y1, x0, x1, iy0, iy1, ix0, ix1; };
+    const int ntiles = tp.ny * tp.nx;
+    T *tl = new T[ntiles];
+    for (int i = 0; i < tp.ny; ++i)
+        for (int j = 0; j < tp.nx; ++j) {
+            T &t = tl[i * tp.nx + j];
+            tile_region(tp, H, W, i, j, &t.y0, &t.y1, &t.x0, &t.x1);
+            t.iy0 = i * tp.T;
+            t.ix0 = j * tp.T;
+            t.iy1 = t.iy0 + tp.T < H ? t.iy0 + tp.T : H;
+            t.ix1 = t.ix0 + tp.T < W ? t.ix0 + tp.T : W;
+        }
+    bool *done = new bool[ntiles]();
+    float sig[1024];
+    for (int i = 0; i < 1024; ++i) sig[i] = sigma;
+    int *batch = new int[max_batch];
+    dn_status st = DN_OK;
+    const size_t HW = (size_t)H * W;
+    for (int a = 0; a < ntiles && st == DN_OK; ++a) {
+        if (done[a]) continue;
+        const int rh = tl[a].y1 - tl[a].y0, rw = tl[a].x1 - tl[a].x0;
+        int nb = 0;
+        for (int b = a; b < ntiles && nb < max_batch; ++b)
+            if (!done[b] && tl[b].y1 - tl[b].y0 == rh && tl[b].x1 - tl[b].x0 == rw) {
+                batch[nb++] = b;
+                done[b] = true;
+            }
+        const size_t plane = (size_t)rh * rw;
+        for (int k = 0; k < nb && st == DN_OK; ++k) {
+            const T &t = tl[batch[k]];
+            for (int c = 0; c < C; ++c)
+                if (cudaMemcpy2DAsync(w.in + ((size_t)k * C + c) * plane, (size_t)rw * sizeof(float),
+                                      noisy + (size_t)c * HW + (size_t)t.y0 * W + t.x0, (size_t)W * sizeof(float),
+                                      (size_t)rw * sizeof(float), rh, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+                    st = DN_ECUDA;
+        }
+        if (st != DN_OK) break;
+        st = run_bm3d(w.in, w.out, nb, C, rh, rw, sig, p, bm3d_layout(w.rest, nb, C, rh, rw, p), s);
+        for (int k = 0; k < nb && st == DN_OK; ++k) {
+            const T &t = tl[batch[k]];
+            const int oy = t.iy0 - t.y0, ox = t.ix0 - t.x0, ih = t.iy1 - t.iy0, iw = t.ix1 - t.ix0;
+            for (int c = 0; c < C; ++c)
+                if (cudaMemcpy2DAsync(out + (size_t)c * HW + (size_t)t.iy0 * W + t.ix0, (size_t)W * sizeof(float),
+                                      w.out + ((size_t)k * C + c) * plane + (size_t)oy * rw + ox,
+                                      (size_t)rw * sizeof(float), (size_t)iw * sizeof(float), ih,
+                                      cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+                    st = DN_ECUDA;
+        }
+    }
+    delete[] tl;
+    delete[] done;
+    delete[] batch;
+    return st;
+    DN_GUARD_END
+}
+
 const char *dn_strerror(dn_status st)
 {
     switch (st) {
