@@ -307,6 +307,23 @@ dn_status dn_conv3x3_bwd_data(const float *dy, const float *w, const float *mask
 dn_status dn_conv3x3_bwd_weight(const float *x, const float *dy, float *dw, float *db, int N, int Cin, int Cout,
                                 int H, int W, dn_stream_t stream);
 
+/* Gradient of the L1 loss of Eq. 2 for the grey network of width 32
+ * (cnn->precision DN_BF16, channels 1) with BF16 tensor-core kernels: the
+ * forward keeps every activation (NHWC BF16); dL/dr = 255 sign(out - clean)
+ * / count; the hidden layers' weight gradients are tcgen05 GEMMs over the
+ * pixels (BF16 operands, FP32 accumulation), their data gradients the
+ * transposed convolution on tcgen05 (flipped weights) with the ReLU mask in
+ * its epilogue; the thin first and last layers run on CUDA cores; every sum
+ * over pixels is a fixed-order sum of per-CTA partials (reproducible).
+ * noisy, pre, clean: device [N][H][W]; grad: device FP32 in the layout of
+ * cnn->weights, OVERWRITTEN; loss_sum: device double [1], += sum |out -
+ * clean| (caller zeroes).  The FP32 master weights are cnn->weights.
+ * DN_EUNSUPPORTED for other precisions, widths or colour-native networks
+ * (the FP32 layer entry points below cover those). */
+dn_status dn_cnn_grad(const float *noisy, const float *pre, const float *clean, int N, int H, int W, const dn_cnn *cnn,
+                      float *grad, double *loss_sum, void *workspace, size_t ws_bytes, dn_stream_t stream);
+size_t dn_cnn_grad_workspace_bytes(int N, int H, int W, const dn_cnn *cnn);
+
 /* Full network forward (Eq. 2-3), FP32 or BF16: noisy, pre, out: device
  * [N][cc][H][W] with cc = 3 for a colour-native network (channels = 3), else
  * cc = 1; out = pre + 255 F([pre, noisy]/255).
@@ -322,6 +339,22 @@ size_t dn_cnn_workspace_bytes(int N, int H, int W, const dn_cnn *cnn);
  * BF16.  workspace: device, >= 9 * C * C * 2 bytes (packed weights). */
 dn_status dn_conv3x3_tc_fwd(const void *x, const float *w, const float *b, void *y, int N, int H, int W, int C,
                             int relu, void *workspace, size_t ws_bytes, dn_stream_t stream);
+
+/* Backward of one hidden C -> C layer on the tensor cores (NHWC bf16, as
+ * dn_conv3x3_tc_fwd), the two halves of dn_cnn_grad's hidden-layer step:
+ *   weight: dw [C][3][3][C] = sum_px g[px][co] x[px + tap - 1][ci] and
+ *           db [C] = sum_px g[px][co] (FP32, overwritten; C = 32), a tcgen05
+ *           GEMM over the pixels with BF16 operands and FP32 accumulation;
+ *   data:   dx = conv3x3^T(g, w) (zero padding) on tcgen05 with the weights
+ *           flipped and transposed, rounded to bf16; where mask (NHWC bf16,
+ *           or NULL) is not positive the result is 0 (the ReLU of the layer
+ *           input).  C = 32 or 64.
+ * workspace >= dn_conv3x3_tc_bwd_workspace_bytes(N, H, W, C). */
+size_t dn_conv3x3_tc_bwd_workspace_bytes(int N, int H, int W, int C);
+dn_status dn_conv3x3_tc_bwd_weight(const void *x, const void *g, float *dw, float *db, int N, int H, int W, int C,
+                                   void *workspace, size_t ws_bytes, dn_stream_t stream);
+dn_status dn_conv3x3_tc_bwd_data(const void *g, const float *w, const void *mask, void *dx, int N, int H, int W, int C,
+                                 void *workspace, size_t ws_bytes, dn_stream_t stream);
 
 /* ---- layers of the flexible lightweight network (Sec. III, "Ours-FL") -----
  * A U-Net of depthwise-separable 3x3 convolutions with stride-2 downsampling,

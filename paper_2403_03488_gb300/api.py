@@ -18,7 +18,7 @@ from ._lib import (BM3DParams, BM3DPass, CNN, DN_BF16, DN_BF16_MATCH, DN_FP32, D
 __all__ = ["denoise_bm3d", "denoise_nlm", "denoise_hybrid", "bm3d_match", "bm3d_filter_hard", "bm3d_filter_wiener",
            "rgb_to_ycc", "ycc_to_rgb", "error_reduce", "conv3x3_fwd", "conv3x3_bwd_data", "conv3x3_bwd_weight",
            "cnn_forward", "l1_residual_grad", "adam_step", "grid", "default_bm3d_params", "default_nlm_params",
-           "cnn_param_count", "profile", "bm3d_halo", "denoise_bm3d_tiled", "DN_FP32", "DN_BF16", "DN_BF16_MATCH",
+           "cnn_param_count", "profile", "bm3d_halo", "denoise_bm3d_tiled", "cnn_grad", "DN_FP32", "DN_BF16", "DN_BF16_MATCH",
            "DN_PREFILTER_BM3D", "DN_PREFILTER_NLM"]
 
 
@@ -351,6 +351,51 @@ def cnn_forward(noisy, pre, weights, layers=10, width=32, precision=DN_FP32, str
     check(L.lib().dn_cnn_forward(_vp(noisy), _vp(pre), _vp(out), N, H, W, ctypes.byref(cnn), _vp(ws), nb,
                                  _stream(stream)), "dn_cnn_forward")
     return out
+
+
+def cnn_grad(noisy, pre, clean, weights, layers=10, width=32, grad=None, loss=None, workspace=None, stream=None):
+    """Gradient of the L1 loss of Eq. 2 for the grey network on planes
+    [N, H, W] with the BF16 tensor-core forward and backward kernels.
+    Returns (grad in the layout of weights, loss_sum device double [1])."""
+    _need(noisy, "noisy", dim=3)
+    _need(pre, "pre", dim=3)
+    _need(clean, "clean", dim=3)
+    N, H, W = noisy.shape
+    cnn = make_cnn(weights, layers, width, DN_BF16, 1)
+    grad = torch.empty_like(weights) if grad is None else grad
+    if loss is None:
+        loss = torch.zeros(1, dtype=torch.float64, device=noisy.device)
+    ws, nb = _ws(int(L.lib().dn_cnn_grad_workspace_bytes(N, H, W, ctypes.byref(cnn))), noisy.device, workspace)
+    check(L.lib().dn_cnn_grad(_vp(noisy), _vp(pre), _vp(clean), N, H, W, ctypes.byref(cnn), _vp(grad), _vp(loss),
+                              _vp(ws), nb, _stream(stream)), "dn_cnn_grad")
+    return grad, loss
+
+
+def conv3x3_tc_bwd_weight(x_nhwc, g_nhwc, stream=None):
+    """(dw [C, 3, 3, C], db [C]) of one hidden tensor-core layer (C = 32)."""
+    _need(x_nhwc, "x_nhwc", torch.bfloat16, dim=4)
+    _need(g_nhwc, "g_nhwc", torch.bfloat16, dim=4)
+    N, H, W, C = x_nhwc.shape
+    dw = torch.empty((C, 3, 3, C), dtype=torch.float32, device=x_nhwc.device)
+    db = torch.empty(C, dtype=torch.float32, device=x_nhwc.device)
+    ws, nb = _ws(int(L.lib().dn_conv3x3_tc_bwd_workspace_bytes(N, H, W, C)), x_nhwc.device, None)
+    check(L.lib().dn_conv3x3_tc_bwd_weight(_vp(x_nhwc), _vp(g_nhwc), _vp(dw), _vp(db), N, H, W, C, _vp(ws), nb,
+                                           _stream(stream)), "dn_conv3x3_tc_bwd_weight")
+    return dw, db
+
+
+def conv3x3_tc_bwd_data(g_nhwc, w, mask_nhwc=None, stream=None):
+    """Data gradient (NHWC bf16) of one hidden tensor-core layer with weights
+    w [C, 3, 3, C], zeroed where mask_nhwc (the layer input) is not positive."""
+    _need(g_nhwc, "g_nhwc", torch.bfloat16, dim=4)
+    N, H, W, C = g_nhwc.shape
+    dx = torch.empty_like(g_nhwc)
+    ws, nb = _ws(int(L.lib().dn_conv3x3_tc_bwd_workspace_bytes(N, H, W, 32)) if C == 32 else 9 * C * C * 2,
+                 g_nhwc.device, None)
+    check(L.lib().dn_conv3x3_tc_bwd_data(_vp(g_nhwc), _vp(w.contiguous()), _vp(mask_nhwc) if mask_nhwc is not None
+                                         else None, _vp(dx), N, H, W, C, _vp(ws), nb, _stream(stream)),
+          "dn_conv3x3_tc_bwd_data")
+    return dx
 
 
 def conv3x3_tc_fwd(x_nhwc, w, b, relu=True, stream=None):

@@ -98,6 +98,18 @@ class ResidualNet(torch.nn.Module):
     def last_grads(self):
         return self.params(self.grad_flat)
 
+    def _grad_ws(self, like):
+        """Workspace of dn_cnn_grad for this batch shape, kept between steps."""
+        import ctypes
+        from . import _lib as L
+        N, H, W = like.shape
+        cnn = api.make_cnn(self.flat.data, self.layers, self.width, api.DN_BF16, 1)
+        nbytes = int(L.lib().dn_cnn_grad_workspace_bytes(N, H, W, ctypes.byref(cnn)))
+        ws = getattr(self, "_gws", None)
+        if ws is None or ws.numel() < nbytes or ws.device != like.device:
+            self._gws = torch.empty(nbytes, dtype=torch.uint8, device=like.device)
+        return self._gws
+
     def forward(self, noisy: torch.Tensor, pre: torch.Tensor) -> torch.Tensor:
         """Autograd path: noisy, pre [N, H, W] -> pre + 255 F(z) (Eq. 2-3)."""
         z = api.cnn_pack_input(pre.contiguous(), noisy.contiguous())
@@ -107,11 +119,21 @@ class ResidualNet(torch.nn.Module):
         return ResidualOutFn.apply(pre.contiguous(), h[:, 0].contiguous())
 
     @torch.no_grad()
-    def train_step(self, noisy, pre, clean, lr=1e-3, sync=True):
-        """One explicit L1 + Adam step entirely on the library's kernels.
-        Returns the mean L1 loss (a host float when sync, else a device tensor)."""
+    def train_step(self, noisy, pre, clean, lr=1e-3, sync=True, precision=api.DN_FP32):
+        """One explicit L1 + Adam step entirely on the library's kernels:
+        precision DN_FP32 runs the FP32 CUDA-core layers one by one,
+        DN_BF16 (grey, width 32) the tensor-core forward and backward of
+        dn_cnn_grad with the FP32 master weights.  Returns the mean L1 loss
+        (a host float when sync, else a device tensor)."""
         self._before = self.numpy_params() if sync else None
         noisy, pre, clean = noisy.contiguous(), pre.contiguous(), clean.contiguous()
+        if precision == api.DN_BF16:
+            _, loss = api.cnn_grad(noisy, pre, clean, self.flat.data, self.layers, self.width, grad=self.grad_flat,
+                                   workspace=self._grad_ws(noisy))
+            self.t += 1
+            api.adam_step(self.flat.data, self.grad_flat, self.m, self.v, self.t, lr=lr)
+            count = noisy.numel()
+            return float(loss.item()) / count if sync else loss / count
         z = api.cnn_pack_input(pre, noisy)
         acts = [z]
         prm = self.params()

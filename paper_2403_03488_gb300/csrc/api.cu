@@ -453,6 +453,68 @@ dn_status denoise_hybrid(const float *noisy, float *out, int B, int C, int H, in
     DN_GUARD_END
 }
 
+// ---- training gradient on the tensor cores -------------------------------------------
+
+size_t dn_cnn_grad_workspace_bytes(int N, int H, int W, const dn_cnn *cnn)
+{
+    if (N < 1 || H < 1 || W < 1 || !valid_cnn(cnn) || cnn->precision != DN_BF16 || cnn->width != 32 ||
+        cnn_cc(cnn) != 1)
+        return 0;
+    return cnn_grad_tc_workspace_bytes(N, H, W, cnn->layers);
+}
+
+dn_status dn_cnn_grad(const float *noisy, const float *pre, const float *clean, int N, int H, int W, const dn_cnn *cnn,
+                      float *grad, double *loss_sum, void *workspace, size_t ws_bytes, dn_stream_t stream)
+{
+    DN_GUARD_BEGIN
+    if (!noisy || !pre || !clean || !grad || !loss_sum || N < 1 || H < 1 || W < 1 || !valid_cnn(cnn))
+        return DN_EINVAL;
+    if (cnn->precision != DN_BF16 || cnn->width != 32 || cnn_cc(cnn) != 1) return DN_EUNSUPPORTED;
+    if ((size_t)N * H * W > ((size_t)1 << 31)) return DN_EINVAL;
+    const size_t need = cnn_grad_tc_workspace_bytes(N, H, W, cnn->layers);
+    if (!workspace || ws_bytes < need) return DN_ENOMEM;
+    int *err = device_error_ptr();
+    if (!err) return DN_ECUDA;
+    return cnn_grad_tc(noisy, pre, clean, N, H, W, cnn->layers, cnn->weights, grad, loss_sum, workspace, err,
+                       (cudaStream_t)stream);
+    DN_GUARD_END
+}
+
+size_t dn_conv3x3_tc_bwd_workspace_bytes(int N, int H, int W, int C)
+{
+    if (N < 1 || H < 1 || W < 1 || C != 32) return 0;
+    const size_t a = conv_bwd_w_tc_workspace_bytes(N, H, W), b = wpack_bytes(C);
+    return a > b ? a : b;
+}
+
+dn_status dn_conv3x3_tc_bwd_weight(const void *x, const void *g, float *dw, float *db, int N, int H, int W, int C,
+                                   void *workspace, size_t ws_bytes, dn_stream_t stream)
+{
+    DN_GUARD_BEGIN
+    if (!x || !g || !dw || !db || N < 1 || H < 1 || W < 1) return DN_EINVAL;
+    if (C != 32) return DN_EUNSUPPORTED;
+    if (!workspace || ws_bytes < conv_bwd_w_tc_workspace_bytes(N, H, W)) return DN_ENOMEM;
+    int *err = device_error_ptr();
+    if (!err) return DN_ECUDA;
+    return conv_bwd_w_tc(x, g, dw, db, N, H, W, workspace, err, (cudaStream_t)stream);
+    DN_GUARD_END
+}
+
+dn_status dn_conv3x3_tc_bwd_data(const void *g, const float *w, const void *mask, void *dx, int N, int H, int W, int C,
+                                 void *workspace, size_t ws_bytes, dn_stream_t stream)
+{
+    DN_GUARD_BEGIN
+    if (!g || !w || !dx || N < 1 || H < 1 || W < 1) return DN_EINVAL;
+    if (C != 32 && C != 64) return DN_EUNSUPPORTED;
+    if (!workspace || ws_bytes < wpack_bytes(C)) return DN_ENOMEM;
+    int *err = device_error_ptr();
+    if (!err) return DN_ECUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    DN_TRY(pack_w_tc(w, workspace, C, s, true));
+    return conv3x3_tc(g, dx, workspace, nullptr, N, H, W, C, 0, err, s, mask);
+    DN_GUARD_END
+}
+
 // ---- one image in tiles with a halo -------------------------------------------------
 
 int dn_bm3d_halo(const dn_bm3d_params *p)

@@ -124,14 +124,26 @@ dn_status match_tc(const float *guide, size_t plane, int B, int H, int W, const 
                    int *idx, int *n, int *err, int *fb_ws, cudaStream_t s, float *cross = nullptr, int cross_tx = 0,
                    int cross_ty = 0);
 size_t conv_tc_smem_bytes();
-dn_status pack_w_tc(const float *w, void *out, int C, cudaStream_t s);
+// W [C][3][3][C] -> the tensor-core B operand; flip: of the transposed (data-gradient) layer.
+dn_status pack_w_tc(const float *w, void *out, int C, cudaStream_t s, bool flip = false);
+// Hidden C -> C layer on the tensor cores (NHWC bf16); bias may be null; mask (NHWC bf16, or
+// null) zeroes the outputs where the mask is not positive (the ReLU backward of the data gradient).
 dn_status conv3x3_tc(const void *x, void *y, const void *wpack, const float *bias, int N, int H, int W, int C,
-                     int relu, int *err, cudaStream_t s);
+                     int relu, int *err, cudaStream_t s, const void *mask = nullptr);
 dn_status conv_first_bf16(const float *pre, const float *noisy, const float *w, const float *b, void *y, int N,
                           int cc, int H, int W, int C, cudaStream_t s);
 dn_status conv_last_bf16(const void *x, const float *w, const float *b, const float *pre, float *out, int N, int cc,
                          int H, int W, int C, cudaStream_t s);
 dn_status adam(float *p, const float *g, float *m, float *v, size_t count, int t, float lr, float b1, float b2,
                float eps, cudaStream_t s);
+// Gradient of the L1 loss of the grey width-32 residual network with BF16 tensor-core
+// forward and backward (cnn_train_tc.cu); grad is overwritten, loss accumulated.
+size_t cnn_grad_tc_workspace_bytes(int N, int H, int W, int layers);
+// Weight and bias gradient of one 32 -> 32 layer from its NHWC bf16 input x and output gradient g.
+size_t conv_bwd_w_tc_workspace_bytes(int N, int H, int W);
+dn_status conv_bwd_w_tc(const void *x, const void *g, float *dw, float *db, int N, int H, int W, void *ws, int *err,
+                        cudaStream_t s);
+dn_status cnn_grad_tc(const float *noisy, const float *pre, const float *clean, int N, int H, int W, int layers,
+                      const float *weights, float *grad, double *loss, void *ws, int *err, cudaStream_t s);
 
 }  // namespace dn

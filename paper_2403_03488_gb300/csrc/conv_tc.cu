@@ -53,7 +53,8 @@ struct ConvTcArgs {
     const uint4 *x;       // [N][H][W][C] bf16, C / 8 x uint4 per pixel
     uint4 *y;             // same layout
     const uint4 *wpack;   // Shape<C>::kWBytes
-    const float *bias;    // [C]
+    const float *bias;    // [C], or null (no bias)
+    const uint4 *mask;    // null, or [N][H][W][C] bf16: outputs where mask <= 0 are zeroed (ReLU backward)
     int N, H, W, strips, chunks, relu;
     int *err;
 };
@@ -91,7 +92,7 @@ __global__ void __launch_bounds__(128) k_conv3x3_tc(ConvTcArgs a)
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     for (int i = tid; i < S::kWBytes / 16; i += 128) reinterpret_cast<uint4 *>(wsm)[i] = a.wpack[i];
-    for (int i = tid; i < C; i += 128) sbias[i] = a.bias[i];
+    for (int i = tid; i < C; i += 128) sbias[i] = a.bias ? a.bias[i] : 0.0f;
     if (warp == 0) tc::tmem_alloc(tslot, 2 * C);
     if (tid == 0) {
         tc::mbar_init(&mbar[0], 1);
@@ -124,6 +125,18 @@ __global__ void __launch_bounds__(128) k_conv3x3_tc(ConvTcArgs a)
             tc::tmem_ld32(tmem + (uint32_t)(C * buf + 32 * h) + ((uint32_t)(warp * 32) << 16), r);
             tc::tmem_wait_ld();
             if (x < a.W) {
+                uint32_t mk[16];
+                if (a.mask) {
+                    const uint4 *ms = a.mask + (((size_t)n * a.H + yy) * a.W + x) * K + 4 * h;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const uint4 u = ms[q];
+                        mk[4 * q] = u.x;
+                        mk[4 * q + 1] = u.y;
+                        mk[4 * q + 2] = u.z;
+                        mk[4 * q + 3] = u.w;
+                    }
+                }
                 uint32_t pk[16];
 #pragma unroll
                 for (int c = 0; c < 16; ++c) {
@@ -132,6 +145,10 @@ __global__ void __launch_bounds__(128) k_conv3x3_tc(ConvTcArgs a)
                     if (a.relu) {
                         v0 = fmaxf(v0, 0.0f);
                         v1 = fmaxf(v1, 0.0f);
+                    }
+                    if (a.mask) {  // the layer input's ReLU: pass the gradient where it was positive
+                        v0 = tc::bf16_lo(mk[c]) > 0.0f ? v0 : 0.0f;
+                        v1 = tc::bf16_hi(mk[c]) > 0.0f ? v1 : 0.0f;
                     }
                     pk[c] = tc::pack_bf16x2(v0, v1);
                 }
@@ -201,14 +218,16 @@ __global__ void __launch_bounds__(128) k_conv3x3_tc(ConvTcArgs a)
 }
 
 // W [C][3][3][C] fp32 -> [tap][chunk][cout][8 ch] bf16 (the B operand layout).
-template <int C>
+// FLIP packs the data-gradient layer instead: output channel i, input channel
+// o, tap (ky, kx) takes W[o][2 - ky][2 - kx][i] (the transposed convolution).
+template <int C, bool FLIP>
 __global__ void k_pack_w_tc(const float *w, uint16_t *out)
 {
     constexpr int K = C / 8;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= 9 * K * C * 8) return;
     const int j = i & 7, co = (i >> 3) % C, ck = (i / (8 * C)) % K, t = i / (8 * C * K);
-    const float v = w[(co * 9 + t) * C + ck * 8 + j];
+    const float v = FLIP ? w[((ck * 8 + j) * 9 + (8 - t)) * C + co] : w[(co * 9 + t) * C + ck * 8 + j];
     __nv_bfloat16 b = __float2bfloat16_rn(v);
     out[i] = *reinterpret_cast<uint16_t *>(&b);
 }
@@ -464,14 +483,22 @@ __global__ void __launch_bounds__(256) k_conv_last_bf16(const uint4 *x, const fl
 
 size_t conv_tc_smem_bytes() { return Shape<kCh>::kSmem; }
 
-dn_status pack_w_tc(const float *w, void *out, int C, cudaStream_t s)
+dn_status pack_w_tc(const float *w, void *out, int C, cudaStream_t s, bool flip)
 {
     if (C == 32)
-        return launch("pack_w_tc", s,
-                      [&] { k_pack_w_tc<32><<<(9 * 4 * 32 * 8 + 255) / 256, 256, 0, s>>>(w, (uint16_t *)out); });
+        return launch("pack_w_tc", s, [&] {
+            if (flip)
+                k_pack_w_tc<32, true><<<(9 * 4 * 32 * 8 + 255) / 256, 256, 0, s>>>(w, (uint16_t *)out);
+            else
+                k_pack_w_tc<32, false><<<(9 * 4 * 32 * 8 + 255) / 256, 256, 0, s>>>(w, (uint16_t *)out);
+        });
     if (C == 64)
-        return launch("pack_w_tc", s,
-                      [&] { k_pack_w_tc<64><<<(9 * 8 * 64 * 8 + 255) / 256, 256, 0, s>>>(w, (uint16_t *)out); });
+        return launch("pack_w_tc", s, [&] {
+            if (flip)
+                k_pack_w_tc<64, true><<<(9 * 8 * 64 * 8 + 255) / 256, 256, 0, s>>>(w, (uint16_t *)out);
+            else
+                k_pack_w_tc<64, false><<<(9 * 8 * 64 * 8 + 255) / 256, 256, 0, s>>>(w, (uint16_t *)out);
+        });
     return DN_EUNSUPPORTED;
 }
 
@@ -488,13 +515,14 @@ dn_status conv3x3_tc_c(ConvTcArgs &a, cudaStream_t s)
 }
 
 dn_status conv3x3_tc(const void *x, void *y, const void *wpack, const float *bias, int N, int H, int W, int C,
-                     int relu, int *err, cudaStream_t s)
+                     int relu, int *err, cudaStream_t s, const void *mask)
 {
     ConvTcArgs a;
     a.x = static_cast<const uint4 *>(x);
     a.y = static_cast<uint4 *>(y);
     a.wpack = static_cast<const uint4 *>(wpack);
     a.bias = bias;
+    a.mask = static_cast<const uint4 *>(mask);
     a.N = N;
     a.H = H;
     a.W = W;

@@ -75,7 +75,11 @@ class CropSampler:
 
 
 def train(steps=20000, batch=64, crop=64, lr=1e-3, seed=0, n_images=256, prefilter="bm3d", log_every=500,
-          checkpoint=None, resume=True, device="cuda", log=print, net_kind="resnet", max_minutes=None):
+          checkpoint=None, resume=True, device="cuda", log=print, net_kind="resnet", max_minutes=None,
+          precision="fp32"):
+    """precision (residual network only): "fp32" = the FP32 CUDA-core layer
+    kernels, "bf16" = dn_cnn_grad's tensor-core forward and backward (BF16
+    operands, FP32 accumulation and master weights)."""
     t0 = time.time()
     clean, noisy, pre, sig = make_pool(n_images=n_images, prefilter=prefilter, device=device)
     torch.cuda.synchronize()
@@ -101,7 +105,8 @@ def train(steps=20000, batch=64, crop=64, lr=1e-3, seed=0, n_images=256, prefilt
         if fl:
             acc += net.train_step(nc, pc, cc, list(sig[sampler.last]), lr=lr, sync=False)
         else:
-            acc += net.train_step(nc, pc, cc, lr=lr, sync=False)
+            acc += net.train_step(nc, pc, cc, lr=lr, sync=False,
+                                  precision=api.DN_BF16 if precision == "bf16" else api.DN_FP32)
         # wall-clock cap: stop at a multiple of 50 steps once the budget is spent
         stop = max_minutes is not None and (s + 1) % 50 == 0 and time.time() - t1 > 60.0 * max_minutes
         if (s + 1) % log_every == 0 or s + 1 == steps or stop:
@@ -176,13 +181,16 @@ def main():
     ap.add_argument("--net", default="resnet", choices=["resnet", "fl"],
                     help="resnet: the 10x32 residual CNN of Sec. II; fl: the flexible network of Sec. III")
     ap.add_argument("--max-minutes", type=float, default=None, help="stop training after this wall-clock time")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"],
+                    help="residual network: FP32 CUDA-core kernels or the BF16 tensor-core forward/backward")
     ap.add_argument("--out", default=DEFAULT_OUT)
     ap.add_argument("--checkpoint", default=None)
     ap.add_argument("--eval-images", type=int, default=32)
     ap.add_argument("--report", default=None)
     args = ap.parse_args()
     net, hist = train(args.steps, args.batch, args.crop, args.lr, args.seed, args.images, args.prefilter,
-                      checkpoint=args.checkpoint, net_kind=args.net, max_minutes=args.max_minutes)
+                      checkpoint=args.checkpoint, net_kind=args.net, max_minutes=args.max_minutes,
+                      precision=args.precision)
     os.makedirs(os.path.dirname(os.path.abspath(args.out)), exist_ok=True)
     w = net.flat.detach().cpu().numpy().astype(np.float32)
     np.save(args.out, w)
