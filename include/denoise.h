@@ -340,6 +340,16 @@ size_t dn_cnn_workspace_bytes(int N, int H, int W, const dn_cnn *cnn);
 dn_status dn_conv3x3_tc_fwd(const void *x, const float *w, const float *b, void *y, int N, int H, int W, int C,
                             int relu, void *workspace, size_t ws_bytes, dn_stream_t stream);
 
+/* Two hidden C -> C layers (C = 32) in one pass on the tensor cores:
+ * y = ReLU(conv_b(ReLU(conv_a(x) + ba)) + bb), the intermediate rounded to
+ * bf16 exactly as dn_conv3x3_tc_fwd rounds its output but kept in shared
+ * memory (bit-identical to two dn_conv3x3_tc_fwd calls with relu = 1).
+ * x, y: NHWC bf16 [N][H][W][C]; wa, wb: FP32 [C][3][3][C]; ba, bb: FP32 [C];
+ * workspace >= 2 * 9 * C * C * 2 bytes (packed weights). */
+dn_status dn_conv3x3_tc_pair_fwd(const void *x, const float *wa, const float *ba, const float *wb, const float *bb,
+                                 void *y, int N, int H, int W, int C, void *workspace, size_t ws_bytes,
+                                 dn_stream_t stream);
+
 /* Backward of one hidden C -> C layer on the tensor cores (NHWC bf16, as
  * dn_conv3x3_tc_fwd), the two halves of dn_cnn_grad's hidden-layer step:
  *   weight: dw [C][3][3][C] = sum_px g[px][co] x[px + tap - 1][ci] and

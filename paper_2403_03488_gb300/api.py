@@ -371,6 +371,18 @@ def cnn_grad(noisy, pre, clean, weights, layers=10, width=32, grad=None, loss=No
     return grad, loss
 
 
+def conv3x3_tc_pair_fwd(x_nhwc, wa, ba, wb, bb, stream=None):
+    """Two hidden 32 -> 32 layers (bias + ReLU each) in one tensor-core pass."""
+    _need(x_nhwc, "x_nhwc", torch.bfloat16, dim=4)
+    N, H, W, C = x_nhwc.shape
+    y = torch.empty_like(x_nhwc)
+    ws, nb = _ws(2 * 9 * C * C * 2, x_nhwc.device, None)
+    check(L.lib().dn_conv3x3_tc_pair_fwd(_vp(x_nhwc), _vp(wa.contiguous()), _vp(ba.contiguous()),
+                                         _vp(wb.contiguous()), _vp(bb.contiguous()), _vp(y), N, H, W, C, _vp(ws), nb,
+                                         _stream(stream)), "dn_conv3x3_tc_pair_fwd")
+    return y
+
+
 def conv3x3_tc_bwd_weight(x_nhwc, g_nhwc, stream=None):
     """(dw [C, 3, 3, C], db [C]) of one hidden tensor-core layer (C = 32)."""
     _need(x_nhwc, "x_nhwc", torch.bfloat16, dim=4)

@@ -285,13 +285,25 @@ dn_status run_cnn(const float *noisy, const float *pre, float *out, int N, int H
         DN_TRY(conv_first_bf16(pre, noisy, c->weights, c->weights + (size_t)C * 9 * 2 * cc, w.act[0], N, cc, H, W, C,
                                s));
         int cur = 0;
-        for (int l = 1; l < c->layers - 1; ++l) {
+        for (int l = 1; l < c->layers - 1;) {
             const float *wl = c->weights + off;
             const float *bl = wl + (size_t)C * 9 * C;
-            off += (size_t)C * 9 * C + C;
             char *wp = w.wpack + wpack_bytes(C) * (size_t)(l - 1);
             DN_TRY(pack_w_tc(wl, wp, C, s));
-            DN_TRY(conv3x3_tc(w.act[cur], w.act[cur ^ 1], wp, bl, N, H, W, C, 1, err, s));
+            if (C == 32 && l + 1 < c->layers - 1) {
+                // two hidden layers per pass: the intermediate rows stay in shared memory
+                const float *wl2 = bl + C;
+                const float *bl2 = wl2 + (size_t)C * 9 * C;
+                char *wp2 = wp + wpack_bytes(C);
+                DN_TRY(pack_w_tc(wl2, wp2, C, s));
+                DN_TRY(conv3x3_tc_pair(w.act[cur], w.act[cur ^ 1], wp, bl, wp2, bl2, N, H, W, C, err, s));
+                off += 2 * ((size_t)C * 9 * C + C);
+                l += 2;
+            } else {
+                DN_TRY(conv3x3_tc(w.act[cur], w.act[cur ^ 1], wp, bl, N, H, W, C, 1, err, s));
+                off += (size_t)C * 9 * C + C;
+                l += 1;
+            }
             cur ^= 1;
         }
         const float *wl = c->weights + off;
@@ -477,6 +489,24 @@ dn_status dn_cnn_grad(const float *noisy, const float *pre, const float *clean, 
     if (!err) return DN_ECUDA;
     return cnn_grad_tc(noisy, pre, clean, N, H, W, cnn->layers, cnn->weights, grad, loss_sum, workspace, err,
                        (cudaStream_t)stream);
+    DN_GUARD_END
+}
+
+dn_status dn_conv3x3_tc_pair_fwd(const void *x, const float *wa, const float *ba, const float *wb, const float *bb,
+                                 void *y, int N, int H, int W, int C, void *workspace, size_t ws_bytes,
+                                 dn_stream_t stream)
+{
+    DN_GUARD_BEGIN
+    if (!x || !wa || !ba || !wb || !bb || !y || N < 1 || H < 1 || W < 1) return DN_EINVAL;
+    if (C != 32) return DN_EUNSUPPORTED;
+    if (!workspace || ws_bytes < 2 * wpack_bytes(C)) return DN_ENOMEM;
+    int *err = device_error_ptr();
+    if (!err) return DN_ECUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    char *wp = static_cast<char *>(workspace);
+    DN_TRY(pack_w_tc(wa, wp, C, s));
+    DN_TRY(pack_w_tc(wb, wp + wpack_bytes(C), C, s));
+    return conv3x3_tc_pair(x, y, wp, ba, wp + wpack_bytes(C), bb, N, H, W, C, err, s);
     DN_GUARD_END
 }
 

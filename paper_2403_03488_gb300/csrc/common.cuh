@@ -124,6 +124,9 @@ dn_status match_tc(const float *guide, size_t plane, int B, int H, int W, const 
                    int *idx, int *n, int *err, int *fb_ws, cudaStream_t s, float *cross = nullptr, int cross_tx = 0,
                    int cross_ty = 0);
 size_t conv_tc_smem_bytes();
+// Two hidden C -> C layers (bias + ReLU each) in one pass on the tensor cores (C = 32).
+dn_status conv3x3_tc_pair(const void *x, void *y, const void *wpa, const float *ba, const void *wpb, const float *bb,
+                          int N, int H, int W, int C, int *err, cudaStream_t s);
 // W [C][3][3][C] -> the tensor-core B operand; flip: of the transposed (data-gradient) layer.
 dn_status pack_w_tc(const float *w, void *out, int C, cudaStream_t s, bool flip = false);
 // Hidden C -> C layer on the tensor cores (NHWC bf16); bias may be null; mask (NHWC bf16, or

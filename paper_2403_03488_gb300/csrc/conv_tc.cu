@@ -217,6 +217,249 @@ __global__ void __launch_bounds__(128) k_conv3x3_tc(ConvTcArgs a)
     }
 }
 
+// Two hidden C -> C layers (A then B, bias + ReLU each) in one pass: layer A's
+// output rows never leave shared memory.  A work item is 32 output rows of a
+// strip of kPX - 2 = 126 output pixels: layer A computes 128 pixels (the strip
+// plus one on each side, the halo layer B needs) into a ring of kMid rows in
+// the operand layout (zero outside the image: layer B's zero padding), and
+// layer B reads them like staged input rows.  Layer B runs three rows behind
+// layer A, so at every step both layers' MMAs depend only on rows finished in
+// earlier steps.  Warp 4 issues them (one thread, descriptors advanced from
+// precomputed bases) into one of two TMEM buffer pairs as soon as the 128
+// loader / epilogue threads signal on an mbarrier that the step's rows are
+// staged; those threads then drain the previous step's two results (A into
+// the ring, B to global memory) while the tensor cores work.  Two CTAs per
+// SM (measured: one CTA with two more rows of prefetch took 1.76 ms per
+// 16 x 1024^2 pair against 1.01 ms).
+constexpr int kMid = 4;          // ring rows of layer A's output
+constexpr int kPairPF = 0;       // input rows in flight beyond the next one (two CTAs per SM)
+constexpr int kPairSlots = kPairPF + 5;
+constexpr int kPairOut = kPX - 2;  // output pixels per strip
+
+template <int C>
+struct PairShape {
+    static constexpr int kChunks = C / 8;
+    static constexpr int kRowBytes = kP * C * 2;
+    static constexpr int kWBytes = 9 * kChunks * C * 16;
+    static constexpr int kSmem = 2 * kWBytes + (kPairSlots + kMid) * kRowBytes + 64 + 2 * C * 4;  // + barriers
+    static constexpr int kCtasPerSm = (227 * 1024) / (kSmem + 1024);
+    static constexpr uint32_t kIdesc = tc::idesc_bf16(128, C);
+};
+
+struct ConvPairArgs {
+    const uint4 *x;
+    uint4 *y;
+    const uint4 *wa, *wb;        // packed weights of layers A and B
+    const float *ba, *bb;        // biases
+    int N, H, W, strips, chunks;
+    int *err;
+};
+
+__device__ __forceinline__ void mbar_arrive_cta(uint64_t *mbar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(mbar)) : "memory");
+}
+
+template <int C>
+__global__ void __launch_bounds__(160, 2) k_conv3x3_tc_pair(ConvPairArgs a)
+{
+    using S = PairShape<C>;
+    constexpr int K = S::kChunks;
+    extern __shared__ __align__(128) uint8_t sm[];
+    uint8_t *wsa = sm, *wsb = sm + S::kWBytes;
+    uint8_t *ring = sm + 2 * S::kWBytes;                      // input rows
+    uint8_t *mid = ring + kPairSlots * S::kRowBytes;          // layer A rows
+    uint64_t *ready = reinterpret_cast<uint64_t *>(mid + kMid * S::kRowBytes);  // [2]: operands of step staged
+    uint64_t *done = ready + 2;                                                  // [2]: MMAs of step complete
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(done + 2);
+    int *abort_flag = reinterpret_cast<int *>(tslot + 1);
+    float *sba = reinterpret_cast<float *>(tslot + 4), *sbb = sba + C;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool mma_warp = warp == 4;
+    for (int i = tid; i < S::kWBytes / 16; i += 160) {
+        reinterpret_cast<uint4 *>(wsa)[i] = a.wa[i];
+        reinterpret_cast<uint4 *>(wsb)[i] = a.wb[i];
+    }
+    for (int i = tid; i < C; i += 160) {
+        sba[i] = a.ba[i];
+        sbb[i] = a.bb[i];
+    }
+    // ring pixels 128, 129 of layer A's rows are never computed: zero (layer B's garbage lanes only)
+    for (int i = tid; i < kMid * K * 2; i += 160) {
+        const int slot = i / (K * 2), rem = i % (K * 2), ck = rem >> 1, px = 128 + (rem & 1);
+        *reinterpret_cast<uint4 *>(mid + slot * S::kRowBytes + ck * kP * 16 + px * 16) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    if (warp == 0) tc::tmem_alloc(tslot, 4 * C);  // [buffer 0: A, B][buffer 1: A, B]
+    if (tid == 0) {
+        tc::mbar_init(&ready[0], 128);
+        tc::mbar_init(&ready[1], 128);
+        tc::mbar_init(&done[0], 1);
+        tc::mbar_init(&done[1], 1);
+        *abort_flag = 0;
+    }
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    volatile int *abort_v = abort_flag;
+    // descriptors: the start-address field (bits 0-13, address >> 4) is advanced by offsets
+    const uint64_t wa_d = tc::sdesc(tc::smem_u32(wsa), C * 16, 128), wb_d = tc::sdesc(tc::smem_u32(wsb), C * 16, 128);
+    const uint64_t ring_d = tc::sdesc(tc::smem_u32(ring), kP * 16, 128), mid_d = tc::sdesc(tc::smem_u32(mid), kP * 16, 128);
+    uint32_t g = 0;  // steps so far (all items): buffer g & 1, barrier parity (g >> 1) & 1
+
+    const int items = a.N * a.strips * a.chunks;
+    for (int it = blockIdx.x; it < items; it += gridDim.x) {
+        if (*abort_v) break;
+        const int chunk = it % a.chunks, rest = it / a.chunks;
+        const int strip = rest % a.strips, n = rest / a.strips;
+        const int xo = strip * kPairOut;                    // first output pixel of the strip
+        const int x0 = xo - 1;                              // layer A's first pixel
+        const int y0 = chunk * kItemRows, y1 = min(a.H, y0 + kItemRows);
+        // layer A row of step t: y0 - 1 + t (t < tA); layer B row: y0 - 4 + t (in [y0, y1))
+        const int tA = y1 - y0 + 2, tEnd = y1 - y0 + 4;
+        auto in_idx = [&](int r) { return (r - (y0 - 2)) % kPairSlots; };
+        auto mid_idx = [&](int r) { return (r - (y0 - 1)) % kMid; };
+        if (mma_warp) {
+            if (lane == 0) {
+                for (int t = 0; t < tEnd; ++t, ++g) {
+                    const int buf = g & 1;
+                    if (!tc::mbar_wait(&ready[buf], (g >> 1) & 1u) || *abort_v) {
+                        atomicExch(abort_flag, 1);
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    const int rA = y0 - 1 + t, rB = y0 - 4 + t;
+                    if (t < tA) {
+#pragma unroll
+                        for (int tap = 0; tap < 9; ++tap) {
+                            const uint32_t rowo = (uint32_t)(in_idx(rA - 1 + tap / 3) * S::kRowBytes + (tap % 3) * 16);
+#pragma unroll
+                            for (int k = 0; k < C / 16; ++k)
+                                tc::mma_bf16(tmem + (uint32_t)(2 * C * buf),
+                                             ring_d + ((rowo + (uint32_t)(2 * k * kP * 16)) >> 4),
+                                             wa_d + ((uint32_t)((tap * K + 2 * k) * C * 16) >> 4), S::kIdesc,
+                                             (tap | k) != 0);
+                        }
+                    }
+                    if (rB >= y0 && rB < y1) {
+#pragma unroll
+                        for (int tap = 0; tap < 9; ++tap) {
+                            const uint32_t rowo = (uint32_t)(mid_idx(rB - 1 + tap / 3) * S::kRowBytes + (tap % 3) * 16);
+#pragma unroll
+                            for (int k = 0; k < C / 16; ++k)
+                                tc::mma_bf16(tmem + (uint32_t)(2 * C * buf + C),
+                                             mid_d + ((rowo + (uint32_t)(2 * k * kP * 16)) >> 4),
+                                             wb_d + ((uint32_t)((tap * K + 2 * k) * C * 16) >> 4), S::kIdesc,
+                                             (tap | k) != 0);
+                        }
+                    }
+                    tc::mma_commit(&done[buf]);
+                }
+            }
+            g = __shfl_sync(0xffffffffu, g, 0);
+            continue;
+        }
+        // loader / epilogue warps (thread = pixel = TMEM lane)
+        for (int r = y0 - 2; r <= y0 + kPairPF; ++r) {
+            issue_row<C>(ConvTcArgs{a.x, nullptr, nullptr, nullptr, nullptr, a.N, a.H, a.W, 0, 0, 0, nullptr},
+                         ring + in_idx(r) * S::kRowBytes, n, r, x0, tid);
+            tc::cp_async_commit();
+        }
+        bool stop = false;
+        for (int t = 0; t <= tEnd; ++t, ++g) {
+            const int rA = y0 - 1 + t;
+            if (t < tEnd) {
+                const int rn = rA + 2 + kPairPF;  // input row of step t + 1 + kPairPF
+                if (rn <= y1 + 1)
+                    issue_row<C>(ConvTcArgs{a.x, nullptr, nullptr, nullptr, nullptr, a.N, a.H, a.W, 0, 0, 0, nullptr},
+                                 ring + in_idx(rn) * S::kRowBytes, n, rn, x0, tid);
+                tc::cp_async_commit();
+                tc::cp_async_wait<kPairPF + 1>();  // this thread's copies of rows up to rA + 1 have landed
+                tc::fence_proxy_async();           // ... and its ring writes of earlier steps are visible
+                tc::fence_before_sync();
+                mbar_arrive_cta(&ready[g & 1]);
+            }
+            if (t == 0) continue;
+            // drain step t - 1 (buffer (g - 1) & 1)
+            const uint32_t pg = g - 1;
+            const int pb = pg & 1, prA = rA - 1, prB = y0 - 5 + t;
+            const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(&done[pb], (pg >> 1) & 1u));
+            if (!ok || *abort_v) {
+                atomicExch(abort_flag, 1);
+                stop = true;
+                ++g;
+                break;
+            }
+            tc::fence_after_sync();
+            const int m = warp * 32 + lane;
+            if (t - 1 < tA) {
+                // layer A row prA, pixel x0 + m, into the ring; zero outside the image
+                const int x = x0 + m;
+                const bool inside = prA >= 0 && prA < a.H && x >= 0 && x < a.W;
+                uint8_t *dst = mid + mid_idx(prA) * S::kRowBytes + m * 16;
+#pragma unroll
+                for (int h = 0; h < C / 32; ++h) {
+                    uint32_t r[32];
+                    tc::tmem_ld32(tmem + (uint32_t)(2 * C * pb + 32 * h) + ((uint32_t)(warp * 32) << 16), r);
+                    tc::tmem_wait_ld();
+                    uint32_t pk[16];
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) {
+                        const float v0 = fmaxf(__uint_as_float(r[2 * c]) + sba[32 * h + 2 * c], 0.0f);
+                        const float v1 = fmaxf(__uint_as_float(r[2 * c + 1]) + sba[32 * h + 2 * c + 1], 0.0f);
+                        pk[c] = inside ? tc::pack_bf16x2(v0, v1) : 0u;
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        *reinterpret_cast<uint4 *>(dst + (4 * h + q) * kP * 16) =
+                            make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+                }
+            }
+            if (prB >= y0 && prB < y1) {
+                const int x = xo + m;
+                uint4 *dst = a.y + (((size_t)n * a.H + prB) * a.W + x) * K;
+#pragma unroll
+                for (int h = 0; h < C / 32; ++h) {
+                    uint32_t r[32];
+                    tc::tmem_ld32(tmem + (uint32_t)(2 * C * pb + C + 32 * h) + ((uint32_t)(warp * 32) << 16), r);
+                    tc::tmem_wait_ld();
+                    if (m < kPairOut && x < a.W) {
+                        uint32_t pk[16];
+#pragma unroll
+                        for (int c = 0; c < 16; ++c) {
+                            const float v0 = fmaxf(__uint_as_float(r[2 * c]) + sbb[32 * h + 2 * c], 0.0f);
+                            const float v1 = fmaxf(__uint_as_float(r[2 * c + 1]) + sbb[32 * h + 2 * c + 1], 0.0f);
+                            pk[c] = tc::pack_bf16x2(v0, v1);
+                        }
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            dst[4 * h + q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+                    }
+                }
+            }
+            tc::fence_before_sync();
+        }
+        // g counted the tEnd + 1 iterations; the MMA warp counted tEnd steps
+        g -= 1;
+        tc::cp_async_wait<0>();
+        if (stop) break;
+    }
+    tc::cp_async_wait<0>();
+    __syncthreads();
+    if (*abort_v) {
+        if (tid == 0) atomicExch(a.err, 1);
+        // bounded waits for MMAs that may still be in flight before the TMEM is freed
+        tc::mbar_wait(&done[0], 0);
+        tc::mbar_wait(&done[1], 0);
+    }
+    if (warp == 0) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tmem, 4 * C);
+    }
+}
+
 // W [C][3][3][C] fp32 -> [tap][chunk][cout][8 ch] bf16 (the B operand layout).
 // FLIP packs the data-gradient layer instead: output channel i, input channel
 // o, tap (ky, kx) takes W[o][2 - ky][2 - kx][i] (the transposed convolution).
@@ -532,6 +775,39 @@ dn_status conv3x3_tc(const void *x, void *y, const void *wpack, const float *bia
     a.chunks = (H + kItemRows - 1) / kItemRows;
     if (C == 32) return conv3x3_tc_c<32>(a, s);
     if (C == 64) return conv3x3_tc_c<64>(a, s);
+    return DN_EUNSUPPORTED;
+}
+
+template <int C>
+dn_status conv3x3_tc_pair_c(ConvPairArgs &a, cudaStream_t s)
+{
+    using S = PairShape<C>;
+    const long items = (long)a.N * a.strips * a.chunks;
+    const long cap = 152L * (S::kCtasPerSm > 0 ? S::kCtasPerSm : 1);
+    const int grid = (int)(items < cap ? items : cap);
+    if (cudaFuncSetAttribute(k_conv3x3_tc_pair<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kSmem) !=
+        cudaSuccess)
+        return DN_ECUDA;
+    return launch("conv3x3_tc_pair_bf16", s, [&] { k_conv3x3_tc_pair<C><<<grid, 160, S::kSmem, s>>>(a); });
+}
+
+dn_status conv3x3_tc_pair(const void *x, void *y, const void *wpa, const float *ba, const void *wpb, const float *bb,
+                          int N, int H, int W, int C, int *err, cudaStream_t s)
+{
+    ConvPairArgs a;
+    a.x = static_cast<const uint4 *>(x);
+    a.y = static_cast<uint4 *>(y);
+    a.wa = static_cast<const uint4 *>(wpa);
+    a.wb = static_cast<const uint4 *>(wpb);
+    a.ba = ba;
+    a.bb = bb;
+    a.N = N;
+    a.H = H;
+    a.W = W;
+    a.err = err;
+    a.strips = (W + kPairOut - 1) / kPairOut;
+    a.chunks = (H + kItemRows - 1) / kItemRows;
+    if (C == 32) return conv3x3_tc_pair_c<32>(a, s);
     return DN_EUNSUPPORTED;
 }
 

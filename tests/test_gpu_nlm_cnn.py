@@ -279,3 +279,23 @@ def test_cnn_forward_bf16_close_to_oracle(oracle):
     r = np.abs(ref - pre).max()
     assert np.abs(out - ref).max() <= 0.03 * r + 1e-2
     assert A.device_error() == 0
+
+
+@pytest.mark.parametrize("N,H,W", [(2, 70, 300), (1, 33, 126), (3, 64, 127), (1, 1, 9), (16, 256, 256)])
+def test_conv3x3_tc_pair_equals_two_layers(N, H, W):
+    """Two hidden layers fused in one pass (the intermediate rows kept in
+    shared memory, strips of 126 output pixels) give bit for bit the result of
+    two single-layer launches: same BF16 rounding of the intermediate, same
+    MMA order.  Ragged strips and items, strip-wide and one-row images."""
+    import torch
+    A = api()
+    g = torch.Generator(device="cuda").manual_seed(N * 7 + H + W)
+    x = torch.relu(torch.randn(N, H, W, 32, device="cuda", generator=g)).to(torch.bfloat16)
+    wa = torch.randn(32, 3, 3, 32, device="cuda", generator=g) * (2.0 / 288) ** 0.5
+    wb = torch.randn(32, 3, 3, 32, device="cuda", generator=g) * (2.0 / 288) ** 0.5
+    ba = torch.randn(32, device="cuda", generator=g) * 0.1
+    bb = torch.randn(32, device="cuda", generator=g) * 0.1
+    two = A.conv3x3_tc_fwd(A.conv3x3_tc_fwd(x, wa, ba, relu=True), wb, bb, relu=True)
+    fused = A.conv3x3_tc_pair_fwd(x, wa, ba, wb, bb)
+    assert torch.equal(two.view(torch.int16), fused.view(torch.int16))
+    assert A.device_error() == 0
