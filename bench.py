@@ -506,13 +506,16 @@ def serving_replay(args):
     fast = serve.replay(rate=args.serve_rate, n=args.serve_requests, side=(128, 2048),
                         bm3d_precision=bm3d_precision(args),
                         cnn_precision=api.DN_BF16 if args.cnn == "bf16" else api.DN_FP32)
-    plain = serve.replay(rate=args.serve_rate, n=args.serve_requests, side=(128, 2048),
+    # the FP32 plain path serves the first 300 requests of the same trace (at about 36 MPix/s it
+    # would need minutes for all of them)
+    plain = serve.replay(rate=args.serve_rate, n=min(args.serve_requests, 300), side=(128, 2048),
                          bm3d_precision=api.DN_FP32, cnn_precision=api.DN_FP32, warm=False)
-    keys = ("p50_ms", "p99_ms", "served_mpix_s", "served_channel_mpix_s", "makespan_s", "max_inflight")
+    keys = ("p50_ms", "p99_ms", "served_mpix_s", "served_channel_mpix_s", "makespan_s", "max_inflight", "launches",
+            "max_batch")
     out = {k: round(fast[k], 3) for k in keys}
     out.update({"offered_mpix_s": round(fast["offered_mpix_s"], 1), "trace": fast["trace"],
                 "budget_gb": 60, "slots": 8,
-                "fp32_plain": {k: round(plain[k], 3) for k in keys}})
+                "fp32_plain": dict({k: round(plain[k], 3) for k in keys}, trace=plain["trace"])})
     out["saturated"] = bool(fast["served_mpix_s"] < 0.9 * fast["offered_mpix_s"])
     if out["saturated"]:
         # the same trace shape at 60 % of the served rate: latency without a growing queue
@@ -678,7 +681,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-rate", type=float, default=200.0)
-    ap.add_argument("--serve-requests", type=int, default=300)
+    ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--batch", type=int, default=None, help="images per step (profiling runs; default 16)")
     ap.add_argument("--size", type=int, default=None, help="image side (profiling runs; default 1024)")
     ap.add_argument("--sigma", type=float, default=None,

@@ -1,14 +1,18 @@
 """Continuous-batching denoising server on one GPU.
 
 Requests (an image of either colour mode and any size, and its sigma) arrive
-over time.  The scheduler admits a waiting request as soon as a stream slot
-is free and the device-memory footprint of everything in flight plus the
-request fits the HBM budget; each admitted request runs on its own CUDA
-stream (host-to-device copy from pinned memory, denoise_hybrid, device-to-host
+over time.  The scheduler admits work as soon as a stream slot is free and
+the device-memory footprint of everything in flight plus the new work fits
+the HBM budget.  Queued requests of the same shape (C, H, W) are coalesced
+into one batched launch (up to max_batch images, each with its own sigma):
+the library treats every image of a batch independently and
+deterministically, so a request's result is bit for bit the same alone, in
+a batch, and beside other requests.  Each launch runs on its own CUDA stream
+(host-to-device copy from pinned memory, denoise_hybrid, device-to-host
 copy), so work of requests that arrive while others are running overlaps on
-the device.  Completion is detected with CUDA events; the request's buffers
-are then released and the next ones admitted.  Latency = result ready on the
-host minus arrival.  Requests larger than the whole budget are rejected.
+the device.  Completion is detected with CUDA events; the buffers are then
+released and the next work admitted.  Latency = result ready on the host
+minus arrival.  Requests larger than the whole budget are rejected.
 
     python -m paper_2403_03488_gb300.serve --rate 200 --requests 2000
 """
@@ -51,6 +55,8 @@ class ServerStats:
     max_inflight: int = 0
     rejected: int = 0
     makespan_s: float = 0.0
+    launches: int = 0
+    max_batch: int = 0
 
     def summary(self):
         lat = np.array(self.latencies_ms) if self.latencies_ms else np.zeros(1)
@@ -59,7 +65,7 @@ class ServerStats:
                 "mean_ms": float(lat.mean()), "served_mpix_s": self.pixels / 1e6 / max(self.makespan_s, 1e-9),
                 "served_channel_mpix_s": self.channel_pixels / 1e6 / max(self.makespan_s, 1e-9),
                 "makespan_s": self.makespan_s, "max_inflight_bytes": self.max_inflight_bytes,
-                "max_inflight": self.max_inflight}
+                "max_inflight": self.max_inflight, "launches": self.launches, "max_batch": self.max_batch}
 
 
 def make_trace(n, rate, seed=0, side=(128, 2048), sigmas=(15.0, 25.0, 50.0), p_rgb=0.5):
@@ -111,8 +117,9 @@ class Server:
     """Admission-controlled, stream-overlapped execution of denoise requests."""
 
     def __init__(self, weights: torch.Tensor, budget_bytes=60 << 30, slots=8, bm3d_precision=api.DN_FP32,
-                 cnn_precision=api.DN_BF16, prefilter=api.DN_PREFILTER_BM3D, device="cuda"):
+                 cnn_precision=api.DN_BF16, prefilter=api.DN_PREFILTER_BM3D, device="cuda", max_batch=8):
         self.dev = torch.device(device)
+        self.max_batch = max(1, int(max_batch))
         self.weights = weights
         self.budget = int(budget_bytes)
         self.streams = [torch.cuda.Stream(device=self.dev) for _ in range(slots)]
@@ -126,42 +133,61 @@ class Server:
         self.inflight_bytes = 0
         self.stats = ServerStats()
 
-    def footprint(self, C, H, W) -> int:
+    def footprint(self, C, H, W, B=1) -> int:
         img = C * H * W * 4
-        ws = api.hybrid_workspace_bytes(1, C, H, W, self.prefilter, self.pparams, self.cnn)
-        return 2 * img + ws + (1 << 20)
+        ws = api.hybrid_workspace_bytes(B, C, H, W, self.prefilter, self.pparams, self.cnn)
+        return 2 * B * img + ws + (1 << 20)
 
-    def _launch(self, req: Request, t0: float):
+    def _take_batch(self, queue):
+        """The head of the queue and up to max_batch - 1 later requests of the
+        same shape, if their launch fits the budget (else the largest prefix
+        that does); None when not even the head fits right now."""
+        head = queue[0]
+        same = [head] + [r for r in list(queue)[1:] if r.image.shape == head.image.shape][:self.max_batch - 1]
+        C, H, W = head.image.shape
+        while same:
+            fp = self.footprint(C, H, W, len(same)) if len(same) > 1 else head.footprint
+            if self.inflight_bytes + fp <= self.budget:
+                for r in same:
+                    queue.remove(r)
+                return same, fp
+            same = same[:-1]
+        return None, 0
+
+    def _launch(self, batch, fp, t0: float):
         si = self.free_streams.pop()
         s = self.streams[si]
-        C, H, W = req.image.shape
-        host_in = torch.from_numpy(req.image).pin_memory()
+        host_in = torch.from_numpy(np.stack([r.image for r in batch])).pin_memory()
         host_out = torch.empty_like(host_in).pin_memory()
         with torch.cuda.stream(s):
-            x = host_in.to(self.dev, non_blocking=True).unsqueeze(0)
-            y = api.denoise_hybrid(x, req.sigma, self.weights, prefilter=self.prefilter,
+            x = host_in.to(self.dev, non_blocking=True)
+            y = api.denoise_hybrid(x, [r.sigma for r in batch], self.weights, prefilter=self.prefilter,
                                    prefilter_params=self.pparams, cnn_precision=self.cnn_precision, stream=s)
-            host_out.copy_(y[0], non_blocking=True)
+            host_out.copy_(y, non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(s)
-        self.inflight.append((req, si, ev, (host_in, host_out, x, y)))
-        self.inflight_bytes += req.footprint
+        self.inflight.append((batch, si, ev, (host_in, host_out, x, y), fp))
+        self.inflight_bytes += fp
+        self.stats.launches += 1
+        self.stats.max_batch = max(self.stats.max_batch, len(batch))
         self.stats.max_inflight_bytes = max(self.stats.max_inflight_bytes, self.inflight_bytes)
-        self.stats.max_inflight = max(self.stats.max_inflight, len(self.inflight))
+        self.stats.max_inflight = max(self.stats.max_inflight, sum(len(b[0]) for b in self.inflight))
 
     def _poll(self, t0: float, keep_results: bool):
         still = []
         for item in self.inflight:
-            req, si, ev, bufs = item
+            batch, si, ev, bufs, fp = item
             if ev.query():
-                req.done = time.perf_counter() - t0
-                if keep_results:
-                    req.result = bufs[1].numpy().copy()
-                self.stats.latencies_ms.append(1e3 * (req.done - req.arrival))
-                C, H, W = req.image.shape
-                self.stats.pixels += H * W
-                self.stats.channel_pixels += C * H * W
-                self.inflight_bytes -= req.footprint
+                done = time.perf_counter() - t0
+                for k, req in enumerate(batch):
+                    req.done = done
+                    if keep_results:
+                        req.result = bufs[1][k].numpy().copy()
+                    self.stats.latencies_ms.append(1e3 * (req.done - req.arrival))
+                    C, H, W = req.image.shape
+                    self.stats.pixels += H * W
+                    self.stats.channel_pixels += C * H * W
+                self.inflight_bytes -= fp
                 self.free_streams.append(si)
             else:
                 still.append(item)
@@ -188,8 +214,11 @@ class Server:
                     continue
                 queue.append(r)
             self._poll(t0, keep_results)
-            while queue and self.free_streams and self.inflight_bytes + queue[0].footprint <= self.budget:
-                self._launch(queue.popleft(), t0)
+            while queue and self.free_streams:
+                batch, fp = self._take_batch(queue)
+                if batch is None:
+                    break
+                self._launch(batch, fp, t0)
             if not (queue and self.free_streams) and self.inflight:
                 time.sleep(0.0002)
             elif not self.inflight and not queue and pending and realtime:
@@ -205,13 +234,13 @@ def load_weights(device="cuda"):
 
 
 def replay(rate=200.0, n=2000, seed=0, budget_gb=60.0, slots=8, bm3d_precision=api.DN_FP32,
-           cnn_precision=api.DN_BF16, side=(128, 2048), warm=True):
+           cnn_precision=api.DN_BF16, side=(128, 2048), warm=True, max_batch=8):
     """Builds the trace (host images first, outside the timed replay) and serves it."""
     specs = make_trace(n, rate, seed, side=side)
     pool = ScenePool(seed, side=max(side[1], 256))
     reqs = [pool.build(s) for s in specs]
     srv = Server(load_weights(), budget_bytes=int(budget_gb * (1 << 30)), slots=slots,
-                 bm3d_precision=bm3d_precision, cnn_precision=cnn_precision)
+                 bm3d_precision=bm3d_precision, cnn_precision=cnn_precision, max_batch=max_batch)
     if warm:
         Server(srv.weights, srv.budget, 2, bm3d_precision, cnn_precision).run(
             [build_request(dict(rid=-1, arrival=0.0, H=160, W=144, C=c, sigma=25.0, seed=7 + c)) for c in (1, 3)],
@@ -231,10 +260,11 @@ def main():
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--budget-gb", type=float, default=60.0)
     ap.add_argument("--slots", type=int, default=8)
+    ap.add_argument("--max-batch", type=int, default=8)
     ap.add_argument("--plain", action="store_true", help="FP32 plain path (BM3D FP32 + CNN FP32)")
     args = ap.parse_args()
     res = replay(args.rate, args.requests, budget_gb=args.budget_gb, slots=args.slots,
-                 cnn_precision=api.DN_FP32 if args.plain else api.DN_BF16)
+                 cnn_precision=api.DN_FP32 if args.plain else api.DN_BF16, max_batch=args.max_batch)
     print(json.dumps(res))
 
 

@@ -1,6 +1,7 @@
 """Continuous-batching server: trace generation and admission on the host,
-and on the GPU: each result is the same alone and in the mix, the HBM budget
-is never exceeded, oversize requests are refused, latency is reported."""
+and on the GPU: each result is bit for bit the same alone, in a batch of
+same-shape requests and beside other requests, the HBM budget is never
+exceeded, oversize requests are refused, latency is reported."""
 import numpy as np
 import pytest
 
@@ -59,7 +60,32 @@ def test_results_same_alone_and_in_the_mix(bm3d_bf16):
     assert st.max_inflight > 1  # the requests really overlapped
     for q, ref in zip(mix, alone):
         assert q.result.shape == ref.shape
-        assert np.abs(q.result - ref).max() <= 1e-3
+        np.testing.assert_array_equal(q.result, ref)
+
+
+@pytest.mark.gpu
+def test_same_shape_requests_are_batched_and_unchanged():
+    """Queued requests of equal (C, H, W) go out as one batched launch with
+    their own sigmas, and each result is bit for bit its result alone."""
+    from gpu_util import need_gpu
+    need_gpu()
+    w = serve.load_weights()
+    pool = serve.ScenePool(seed=9, side=384, n_scenes=2)
+    shapes = [(1, 200, 176), (3, 128, 150), (1, 96, 320)]
+    sig = [15.0, 25.0, 50.0]
+    specs = [dict(rid=i, arrival=0.0, H=shapes[i % 3][1], W=shapes[i % 3][2], C=shapes[i % 3][0],
+                  sigma=sig[(i // 3) % 3], seed=500 + i) for i in range(12)]
+    reqs = [pool.build(sp) for sp in specs]
+    alone = []
+    for r in reqs:
+        q = serve.Request(r.rid, r.image, r.sigma)
+        serve.Server(w, slots=1, max_batch=1).run([q], realtime=False, keep_results=True)
+        alone.append(q.result)
+    mix = [serve.Request(r.rid, r.image, r.sigma) for r in reqs]
+    st = serve.Server(w, slots=2, max_batch=8).run(mix, realtime=False, keep_results=True)
+    assert st.max_batch > 1 and st.launches < len(mix)
+    for q, ref in zip(mix, alone):
+        np.testing.assert_array_equal(q.result, ref)
 
 
 @pytest.mark.gpu
