@@ -29,6 +29,7 @@ H = W = 1024
 B = 16
 SIGMA = 25.0
 SEEDS0 = 100
+FL_PREC = "fp32"  # contractions of the flexible network (--fl)
 METRIC = "MPix/s BM3D+CNN at <=0.05 dB PSNR loss vs FP32 plain; served p50/p99 ms"
 # the machine the FP32 ALU peak is derived for when the device is not queried
 # (host-only use of the work counts): GB300's SM count and maximum SM clock
@@ -47,7 +48,7 @@ def fp32_note(hw):
 
 def workload_name(bm3d, cnn, prefilter="bm3d", net="resnet"):
     pre = "BM3D(%s)" % bm3d if prefilter == "bm3d" else "NLM(fp32)"
-    body = "CNN(10x32, %s)" % cnn if net == "resnet" else "FL-UNet(48-192, fp32)"
+    body = "CNN(10x32, %s)" % cnn if net == "resnet" else "FL-UNet(48-192, %s)" % FL_PREC
     return "hybrid %s+%s denoise, %d grey %dx%d synthetic images, sigma=%g" % (pre, body, B, H, W, SIGMA)
 
 
@@ -302,7 +303,7 @@ def run_ours(args):
 
     fl = args.net == "fl"
     if fl:
-        flnet, wsrc = load_fl(dev, args.prefilter)
+        flnet, wsrc = load_fl(dev, args.prefilter, api.DN_BF16 if args.fl == "bf16" else api.DN_FP32)
         pre_d = torch.empty_like(noisy_d)
         ws_pre = torch.empty(api.bm3d_workspace_bytes(B, 1, H, W, bp) if not nlm else 1, dtype=torch.uint8,
                              device=dev)
@@ -361,8 +362,14 @@ def run_ours(args):
     mse = float(sse_d.sum().item()) / (B * H * W)
     psnr_out = 10 * np.log10(255.0 ** 2 / mse)
     # the FP32 plain path on the same batch (untimed), for the PSNR-loss criterion
-    if fl:
-        plain = out_d.clone()  # the flexible network runs in FP32 only: it is its own plain path
+    if fl and args.fl == "fp32":
+        plain = out_d.clone()  # the FP32 flexible network is its own plain path
+    elif fl:
+        fl32, _ = load_fl(dev, args.prefilter, api.DN_FP32)
+        plain = torch.empty_like(out_d)
+        with torch.no_grad():
+            fl32(noisy_d.view(B, H, W), pre_d.view(B, H, W), [SIGMA] * B, out=plain.view(B, H, W))
+        del fl32
     else:
         plain = api.denoise_hybrid(noisy_d, SIGMA, weights, prefilter=pf,
                                    prefilter_params=bp if nlm else api.default_bm3d_params(),
@@ -453,7 +460,8 @@ def run_ours(args):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "+".join(sorted({"f32" if bprec == api.DN_FP32 else "bf16",
-                                  "f32" if prec == api.DN_FP32 or args.net == "fl" else "bf16"})),
+                                  ("f32" if args.fl == "fp32" else "bf16") if args.net == "fl" else
+                                  ("f32" if prec == api.DN_FP32 else "bf16")})),
         "data": "synthetic (seeded piecewise-smooth + gratings + repeated tile, AWGN sigma=%g)" % SIGMA,
         "config": {"workload": workload_name(args.bm3d, args.cnn, args.prefilter, args.net), "global_batch": B * world,
                    "image": [H, W],
@@ -539,16 +547,18 @@ def load_weights(dev):
     return ResidualNet(10, 32, seed=0).to(dev).flat_weights(), "random init (He, seed 0)"
 
 
-def load_fl(dev, prefilter="bm3d"):
+def load_fl(dev, prefilter="bm3d", precision=None):
     """The flexible network with the shipped weights trained on this prefilter's
     output when present, else He init (seed 0)."""
+    from paper_2403_03488_gb300 import api
     from paper_2403_03488_gb300.flnet import FLNet
     import torch
+    prec = api.DN_FP32 if precision is None else precision
     p = os.path.join(ROOT, "paper_2403_03488_gb300", "weights", "flnet_%s.npy" % prefilter)
     if os.path.exists(p):
-        return FLNet(flat=torch.from_numpy(np.load(p).astype(np.float32))).to(dev), \
+        return FLNet(flat=torch.from_numpy(np.load(p).astype(np.float32)), precision=prec).to(dev), \
             "trained weights (" + os.path.basename(p) + ")"
-    return FLNet(seed=0).to(dev), "random init (He, seed 0)"
+    return FLNet(seed=0, precision=prec).to(dev), "random init (He, seed 0)"
 
 
 def load_traffic(kname):
@@ -674,6 +684,8 @@ def main():
     ap.add_argument("--cnn", default="bf16", choices=["fp32", "bf16"], help="CNN precision")
     ap.add_argument("--net", default="resnet", choices=["resnet", "fl"],
                     help="network after the prefilter: the 10x32 residual CNN, or the flexible U-Net of Sec. III")
+    ap.add_argument("--fl", default="fp32", choices=["fp32", "bf16"],
+                    help="flexible network: FP32 CUDA-core layers, or its contractions on the tensor cores")
     ap.add_argument("--prefilter", default="bm3d", choices=["bm3d", "nlm"],
                     help="nonlocal prefilter of the hybrid (nlm: the lighter NL-means + CNN variant)")
     ap.add_argument("--cpu-side", type=int, default=1024)
@@ -695,6 +707,8 @@ def main():
     if args.batch:
         B = args.batch
     args.warmup = max(3, args.warmup) if args.impl == "ours" else args.warmup
+    global FL_PREC
+    FL_PREC = "bf16 contractions" if args.fl == "bf16" else "fp32"
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -388,6 +388,14 @@ dn_status dn_dw3x3_bwd(const float *x, const float *g, const float *w, float *dx
  * transpose of a [Cin][Cout] weight instead (the data gradient of a Cout -> Cin layer). */
 dn_status dn_pw_fwd(const float *x, const float *w, const float *b, float *y, int N, int Cin, int Cout, int HW,
                     int relu, int transposed, dn_stream_t stream);
+/* The same two contractions on the tensor cores (tcgen05): x and w rounded
+ * to BF16, products accumulated in FP32, FP32 in and out; Cin, Cout <= 256.
+ * Per output |y - exact| <= (2^-7 + 2^-14) sum_ci |w| |x| (two roundings of
+ * unit roundoff 2^-8, FP32 accumulation). */
+dn_status dn_pw_fwd_bf16(const float *x, const float *w, const float *b, float *y, int N, int Cin, int Cout, int HW,
+                         int relu, int transposed, dn_stream_t stream);
+dn_status dn_deconv2x2_fwd_bf16(const float *x, const float *w, const float *b, const float *skip, float *y, int N,
+                                int Cin, int Cout, int H, int W, dn_stream_t stream);
 /* dw [Cout][Cin] = sum_{n,p} g[n][co][p] x[n][ci][p]; db [Cout] = sum g (NULL: skipped). */
 dn_status dn_pw_bwd_weight(const float *x, const float *g, float *dw, float *db, int N, int Cin, int Cout, int HW,
                            dn_stream_t stream);

@@ -98,6 +98,8 @@ def lib():
         "dn_cnn_grad": (i, [vp, vp, vp, i, i, i, P(CNN), vp, vp, vp, sz, vp]),
         "dn_cnn_grad_workspace_bytes": (sz, [i, i, i, P(CNN)]),
         "dn_conv3x3_tc_bwd_workspace_bytes": (sz, [i, i, i, i]),
+        "dn_pw_fwd_bf16": (i, [vp, vp, vp, vp, i, i, i, i, i, i, vp]),
+        "dn_deconv2x2_fwd_bf16": (i, [vp, vp, vp, vp, vp, i, i, i, i, i, vp]),
         "dn_conv3x3_tc_pair_fwd": (i, [vp, vp, vp, vp, vp, vp, i, i, i, i, vp, sz, vp]),
         "dn_conv3x3_tc_bwd_weight": (i, [vp, vp, vp, vp, i, i, i, i, vp, sz, vp]),
         "dn_conv3x3_tc_bwd_data": (i, [vp, vp, vp, vp, i, i, i, i, vp, sz, vp]),

@@ -503,15 +503,17 @@ def dw3x3_bwd(x, g, w, stride=1, need_dx=True, stream=None):
     return dx, dw, db
 
 
-def pw_fwd(x, w, b=None, relu=False, transposed=False, stream=None):
-    """Pointwise: x [N, Cin, H, W], w [Cout, Cin] -> [N, Cout, H, W]; transposed: w [Cin', Cout'] used as W^T."""
+def pw_fwd(x, w, b=None, relu=False, transposed=False, precision=DN_FP32, stream=None):
+    """Pointwise: x [N, Cin, H, W], w [Cout, Cin] -> [N, Cout, H, W]; transposed: w [Cin', Cout'] used as W^T.
+    precision DN_BF16: the tensor-core kernel (BF16 operands, FP32 accumulation)."""
     _need(x, "x", dim=4)
     _need(w, "w")
     N, Cin, H, W = x.shape
     Cout = w.shape[1] if transposed else w.shape[0]
     y = torch.empty(N, Cout, H, W, device=x.device)
-    check(L.lib().dn_pw_fwd(_vp(x), _vp(w), _vp(b), _vp(y), N, Cin, Cout, H * W, int(relu), int(transposed),
-                            _stream(stream)), "dn_pw_fwd")
+    fn = L.lib().dn_pw_fwd_bf16 if precision == DN_BF16 else L.lib().dn_pw_fwd
+    check(fn(_vp(x), _vp(w), _vp(b), _vp(y), N, Cin, Cout, H * W, int(relu), int(transposed), _stream(stream)),
+          "dn_pw_fwd")
     return y
 
 
@@ -528,15 +530,16 @@ def pw_bwd_weight(x, g, stream=None):
     return dw, db
 
 
-def deconv2x2_fwd(x, w, b=None, skip=None, stream=None):
-    """Transposed 2x2 conv, stride 2: x [N, Cin, H, W], w [Cin, Cout, 2, 2] -> [N, Cout, 2H, 2W] (+ skip)."""
+def deconv2x2_fwd(x, w, b=None, skip=None, precision=DN_FP32, stream=None):
+    """Transposed 2x2 conv, stride 2: x [N, Cin, H, W], w [Cin, Cout, 2, 2] -> [N, Cout, 2H, 2W] (+ skip).
+    precision DN_BF16: four tensor-core GEMMs, one per tap."""
     _need(x, "x", dim=4)
     _need(w, "w")
     N, Cin, H, W = x.shape
     Cout = w.shape[1]
     y = torch.empty(N, Cout, 2 * H, 2 * W, device=x.device)
-    check(L.lib().dn_deconv2x2_fwd(_vp(x), _vp(w), _vp(b), _vp(skip), _vp(y), N, Cin, Cout, H, W, _stream(stream)),
-          "dn_deconv2x2_fwd")
+    fn = L.lib().dn_deconv2x2_fwd_bf16 if precision == DN_BF16 else L.lib().dn_deconv2x2_fwd
+    check(fn(_vp(x), _vp(w), _vp(b), _vp(skip), _vp(y), N, Cin, Cout, H, W, _stream(stream)), "dn_deconv2x2_fwd")
     return y
 
 

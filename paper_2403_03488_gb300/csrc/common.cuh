@@ -124,6 +124,11 @@ dn_status match_tc(const float *guide, size_t plane, int B, int H, int W, const 
                    int *idx, int *n, int *err, int *fb_ws, cudaStream_t s, float *cross = nullptr, int cross_tx = 0,
                    int cross_ty = 0);
 size_t conv_tc_smem_bytes();
+// Flexible network contractions on the tensor cores (flnet_tc.cu): BF16 operands, FP32 in and out.
+dn_status pw_fwd_tc(const float *x, const float *w, const float *b, float *y, int N, int Cin, int Cout, int HW,
+                    int relu, int transposed, int *err, cudaStream_t s);
+dn_status deconv2x2_fwd_tc(const float *x, const float *w, const float *b, const float *skip, float *y, int N,
+                           int Cin, int Cout, int H, int W, int *err, cudaStream_t s);
 // Two hidden C -> C layers (bias + ReLU each) in one pass on the tensor cores (C = 32).
 dn_status conv3x3_tc_pair(const void *x, void *y, const void *wpa, const float *ba, const void *wpb, const float *bb,
                           int N, int H, int W, int C, int *err, cudaStream_t s);

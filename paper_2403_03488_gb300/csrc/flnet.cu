@@ -720,6 +720,26 @@ dn_status dn_pw_fwd(const float *x, const float *w, const float *b, float *y, in
     return launch("fl_pw_fwd", s, [&] { k_pw<<<grid, kT, 0, s>>>(x, w, b, y, N, Cin, Cout, HW, wso, wsi, relu); });
 }
 
+dn_status dn_pw_fwd_bf16(const float *x, const float *w, const float *b, float *y, int N, int Cin, int Cout, int HW,
+                         int relu, int transposed, dn_stream_t stream)
+{
+    if (!x || !w || !y || !dims_ok(N, Cin, Cout, HW)) return DN_EINVAL;
+    if (Cin > 256 || Cout > 256) return DN_EUNSUPPORTED;
+    int *err = device_error_ptr();
+    if (!err) return DN_ECUDA;
+    return pw_fwd_tc(x, w, b, y, N, Cin, Cout, HW, relu, transposed, err, (cudaStream_t)stream);
+}
+
+dn_status dn_deconv2x2_fwd_bf16(const float *x, const float *w, const float *b, const float *skip, float *y, int N,
+                                int Cin, int Cout, int H, int W, dn_stream_t stream)
+{
+    if (!x || !w || !y || !dims_ok(N, Cin, Cout, (long)H * W)) return DN_EINVAL;
+    if (Cin > 256 || Cout > 256) return DN_EUNSUPPORTED;
+    int *err = device_error_ptr();
+    if (!err) return DN_ECUDA;
+    return deconv2x2_fwd_tc(x, w, b, skip, y, N, Cin, Cout, H, W, err, (cudaStream_t)stream);
+}
+
 dn_status dn_pw_bwd_weight(const float *x, const float *g, float *dw, float *db, int N, int Cin, int Cout, int HW,
                            dn_stream_t stream)
 {

@@ -128,10 +128,11 @@ class DwFn(torch.autograd.Function):
 
 class PwFn(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, x, w, b, relu):
+    def forward(ctx, x, w, b, relu, precision=api.DN_FP32):
         x = x.contiguous()
-        y = api.pw_fwd(x, w, b, relu=relu)
+        y = api.pw_fwd(x, w, b, relu=relu, precision=precision)
         ctx.relu = bool(relu)
+        ctx.precision = precision
         ctx.save_for_backward(x, w, y)
         return y
 
@@ -141,29 +142,35 @@ class PwFn(torch.autograd.Function):
         g = g.contiguous()
         if ctx.relu:
             g = api.relu_bwd(g, y)
-        dx = api.pw_fwd(g, w, None, transposed=True) if ctx.needs_input_grad[0] else None
+        dx = api.pw_fwd(g, w, None, transposed=True, precision=ctx.precision) if ctx.needs_input_grad[0] else None
         dw, db = api.pw_bwd_weight(x, g)
-        return dx, dw, db, None
+        return dx, dw, db, None, None
 
 
 class UpFn(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, x, w, b, skip):
+    def forward(ctx, x, w, b, skip, precision=api.DN_FP32):
         x = x.contiguous()
         ctx.save_for_backward(x, w)
-        return api.deconv2x2_fwd(x, w, b, skip.contiguous())
+        return api.deconv2x2_fwd(x, w, b, skip.contiguous(), precision=precision)
 
     @staticmethod
     def backward(ctx, g):
         x, w = ctx.saved_tensors
         g = g.contiguous()
         dx, dw, db = api.deconv2x2_bwd(x, g, w, need_dx=ctx.needs_input_grad[0])
-        return dx, dw, db, g
+        return dx, dw, db, g, None
 
 
 class FLNet(torch.nn.Module):
-    def __init__(self, widths=WIDTHS, seed=0, flat: torch.Tensor = None):
+    """precision DN_FP32: every layer on the FP32 CUDA-core kernels; DN_BF16:
+    the pointwise layers (forward and data gradient) and the transposed 2x2
+    convolutions on the tensor cores (BF16 operands, FP32 accumulation, FP32
+    activations), the depthwise layers and the weight gradients in FP32."""
+
+    def __init__(self, widths=WIDTHS, seed=0, flat: torch.Tensor = None, precision=api.DN_FP32):
         super().__init__()
+        self.precision = precision
         self.widths = tuple(widths)
         self.shapes = param_shapes(self.widths)
         self.offsets = []
@@ -199,7 +206,7 @@ class FLNet(torch.nn.Module):
             nonlocal i
             dw_w, dw_b, pw_w, pw_b = P[i:i + 4]
             i += 4
-            return PwFn.apply(DwFn.apply(h, dw_w, dw_b, s), pw_w, pw_b, True)
+            return PwFn.apply(DwFn.apply(h, dw_w, dw_b, s), pw_w, pw_b, True, self.precision)
 
         h = ds(ds(api.fl_pack_input(pre.contiguous(), noisy.contiguous(), sigma), 1), 1)
         e = [h]
@@ -207,10 +214,10 @@ class FLNet(torch.nn.Module):
             h = ds(ds(h, 2), 1)
             e.append(h)
         for k in range(4, 0, -1):  # decoders: up to level k-1, add its encoder output, a block
-            h = UpFn.apply(h, P[i], P[i + 1], e[k - 1])
+            h = UpFn.apply(h, P[i], P[i + 1], e[k - 1], self.precision)
             i += 2
             h = ds(h, 1)
-        r = PwFn.apply(h, P[i], P[i + 1], False)
+        r = PwFn.apply(h, P[i], P[i + 1], False, self.precision)
         return r[:, 0]
 
     def forward(self, noisy, pre, sigma, out=None):

@@ -165,3 +165,81 @@ def test_short_training_lowers_the_loss():
     assert np.isfinite(losses).all()
     assert np.mean(losses[-10:]) < 0.8 * np.mean(losses[:5]), (losses[:5], losses[-10:])
     assert A().device_error() == 0
+
+
+# ---- the tensor-core (BF16 operand) contractions -------------------------------------
+# Each output of a pointwise or transposed-convolution layer is a sum of
+# products w x with both factors rounded to BF16 (unit roundoff 2^-8) and the
+# products accumulated in FP32: |y - exact| <= (2^-7 + 2^-14) sum |w| |x|.
+
+def _bf16_bound(absprod):
+    return (2.0 ** -7 + 2.0 ** -14) * absprod + 1e-6
+
+
+@pytest.mark.parametrize("cin,cout,shape,transposed", [(3, 48, (2, 37, 50), False), (48, 48, (1, 64, 128), False),
+                                                       (192, 96, (2, 16, 30), False), (96, 192, (1, 33, 70), True),
+                                                       (48, 1, (3, 20, 20), False), (128, 192, (1, 8, 8), False),
+                                                       (64, 48, (1, 9, 7), True)])
+def test_pointwise_bf16_within_bound(cin, cout, shape, transposed):
+    import torch.nn.functional as F
+    rng = np.random.default_rng(cin * 7 + cout)
+    N, H, W = shape
+    x = rng.normal(0, 1, (N, cin, H, W)).astype(np.float32)
+    w = (rng.normal(0, 1, (cin, cout) if transposed else (cout, cin)) / np.sqrt(cin)).astype(np.float32)
+    b = rng.normal(0, 0.1, cout).astype(np.float32)
+    for relu in (False, True):
+        y = host(A().pw_fwd(dev(x), dev(w), dev(b), relu=relu, transposed=transposed, precision=A().DN_BF16))
+        wm = (w.T if transposed else w).astype(np.float64)
+        t = lambda a, ww: F.conv2d(torch.as_tensor(a, dtype=torch.float64), torch.as_tensor(ww)[:, :, None, None])
+        ref = t(x, wm).numpy() + b[None, :, None, None]
+        bound = _bf16_bound(t(np.abs(x), np.abs(wm)).numpy())
+        if relu:
+            ref = np.maximum(ref, 0.0)
+        assert np.all(np.abs(y - ref) <= bound), np.abs(y - ref).max()
+    assert A().device_error() == 0
+
+
+@pytest.mark.parametrize("cin,cout,shape", [(192, 128, (2, 8, 8)), (64, 48, (1, 33, 40)), (96, 64, (2, 16, 22))])
+def test_transposed_convolution_bf16_within_bound(cin, cout, shape):
+    import torch.nn.functional as F
+    rng = np.random.default_rng(cin + cout)
+    N, H, W = shape
+    x = rng.normal(0, 1, (N, cin, H, W)).astype(np.float32)
+    w = (rng.normal(0, 1, (cin, cout, 2, 2)) / np.sqrt(cin)).astype(np.float32)
+    b = rng.normal(0, 0.1, cout).astype(np.float32)
+    skip = rng.normal(0, 1, (N, cout, 2 * H, 2 * W)).astype(np.float32)
+    y = host(A().deconv2x2_fwd(dev(x), dev(w), dev(b), dev(skip), precision=A().DN_BF16))
+    t = lambda a, ww: F.conv_transpose2d(torch.as_tensor(a, dtype=torch.float64), torch.as_tensor(ww, dtype=torch.float64),
+                                         stride=2).numpy()
+    ref = t(x, w) + b[None, :, None, None] + skip
+    assert np.all(np.abs(y - ref) <= _bf16_bound(t(np.abs(x), np.abs(w))))
+    assert A().device_error() == 0
+
+
+def test_network_bf16_close_to_oracle_and_fp32():
+    """The trained network with its contractions on the tensor cores against
+    the FP64 oracle.  Its ~20 contractions each round activations of up to a
+    few hundred times the residual's size to BF16, so the bound is stated on
+    the intensity scale, not relative to the (small) residual: every output
+    within one grey level of the oracle's, and PSNR within 0.05 dB of the
+    oracle's and of the FP32 path's on synthetic scenes."""
+    import os
+    import oracle
+    from paper_2403_03488_gb300 import synth
+    from paper_2403_03488_gb300.flnet import FLNet
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    wf = os.path.join(root, "paper_2403_03488_gb300", "weights", "flnet_bm3d.npy")
+    flat = torch.from_numpy(np.load(wf).astype(np.float32)) if os.path.exists(wf) else None
+    fp32 = (FLNet(flat=flat) if flat is not None else FLNet(seed=0)).cuda()
+    bf16 = FLNet(flat=fp32.flat.detach().cpu(), precision=A().DN_BF16).cuda()
+    clean, noisy = synth.make_batch([71, 72], 96, 160, 25.0)
+    pre = (clean[:, 0] + np.random.default_rng(3).normal(0, 4, clean[:, 0].shape)).astype(np.float32)
+    with torch.no_grad():
+        o16 = host(bf16(dev(noisy[:, 0]), dev(pre), [25.0, 25.0]))
+        o32 = host(fp32(dev(noisy[:, 0]), dev(pre), [25.0, 25.0]))
+    ref = oracle.fl_forward(noisy[:, 0], pre, [25.0, 25.0], fp32.numpy_params())
+    assert np.abs(o16 - ref).max() <= 1.0, np.abs(o16 - ref).max()
+    for k in range(2):
+        assert abs(oracle.psnr(o16[k], clean[k, 0]) - oracle.psnr(o32[k], clean[k, 0])) <= 0.05
+        assert abs(oracle.psnr(o16[k], clean[k, 0]) - oracle.psnr(ref[k], clean[k, 0])) <= 0.05
+    assert A().device_error() == 0
