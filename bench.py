@@ -187,6 +187,7 @@ def algorithmic(kernel, launches_per_step, batch, hw=None):
     px = H * W * batch  # every launch of these kernels covers the whole batch
     hbm_bytes = {
         "conv3x3_tc_bf16": 2 * px * 32 * 2,   # NHWC BF16 activations in and out
+        "conv3x3_tc_pair_bf16": 2 * px * 32 * 2,  # two layers per launch: in and out once
         "conv_first_bf16": px * (8 + 64),     # prefilter + noisy FP32 in, 32 BF16 channels out
         "conv_last_bf16": px * (64 + 4 + 4),  # 32 BF16 channels + prefilter in, FP32 out
         "bm3d_normalize": px * (4 * 8 + 4),   # four 64-bit fixed-point planes in, FP32 out
@@ -199,6 +200,9 @@ def algorithmic(kernel, launches_per_step, batch, hw=None):
         wpp, px = work_per_pixel(), H * W * batch / launches_per_step
         if kernel.startswith("fl_dw3x3_fwd"):  # 9 MAC per output: moves bytes, not FLOPs
             return "hbm", "GB/s", wpp["dw_bytes"] * px, hbm, "measured hbm_gbs"
+        if kernel.endswith("_tc"):  # tensor-core contractions of FP32 planes: the planes' bytes bound them
+            return "hbm", "GB/s", wpp["pw_bytes" if kernel.startswith("fl_pw") else "up_bytes"] * px, hbm, \
+                "measured hbm_gbs"
         macs = wpp["pw_macs"] if kernel.startswith("fl_pw_fwd") else wpp["up_macs"]
         return "alu", "TFLOP/s", 2.0 * macs * px, fpk, fnote
     # fall back to bytes: read + write of the image planes
@@ -220,14 +224,21 @@ def kernel_rooflines(res, steps, batch, hw=None):
         peaks = json.load(open(p))
     for k, (n, ms) in res.items():
         if not k.startswith(("bm3d_match_fp32", "bm3d_match_pre", "bm3d_match_tc", "bm3d_filter_", "nlm_fp32",
-                             "fl_pw_fwd", "fl_deconv2x2_fwd", "fl_dw3x3_fwd", "conv3x3_tc_bf16", "conv_first_bf16",
-                             "conv_last_bf16", "bm3d_normalize", "error_reduce_fp64")):
+                             "fl_pw_fwd", "fl_deconv2x2_fwd", "fl_dw3x3_fwd", "conv3x3_tc_bf16", "conv3x3_tc_pair",
+                             "conv_first_bf16", "conv_last_bf16", "bm3d_normalize", "error_reduce_fp64")):
             continue
         avg = ms / n
         bound, unit, work, peak, _ = algorithmic(k, n / steps, batch, hw)
         ach = work / (avg / 1e3) / (1e12 if unit == "TFLOP/s" else 1e9)
         out[k] = {"bound": bound, "achieved": round(ach, 3 if unit == "TFLOP/s" else 1), "peak": round(peak, 1),
-                  "unit": unit, "frac": round(ach / peak, 4), "avg_launch_ms": round(avg, 4)}
+                  "unit": unit, "frac": round(ach / peak, 4), "avg_launch_ms": round(avg, 4),
+                  "traffic": load_traffic(k)}
+        if k.startswith(("conv3x3_tc_bf16", "conv3x3_tc_pair")):
+            nl = 2 if "pair" in k else 1  # hidden 32 -> 32 layers per launch, 2 * 9 * 32 * 32 FLOP per pixel each
+            t_ach = nl * 2.0 * 9 * 32 * 32 * H * W * batch / (avg / 1e3) / 1e12
+            bf = peaks.get("bf16_tflops_sustained", 1700.0)
+            out[k].update({"tensor_achieved": round(t_ach, 3), "tensor_peak": round(bf, 1),
+                           "tensor_frac": round(t_ach / bf, 4)})
         if k.startswith("bm3d_filter_") and k.endswith("fp32"):
             tensor, _ = filter_work("wiener" in k, H, W, batch)
             t_ach = tensor / (avg / 1e3) / 1e12

@@ -80,7 +80,7 @@ def work_per_pixel(widths=WIDTHS):
     kind: multiply-adds of the depthwise, pointwise (output layer included) and
     transposed layers, and the FP32 bytes the depthwise layers must move (input
     plane read once, output plane written once)."""
-    w = {"dw_macs": 0.0, "pw_macs": 0.0, "up_macs": 0.0, "dw_bytes": 0.0}
+    w = {"dw_macs": 0.0, "pw_macs": 0.0, "up_macs": 0.0, "dw_bytes": 0.0, "pw_bytes": 0.0, "up_bytes": 0.0}
     level = 0
     for kind, cin, cout, s in layer_specs(widths):
         if kind == "ds":
@@ -88,12 +88,16 @@ def work_per_pixel(widths=WIDTHS):
             w["dw_macs"] += 9 * cin / 4 ** lo
             w["pw_macs"] += cin * cout / 4 ** lo
             w["dw_bytes"] += 4 * cin / 4 ** level + 4 * cin / 4 ** lo
+            w["pw_bytes"] += 4 * (cin + cout) / 4 ** lo
             level = lo
         elif kind == "up":
+            # input plane of the coarser level read, output and skip planes of the finer level
+            w["up_bytes"] += 4 * cin / 4 ** level + 2 * 4 * cout / 4 ** (level - 1)
             level -= 1
             w["up_macs"] += cin * cout / 4 ** level
         else:
             w["pw_macs"] += cin * cout / 4 ** level
+            w["pw_bytes"] += 4 * (cin + cout) / 4 ** level
     return w
 
 
