@@ -49,10 +49,13 @@ def lib():
         up = ctypes.POINTER(ctypes.c_ubyte)
         i, d = ctypes.c_int, ctypes.c_double
         L.or_dct8.argtypes = [dp]
+        L.or_dct.argtypes = [i, dp]
         L.or_dct2d_matrix.argtypes = [dp]
+        L.or_dct2d_matrix_k.argtypes = [i, dp]
         L.or_hadamard.argtypes = [i, dp]
         L.or_kaiser.argtypes = [i, d, dp]
         L.or_t3d.argtypes = [dp, i, i, dp]
+        L.or_t3d_k.argtypes = [dp, i, i, i, dp]
         L.or_grid.argtypes = [i, i, i, ip]
         L.or_match.argtypes = [dp, i, i, i, i, i, i, d, ip, dp, ip, ip, up]
         L.or_match_pre.argtypes = [dp, i, i, i, i, i, i, d, d, d, d, d, ip, dp, ip, ip, up]
@@ -96,9 +99,20 @@ def dct8() -> np.ndarray:
     return C
 
 
-def dct2d_matrix() -> np.ndarray:
-    T = np.empty((64, 64))
-    lib().or_dct2d_matrix(_dp(T))
+def dct(k: int) -> np.ndarray:
+    """Orthonormal DCT-II matrix of size k (rows = frequencies)."""
+    C = np.empty((k, k))
+    lib().or_dct(k, _dp(C))
+    return C
+
+
+def dct2d_matrix(k: int = 8) -> np.ndarray:
+    """The 2D DCT of a k x k patch as a k^2 x k^2 matrix on the row-major patch."""
+    T = np.empty((k * k, k * k))
+    if k == 8:
+        lib().or_dct2d_matrix(_dp(T))
+    else:
+        lib().or_dct2d_matrix_k(k, _dp(T))
     return T
 
 
@@ -116,11 +130,17 @@ def kaiser(M: int, beta: float) -> np.ndarray:
 
 
 def t3d(G: np.ndarray, inverse: bool = False) -> np.ndarray:
-    """3D transform of a group G [n, 64] (2D DCT per patch, Hadamard along n)."""
+    """3D transform of a group G [n, k*k] (2D DCT per k x k patch, Hadamard
+    along n); k = 8 for 64 columns."""
     G = _f64(G)
     Z = np.empty_like(G)
-    if lib().or_t3d(_dp(G), G.shape[0], int(inverse), _dp(Z)):
-        raise ValueError("bad group size")
+    k = int(round(np.sqrt(G.shape[1])))
+    if k * k != G.shape[1]:
+        raise ValueError("patches must be square")
+    rc = (lib().or_t3d(_dp(G), G.shape[0], int(inverse), _dp(Z)) if k == 8
+          else lib().or_t3d_k(_dp(G), G.shape[0], k, int(inverse), _dp(Z)))
+    if rc:
+        raise ValueError("bad group or patch size")
     return Z
 
 

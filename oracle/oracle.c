@@ -12,7 +12,9 @@
  * (BM3D: Dabov et al. 2007; NL-means: Buades et al. 2005) with the
  * parameters of the workloads this library is checked on.  Every step is
  * plain and slow on purpose: exhaustive matching with a full sort, the 2D
- * transform as an explicit 64x64 Kronecker matrix, the group transform as an
+ * transform as an explicit k^2 x k^2 Kronecker matrix (k = the patch side,
+ * 8 by default, up to 16 for the larger patches of the high-noise profile), the
+ * group transform as an
  * explicit Hadamard matrix, aggregation by direct accumulation, convolution
  * by a 7-deep loop.
  *
@@ -27,37 +29,46 @@
 #include <omp.h>
 #endif
 
-#define OR_K 8          /* BM3D patch side; the 2D transform is 8x8 */
-#define OR_K2 64
+#define OR_K 8          /* default BM3D patch side */
+#define OR_KMIN 4       /* patch sides accepted: OR_KMIN .. OR_KMAX */
+#define OR_KMAX 16
 #define OR_NMAX 64      /* largest group size accepted */
 
 /* ------------------------------------------------------------------ */
 /* Transforms and windows                                              */
 /* ------------------------------------------------------------------ */
 
-/* Orthonormal DCT-II matrix: C[u][m] = a_u cos(pi (2m+1) u / 16),
- * a_0 = sqrt(1/8), a_u = sqrt(2/8) = 1/2. */
-void or_dct8(double *C)
+/* Orthonormal DCT-II matrix of size k: C[u][m] = a_u cos(pi (2m+1) u / (2k)),
+ * a_0 = sqrt(1/k), a_u = sqrt(2/k). */
+void or_dct(int k, double *C)
 {
-    for (int u = 0; u < OR_K; ++u)
-        for (int m = 0; m < OR_K; ++m) {
-            double a = (u == 0) ? sqrt(1.0 / OR_K) : sqrt(2.0 / OR_K);
-            C[u * OR_K + m] = a * cos(M_PI * (2.0 * m + 1.0) * u / (2.0 * OR_K));
+    for (int u = 0; u < k; ++u)
+        for (int m = 0; m < k; ++m) {
+            double a = (u == 0) ? sqrt(1.0 / k) : sqrt(2.0 / k);
+            C[u * k + m] = a * cos(M_PI * (2.0 * m + 1.0) * u / (2.0 * k));
         }
 }
 
-/* 2D DCT as one 64x64 matrix acting on vec(P) (row-major, index i*8+j):
- * T[u*8+v][i*8+j] = C[u][i] C[v][j], i.e. vec(C P C^T) = T vec(P). */
-void or_dct2d_matrix(double *T)
+void or_dct8(double *C) { or_dct(OR_K, C); }
+
+/* 2D DCT of a k x k patch as one k^2 x k^2 matrix acting on vec(P)
+ * (row-major, index i*k+j): T[u*k+v][i*k+j] = C[u][i] C[v][j], i.e.
+ * vec(C P C^T) = T vec(P). */
+void or_dct2d_matrix_k(int k, double *T)
 {
-    double C[OR_K2];
-    or_dct8(C);
-    for (int u = 0; u < OR_K; ++u)
-        for (int v = 0; v < OR_K; ++v)
-            for (int i = 0; i < OR_K; ++i)
-                for (int j = 0; j < OR_K; ++j)
-                    T[(u * OR_K + v) * OR_K2 + i * OR_K + j] = C[u * OR_K + i] * C[v * OR_K + j];
+    const int k2 = k * k;
+    double C[OR_KMAX * OR_KMAX];
+    or_dct(k, C);
+    for (int u = 0; u < k; ++u)
+        for (int v = 0; v < k; ++v)
+            for (int i = 0; i < k; ++i)
+                for (int j = 0; j < k; ++j)
+                    T[(size_t)(u * k + v) * k2 + i * k + j] = C[u * k + i] * C[v * k + j];
 }
+
+void or_dct2d_matrix(double *T) { or_dct2d_matrix_k(OR_K, T); }
+
+static int patch_ok(int k) { return k >= OR_KMIN && k <= OR_KMAX; }
 
 /* Sylvester Hadamard matrix in natural order, scaled by 1/sqrt(n)
  * (orthonormal and symmetric).  n must be a power of two. */
@@ -99,53 +110,65 @@ void or_kaiser(int M, double beta, double *w)
     }
 }
 
-/* 3D transform of a group G[n][64]: Z = H_n (G T^T), i.e. the 2D DCT of
- * every patch followed by the normalised Hadamard transform along the group. */
-static void t3d_forward(const double *T, const double *Hn, int n, const double *G, double *Z)
+/* 3D transform of a group G[n][k2] (k2 = k^2 pixels per patch): Z = H_n (G T^T),
+ * i.e. the 2D DCT of every patch followed by the normalised Hadamard
+ * transform along the group.  T2: scratch of n * k2 doubles. */
+static void t3d_forward(const double *T, const double *Hn, int n, int k2, const double *G, double *Z, double *T2)
 {
-    double T2[OR_NMAX * OR_K2];
     for (int k = 0; k < n; ++k)
-        for (int a = 0; a < OR_K2; ++a) {
+        for (int a = 0; a < k2; ++a) {
             double s = 0.0;
-            for (int b = 0; b < OR_K2; ++b) s += T[a * OR_K2 + b] * G[k * OR_K2 + b];
-            T2[k * OR_K2 + a] = s;
+            for (int b = 0; b < k2; ++b) s += T[(size_t)a * k2 + b] * G[k * k2 + b];
+            T2[k * k2 + a] = s;
         }
     for (int m = 0; m < n; ++m)
-        for (int a = 0; a < OR_K2; ++a) {
+        for (int a = 0; a < k2; ++a) {
             double s = 0.0;
-            for (int k = 0; k < n; ++k) s += Hn[m * n + k] * T2[k * OR_K2 + a];
-            Z[m * OR_K2 + a] = s;
+            for (int k = 0; k < n; ++k) s += Hn[m * n + k] * T2[k * k2 + a];
+            Z[m * k2 + a] = s;
         }
 }
 
 /* Inverse of t3d_forward (both factors are orthonormal): G = T^T (H_n^T Z). */
-static void t3d_inverse(const double *T, const double *Hn, int n, const double *Z, double *G)
+static void t3d_inverse(const double *T, const double *Hn, int n, int k2, const double *Z, double *G, double *T2)
 {
-    double T2[OR_NMAX * OR_K2];
     for (int k = 0; k < n; ++k)
-        for (int a = 0; a < OR_K2; ++a) {
+        for (int a = 0; a < k2; ++a) {
             double s = 0.0;
-            for (int m = 0; m < n; ++m) s += Hn[m * n + k] * Z[m * OR_K2 + a];
-            T2[k * OR_K2 + a] = s;
+            for (int m = 0; m < n; ++m) s += Hn[m * n + k] * Z[m * k2 + a];
+            T2[k * k2 + a] = s;
         }
     for (int k = 0; k < n; ++k)
-        for (int b = 0; b < OR_K2; ++b) {
+        for (int b = 0; b < k2; ++b) {
             double s = 0.0;
-            for (int a = 0; a < OR_K2; ++a) s += T[a * OR_K2 + b] * T2[k * OR_K2 + a];
-            G[k * OR_K2 + b] = s;
+            for (int a = 0; a < k2; ++a) s += T[(size_t)a * k2 + b] * T2[k * k2 + a];
+            G[k * k2 + b] = s;
         }
 }
 
-/* Exported for the transform pins. */
-int or_t3d(const double *G, int n, int inverse, double *Z)
+/* Exported for the transform pins: the 3D transform of n patches of side k. */
+int or_t3d_k(const double *G, int n, int k, int inverse, double *Z)
 {
-    double T[OR_K2 * OR_K2], Hn[OR_NMAX * OR_NMAX];
+    if (!patch_ok(k)) return -1;
+    const int k2 = k * k;
+    double Hn[OR_NMAX * OR_NMAX];
     if (or_hadamard(n, Hn)) return -1;
-    or_dct2d_matrix(T);
-    if (inverse) t3d_inverse(T, Hn, n, G, Z);
-    else t3d_forward(T, Hn, n, G, Z);
+    double *T = (double *)malloc(sizeof(double) * (size_t)k2 * k2);
+    double *T2 = (double *)malloc(sizeof(double) * (size_t)n * k2);
+    if (!T || !T2) {
+        free(T);
+        free(T2);
+        return -2;
+    }
+    or_dct2d_matrix_k(k, T);
+    if (inverse) t3d_inverse(T, Hn, n, k2, G, Z, T2);
+    else t3d_forward(T, Hn, n, k2, G, Z, T2);
+    free(T);
+    free(T2);
     return 0;
 }
+
+int or_t3d(const double *G, int n, int inverse, double *Z) { return or_t3d_k(G, n, OR_K, inverse, Z); }
 
 /* ------------------------------------------------------------------ */
 /* Block matching                                                      */
@@ -202,7 +225,7 @@ static int pow2_floor(int v)
 int or_match(const double *g, int H, int W, int k, int step, int search, int n2, double tau,
              int *idx, double *dist, int *nkept, int *ngroup, unsigned char *flag)
 {
-    if (k != OR_K || H < k || W < k || search < 1 || (search & 1) == 0 || n2 < 1 || n2 > OR_NMAX)
+    if (!patch_ok(k) || H < k || W < k || search < 1 || (search & 1) == 0 || n2 < 1 || n2 > OR_NMAX)
         return -1;
     int gy[4096], gx[4096];
     int Ry = or_grid(H, k, step, gy), Rx = or_grid(W, k, step, gx);
@@ -265,7 +288,7 @@ int or_match(const double *g, int H, int W, int k, int step, int search, int n2,
  * ordering, group size and outputs as or_match.  Two distances a, b count as
  * tied when |a - b| <= rtie max(a, b) + atie (sqrt(a) + sqrt(b)): an error
  * of at most delta on each coefficient difference moves a distance d by at
- * most 2 delta sqrt(d) (Cauchy-Schwarz over the 64 terms), so atie = 2 delta
+ * most 2 delta sqrt(d) (Cauchy-Schwarz over the k^2 terms), so atie = 2 delta
  * covers coefficients computed in lower precision.  Flags:
  *   OR_FLAG_TAU  a candidate tied with tau;
  *   OR_FLAG_TIE  two ranked neighbours (up to the group cut) tied;
@@ -275,42 +298,51 @@ int or_match(const double *g, int H, int W, int k, int step, int search, int n2,
  *                reach the group: its smallest possible distance is <= the
  *                distance of the last listed candidate (of tau while at most
  *                n2 candidates are kept, when one more or one fewer changes
- *                the group size). */
+ *                the group size).
+ * Patches of any side k in OR_KMIN .. OR_KMAX (the 2D DCT of size k). */
 int or_match_pre(const double *g, int H, int W, int k, int step, int search, int n2, double tau, double thr,
                  double band, double rtie, double atie, int *idx, double *dist, int *nkept, int *ngroup,
                  unsigned char *flag)
 {
-    if (k != OR_K || H < k || W < k || search < 1 || (search & 1) == 0 || n2 < 1 || n2 > OR_NMAX || thr < 0.0)
+    if (!patch_ok(k) || H < k || W < k || search < 1 || (search & 1) == 0 || n2 < 1 || n2 > OR_NMAX || thr < 0.0)
         return -1;
     int gy[4096], gx[4096];
     int Ry = or_grid(H, k, step, gy), Rx = or_grid(W, k, step, gx);
     if (Ry > 4096 || Rx > 4096) return -1;
     const int Hp = H - k + 1, Wp = W - k + 1;
     const size_t np = (size_t)Hp * Wp;
-    double *Y = (double *)malloc(sizeof(double) * np * OR_K2);     /* prethresholded coefficients */
-    double *A = (double *)malloc(sizeof(double) * np * OR_K2);     /* value under the other decision */
-    unsigned char *hz = (unsigned char *)malloc(np);               /* patch has a coefficient in the band */
-    if (!Y || !A || !hz) return -2;
-    double T[OR_K2 * OR_K2];
-    or_dct2d_matrix(T);
+    const int k2 = k * k;
+    double *Y = (double *)malloc(sizeof(double) * np * k2);     /* prethresholded coefficients */
+    double *A = (double *)malloc(sizeof(double) * np * k2);     /* value under the other decision */
+    unsigned char *hz = (unsigned char *)malloc(np);            /* patch has a coefficient in the band */
+    double *T = (double *)malloc(sizeof(double) * (size_t)k2 * k2);
+    if (!Y || !A || !hz || !T) {
+        free(Y);
+        free(A);
+        free(hz);
+        free(T);
+        return -2;
+    }
+    or_dct2d_matrix_k(k, T);
 #pragma omp parallel for schedule(static)
     for (long q = 0; q < (long)np; ++q) {
         int y = (int)(q / Wp), x = (int)(q % Wp);
-        double P[OR_K2];
-        for (int i = 0; i < OR_K; ++i)
-            for (int j = 0; j < OR_K; ++j) P[i * OR_K + j] = g[(size_t)(y + i) * W + x + j];
+        double P[OR_KMAX * OR_KMAX];
+        for (int i = 0; i < k; ++i)
+            for (int j = 0; j < k; ++j) P[i * k + j] = g[(size_t)(y + i) * W + x + j];
         unsigned char h = 0;
-        for (int a = 0; a < OR_K2; ++a) {
+        for (int a = 0; a < k2; ++a) {
             double c = 0.0;
-            for (int m = 0; m < OR_K2; ++m) c += T[a * OR_K2 + m] * P[m];
+            for (int m = 0; m < k2; ++m) c += T[(size_t)a * k2 + m] * P[m];
             int keep = fabs(c) > thr;
             int near = fabs(fabs(c) - thr) <= band;
-            Y[(size_t)q * OR_K2 + a] = keep ? c : 0.0;
-            A[(size_t)q * OR_K2 + a] = near ? (keep ? 0.0 : c) : (keep ? c : 0.0);
+            Y[(size_t)q * k2 + a] = keep ? c : 0.0;
+            A[(size_t)q * k2 + a] = near ? (keep ? 0.0 : c) : (keep ? c : 0.0);
             h |= (unsigned char)near;
         }
         hz[q] = h;
     }
+    free(T);
     int hs = search / 2;
     int ncand_max = search * search;
     int fail = 0;
@@ -323,7 +355,7 @@ int or_match_pre(const double *g, int H, int W, int k, int step, int search, int
         for (int r = 0; r < Ry * Rx; ++r) {
             if (fail) continue;
             int y0 = gy[r / Rx], x0 = gx[r % Rx];
-            const double *yr = Y + ((size_t)y0 * Wp + x0) * OR_K2;
+            const double *yr = Y + ((size_t)y0 * Wp + x0) * k2;
             int nc = 0, nh = 0;
             unsigned char fl = hz[(size_t)y0 * Wp + x0] ? OR_FLAG_PRE : 0;
             int ylo = y0 - hs < 0 ? 0 : y0 - hs, yhi = y0 + hs > H - k ? H - k : y0 + hs;
@@ -332,9 +364,9 @@ int or_match_pre(const double *g, int H, int W, int k, int step, int search, int
                 for (int x = xlo; x <= xhi; ++x) {
                     if (y == y0 && x == x0) continue;
                     size_t q = (size_t)y * Wp + x;
-                    const double *yq = Y + q * OR_K2, *aq = A + q * OR_K2;
+                    const double *yq = Y + q * k2, *aq = A + q * k2;
                     double s = 0.0, slo = 0.0;
-                    for (int a = 0; a < OR_K2; ++a) {
+                    for (int a = 0; a < k2; ++a) {
                         double e = yr[a] - yq[a], f = yr[a] - aq[a];
                         s += e * e;
                         slo += (e * e < f * f) ? e * e : f * f;
@@ -408,13 +440,13 @@ static void acc_finish(acc_t *a, size_t plane, double *out)
 }
 
 /* Mark every pixel covered by the group's patches. */
-static void mark_group(unsigned char *pxflag, int W, const int *I, int n, unsigned char bits)
+static void mark_group(unsigned char *pxflag, int W, int k, const int *I, int n, unsigned char bits)
 {
     if (!pxflag) return;
     for (int t = 0; t < n; ++t) {
         int y = I[t] / W, x = I[t] % W;
-        for (int i = 0; i < OR_K; ++i)
-            for (int j = 0; j < OR_K; ++j) {
+        for (int i = 0; i < k; ++i)
+            for (int j = 0; j < k; ++j) {
                 unsigned char *p = &pxflag[(size_t)(y + i) * W + x + j];
 #pragma omp atomic
                 *p |= bits;
@@ -436,7 +468,7 @@ int or_bm3d_pass1(const double *img, int C, int H, int W, const double *sig,
                   double band, double thr2d, double band2d, double *basic, unsigned char *pxflag,
                   unsigned char *gflag)
 {
-    if (C < 1 || k != OR_K) return -1;
+    if (C < 1 || !patch_ok(k)) return -1;
     int Ry = or_grid(H, k, step, NULL), Rx = or_grid(W, k, step, NULL);
     int R = Ry * Rx;
     if (R <= 0) return -1;
@@ -452,9 +484,11 @@ int or_bm3d_pass1(const double *img, int C, int H, int W, const double *sig,
                     : or_match(img, H, W, k, step, search, n2, tau, idx, dist, nk, ng, fl))
         return -1;
 
-    double T[OR_K2 * OR_K2], kw[OR_K];
-    or_dct2d_matrix(T);
-    or_kaiser(OR_K, beta, kw);
+    const int k2 = k * k;
+    double *T = (double *)malloc(sizeof(double) * (size_t)k2 * k2), kw[OR_KMAX];
+    if (!T) return -2;
+    or_dct2d_matrix_k(k, T);
+    or_kaiser(k, beta, kw);
     size_t HW = (size_t)H * W, plane = (size_t)C * HW;
     if (pxflag) memset(pxflag, 0, HW);
     acc_t acc;
@@ -467,7 +501,10 @@ int or_bm3d_pass1(const double *img, int C, int H, int W, const double *sig,
         tid = omp_get_thread_num();
 #endif
         double *num = acc.acc + (size_t)tid * plane * 2, *den = num + plane;
-        double G[OR_NMAX * OR_K2], Z[OR_NMAX * OR_K2], E[OR_NMAX * OR_K2], Hn[OR_NMAX * OR_NMAX];
+        /* group, coefficients, estimate and transform scratch: OR_NMAX patches each */
+        double *G = (double *)malloc(sizeof(double) * 4 * OR_NMAX * (size_t)k2);
+        double *Z = G + OR_NMAX * k2, *E = Z + OR_NMAX * k2, *S = E + OR_NMAX * k2;
+        double Hn[OR_NMAX * OR_NMAX];
 #pragma omp for schedule(static)
         for (int r = 0; r < R; ++r) {
             int n = ng[r];
@@ -479,36 +516,37 @@ int or_bm3d_pass1(const double *img, int C, int H, int W, const double *sig,
                 double thr = lambda3d * sig[c];
                 for (int t = 0; t < n; ++t) {
                     int y = I[t] / W, x = I[t] % W;
-                    for (int i = 0; i < OR_K; ++i)
-                        for (int j = 0; j < OR_K; ++j)
-                            G[t * OR_K2 + i * OR_K + j] = ch[(size_t)(y + i) * W + x + j];
+                    for (int i = 0; i < k; ++i)
+                        for (int j = 0; j < k; ++j)
+                            G[t * k2 + i * k + j] = ch[(size_t)(y + i) * W + x + j];
                 }
-                t3d_forward(T, Hn, n, G, Z);
+                t3d_forward(T, Hn, n, k2, G, Z, S);
                 int nhar = 0;
-                for (int a = 0; a < n * OR_K2; ++a) {
+                for (int a = 0; a < n * k2; ++a) {
                     double m = fabs(Z[a]);
                     if (fabs(m - thr) <= 1e-5 * thr + band) f |= OR_FLAG_THR;
                     if (m > thr) ++nhar; else Z[a] = 0.0;
                 }
-                t3d_inverse(T, Hn, n, Z, E);
+                t3d_inverse(T, Hn, n, k2, Z, E, S);
                 double w = nhar > 0 ? 1.0 / (sig[c] * sig[c] * nhar) : 1.0;
                 for (int t = 0; t < n; ++t) {
                     int y = I[t] / W, x = I[t] % W;
-                    for (int i = 0; i < OR_K; ++i)
-                        for (int j = 0; j < OR_K; ++j) {
+                    for (int i = 0; i < k; ++i)
+                        for (int j = 0; j < k; ++j) {
                             size_t p = (size_t)c * HW + (size_t)(y + i) * W + x + j;
                             double kk = w * kw[i] * kw[j];
-                            num[p] += kk * E[t * OR_K2 + i * OR_K + j];
+                            num[p] += kk * E[t * k2 + i * k + j];
                             den[p] += kk;
                         }
                 }
             }
             if (gflag) gflag[r] = f;
-            if (f) mark_group(pxflag, W, I, n, f);
+            if (f) mark_group(pxflag, W, k, I, n, f);
         }
+        free(G);
     }
     acc_finish(&acc, plane, basic);
-    free(idx); free(dist); free(nk); free(ng); free(fl);
+    free(T); free(idx); free(dist); free(nk); free(ng); free(fl);
     return 0;
 }
 
@@ -521,7 +559,7 @@ int or_bm3d_pass2(const double *noisy, const double *basic, int C, int H, int W,
                   int k, int step, int search, int n2, double tau, double beta,
                   double *out, unsigned char *pxflag, unsigned char *gflag)
 {
-    if (C < 1 || k != OR_K) return -1;
+    if (C < 1 || !patch_ok(k)) return -1;
     int Ry = or_grid(H, k, step, NULL), Rx = or_grid(W, k, step, NULL);
     int R = Ry * Rx;
     if (R <= 0) return -1;
@@ -532,9 +570,11 @@ int or_bm3d_pass2(const double *noisy, const double *basic, int C, int H, int W,
     if (!idx || !dist || !nk || !ng || !fl) return -2;
     if (or_match(basic, H, W, k, step, search, n2, tau, idx, dist, nk, ng, fl)) return -1;
 
-    double T[OR_K2 * OR_K2], kw[OR_K];
-    or_dct2d_matrix(T);
-    or_kaiser(OR_K, beta, kw);
+    const int k2 = k * k;
+    double *T = (double *)malloc(sizeof(double) * (size_t)k2 * k2), kw[OR_KMAX];
+    if (!T) return -2;
+    or_dct2d_matrix_k(k, T);
+    or_kaiser(k, beta, kw);
     size_t HW = (size_t)H * W, plane = (size_t)C * HW;
     if (pxflag) memset(pxflag, 0, HW);
     acc_t acc;
@@ -547,8 +587,11 @@ int or_bm3d_pass2(const double *noisy, const double *basic, int C, int H, int W,
         tid = omp_get_thread_num();
 #endif
         double *num = acc.acc + (size_t)tid * plane * 2, *den = num + plane;
-        double Gb[OR_NMAX * OR_K2], Gy[OR_NMAX * OR_K2], Zb[OR_NMAX * OR_K2], Zy[OR_NMAX * OR_K2];
-        double E[OR_NMAX * OR_K2], Hn[OR_NMAX * OR_NMAX];
+        /* basic and noisy groups, their coefficients, the estimate, transform scratch */
+        double *Gb = (double *)malloc(sizeof(double) * 6 * OR_NMAX * (size_t)k2);
+        double *Gy = Gb + OR_NMAX * k2, *Zb = Gy + OR_NMAX * k2, *Zy = Zb + OR_NMAX * k2;
+        double *E = Zy + OR_NMAX * k2, *S = E + OR_NMAX * k2;
+        double Hn[OR_NMAX * OR_NMAX];
 #pragma omp for schedule(static)
         for (int r = 0; r < R; ++r) {
             int n = ng[r];
@@ -559,41 +602,42 @@ int or_bm3d_pass2(const double *noisy, const double *basic, int C, int H, int W,
                 double s2 = sig[c] * sig[c];
                 for (int t = 0; t < n; ++t) {
                     int y = I[t] / W, x = I[t] % W;
-                    for (int i = 0; i < OR_K; ++i)
-                        for (int j = 0; j < OR_K; ++j) {
+                    for (int i = 0; i < k; ++i)
+                        for (int j = 0; j < k; ++j) {
                             size_t p = (size_t)(y + i) * W + x + j;
-                            Gb[t * OR_K2 + i * OR_K + j] = cb[p];
-                            Gy[t * OR_K2 + i * OR_K + j] = cy[p];
+                            Gb[t * k2 + i * k + j] = cb[p];
+                            Gy[t * k2 + i * k + j] = cy[p];
                         }
                 }
-                t3d_forward(T, Hn, n, Gb, Zb);
-                t3d_forward(T, Hn, n, Gy, Zy);
+                t3d_forward(T, Hn, n, k2, Gb, Zb, S);
+                t3d_forward(T, Hn, n, k2, Gy, Zy, S);
                 double wsq = 0.0;
-                for (int a = 0; a < n * OR_K2; ++a) {
+                for (int a = 0; a < n * k2; ++a) {
                     double b2 = Zb[a] * Zb[a];
                     double om = b2 / (b2 + s2);
                     Zy[a] *= om;
                     wsq += om * om;
                 }
-                t3d_inverse(T, Hn, n, Zy, E);
+                t3d_inverse(T, Hn, n, k2, Zy, E, S);
                 double w = wsq > 0.0 ? 1.0 / (s2 * wsq) : 1.0;
                 for (int t = 0; t < n; ++t) {
                     int y = I[t] / W, x = I[t] % W;
-                    for (int i = 0; i < OR_K; ++i)
-                        for (int j = 0; j < OR_K; ++j) {
+                    for (int i = 0; i < k; ++i)
+                        for (int j = 0; j < k; ++j) {
                             size_t p = (size_t)c * HW + (size_t)(y + i) * W + x + j;
                             double kk = w * kw[i] * kw[j];
-                            num[p] += kk * E[t * OR_K2 + i * OR_K + j];
+                            num[p] += kk * E[t * k2 + i * k + j];
                             den[p] += kk;
                         }
                 }
             }
             if (gflag) gflag[r] = fl[r];
-            if (fl[r]) mark_group(pxflag, W, I, n, fl[r]);
+            if (fl[r]) mark_group(pxflag, W, k, I, n, fl[r]);
         }
+        free(Gb);
     }
     acc_finish(&acc, plane, out);
-    free(idx); free(dist); free(nk); free(ng); free(fl);
+    free(T); free(idx); free(dist); free(nk); free(ng); free(fl);
     return 0;
 }
 

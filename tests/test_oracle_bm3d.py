@@ -139,3 +139,84 @@ def test_psnr_closed_form(oracle):
     assert abs(oracle.psnr(clean + 5.0, clean) - 20 * np.log10(255.0 / 5.0)) < 1e-12
     assert oracle.psnr(clean, clean) == float("inf")
     assert abs(oracle.psnr(np.full((1, 4, 4), 300.0), np.full((1, 4, 4), 250.0)) - 20 * np.log10(255.0 / 5)) < 1e-12
+
+
+# ---- larger patches (the high-noise profile: 12 x 12 step 4, 11 x 11 step 6) ----------
+
+HARD12 = dict(patch=12, step=4, n2=16, tau=5000.0)
+WIENER11 = dict(patch=11, step=6, n2=32, tau=3500.0)
+
+
+@pytest.mark.parametrize("C", [1, 3])
+def test_lambda_zero_is_identity_12x12(oracle, C):
+    _, noisy = synth.make_batch([14], 41, 37, 50.0, C=C)
+    x = noisy[0].astype(np.float64)
+    basic, _, _ = oracle.bm3d_pass1(x, [50.0] * C, oracle.Pass(lambda3d=0.0, **HARD12))
+    np.testing.assert_allclose(basic, x, atol=1e-9)
+
+
+@pytest.mark.parametrize("c,sigma", [(100.0, 50.0), (30.0, 60.0)])
+def test_constant_image_closed_form_larger_patches(oracle, c, sigma):
+    """As the 8 x 8 case: the 12 x 12 hard pass keeps only the DC coefficient
+    12 c sqrt(n) (a fixed point); in the 11 x 11 Wiener pass every group has
+    32 equal patches and the DC coefficient B = 11 c sqrt(32)."""
+    img = np.full((1, 35, 40), c)
+    basic, final = oracle.bm3d(img, sigma, hard=oracle.Pass(**HARD12), wiener=oracle.Pass(**WIENER11))
+    np.testing.assert_allclose(basic, c, atol=1e-9)
+    B2 = 121.0 * 32.0 * c * c
+    np.testing.assert_allclose(final, c * B2 / (B2 + sigma * sigma), atol=1e-9)
+
+
+def test_two_patch_weighting_closed_form_12x12(oracle):
+    """12 x 13 image, references x = 0 and x = 1 (step 4 puts the second at
+    W - 12 = 1), one patch per group: scipy's 12-point DCT, weight
+    1/(sigma^2 N_har) and the kaiser(12, 2) window (numpy)."""
+    rng = np.random.default_rng(20)
+    img = 100.0 + rng.normal(0, 30, (12, 13))
+    sigma, lam = 10.0, 2.7
+    k = np.kaiser(12, 2.0)
+    K = np.outer(k, k)
+    num = np.zeros((12, 13))
+    den = np.zeros((12, 13))
+    for x0 in (0, 1):
+        D = scipy.fft.dctn(img[:, x0:x0 + 12], norm="ortho")
+        keep = np.abs(D) > lam * sigma
+        e = scipy.fft.idctn(D * keep, norm="ortho")
+        w = 1.0 / (sigma ** 2 * keep.sum())
+        num[:, x0:x0 + 12] += w * K * e
+        den[:, x0:x0 + 12] += w * K
+    d01 = ((img[:, 0:12] - img[:, 1:13]) ** 2).mean()
+    p = oracle.Pass(patch=12, step=4, tau=0.5 * d01, lambda3d=lam)
+    basic, _, _ = oracle.bm3d_pass1(img[None], [sigma], p)
+    np.testing.assert_allclose(basic[0], num / den, atol=1e-10)
+
+
+def test_two_patch_wiener_closed_form_11x11(oracle):
+    rng = np.random.default_rng(21)
+    basic = 100.0 + rng.normal(0, 30, (11, 12))
+    noisy = basic + rng.normal(0, 10, (11, 12))
+    sigma = 10.0
+    k = np.kaiser(11, 2.0)
+    K = np.outer(k, k)
+    num = np.zeros((11, 12))
+    den = np.zeros((11, 12))
+    for x0 in (0, 1):
+        B = scipy.fft.dctn(basic[:, x0:x0 + 11], norm="ortho")
+        Y = scipy.fft.dctn(noisy[:, x0:x0 + 11], norm="ortho")
+        om = B ** 2 / (B ** 2 + sigma ** 2)
+        e = scipy.fft.idctn(om * Y, norm="ortho")
+        w = 1.0 / (sigma ** 2 * (om ** 2).sum())
+        num[:, x0:x0 + 11] += w * K * e
+        den[:, x0:x0 + 11] += w * K
+    d01 = ((basic[:, 0:11] - basic[:, 1:12]) ** 2).mean()
+    p = oracle.Pass(patch=11, step=6, n2=32, tau=0.5 * d01)
+    out, _, _ = oracle.bm3d_pass2(noisy[None], basic[None], [sigma], p)
+    np.testing.assert_allclose(out[0], num / den, atol=1e-10)
+
+
+def test_high_noise_profile_denoises_synthetic_scene(oracle):
+    clean, noisy = synth.make_batch([1], 80, 80, 50.0)
+    basic, final = oracle.bm3d(noisy[0], 50.0, hard=oracle.Pass(lambda2d=2.0, **HARD12),
+                               wiener=oracle.Pass(**WIENER11))
+    p0 = oracle.psnr(noisy[0], clean[0])
+    assert oracle.psnr(basic, clean[0]) > p0 + 6.0 and oracle.psnr(final, clean[0]) > p0 + 6.0

@@ -122,3 +122,24 @@ def test_synthetic_scene_match_smoke(oracle):
     m = oracle.match(noisy[0, 0], oracle.Pass())
     assert m["n"].min() >= 1 and m["n"].max() <= 16
     assert np.all((m["n"] & (m["n"] - 1)) == 0)
+
+
+@pytest.mark.parametrize("k,step,search,H,W,tau,n2", [(12, 4, 39, 30, 34, 5000.0, 16), (11, 6, 39, 29, 40, 3500.0, 32),
+                                                      (12, 4, 9, 25, 26, 1e9, 16), (11, 6, 15, 11, 23, 3500.0, 8)])
+def test_match_larger_patches_equal_numpy_brute_force(oracle, k, step, search, H, W, tau, n2):
+    """The high-noise profile's 12 x 12 / step 4 and 11 x 11 / step 6 patches
+    against the same independent brute force (distances / k^2)."""
+    rng = np.random.default_rng(k * 1000 + H)
+    g = rng.normal(128, 60, (H, W))
+    p = oracle.Pass(patch=k, step=step, search=search, n2=n2, tau=tau)
+    m = oracle.match(g, p)
+    ref = brute_match(g, k, step, search, n2, tau)
+    idx = m["idx"].reshape(-1, n2)
+    dist = m["dist"].reshape(-1, n2 + 1)
+    assert len(ref) == idx.shape[0]
+    for r, (lst, ds, kept, n) in enumerate(ref):
+        assert m["nkept"].ravel()[r] == kept
+        assert m["n"].ravel()[r] == n
+        np.testing.assert_array_equal(idx[r, :len(lst)], lst)
+        L = min(len(ds), n2 + 1)
+        np.testing.assert_allclose(dist[r, :L], ds[:L], rtol=1e-12, atol=1e-9)

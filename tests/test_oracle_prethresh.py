@@ -23,28 +23,29 @@ from paper_2403_03488_gb300 import synth
 def brute(g, p, thr):
     g = np.asarray(g, np.float64)
     H, W = g.shape
-    Hp, Wp = H - 7, W - 7
-    Y = np.empty((Hp, Wp, 64))
+    k = p.patch
+    Hp, Wp = H - k + 1, W - k + 1
+    Y = np.empty((Hp, Wp, k * k))
     for y in range(Hp):
         for x in range(Wp):
-            c = dctn(g[y:y + 8, x:x + 8], norm="ortho").ravel()
+            c = dctn(g[y:y + k, x:x + k], norm="ortho").ravel()
             Y[y, x] = np.where(np.abs(c) > thr, c, 0.0)
-    gy = [int(v) for v in range(0, H - 7, p.step)]
-    gx = [int(v) for v in range(0, W - 7, p.step)]
-    if gy[-1] != H - 8:
-        gy.append(H - 8)
-    if gx[-1] != W - 8:
-        gx.append(W - 8)
+    gy = [int(v) for v in range(0, H - k + 1, p.step)]
+    gx = [int(v) for v in range(0, W - k + 1, p.step)]
+    if gy[-1] != H - k:
+        gy.append(H - k)
+    if gx[-1] != W - k:
+        gx.append(W - k)
     hs = p.search // 2
     out = {}
     for ry, y0 in enumerate(gy):
         for rx, x0 in enumerate(gx):
             cand = []
-            for y in range(max(0, y0 - hs), min(H - 8, y0 + hs) + 1):
-                for x in range(max(0, x0 - hs), min(W - 8, x0 + hs) + 1):
+            for y in range(max(0, y0 - hs), min(H - k, y0 + hs) + 1):
+                for x in range(max(0, x0 - hs), min(W - k, x0 + hs) + 1):
                     if (y, x) == (y0, x0):
                         continue
-                    d = ((Y[y0, x0] - Y[y, x]) ** 2).sum() / 64.0
+                    d = ((Y[y0, x0] - Y[y, x]) ** 2).sum() / float(k * k)
                     if d <= p.tau:
                         cand.append((d, y * W + x))
             cand.sort()
@@ -72,6 +73,25 @@ def test_brute_force_with_scipy_dct(oracle, thr, step, search, n2, H, W):
     _, noisy = synth.make_batch([5], H, W, 50.0)
     g = noisy[0, 0]
     p = oracle.Pass(step=step, search=search, n2=n2, tau=5000.0)
+    om = oracle.match_pre(g, p, thr)
+    bf = brute(g, p, thr)
+    checked = 0
+    for (ry, rx), (n, lst, dl) in bf.items():
+        if om["flag"][ry, rx]:
+            continue
+        checked += 1
+        assert om["n"][ry, rx] == n
+        np.testing.assert_array_equal(om["idx"][ry, rx, :n], lst)
+        np.testing.assert_allclose(om["dist"][ry, rx, :n], dl, rtol=1e-9, atol=1e-9)
+    assert checked >= 0.5 * len(bf)
+
+
+@pytest.mark.parametrize("thr,H,W", [(100.0, 30, 33), (40.0, 25, 29)])
+def test_brute_force_with_scipy_dct_12x12_step_4(oracle, thr, H, W):
+    """The high-noise profile's first pass: 12 x 12 patches on a step-4 grid."""
+    _, noisy = synth.make_batch([9], H, W, 50.0)
+    g = noisy[0, 0]
+    p = oracle.Pass(patch=12, step=4, search=39, n2=16, tau=5000.0)
     om = oracle.match_pre(g, p, thr)
     bf = brute(g, p, thr)
     checked = 0
