@@ -30,6 +30,7 @@ B = 16
 SIGMA = 25.0
 SEEDS0 = 100
 FL_PREC = "fp32"  # contractions of the flexible network (--fl)
+HIGH_PATCHES = False  # --bm3d-patches high: 12 x 12 / 11 x 11 patches above sigma 40
 METRIC = "MPix/s BM3D+CNN at <=0.05 dB PSNR loss vs FP32 plain; served p50/p99 ms"
 # the machine the FP32 ALU peak is derived for when the device is not queried
 # (host-only use of the work counts): GB300's SM count and maximum SM clock
@@ -46,8 +47,25 @@ def fp32_note(hw):
             % (hw["sm_count"], hw["sm_mhz"], fp32_peak(hw), hw["source"]))
 
 
+def bm3d_params(precision=None):
+    """The library's BM3D parameters (with the high-noise patch sides under
+    --bm3d-patches high)."""
+    from paper_2403_03488_gb300 import api
+    return api.default_bm3d_params(precision=api.DN_FP32 if precision is None else precision,
+                                   high_noise_patches=HIGH_PATCHES)
+
+
+def oracle_passes(oracle):
+    """The oracle's passes for the workload's sigma, as bm3d_params() selects them."""
+    if HIGH_PATCHES and SIGMA > 40.0:
+        return (oracle.Pass(patch=12, step=4, n2=16, tau=5000.0, lambda2d=oracle.LAMBDA2D_HIGH),
+                oracle.Pass(patch=11, step=6, n2=32, tau=3500.0))
+    return oracle.default_passes(SIGMA)
+
+
 def workload_name(bm3d, cnn, prefilter="bm3d", net="resnet"):
-    pre = "BM3D(%s)" % bm3d if prefilter == "bm3d" else "NLM(fp32)"
+    pre = "BM3D(%s%s)" % (bm3d, ", 12x12/11x11 patches" if HIGH_PATCHES and SIGMA > 40.0 else "") \
+        if prefilter == "bm3d" else "NLM(fp32)"
     body = "CNN(10x32, %s)" % cnn if net == "resnet" else "FL-UNet(48-192, %s)" % FL_PREC
     return "hybrid %s+%s denoise, %d grey %dx%d synthetic images, sigma=%g" % (pre, body, B, H, W, SIGMA)
 
@@ -306,7 +324,7 @@ def run_ours(args):
     prec = api.DN_BF16 if args.cnn == "bf16" else api.DN_FP32
     nlm = args.prefilter == "nlm"
     pf = api.DN_PREFILTER_NLM if nlm else api.DN_PREFILTER_BM3D
-    bp = api.default_nlm_params() if nlm else api.default_bm3d_params(precision=bprec)
+    bp = api.default_nlm_params() if nlm else bm3d_params(bprec)
     cnn = api.make_cnn(weights, 10, 32, prec)
     ws = torch.empty(api.hybrid_workspace_bytes(B, 1, H, W, pf, bp, cnn), dtype=torch.uint8, device=dev)
     sse = torch.empty(B, dtype=torch.float64, device=dev)
@@ -383,7 +401,7 @@ def run_ours(args):
         del fl32
     else:
         plain = api.denoise_hybrid(noisy_d, SIGMA, weights, prefilter=pf,
-                                   prefilter_params=bp if nlm else api.default_bm3d_params(),
+                                   prefilter_params=bp if nlm else bm3d_params(),
                                    cnn_precision=api.DN_FP32)
     sse_p, _ = api.error_reduce(plain, clean_d)
     psnr_plain = 10 * np.log10(255.0 ** 2 / (float(sse_p.sum().item()) / (B * H * W)))
@@ -391,7 +409,7 @@ def run_ours(args):
     plain_ms = None
     if not fl:
         plain_out = torch.empty_like(noisy_d)
-        pparams = bp if nlm else api.default_bm3d_params()
+        pparams = bp if nlm else bm3d_params()
         plain_steps = 2
         plain_ms = 0.0
         for _ in range(plain_steps):
@@ -601,7 +619,8 @@ def oracle_step(side, weights=None):
         from paper_2403_03488_gb300.autograd import ResidualNet
         params = ResidualNet(10, 32, flat=weights.detach().cpu()).numpy_params()
     t0 = time.perf_counter()
-    _, final = oracle.bm3d(crop, SIGMA)
+    hard, wiener = oracle_passes(oracle)
+    _, final = oracle.bm3d(crop, SIGMA, hard=hard, wiener=wiener)
     out = oracle.cnn_forward(crop[:, :, :], final, params)
     dt = time.perf_counter() - t0
     return dt, side * side / 1e6, np.asarray(out)[0]
@@ -631,7 +650,7 @@ def vs_oracle(ref, noisy_d, clean, side, out0, plain0, denoise, weights, pf, bp,
         denoise(x, o)
         fast = o[0, 0].cpu().numpy()
         plain = api.denoise_hybrid(x, SIGMA, weights, prefilter=pf,
-                                   prefilter_params=bp if nlm else api.default_bm3d_params(),
+                                   prefilter_params=bp if nlm else bm3d_params(),
                                    cnn_precision=api.DN_FP32)[0, 0].cpu().numpy()
 
     def psnr(a):
@@ -709,8 +728,11 @@ def main():
     ap.add_argument("--size", type=int, default=None, help="image side (profiling runs; default 1024)")
     ap.add_argument("--sigma", type=float, default=None,
                     help="noise level (default 25; above 40 the first pass matches on prethresholded patches)")
+    ap.add_argument("--bm3d-patches", default="8", choices=["8", "high"],
+                    help="high: the 12 x 12 / 11 x 11 patches of the high-noise profile above sigma 40")
     args = ap.parse_args()
-    global H, W, B, SIGMA
+    global H, W, B, SIGMA, HIGH_PATCHES
+    HIGH_PATCHES = args.bm3d_patches == "high"
     if args.sigma:
         SIGMA = args.sigma
     if args.size:

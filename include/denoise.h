@@ -49,7 +49,9 @@ typedef enum {
     DN_EUNSUPPORTED = -5  /* valid but not implemented combination               */
 } dn_status;
 
-/* Arithmetic of the BM3D stages (dn_bm3d_params.precision is a bit set):
+/* Arithmetic of the BM3D stages (dn_bm3d_params.precision is a bit set; the
+ * tensor-core paths are built for 8 x 8 patches, passes with 11 x 11 or
+ * 12 x 12 patches run in FP32 whatever the bits):
  *   DN_FP32        every stage in FP32 on the CUDA cores;
  *   DN_BF16        the 2D patch transforms of both filtering passes as 64 x 64
  *                  contractions on the tensor cores (BF16 operands, FP32
@@ -64,9 +66,13 @@ typedef enum {
 typedef enum { DN_FP32 = 0, DN_BF16 = 1, DN_BF16_MATCH = 2 } dn_precision;
 typedef enum { DN_PREFILTER_BM3D = 0, DN_PREFILTER_NLM = 1 } dn_prefilter;
 
-/* One BM3D pass.  Distances are mean squared differences over the patch. */
+/* One BM3D pass.  Distances are mean squared differences over the patch.
+ * Above sigma 40 (sigma_regime 0) a pass may switch to the larger patches of
+ * BM3D's high-noise profile (patch_high, step_high: 12 x 12 on a step-4 grid
+ * for the hard pass, 11 x 11 on a step-6 grid for the Wiener pass); images of
+ * one call then run in groups of equal regime. */
 typedef struct {
-    int patch;       /* patch side; only 8 is supported                        */
+    int patch;       /* patch side: 8 (all kernels) or 11, 12 (FP32 kernels)   */
     int step;        /* reference grid step (3): 0, step, ... plus L-patch     */
     int search;      /* odd side of the search window of top-left corners (39) */
     int n2;          /* largest group size, a power of two in [1, 32]          */
@@ -78,6 +84,10 @@ typedef struct {
                         2D-prethresholded patches, coefficients of magnitude
                         <= lambda2d * sigma zeroed (BM3D's high-noise distance;
                         0 disables; ignored by the second pass)              */
+    int patch_high;  /* patch side when sigma > 40 and sigma_regime == 0: 0
+                        (= patch), 8, 11 or 12; a prethresholded first pass
+                        (lambda2d > 0) takes 8 or 12 with n2 <= 16          */
+    int step_high;   /* grid step then (0 = step)                              */
 } dn_bm3d_pass;
 
 typedef struct {
@@ -112,9 +122,12 @@ typedef struct {
 
 /* ---- parameters ---------------------------------------------------------- */
 
-/* Defaults: hard {8, 3, 39, 16, 2500, 5000, 2.7, 2, 2}, wiener {8, 3, 39, 32,
- * 400, 3500, 0, 2, 0}, precision DN_FP32, sigma_regime 0. */
+/* Defaults: hard {8, 3, 39, 16, 2500, 5000, 2.7, 2, 2, 0, 0}, wiener {8, 3, 39,
+ * 32, 400, 3500, 0, 2, 0, 0, 0}, precision DN_FP32, sigma_regime 0. */
 void dn_bm3d_default_params(dn_bm3d_params *p);
+/* The defaults with the larger patches of BM3D's high-noise profile above
+ * sigma 40: hard patch_high 12, step_high 4; wiener patch_high 11, step_high 6. */
+void dn_bm3d_high_noise_params(dn_bm3d_params *p);
 /* Defaults: {7, 21, 0.4}. */
 void dn_nlm_default_params(dn_nlm_params *p);
 /* Number of floats in a dn_cnn weight buffer (grey network, channels = 1). */
@@ -135,13 +148,16 @@ size_t dn_hybrid_workspace_bytes(int B, int C, int H, int W, int prefilter, cons
 /* ---- the three denoisers ------------------------------------------------- */
 
 /* BM3D, both passes (standard definition; the paper's BM3D-G stage, Sec. II).
- * noisy/out: device [B][C][H][W] (may not alias); H, W >= patch.
+ * noisy/out: device [B][C][H][W] (may not alias); H, W >= every patch side
+ * an image's regime selects (DN_EINVAL otherwise).
  * DN_EUNSUPPORTED (before any launch) when an image takes the high-noise
  * first pass (sigma > 40, sigma_regime 0, hard.lambda2d > 0) and the
- * prethresholded matcher's staged window, (31 step + search) columns wide,
- * does not fit in 200 KB of shared memory (for example step 12 with search
- * 21 on an image wider than 400 pixels); the same
- * holds for denoise_hybrid and denoise_bm3d_noalloc. */
+ * prethresholded matcher's staged window, (31 step + search) columns wide
+ * for 8 x 8 patches, (15 step + search) for 12 x 12, does not fit in 200 KB
+ * of shared memory (for example step 12 with search 21 on an image wider
+ * than 400 pixels), or its patch side or group size is not one it takes
+ * (11, or n2 = 32 with 12); the same holds for denoise_hybrid and
+ * denoise_bm3d_noalloc. */
 dn_status denoise_bm3d(const float *noisy, float *out, int B, int C, int H, int W, const float *sigma,
                        const dn_bm3d_params *p, void *workspace, size_t ws_bytes, dn_stream_t stream);
 
@@ -226,9 +242,12 @@ dn_status denoise_bm3d_noalloc(const float *noisy, float *out, int B, int C, int
  *      then the other candidates with d <= tau in ascending (d, y*W + x)
  *      order; -1 past the kept count.
  * n:   device int32 [B][Ry][Rx]: group size min(n2, 2^floor(log2 #kept)).
+ * Patches of side p->patch (8, 11 or 12) on the grid of step p->step; the
+ * distance is ||P - Q||^2 / patch^2.
  * precision: DN_FP32 (exhaustive FP32), or DN_BF16_MATCH (DN_BF16 is taken
  * as the same): tensor-core prefilter with a proven margin, survivors
- * re-ranked exactly in FP32, so the lists equal the FP32 ones. */
+ * re-ranked exactly in FP32, so the lists equal the FP32 ones (8 x 8 patches;
+ * other sides are matched in FP32). */
 dn_status dn_bm3d_match(const float *guide, size_t plane_stride, int B, int H, int W, const dn_bm3d_pass *p,
                         const float *tau, int precision, int *idx, int *n, void *workspace, size_t ws_bytes,
                         dn_stream_t stream);
@@ -236,13 +255,14 @@ size_t dn_bm3d_match_workspace_bytes(int B, int H, int W, const dn_bm3d_pass *p,
 
 /* Block matching on 2D-prethresholded patches (the first-pass distance BM3D
  * uses at high noise; the denoisers select it per image, see
- * dn_bm3d_pass.lambda2d): every patch P becomes Y(P), its orthonormal 8 x 8
- * DCT-II with the coefficients of magnitude <= thr[b] set to zero, and
- * d(P, Q) = ||Y(P) - Y(Q)||^2 / 64; window, tau test, ordering and group size
- * as dn_bm3d_match.  guide as dn_bm3d_match; tau, thr: host [B] (tau > 0,
- * thr >= 0); idx/n as dn_bm3d_match with p->n2.  FP32 transforms and
- * distances; no workspace.  DN_EUNSUPPORTED when the staged window exceeds
- * shared memory (search > 127 is already DN_EINVAL). */
+ * dn_bm3d_pass.lambda2d): every patch P (side k = p->patch, 8 or 12) becomes
+ * Y(P), its orthonormal k x k DCT-II with the coefficients of magnitude
+ * <= thr[b] set to zero, and d(P, Q) = ||Y(P) - Y(Q)||^2 / k^2; window, tau
+ * test, ordering and group size as dn_bm3d_match.  guide as dn_bm3d_match;
+ * tau, thr: host [B] (tau > 0, thr >= 0); idx/n as dn_bm3d_match with p->n2.
+ * FP32 transforms and distances; no workspace.  DN_EUNSUPPORTED when the
+ * staged window exceeds shared memory, for side 11, and for side 12 with
+ * n2 = 32 (search > 127 is already DN_EINVAL). */
 dn_status dn_bm3d_match_prethresh(const float *guide, size_t plane_stride, int B, int H, int W,
                                   const dn_bm3d_pass *p, const float *tau, const float *thr, int *idx, int *n,
                                   dn_stream_t stream);
@@ -265,10 +285,11 @@ dn_status dn_bm3d_match_cross_terms(const float *guide, int H, int W, const dn_b
 /* Collaborative hard thresholding + aggregation (first pass) given match lists.
  * img: device [B][C][H][W] (already in the filtering colour space);
  * sigma_c: host [B*C] per-channel noise std; idx/n as produced by
- * dn_bm3d_match with p->n2; basic: device [B][C][H][W].
- * precision: DN_FP32 (FP32 SIMT transforms) or DN_BF16 (2D transforms on the
- * tensor cores, see dn_precision; DN_EDEVICE-class failures set the device
- * status word, see dn_device_error).
+ * dn_bm3d_match with p->n2 (patches of side p->patch, grid step p->step);
+ * basic: device [B][C][H][W].
+ * precision: DN_FP32 (FP32 SIMT transforms) or DN_BF16 (2D transforms of 8 x 8
+ * patches on the tensor cores, see dn_precision; DN_EDEVICE-class failures
+ * set the device status word, see dn_device_error).
  * workspace >= dn_bm3d_filter_workspace_bytes(B, C, H, W). */
 dn_status dn_bm3d_filter_hard(const float *img, const int *idx, const int *n, int B, int C, int H, int W,
                               const float *sigma_c, const dn_bm3d_pass *p, int precision, float *basic,

@@ -29,7 +29,8 @@ class DenoiseError(RuntimeError):
 class BM3DPass(ctypes.Structure):
     _fields_ = [("patch", ctypes.c_int), ("step", ctypes.c_int), ("search", ctypes.c_int), ("n2", ctypes.c_int),
                 ("tau", ctypes.c_float), ("tau_high", ctypes.c_float), ("lambda3d", ctypes.c_float),
-                ("beta", ctypes.c_float), ("lambda2d", ctypes.c_float)]
+                ("beta", ctypes.c_float), ("lambda2d", ctypes.c_float), ("patch_high", ctypes.c_int),
+                ("step_high", ctypes.c_int)]
 
 
 class BM3DParams(ctypes.Structure):
@@ -64,6 +65,7 @@ def lib():
     P = ctypes.POINTER
     sig = {
         "dn_bm3d_default_params": (None, [P(BM3DParams)]),
+        "dn_bm3d_high_noise_params": (None, [P(BM3DParams)]),
         "dn_nlm_default_params": (None, [P(NLMParams)]),
         "dn_cnn_param_count": (sz, [i, i]),
         "dn_cnn_param_count_c": (sz, [i, i, i]),
@@ -147,9 +149,14 @@ def check(status: int, what: str):
         raise DenoiseError(status, what)
 
 
-def default_bm3d_params(precision: int = DN_FP32, regime: int = 0) -> BM3DParams:
+def default_bm3d_params(precision: int = DN_FP32, regime: int = 0, high_noise_patches: bool = False) -> BM3DParams:
+    """The library defaults; high_noise_patches: the larger patches of BM3D's
+    high-noise profile above sigma 40 (12 x 12 step 4, 11 x 11 step 6)."""
     p = BM3DParams()
-    lib().dn_bm3d_default_params(ctypes.byref(p))
+    if high_noise_patches:
+        lib().dn_bm3d_high_noise_params(ctypes.byref(p))
+    else:
+        lib().dn_bm3d_default_params(ctypes.byref(p))
     p.precision = precision
     p.sigma_regime = regime
     return p

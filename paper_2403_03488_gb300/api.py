@@ -189,7 +189,7 @@ def bm3d_match(guide: torch.Tensor, tau, p: BM3DPass, precision: int = DN_FP32, 
         B, H, W = guide.shape
         plane = H * W
     _need(guide, "guide")
-    Ry, Rx = len(grid(H, 8, p.step)), len(grid(W, 8, p.step))
+    Ry, Rx = len(grid(H, p.patch, p.step)), len(grid(W, p.patch, p.step))
     idx = torch.empty((B, Ry, Rx, p.n2), dtype=torch.int32, device=guide.device)
     n = torch.empty((B, Ry, Rx), dtype=torch.int32, device=guide.device)
     nbytes = int(L.lib().dn_bm3d_match_workspace_bytes(B, H, W, ctypes.byref(p), precision))
@@ -210,7 +210,7 @@ def bm3d_match_prethresh(guide: torch.Tensor, tau, thr, p: BM3DPass, stream=None
         B, H, W = guide.shape
         plane = H * W
     _need(guide, "guide")
-    Ry, Rx = len(grid(H, 8, p.step)), len(grid(W, 8, p.step))
+    Ry, Rx = len(grid(H, p.patch, p.step)), len(grid(W, p.patch, p.step))
     idx = torch.empty((B, Ry, Rx, p.n2), dtype=torch.int32, device=guide.device)
     n = torch.empty((B, Ry, Rx), dtype=torch.int32, device=guide.device)
     check(L.lib().dn_bm3d_match_prethresh(_vp(guide), plane, B, H, W, ctypes.byref(p), _sigmas(tau, B),

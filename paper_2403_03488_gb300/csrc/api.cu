@@ -34,10 +34,14 @@ bool valid_sigmas(const float *sigma, int B)
     return true;
 }
 
+bool patch_side_ok(int k) { return k == 8 || large_patch_supported(k); }
+
 bool valid_pass(const dn_bm3d_pass *p)
 {
     if (!p) return false;
-    if (p->patch != 8 || p->step < 1 || p->search < 1 || (p->search & 1) == 0 || p->search > 127) return false;
+    if (!patch_side_ok(p->patch) || p->step < 1 || p->search < 1 || (p->search & 1) == 0 || p->search > 127)
+        return false;
+    if ((p->patch_high != 0 && !patch_side_ok(p->patch_high)) || p->step_high < 0 || p->step_high > 64) return false;
     if (p->n2 < 1 || p->n2 > 32 || (p->n2 & (p->n2 - 1)) != 0) return false;
     if (!(p->tau > 0.0f) || !(p->tau_high > 0.0f) || !(p->lambda3d >= 0.0f) || !(p->beta >= 0.0f)) return false;
     if (!(p->lambda2d >= 0.0f) || !std::isfinite(p->lambda2d)) return false;
@@ -67,20 +71,53 @@ bool valid_cnn(const dn_cnn *c)
 // Colour planes the network takes and produces (1: grey network).
 int cnn_cc(const dn_cnn *c) { return c->channels == 3 ? 3 : 1; }
 
-// The high-noise first pass (prethresholded patches) stages a window as wide
-// as the CTA's union of search windows in shared memory; wide windows with
-// large steps do not fit.  Checked on the host before any launch.
-bool prethresh_fits(int B, int W, const float *sigma, const dn_bm3d_params *p)
+// Whether image noise sigma takes the high-noise settings (tau_high, the
+// prethresholded first-pass distance, patch_high and step_high).
+bool is_high(const dn_bm3d_params *p, float sigma) { return p->sigma_regime == 0 && sigma > 40.0f; }
+
+// The pass as an image of that regime runs it: tau, patch side and step
+// resolved; lambda2d kept only for a high-noise first pass.
+dn_bm3d_pass pass_at(const dn_bm3d_pass &p, bool high, bool first)
 {
-    if (p->sigma_regime != 0 || !(p->hard.lambda2d > 0.0f)) return true;
-    for (int b = 0; b < B; ++b)
-        if (sigma[b] > 40.0f) return match_pre_smem_bytes(W, p->hard) <= 200 * 1024;
+    dn_bm3d_pass q = p;
+    if (high) {
+        q.tau = p.tau_high;
+        if (p.patch_high > 0) q.patch = p.patch_high;
+        if (p.step_high > 0) q.step = p.step_high;
+    }
+    q.lambda2d = (first && high) ? p.lambda2d : 0.0f;
+    q.patch_high = q.patch;
+    q.step_high = q.step;
+    return q;
+}
+
+// Smallest image side every image of the call can take: the largest patch side
+// its regime selects in either pass.
+bool sides_ok(int B, int H, int W, const float *sigma, const dn_bm3d_params *p)
+{
+    for (int b = 0; b < B; ++b) {
+        const bool hi = is_high(p, sigma[b]);
+        const int k1 = pass_at(p->hard, hi, true).patch, k2 = pass_at(p->wiener, hi, false).patch;
+        const int k = k1 > k2 ? k1 : k2;
+        if (H < k || W < k) return false;
+    }
     return true;
 }
 
-float tau_for(const dn_bm3d_pass &p, float sigma, int regime)
+// The high-noise first pass (prethresholded patches) stages a window as wide
+// as the CTA's union of search windows in shared memory; wide windows with
+// large steps do not fit, and only some patch sides and group sizes are
+// built.  Checked on the host before any launch.
+bool prethresh_fits(int B, int W, const float *sigma, const dn_bm3d_params *p)
 {
-    return (regime == 0 && sigma > 40.0f) ? p.tau_high : p.tau;
+    for (int b = 0; b < B; ++b) {
+        if (!is_high(p, sigma[b])) continue;
+        const dn_bm3d_pass h = pass_at(p->hard, true, true);
+        if (!(h.lambda2d > 0.0f)) return true;
+        if (h.patch == 8) return match_pre_smem_bytes(W, h) <= 200 * 1024;
+        return large_prethresh_supported(h.patch) && h.n2 <= 16 && match_pre_large_smem_bytes(W, h) <= 200 * 1024;
+    }
+    return true;
 }
 
 // ---- workspace layouts (a null base computes the size) -------------------------
@@ -95,11 +132,22 @@ struct Bm3dWs {
     size_t bytes;
 };
 
+// Reference count of a pass in either regime (the larger).
+size_t refs_max(const dn_bm3d_pass &p, int H, int W)
+{
+    size_t r = 0;
+    for (int hi = 0; hi < 2; ++hi) {
+        const dn_bm3d_pass q = pass_at(p, hi != 0, false);
+        const size_t v = (size_t)grid_count(H, q.patch, q.step) * grid_count(W, q.patch, q.step);
+        r = v > r ? v : r;
+    }
+    return r;
+}
+
 Bm3dWs bm3d_layout(void *base, int B, int C, int H, int W, const dn_bm3d_params *p)
 {
     Carver cv(base);
-    const size_t HW = (size_t)H * W, R = (size_t)grid_count(H, 8, p->hard.step) * grid_count(W, 8, p->hard.step);
-    const size_t R2 = (size_t)grid_count(H, 8, p->wiener.step) * grid_count(W, 8, p->wiener.step);
+    const size_t HW = (size_t)H * W, R = refs_max(p->hard, H, W), R2 = refs_max(p->wiener, H, W);
     const size_t Rm = R > R2 ? R : R2;
     const int n2 = p->hard.n2 > p->wiener.n2 ? p->hard.n2 : p->wiener.n2;
     Bm3dWs w;
@@ -108,8 +156,17 @@ Bm3dWs bm3d_layout(void *base, int B, int C, int H, int W, const dn_bm3d_params 
     w.n = cv.take<int>((size_t)B * Rm);
     w.acc = cv.take<float>(kAccBytesPerPixel / sizeof(float) * (size_t)B * C * HW);
     w.basic = cv.take<float>((size_t)B * C * HW);
-    const size_t m1 = match_tc_workspace_bytes(B, H, W, p->hard), m2 = match_tc_workspace_bytes(B, H, W, p->wiener);
-    w.mws = (p->precision & DN_BF16_MATCH) ? cv.take<int>((m1 > m2 ? m1 : m2) / sizeof(int)) : nullptr;
+    // the tensor-core matcher's deferred-reference list, for every 8 x 8 pass either regime runs
+    size_t mt = 0;
+    for (int hi = 0; hi < 2; ++hi) {
+        const dn_bm3d_pass q[2] = {pass_at(p->hard, hi != 0, false), pass_at(p->wiener, hi != 0, false)};
+        for (const dn_bm3d_pass &e : q)
+            if (e.patch == 8) {
+                const size_t m = match_tc_workspace_bytes(B, H, W, e);
+                mt = m > mt ? m : mt;
+            }
+    }
+    w.mws = (p->precision & DN_BF16_MATCH) && mt > 0 ? cv.take<int>(mt / sizeof(int)) : nullptr;
     w.bytes = cv.off;
     return w;
 }
@@ -163,12 +220,14 @@ CnnWs cnn_layout(void *base, int N, int H, int W, const dn_cnn *c)
 
 // Block matching in the requested precision: with DN_BF16_MATCH the BF16
 // tensor-core prefilter with exact FP32 re-rank (same result as FP32) when its
-// tiling supports the parameters, the exhaustive FP32 kernel otherwise.
-bool tc_match_supported(const dn_bm3d_pass &p) { return match_tc_supported(p); }
+// tiling supports the parameters, the exhaustive FP32 kernel otherwise; the
+// larger patch sides on their own FP32 kernel.
+bool tc_match_supported(const dn_bm3d_pass &p) { return p.patch == 8 && match_tc_supported(p); }
 
 dn_status match_any(const float *guide, size_t plane, int B, int H, int W, const dn_bm3d_pass &p, const float *tau,
                     int precision, int *idx, int *n, int *mws, cudaStream_t s)
 {
+    if (p.patch != 8) return match_large(guide, plane, B, H, W, p, tau, idx, n, s);
     if ((precision & DN_BF16_MATCH) && mws && tc_match_supported(p)) {
         int *err = device_error_ptr();
         if (!err) return DN_ECUDA;
@@ -177,38 +236,22 @@ dn_status match_any(const float *guide, size_t plane, int B, int H, int W, const
     return match_fp32(guide, plane, B, H, W, p, tau, idx, n, s);
 }
 
-// First-pass matching of nb images: those in the high-noise regime (sigma >
-// 40 with sigma_regime 0 and lambda2d > 0) on 2D-prethresholded patches with
-// threshold lambda2d * (guide-channel sigma), runs of the others through
-// match_any.  sig: per-image, per-channel noise std [nb][C].
-dn_status match_pass1(const float *x, size_t plane, int nb, int C, int H, int W, const dn_bm3d_params *p,
-                      const float *sigma, const float *sig, const float *tau, int *idx, int *n, int *mws,
-                      cudaStream_t s)
+// Matching on 2D-prethresholded patches (threshold thr[b]) for the patch
+// side of p.
+dn_status match_prethresh_any(const float *guide, size_t plane, int B, int H, int W, const dn_bm3d_pass &p,
+                              const float *tau, const float *thr, int *idx, int *n, cudaStream_t s)
 {
-    if (nb > 1024) return DN_EINVAL;  // callers pass chunks of at most 1024 images
-    const size_t R = (size_t)grid_count(H, 8, p->hard.step) * grid_count(W, 8, p->hard.step);
-    auto pre = [&](int i) { return p->sigma_regime == 0 && sigma[i] > 40.0f && p->hard.lambda2d > 0.0f; };
-    float thr[1024];
-    for (int i = 0; i < nb; ++i) thr[i] = p->hard.lambda2d * sig[(size_t)i * C];
-    for (int i0 = 0; i0 < nb;) {
-        int i1 = i0 + 1;
-        while (i1 < nb && pre(i1) == pre(i0)) ++i1;
-        const float *g = x + (size_t)i0 * plane;
-        int *ix = idx + (size_t)i0 * R * p->hard.n2, *nn = n + (size_t)i0 * R;
-        if (pre(i0))
-            DN_TRY(match_prethresh(g, plane, i1 - i0, H, W, p->hard, tau + i0, thr + i0, ix, nn, s));
-        else
-            DN_TRY(match_any(g, plane, i1 - i0, H, W, p->hard, tau + i0, p->precision, ix, nn, mws, s));
-        i0 = i1;
-    }
-    return DN_OK;
+    if (p.patch == 8) return match_prethresh(guide, plane, B, H, W, p, tau, thr, idx, n, s);
+    return match_prethresh_large(guide, plane, B, H, W, p, tau, thr, idx, n, s);
 }
 
 // Collaborative filtering (pass 1, or pass 2 when `wiener`) with the 2D
-// transforms on the tensor cores when `tc`, FP32 SIMT otherwise.
+// transforms on the tensor cores when `tc` (8 x 8 patches), FP32 SIMT
+// otherwise.
 dn_status filter_any(bool wiener, bool tc, const float *img, const float *basic, const int *idx, const int *n, int B,
                      int C, int H, int W, const float *sig, const dn_bm3d_pass &p, float *acc, cudaStream_t s)
 {
+    if (p.patch != 8) return filter_large(wiener, img, basic, idx, n, B, C, H, W, sig, p, acc, s);
     if (tc) {
         int *err = device_error_ptr();
         if (!err) return DN_ECUDA;
@@ -227,27 +270,39 @@ dn_status run_bm3d(const float *noisy, float *out, int B, int C, int H, int W, c
         DN_TRY(colour(noisy, w.ycc, B, H, W, 0, s));
         x = w.ycc;
     }
-    float tau1[1024], tau2[1024], sig[3 * 1024];
-    for (int b0 = 0; b0 < B; b0 += 1024) {
-        const int nb = B - b0 < 1024 ? B - b0 : 1024;
+    float tau1[1024], tau2[1024], thr[1024], sig[3 * 1024];
+    // runs of consecutive images in the same regime (their passes share patch side, grid and
+    // distance), at most 1024 images each
+    for (int b0 = 0; b0 < B;) {
+        const bool hi = is_high(p, sigma[b0]);
+        int b1 = b0 + 1;
+        while (b1 < B && b1 - b0 < 1024 && is_high(p, sigma[b1]) == hi) ++b1;
+        const int nb = b1 - b0;
+        const dn_bm3d_pass ph = pass_at(p->hard, hi, true), pw = pass_at(p->wiener, hi, false);
         for (int i = 0; i < nb; ++i) {
-            tau1[i] = tau_for(p->hard, sigma[b0 + i], p->sigma_regime);
-            tau2[i] = tau_for(p->wiener, sigma[b0 + i], p->sigma_regime);
+            tau1[i] = ph.tau;
+            tau2[i] = pw.tau;
             for (int c = 0; c < C; ++c) sig[i * C + c] = channel_sigma(sigma[b0 + i], C, c);
+            thr[i] = ph.lambda2d * sig[(size_t)i * C];  // guide-channel sigma
         }
         const size_t off = (size_t)b0 * C * HW;
         const size_t Nb = (size_t)nb * C * HW;
-        // pass 1: match on channel 0 of the noisy image, hard thresholding
-        DN_TRY(match_pass1(x + off, (size_t)C * HW, nb, C, H, W, p, sigma + b0, sig, tau1, w.idx, w.n, w.mws, s));
-        if (cudaMemsetAsync(w.acc, 0, kAccBytesPerPixel * Nb, s) != cudaSuccess) return DN_ECUDA;
         const bool tc = (p->precision & DN_BF16) != 0;
-        DN_TRY(filter_any(false, tc, x + off, nullptr, w.idx, w.n, nb, C, H, W, sig, p->hard, w.acc, s));
-        DN_TRY(normalize(w.acc, w.basic + off, nb, C, H, W, p->hard.beta, s));
-        // pass 2: match on channel 0 of the basic estimate, Wiener filtering
-        DN_TRY(match_any(w.basic + off, (size_t)C * HW, nb, H, W, p->wiener, tau2, p->precision, w.idx, w.n, w.mws, s));
+        // pass 1: match on channel 0 of the noisy image (2D-prethresholded patches in the
+        // high-noise regime), hard thresholding
+        if (ph.lambda2d > 0.0f)
+            DN_TRY(match_prethresh_any(x + off, (size_t)C * HW, nb, H, W, ph, tau1, thr, w.idx, w.n, s));
+        else
+            DN_TRY(match_any(x + off, (size_t)C * HW, nb, H, W, ph, tau1, p->precision, w.idx, w.n, w.mws, s));
         if (cudaMemsetAsync(w.acc, 0, kAccBytesPerPixel * Nb, s) != cudaSuccess) return DN_ECUDA;
-        DN_TRY(filter_any(true, tc, x + off, w.basic + off, w.idx, w.n, nb, C, H, W, sig, p->wiener, w.acc, s));
-        DN_TRY(normalize(w.acc, (C == 3 ? w.ycc : out) + off, nb, C, H, W, p->wiener.beta, s));
+        DN_TRY(filter_any(false, tc, x + off, nullptr, w.idx, w.n, nb, C, H, W, sig, ph, w.acc, s));
+        DN_TRY(normalize(w.acc, w.basic + off, nb, C, H, W, ph.beta, s, ph.patch));
+        // pass 2: match on channel 0 of the basic estimate, Wiener filtering
+        DN_TRY(match_any(w.basic + off, (size_t)C * HW, nb, H, W, pw, tau2, p->precision, w.idx, w.n, w.mws, s));
+        if (cudaMemsetAsync(w.acc, 0, kAccBytesPerPixel * Nb, s) != cudaSuccess) return DN_ECUDA;
+        DN_TRY(filter_any(true, tc, x + off, w.basic + off, w.idx, w.n, nb, C, H, W, sig, pw, w.acc, s));
+        DN_TRY(normalize(w.acc, (C == 3 ? w.ycc : out) + off, nb, C, H, W, pw.beta, s, pw.patch));
+        b0 = b1;
     }
     if (C == 3) DN_TRY(colour(w.ycc, out, B, H, W, 1, s));
     (void)N;
@@ -338,10 +393,20 @@ extern "C" {
 void dn_bm3d_default_params(dn_bm3d_params *p)
 {
     if (!p) return;
-    p->hard = dn_bm3d_pass{8, 3, 39, 16, 2500.0f, 5000.0f, 2.7f, 2.0f, 2.0f};
-    p->wiener = dn_bm3d_pass{8, 3, 39, 32, 400.0f, 3500.0f, 0.0f, 2.0f, 0.0f};
+    p->hard = dn_bm3d_pass{8, 3, 39, 16, 2500.0f, 5000.0f, 2.7f, 2.0f, 2.0f, 0, 0};
+    p->wiener = dn_bm3d_pass{8, 3, 39, 32, 400.0f, 3500.0f, 0.0f, 2.0f, 0.0f, 0, 0};
     p->precision = DN_FP32;
     p->sigma_regime = 0;
+}
+
+void dn_bm3d_high_noise_params(dn_bm3d_params *p)
+{
+    if (!p) return;
+    dn_bm3d_default_params(p);
+    p->hard.patch_high = 12;
+    p->hard.step_high = 4;
+    p->wiener.patch_high = 11;
+    p->wiener.step_high = 6;
 }
 
 void dn_nlm_default_params(dn_nlm_params *p)
@@ -410,7 +475,8 @@ dn_status denoise_bm3d(const float *noisy, float *out, int B, int C, int H, int 
                        const dn_bm3d_params *p, void *workspace, size_t ws_bytes, dn_stream_t stream)
 {
     DN_GUARD_BEGIN
-    if (!noisy || !out || !valid_image(B, C, H, W, 8) || !valid_sigmas(sigma, B) || !valid_bm3d(p))
+    if (!noisy || !out || !valid_image(B, C, H, W, 8) || !valid_sigmas(sigma, B) || !valid_bm3d(p) ||
+        !sides_ok(B, H, W, sigma, p))
         return DN_EINVAL;
     if (!prethresh_fits(B, W, sigma, p)) return DN_EUNSUPPORTED;
     Bm3dWs w = bm3d_layout(workspace, B, C, H, W, p);
@@ -439,7 +505,9 @@ dn_status denoise_hybrid(const float *noisy, float *out, int B, int C, int H, in
     if (!noisy || !out || !valid_image(B, C, H, W, 8) || !valid_sigmas(sigma, B) || !valid_cnn(cnn))
         return DN_EINVAL;
     if (prefilter == DN_PREFILTER_BM3D) {
-        if (!valid_bm3d(static_cast<const dn_bm3d_params *>(pp))) return DN_EINVAL;
+        if (!valid_bm3d(static_cast<const dn_bm3d_params *>(pp)) ||
+            !sides_ok(B, H, W, sigma, static_cast<const dn_bm3d_params *>(pp)))
+            return DN_EINVAL;
         if (!prethresh_fits(B, W, sigma, static_cast<const dn_bm3d_params *>(pp))) return DN_EUNSUPPORTED;
     } else if (prefilter == DN_PREFILTER_NLM) {
         if (!valid_nlm(static_cast<const dn_nlm_params *>(pp))) return DN_EINVAL;
@@ -550,7 +618,8 @@ dn_status dn_conv3x3_tc_bwd_data(const void *g, const float *w, const void *mask
 int dn_bm3d_halo(const dn_bm3d_params *p)
 {
     if (!valid_bm3d(p)) return -1;
-    return (2 * (p->hard.search / 2) + 7) + (2 * (p->wiener.search / 2) + 7);
+    auto kmax = [](const dn_bm3d_pass &q) { return q.patch_high > q.patch ? q.patch_high : q.patch; };
+    return (2 * (p->hard.search / 2) + kmax(p->hard) - 1) + (2 * (p->wiener.search / 2) + kmax(p->wiener) - 1);
 }
 
 namespace {
@@ -564,8 +633,11 @@ struct TilePlan {
 
 bool tile_plan(int H, int W, const dn_bm3d_params *p, int tile, TilePlan *tp)
 {
-    const int s1 = p->hard.step, s2 = p->wiener.step;
-    const int g = s1 / gcd_int(s1, s2) * s2;  // tile origins on both reference grids
+    // tile origins on every reference grid either regime uses
+    int g = 1;
+    const int steps[4] = {p->hard.step, p->wiener.step, p->hard.step_high, p->wiener.step_high};
+    for (int q : steps)
+        if (q > 0) g = g / gcd_int(g, q) * q;
     if (tile < 8 || g > 4096) return false;
     const int R = dn_bm3d_halo(p);
     tp->T = (tile + g - 1) / g * g;
@@ -622,7 +694,7 @@ dn_status denoise_bm3d_tiled(const float *noisy, float *out, int C, int H, int W
     DN_GUARD_BEGIN
     TilePlan tp;
     if (!noisy || !out || !valid_image(1, C, H, W, 8) || !valid_sigmas(&sigma, 1) || !valid_bm3d(p) ||
-        max_batch < 1 || max_batch > 1024 || !tile_plan(H, W, p, tile, &tp))
+        !sides_ok(1, H, W, &sigma, p) || max_batch < 1 || max_batch > 1024 || !tile_plan(H, W, p, tile, &tp))
         return DN_EINVAL;
     if (!prethresh_fits(1, tp.rw_max, &sigma, p)) return DN_EUNSUPPORTED;
     TiledWs w = tiled_layout(workspace, C, tp, p, max_batch);
@@ -700,7 +772,8 @@ const char *dn_strerror(dn_status st)
 
 size_t dn_bm3d_match_workspace_bytes(int B, int H, int W, const dn_bm3d_pass *p, int precision)
 {
-    if ((precision != DN_BF16 && precision != DN_BF16_MATCH) || !valid_image(B, 1, H, W, 8) || !valid_pass(p))
+    if ((precision != DN_BF16 && precision != DN_BF16_MATCH) || !valid_image(B, 1, H, W, 8) || !valid_pass(p) ||
+        p->patch != 8)
         return 0;
     return match_tc_workspace_bytes(B, H, W, *p);
 }
@@ -710,7 +783,7 @@ dn_status dn_bm3d_match(const float *guide, size_t plane_stride, int B, int H, i
                         dn_stream_t stream)
 {
     DN_GUARD_BEGIN
-    if (!guide || !idx || !n || !tau || !valid_image(B, 1, H, W, 8) || !valid_pass(p) ||
+    if (!guide || !idx || !n || !tau || !valid_pass(p) || !valid_image(B, 1, H, W, p->patch) ||
         plane_stride < (size_t)H * W)
         return DN_EINVAL;
     for (int b = 0; b < B; ++b)
@@ -728,12 +801,12 @@ dn_status dn_bm3d_match_prethresh(const float *guide, size_t plane_stride, int B
                                   dn_stream_t stream)
 {
     DN_GUARD_BEGIN
-    if (!guide || !idx || !n || !tau || !thr || !valid_image(B, 1, H, W, 8) || !valid_pass(p) ||
+    if (!guide || !idx || !n || !tau || !thr || !valid_pass(p) || !valid_image(B, 1, H, W, p->patch) ||
         plane_stride < (size_t)H * W)
         return DN_EINVAL;
     for (int b = 0; b < B; ++b)
         if (!(tau[b] > 0.0f) || !(thr[b] >= 0.0f) || !std::isfinite(thr[b])) return DN_EINVAL;
-    return match_prethresh(guide, plane_stride, B, H, W, *p, tau, thr, idx, n, (cudaStream_t)stream);
+    return match_prethresh_any(guide, plane_stride, B, H, W, *p, tau, thr, idx, n, (cudaStream_t)stream);
     DN_GUARD_END
 }
 
@@ -765,7 +838,8 @@ static dn_status filter_entry(bool wiener, const float *img, const float *basic,
                               int C, int H, int W, const float *sigma_c, const dn_bm3d_pass *p, int precision,
                               float *out, void *ws, size_t ws_bytes, cudaStream_t s)
 {
-    if (!img || !idx || !n || !out || !sigma_c || (wiener && !basic) || !valid_image(B, C, H, W, 8) || !valid_pass(p))
+    if (!img || !idx || !n || !out || !sigma_c || (wiener && !basic) || !valid_pass(p) ||
+        !valid_image(B, C, H, W, p->patch))
         return DN_EINVAL;
     for (int i = 0; i < B * C; ++i)
         if (!(sigma_c[i] > 0.0f) || !(sigma_c[i] <= 255.0f)) return DN_EINVAL;
@@ -776,13 +850,14 @@ static dn_status filter_entry(bool wiener, const float *img, const float *basic,
     const size_t HW = (size_t)H * W;
     for (int b0 = 0; b0 < B; b0 += 1024) {
         const int nb = B - b0 < 1024 ? B - b0 : 1024;
-        const size_t off = (size_t)b0 * C * HW, R = (size_t)grid_count(H, 8, p->step) * grid_count(W, 8, p->step);
+        const size_t off = (size_t)b0 * C * HW,
+                     R = (size_t)grid_count(H, p->patch, p->step) * grid_count(W, p->patch, p->step);
         if (cudaMemsetAsync(acc, 0, kAccBytesPerPixel * (size_t)nb * C * HW, s) != cudaSuccess) return DN_ECUDA;
         const int *ib = idx + (size_t)b0 * R * p->n2;
         const int *nbp = n + (size_t)b0 * R;
         DN_TRY(filter_any(wiener, precision == DN_BF16, img + off, wiener ? basic + off : nullptr, ib, nbp, nb, C, H, W,
                           sigma_c + (size_t)b0 * C, *p, acc, s));
-        DN_TRY(normalize(acc, out + off, nb, C, H, W, p->beta, s));
+        DN_TRY(normalize(acc, out + off, nb, C, H, W, p->beta, s, p->patch));
     }
     return DN_OK;
 }

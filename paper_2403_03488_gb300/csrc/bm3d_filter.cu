@@ -696,25 +696,27 @@ __device__ __forceinline__ float fixed_to_float(long long main, long long hi)
 }
 
 // out = num / den, den(y, x) = sum_{i,j} k_i k_j W(y - i, x - j) over patch
-// positions, evaluated separably in FP32 (fixed order, so reproducible) from
-// the exact weight sums.  One CTA per 32 x 32 output tile of one plane.
+// positions (i, j < K, the patch side), evaluated separably in FP32 (fixed
+// order, so reproducible) from the exact weight sums.  One CTA per 32 x 32
+// output tile of one plane.
 constexpr int kNT = 32;
 
 struct Kaiser1 {
-    float k[8];
+    float k[16];
 };
 
+template <int K>
 __global__ void __launch_bounds__(256) k_normalize(const long long *num, const long long *wsum,
                                                    const long long *num_hi, const long long *wsum_hi, float *out,
                                                    int H, int W, Kaiser1 kw)
 {
-    __shared__ float sw[kNT + 7][kNT + 8];  // W at positions (y0-7.., x0-7..)
-    __shared__ float sr[kNT + 7][kNT + 1];  // row pass
+    __shared__ float sw[kNT + K - 1][kNT + K];  // W at positions (y0-K+1.., x0-K+1..)
+    __shared__ float sr[kNT + K - 1][kNT + 1];  // row pass
     const size_t base = (size_t)blockIdx.z * H * W;
     const int y0 = blockIdx.y * kNT, x0 = blockIdx.x * kNT;
-    for (int e = threadIdx.x; e < (kNT + 7) * (kNT + 7); e += blockDim.x) {
-        const int r = e / (kNT + 7), cc = e - r * (kNT + 7);
-        const int y = y0 - 7 + r, x = x0 - 7 + cc;
+    for (int e = threadIdx.x; e < (kNT + K - 1) * (kNT + K - 1); e += blockDim.x) {
+        const int r = e / (kNT + K - 1), cc = e - r * (kNT + K - 1);
+        const int y = y0 - (K - 1) + r, x = x0 - (K - 1) + cc;
         float v = 0.0f;
         if (y >= 0 && y < H && x >= 0 && x < W) {
             const size_t i = base + (size_t)y * W + x;
@@ -723,11 +725,11 @@ __global__ void __launch_bounds__(256) k_normalize(const long long *num, const l
         sw[r][cc] = v;
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < (kNT + 7) * kNT; e += blockDim.x) {
+    for (int e = threadIdx.x; e < (kNT + K - 1) * kNT; e += blockDim.x) {
         const int r = e / kNT, cc = e - r * kNT;
         float acc = 0.0f;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc = fmaf(kw.k[j], sw[r][cc + 7 - j], acc);
+        for (int j = 0; j < K; ++j) acc = fmaf(kw.k[j], sw[r][cc + K - 1 - j], acc);
         sr[r][cc] = acc;
     }
     __syncthreads();
@@ -737,7 +739,7 @@ __global__ void __launch_bounds__(256) k_normalize(const long long *num, const l
         if (y >= H || x >= W) continue;
         float den = 0.0f;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) den = fmaf(kw.k[i], sr[r + 7 - i][cc], den);
+        for (int i = 0; i < K; ++i) den = fmaf(kw.k[i], sr[r + K - 1 - i][cc], den);
         const size_t o = base + (size_t)y * W + x;
         out[o] = fixed_to_float(num[o], num_hi[o]) / den;  // the 2^36 scale cancels
     }
@@ -832,17 +834,25 @@ dn_status filter_wiener_fp32(const float *noisy, const float *basic, const int *
     return filter_common(true, noisy, basic, idx, n, B, C, H, W, sig, p, acc, s);
 }
 
-dn_status normalize(const float *acc, float *out, int B, int C, int H, int W, float beta, cudaStream_t s)
+dn_status normalize(const float *acc, float *out, int B, int C, int H, int W, float beta, cudaStream_t s, int K)
 {
     const size_t N = (size_t)B * C * H * W;
-    Tables t;
-    make_tables(beta, &t);
     Kaiser1 kw;
-    for (int i = 0; i < 8; ++i) kw.k[i] = t.kai1[i];
+    if (K == 8) {
+        Tables t;
+        make_tables(beta, &t);
+        for (int i = 0; i < 8; ++i) kw.k[i] = t.kai1[i];
+    } else if (K == 11 || K == 12) {
+        make_kaiser(K, beta, kw.k);
+    } else {
+        return DN_EUNSUPPORTED;
+    }
     const dim3 grid((W + kNT - 1) / kNT, (H + kNT - 1) / kNT, B * C);
     return launch("bm3d_normalize", s, [&] {
         const long long *fx = reinterpret_cast<const long long *>(acc);
-        k_normalize<<<grid, 256, 0, s>>>(fx, fx + N, fx + 2 * N, fx + 3 * N, out, H, W, kw);
+        if (K == 8) k_normalize<8><<<grid, 256, 0, s>>>(fx, fx + N, fx + 2 * N, fx + 3 * N, out, H, W, kw);
+        else if (K == 11) k_normalize<11><<<grid, 256, 0, s>>>(fx, fx + N, fx + 2 * N, fx + 3 * N, out, H, W, kw);
+        else k_normalize<12><<<grid, 256, 0, s>>>(fx, fx + N, fx + 2 * N, fx + 3 * N, out, H, W, kw);
     });
 }
 

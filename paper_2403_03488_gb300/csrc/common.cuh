@@ -21,6 +21,8 @@ struct Tables {
 };
 
 void make_tables(float beta, Tables *t);
+// Kaiser window of length M: w[m] = I0(beta sqrt(1 - (2m/(M-1) - 1)^2)) / I0(beta).
+void make_kaiser(int M, float beta, float *w);
 
 // Per-image scalars of one launch chunk.
 struct ImageScalars {
@@ -96,8 +98,9 @@ dn_status filter_tc(bool wiener, const float *img, const float *basic, const int
 // Shared memory of the tensor-core filter (0: the search window is too large);
 // *tr receives the side of its tile of reference positions.
 size_t filter_tc_smem_bytes(bool wiener, int step, int search, int *tr);
-// out = num / den with den = the Kaiser window (parameter beta) correlated with wsum
-dn_status normalize(const float *acc, float *out, int B, int C, int H, int W, float beta, cudaStream_t s);
+// out = num / den with den = the Kaiser window (parameter beta, length = the
+// patch side K of the pass) correlated with wsum
+dn_status normalize(const float *acc, float *out, int B, int C, int H, int W, float beta, cudaStream_t s, int K = 8);
 dn_status colour(const float *in, float *out, int B, int H, int W, int inverse, cudaStream_t s);
 dn_status nlm_launch(const float *in, float *out, int B, int C, int H, int W, const float *sig_guide,
                      const dn_nlm_params &p, cudaStream_t s);
@@ -124,6 +127,17 @@ dn_status match_tc(const float *guide, size_t plane, int B, int H, int W, const 
                    int *idx, int *n, int *err, int *fb_ws, cudaStream_t s, float *cross = nullptr, int cross_tx = 0,
                    int cross_ty = 0);
 size_t conv_tc_smem_bytes();
+// Larger patches (bm3d_large.cu): matching on pixels (sides 11, 12) or on
+// 2D-prethresholded patches (side 12), and both filtering passes (11, 12).
+bool large_patch_supported(int K);
+bool large_prethresh_supported(int K);
+dn_status match_large(const float *guide, size_t plane, int B, int H, int W, const dn_bm3d_pass &p, const float *tau,
+                      int *idx, int *n, cudaStream_t s);
+size_t match_pre_large_smem_bytes(int W, const dn_bm3d_pass &p);
+dn_status match_prethresh_large(const float *guide, size_t plane, int B, int H, int W, const dn_bm3d_pass &p,
+                                const float *tau, const float *thr, int *idx, int *n, cudaStream_t s);
+dn_status filter_large(bool wiener, const float *img, const float *basic, const int *idx, const int *n, int B, int C,
+                       int H, int W, const float *sig, const dn_bm3d_pass &p, float *acc, cudaStream_t s);
 // Flexible network contractions on the tensor cores (flnet_tc.cu): BF16 operands, FP32 in and out.
 dn_status pw_fwd_tc(const float *x, const float *w, const float *b, float *y, int N, int Cin, int Cout, int HW,
                     int relu, int transposed, int *err, cudaStream_t s);

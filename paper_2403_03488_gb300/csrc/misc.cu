@@ -22,6 +22,14 @@ static double bessel_i0_series(double x)
     return sum;
 }
 
+void make_kaiser(int M, float beta, float *w)
+{
+    for (int m = 0; m < M; ++m) {
+        const double r = M > 1 ? 2.0 * m / (M - 1) - 1.0 : 0.0;
+        w[m] = (float)(bessel_i0_series(beta * std::sqrt(std::fmax(0.0, 1.0 - r * r))) / bessel_i0_series(beta));
+    }
+}
+
 void make_tables(float beta, Tables *t)
 {
     const double pi = 3.14159265358979323846;
