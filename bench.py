@@ -129,15 +129,16 @@ class ClockSampler:
 # algorithmic work of the dominant kernels (per launch)
 # ---------------------------------------------------------------------------
 
-def match_pairs(Hh, Ww, step=3, search=39):
+def match_pairs(Hh, Ww, step=3, search=39, k=8):
     """Exact number of (reference, candidate) distance evaluations of one
-    matching launch over one image (candidates clipped to the image)."""
+    matching launch over one image (patches of side k, candidates clipped to
+    the image)."""
     from paper_2403_03488_gb300 import api
     hs = search // 2
 
     def per_axis(L):
-        g = np.array(api.grid(L, 8, step))
-        return (np.minimum(L - 8, g + hs) - np.maximum(0, g - hs) + 1).astype(np.int64)
+        g = np.array(api.grid(L, k, step))
+        return (np.minimum(L - k, g + hs) - np.maximum(0, g - hs) + 1).astype(np.int64)
 
     return int(per_axis(Hh).sum() * per_axis(Ww).sum())
 
@@ -149,28 +150,37 @@ def match_pairs(Hh, Ww, step=3, search=39):
 # the group transform as an n x n product per coefficient (2 n per coefficient
 # and direction); pass 1 transforms the noisy group forward and back (2 + 2),
 # pass 2 the basic and noisy groups forward and the estimate back (3 + 3).
-# "alu": the separable form the CUDA-core kernels evaluate: each 2D DCT as 16
-# 8-point matrix-vector products (2 x 8 x 8 each = 2048 FLOP per patch), the
+# "alu": the separable form the CUDA-core kernels evaluate: each 2D DCT as 2k
+# k-point matrix-vector products (2 k^2 each: 2048 FLOP per 8 x 8 patch), the
 # group transform as a fast Walsh-Hadamard transform (log2 n additions per
 # coefficient and direction), 2 FLOP per coefficient for shrinkage (pass 2:
-# 4, the Wiener gain) and 3 per pixel for the windowed aggregation.
-def filter_flops_per_patch(wiener, n):
+# 4, the Wiener gain) and 3 per pixel for the windowed aggregation.  k: the
+# patch side (8; 12 and 11 in the high-noise profile's passes).
+def filter_flops_per_patch(wiener, n, k=8):
     lg = max(1, int(np.log2(n)))
     nt = 3 if wiener else 2  # 2D transforms per patch
-    tensor = nt * 2 * 64 * 64 + nt * 2 * n * 64
-    alu = nt * 2048 + nt * 64 * lg + (4 if wiener else 2) * 64 + 3 * 64
+    k2 = k * k
+    tensor = nt * 2 * k2 * k2 + nt * 2 * n * k2
+    alu = nt * 4 * k ** 3 + nt * k2 * lg + (4 if wiener else 2) * k2 + 3 * k2
     return tensor, alu
 
 
-def filter_work(wiener, Hh, Ww, batch, step=3):
+def filter_work(wiener, Hh, Ww, batch, step=3, k=8):
     """(tensor FLOP, ALU FLOP) of one filtering launch over `batch` images,
     every group full (n = 16 in pass 1, 32 in pass 2): an upper count, since
     groups below the threshold hold fewer patches."""
     from paper_2403_03488_gb300 import api
-    refs = len(api.grid(Hh, 8, step)) * len(api.grid(Ww, 8, step)) * batch
+    refs = len(api.grid(Hh, k, step)) * len(api.grid(Ww, k, step)) * batch
     n = 32 if wiener else 16
-    t, a = filter_flops_per_patch(wiener, n)
+    t, a = filter_flops_per_patch(wiener, n, k)
     return refs * n * t, refs * n * a
+
+
+# Patch side and grid step of the larger-patch kernels (the high-noise
+# profile: 12 x 12 on a step-4 grid in pass 1, 11 x 11 on a step-6 grid in
+# pass 2; the pixel matcher runs pass 2 there).
+LARGE = {"bm3d_match_pre_large": (12, 4), "bm3d_match_large_fp32": (11, 6),
+         "bm3d_filter_hard_large_fp32": (12, 4), "bm3d_filter_wiener_large_fp32": (11, 6)}
 
 
 def algorithmic(kernel, launches_per_step, batch, hw=None):
@@ -181,6 +191,13 @@ def algorithmic(kernel, launches_per_step, batch, hw=None):
     if os.path.exists(p):
         peaks = json.load(open(p))
     fpk, fnote = fp32_peak(hw), fp32_note(hw)
+    if kernel in LARGE:
+        k, step = LARGE[kernel]
+        if kernel.startswith("bm3d_match"):
+            # 3 FLOP (sub, mul, add) per pixel or prethresholded coefficient of each pair
+            return "alu", "TFLOP/s", 3.0 * k * k * match_pairs(H, W, step, 39, k) * min(batch, 64), fpk, fnote
+        tensor, alu = filter_work("wiener" in kernel, H, W, batch, step, k)
+        return "alu", "TFLOP/s", float(alu), fpk, fnote + " (separable count)"
     if kernel.startswith("bm3d_match"):
         # one launch covers up to 64 images of one pass; 192 FLOP (sub, mul, add over 64 pixels or
         # prethresholded coefficients) per (reference, candidate) pair
@@ -241,7 +258,8 @@ def kernel_rooflines(res, steps, batch, hw=None):
     if os.path.exists(p):
         peaks = json.load(open(p))
     for k, (n, ms) in res.items():
-        if not k.startswith(("bm3d_match_fp32", "bm3d_match_pre", "bm3d_match_tc", "bm3d_filter_", "nlm_fp32",
+        if not k.startswith(("bm3d_match_fp32", "bm3d_match_pre", "bm3d_match_tc", "bm3d_match_large", "bm3d_filter_",
+                             "nlm_fp32",
                              "fl_pw_fwd", "fl_deconv2x2_fwd", "fl_dw3x3_fwd", "conv3x3_tc_bf16", "conv3x3_tc_pair",
                              "conv_first_bf16", "conv_last_bf16", "bm3d_normalize", "error_reduce_fp64")):
             continue
@@ -258,7 +276,8 @@ def kernel_rooflines(res, steps, batch, hw=None):
             out[k].update({"tensor_achieved": round(t_ach, 3), "tensor_peak": round(bf, 1),
                            "tensor_frac": round(t_ach / bf, 4)})
         if k.startswith("bm3d_filter_") and k.endswith("fp32"):
-            tensor, _ = filter_work("wiener" in k, H, W, batch)
+            ks, st = LARGE.get(k, (8, 3))
+            tensor, _ = filter_work("wiener" in k, H, W, batch, st, ks)
             t_ach = tensor / (avg / 1e3) / 1e12
             bf = peaks.get("bf16_tflops_sustained", 1700.0)
             out[k].update({"tensor_achieved": round(t_ach, 3), "tensor_peak": round(bf, 1),

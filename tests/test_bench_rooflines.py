@@ -66,3 +66,24 @@ def test_fp32_peak_from_device_numbers(bench):
     hw2 = dict(hw, sm_count=144, sm_mhz=1900.0)
     b, u, w, peak, note = bench.algorithmic("bm3d_match_fp32", 2, 2, hw2)
     assert peak == pytest.approx(144 * 128 * 2 * 1.9e9 / 1e12) and "144 SM" in note
+
+
+def test_larger_patch_work_counts():
+    """The larger-patch counts reduce to the 8 x 8 ones at k = 8 (2048 FLOP per
+    separable 2D DCT, 8192 per dense one) and scale with k as the definitions
+    say: 4 k^3 per separable 2D DCT, 2 k^4 per dense one, 3 k^2 per matching pair."""
+    import bench
+    t8, a8 = bench.filter_flops_per_patch(False, 16, 8)
+    assert t8 == 2 * 2 * 64 * 64 + 2 * 2 * 16 * 64
+    assert a8 == 2 * 2048 + 2 * 64 * 4 + 2 * 64 + 3 * 64
+    t12, a12 = bench.filter_flops_per_patch(True, 32, 12)
+    assert t12 == 3 * 2 * 144 * 144 + 3 * 2 * 32 * 144
+    assert a12 == 3 * 4 * 12 ** 3 + 3 * 144 * 5 + 4 * 144 + 3 * 144
+    assert bench.match_pairs(40, 40, 3, 39, 8) == bench.match_pairs(40, 40)
+    old = (bench.H, bench.W)
+    try:
+        bench.H = bench.W = 64
+        b, u, w, _, _ = bench.algorithmic("bm3d_match_pre_large", 1, 2)
+        assert (b, u) == ("alu", "TFLOP/s") and w == 3.0 * 144 * bench.match_pairs(64, 64, 4, 39, 12) * 2
+    finally:
+        bench.H, bench.W = old
