@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(kQT) k_match_pre_k(const __grid_constant__ Pre
     auto load_row = [&](int y) {
         for (int i = tid; i < npx; i += kQT) prow[i] = g[(size_t)y * W + X0 + i];
     };
-    float nxt[kQF];
+    float nxt[kQF];  // the next pixel row, in flight while a row is matched (npx <= kQT kQF: host check)
     auto fetch_row = [&](int y) {
 #pragma unroll
         for (int j = 0; j < kQF; ++j) {
@@ -296,12 +296,10 @@ __global__ void __launch_bounds__(kQT) k_match_pre_k(const __grid_constant__ Pre
     const int xs = max(0, x0 - a.hs), xe = min(W - K, x0 + a.hs);
     const int ys = max(0, y0 - a.hs), ye = min(H - K, y0 + a.hs);
 
-    const bool prefetch = npx <= kQT * kQF;  // else (wide windows) rows are loaded directly
-    if (prefetch) fetch_row(Y0 + K - 1);
+    fetch_row(Y0 + K - 1);
     for (int yy = Y0; yy <= Y1; ++yy) {
         __syncthreads();  // the previous row's readers of prow and S are done
-        if (prefetch) store_row();  // pixel row yy + K - 1
-        else load_row(yy + K - 1);
+        store_row();      // pixel row yy + K - 1
         __syncthreads();
         row_transform(yy + K - 1);
         __syncthreads();
@@ -320,7 +318,7 @@ __global__ void __launch_bounds__(kQT) k_match_pre_k(const __grid_constant__ Pre
             }
         }
         __syncthreads();
-        if (prefetch && yy < Y1) fetch_row(yy + K);
+        if (yy < Y1) fetch_row(yy + K);
         if (!active || yy < ys || yy > ye) continue;
         for (int x = xs; x <= xe; ++x) {
             if (x == x0 && yy == y0) continue;
@@ -847,7 +845,9 @@ dn_status match_prethresh_large(const float *guide, size_t plane, int B, int H, 
     a.spad = pre_spad(K, p.step);
     make_large_tables(K, p.beta, &a.t);
     const size_t smem = match_pre_large_smem_bytes(W, p);
-    if (smem > 200 * 1024) return DN_EUNSUPPORTED;
+    // (about 1.2 KB per staged column: the 200 KB bound keeps a row's K - 1 + columns far below
+    // the kQT kQF pixels the prefetch registers hold)
+    if (smem > 200 * 1024 || a.ncol_max + K - 1 > kQT * kQF) return DN_EUNSUPPORTED;
     for (int b0 = 0; b0 < B; b0 += kChunk) {
         const int nb = B - b0 < kChunk ? B - b0 : kChunk;
         a.g = guide + (size_t)b0 * plane;
