@@ -279,3 +279,36 @@ def test_denoise_high_noise_profile_full_size_properties(oracle):
     for b in range(16):
         assert oracle.psnr(o[b], clean[b]) > oracle.psnr(noisy[b], clean[b]) + 10.0
     assert A.device_error() == 0
+
+
+def test_noalloc_with_the_larger_patches_equals_denoise_bm3d():
+    """The allocation-free entry point sizes its request for both regimes'
+    grids and runs the larger patches bit-identically to denoise_bm3d."""
+    A = api()
+    params = A.default_bm3d_params(high_noise_patches=True)
+    _, noisy = synth.make_batch([77, 78], 96, 120, [50.0, 25.0])
+    x = dev(noisy)
+    ref = host(A.denoise_bm3d(x, [50.0, 25.0], params))
+    got = host(A.denoise_bm3d_noalloc(x, [50.0, 25.0], params))
+    np.testing.assert_array_equal(got, ref)
+
+
+def test_hybrid_with_the_larger_patches_is_the_network_on_their_bm3d(oracle):
+    """denoise_hybrid with the high-noise profile = the BF16 network applied
+    to denoise_bm3d's output with the same parameters (bit for bit), and the
+    network still gains over that BM3D at sigma = 50."""
+    import torch
+    A = api()
+    from paper_2403_03488_gb300.serve import load_weights
+    weights = load_weights().cuda()
+    params = A.default_bm3d_params(high_noise_patches=True)
+    clean, noisy = synth.make_batch([79, 80], 128, 128, 50.0)
+    x = dev(noisy)
+    pre = A.denoise_bm3d(x, 50.0, params)
+    out = A.denoise_hybrid(x, 50.0, weights, prefilter_params=params, cnn_precision=A.DN_BF16)
+    net = A.cnn_forward(x[:, 0].contiguous(), pre[:, 0].contiguous(), weights, precision=A.DN_BF16)
+    np.testing.assert_array_equal(host(out)[:, 0], host(net))
+    o, p_ = host(out), host(pre)
+    for b in range(2):
+        assert oracle.psnr(o[b], clean[b]) > oracle.psnr(p_[b], clean[b])
+    assert torch.isfinite(out).all()
