@@ -180,18 +180,20 @@ const char *dn_strerror(dn_status s);
 /* ---- one large image in tiles with a halo ---------------------------------
  * A BM3D output pixel depends only on the noisy pixels within a fixed
  * distance (per axis) of it: a pass-1 estimate at p comes from the groups
- * whose reference lies within search/2 + 7 of p, and each group's matching
- * and filtering read pixels within another search/2 + 7 of its reference;
- * the second pass does the same on the basic estimate.  So a tile extended by
- * that radius on every side (clipped at the image border), with its origin on
- * both passes' reference grids, yields exactly the whole-image result inside
+ * whose reference lies within search/2 + k - 1 of p (k the patch side), and
+ * each group's matching and filtering read pixels within another
+ * search/2 + k - 1 of its reference; the second pass does the same on the
+ * basic estimate.  So a tile extended by that radius on every side (clipped
+ * at the image border), with its origin on the reference grids, yields exactly the whole-image result inside
  * its interior: every kernel here is deterministic and the aggregation sums
  * are exact, so the tiled result equals denoise_bm3d bit for bit.  This bounds
  * the workspace of very large images (and shards one image across devices,
  * each processing its tiles). */
 
-/* The radius: (2 (hard.search / 2) + 7) + (2 (wiener.search / 2) + 7),
- * 90 for the defaults; -1 for invalid parameters. */
+/* The radius: (2 (hard.search / 2) + k1 - 1) + (2 (wiener.search / 2) + k2 - 1),
+ * k the larger patch side a pass takes in either regime (patch, patch_high):
+ * 90 for the defaults, 97 with dn_bm3d_high_noise_params; -1 for invalid
+ * parameters.  Tile origins lie on every grid step either regime uses. */
 int dn_bm3d_halo(const dn_bm3d_params *p);
 
 /* Workspace of denoise_bm3d_tiled (0 for invalid arguments). */
