@@ -19,20 +19,24 @@
 // image window staged in shared memory, and aggregates its groups into a
 // shared-memory num window first (one global add per window pixel instead of
 // one per contribution).  A warp filters one group at a time (in the first
-// pass, two groups of at most 16 patches at once): lane k owns patch k and
-// computes its 8x8 DCT with an even/odd fast DCT in two passes through its
-// row of a per-warp transpose buffer (rows of 65 floats, conflict-free both
-// ways), two 1D transforms per packed FP32x2 instruction (scalar for the noisy
-// patches of the second pass, whose gains then hold 64 registers); for the
-// group transform each lane owns two coefficient positions across all patches
-// and runs the Walsh-Hadamard butterflies for both in packed registers; the
-// inverse goes back the same way, and the warp then aggregates patch by patch
-// with its lanes spread over the 64 pixels.
+// pass, two groups of at most 16 patches at once): lane k owns patch k,
+// holds it in registers and computes its 8x8 DCT with an even/odd fast DCT,
+// two 1D transforms per packed FP32x2 instruction (row pairs, then column
+// pairs; the noisy patches of the second pass, whose gains then hold 64
+// registers, take a scalar version through the buffer below), and writes the
+// spectrum to its row of a per-warp transpose buffer (rows of 65 floats,
+// conflict-free both ways); for the group transform each lane owns two
+// coefficient positions across all patches and runs the Walsh-Hadamard
+// butterflies for both in packed registers; the inverse goes back the same
+// way, and the warp then aggregates in chunks of patches with its lanes spread
+// over the 64 pixels (each 64-bit fixed-point addition to the shared window
+// as two 32-bit atomics, see split_add).
 #include <cmath>
 
 #include "common.cuh"
 #include "f32x2.cuh"
 #include "fixed_point.cuh"
+#include "tc.cuh"
 
 namespace dn {
 
@@ -329,48 +333,9 @@ __device__ __forceinline__ bool in_window(const Window &win, int py, int px)
     return py >= win.Y0 && py + 8 <= win.Y0 + win.RH && px >= win.X0 && px + 8 <= win.X0 + win.RW;
 }
 
-// Forward 2D DCT of the valid lanes' patches into row `lane` of T, in two
-// passes with two 1D transforms per packed instruction: patch rows (r, r+1)
-// from the shared image window (or from global memory when some patch of the
-// batch lies outside it, only possible for match lists not produced by the
-// matcher of this library) into T, then column pairs (j, j+1) of T in place.
-__device__ __forceinline__ void dct_2pass(float *T, const Window &win, const float *wimg, const float *gimg, int W,
-                                          bool valid, int lane, int py, int px, const DctK2 &K)
-{
-    const bool all_in = __all_sync(0xffffffffu, !valid || in_window(win, py, px));
-    if (valid) {
-        const float *src = all_in ? wimg + (py - win.Y0) * win.RW + (px - win.X0) : gimg + (size_t)py * W + px;
-        const int stride = all_in ? win.RW : W;
-        float *row = T + lane * kTS;
-#pragma unroll
-        for (int r = 0; r < 8; r += 2) {
-            f2 x[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) x[j] = f2_pack(src[r * stride + j], src[(r + 1) * stride + j]);
-            dct8_2(x, K);
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                row[r * 8 + j] = f2_lo(x[j]);
-                row[(r + 1) * 8 + j] = f2_hi(x[j]);
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < 8; j += 2) {
-            f2 x[8];
-#pragma unroll
-            for (int r = 0; r < 8; ++r) x[r] = f2_pack(row[r * 8 + j], row[r * 8 + j + 1]);
-            dct8_2(x, K);
-#pragma unroll
-            for (int r = 0; r < 8; ++r) {
-                row[r * 8 + j] = f2_lo(x[r]);
-                row[r * 8 + j + 1] = f2_hi(x[r]);
-            }
-        }
-    }
-}
-
-// Scalar variant of dct_2pass with the smallest register footprint, for the
-// noisy patches of the Wiener pass (the gains occupy 64 registers then).
+// Scalar variant of dct_reg with the smallest register footprint (the row
+// pass goes through row `lane` of T), for the noisy patches of the Wiener
+// pass (the gains occupy 64 registers then).
 __device__ __forceinline__ void dct_2pass_scalar(float *T, const Window &win, const float *wimg, const float *gimg,
                                                  int W, bool valid, int lane, int py, int px, const DctK &K)
 {
@@ -400,28 +365,61 @@ __device__ __forceinline__ void dct_2pass_scalar(float *T, const Window &win, co
     }
 }
 
-// Inverse 2D DCT of row `lane` of T in place: column pairs, then row pairs.
-__device__ __forceinline__ void idct_2pass(float *T, bool valid, int lane, const DctK2 &K)
+// Forward 2D DCT of the valid lanes' patches kept in registers: row pairs
+// (r, r+1) packed for the row pass, column pairs (j, j+1) for the column pass;
+// the result goes to row `lane` of T.
+__device__ __forceinline__ void dct_reg(float *T, const Window &win, const float *wimg, const float *gimg, int W,
+                                        bool valid, int lane, int py, int px, const DctK2 &K)
 {
+    const bool all_in = __all_sync(0xffffffffu, !valid || in_window(win, py, px));
     if (valid) {
+        const float *src = all_in ? wimg + (py - win.Y0) * win.RW + (px - win.X0) : gimg + (size_t)py * W + px;
+        const int stride = all_in ? win.RW : W;
+        f2 x[4][8];
+#pragma unroll
+        for (int r2 = 0; r2 < 4; ++r2) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) x[r2][j] = f2_pack(src[2 * r2 * stride + j], src[(2 * r2 + 1) * stride + j]);
+            dct8_2(x[r2], K);
+        }
         float *row = T + lane * kTS;
 #pragma unroll
         for (int j = 0; j < 8; j += 2) {
-            f2 x[8];
+            f2 y[8];
 #pragma unroll
-            for (int r = 0; r < 8; ++r) x[r] = f2_pack(row[r * 8 + j], row[r * 8 + j + 1]);
-            idct8_2(x, K);
+            for (int r = 0; r < 8; ++r)
+                y[r] = (r & 1) ? f2_pack(f2_hi(x[r >> 1][j]), f2_hi(x[r >> 1][j + 1]))
+                               : f2_pack(f2_lo(x[r >> 1][j]), f2_lo(x[r >> 1][j + 1]));
+            dct8_2(y, K);
 #pragma unroll
             for (int r = 0; r < 8; ++r) {
-                row[r * 8 + j] = f2_lo(x[r]);
-                row[r * 8 + j + 1] = f2_hi(x[r]);
+                row[r * 8 + j] = f2_lo(y[r]);
+                row[r * 8 + j + 1] = f2_hi(y[r]);
             }
+        }
+    }
+}
+
+// Inverse 2D DCT of row `lane` of T in place, the patch kept in registers
+// between the column pass and the row pass.
+__device__ __forceinline__ void idct_reg(float *T, bool valid, int lane, const DctK2 &K)
+{
+    if (valid) {
+        float *row = T + lane * kTS;
+        f2 y[4][8];
+#pragma unroll
+        for (int j2 = 0; j2 < 4; ++j2) {
+#pragma unroll
+            for (int r = 0; r < 8; ++r) y[j2][r] = f2_pack(row[r * 8 + 2 * j2], row[r * 8 + 2 * j2 + 1]);
+            idct8_2(y[j2], K);
         }
 #pragma unroll
         for (int r = 0; r < 8; r += 2) {
             f2 x[8];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) x[j] = f2_pack(row[r * 8 + j], row[(r + 1) * 8 + j]);
+            for (int j = 0; j < 8; ++j)
+                x[j] = (j & 1) ? f2_pack(f2_hi(y[j >> 1][r]), f2_hi(y[j >> 1][r + 1]))
+                               : f2_pack(f2_lo(y[j >> 1][r]), f2_lo(y[j >> 1][r + 1]));
             idct8_2(x, K);
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
@@ -439,7 +437,7 @@ template <int N>
 __device__ __forceinline__ float wiener_group(const FilterArgs &a, const Window &win, float *T, size_t cbase,
                                               int lane, int py, int px, float s2, const DctK2 &K)
 {
-    dct_2pass(T, win, win.basic, a.basic + cbase, a.W, lane < N, lane, py, px, K);
+    dct_reg(T, win, win.basic, a.basic + cbase, a.W, lane < N, lane, py, px, K);
     __syncwarp();
     f2 om[N];
     const float wsq = wiener_gains<N>(T, lane, s2, om);
@@ -476,13 +474,26 @@ __device__ __forceinline__ void agg_chunk(const FilterArgs &a, const Window &win
         fast = fast && fabsf(f2_lo(t[q])) < 4194304.0f && fabsf(f2_hi(t[q])) < 4194304.0f;  // |term| < 512
     }
     if (__all_sync(0xffffffffu, fast)) {
+        // the low words of up to 4 patches first, then their high words (the
+        // carries need the low words' previous values)
+        constexpr int H = K < 4 ? K : 4;
 #pragma unroll
-        for (int q = 0; q < K; ++q) {
-            const int o = __shfl_sync(0xffffffffu, wo, k0 + q) + poff;
-            long long x0, x1;
-            fix_t2(t[q], x0, x1);
-            atomicAdd(win.num + o, (unsigned long long)x0);
-            atomicAdd(win.num + o + 4 * win.RS, (unsigned long long)x1);
+        for (int q0 = 0; q0 < K; q0 += H) {
+            long long x[2 * H];
+            unsigned old[2 * H];
+            int os[H];
+#pragma unroll
+            for (int q = 0; q < H; ++q) {
+                os[q] = __shfl_sync(0xffffffffu, wo, k0 + q0 + q) + poff;
+                fix_t2(t[q0 + q], x[2 * q], x[2 * q + 1]);
+                old[2 * q] = split_lo(win.num + os[q], x[2 * q]);
+                old[2 * q + 1] = split_lo(win.num + os[q] + 4 * win.RS, x[2 * q + 1]);
+            }
+#pragma unroll
+            for (int q = 0; q < H; ++q) {
+                split_hi(win.num + os[q], x[2 * q], old[2 * q]);
+                split_hi(win.num + os[q] + 4 * win.RS, x[2 * q + 1], old[2 * q + 1]);
+            }
         }
     } else {
 #pragma unroll
@@ -490,8 +501,8 @@ __device__ __forceinline__ void agg_chunk(const FilterArgs &a, const Window &win
             const int o = __shfl_sync(0xffffffffu, wo, k0 + q) + poff;
             const size_t g = cbase + (size_t)__shfl_sync(0xffffffffu, gpos, k0 + q) + pg;
             const Fix f0 = to_fixed(f2_lo(t[q]) * (1.0f / 8192.0f)), f1 = to_fixed(f2_hi(t[q]) * (1.0f / 8192.0f));
-            atomicAdd(win.num + o, f0.lo);
-            atomicAdd(win.num + o + 4 * win.RS, f1.lo);
+            split_add(win.num + o, (long long)f0.lo);
+            split_add(win.num + o + 4 * win.RS, (long long)f1.lo);
             if (f0.hi != 0) atomicAdd(a.num_hi + g, (unsigned long long)f0.hi);
             if (f1.hi != 0) atomicAdd(a.num_hi + g + 4 * (size_t)a.W, (unsigned long long)f1.hi);
         }
@@ -550,7 +561,7 @@ __device__ __forceinline__ void aggregate(const FilterArgs &a, const Window &win
         for (int h = 0; h < 2; ++h) {
             const int i = i0 + 4 * h;
             if (inside) {
-                atomicAdd(win.num + (ly0 + i) * win.RS + lx0 + j, f[h].lo);
+                split_add(win.num + (ly0 + i) * win.RS + lx0 + j, (long long)f[h].lo);
             } else {
                 atomicAdd(a.num + cbase + (size_t)(yk + i) * a.W + xk + j, f[h].lo);
             }
@@ -566,7 +577,7 @@ __device__ __forceinline__ void hard_batch(const FilterArgs &a, const Window &wi
                                            int nA, int nB, int lane, int py, int px, const float (&ka)[2])
 {
     const bool valid = lane < nA || (lane >= 16 && lane < 16 + nB);
-    dct_2pass(T, win, win.img, a.img + cbase, a.W, valid, lane, py, px, pack_dct());
+    dct_reg(T, win, win.img, a.img + cbase, a.W, valid, lane, py, px, pack_dct());
     __syncwarp();
     const float thr = a.lambda * sig;
     const int nharA = __reduce_add_sync(0xffffffffu, hard_columns(T, nA, lane, thr));
@@ -575,7 +586,7 @@ __device__ __forceinline__ void hard_batch(const FilterArgs &a, const Window &wi
     const float wA = nharA > 0 ? 1.0f / (float)nharA : sig * sig;
     const float wB = nharB > 0 ? 1.0f / (float)nharB : sig * sig;
     __syncwarp();
-    idct_2pass(T, valid, lane, pack_dct());
+    idct_reg(T, valid, lane, pack_dct());
     __syncwarp();
     aggregate(a, win, T, cbase, 0, nA, lane, py, px, wA, ka);
     if (nB) aggregate(a, win, T, cbase, 16, nB, lane, py, px, wB, ka);
@@ -600,7 +611,7 @@ __device__ __forceinline__ void wiener_one(const FilterArgs &a, const Window &wi
     for (int o = 16; o > 0; o >>= 1) wsq += __shfl_xor_sync(0xffffffffu, wsq, o);
     const float w = wsq > 0.0f ? 1.0f / wsq : s2;  // 1/(sigma^2 sum w^2) or 1, times sigma^2
     __syncwarp();
-    idct_2pass(T, lane < n, lane, pack_dct());
+    idct_reg(T, lane < n, lane, pack_dct());
     __syncwarp();
     aggregate(a, win, T, cbase, 0, n, lane, py, px, w, ka);
     __syncwarp();
@@ -648,9 +659,11 @@ __global__ void __launch_bounds__(512) k_filter(FilterArgs a, int TR, int RH, in
         for (int i = threadIdx.x; i < rh * rw; i += blockDim.x) {
             const int ly = i / rw, lx = i - ly * rw;
             const size_t g = cbase + (size_t)(win.Y0 + ly) * a.W + win.X0 + lx;
-            simg[ly * RW + lx] = a.img[g];
-            if (WIENER) simg[(size_t)RH * RW + ly * RW + lx] = a.basic[g];
+            tc::cp_async4(tc::smem_u32(simg + ly * RW + lx), a.img + g);
+            if (WIENER) tc::cp_async4(tc::smem_u32(simg + (size_t)RH * RW + ly * RW + lx), a.basic + g);
         }
+        tc::cp_async_commit();
+        tc::cp_async_wait<0>();
         __syncthreads();
         if (WIENER) {
             for (int q = warp; q < cnt; q += nw) {

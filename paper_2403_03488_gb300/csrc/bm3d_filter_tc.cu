@@ -290,10 +290,11 @@ __device__ __forceinline__ void agg_n(const float (&v)[S], const WgMeta &mt, int
             fix_t2(f2_pack(t[k], N > 1 ? t[k + (N > 1)] : 0.0f), x0, x1);
             if constexpr (N > 1) {
                 const int2 wo = *reinterpret_cast<const int2 *>(&mt.woff[j0 + k]);
-                atomicAdd(wnum + wo.x + poffw, (unsigned long long)x0);
-                atomicAdd(wnum + wo.y + poffw, (unsigned long long)x1);
+                const unsigned o0 = split_lo(wnum + wo.x + poffw, x0), o1 = split_lo(wnum + wo.y + poffw, x1);
+                split_hi(wnum + wo.x + poffw, x0, o0);
+                split_hi(wnum + wo.y + poffw, x1, o1);
             } else {
-                atomicAdd(wnum + mt.woff[j0] + poffw, (unsigned long long)x0);
+                split_add(wnum + mt.woff[j0] + poffw, x0);
             }
         }
     } else {
@@ -303,7 +304,7 @@ __device__ __forceinline__ void agg_n(const float (&v)[S], const WgMeta &mt, int
             const int o = mt.woff[j0 + k];
             const size_t gp = poffg + (size_t)mt.gpos[j0 + k];
             if (o >= 0)
-                atomicAdd(wnum + o + poffw, f.lo);
+                split_add(wnum + o + poffw, (long long)f.lo);
             else
                 atomicAdd(a.num + gp, f.lo);
             if (f.hi != 0) atomicAdd(a.num_hi + gp, (unsigned long long)f.hi);
@@ -390,9 +391,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_filter_tc(TcArgs a)
             for (int i = tid; i < rh * rw; i += kThreads) {
                 const int ly = i / rw, lx = i - ly * rw;
                 const size_t g = cbase + (size_t)(Y0 + ly) * a.W + X0 + lx;
-                simg[ly * a.RW + lx] = a.img[g];
-                if (WIENER) simg[(size_t)a.RH * a.RW + ly * a.RW + lx] = a.basic[g];
+                tc::cp_async4(tc::smem_u32(simg + ly * a.RW + lx), a.img + g);
+                if (WIENER) tc::cp_async4(tc::smem_u32(simg + (size_t)a.RH * a.RW + ly * a.RW + lx), a.basic + g);
             }
+            tc::cp_async_commit();
+            tc::cp_async_wait<0>();
             __syncthreads();
             failed = failed || *sfail != 0;
             // group size and match index of this thread's column in tile gtt (both

@@ -646,7 +646,7 @@ __global__ void __launch_bounds__(kFW * 32) k_filter_k(const __grid_constant__ F
                     if (e < K * K) {
                         const Fix f = to_fixed(wn * kk[m] * T[t * KS + ei[m] * RSP + ej[m]]);
                         const size_t g = cbase + (size_t)(yt + ei[m]) * W + xt + ej[m];
-                        if (inside) atomicAdd(win + (ly + ei[m]) * a.RS + lx + ej[m], f.lo);
+                        if (inside) split_add(win + (ly + ei[m]) * a.RS + lx + ej[m], (long long)f.lo);
                         else atomicAdd(a.num + g, f.lo);
                         if (f.hi != 0) atomicAdd(a.num_hi + g, (unsigned long long)f.hi);
                     }

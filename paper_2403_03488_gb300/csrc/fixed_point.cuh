@@ -60,6 +60,32 @@ __device__ __forceinline__ void fix_fast2(f2 c, long long &x0, long long &x1)
     fix_t2(f2_mul(c, f2_pack(8192.0f, 8192.0f)), x0, x1);
 }
 
+// Adds a 64-bit fixed-point term to a sum in shared memory with two 32-bit
+// atomics (a 64-bit shared-memory atomic costs several times as much): the
+// low word's atomic returns its previous value, which gives the carry out of
+// bit 31 exactly, and the high word then gets (x >> 32) + carry (nothing when
+// that is 0).  Every carry is counted once, by the addition that produced it,
+// so once all additions are done the word holds the exact sum (mod 2^64)
+// whatever their order.  A word is updated this way only (never by a 64-bit
+// atomic at the same time).  split_lo / split_hi are the two halves, for
+// callers that issue a batch of low-word atomics before their high words.
+__device__ __forceinline__ unsigned split_lo(unsigned long long *p, long long x)
+{
+    return atomicAdd(reinterpret_cast<unsigned *>(p), (unsigned)x);
+}
+
+__device__ __forceinline__ void split_hi(unsigned long long *p, long long x, unsigned old)
+{
+    const unsigned l = (unsigned)x;
+    const int d = (int)(x >> 32) + (old + l < l ? 1 : 0);
+    if (d != 0) atomicAdd(reinterpret_cast<unsigned *>(p) + 1, (unsigned)d);
+}
+
+__device__ __forceinline__ void split_add(unsigned long long *p, long long x)
+{
+    split_hi(p, x, split_lo(p, x));
+}
+
 struct Fix {
     unsigned long long lo;  // main-plane part
     long long hi;           // high-word part (0 on the fast path)
