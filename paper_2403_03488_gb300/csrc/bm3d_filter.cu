@@ -29,8 +29,8 @@
 // coefficient positions across all patches and runs the Walsh-Hadamard
 // butterflies for both in packed registers; the inverse goes back the same
 // way, and the warp then aggregates in chunks of patches with its lanes spread
-// over the 64 pixels (each 64-bit fixed-point addition to the shared window
-// as two 32-bit atomics, see split_add).
+// over the 64 pixels (into the two 32-bit planes of the shared window, see
+// WinFmt).
 #include <cmath>
 
 #include "common.cuh"
@@ -60,6 +60,7 @@ struct FilterArgs {
     unsigned long long *num_hi, *wsum_hi;  // their high words (signed, units of 2^32)
     int C, H, W, R, Rx, Ry, n2, step, hs;
     float lambda;
+    WinFmt wf;  // format of the shared num window
     float sig[kChunk * 3];
     float kai[64];  // Kaiser outer product
     DctK k;
@@ -458,8 +459,9 @@ __device__ __forceinline__ float wiener_group(const FilterArgs &a, const Window 
 // one warp vote picks the branch-free fast path for the whole chunk, so the
 // chunk's conversions and atomics are independent and overlap.
 
-// Terms of patches [k0, k0+K) scaled by 2^13 (wk carries the exact factor),
-// then their exact fixed-point additions to the window; wo = the window
+// Terms of patches [k0, k0+K) scaled by 2^(F - 23) (wk carries the exact factor),
+// then their exact fixed-point additions to the window (or, for a chunk with
+// a term beyond the window's bound, to the global planes); wo = the window
 // offset of the lane's own patch, poff = the lane's pixel offset.
 template <int K>
 __device__ __forceinline__ void agg_chunk(const FilterArgs &a, const Window &win, const float *T, size_t cbase, int k0,
@@ -471,38 +473,25 @@ __device__ __forceinline__ void agg_chunk(const FilterArgs &a, const Window &win
     for (int q = 0; q < K; ++q) {
         const int k = k0 + q;
         t[q] = f2_mul(wk, f2_pack(T[k * kTS + lane], T[k * kTS + lane + 32]));
-        fast = fast && fabsf(f2_lo(t[q])) < 4194304.0f && fabsf(f2_hi(t[q])) < 4194304.0f;  // |term| < 512
+        fast = fast && fabsf(f2_lo(t[q])) < a.wf.tlim && fabsf(f2_hi(t[q])) < a.wf.tlim;
     }
     if (__all_sync(0xffffffffu, fast)) {
-        // the low words of up to 4 patches first, then their high words (the
-        // carries need the low words' previous values)
-        constexpr int H = K < 4 ? K : 4;
 #pragma unroll
-        for (int q0 = 0; q0 < K; q0 += H) {
-            long long x[2 * H];
-            unsigned old[2 * H];
-            int os[H];
-#pragma unroll
-            for (int q = 0; q < H; ++q) {
-                os[q] = __shfl_sync(0xffffffffu, wo, k0 + q0 + q) + poff;
-                fix_t2(t[q0 + q], x[2 * q], x[2 * q + 1]);
-                old[2 * q] = split_lo(win.num + os[q], x[2 * q]);
-                old[2 * q + 1] = split_lo(win.num + os[q] + 4 * win.RS, x[2 * q + 1]);
-            }
-#pragma unroll
-            for (int q = 0; q < H; ++q) {
-                split_hi(win.num + os[q], x[2 * q], old[2 * q]);
-                split_hi(win.num + os[q] + 4 * win.RS, x[2 * q + 1], old[2 * q + 1]);
-            }
+        for (int q = 0; q < K; ++q) {
+            const int o = __shfl_sync(0xffffffffu, wo, k0 + q) + poff;
+            int A[2], B[2];
+            fix_parts2(t[q], A, B);
+            win_add(win.num + o, A[0], B[0], a.wf.s);
+            win_add(win.num + o + 4 * win.RS, A[1], B[1], a.wf.s);
         }
     } else {
 #pragma unroll
         for (int q = 0; q < K; ++q) {
-            const int o = __shfl_sync(0xffffffffu, wo, k0 + q) + poff;
             const size_t g = cbase + (size_t)__shfl_sync(0xffffffffu, gpos, k0 + q) + pg;
-            const Fix f0 = to_fixed(f2_lo(t[q]) * (1.0f / 8192.0f)), f1 = to_fixed(f2_hi(t[q]) * (1.0f / 8192.0f));
-            split_add(win.num + o, (long long)f0.lo);
-            split_add(win.num + o + 4 * win.RS, (long long)f1.lo);
+            const float ri = 1.0f / a.wf.tscale;  // exact: a power of two
+            const Fix f0 = to_fixed(f2_lo(t[q]) * ri), f1 = to_fixed(f2_hi(t[q]) * ri);
+            atomicAdd(a.num + g, f0.lo);
+            atomicAdd(a.num + g + 4 * (size_t)a.W, f1.lo);
             if (f0.hi != 0) atomicAdd(a.num_hi + g, (unsigned long long)f0.hi);
             if (f1.hi != 0) atomicAdd(a.num_hi + g + 4 * (size_t)a.W, (unsigned long long)f1.hi);
         }
@@ -525,8 +514,8 @@ __device__ __forceinline__ void aggregate(const FilterArgs &a, const Window &win
     const bool in = ly >= 0 && ly + 8 <= win.RH && lx >= 0 && lx + 8 <= win.RW;
     const unsigned gm = n == 32 ? 0xffffffffu : ((1u << n) - 1u) << s;
     if ((__ballot_sync(0xffffffffu, in && mine) & gm) == gm) {
-        // w kai / n times the fixed-point scale 2^13 (exact powers of two)
-        const f2 wk = f2_pack(w * ka[0] * vs * 8192.0f, w * ka[1] * vs * 8192.0f);
+        // w kai / n times the window's scale (exact powers of two)
+        const f2 wk = f2_pack(w * ka[0] * vs * a.wf.tscale, w * ka[1] * vs * a.wf.tscale);
         const int wo = ly * win.RS + lx, poff = i0 * win.RS + j, gpos = py * a.W + px, pg = i0 * a.W + j;
         switch (n) {
             case 1: agg_chunk<1>(a, win, T, cbase, s, lane, wk, wo, poff, gpos, pg); break;
@@ -546,27 +535,18 @@ __device__ __forceinline__ void aggregate(const FilterArgs &a, const Window &win
         const bool inside = ly0 >= 0 && ly0 + 8 <= win.RH && lx0 >= 0 && lx0 + 8 <= win.RW;
         // the lane's two pixels (rows i0 and i0 + 4 of the patch, column j)
         const f2 c = f2_mul(wk, f2_pack(T[k * kTS + lane], T[k * kTS + lane + 32]));
-        Fix f[2];
-        if (fabsf(f2_lo(c)) < 512.0f && fabsf(f2_hi(c)) < 512.0f) {
-            long long x0, x1;
-            fix_fast2(c, x0, x1);
-            f[0].lo = (unsigned long long)x0;
-            f[1].lo = (unsigned long long)x1;
-            f[0].hi = f[1].hi = 0;
-        } else {
-            f[0] = to_fixed(f2_lo(c));
-            f[1] = to_fixed(f2_hi(c));
-        }
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int i = i0 + 4 * h;
-            if (inside) {
-                split_add(win.num + (ly0 + i) * win.RS + lx0 + j, (long long)f[h].lo);
+            const float ch = h ? f2_hi(c) : f2_lo(c);
+            if (inside && fabsf(ch) * a.wf.tscale < a.wf.tlim) {
+                win_add1(win.num + (ly0 + i) * win.RS + lx0 + j, ch * a.wf.tscale, a.wf.s);
             } else {
-                atomicAdd(a.num + cbase + (size_t)(yk + i) * a.W + xk + j, f[h].lo);
+                const Fix f = to_fixed(ch);
+                atomicAdd(a.num + cbase + (size_t)(yk + i) * a.W + xk + j, f.lo);
+                if (f.hi != 0)
+                    atomicAdd(a.num_hi + cbase + (size_t)(yk + i) * a.W + xk + j, (unsigned long long)f.hi);
             }
-            if (f[h].hi != 0)
-                atomicAdd(a.num_hi + cbase + (size_t)(yk + i) * a.W + xk + j, (unsigned long long)f[h].hi);
         }
     }
 }
@@ -690,8 +670,8 @@ __global__ void __launch_bounds__(512) k_filter(FilterArgs a, int TR, int RH, in
         __syncthreads();
         for (int i = threadIdx.x; i < rh * rw; i += blockDim.x) {
             const int ly = i / rw, lx = i - ly * rw;
-            const unsigned long long v = win.num[ly * RS + lx];
-            if (v != 0ull) atomicAdd(a.num + cbase + (size_t)(win.Y0 + ly) * a.W + win.X0 + lx, v);
+            const long long v = win_value(win.num[ly * RS + lx], a.wf);
+            if (v != 0) atomicAdd(a.num + cbase + (size_t)(win.Y0 + ly) * a.W + win.X0 + lx, (unsigned long long)v);
         }
         __syncthreads();  // the windows are refilled for the next channel
     }
@@ -806,6 +786,7 @@ dn_status filter_common(bool wiener, const float *img, const float *basic, const
         if (smem <= 225 * 1024) break;
     }
     if (TR < 1) return DN_EUNSUPPORTED;
+    a.wf = win_format((long long)TR * TR * p.n2);  // a pixel gets at most one term per patch of each group
     const void *fn = wiener ? (const void *)k_filter<true> : (const void *)k_filter<false>;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return DN_ECUDA;

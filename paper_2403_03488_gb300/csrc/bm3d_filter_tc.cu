@@ -88,6 +88,7 @@ struct TcArgs {
     int C, H, W, R, Rx, Ry, n2, step, hs, nb;
     int TR, RH, RW, RS, tiles_x, tiles_y;
     float lambda;
+    WinFmt wf;  // format of the shared num window
     float sig[kChunk * 3];
     float kai[64];
     float dct[64];  // C[u][m] = a_u cos(pi (2m+1) u / 16)
@@ -259,10 +260,10 @@ __device__ __forceinline__ void store_spectra(uint8_t *op, int lbo, int u, int c
 }
 
 // Aggregation of one group's N estimates of pixel p (this thread): term
-// t_k = (v_k + dc_k) w kai(p) / n scaled by 2^13, added to the num window as
-// exact fixed point.  The terms are formed first and one warp vote picks the
-// branch-free fast path (every term below 512 and every patch inside the
-// window, the common case) for the whole group.
+// t_k = (v_k + dc_k) w kai(p) / n scaled by 2^(F - 23), added to the num window as
+// exact fixed point (see WinFmt).  The terms are formed first and one warp
+// vote picks the branch-free fast path (every term within the window's bound
+// and every patch inside the window, the common case) for the whole group.
 template <int N, int S>
 __device__ __forceinline__ void agg_n(const float (&v)[S], const WgMeta &mt, int j0, float wk, bool inall,
                                       unsigned long long *wnum, int poffw, const TcArgs &a, size_t poffg)
@@ -282,32 +283,33 @@ __device__ __forceinline__ void agg_n(const float (&v)[S], const WgMeta &mt, int
     }
     bool fast = inall;
 #pragma unroll
-    for (int k = 0; k < N; ++k) fast = fast && fabsf(t[k]) < 4194304.0f;  // |term| < 512
+    for (int k = 0; k < N; ++k) fast = fast && fabsf(t[k]) < a.wf.tlim;
     if (__all_sync(0xffffffffu, fast)) {
 #pragma unroll
         for (int k = 0; k < N; k += 2) {
-            long long x0, x1;
-            fix_t2(f2_pack(t[k], N > 1 ? t[k + (N > 1)] : 0.0f), x0, x1);
+            int A[2], B[2];
+            fix_parts2(f2_pack(t[k], N > 1 ? t[k + (N > 1)] : 0.0f), A, B);
             if constexpr (N > 1) {
                 const int2 wo = *reinterpret_cast<const int2 *>(&mt.woff[j0 + k]);
-                const unsigned o0 = split_lo(wnum + wo.x + poffw, x0), o1 = split_lo(wnum + wo.y + poffw, x1);
-                split_hi(wnum + wo.x + poffw, x0, o0);
-                split_hi(wnum + wo.y + poffw, x1, o1);
+                win_add(wnum + wo.x + poffw, A[0], B[0], a.wf.s);
+                win_add(wnum + wo.y + poffw, A[1], B[1], a.wf.s);
             } else {
-                split_add(wnum + mt.woff[j0] + poffw, x0);
+                win_add(wnum + mt.woff[j0] + poffw, A[0], B[0], a.wf.s);
             }
         }
     } else {
 #pragma unroll
         for (int k = 0; k < N; ++k) {
-            const Fix f = to_fixed(t[k] * (1.0f / 8192.0f));  // exact
+            const float c = t[k] * (1.0f / a.wf.tscale);  // exact: a power of two
             const int o = mt.woff[j0 + k];
             const size_t gp = poffg + (size_t)mt.gpos[j0 + k];
-            if (o >= 0)
-                split_add(wnum + o + poffw, (long long)f.lo);
-            else
+            if (o >= 0 && fabsf(t[k]) < a.wf.tlim) {
+                win_add1(wnum + o + poffw, t[k], a.wf.s);
+            } else {
+                const Fix f = to_fixed(c);
                 atomicAdd(a.num + gp, f.lo);
-            if (f.hi != 0) atomicAdd(a.num_hi + gp, (unsigned long long)f.hi);
+                if (f.hi != 0) atomicAdd(a.num_hi + gp, (unsigned long long)f.hi);
+            }
         }
     }
 }
@@ -578,7 +580,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_filter_tc(TcArgs a)
                         float v[S];
                         tmem_ld_slot<S>(tmem + tlane + (uint32_t)(g * S), v);
                         // w kai(p) / n with the fixed-point scale 2^13 folded in (powers of two: exact)
-                        const float wk = weight(g) * kp * (8192.0f / (float)n);
+                        const float wk = weight(g) * kp * (a.wf.tscale / (float)n);
                         const bool inall = mt.inall[g] != 0;
                         const int j0 = g * S;
                         switch (n) {
@@ -602,8 +604,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_filter_tc(TcArgs a)
             __syncthreads();
             for (int i = tid; i < rh * rw; i += kThreads) {
                 const int ly = i / rw, lx = i - ly * rw;
-                const unsigned long long v = wnum[ly * a.RS + lx];
-                if (v != 0ull) atomicAdd(a.num + cbase + (size_t)(Y0 + ly) * a.W + X0 + lx, v);
+                const long long v = win_value(wnum[ly * a.RS + lx], a.wf);
+                if (v != 0) atomicAdd(a.num + cbase + (size_t)(Y0 + ly) * a.W + X0 + lx, (unsigned long long)v);
             }
             __syncthreads();  // windows are refilled for the next channel / tile
             failed = failed || *sfail != 0;
@@ -671,6 +673,7 @@ dn_status filter_tc(bool wiener, const float *img, const float *basic, const int
     a.RS = a.RW + ((8 - a.RW % 16) + 16) % 16;
     a.tiles_x = (a.Rx + TR - 1) / TR;
     a.tiles_y = (a.Ry + TR - 1) / TR;
+    a.wf = win_format((long long)TR * TR * p.n2);  // a pixel gets at most one term per patch of each group
     const bool s16 = p.n2 <= 16;
     const void *fn = wiener ? (s16 ? (const void *)k_filter_tc<true, 16> : (const void *)k_filter_tc<true, 32>)
                             : (s16 ? (const void *)k_filter_tc<false, 16> : (const void *)k_filter_tc<false, 32>);

@@ -86,6 +86,81 @@ __device__ __forceinline__ void split_add(unsigned long long *p, long long x)
     split_hi(p, x, split_lo(p, x));
 }
 
+// ---- the shared-memory num window of a filtering CTA ----
+//
+// There a pixel's sum is kept in units of 2^-F (F <= 36) as two 32-bit
+// integer planes, the low and high words of its 64-bit slot: a term
+// x = round(c 2^F) is split as x = h 2^s + l with 0 <= l < 2^s, l goes to the
+// low plane and h to the high plane, each with a plain 32-bit atomic (no
+// returned value, no carry), and the pixel's sum is H 2^s + L once the window
+// is complete (win_value, which also rescales it to the global planes' 2^-36).
+// With at most 2^m terms per pixel and window, s = 32 - m keeps L below 2^32,
+// and terms with |x| < 2^(62 - 2m) keep |H| below 2^31 (|h| <= 2^(30 - m) + 1),
+// so neither plane can overflow and the sum is exact; F = min(36, 54 - 2m)
+// lets every term with |c| < 256 in (the rounding to 2^-F is then at most
+// 2^-35 for m <= 10 and 2^-33 for m = 11), and a larger term goes to the
+// global planes directly.  A term is formed as t = c 2^(F - 23) (an exact
+// power-of-two scale folded into its weight), x = round(t 2^23).  (A 64-bit
+// shared-memory atomic costs several times as much as a 32-bit one.)
+struct WinFmt {
+    int s;         // bits of the low plane: 32 - m, m >= 9
+    int sh;        // 36 - F
+    float tscale;  // 2^(F - 23)
+    float tlim;    // the window takes terms with |t| < tlim = 2^(39 - 2m)
+};
+
+// The format for windows whose pixels receive at most max_terms terms.
+inline WinFmt win_format(long long max_terms)
+{
+    int m = 9;
+    while ((1ll << m) < max_terms) ++m;
+    const int F = 54 - 2 * m < 36 ? 54 - 2 * m : 36;
+    WinFmt f;
+    f.s = 32 - m;
+    f.sh = 36 - F;
+    f.tscale = ldexpf(1.0f, F - 23);
+    f.tlim = ldexpf(1.0f, 39 - 2 * m);
+    return f;
+}
+
+// fix_t2's steps on both lanes of t (|t| < 2^22), stopped before the 64-bit
+// composition: A = round(t), B = round((t - A) 2^23), so that
+// round(t 2^23) = A 2^23 + B with |B| <= 2^22.
+__device__ __forceinline__ void fix_parts2(f2 t, int (&A)[2], int (&B)[2])
+{
+    const f2 M = f2_pack(12582912.0f, 12582912.0f);
+    const f2 ta = f2_add(t, M);
+    const f2 r = f2_sub(t, f2_sub(ta, M));
+    const f2 u = f2_fma(r, f2_pack(8388608.0f, 8388608.0f), M);
+    A[0] = __float_as_int(f2_lo(ta)) - 0x4B400000;
+    A[1] = __float_as_int(f2_hi(ta)) - 0x4B400000;
+    B[0] = __float_as_int(f2_lo(u)) - 0x4B400000;
+    B[1] = __float_as_int(f2_hi(u)) - 0x4B400000;
+}
+
+// Adds A 2^23 + B to a window slot: l = B mod 2^s, h = A 2^(23 - s) + floor(B / 2^s).
+__device__ __forceinline__ void win_add(unsigned long long *p, int A, int B, int s)
+{
+    unsigned *w = reinterpret_cast<unsigned *>(p);
+    atomicAdd(w, (unsigned)B & ((1u << s) - 1u));
+    atomicAdd(w + 1, ((unsigned)A << (23 - s)) + (unsigned)(B >> s));
+}
+
+// Adds one term t (|t| < tlim) to a window slot.
+__device__ __forceinline__ void win_add1(unsigned long long *p, float t, int s)
+{
+    int A[2], B[2];
+    fix_parts2(f2_pack(t, 0.0f), A, B);
+    win_add(p, A[0], B[0], s);
+}
+
+// The sum held by a window slot, in units of 2^-36.
+__device__ __forceinline__ long long win_value(unsigned long long v, const WinFmt &f)
+{
+    const long long x = (long long)(int)(unsigned)(v >> 32) * (1ll << f.s) + (long long)(unsigned)(v & 0xFFFFFFFFull);
+    return x * (1ll << f.sh);
+}
+
 struct Fix {
     unsigned long long lo;  // main-plane part
     long long hi;           // high-word part (0 on the fast path)
