@@ -298,11 +298,12 @@ __device__ __forceinline__ int hard_columns(float *T, int n, int lane, float thr
 }
 
 // Shared-memory state of one CTA for the current channel: the num window over
-// pixels [Y0, Y0+RH) x [X0, X0+RW) (row stride RS = 8 mod 16 words, so that two
-// rows of 8 consecutive 64-bit words fill all 32 banks) and the image windows
-// the patches are read from (row stride RW).
+// pixels [Y0, Y0+RH) x [X0, X0+RW) (two planes of 32-bit words, row stride
+// RS = 8 mod 32 words, so that four rows of 8 consecutive words fill all 32
+// banks) and the image windows the patches are read from (row stride RW).
 struct Window {
-    unsigned long long *num;  // [RH][RS] fixed point
+    unsigned *num;            // [2][RH][RS]: low and high planes (WinFmt)
+    int plane;                // RH * RS
     const float *img;         // [RH][RW]: the image to filter (noisy in pass 2)
     const float *basic;       // [RH][RW]: pass 2 only
     int X0, Y0, RH, RW, RS;
@@ -479,10 +480,10 @@ __device__ __forceinline__ void agg_chunk(const FilterArgs &a, const Window &win
 #pragma unroll
         for (int q = 0; q < K; ++q) {
             const int o = __shfl_sync(0xffffffffu, wo, k0 + q) + poff;
-            int A[2], B[2];
-            fix_parts2(t[q], A, B);
-            win_add(win.num + o, A[0], B[0], a.wf.s);
-            win_add(win.num + o + 4 * win.RS, A[1], B[1], a.wf.s);
+            int h[2], l[2];
+            win_parts2(t[q], a.wf.s, h, l);
+            win_red(win.num + o, win.plane, h[0], l[0]);
+            win_red(win.num + o + 4 * win.RS, win.plane, h[1], l[1]);
         }
     } else {
 #pragma unroll
@@ -540,7 +541,7 @@ __device__ __forceinline__ void aggregate(const FilterArgs &a, const Window &win
             const int i = i0 + 4 * h;
             const float ch = h ? f2_hi(c) : f2_lo(c);
             if (inside && fabsf(ch) * a.wf.tscale < a.wf.tlim) {
-                win_add1(win.num + (ly0 + i) * win.RS + lx0 + j, ch * a.wf.tscale, a.wf.s);
+                win_add1(win.num + (ly0 + i) * win.RS + lx0 + j, win.plane, ch * a.wf.tscale, a.wf.s);
             } else {
                 const Fix f = to_fixed(ch);
                 atomicAdd(a.num + cbase + (size_t)(yk + i) * a.W + xk + j, f.lo);
@@ -609,11 +610,12 @@ __global__ void __launch_bounds__(512) k_filter(FilterArgs a, int TR, int RH, in
     extern __shared__ __align__(16) unsigned char dsm_raw[];
     const int nw = blockDim.x >> 5;
     Window win;
-    win.num = reinterpret_cast<unsigned long long *>(dsm_raw);
+    win.num = reinterpret_cast<unsigned *>(dsm_raw);
+    win.plane = RH * RS;
     win.RH = RH;
     win.RW = RW;
     win.RS = RS;
-    float *simg = reinterpret_cast<float *>(win.num + (size_t)RH * RS);  // [1 or 2][RH][RW]
+    float *simg = reinterpret_cast<float *>(win.num + 2 * (size_t)RH * RS);  // [1 or 2][RH][RW]
     float *tbufs = simg + (size_t)(WIENER ? 2 : 1) * RH * RW;            // [nw][32][65]
     win.img = simg;
     win.basic = WIENER ? simg + (size_t)RH * RW : nullptr;
@@ -635,7 +637,7 @@ __global__ void __launch_bounds__(512) k_filter(FilterArgs a, int TR, int RH, in
     for (int c = 0; c < a.C; ++c) {
         const size_t cbase = ((size_t)b * a.C + c) * HW;
         const float sig = a.sig[b * 3 + c];
-        for (int i = threadIdx.x; i < RH * RS; i += blockDim.x) win.num[i] = 0ull;
+        for (int i = threadIdx.x; i < 2 * RH * RS; i += blockDim.x) win.num[i] = 0u;
         for (int i = threadIdx.x; i < rh * rw; i += blockDim.x) {
             const int ly = i / rw, lx = i - ly * rw;
             const size_t g = cbase + (size_t)(win.Y0 + ly) * a.W + win.X0 + lx;
@@ -670,7 +672,7 @@ __global__ void __launch_bounds__(512) k_filter(FilterArgs a, int TR, int RH, in
         __syncthreads();
         for (int i = threadIdx.x; i < rh * rw; i += blockDim.x) {
             const int ly = i / rw, lx = i - ly * rw;
-            const long long v = win_value(win.num[ly * RS + lx], a.wf);
+            const long long v = win_value(win.num[ly * RS + lx], win.num[win.plane + ly * RS + lx], a.wf);
             if (v != 0) atomicAdd(a.num + cbase + (size_t)(win.Y0 + ly) * a.W + win.X0 + lx, (unsigned long long)v);
         }
         __syncthreads();  // the windows are refilled for the next channel
@@ -780,7 +782,7 @@ dn_status filter_common(bool wiener, const float *img, const float *basic, const
     for (; TR >= 1; TR /= 2) {
         RH = (TR - 1) * p.step + 2 * a.hs + 8;
         RW = RH;
-        RS = RW + ((8 - RW % 16) + 16) % 16;  // row stride = 8 (mod 16) words
+        RS = RW + ((8 - RW % 32) + 32) % 32;  // row stride = 8 (mod 32) words
         smem = (size_t)nwarps * per_warp + (size_t)RH * RS * sizeof(unsigned long long) +
                (size_t)nimg * RH * RW * sizeof(float);
         if (smem <= 225 * 1024) break;

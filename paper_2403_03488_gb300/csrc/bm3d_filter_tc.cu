@@ -266,7 +266,7 @@ __device__ __forceinline__ void store_spectra(uint8_t *op, int lbo, int u, int c
 // and every patch inside the window, the common case) for the whole group.
 template <int N, int S>
 __device__ __forceinline__ void agg_n(const float (&v)[S], const WgMeta &mt, int j0, float wk, bool inall,
-                                      unsigned long long *wnum, int poffw, const TcArgs &a, size_t poffg)
+                                      unsigned *wnum, int poffw, const TcArgs &a, size_t poffg)
 {
     float t[N];
     if constexpr (N == 1) {
@@ -287,14 +287,14 @@ __device__ __forceinline__ void agg_n(const float (&v)[S], const WgMeta &mt, int
     if (__all_sync(0xffffffffu, fast)) {
 #pragma unroll
         for (int k = 0; k < N; k += 2) {
-            int A[2], B[2];
-            fix_parts2(f2_pack(t[k], N > 1 ? t[k + (N > 1)] : 0.0f), A, B);
+            int h[2], l[2];
+            win_parts2(f2_pack(t[k], N > 1 ? t[k + (N > 1)] : 0.0f), a.wf.s, h, l);
             if constexpr (N > 1) {
                 const int2 wo = *reinterpret_cast<const int2 *>(&mt.woff[j0 + k]);
-                win_add(wnum + wo.x + poffw, A[0], B[0], a.wf.s);
-                win_add(wnum + wo.y + poffw, A[1], B[1], a.wf.s);
+                win_red(wnum + wo.x + poffw, a.RH * a.RS, h[0], l[0]);
+                win_red(wnum + wo.y + poffw, a.RH * a.RS, h[1], l[1]);
             } else {
-                win_add(wnum + mt.woff[j0] + poffw, A[0], B[0], a.wf.s);
+                win_red(wnum + mt.woff[j0] + poffw, a.RH * a.RS, h[0], l[0]);
             }
         }
     } else {
@@ -304,7 +304,7 @@ __device__ __forceinline__ void agg_n(const float (&v)[S], const WgMeta &mt, int
             const int o = mt.woff[j0 + k];
             const size_t gp = poffg + (size_t)mt.gpos[j0 + k];
             if (o >= 0 && fabsf(t[k]) < a.wf.tlim) {
-                win_add1(wnum + o + poffw, t[k], a.wf.s);
+                win_add1(wnum + o + poffw, a.RH * a.RS, t[k], a.wf.s);
             } else {
                 const Fix f = to_fixed(c);
                 atomicAdd(a.num + gp, f.lo);
@@ -316,7 +316,7 @@ __device__ __forceinline__ void agg_n(const float (&v)[S], const WgMeta &mt, int
 
 // Shared-memory layout of one CTA (dynamic, 1024-byte aligned base):
 //   [A_fwd 16 KB][A_inv 16 KB][operand buffer per warpgroup][WgMeta per warpgroup]
-//   [mbarriers, TMEM address, failure flag (128 B)][num window RH x RS u64][image window(s) RH x RW f32]
+//   [mbarriers, TMEM address, failure flag (128 B)][num window 2 x RH x RS u32][image window(s) RH x RW f32]
 template <bool WIENER, int S>
 __global__ void __launch_bounds__(kThreads, 1) k_filter_tc(TcArgs a)
 {
@@ -334,8 +334,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_filter_tc(TcArgs a)
     uint64_t *mbar = reinterpret_cast<uint64_t *>(ctl) + 2 * wg;  // [forward, inverse]
     uint32_t *tslot = reinterpret_cast<uint32_t *>(ctl + 64);
     int *sfail = reinterpret_cast<int *>(ctl + 72);
-    unsigned long long *wnum = reinterpret_cast<unsigned long long *>(sm + kFixedBytes);
-    float *simg = reinterpret_cast<float *>(wnum + (size_t)a.RH * a.RS);  // [1 or 2][RH][RW]
+    unsigned *wnum = reinterpret_cast<unsigned *>(sm + kFixedBytes);             // [2][RH][RS] (WinFmt)
+    float *simg = reinterpret_cast<float *>(wnum + 2 * (size_t)a.RH * a.RS);  // [1 or 2][RH][RW]
     const float *wbasic = simg + (size_t)a.RH * a.RW;
 
     // A operands: D (forward, [coef][px]) and D^T (inverse, [px][coef]), each
@@ -389,7 +389,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_filter_tc(TcArgs a)
         for (int c = 0; c < a.C; ++c) {
             const size_t cbase = ((size_t)b * a.C + c) * HW;
             const float sig = a.sig[b * 3 + c];
-            for (int i = tid; i < a.RH * a.RS; i += kThreads) wnum[i] = 0ull;
+            for (int i = tid; i < 2 * a.RH * a.RS; i += kThreads) wnum[i] = 0u;
             for (int i = tid; i < rh * rw; i += kThreads) {
                 const int ly = i / rw, lx = i - ly * rw;
                 const size_t g = cbase + (size_t)(Y0 + ly) * a.W + X0 + lx;
@@ -604,7 +604,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_filter_tc(TcArgs a)
             __syncthreads();
             for (int i = tid; i < rh * rw; i += kThreads) {
                 const int ly = i / rw, lx = i - ly * rw;
-                const long long v = win_value(wnum[ly * a.RS + lx], a.wf);
+                const long long v = win_value(wnum[ly * a.RS + lx], wnum[a.RH * a.RS + ly * a.RS + lx], a.wf);
                 if (v != 0) atomicAdd(a.num + cbase + (size_t)(Y0 + ly) * a.W + X0 + lx, (unsigned long long)v);
             }
             __syncthreads();  // windows are refilled for the next channel / tile
@@ -633,7 +633,7 @@ size_t filter_tc_smem_bytes(bool wiener, int step, int search, int *tr)
     const int hs = search / 2;
     for (int TR = 8; TR >= 1; TR /= 2) {
         const int RH = (TR - 1) * step + 2 * hs + 8, RW = RH;
-        const int RS = RW + ((8 - RW % 16) + 16) % 16;  // row stride = 8 (mod 16) words
+        const int RS = RW + ((8 - RW % 32) + 32) % 32;  // row stride = 8 (mod 32) words
         const size_t smem = (size_t)kFixedBytes + (size_t)RH * RS * 8 + (size_t)(wiener ? 2 : 1) * RH * RW * 4;
         if (smem <= 227 * 1024) {
             if (tr) *tr = TR;
@@ -670,7 +670,7 @@ dn_status filter_tc(bool wiener, const float *img, const float *basic, const int
     a.TR = TR;
     a.RH = (TR - 1) * p.step + 2 * a.hs + 8;
     a.RW = a.RH;
-    a.RS = a.RW + ((8 - a.RW % 16) + 16) % 16;
+    a.RS = a.RW + ((8 - a.RW % 32) + 32) % 32;
     a.tiles_x = (a.Rx + TR - 1) / TR;
     a.tiles_y = (a.Ry + TR - 1) / TR;
     a.wf = win_format((long long)TR * TR * p.n2);  // a pixel gets at most one term per patch of each group

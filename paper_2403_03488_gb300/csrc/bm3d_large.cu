@@ -375,6 +375,7 @@ struct FilterKArgs {
     int C, H, W, R, Rx, Ry, n2, step, hs;
     int TR, RH, RW, RS;                    // reference tile side and window (rows, columns, num stride)
     float lambda;
+    WinFmt wf;                             // format of the shared num window
     float sig[kChunk * 3];
     LargeTables t;
 };
@@ -543,8 +544,8 @@ __global__ void __launch_bounds__(kFW * 32) k_filter_k(const __grid_constant__ F
     using F = FShape<K>;
     constexpr int KS = F::KS, RSP = F::RSP, NE = F::NE;
     extern __shared__ __align__(16) unsigned char fsm_raw[];
-    unsigned long long *win = reinterpret_cast<unsigned long long *>(fsm_raw);  // [RH][RS]
-    float *simg = reinterpret_cast<float *>(win + (size_t)a.RH * a.RS);          // [RH][RW]
+    unsigned *win = reinterpret_cast<unsigned *>(fsm_raw);              // [2][RH][RS] (WinFmt)
+    float *simg = reinterpret_cast<float *>(win + 2 * (size_t)a.RH * a.RS);  // [RH][RW]
     float *sbas = simg + (size_t)a.RH * a.RW;                                    // pass 2: [RH][RW]
     float *bufs = sbas + (WIENER ? (size_t)a.RH * a.RW : 0);                     // [kFW][1 or 2][n2][KS]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -571,7 +572,7 @@ __global__ void __launch_bounds__(kFW * 32) k_filter_k(const __grid_constant__ F
     for (int c = 0; c < a.C; ++c) {
         const size_t cbase = ((size_t)b * a.C + c) * HW;
         const float sig = a.sig[b * 3 + c];
-        for (int i = threadIdx.x; i < a.RH * a.RS; i += blockDim.x) win[i] = 0ull;
+        for (int i = threadIdx.x; i < 2 * a.RH * a.RS; i += blockDim.x) win[i] = 0u;
         for (int i = threadIdx.x; i < rh * rw; i += blockDim.x) {
             const int ly = i / rw, lx = i - ly * rw;
             const size_t g = cbase + (size_t)(Y0 + ly) * W + X0 + lx;
@@ -644,11 +645,15 @@ __global__ void __launch_bounds__(kFW * 32) k_filter_k(const __grid_constant__ F
                 for (int m = 0; m < NE; ++m) {
                     const int e = lane + 32 * m;
                     if (e < K * K) {
-                        const Fix f = to_fixed(wn * kk[m] * T[t * KS + ei[m] * RSP + ej[m]]);
-                        const size_t g = cbase + (size_t)(yt + ei[m]) * W + xt + ej[m];
-                        if (inside) split_add(win + (ly + ei[m]) * a.RS + lx + ej[m], (long long)f.lo);
-                        else atomicAdd(a.num + g, f.lo);
-                        if (f.hi != 0) atomicAdd(a.num_hi + g, (unsigned long long)f.hi);
+                        const float c = wn * kk[m] * T[t * KS + ei[m] * RSP + ej[m]];
+                        if (inside && fabsf(c) * a.wf.tscale < a.wf.tlim) {
+                            win_add1(win + (ly + ei[m]) * a.RS + lx + ej[m], a.RH * a.RS, c * a.wf.tscale, a.wf.s);
+                        } else {
+                            const Fix f = to_fixed(c);
+                            const size_t g = cbase + (size_t)(yt + ei[m]) * W + xt + ej[m];
+                            atomicAdd(a.num + g, f.lo);
+                            if (f.hi != 0) atomicAdd(a.num_hi + g, (unsigned long long)f.hi);
+                        }
                     }
                 }
             }
@@ -657,8 +662,8 @@ __global__ void __launch_bounds__(kFW * 32) k_filter_k(const __grid_constant__ F
         __syncthreads();
         for (int i = threadIdx.x; i < rh * rw; i += blockDim.x) {
             const int ly = i / rw, lx = i - ly * rw;
-            const unsigned long long v = win[ly * a.RS + lx];
-            if (v != 0ull) atomicAdd(a.num + cbase + (size_t)(Y0 + ly) * W + X0 + lx, v);
+            const long long v = win_value(win[ly * a.RS + lx], win[a.RH * a.RS + ly * a.RS + lx], a.wf);
+            if (v != 0) atomicAdd(a.num + cbase + (size_t)(Y0 + ly) * W + X0 + lx, (unsigned long long)v);
         }
         __syncthreads();  // the windows are refilled for the next channel
     }
@@ -747,6 +752,7 @@ dn_status filter_k_impl(bool wiener, const float *img, const float *basic, const
     if (TR < 1) return DN_EUNSUPPORTED;
     a.TR = TR;
     a.RW = a.RH;
+    a.wf = win_format((long long)TR * TR * p.n2);  // a pixel gets at most one term per patch of each group
     const void *fn = wiener ? (const void *)k_filter_k<K, true> : (const void *)k_filter_k<K, false>;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return DN_ECUDA;
