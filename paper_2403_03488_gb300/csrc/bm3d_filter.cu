@@ -11,7 +11,7 @@
 //   (1 when the sum is 0).
 // Aggregation: every estimate pixel adds weight * kaiser(i) kaiser(j) * value to
 // num and weight * kaiser(i) kaiser(j) to den; the output is num / den.  The
-// sums are exact (64-bit fixed point, see to_fixed), so the result does not
+// sums are exact (fixed point, see fixed_point.cuh), so the result does not
 // depend on the order in which groups are aggregated; den is formed from the
 // per-position weight sums (see the aggregation section).
 //
@@ -22,15 +22,15 @@
 // pass, two groups of at most 16 patches at once): lane k owns patch k,
 // holds it in registers and computes its 8x8 DCT with an even/odd fast DCT,
 // two 1D transforms per packed FP32x2 instruction (row pairs, then column
-// pairs; the noisy patches of the second pass, whose gains then hold 64
-// registers, take a scalar version through the buffer below), and writes the
-// spectrum to its row of a per-warp transpose buffer (rows of 65 floats,
-// conflict-free both ways); for the group transform each lane owns two
-// coefficient positions across all patches and runs the Walsh-Hadamard
-// butterflies for both in packed registers; the inverse goes back the same
-// way, and the warp then aggregates in chunks of patches with its lanes spread
-// over the 64 pixels (into the two 32-bit planes of the shared window, see
-// WinFmt).
+// pairs), and writes the spectrum to its row of a per-warp transpose buffer
+// (rows of 65 floats, conflict-free both ways); for the group transform each
+// lane owns two coefficient positions across all patches and runs the
+// Walsh-Hadamard butterflies for both in packed registers (in the second
+// pass the Wiener gains of the basic group wait in the warp's TMEM columns,
+// 64 per lane, while the noisy group is transformed); the inverse goes back
+// the same way, and the warp then aggregates in chunks of patches with its
+// lanes spread over the 64 pixels (into the two 32-bit planes of the shared
+// window, see WinFmt).
 #include <cmath>
 
 #include "common.cuh"
@@ -45,12 +45,6 @@ namespace {
 constexpr int kTS = 65;    // transpose buffer row stride (floats)
 constexpr int kNMax = 32;
 
-// h_k = cos(k pi / 16) / 2 for k = 1..7 (h_4 = 1/sqrt(8)) and r8 = 1/sqrt(8):
-// the constants of the orthonormal 8-point DCT with the 1/2 scale folded in.
-struct DctK {
-    float h1, h2, h3, h5, h6, h7, r8;
-};
-
 struct FilterArgs {
     const float *img;    // [b][C][H][W]: noisy (pass 2) or the image to filter (pass 1)
     const float *basic;  // pass 2 only
@@ -63,40 +57,19 @@ struct FilterArgs {
     WinFmt wf;  // format of the shared num window
     float sig[kChunk * 3];
     float kai[64];  // Kaiser outer product
-    DctK k;
 };
 
-// ---- 8-point orthonormal DCT-II and its inverse (even/odd decomposition) ----
-
-// x[o], x[o+s], ..., x[o+7s] -> X[u] = a_u sum_m x[m] cos(pi (2m+1) u / 16)
-template <int O, int S, int NV>
-__device__ __forceinline__ void dct8(float (&v)[NV], const DctK &K)
-{
-    const float s0 = v[O] + v[O + 7 * S], d0 = v[O] - v[O + 7 * S];
-    const float s1 = v[O + S] + v[O + 6 * S], d1 = v[O + S] - v[O + 6 * S];
-    const float s2 = v[O + 2 * S] + v[O + 5 * S], d2 = v[O + 2 * S] - v[O + 5 * S];
-    const float s3 = v[O + 3 * S] + v[O + 4 * S], d3 = v[O + 3 * S] - v[O + 4 * S];
-    const float e0 = s0 + s3, e1 = s1 + s2, f0 = s0 - s3, f1 = s1 - s2;
-    v[O] = K.r8 * (e0 + e1);
-    v[O + 4 * S] = K.r8 * (e0 - e1);
-    v[O + 2 * S] = fmaf(K.h2, f0, K.h6 * f1);
-    v[O + 6 * S] = fmaf(K.h6, f0, -(K.h2 * f1));
-    v[O + 1 * S] = fmaf(K.h1, d0, fmaf(K.h3, d1, fmaf(K.h5, d2, K.h7 * d3)));
-    v[O + 3 * S] = fmaf(K.h3, d0, fmaf(-K.h7, d1, fmaf(-K.h1, d2, -(K.h5 * d3))));
-    v[O + 5 * S] = fmaf(K.h5, d0, fmaf(-K.h1, d1, fmaf(K.h7, d2, K.h3 * d3)));
-    v[O + 7 * S] = fmaf(K.h7, d0, fmaf(-K.h5, d1, fmaf(K.h3, d2, -(K.h1 * d3))));
-}
-
-
-// ---- packed versions: two independent 8-point transforms per instruction ----
+// ---- 8-point orthonormal DCT-II and its inverse (even/odd decomposition), ----
+// ---- two independent transforms per packed FP32x2 instruction            ----
 
 // The DCT constants broadcast to both lanes (and negated where subtracted).
 struct DctK2 {
     f2 h1, h2, h3, h5, h6, h7, r8, nh1, nh2, nh5, nh7;
 };
 
-// cos(k pi / 16) / 2 and 1/sqrt(8) rounded to FP32 (the values make_dct_constants
-// derives on the host); as compile-time literals the packed pairs can be
+// h_k = cos(k pi / 16) / 2 for k = 1..7 (h_4 = 1/sqrt(8)) and r8 = 1/sqrt(8),
+// rounded to FP32: the constants of the orthonormal 8-point DCT with the 1/2
+// scale folded in; as compile-time literals the packed pairs can be
 // rematerialised instead of occupying registers.
 constexpr float kH1 = 0.490392625f, kH2 = 0.461939752f, kH3 = 0.415734798f, kH5 = 0.277785122f,
                 kH6 = 0.191341713f, kH7 = 0.0975451618f, kR8 = 0.353553385f;
@@ -118,8 +91,8 @@ __device__ __forceinline__ DctK2 pack_dct()
     return P;
 }
 
-// The 8-point DCT (the same operations as dct8) and its inverse, on two vectors
-// at once:
+// The 8-point DCT and its inverse, on two vectors at once:
+//   forward X[u] = a_u sum_m x[m] cos(pi (2m+1) u / 16),
 //   inverse x[m] = sum_u a_u X[u] cos(pi (2m+1) u / 16).
 __device__ __forceinline__ void dct8_2(f2 (&v)[8], const DctK2 &K)
 {
@@ -158,21 +131,6 @@ __device__ __forceinline__ void idct8_2(f2 (&v)[8], const DctK2 &K)
 }
 
 // ---- group transform along the patches (one coefficient column) -------------
-
-template <int N>
-__device__ __forceinline__ void fwht(float (&v)[N])
-{
-#pragma unroll
-    for (int h = 1; h < N; h <<= 1)
-#pragma unroll
-        for (int i = 0; i < N; i += 2 * h)
-#pragma unroll
-            for (int j = i; j < i + h; ++j) {
-                float x = v[j], y = v[j + h];
-                v[j] = x + y;
-                v[j + h] = x - y;
-            }
-}
 
 template <int N>
 __device__ __forceinline__ float sqrt_n()
@@ -264,27 +222,6 @@ __device__ __forceinline__ float wiener_gains(const float *T, int lane, float s2
     return f2_lo(wsq) + f2_hi(wsq);
 }
 
-// Applies the gains to the lane's two coefficient columns of the noisy group
-// in T (in place), one column at a time (a packed pair of columns would keep
-// 128 registers live next to the gains).
-template <int N>
-__device__ __forceinline__ void wiener_apply(float *T, int lane, const f2 (&om)[N])
-{
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int col = lane + 32 * h;
-        float v[N];
-#pragma unroll
-        for (int k = 0; k < N; ++k) v[k] = T[k * kTS + col];
-        fwht<N>(v);
-#pragma unroll
-        for (int k = 0; k < N; ++k) v[k] *= h ? f2_hi(om[k]) : f2_lo(om[k]);
-        fwht<N>(v);
-#pragma unroll
-        for (int k = 0; k < N; ++k) T[k * kTS + col] = v[k];
-    }
-}
-
 __device__ __forceinline__ int hard_columns(float *T, int n, int lane, float thr)
 {
     switch (n) {
@@ -333,38 +270,6 @@ __device__ __forceinline__ int load_group(const FilterArgs &a, int b, int r, int
 __device__ __forceinline__ bool in_window(const Window &win, int py, int px)
 {
     return py >= win.Y0 && py + 8 <= win.Y0 + win.RH && px >= win.X0 && px + 8 <= win.X0 + win.RW;
-}
-
-// Scalar variant of dct_reg with the smallest register footprint (the row
-// pass goes through row `lane` of T), for the noisy patches of the Wiener
-// pass (the gains occupy 64 registers then).
-__device__ __forceinline__ void dct_2pass_scalar(float *T, const Window &win, const float *wimg, const float *gimg,
-                                                 int W, bool valid, int lane, int py, int px, const DctK &K)
-{
-    const bool all_in = __all_sync(0xffffffffu, !valid || in_window(win, py, px));
-    if (valid) {
-        const float *src = all_in ? wimg + (py - win.Y0) * win.RW + (px - win.X0) : gimg + (size_t)py * W + px;
-        const int stride = all_in ? win.RW : W;
-        float *row = T + lane * kTS;
-#pragma unroll 2
-        for (int r = 0; r < 8; ++r) {
-            float x[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) x[j] = src[r * stride + j];
-            dct8<0, 1>(x, K);
-#pragma unroll
-            for (int j = 0; j < 8; ++j) row[r * 8 + j] = x[j];
-        }
-#pragma unroll 2
-        for (int j = 0; j < 8; ++j) {
-            float x[8];
-#pragma unroll
-            for (int r = 0; r < 8; ++r) x[r] = row[r * 8 + j];
-            dct8<0, 1>(x, K);
-#pragma unroll
-            for (int r = 0; r < 8; ++r) row[r * 8 + j] = x[r];
-        }
-    }
 }
 
 // Forward 2D DCT of the valid lanes' patches kept in registers: row pairs
@@ -432,21 +337,81 @@ __device__ __forceinline__ void idct_reg(float *T, bool valid, int lane, const D
     }
 }
 
+// The lane's gains om[0, N) to its TMEM lane, columns tm .. tm + 2N.
+template <int N>
+__device__ __forceinline__ void gains_to_tmem(uint32_t tm, const f2 (&om)[N])
+{
+    if constexpr (N >= 4) {
+#pragma unroll
+        for (int k = 0; k < N; k += 4) {
+            const uint32_t r[8] = {(uint32_t)om[k].v, (uint32_t)(om[k].v >> 32), (uint32_t)om[k + 1].v,
+                                   (uint32_t)(om[k + 1].v >> 32), (uint32_t)om[k + 2].v, (uint32_t)(om[k + 2].v >> 32),
+                                   (uint32_t)om[k + 3].v, (uint32_t)(om[k + 3].v >> 32)};
+            tc::tmem_st8(tm + 2 * k, r);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < N; ++k) tc::tmem_st2(tm + 2 * k, (uint32_t)om[k].v, (uint32_t)(om[k].v >> 32));
+    }
+    tc::tmem_wait_st();
+}
+
+// Applies the gains kept in TMEM to the lane's two coefficient columns of the
+// noisy group in T (in place), both columns per packed instruction.
+template <int N>
+__device__ __forceinline__ void wiener_apply_tm(float *T, int lane, uint32_t tm)
+{
+    f2 v[N];
+    load_cols<N>(T, lane, v);
+    fwht2<N>(v);
+    if constexpr (N >= 8) {
+#pragma unroll
+        for (int k = 0; k < N; k += 8) {
+            uint32_t r[16];
+            tc::tmem_ld16(tm + 2 * k, r);
+            tc::tmem_wait_ld();
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                f2 g;
+                g.v = (unsigned long long)r[2 * q] | ((unsigned long long)r[2 * q + 1] << 32);
+                v[k + q] = f2_mul(v[k + q], g);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            uint32_t r0, r1;
+            tc::tmem_ld2(tm + 2 * k, r0, r1);
+            tc::tmem_wait_ld();
+            f2 g;
+            g.v = (unsigned long long)r0 | ((unsigned long long)r1 << 32);
+            v[k] = f2_mul(v[k], g);
+        }
+    }
+    fwht2<N>(v);
+    store_cols<N>(T, lane, v);
+}
+
 // Wiener transform of one group of N patches (rows [0, N) of T): gains from
-// the basic-estimate group (kept in registers), applied to the noisy group;
-// T is left holding the filtered spectra of the noisy patches.
+// the basic-estimate group, parked in the warp's TMEM columns while the noisy
+// patches are transformed, then applied to the noisy group; T is left holding
+// the filtered spectra of the noisy patches.
 template <int N>
 __device__ __forceinline__ float wiener_group(const FilterArgs &a, const Window &win, float *T, size_t cbase,
-                                              int lane, int py, int px, float s2, const DctK2 &K)
+                                              int lane, int py, int px, float s2, const DctK2 &K, uint32_t tm)
 {
     dct_reg(T, win, win.basic, a.basic + cbase, a.W, lane < N, lane, py, px, K);
     __syncwarp();
-    f2 om[N];
-    const float wsq = wiener_gains<N>(T, lane, s2, om);
+    float wsq;
+    {
+        f2 om[N];
+        wsq = wiener_gains<N>(T, lane, s2, om);
+        gains_to_tmem<N>(tm, om);
+    }
     __syncwarp();
-    dct_2pass_scalar(T, win, win.img, a.img + cbase, a.W, lane < N, lane, py, px, a.k);
+    dct_reg(T, win, win.img, a.img + cbase, a.W, lane < N, lane, py, px, K);
     __syncwarp();
-    wiener_apply<N>(T, lane, om);
+    wiener_apply_tm<N>(T, lane, tm);
     return wsq;
 }
 
@@ -576,17 +541,17 @@ __device__ __forceinline__ void hard_batch(const FilterArgs &a, const Window &wi
 
 // Second pass on one group of n patches (rows [0, n)).
 __device__ __forceinline__ void wiener_one(const FilterArgs &a, const Window &win, float *T, size_t cbase, float sig,
-                                           int n, int lane, int py, int px, const float (&ka)[2])
+                                           int n, int lane, int py, int px, const float (&ka)[2], uint32_t tm)
 {
     const float s2 = sig * sig;
     float wsq;
     switch (n) {
-        case 1: wsq = wiener_group<1>(a, win, T, cbase, lane, py, px, s2, pack_dct()); break;
-        case 2: wsq = wiener_group<2>(a, win, T, cbase, lane, py, px, s2, pack_dct()); break;
-        case 4: wsq = wiener_group<4>(a, win, T, cbase, lane, py, px, s2, pack_dct()); break;
-        case 8: wsq = wiener_group<8>(a, win, T, cbase, lane, py, px, s2, pack_dct()); break;
-        case 16: wsq = wiener_group<16>(a, win, T, cbase, lane, py, px, s2, pack_dct()); break;
-        default: wsq = wiener_group<32>(a, win, T, cbase, lane, py, px, s2, pack_dct()); break;
+        case 1: wsq = wiener_group<1>(a, win, T, cbase, lane, py, px, s2, pack_dct(), tm); break;
+        case 2: wsq = wiener_group<2>(a, win, T, cbase, lane, py, px, s2, pack_dct(), tm); break;
+        case 4: wsq = wiener_group<4>(a, win, T, cbase, lane, py, px, s2, pack_dct(), tm); break;
+        case 8: wsq = wiener_group<8>(a, win, T, cbase, lane, py, px, s2, pack_dct(), tm); break;
+        case 16: wsq = wiener_group<16>(a, win, T, cbase, lane, py, px, s2, pack_dct(), tm); break;
+        default: wsq = wiener_group<32>(a, win, T, cbase, lane, py, px, s2, pack_dct(), tm); break;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) wsq += __shfl_xor_sync(0xffffffffu, wsq, o);
@@ -627,6 +592,15 @@ __global__ void __launch_bounds__(512) k_filter(FilterArgs a, int TR, int RH, in
     win.X0 = max(0, gx0 - a.hs);
     win.Y0 = max(0, gy0 - a.hs);
     const float ka[2] = {a.kai[lane], a.kai[lane + 32]};
+    // Wiener pass: 64 TMEM columns per warp (its lane quarter) park the gains
+    __shared__ uint32_t s_tmem;
+    if (WIENER) {
+        if (warp == 0) tc::tmem_alloc(&s_tmem, 256);
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+    }
+    const uint32_t tm = WIENER ? s_tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(warp >> 2) * 64 : 0u;
 
     float *T = tbufs + (size_t)warp * 32 * kTS;
     const int tw = min(TR, Rx - rx0), th = min(TR, Ry - ry0), cnt = tw * th;
@@ -634,27 +608,40 @@ __global__ void __launch_bounds__(512) k_filter(FilterArgs a, int TR, int RH, in
     const int rh = min(RH, a.H - win.Y0), rw = min(RW, a.W - win.X0);
     auto ref_of = [&](int q) { return (ry0 + q / tw) * Rx + rx0 + q % tw; };
 
+    __shared__ int s_next[2];
     for (int c = 0; c < a.C; ++c) {
         const size_t cbase = ((size_t)b * a.C + c) * HW;
         const float sig = a.sig[b * 3 + c];
-        for (int i = threadIdx.x; i < 2 * RH * RS; i += blockDim.x) win.num[i] = 0u;
-        for (int i = threadIdx.x; i < rh * rw; i += blockDim.x) {
-            const int ly = i / rw, lx = i - ly * rw;
-            const size_t g = cbase + (size_t)(win.Y0 + ly) * a.W + win.X0 + lx;
-            tc::cp_async4(tc::smem_u32(simg + ly * RW + lx), a.img + g);
-            if (WIENER) tc::cp_async4(tc::smem_u32(simg + (size_t)RH * RW + ly * RW + lx), a.basic + g);
+        if (threadIdx.x == 0) s_next[c & 1] = 0;
+        for (int i = threadIdx.x; i < (2 * RH * RS) / 4; i += blockDim.x)
+            reinterpret_cast<uint4 *>(win.num)[i] = make_uint4(0u, 0u, 0u, 0u);
+        for (int ly = warp; ly < rh; ly += nw) {
+            const float *gi = a.img + cbase + (size_t)(win.Y0 + ly) * a.W + win.X0;
+            const float *gb = WIENER ? a.basic + cbase + (size_t)(win.Y0 + ly) * a.W + win.X0 : nullptr;
+            for (int lx = lane; lx < rw; lx += 32) {
+                tc::cp_async4(tc::smem_u32(simg + ly * RW + lx), gi + lx);
+                if (WIENER) tc::cp_async4(tc::smem_u32(simg + (size_t)RH * RW + ly * RW + lx), gb + lx);
+            }
         }
         tc::cp_async_commit();
         tc::cp_async_wait<0>();
         __syncthreads();
         if (WIENER) {
-            for (int q = warp; q < cnt; q += nw) {
+            for (;;) {
+                int q = 0;
+                if (lane == 0) q = atomicAdd(&s_next[c & 1], 1);
+                q = __shfl_sync(0xffffffffu, q, 0);
+                if (q >= cnt) break;
                 int py = 0, px = 0;
                 const int n = load_group(a, b, ref_of(q), lane, 0, py, px);
-                if (n > 0) wiener_one(a, win, T, cbase, sig, n, lane, py, px, ka);
+                if (n > 0) wiener_one(a, win, T, cbase, sig, n, lane, py, px, ka, tm);
             }
         } else {
-            for (int q = 2 * warp; q < cnt; q += 2 * nw) {
+            for (;;) {
+                int q = 0;
+                if (lane == 0) q = 2 * atomicAdd(&s_next[c & 1], 1);
+                q = __shfl_sync(0xffffffffu, q, 0);
+                if (q >= cnt) break;
                 int py = 0, px = 0;
                 const int nA = load_group(a, b, ref_of(q), lane, 0, py, px);
                 int nB = 0;
@@ -670,12 +657,22 @@ __global__ void __launch_bounds__(512) k_filter(FilterArgs a, int TR, int RH, in
             }
         }
         __syncthreads();
-        for (int i = threadIdx.x; i < rh * rw; i += blockDim.x) {
-            const int ly = i / rw, lx = i - ly * rw;
-            const long long v = win_value(win.num[ly * RS + lx], win.num[win.plane + ly * RS + lx], a.wf);
-            if (v != 0) atomicAdd(a.num + cbase + (size_t)(win.Y0 + ly) * a.W + win.X0 + lx, (unsigned long long)v);
+        for (int ly = warp; ly < rh; ly += nw) {
+            unsigned long long *gn = a.num + cbase + (size_t)(win.Y0 + ly) * a.W + win.X0;
+            for (int lx = lane; lx < rw; lx += 32) {
+                const long long v = win_value(win.num[ly * RS + lx], win.num[win.plane + ly * RS + lx], a.wf);
+                if (v != 0) atomicAdd(gn + lx, (unsigned long long)v);
+            }
         }
         __syncthreads();  // the windows are refilled for the next channel
+    }
+    if (WIENER) {
+        tc::fence_before_sync();
+        __syncthreads();
+        if (warp == 0) {
+            tc::fence_after_sync();
+            tc::tmem_dealloc(s_tmem, 256);
+        }
     }
 }
 
@@ -740,19 +737,6 @@ __global__ void __launch_bounds__(256) k_normalize(const long long *num, const l
     }
 }
 
-DctK make_dct_constants()
-{
-    DctK k;
-    k.h1 = kH1;
-    k.h2 = kH2;
-    k.h3 = kH3;
-    k.h5 = kH5;
-    k.h6 = kH6;
-    k.h7 = kH7;
-    k.r8 = kR8;
-    return k;
-}
-
 dn_status filter_common(bool wiener, const float *img, const float *basic, const int *idx, const int *n, int B,
                         int C, int H, int W, const float *sig, const dn_bm3d_pass &p, float *acc, cudaStream_t s)
 {
@@ -770,7 +754,6 @@ dn_status filter_common(bool wiener, const float *img, const float *basic, const
     Tables t;
     make_tables(p.beta, &t);
     for (int i = 0; i < 64; ++i) a.kai[i] = t.kai[i];
-    a.k = make_dct_constants();
     const size_t HW = (size_t)H * W, N = (size_t)B * C * HW;
     // tile of references per CTA and its aggregation window
     const int nwarps = 16;
