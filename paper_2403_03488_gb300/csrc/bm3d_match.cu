@@ -22,15 +22,18 @@
 // instruction.  The row sums go through a double-buffered shared array (the
 // two offsets of a pair interleaved); then each thread, owning one reference,
 // combines its 8 row sums (3 + 3 + 2 rows), again two offsets per packed
-// instruction, and updates its sorted list in registers.  Packed lanes round
-// exactly like the scalar operations, so the distances are those of the
-// fixed association.
+// instruction, and updates its sorted list in registers (the 31-entry list
+// of n2 = 32 waits in the warp's TMEM lanes while the row sums are formed,
+// which keeps the kernel within 128 registers without spilling).  Packed
+// lanes round exactly like the scalar operations, so the distances are those
+// of the fixed association.
 //
 // Other steps: k_match_fp32, one thread per reference over a 16 x 8 tile,
 // register-blocked over 8 horizontally adjacent candidates (15 shared loads
 // per patch row feed 8 candidates), same association.
 #include "common.cuh"
 #include "match_exact.cuh"
+#include "tc.cuh"
 
 namespace dn {
 
@@ -70,12 +73,32 @@ __global__ void __launch_bounds__(kS3T, 4) k_match3(Match3Args a)
     const int H = a.H, W = a.W, hs = a.hs, P = a.pitch;
     const int c0 = blockIdx.x * kSX, r0 = blockIdx.y * kSY;
     const int RX0 = 3 * c0 - hs, RY0 = 3 * r0 - hs;
+    // the 31-entry list waits in TMEM (64 columns per CTA, the warp's lane
+    // quarter) while the row sums are formed, which keeps it out of the
+    // registers the row-sum role needs
+    constexpr bool kPark = L >= 16;
+    __shared__ uint32_t s_tm;
+    if (kPark && threadIdx.x < 32) tc::tmem_alloc(&s_tm, 64);
     for (int i = threadIdx.x; i < a.rows * P; i += kS3T) {
         const int yy = i / P, xx = i - yy * P;
         const int gy = RY0 + yy, gx = RX0 + xx;
         img[i] = (gy >= 0 && gy < H && gx >= 0 && gx < W) ? g[(size_t)gy * W + gx] : 0.0f;
     }
+    if (kPark) tc::fence_before_sync();
     __syncthreads();
+    if (kPark) tc::fence_after_sync();
+    const uint32_t tm = kPark ? s_tm + ((uint32_t)((threadIdx.x >> 5) * 32) << 16) : 0u;
+    auto park = [&](const float (&d)[L], const int (&id)[L]) {
+        uint32_t r[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) r[j] = j < L ? __float_as_uint(d[j < L ? j : 0]) : 0u;
+        tc::tmem_st32(tm, r);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) r[j] = j < L ? (uint32_t)id[j < L ? j : 0] : 0u;
+        tc::tmem_st32(tm + 32, r);
+        tc::tmem_wait_st();
+    };
+    uint32_t ud[32], ui[32];
 
     const int t = threadIdx.x;
     // row-sum role: tile row ay, reference columns 4 ag .. 4 ag + 3 (pixels 12 ag .. 12 ag + 16)
@@ -95,6 +118,18 @@ __global__ void __launch_bounds__(kS3T, 4) k_match3(Match3Args a)
         bi[j] = -1;
     }
     const float tau = a.tau[b];
+    if constexpr (kPark) park(bd, bi);
+    // the segment's reference pixels in both lanes, loaded once when the list
+    // stays in registers (with the parked 31-entry list, reloading them per
+    // chunk measured faster: 14.62 against 14.89 ms per 16 x 1024^2 launch)
+    f2 RR0[kPark ? 1 : 17];
+    if constexpr (!kPark) {
+#pragma unroll
+        for (int x = 0; x < 17; ++x) {
+            const float r = task ? rrow[x] : 0.0f;
+            RR0[x] = f2_pack(r, r);
+        }
+    }
     int kept = 0;
     int it = 0;
     for (int oy = -hs; oy <= hs; ++oy) {
@@ -109,8 +144,12 @@ __global__ void __launch_bounds__(kS3T, 4) k_match3(Match3Args a)
                 f2 RR[17];
 #pragma unroll
                 for (int x = 0; x < 17; ++x) {
-                    const float r = rrow[x];
-                    RR[x] = f2_pack(r, r);
+                    if constexpr (kPark) {
+                        const float r = rrow[x];
+                        RR[x] = f2_pack(r, r);
+                    } else {
+                        RR[x] = RR0[x < (kPark ? 1 : 17) ? x : 0];
+                    }
                 }
                 // offsets (2 kp, 2 kp + 1) in the two lanes of every packed value
 #pragma unroll
@@ -139,7 +178,20 @@ __global__ void __launch_bounds__(kS3T, 4) k_match3(Match3Args a)
                     dst[1] = make_ulonglong2(h2.v, h3.v);
                 }
             }
+            if constexpr (kPark) {
+                __syncwarp();
+                tc::tmem_ld32(tm, ud);
+                tc::tmem_ld32(tm + 32, ui);
+            }
             __syncthreads();  // one barrier per chunk: the buffers alternate
+            if constexpr (kPark) {
+                tc::tmem_wait_ld();
+#pragma unroll
+                for (int j = 0; j < L; ++j) {
+                    bd[j] = __uint_as_float(ud[j < 32 ? j : 0]);
+                    bi[j] = (int)ui[j < 32 ? j : 0];
+                }
+            }
             // offsets ox0 + k inside the window (|ox| <= hs), the image and not the reference itself
             const int klo = max(0, -xr - ox0), khi = min(kSK - 1, min(hs, W - 8 - xr) - ox0);
             unsigned valid = (yok && khi >= klo) ? ((2u << (khi - klo)) - 1u) << klo : 0u;
@@ -184,6 +236,26 @@ __global__ void __launch_bounds__(kS3T, 4) k_match3(Match3Args a)
                     }
                 }
             }
+            if constexpr (kPark) {
+                __syncwarp();
+                park(bd, bi);
+            }
+        }
+    }
+    if constexpr (kPark) {
+        tc::tmem_ld32(tm, ud);
+        tc::tmem_ld32(tm + 32, ui);
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < L; ++j) {
+            bd[j] = __uint_as_float(ud[j < 32 ? j : 0]);
+            bi[j] = (int)ui[j < 32 ? j : 0];
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            tc::fence_after_sync();
+            tc::tmem_dealloc(s_tm, 64);
         }
     }
     if (!own) return;
