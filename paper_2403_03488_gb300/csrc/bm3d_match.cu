@@ -62,6 +62,15 @@ struct Match3Args {
     int n2, Rx, Ry;
 };
 
+// match_ref_warp out of line (only the rare references with a tie take it,
+// and inlined its 64-pixel reference would crowd the registers of k_match3).
+template <int L>
+__device__ __noinline__ void match_ref_warp_call(const float *g, int H, int W, int hs, float tau, int n2, int rx,
+                                                 int ry, int *out, int *nout)
+{
+    match_ref_warp<L>(g, H, W, 3, hs, tau, n2, rx, ry, out, nout);
+}
+
 template <int L>
 __global__ void __launch_bounds__(kS3T, 4) k_match3(Match3Args a)
 {
@@ -132,7 +141,22 @@ __global__ void __launch_bounds__(kS3T, 4) k_match3(Match3Args a)
     }
     int kept = 0;
     int it = 0;
-    for (int oy = -hs; oy <= hs; ++oy) {
+    // For the 31-entry list, candidate rows from the centre out (oy = 0, -1,
+    // 1, -2, 2, ...): near rows hold the closest matches, so the list settles
+    // early and later candidates rarely enter it (its insertions, divergent
+    // across the warp, were 44 % of the launch; 14.65 -> 12.82 ms per
+    // 16 x 1024^2 launch).  Out of index order, a candidate whose distance
+    // equals an entry's could be ranked wrongly, so every equality that could
+    // matter raises `tie` (a candidate equal to the full list's last entry, an
+    // eviction while the last two entries are equal, equal entries in the
+    // final list; about 1 reference in 2000 on noisy images) and that
+    // reference is matched again in index order by its warp (match_ref_warp).
+    // The shorter lists keep the index order (the same change measured slower
+    // there: 8.86 -> 9.45 ms).
+    constexpr bool kCentre = L >= 16;
+    bool tie = false;
+    for (int so = 0; so <= 2 * hs; ++so) {
+        const int oy = !kCentre ? so - hs : (so & 1) ? -((so + 1) >> 1) : (so >> 1);
         const bool yok = own && (unsigned)(yr + oy) <= (unsigned)(H - 8);
         for (int ox0 = -hs; ox0 <= hs; ox0 += kSK, ++it) {
             float *hbuf = hb + (it & 1) * kSBuf;
@@ -223,6 +247,7 @@ __global__ void __launch_bounds__(kS3T, 4) k_match3(Match3Args a)
                             if (((valid >> c) & 1u) && d <= tau) {
                                 ++kept;
                                 if (d < bd[L - 1]) ins |= 1u << (c - g0);
+                                else if (kCentre) tie = tie || d == bd[L - 1];
                             }
                         }
                     }
@@ -232,6 +257,11 @@ __global__ void __launch_bounds__(kS3T, 4) k_match3(Match3Args a)
                         float d = dk[0];
 #pragma unroll
                         for (int j = 1; j < kG; ++j) d = k == j ? dk[j] : d;
+                        // (an eviction only once the list is full: its last entry finite)
+                        if (kCentre)
+                            tie = tie || d == bd[L - 1] ||
+                                  (d < bd[L - 1] && bd[L - 1] < __int_as_float(0x7f800000) &&
+                                   bd[L > 1 ? L - 2 : 0] == bd[L - 1]);
                         insert_sorted<L>(bd, bi, d, (yr + oy) * W + xr + ox0 + g0 + k);
                     }
                 }
@@ -258,14 +288,26 @@ __global__ void __launch_bounds__(kS3T, 4) k_match3(Match3Args a)
             tc::tmem_dealloc(s_tm, 64);
         }
     }
-    if (!own) return;
-    const size_t r = ((size_t)b * a.Ry + ry) * a.Rx + rx;
-    int *out = a.idx + r * a.n2;
-    out[0] = yr * W + xr;
+    if (kCentre) {
 #pragma unroll
-    for (int j = 0; j < L; ++j)
-        if (1 + j < a.n2) out[1 + j] = bi[j];
-    a.n[r] = group_size(kept, a.n2);
+        for (int j = 1; j < L; ++j) tie = tie || (bd[j] == bd[j - 1] && bi[j] >= 0);
+    }
+    if (own && !tie) {
+        const size_t r = ((size_t)b * a.Ry + ry) * a.Rx + rx;
+        int *out = a.idx + r * a.n2;
+        out[0] = yr * W + xr;
+#pragma unroll
+        for (int j = 0; j < L; ++j)
+            if (1 + j < a.n2) out[1 + j] = bi[j];
+        a.n[r] = group_size(kept, a.n2);
+    }
+    // the references with a tie, one at a time by the whole warp, in index order
+    for (unsigned fl = kCentre ? __ballot_sync(0xffffffffu, own && tie) : 0u; fl; fl &= fl - 1) {
+        const int l = __ffs(fl) - 1;
+        const int frx = __shfl_sync(0xffffffffu, rx, l), fry = __shfl_sync(0xffffffffu, ry, l);
+        const size_t fr = ((size_t)b * a.Ry + fry) * a.Rx + frx;
+        match_ref_warp_call<L>(g, H, W, hs, tau, a.n2, frx, fry, a.idx + fr * a.n2, a.n + fr);
+    }
 }
 
 // The references off the 3-aligned grid (column Rx - 1 when Rxa < Rx, row

@@ -122,6 +122,39 @@ def test_match_repeated_tile_exact(oracle):
             np.testing.assert_array_equal(gi[ry, rx, :k], om["idx"][ry, rx, :k])
 
 
+@pytest.mark.parametrize("n2,tau", [(32, 400.0), (16, 2500.0), (32, 1e9)])
+def test_match_exact_ties_in_index_order(oracle, n2, tau):
+    """Pixels of 4 levels make every distance an exact multiple of 1/64 in
+    FP32 as in FP64, so equal distances abound at every rank: the lists must
+    equal the oracle's (ties by index) whatever order the kernel scans its
+    candidates in (the 31-entry list scans rows from the centre out and
+    re-matches a reference with a tie in index order)."""
+    A = api()
+    rng = np.random.default_rng(11)
+    g = rng.integers(0, 4, (53, 67)).astype(np.float32)
+    p = A.default_bm3d_params().wiener
+    p.n2 = n2
+    idx, n = A.bm3d_match(dev(g[None]), [tau], p)
+    om = oracle.match(g, oracle.Pass(n2=n2, tau=tau))
+    np.testing.assert_array_equal(host(n)[0], om["n"])
+    gi = host(idx)[0]
+    for ry in range(om["n"].shape[0]):
+        for rx in range(om["n"].shape[1]):
+            k = om["n"][ry, rx]
+            np.testing.assert_array_equal(gi[ry, rx, :k], om["idx"][ry, rx, :k], err_msg=str((ry, rx)))
+
+
+def test_match_constant_image_index_order(oracle):
+    """All distances 0: every list is the first candidates in index order."""
+    A = api()
+    g = np.full((40, 45), 77.0, np.float32)
+    p = A.default_bm3d_params().wiener
+    idx, n = A.bm3d_match(dev(g[None]), [400.0], p)
+    om = oracle.match(g, oracle.Pass(n2=32, tau=400.0))
+    np.testing.assert_array_equal(host(n)[0], om["n"])
+    np.testing.assert_array_equal(host(idx)[0], om["idx"])
+
+
 def _ycc_or_grey(oracle, noisy):
     return noisy.astype(np.float64) if noisy.shape[1] == 1 else np.stack([oracle.rgb_to_ycc(x) for x in noisy])
 
