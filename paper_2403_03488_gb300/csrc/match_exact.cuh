@@ -61,6 +61,25 @@ __device__ __forceinline__ float canon_d64(const float (&ref)[64], Q q)
     return tree8(h[0], h[1], h[2], h[3], h[4], h[5], h[6], h[7]);
 }
 
+// insert_sorted restricted to slots [S, L): valid when d >= bd[S - 1] (the
+// candidate lands at or after slot S, so the slots before it do not move).
+template <int L, int S>
+__device__ __forceinline__ void insert_sorted_tail(float (&bd)[L], int (&bi)[L], float d, int id)
+{
+    bool after = d < bd[L - 1];
+#pragma unroll
+    for (int j = L - 1; j > S; --j) {
+        const bool before_prev = d < bd[j - 1];
+        bd[j] = before_prev ? bd[j - 1] : (after ? d : bd[j]);
+        bi[j] = before_prev ? bi[j - 1] : (after ? id : bi[j]);
+        after = before_prev;
+    }
+    if (after) {
+        bd[S] = d;
+        bi[S] = id;
+    }
+}
+
 // Sorted insertion; candidates arrive in increasing index order, so a strict
 // comparison keeps equal distances in index order.
 template <int L>
