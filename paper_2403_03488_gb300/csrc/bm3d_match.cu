@@ -263,12 +263,15 @@ __global__ void __launch_bounds__(kS3T, 4) k_match3(Match3Args a)
                                   (d < bd[L - 1] && bd[L - 1] < __int_as_float(0x7f800000) &&
                                    bd[L > 1 ? L - 2 : 0] == bd[L - 1]);
                         if constexpr (L >= 16) {
-                            // only the second half of the list moves unless some lane's candidate lands in
-                            // the first (12.81 -> 12.47 ms; a per-lane choice between the two diverged: 13.56)
-                            if (__any_sync(__activemask(), d < bd[L / 2 - 1]))
+                            // only the last quarter (or half) of the list moves unless some lane's candidate
+                            // lands before it (12.81 -> 12.39 ms; a per-lane choice diverged: 13.56)
+                            const unsigned am = __activemask();
+                            if (__any_sync(am, d < bd[L / 2 - 1]))
                                 insert_sorted<L>(bd, bi, d, (yr + oy) * W + xr + ox0 + g0 + k);
-                            else
+                            else if (__any_sync(am, d < bd[3 * L / 4 - 1]))
                                 insert_sorted_tail<L, L / 2>(bd, bi, d, (yr + oy) * W + xr + ox0 + g0 + k);
+                            else
+                                insert_sorted_tail<L, 3 * L / 4>(bd, bi, d, (yr + oy) * W + xr + ox0 + g0 + k);
                         } else {
                             insert_sorted<L>(bd, bi, d, (yr + oy) * W + xr + ox0 + g0 + k);
                         }
