@@ -222,6 +222,34 @@ __device__ __forceinline__ float wiener_gains(const float *T, int lane, float s2
     return f2_lo(wsq) + f2_hi(wsq);
 }
 
+// hard_cols<16> on two 16-patch groups at once (rows 0-15 and 16-31 of T):
+// two independent chains for the scheduler to interleave.
+__device__ __forceinline__ int2 hard_cols_pair16(float *T, int lane, float thr)
+{
+    f2 va[16], vb[16];
+    load_cols<16>(T, lane, va);
+    load_cols<16>(T + 16 * kTS, lane, vb);
+    fwht2<16>(va);
+    fwht2<16>(vb);
+    const float thr_n = thr * sqrt_n<16>();
+    int ca = 0, cb = 0;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        const float alo = f2_lo(va[k]), ahi = f2_hi(va[k]), blo = f2_lo(vb[k]), bhi = f2_hi(vb[k]);
+        const bool kalo = fabsf(alo) > thr_n, kahi = fabsf(ahi) > thr_n;
+        const bool kblo = fabsf(blo) > thr_n, kbhi = fabsf(bhi) > thr_n;
+        ca += (kalo ? 1 : 0) + (kahi ? 1 : 0);
+        cb += (kblo ? 1 : 0) + (kbhi ? 1 : 0);
+        va[k] = f2_pack(kalo ? alo : 0.0f, kahi ? ahi : 0.0f);
+        vb[k] = f2_pack(kblo ? blo : 0.0f, kbhi ? bhi : 0.0f);
+    }
+    fwht2<16>(va);
+    fwht2<16>(vb);
+    store_cols<16>(T, lane, va);
+    store_cols<16>(T + 16 * kTS, lane, vb);
+    return make_int2(ca, cb);
+}
+
 __device__ __forceinline__ int hard_columns(float *T, int n, int lane, float thr)
 {
     switch (n) {
@@ -249,6 +277,24 @@ struct Window {
 // Loads a group's positions into lanes [base, base+n) (lane base+k gets patch
 // k; other lanes keep theirs).  Returns n, 0 if the list is invalid (the group
 // is skipped), or -n if it does not fit below row 32 (nothing loaded).
+// The same from the group's size n and this lane's list entry rid (entry
+// lane - base, loaded ahead by the caller).
+__device__ __forceinline__ int decode_group(const FilterArgs &a, int n, int rid, int lane, int base, int &py, int &px)
+{
+    if (n < 1 || n > a.n2 || n > kNMax || (n & (n - 1)) != 0) return 0;
+    if (base + n > 32) return -n;
+    const bool mine = lane >= base && lane < base + n;
+    const int id = mine ? rid : 0;
+    const int y = id / a.W, x = id - (id / a.W) * a.W;
+    const bool bad = mine && (id < 0 || y > a.H - 8 || x > a.W - 8);
+    if (__any_sync(0xffffffffu, bad)) return 0;
+    if (mine) {
+        py = y;
+        px = x;
+    }
+    return n;
+}
+
 __device__ __forceinline__ int load_group(const FilterArgs &a, int b, int r, int lane, int base, int &py, int &px)
 {
     const size_t gr = (size_t)b * a.R + r;
@@ -526,8 +572,15 @@ __device__ __forceinline__ void hard_batch(const FilterArgs &a, const Window &wi
     dct_reg(T, win, win.img, a.img + cbase, a.W, valid, lane, py, px, pack_dct());
     __syncwarp();
     const float thr = a.lambda * sig;
-    const int nharA = __reduce_add_sync(0xffffffffu, hard_columns(T, nA, lane, thr));
-    const int nharB = nB ? __reduce_add_sync(0xffffffffu, hard_columns(T + 16 * kTS, nB, lane, thr)) : 0;
+    int nharA, nharB;
+    if (nA == 16 && nB == 16) {
+        const int2 cc = hard_cols_pair16(T, lane, thr);
+        nharA = __reduce_add_sync(0xffffffffu, cc.x);
+        nharB = __reduce_add_sync(0xffffffffu, cc.y);
+    } else {
+        nharA = __reduce_add_sync(0xffffffffu, hard_columns(T, nA, lane, thr));
+        nharB = nB ? __reduce_add_sync(0xffffffffu, hard_columns(T + 16 * kTS, nB, lane, thr)) : 0;
+    }
     // 1/(sigma^2 N_har), or 1 when nothing survives, both times sigma^2
     const float wA = nharA > 0 ? 1.0f / (float)nharA : sig * sig;
     const float wB = nharB > 0 ? 1.0f / (float)nharB : sig * sig;
@@ -626,15 +679,57 @@ __global__ void __launch_bounds__(512) k_filter(FilterArgs a, int TR, int RH, in
         tc::cp_async_commit();
         tc::cp_async_wait<0>();
         __syncthreads();
+        // the next group's list is loaded while the current one is filtered
+        auto grab = [&](int per) {
+            int q = 0;
+            if (lane == 0) q = per * atomicAdd(&s_next[c & 1], 1);
+            return __shfl_sync(0xffffffffu, q, 0);
+        };
+        auto raw = [&](int q, int base, int &n, int &rid) {
+            const size_t gr = (size_t)b * a.R + ref_of(q);
+            n = a.n[gr];
+            if (lane >= base && lane - base < a.n2) rid = a.idx[gr * a.n2 + lane - base];
+        };
         if (WIENER) {
-            for (;;) {
-                int q = 0;
-                if (lane == 0) q = atomicAdd(&s_next[c & 1], 1);
-                q = __shfl_sync(0xffffffffu, q, 0);
-                if (q >= cnt) break;
+            int q = grab(1), rn = 0, rid = 0;
+            if (q < cnt) raw(q, 0, rn, rid);
+            while (q < cnt) {
+                const int qn = grab(1);
+                int nn = 0, nid = 0;
+                if (qn < cnt) raw(qn, 0, nn, nid);
                 int py = 0, px = 0;
-                const int n = load_group(a, b, ref_of(q), lane, 0, py, px);
+                const int n = decode_group(a, rn, rid, lane, 0, py, px);
                 if (n > 0) wiener_one(a, win, T, cbase, sig, n, lane, py, px, ka, tm);
+                q = qn;
+                rn = nn;
+                rid = nid;
+            }
+        } else if (a.n2 <= 16) {
+            // group pairs: lanes 0-15 hold the first group's entries, lanes 16-31 the second's
+            int q = grab(2), rnA = 0, rnB = 0, rid = 0;
+            if (q < cnt) raw(q, 0, rnA, rid);
+            if (q + 1 < cnt) raw(q + 1, 16, rnB, rid);
+            while (q < cnt) {
+                const int qn = grab(2);
+                int nA_ = 0, nB_ = 0, nid = 0;
+                if (qn < cnt) raw(qn, 0, nA_, nid);
+                if (qn + 1 < cnt) raw(qn + 1, 16, nB_, nid);
+                int py = 0, px = 0;
+                const int nA = decode_group(a, rnA, rid, lane, 0, py, px);
+                int nB = 0;
+                if (q + 1 < cnt) {
+                    nB = nA > 0 ? decode_group(a, rnB, rid, lane, 16, py, px) : -1;
+                    if (nB < 0) nB = -1;  // filtered on its own below
+                }
+                if (nA > 0) hard_batch(a, win, T, cbase, sig, nA, nB > 0 ? nB : 0, lane, py, px, ka);
+                if (nB < 0) {
+                    const int n = load_group(a, b, ref_of(q + 1), lane, 0, py, px);
+                    if (n > 0) hard_batch(a, win, T, cbase, sig, n, 0, lane, py, px, ka);
+                }
+                q = qn;
+                rnA = nA_;
+                rnB = nB_;
+                rid = nid;
             }
         } else {
             for (;;) {
