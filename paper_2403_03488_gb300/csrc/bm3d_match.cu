@@ -24,9 +24,10 @@
 // combines its 8 row sums (3 + 3 + 2 rows), again two offsets per packed
 // instruction, and updates its sorted list in registers (the 31-entry list
 // of n2 = 32 waits in the warp's TMEM lanes while the row sums are formed,
-// which keeps the kernel within 128 registers without spilling).  Packed
-// lanes round exactly like the scalar operations, so the distances are those
-// of the fixed association.
+// which keeps it out of the registers that phase needs, and its candidate
+// rows are scanned from the centre out, see below).  Packed lanes round
+// exactly like the scalar operations, so the distances are those of the
+// fixed association.
 //
 // Other steps: k_match_fp32, one thread per reference over a 16 x 8 tile,
 // register-blocked over 8 horizontally adjacent candidates (15 shared loads
