@@ -187,6 +187,30 @@ def test_filter_hard_parity_given_oracle_matches(oracle, C, H, W, sigmas):
         assert err.max() <= TOL, (b, err.max())
 
 
+@pytest.mark.parametrize("n2", [32, 8])
+def test_filter_hard_parity_other_group_sizes(oracle, n2):
+    """The first pass with groups of up to 32 patches (one group per warp)
+    and of up to 8 (two groups per warp, lists loaded one pair ahead): within
+    TOL of the oracle outside the hazard band."""
+    A = api()
+    _, noisy = synth.make_batch([33], 70, 75, 25.0)
+    img = noisy.astype(np.float64).astype(np.float32)
+    hard = A.default_bm3d_params().hard
+    hard.n2 = n2
+    sc = oracle.channel_sigmas(25.0, 1)
+    P = oracle.default_passes(25.0)[0]
+    P.n2 = n2
+    om = oracle.pass1_matches(img[0, 0], P, sc[0])
+    basic, pf, _ = oracle.bm3d_pass1(img[0], sc, P, band=BAND)
+    hard.tau = P.tau
+    out = host(A.bm3d_filter_hard(dev(img), dev(om["idx"][None].astype(np.int32)), dev(om["n"][None].astype(np.int32)),
+                                  list(sc), hard))
+    m = (pf & oracle.FLAG_THR) == 0
+    assert m.mean() > 0.5, "too many hazard pixels: %.3f" % m.mean()
+    err = np.abs(out[0] - basic)[:, m]
+    assert err.max() <= TOL, err.max()
+
+
 @pytest.mark.parametrize("C,H,W,sigma", [(1, 64, 80, 25.0), (3, 40, 57, 15.0), (1, 50, 50, 50.0)])
 def test_filter_wiener_parity_given_oracle_basic(oracle, C, H, W, sigma):
     A = api()
