@@ -176,8 +176,16 @@ __global__ void __launch_bounds__(kPT) k_match_pre(PreArgs a)
         __syncthreads();
         if (prefetch && yy < Y1) fetch_row(yy + 8);
         if (!active || yy < ys || yy > ye) continue;
-        for (int x = xs; x <= xe; ++x) {
-            if (x == x0 && yy == y0) continue;
+        // insertions deferred over groups of 8 candidates and then made in index order, one loop
+        // trip per inserting candidate (26.60 -> 25.95 ms per 16 x 1024^2 launch)
+        for (int xg = xs; xg <= xe; xg += 8) {
+          float dk[8];
+          unsigned ins = 0;
+#pragma unroll
+          for (int kk = 0; kk < 8; ++kk) {
+            const int x = xg + kk;
+            dk[kk] = 0.0f;
+            if (x > xe || (x == x0 && yy == y0)) continue;
             // 16-byte loads straight into two packed pairs (no repacking of float4 lanes)
             const ulonglong2 *q4 = reinterpret_cast<const ulonglong2 *>(S + (x - X0) * kCS);
             f2 acc[4];
@@ -202,10 +210,20 @@ __global__ void __launch_bounds__(kPT) k_match_pre(PreArgs a)
             const float h01 = __fadd_rn(__fadd_rn(f2_lo(s0), f2_hi(s0)), __fadd_rn(f2_lo(s1), f2_hi(s1)));
             const float h23 = __fadd_rn(__fadd_rn(f2_lo(s2), f2_hi(s2)), __fadd_rn(f2_lo(s3), f2_hi(s3)));
             const float d = __fmul_rn(__fadd_rn(h01, h23), 0.015625f);  // / 64, exact
+            dk[kk] = d;
             if (d <= tau) {
                 ++kept;
-                if (d < bd[L - 1]) insert_sorted<L>(bd, bi, d, yy * W + x);
+                if (d < bd[L - 1]) ins |= 1u << kk;
             }
+          }
+          while (ins) {
+            const int k = __ffs(ins) - 1;
+            ins &= ins - 1;
+            float d = dk[0];
+#pragma unroll
+            for (int j = 1; j < 8; ++j) d = k == j ? dk[j] : d;
+            insert_sorted<L>(bd, bi, d, yy * W + xg + k);
+          }
         }
     }
 
