@@ -147,14 +147,24 @@ __global__ void __launch_bounds__(kMT) k_match_k(const __grid_constant__ MatchKA
                     acc[c] = __fadd_rn(acc[c], h);
                 }
             }
+            unsigned ins = 0;
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
                 const int x = xc + c;
-                const float d = __fdiv_rn(acc[c], k2);
-                if (x <= xe && !(x == x0 && y == y0) && d <= tau) {
+                acc[c] = __fdiv_rn(acc[c], k2);
+                if (x <= xe && !(x == x0 && y == y0) && acc[c] <= tau) {
                     ++kept;
-                    if (d < bd[L - 1]) insert_sorted<L>(bd, bi, d, y * W + x);
+                    if (acc[c] < bd[L - 1]) ins |= 1u << c;
                 }
+            }
+            // insertions after the chunk's 8 distances, in index order
+            while (ins) {
+                const int c = __ffs(ins) - 1;
+                ins &= ins - 1;
+                float d = acc[0];
+#pragma unroll
+                for (int j = 1; j < 8; ++j) d = c == j ? acc[j] : d;
+                insert_sorted<L>(bd, bi, d, y * W + xc + c);
             }
         }
     }
@@ -320,8 +330,16 @@ __global__ void __launch_bounds__(kQT) k_match_pre_k(const __grid_constant__ Pre
         __syncthreads();
         if (yy < Y1) fetch_row(yy + K);
         if (!active || yy < ys || yy > ye) continue;
-        for (int x = xs; x <= xe; ++x) {
-            if (x == x0 && yy == y0) continue;
+        // insertions deferred over groups of 4 candidates, made in index order (65.2 -> 63.3 ms per
+        // 16 x 1024^2 launch)
+        for (int xg = xs; xg <= xe; xg += 4) {
+          float dk[4];
+          unsigned ins = 0;
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const int x = xg + kk;
+            dk[kk] = 0.0f;
+            if (x > xe || (x == x0 && yy == y0)) continue;
             const ulonglong2 *q4 = reinterpret_cast<const ulonglong2 *>(S + soff(x - X0));
             // partial sum j takes loads j NL/4 .. (j+1) NL/4 - 1 in order (load l holds pairs 2l, 2l+1)
             f2 acc[4];
@@ -344,10 +362,20 @@ __global__ void __launch_bounds__(kQT) k_match_pre_k(const __grid_constant__ Pre
             const float h01 = __fadd_rn(__fadd_rn(f2_lo(acc[0]), f2_hi(acc[0])), __fadd_rn(f2_lo(acc[1]), f2_hi(acc[1])));
             const float h23 = __fadd_rn(__fadd_rn(f2_lo(acc[2]), f2_hi(acc[2])), __fadd_rn(f2_lo(acc[3]), f2_hi(acc[3])));
             const float d = __fdiv_rn(__fadd_rn(h01, h23), (float)(K * K));
+            dk[kk] = d;
             if (d <= tau) {
                 ++kept;
-                if (d < bd[L - 1]) insert_sorted<L>(bd, bi, d, yy * W + x);
+                if (d < bd[L - 1]) ins |= 1u << kk;
             }
+          }
+          while (ins) {
+            const int k = __ffs(ins) - 1;
+            ins &= ins - 1;
+            float d = dk[0];
+#pragma unroll
+            for (int j = 1; j < 4; ++j) d = k == j ? dk[j] : d;
+            insert_sorted<L>(bd, bi, d, yy * W + xg + k);
+          }
         }
     }
 
