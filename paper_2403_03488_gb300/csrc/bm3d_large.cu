@@ -40,6 +40,7 @@
 
 #include "common.cuh"
 #include "fixed_point.cuh"
+#include "tc.cuh"
 #include "match_exact.cuh"
 
 namespace dn {
@@ -604,9 +605,11 @@ __global__ void __launch_bounds__(kFW * 32) k_filter_k(const __grid_constant__ F
         for (int i = threadIdx.x; i < rh * rw; i += blockDim.x) {
             const int ly = i / rw, lx = i - ly * rw;
             const size_t g = cbase + (size_t)(Y0 + ly) * W + X0 + lx;
-            simg[ly * a.RW + lx] = a.img[g];
-            if (WIENER) sbas[ly * a.RW + lx] = a.basic[g];
+            tc::cp_async4(tc::smem_u32(simg + ly * a.RW + lx), a.img + g);
+            if (WIENER) tc::cp_async4(tc::smem_u32(sbas + ly * a.RW + lx), a.basic + g);
         }
+        tc::cp_async_commit();
+        tc::cp_async_wait<0>();
         __syncthreads();
         for (int q = warp; q < cnt; q += kFW) {
             const size_t r = (size_t)b * a.R + (size_t)(ry0 + q / tw) * a.Rx + rx0 + q % tw;
