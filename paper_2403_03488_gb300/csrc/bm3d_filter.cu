@@ -533,6 +533,10 @@ __device__ __forceinline__ void aggregate(const FilterArgs &a, const Window &win
             case 1: agg_chunk<1>(a, win, T, cbase, s, lane, wk, wo, poff, gpos, pg); break;
             case 2: agg_chunk<2>(a, win, T, cbase, s, lane, wk, wo, poff, gpos, pg); break;
             case 4: agg_chunk<4>(a, win, T, cbase, s, lane, wk, wo, poff, gpos, pg); break;
+            case 16:  // the common first-pass size, unrolled (4.48 -> 4.42 ms; 32 unrolled was slower)
+                agg_chunk<8>(a, win, T, cbase, s, lane, wk, wo, poff, gpos, pg);
+                agg_chunk<8>(a, win, T, cbase, s + 8, lane, wk, wo, poff, gpos, pg);
+                break;
             default:
                 for (int k0 = s; k0 < s + n; k0 += 8) agg_chunk<8>(a, win, T, cbase, k0, lane, wk, wo, poff, gpos, pg);
                 break;
